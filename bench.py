@@ -1,0 +1,377 @@
+"""Benchmark of the rank-structured Coulomb convolution hot path on GB300.
+
+One step = one pass of the hot path over the density600_n8192 workload (a
+molecule-like density of 600 Gaussians on an 8192^3 grid of [-20,20]^3, Newton
+kernel with R_N = 61 terms): grid sampling of the factors, the 3 x 36600
+batched 1D convolutions giving the Hartree potential factors, the convolution
+matrices and the Hartree energy E_H.  The kernel tables (nodes, weights, cell
+integrals, spectra) are built once before timing.
+
+Prints one JSON line (see the metric/config keys).  `--impl reference` times
+the float64 CPU oracle on a bounded sample of the same workload instead.
+Under torchrun every rank runs its own density (weak scaling, no collective
+on the data path); the step time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+WORKLOAD = "density600_n8192"
+METRIC = "1D factor convolutions/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# GB300 unit counts for ALU roofs: 152 SMs, 128 FP32 lanes per SM (FMA = 2 flop)
+SMS = 152
+FP32_LANES = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--seed", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws, device=None):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(cfg, seed, budget_s=20.0):
+    """The oracle, as it stands, on a bounded sample of the workload: direct
+    O(n^2) convolutions (Toeplitz products) of a subset of the factor columns
+    with a subset of kernel terms, on all three axes."""
+    from oracle import cp as ocp
+    from oracle import kernel_vectors as okv
+    from oracle import sinc as osinc
+    n, b, M = cfg["n"], cfg["b"], cfg["M"]
+    g = workloads.mixture_for(WORKLOAD, seed)
+    t, a = osinc.conv_nodes(n, b, M)
+    k_sub, q_sub = 16, 4
+    qs = np.linspace(0, 2 * M, q_sub).round().astype(int)
+    P = okv.conv_kernel_vectors(n, b, t[qs], a[qs])
+    U = ocp.sample_gaussians(n, b, g["a"][:k_sub], g["X"][:k_sub])
+    done = 0
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        ocp.convolve_factors(U, P)
+        done += 3 * k_sub * q_sub
+        reps += 1
+        if time.perf_counter() - t0 > budget_s or reps >= 4:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": "convolutions/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{reps} x ({k_sub} Gaussians x {q_sub} kernel terms x 3 axes) direct length-{n} "
+                      f"convolutions of {WORKLOAD} ({done} convolutions, {dt:.1f} s)"}
+
+
+def run_reference(args, ws, rank):
+    cfg = workloads.CONFIGS[WORKLOAD]
+    if rank != 0:
+        return
+    from oracle import cp as ocp
+    from oracle import kernel_vectors as okv
+    from oracle import sinc as osinc
+    n, b, M = cfg["n"], cfg["b"], cfg["M"]
+    g = workloads.mixture_for(WORKLOAD, args.seed)
+    t, a = osinc.conv_nodes(n, b, M)
+    qs = np.array([0, 20, 40, 60])
+    P = okv.conv_kernel_vectors(n, b, t[qs], a[qs])
+    U = ocp.sample_gaussians(n, b, g["a"][:4], g["X"][:4])
+    per_step = 3 * 4 * len(qs)
+    for _ in range(args.warmup):
+        ocp.convolve_factors(U, P)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ocp.convolve_factors(U, P)
+    dt = time.perf_counter() - t0
+    value = per_step * args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "convolutions/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "R_f": cfg["R_f"], "R_N": 2 * M + 1,
+                   "sample_per_step": "4 Gaussians x 4 kernel terms x 3 axes (48 direct convolutions)"},
+        "cpu_baseline": {"value": value, "unit": "convolutions/s", "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": "48 direct length-8192 convolutions per step"},
+        "e2e": {"value": value, "unit": "convolutions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_1504_06289_gb300 as cpc
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = workloads.CONFIGS[WORKLOAD]
+    n, b, M, R_f = cfg["n"], cfg["b"], cfg["M"], cfg["R_f"]
+    P = cpc.make_newton_kernel(n, b, M, "conv", device=dev)
+    R_N = P.R_N
+    g = workloads.mixture_for(WORKLOAD, args.seed + rank)
+    a_h = torch.tensor(g["a"]).pin_memory()
+    X_h = torch.tensor(g["X"]).pin_memory()
+    c_h = torch.tensor(g["c"]).pin_memory()
+    a, X, c = a_h.to(dev), X_h.to(dev), c_h.to(dev)
+    stream = torch.cuda.current_stream(dev)
+    lib = cpc.load()
+
+    def buffers(prec):
+        W = torch.empty((3, R_f * R_N, n), dtype=torch.float64 if prec == "fp64" else torch.float32, device=dev)
+        U = torch.empty((3, R_f, n), dtype=torch.float64, device=dev)
+        E = torch.empty((), dtype=torch.float64, device=dev)
+        ws_c = torch.empty(lib.cp_convolve_workspace(P.handle, R_f, cpc._prec(prec)), dtype=torch.uint8, device=dev)
+        ws_g = torch.empty(max(256, lib.cp_hartree_energy_from_factors_workspace(P.handle, R_f)), dtype=torch.uint8,
+                           device=dev)
+        return W, U, E, ws_c, ws_g
+
+    def step(prec, bufs, ev=None):
+        W, U, E, ws_c, ws_g = bufs
+        st = lib.cp_sample_gaussians(n, b, R_f, cpc._ptr(a), cpc._ptr(X), cpc._ptr(U), cpc._stream(stream))
+        cpc.check(st, "sample")
+        if ev is not None:
+            ev[0].record(stream)
+        cpc.check(lib.cp_convolve(P.handle, R_f, cpc._ptr(U), cpc._ptr(W), cpc._prec(prec), cpc._ptr(ws_c),
+                                  ws_c.numel(), cpc._stream(stream)), "cp_convolve")
+        if ev is not None:
+            ev[1].record(stream)
+        cpc.check(lib.cp_hartree_energy_from_factors(P.handle, R_f, cpc._ptr(U), cpc._ptr(c), cpc._ptr(W), None,
+                                                     cpc._ptr(E), cpc._prec(prec), cpc._ptr(ws_g), ws_g.numel(),
+                                                     cpc._stream(stream)), "cp_hartree_energy_from_factors")
+        if ev is not None:
+            ev[2].record(stream)
+        return E
+
+    prec = args.precision
+    bufs = buffers(prec)
+    for _ in range(args.warmup):
+        step(prec, bufs)
+    torch.cuda.synchronize(dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        barrier(ws)
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for k in range(args.steps):
+            step(prec, bufs, evs[k])
+        stop.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(ws)
+    ms_total = start.elapsed_time(stop)
+    ms_total = max_over_ranks(ms_total, ws, dev)
+    E_fast = bufs[2].item()
+    conv_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    gram_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    ms_step = ms_total / args.steps
+    convs_per_step = 3 * R_f * R_N
+    value = ws * convs_per_step * args.steps / (ms_total * 1e-3)
+
+    # end to end through the public API: pinned host inputs -> device, step, E_H -> host
+    e2e_steps = max(1, min(args.steps, 5))
+    E_host = torch.empty((), dtype=torch.float64).pin_memory()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        a.copy_(a_h, non_blocking=True)
+        X.copy_(X_h, non_blocking=True)
+        c.copy_(c_h, non_blocking=True)
+        E = step(prec, bufs)
+        E_host.copy_(E, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
+    h2d = a_h.numel() * 8 + X_h.numel() * 8 + c_h.numel() * 8
+
+    # plain float64 GPU path on the same GPU (the baseline the reduced-precision form is compared with)
+    fp64 = None
+    if args.fp64_steps > 0 and prec != "fp64":
+        del bufs
+        torch.cuda.empty_cache()
+        b64 = buffers("fp64")
+        step("fp64", b64)
+        torch.cuda.synchronize(dev)
+        e64 = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.fp64_steps)]
+        s64, t64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s64.record(stream)
+        for k in range(args.fp64_steps):
+            step("fp64", b64, e64[k])
+        t64.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = s64.elapsed_time(t64) / args.fp64_steps
+        E64 = b64[2].item()
+        fp64 = {"ms_per_step": ms64, "value": convs_per_step / (ms64 * 1e-3),
+                "conv_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in e64])),
+                "contraction_ms": float(np.mean([e[1].elapsed_time(e[2]) for e in e64])),
+                "E_H": E64, "rel_err_E_H_of_fast_form": abs(E_fast / E64 - 1)}
+        del b64
+        torch.cuda.empty_cache()
+
+    if rank != 0:
+        return
+    peaks, peak_kind = load_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    clk = clocks.summary()
+    elem = 8 if prec == "fp64" else 4
+    # conv kernel algorithmic bytes per step: write all V_H factors, read spectra of U and p
+    conv_bytes = 3 * R_f * R_N * n * elem + 3 * R_f * (n + 1) * 2 * elem + R_N * (n + 1) * elem
+    conv_gbs = conv_bytes / (conv_ms * 1e-3) / 1e9
+    # contraction: unique Gram entries (symmetric) x 3 axes x R_N, 2 flop per multiply-add over n cells
+    gram_flops = 3 * R_N * (R_f * (R_f + 1) // 2) * n * 2
+    sm_mhz = clk["sm_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak_tf = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12 if prec != "fp64" else None
+    gram_tf = gram_flops / (gram_ms * 1e-3) / 1e12
+    kernels = {
+        "conv_kernel": {"ms": conv_ms, "bound": "hbm", "achieved": conv_gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": conv_gbs / hbm_peak, "algorithmic_bytes": conv_bytes},
+        "tri_gram_kernel": {"ms": gram_ms, "bound": "alu", "achieved": gram_tf, "unit": "TFLOP/s",
+                            "peak": alu_peak_tf, "frac": (gram_tf / alu_peak_tf) if alu_peak_tf else None,
+                            "algorithmic_flops": gram_flops,
+                            "peak_note": "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x median SM clock"},
+    }
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    d = kernels[dom]
+    roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
+                "unit": d["unit"], "frac": d["frac"], "traffic": None,
+                "peak_source": peak_kind if d["bound"] == "hbm" else "derived (unit counts x clock)"}
+    out = {
+        "metric": METRIC, "value": value, "unit": "convolutions/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "box": [-b, b], "R_f": R_f, "R_N": R_N,
+                   "convolutions_per_step": convs_per_step, "precision_form": prec,
+                   "l2": "each step writes the V_H factors (%.2f GB), far larger than L2" % (
+                       3 * R_f * R_N * n * elem / 1e9)},
+        "E_H": E_fast, "E_H_evals_per_s": ws * args.steps / (ms_total * 1e-3),
+        "phases_ms": {"convolve": conv_ms, "contraction": gram_ms},
+        "kernels": kernels, "roofline": roofline,
+        "fp64_gpu": fp64,
+        "speedup_vs_fp64_gpu": (fp64["ms_per_step"] / ms_step) if fp64 else None,
+        "e2e": {"value": ws * convs_per_step * e2e_steps / e2e_s, "unit": "convolutions/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clk,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, args.seed)
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

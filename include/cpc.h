@@ -1,0 +1,212 @@
+/*
+ * cpc.h -- C ABI of the GB300 (sm_103a) rank-structured 3D Coulomb convolution.
+ *
+ * The library convolves functions given in canonical (CP) format on an
+ * n x n x n cell-centred grid with the sinc-quadrature CP representation of
+ * the Newton kernel 1/|x|, and forms the rank-sum contractions that give the
+ * Hartree potential factors, the Hartree energy, Coulomb-matrix entries over
+ * product functions and assembled lattice sums (Khoromskaia & Khoromskij,
+ * arXiv:1504.06289: Sec. 2.5 Eqs. scal/had/conc/conv, Sec. 3.1, Sec. 3.2
+ * Eq. Factor_Mk_Conv, Sec. 5.1 Eqs. refTensor/CoulombLatTensCan, Appendix 3
+ * Eqs. galten/sinc_Newt/sinc_general).
+ *
+ * Conventions shared by every call
+ *   Grid:   box [-b, b]^3, n cells per axis of width h = 2b/n, cell centres
+ *           x_i = -b + (i + 1/2) h, i = 0..n-1.  n must be a power of two.
+ *   CP data: side matrices are stored "column-major n x R" and the three
+ *           axes are stacked, so a factor array for rank R is a contiguous
+ *           [3][R][n] block: element (axis l, column k, cell i) lives at
+ *           offset (l*R + k)*n + i.  Every column is n contiguous values.
+ *   Pointers: unless marked "host", every pointer is DEVICE memory owned by
+ *           the caller; the library never frees caller memory and, apart from
+ *           make_newton_kernel's tables, never allocates.  Work that needs
+ *           scratch takes a caller workspace (ws, ws_bytes) whose size comes
+ *           from the matching *_workspace query; ws must be 256-byte aligned.
+ *   Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *           default stream).  Calls are stream-ordered and do not
+ *           synchronise, except make_newton_kernel (which returns with its
+ *           tables ready) and the host-side validation before any launch.
+ *   Precision: CPC_FP64 computes in float64 throughout; CPC_FP32 runs the
+ *           bulk convolutions in float32 (factor outputs stored as float) and
+ *           the contractions with float32 products summed in float64;
+ *           CPC_SPLIT is reserved for compensated forms and returns
+ *           CPC_ERR_UNSUPPORTED where not implemented.  Kernel nodes, weights,
+ *           cell integrals and final cross-rank reductions are float64 in
+ *           every form.
+ *   Errors: every entry point returns CPC_OK (0) or a negative status; no
+ *           exception or abort crosses the ABI.  Arguments are validated on
+ *           the host before any launch; a failed CUDA call returns
+ *           CPC_ERR_CUDA and cpc_last_error() gives its message.
+ */
+#ifndef CPC_H
+#define CPC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CPC_OK 0
+#define CPC_ERR_INVALID -1      /* bad size, null pointer, inconsistent arguments */
+#define CPC_ERR_WORKSPACE -2    /* workspace missing, misaligned or too small */
+#define CPC_ERR_CUDA -3         /* a CUDA runtime call failed */
+#define CPC_ERR_DEVICE -4       /* a device-side check flagged an error */
+#define CPC_ERR_UNSUPPORTED -5  /* size or precision form not supported */
+
+#define CPC_FP64 0
+#define CPC_FP32 1
+#define CPC_SPLIT 2
+
+#define CPC_KERNEL_CONV 0   /* cell-centred offsets m = -(n-1)..n-1 (Sec. 3.1) */
+#define CPC_KERNEL_MASTER 1 /* 2n cells [jh,(j+1)h], j = -n..n-1 (Sec. 5.1, Eq. refTensor) */
+
+typedef struct cpc_kernel cpc_kernel; /* opaque; owns device tables */
+
+/* ---- a1/a2: the CP Newton kernel ------------------------------------------
+ * make_newton_kernel -- Appendix 3, Eqs. sinc_Newt and galten; Sec. 5.1 Eq. refTensor.
+ * Builds the R_N = 2M+1 term sinc quadrature 1/r ~ sum_q a_q exp(-t_q^2 r^2)
+ * (nodes t_q = exp(u0 + k hs), a_q = 2 hs t_q / sqrt(pi), k = -M..M, with hs
+ * and u0 balancing discretisation and truncation errors; all float64 on the
+ * host) and the Galerkin vectors p_q = a_q^{1/3} * (cell integrals of
+ * exp(-t_q^2 x^2)).  kind = CPC_KERNEL_CONV stores p_q[m], m = 0..n-1 (the
+ * vector is even in m) and its length-2n real spectrum for FFT convolution;
+ * CPC_KERNEL_MASTER stores p~_q[j], j = -n..n-1 (column j+n).
+ * n: power of two, 16 <= n <= 16384 (CONV: n <= 8192).  b > 0.  1 <= M <= 64.
+ * Allocates device memory for its tables (released by cpc_kernel_free) and
+ * synchronises the given stream before returning.  *out receives the handle. */
+int make_newton_kernel(int n, double b, int M, int kind, void* stream, cpc_kernel** out);
+
+/* The float64 host part of make_newton_kernel alone, with no device work:
+ * t[R_N], a[R_N], p[R_N][len] (len = n for CONV, 2n for MASTER), and the
+ * step hs and shift u0 of the quadrature, into caller HOST buffers (any
+ * pointer may be NULL).  Same argument rules as make_newton_kernel. */
+int make_newton_kernel_tables(int n, double b, int M, int kind, double* t, double* a, double* p,
+                              double* hs, double* u0);
+
+/* Scalars of a kernel (any pointer may be NULL). */
+int cpc_kernel_info(const cpc_kernel* P, int* n, double* b, int* M, int* R_N, int* kind,
+                    double* hs, double* u0);
+
+/* Host copies of the float64 tables: t[R_N], a[R_N] and p[R_N][len] with
+ * len = n (CONV) or 2n (MASTER).  Any pointer may be NULL.  host pointers. */
+int cpc_kernel_tables(const cpc_kernel* P, double* t, double* a, double* p);
+
+/* Releases the kernel's device tables and the handle (NULL is a no-op). */
+int cpc_kernel_free(cpc_kernel* P);
+
+/* ---- a3: grid sampling of Gaussians (Sec. 3.1, Eq. disc_GTO) --------------
+ * U[l][k][i] = exp(-a_k (x_i - X[k][l])^2) for R Gaussians exp(-a_k |x - X_k|^2).
+ * a: [R], X: [R][3] (row k holds X_k), U: [3][R][n]; all float64 device. */
+int cp_sample_gaussians(int n, double b, int R, const double* a, const double* X, double* U,
+                        void* stream);
+
+/* ---- A2: Hadamard products of factor pairs (Sec. 2.5, Eq. had) ------------
+ * For r = 0..n_pairs-1 and every axis l:
+ *   out[l][r][:] = F[l][pa[r]][:] * F[l][pb[r]][:]   (elementwise),
+ *   c_out[r]     = scale[r] * d[pa[r]] * d[pb[r]]      (scale may be NULL = 1).
+ * F: [3][n_in][n] float64; pa, pb: [n_pairs] int32 in [0, n_in); d: [n_in];
+ * out: [3][n_pairs][n]; c_out: [n_pairs].  Builds the CP factors of product
+ * functions g_mu g_nu and of densities from sampled primitives. */
+int cp_hadamard_pairs(int n, int n_in, int n_pairs, const int* pa, const int* pb,
+                      const double* F, const double* d, const double* scale,
+                      double* out, double* c_out, void* stream);
+
+/* ---- a4: batched 1D convolutions (Sec. 2.5 Eq. conv; V_H of Sec. 3.1) -----
+ * W[l][k*R_N + q][i] = sum_{j=0}^{n-1} U[l][k][j] * p_q[i - j],  i = 0..n-1,
+ * for every axis l, rank k < R_f and kernel term q < R_N of a CONV kernel:
+ * the factors of V_H = f * P_R.  U: [3][R_f][n] float64.  W: [3][R_f*R_N][n],
+ * float64 for CPC_FP64, float32 for CPC_FP32.  Implemented as length-2n real
+ * FFT convolutions in the chosen precision (the spectra of U are formed in
+ * float64).  Workspace: cp_convolve_workspace bytes. */
+size_t cp_convolve_workspace(const cpc_kernel* P, int R_f, int precision);
+int cp_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision,
+                void* ws, size_t ws_bytes, void* stream);
+
+/* ---- a5/a6: convolution matrices and the Hartree energy -------------------
+ * G[l][q][k'][k] = sum_i U[l][k'][i] W[l][k*R_N+q][i]   (Sec. 3.2,
+ *                  Eq. Factor_Mk_Conv: U^T (p_q * U), symmetric in k', k),
+ * E_H = h^3 sum_q sum_{k,k'} c_k c_k' prod_l G[l][q][k'][k]
+ *     = h^3 <f, P_R * f>      (Sec. 2.5 Eq. scal with Eq. conv).
+ * Runs cp_convolve into W (required: it receives the V_H factors, type as
+ * in cp_convolve), then the contraction.  c: [R_f] float64.  G: NULL or
+ * [3][R_N][R_f][R_f] float64 (needed by the adjoint).  E_H: one float64 on
+ * the device.  Workspace: cp_hartree_energy_workspace bytes. */
+size_t cp_hartree_energy_workspace(const cpc_kernel* P, int R_f, int precision);
+int cp_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const double* c, void* W,
+                      double* G, double* E_H, int precision, void* ws, size_t ws_bytes,
+                      void* stream);
+
+/* The contraction part of cp_hartree_energy alone: G and E_H from existing
+ * V_H factors W (as written by cp_convolve with the same precision).
+ * Workspace: cp_hartree_energy_from_factors_workspace bytes. */
+size_t cp_hartree_energy_from_factors_workspace(const cpc_kernel* P, int R_f);
+int cp_hartree_energy_from_factors(const cpc_kernel* P, int R_f, const double* U, const double* c,
+                                   const void* W, double* G, double* E_H, int precision, void* ws,
+                                   size_t ws_bytes, void* stream);
+
+/* ---- a7: adjoint of E_H ---------------------------------------------------
+ * Derived from Sec. 2.5 Eq. scal and Eq. conv (each Toeplitz factor of p_q is
+ * symmetric):
+ *   dU[l][m][:] = 2 h^3 c_m sum_q sum_k' c_k' H_q^l[m][k'] W[l][k'*R_N+q][:],
+ *   H_q^l = prod_{l' != l} G[l'][q]  (elementwise),
+ *   dc[m]       = 2 h^3 sum_q sum_k' c_k' prod_l G[l][q][m][k'].
+ * W and G as produced by cp_hartree_energy with the same precision.
+ * dU: [3][R_f][n] float64, dc: [R_f] float64 (dc may be NULL). */
+int cp_hartree_energy_adjoint(const cpc_kernel* P, int R_f, const double* c, const void* W,
+                              const double* G, double* dU, double* dc, int precision,
+                              void* stream);
+
+/* Chain rule from dU to the Gaussians of cp_sample_gaussians:
+ *   da[k]    = sum_l sum_i dU[l][k][i] * (-(x_i - X_kl)^2) * U[l][k][i],
+ *   dX[k][l] = sum_i dU[l][k][i] * 2 a_k (x_i - X_kl) * U[l][k][i].
+ * a [R], X [R][3], U, dU [3][R][n]; da [R], dX [R][3]; float64 device. */
+int cp_gaussian_param_grad(int n, double b, int R, const double* a, const double* X,
+                           const double* U, const double* dU, double* da, double* dX,
+                           void* stream);
+
+/* ---- a8: Coulomb matrix over product functions (Sec. 3.1, J_km) ----------
+ * For item t with CP factors u_r, r in [off[t], off[t+1]) (coefficients c_items[r])
+ * and the density rho = sum_m c_rho[m] u_m^(1) (x) u_m^(2) (x) u_m^(3):
+ *   J[t] = h^3 sum_r c_items[r] sum_m c_rho[m] sum_q prod_l <u_r^(l), W_rho[l][m*R_N+q]>,
+ * with W_rho = the V_H factors of rho (computed here into W_rho, type as in
+ * cp_convolve).  off: [n_items+1] int32 device, nondecreasing, off[0] = 0 and
+ * off[n_items] = n_factors (the caller's contract: offsets outside
+ * [0, n_factors] are clamped, never dereferenced); U_items: [3][n_factors][n];
+ * c_items: [n_factors]; U_rho: [3][R_rho][n]; c_rho: [R_rho]; J: [n_items]
+ * float64.  Item factors are concatenated into one row space, so items of
+ * uneven rank share tiles and no item leaves a tile idle; the contraction runs
+ * as one launch over (row tile, column group) work units.
+ * Workspace: coulomb_matrix_workspace bytes. */
+size_t coulomb_matrix_workspace(const cpc_kernel* P, int n_items, int n_factors, int R_rho,
+                                int precision);
+int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
+                   const double* c_items, int R_rho, const double* U_rho, const double* c_rho,
+                   void* W_rho, double* J, int precision, void* ws, size_t ws_bytes,
+                   void* stream);
+
+/* ---- a9/a10: assembled lattice sums (Sec. 5.1, Eq. CoulombLatTensCan) -----
+ * With a MASTER kernel p~_q and, per axis l, L[l] charge positions given as
+ * grid-cell edge indices e[l][k] in [0, n] (a charge at x = -b + e h):
+ *   S[l][q][i] = sum_{k < L[l]} p~_q[i - e[l][k]],  i = 0..n-1     (a9)
+ * and, when V is not NULL, the potential on the tensor sub-grid
+ *   V[s1][s2][s3] = h^-3 sum_q S[1][q][sub[0][s1]] S[2][q][sub[1][s2]] S[3][q][sub[2][s3]]
+ * for s_l < n_sub (a10; row-major, s3 fastest).  L: host int32[3], each in
+ * [0, 256]; edges: host int32 array of L[0]+L[1]+L[2] entries (axis 0
+ * first), each in [0, n]; sub: device int32 [3][n_sub] in [0, n) (entries
+ * outside are clamped), 1 <= n_sub <= 512.  R_N <= 129.
+ * S: [3][R_N][n] float64.  V: n_sub^3 float64 (CPC_FP64) or float32
+ * (CPC_FP32: float32 products with a float32 compensated sum). */
+int lattice_potential_sum(const cpc_kernel* master, const int* L, const int* edges, double* S,
+                          int n_sub, const int* sub, void* V, int precision, void* stream);
+
+/* ---- status -------------------------------------------------------------- */
+const char* cpc_status_string(int status);
+/* Message of the most recent failure in this thread ("" if none). */
+const char* cpc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPC_H */

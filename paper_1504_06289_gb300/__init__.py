@@ -1,0 +1,275 @@
+"""GB300 (sm_103a) rank-structured 3D Coulomb convolution.
+
+Thin Python binding over the C ABI in include/cpc.h (libcpc.so).  Every
+function here only marshals torch CUDA tensors into pointers and sizes; all
+arithmetic runs in the library's CUDA kernels (and its float64 host set-up of
+the kernel tables).  There is no CPU fallback: without libcpc.so or a CUDA
+device the calls raise.
+
+Method: Khoromskaia & Khoromskij, "Tensor numerical methods in quantum
+chemistry" (arXiv:1504.06289) -- CP convolution with the sinc-quadrature
+Newton kernel (Sec. 2.5, Sec. 3.1, Appendix 3), convolution matrices
+(Sec. 3.2), assembled lattice sums (Sec. 5.1).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from ._abi import KIND, PRECISION, CpcError, check, load
+
+__all__ = [
+    "NewtonKernel", "make_newton_kernel", "make_newton_kernel_tables", "cp_sample_gaussians", "cp_hadamard_pairs",
+    "cp_convolve", "cp_hartree_energy", "cp_hartree_energy_from_factors", "cp_hartree_energy_adjoint", "cp_gaussian_param_grad",
+    "coulomb_matrix", "lattice_potential_sum", "CPHartreeEnergy", "CpcError",
+]
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> C.c_void_p:
+    if t is None:
+        return C.c_void_p(None)
+    if not t.is_cuda or not t.is_contiguous():
+        raise CpcError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _prec(p: str) -> int:
+    try:
+        return PRECISION[p]
+    except KeyError:
+        raise CpcError(f"unknown precision {p!r}; use one of {sorted(PRECISION)}")
+
+
+def _out_dtype(precision: str):
+    return torch.float64 if precision == "fp64" else torch.float32
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+class NewtonKernel:
+    """Handle to a CP Newton kernel built by make_newton_kernel (owns device tables)."""
+
+    def __init__(self, handle: C.c_void_p, device):
+        self._h = handle
+        self.device = device
+        n, M, R_N, kind = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        b, hs, u0 = C.c_double(), C.c_double(), C.c_double()
+        check(load().cpc_kernel_info(handle, C.byref(n), C.byref(b), C.byref(M), C.byref(R_N),
+                                     C.byref(kind), C.byref(hs), C.byref(u0)), "cpc_kernel_info")
+        self.n, self.b, self.M, self.R_N = n.value, b.value, M.value, R_N.value
+        self.kind, self.hs, self.u0 = kind.value, hs.value, u0.value
+        self.h = 2.0 * self.b / self.n
+
+    @property
+    def handle(self) -> C.c_void_p:
+        return self._h
+
+    def tables(self):
+        """Host float64 copies (t, a, p) of the nodes, weights and kernel vectors."""
+        length = self.n if self.kind == KIND["conv"] else 2 * self.n
+        t = np.empty(self.R_N)
+        a = np.empty(self.R_N)
+        p = np.empty((self.R_N, length))
+        check(load().cpc_kernel_tables(self._h, t.ctypes.data, a.ctypes.data, p.ctypes.data),
+              "cpc_kernel_tables")
+        return t, a, p
+
+    def close(self):
+        if self._h is not None:
+            load().cpc_kernel_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_newton_kernel_tables(n: int, b: float, M: int, kind: str = "conv"):
+    """Host float64 tables (t, a, p, hs, u0) of the CP Newton kernel, no GPU needed."""
+    R_N = 2 * M + 1
+    length = n if kind == "conv" else 2 * n
+    t, a, p = np.empty(R_N), np.empty(R_N), np.empty((R_N, length))
+    hs, u0 = C.c_double(), C.c_double()
+    check(load().make_newton_kernel_tables(int(n), float(b), int(M), KIND[kind], t.ctypes.data, a.ctypes.data,
+                                           p.ctypes.data, C.byref(hs), C.byref(u0)), "make_newton_kernel_tables")
+    return t, a, p, hs.value, u0.value
+
+
+def make_newton_kernel(n: int, b: float, M: int, kind: str = "conv", device="cuda",
+                       stream=None) -> NewtonKernel:
+    """Build the R_N = 2M+1 term CP Newton kernel on the n-cell grid of [-b,b]^3."""
+    lib = load()
+    dev = torch.device(device)
+    with torch.cuda.device(dev):
+        h = C.c_void_p()
+        check(lib.make_newton_kernel(int(n), float(b), int(M), KIND[kind], _stream(stream),
+                                     C.byref(h)), "make_newton_kernel")
+    return NewtonKernel(h, dev)
+
+
+def cp_sample_gaussians(n: int, b: float, a: torch.Tensor, X: torch.Tensor, stream=None) -> torch.Tensor:
+    """U[l][k][i] = exp(-a_k (x_i - X_kl)^2) on the cell centres, shape (3, R, n)."""
+    R = a.numel()
+    U = torch.empty((3, R, n), dtype=torch.float64, device=a.device)
+    check(load().cp_sample_gaussians(int(n), float(b), R, _ptr(a), _ptr(X), _ptr(U), _stream(stream)),
+          "cp_sample_gaussians")
+    return U
+
+
+def cp_hadamard_pairs(F: torch.Tensor, pa: torch.Tensor, pb: torch.Tensor, d: torch.Tensor | None = None,
+                      scale: torch.Tensor | None = None, stream=None):
+    """Factors F[l][pa[r]] * F[l][pb[r]] (and coefficients scale*d[pa]*d[pb] if d is given)."""
+    _, n_in, n = F.shape
+    n_pairs = pa.numel()
+    out = torch.empty((3, n_pairs, n), dtype=torch.float64, device=F.device)
+    c_out = torch.empty(n_pairs, dtype=torch.float64, device=F.device) if d is not None else None
+    check(load().cp_hadamard_pairs(n, n_in, n_pairs, _ptr(pa), _ptr(pb), _ptr(F), _ptr(d), _ptr(scale),
+                                   _ptr(out), _ptr(c_out), _stream(stream)), "cp_hadamard_pairs")
+    return out, c_out
+
+
+def cp_convolve(P: NewtonKernel, U: torch.Tensor, precision: str = "fp64", W: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """V_H factors W[l][k*R_N+q] = U[l][k] * p_q, shape (3, R_f*R_N, n)."""
+    lib = load()
+    R_f = U.shape[1]
+    pr = _prec(precision)
+    if W is None:
+        W = torch.empty((3, R_f * P.R_N, P.n), dtype=_out_dtype(precision), device=U.device)
+    nb = lib.cp_convolve_workspace(P.handle, R_f, pr)
+    ws = _workspace(nb, U.device)
+    check(lib.cp_convolve(P.handle, R_f, _ptr(U), _ptr(W), pr, _ptr(ws), ws.numel(), _stream(stream)),
+          "cp_convolve")
+    return W
+
+
+def cp_hartree_energy(P: NewtonKernel, U: torch.Tensor, c: torch.Tensor, precision: str = "fp64",
+                      want_G: bool = False, W: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+                      stream=None):
+    """E_H = h^3 <f, P_R * f> as a device scalar, with the V_H factors W and
+    (optionally) the convolution matrices G[l][q] = U^T (p_q * U)."""
+    lib = load()
+    R_f = U.shape[1]
+    pr = _prec(precision)
+    if W is None:
+        W = torch.empty((3, R_f * P.R_N, P.n), dtype=_out_dtype(precision), device=U.device)
+    G = torch.empty((3, P.R_N, R_f, R_f), dtype=torch.float64, device=U.device) if want_G else None
+    E = torch.empty((), dtype=torch.float64, device=U.device)
+    nb = lib.cp_hartree_energy_workspace(P.handle, R_f, pr)
+    if ws is None or ws.numel() < nb:
+        ws = _workspace(nb, U.device)
+    check(lib.cp_hartree_energy(P.handle, R_f, _ptr(U), _ptr(c), _ptr(W), _ptr(G), _ptr(E), pr, _ptr(ws),
+                                ws.numel(), _stream(stream)), "cp_hartree_energy")
+    return E, W, G
+
+
+def cp_hartree_energy_from_factors(P: NewtonKernel, U: torch.Tensor, c: torch.Tensor, W: torch.Tensor,
+                                   precision: str = "fp64", want_G: bool = False, ws: torch.Tensor | None = None,
+                                   E: torch.Tensor | None = None, stream=None):
+    """E_H (device scalar) and optionally G from existing V_H factors W."""
+    lib = load()
+    R_f = U.shape[1]
+    G = torch.empty((3, P.R_N, R_f, R_f), dtype=torch.float64, device=U.device) if want_G else None
+    if E is None:
+        E = torch.empty((), dtype=torch.float64, device=U.device)
+    nb = lib.cp_hartree_energy_from_factors_workspace(P.handle, R_f)
+    if ws is None or ws.numel() < nb:
+        ws = _workspace(nb, U.device)
+    check(lib.cp_hartree_energy_from_factors(P.handle, R_f, _ptr(U), _ptr(c), _ptr(W), _ptr(G), _ptr(E),
+                                             _prec(precision), _ptr(ws), ws.numel(), _stream(stream)),
+          "cp_hartree_energy_from_factors")
+    return E, G
+
+
+def cp_hartree_energy_adjoint(P: NewtonKernel, c: torch.Tensor, W: torch.Tensor, G: torch.Tensor,
+                              precision: str = "fp64", want_dc: bool = True, stream=None):
+    """dE_H/dU (3, R_f, n) and dE_H/dc (R_f,) from the forward's W and G."""
+    R_f = c.numel()
+    dU = torch.empty((3, R_f, P.n), dtype=torch.float64, device=c.device)
+    dc = torch.empty(R_f, dtype=torch.float64, device=c.device) if want_dc else None
+    check(load().cp_hartree_energy_adjoint(P.handle, R_f, _ptr(c), _ptr(W), _ptr(G), _ptr(dU), _ptr(dc),
+                                           _prec(precision), _stream(stream)), "cp_hartree_energy_adjoint")
+    return dU, dc
+
+
+def cp_gaussian_param_grad(n: int, b: float, a: torch.Tensor, X: torch.Tensor, U: torch.Tensor,
+                           dU: torch.Tensor, stream=None):
+    """Chain rule dE/da (R,), dE/dX (R, 3) from dE/dU."""
+    R = a.numel()
+    da = torch.empty(R, dtype=torch.float64, device=a.device)
+    dX = torch.empty((R, 3), dtype=torch.float64, device=a.device)
+    check(load().cp_gaussian_param_grad(int(n), float(b), R, _ptr(a), _ptr(X), _ptr(U), _ptr(dU), _ptr(da),
+                                        _ptr(dX), _stream(stream)), "cp_gaussian_param_grad")
+    return da, dX
+
+
+def coulomb_matrix(P: NewtonKernel, off: torch.Tensor, U_items: torch.Tensor, c_items: torch.Tensor,
+                   U_rho: torch.Tensor, c_rho: torch.Tensor, precision: str = "fp64",
+                   W_rho: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
+    """J[t] = <item_t, V_H(rho)> for items in CP form (factor offsets `off`, int32)."""
+    lib = load()
+    n_items = off.numel() - 1
+    n_factors = U_items.shape[1]
+    R_rho = U_rho.shape[1]
+    pr = _prec(precision)
+    if W_rho is None:
+        W_rho = torch.empty((3, R_rho * P.R_N, P.n), dtype=_out_dtype(precision), device=U_rho.device)
+    J = torch.empty(n_items, dtype=torch.float64, device=U_rho.device)
+    nb = lib.coulomb_matrix_workspace(P.handle, n_items, n_factors, R_rho, pr)
+    if ws is None or ws.numel() < nb:
+        ws = _workspace(nb, U_rho.device)
+    check(lib.coulomb_matrix(P.handle, n_items, _ptr(off), n_factors, _ptr(U_items), _ptr(c_items), R_rho,
+                             _ptr(U_rho), _ptr(c_rho), _ptr(W_rho), _ptr(J), pr, _ptr(ws), ws.numel(),
+                             _stream(stream)), "coulomb_matrix")
+    return J, W_rho
+
+
+def lattice_potential_sum(P: NewtonKernel, edges, sub: torch.Tensor | None = None, precision: str = "fp64",
+                          stream=None):
+    """Assembled vectors S (3, R_N, n) for charges at grid-cell edges `edges`
+    (a list of three int arrays) and, if `sub` (3, n_sub) int32 is given, the
+    potential on the sub-grid (n_sub, n_sub, n_sub)."""
+    lib = load()
+    L = (C.c_int * 3)(*[len(e) for e in edges])
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(e, dtype=np.int32) for e in edges]))
+    S = torch.empty((3, P.R_N, P.n), dtype=torch.float64, device=P.device)
+    V = None
+    n_sub = 0
+    if sub is not None:
+        n_sub = sub.shape[1]
+        V = torch.empty((n_sub, n_sub, n_sub), dtype=_out_dtype(precision), device=P.device)
+    check(lib.lattice_potential_sum(P.handle, L, flat.ctypes.data, _ptr(S), n_sub, _ptr(sub), _ptr(V),
+                                    _prec(precision), _stream(stream)), "lattice_potential_sum")
+    return S, V
+
+
+class CPHartreeEnergy(torch.autograd.Function):
+    """E_H of a Gaussian mixture f = sum c_k exp(-a_k|x - X_k|^2) with gradients
+    in a, X and c through the hand-written adjoint kernels."""
+
+    @staticmethod
+    def forward(ctx, a, X, c, P: NewtonKernel, precision: str = "fp64"):
+        U = cp_sample_gaussians(P.n, P.b, a.detach(), X.detach())
+        E, W, G = cp_hartree_energy(P, U, c.detach(), precision, want_G=True)
+        ctx.save_for_backward(a.detach(), X.detach(), c.detach())
+        ctx.P, ctx.precision, ctx.U, ctx.W, ctx.G = P, precision, U, W, G
+        return E
+
+    @staticmethod
+    def backward(ctx, gE):
+        a, X, c = ctx.saved_tensors
+        P = ctx.P
+        dU, dc = cp_hartree_energy_adjoint(P, c, ctx.W, ctx.G, ctx.precision)
+        da, dX = cp_gaussian_param_grad(P.n, P.b, a, X, ctx.U, dU)
+        return gE * da, gE * dX, gE * dc, None, None

@@ -1,0 +1,76 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cpc.h"
+
+struct cpc_kernel {
+  int n = 0;          // cells per axis
+  double b = 0.0;     // half box edge
+  double h = 0.0;     // 2b/n
+  int M = 0;
+  int R_N = 0;        // 2M+1
+  int kind = 0;       // CPC_KERNEL_CONV / CPC_KERNEL_MASTER
+  int len = 0;        // n (CONV) or 2n (MASTER)
+  double hs = 0.0, u0 = 0.0;
+  std::vector<double> t, a, p;  // host float64 tables, p is [R_N][len]
+
+  // device tables
+  double* d_p = nullptr;        // [R_N][len]
+  // CONV only: spectrum of the length-2n even kernel, f = 0..n (real)
+  double* d_phat64 = nullptr;   // [R_N][n+1]
+  float* d_phat32 = nullptr;    // [R_N][n+1]
+  // FFT tables for complex size n: tw[e] = exp(-2 pi i e / n), e < n;
+  // half-angle table hw[f] = exp(-2 pi i f / (2n)), f <= n.
+  double2* d_tw64 = nullptr;
+  float2* d_tw32 = nullptr;
+  double2* d_hw64 = nullptr;
+  float2* d_hw32 = nullptr;
+};
+
+namespace cpc {
+
+// error reporting (thread-local message)
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+
+#define CPC_CUDA(call)                                   \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cpc::cuda_fail(e_, #call); \
+  } while (0)
+
+#define CPC_LAUNCH_CHECK(what)                                  \
+  do {                                                          \
+    cudaError_t e_ = cudaGetLastError();                        \
+    if (e_ != cudaSuccess) return cpc::cuda_fail(e_, what);     \
+  } while (0)
+
+inline bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// host: sinc nodes and Galerkin vectors (newton_kernel.cpp)
+void sinc_rule(int M, double h, double r_max, bool master, double* hs, double* u0);
+double gauss_cell_integral(double t, double x0, double x1);
+void build_twiddles(int n, std::vector<double>& tw_re, std::vector<double>& tw_im,
+                    std::vector<double>& hw_re, std::vector<double>& hw_im);
+
+// device-side builders (spectra.cu)
+int compute_kernel_spectrum(cpc_kernel* P, cudaStream_t s);
+
+// spectra of U columns into workspace (float64 and/or float32 copies)
+int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uhat64,
+                    float2* Uhat32, cudaStream_t s);
+// batched convolution from spectra
+int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W,
+                          int precision, cudaStream_t s);
+
+}  // namespace cpc

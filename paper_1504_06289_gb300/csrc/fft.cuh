@@ -1,0 +1,171 @@
+// Shared-memory Stockham FFT building blocks for sm_103a.
+//
+// A complex FFT of size NC = 2^LOGN is computed by NC/P threads, each holding
+// P = 2^LOGP points in registers per pass.  The first pass has radix
+// R1 = 2^(LOGN - (NP-1) LOGP) with B1 = P/R1 butterflies per thread, the other
+// NP-1 passes have radix P.  Passes read and write one shared-memory buffer in
+// place (all loads of a pass complete, a barrier, then all stores); the buffer
+// index is padded by one element per 16 so the strided stores of the early
+// passes do not collide in shared-memory banks.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace cpc {
+
+template <typename T> struct cvec;
+template <> struct cvec<double> { using type = double2; };
+template <> struct cvec<float> { using type = float2; };
+
+template <typename V> __device__ __forceinline__ V cmk(decltype(V::x) x, decltype(V::x) y) { V r; r.x = x; r.y = y; return r; }
+template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
+template <typename V> __device__ __forceinline__ V csub(V a, V b) { return cmk<V>(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return cmk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename V> __device__ __forceinline__ V cmulc(V a, V b) {
+  return cmk<V>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename V> __device__ __forceinline__ V cconj(V a) { return cmk<V>(a.x, -a.y); }
+// multiply by SIGN * i
+template <int SIGN, typename V> __device__ __forceinline__ V mul_si(V a) {
+  return SIGN > 0 ? cmk<V>(-a.y, a.x) : cmk<V>(a.y, -a.x);
+}
+
+__host__ __device__ constexpr int pad_index(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
+
+// cos(2 pi j / 32), sin(2 pi j / 32), j = 0..7 (first octant; the rest by symmetry)
+__device__ __forceinline__ double c32(int j) {
+  const double t[9] = {1.0, 0.98078528040323044913, 0.92387953251128675613, 0.83146961230254523708,
+                       0.70710678118654752440, 0.55557023301960222474, 0.38268343236508977173,
+                       0.19509032201612826785, 0.0};
+  return t[j];
+}
+
+// exp(SIGN * 2 pi i k / R) for R | 32 and 0 <= k < R/2, built from the octant table.
+template <typename V, int R, int SIGN>
+__device__ __forceinline__ V root(int k) {
+  using T = decltype(V::x);
+  int j = k * (32 / R);  // angle 2 pi j / 32, j in [0, 16)
+  double c, s;
+  if (j <= 8) { c = c32(j); s = c32(8 - j); }          // [0, pi/2]
+  else { c = -c32(16 - j); s = c32(j - 8); }            // (pi/2, pi)
+  return cmk<V>(T(c), T(SIGN * s));
+}
+
+// x * exp(SIGN 2 pi i k / R), with the trivial angles special-cased (k is a
+// compile-time constant after unrolling, so the branches fold away).
+template <typename V, int R, int SIGN>
+__device__ __forceinline__ V rotate(V x, int k) {
+  using T = decltype(V::x);
+  if (k == 0) return x;
+  if (4 * k == R) return mul_si<SIGN>(x);
+  if (8 * k == R) {  // (1 + SIGN i)/sqrt2
+    const T r = T(0.70710678118654752440);
+    return SIGN > 0 ? cmk<V>(r * (x.x - x.y), r * (x.x + x.y)) : cmk<V>(r * (x.x + x.y), r * (x.y - x.x));
+  }
+  if (8 * k == 3 * R) {  // (-1 + SIGN i)/sqrt2
+    const T r = T(0.70710678118654752440);
+    return SIGN > 0 ? cmk<V>(-r * (x.x + x.y), r * (x.x - x.y)) : cmk<V>(r * (x.y - x.x), -r * (x.x + x.y));
+  }
+  return cmul(x, root<V, R, SIGN>(k));
+}
+
+// In-register DFT of size R (power of two, R <= 32), unnormalised,
+// X[k] = sum_j v[j] exp(SIGN 2 pi i j k / R); radix-2 decimation in time.
+template <int R, int SIGN, typename V>
+__device__ __forceinline__ void dft(V* v) {
+  if constexpr (R == 1) {
+    return;
+  } else if constexpr (R == 2) {
+    V a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else {
+    V e[R / 2], o[R / 2];
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) { e[i] = v[2 * i]; o[i] = v[2 * i + 1]; }
+    dft<R / 2, SIGN>(e);
+    dft<R / 2, SIGN>(o);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      V t = rotate<V, R, SIGN>(o[k], k);
+      v[k] = cadd(e[k], t);
+      v[k + R / 2] = csub(e[k], t);
+    }
+  }
+}
+
+template <int LOGN, int LOGP>
+struct FftPlan {
+  static constexpr int NC = 1 << LOGN;
+  static constexpr int P = 1 << LOGP;
+  static constexpr int NP = (LOGN + LOGP - 1) / LOGP;  // number of passes
+  static constexpr int LOGR1 = LOGN - (NP - 1) * LOGP;
+  static constexpr int R1 = 1 << LOGR1;
+  static constexpr int B1 = P / R1;
+  static constexpr int TPF = NC / P;  // threads per FFT
+  static_assert(LOGN >= LOGP, "FFT smaller than one thread's points");
+};
+
+// Twiddle: x * w^e for w = exp(-2 pi i / NC) (SIGN < 0) or its conjugate.
+template <int SIGN, typename V>
+__device__ __forceinline__ V twiddle(V x, const V* __restrict__ tw, int e) {
+  V w = __ldg(tw + e);
+  return SIGN > 0 ? cmulc(x, w) : cmul(x, w);
+}
+
+// Load + twiddle + DFT of one pass from the padded shared buffer.
+// Butterfly j of this thread: j = b * (NC / (R*B)) + t; points j + r NC/R.
+template <int NC, int R, int B, int SIGN, typename V>
+__device__ __forceinline__ void pass_compute(const V* sbuf, V (&v)[B][R], int t, int Ns,
+                                             const V* __restrict__ tw) {
+  constexpr int stride = NC / R;
+  constexpr int nbf = NC / (R * B);
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = b * nbf + t;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b][r] = sbuf[pad_index(j + r * stride)];
+    if (Ns > 1) {
+      const int e0 = (j & (Ns - 1)) * (NC / (Ns * R));
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[b][r] = twiddle<SIGN>(v[b][r], tw, e0 * r);
+    }
+    dft<R, SIGN>(v[b]);
+  }
+}
+
+// Stockham store of one pass: output index (j/Ns)*Ns*R + j%Ns + r*Ns.
+template <int NC, int R, int B, typename V>
+__device__ __forceinline__ void pass_store(V* sbuf, const V (&v)[B][R], int t, int Ns) {
+  constexpr int nbf = NC / (R * B);
+#pragma unroll
+  for (int b = 0; b < B; ++b) {
+    const int j = b * nbf + t;
+    const int base = (j & ~(Ns - 1)) * R + (j & (Ns - 1));
+#pragma unroll
+    for (int r = 0; r < R; ++r) sbuf[pad_index(base + r * Ns)] = v[b][r];
+  }
+}
+
+// Middle passes 2..NP-1 (radix P, one butterfly per thread): smem -> smem.
+// Enter with the first pass stored; leave with pass NP-1 stored and synced.
+template <int LOGN, int LOGP, int SIGN, typename V>
+__device__ __forceinline__ void middle_passes(V* sbuf, int t, const V* __restrict__ tw) {
+  using PL = FftPlan<LOGN, LOGP>;
+  int Ns = PL::R1;
+#pragma unroll 1
+  for (int p = 1; p < PL::NP - 1; ++p) {
+    V v[1][PL::P];
+    pass_compute<PL::NC, PL::P, 1, SIGN>(sbuf, v, t, Ns, tw);
+    __syncthreads();
+    pass_store<PL::NC, PL::P, 1>(sbuf, v, t, Ns);
+    __syncthreads();
+    Ns *= PL::P;
+  }
+}
+
+}  // namespace cpc

@@ -1,0 +1,447 @@
+// Rank-sum contractions on CUDA cores.
+//
+// tri_gram_kernel computes, for rows r and columns s of two CP factor sets,
+//   prod(r, s) = prod_{l=1..3} sum_i A[l][r][i] * B[l][col(s)][i]
+// (three Gram matrices multiplied elementwise, Sec. 2.5 Eq. scal) and reduces
+// it with weights:
+//   MODE_EH   : sum_{r,s} wr[r] ws[s] prod(r,s) over symmetric tile pairs,
+//               one partial per CTA (E_H, and the convolution matrices
+//               M_q^(l) = U^T (p_q * U) of Sec. 3.2 Eq. Factor_Mk_Conv when
+//               requested);
+//   MODE_ROWS : per-row sums sum_s ws[s] prod(r,s) (Coulomb matrix rows).
+// Tiles are 64 x 64 with 256 threads (4 x 4 outputs each); the K dimension
+// (grid cells) is staged through shared memory in chunks.  float64 form:
+// float64 FMA.  float32 form: float32 products and float32 partial sums over a
+// chunk, promoted to float64 once per chunk.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "cpc_internal.h"
+
+namespace cpc {
+
+constexpr int TM = 64, TN = 64, TPB = 256;
+
+template <typename TB> struct GramCfg;
+template <> struct GramCfg<double> { static constexpr int KC = 16; using TC = double; };
+template <> struct GramCfg<float> { static constexpr int KC = 32; using TC = float; };
+
+enum { MODE_EH = 0, MODE_ROWS = 1 };
+
+// Accumulate one 64x64 Gram tile of axis l into acc[4][4] (float64).
+// A rows: A + r*n (double); B columns: B + (s*col_stride + col_off)*n (TB).
+template <typename TB>
+__device__ __forceinline__ void gram_tile(int n, int M, int N, const double* __restrict__ A, int r0,
+                                          const TB* __restrict__ B, int s0, int col_stride, int col_off,
+                                          double (&acc)[4][4]) {
+  using C = GramCfg<TB>;
+  using TC = typename C::TC;
+  constexpr int KC = C::KC;
+  __shared__ TC As[KC][TM + 1];
+  __shared__ TC Bs[KC][TN + 1];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+  for (int i0 = 0; i0 < n; i0 += KC) {
+    for (int idx = tid; idx < TM * KC; idx += TPB) {
+      const int row = idx / KC, kk = idx % KC;
+      const int r = r0 + row, i = i0 + kk;
+      As[kk][row] = (r < M && i < n) ? TC(A[(size_t)r * n + i]) : TC(0);
+      const int s = s0 + row;
+      Bs[kk][row] = (s < N && i < n) ? TC(B[((size_t)s * col_stride + col_off) * n + i]) : TC(0);
+    }
+    __syncthreads();
+    TC part[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) part[a][b] = TC(0);
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      TC av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) part[a][b] = fma(av[a], bv[b], part[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] += double(part[a][b]);
+    __syncthreads();
+  }
+}
+
+template <typename TB, int MODE>
+__global__ void __launch_bounds__(TPB)
+tri_gram_kernel(int n, int M, int N, const double* __restrict__ A, long long a_axis,
+                const TB* __restrict__ B, long long b_axis, int col_stride,
+                const double* __restrict__ wr, const double* __restrict__ wcol, int wcol_div,
+                double* __restrict__ partial, double* __restrict__ G, int tiles_per_cta) {
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  __shared__ double red[TPB / 32];
+  if (MODE == MODE_EH) {
+    // blockIdx.x: symmetric tile pair (rt <= st); blockIdx.y: kernel term q
+    const int p = blockIdx.x, q = blockIdx.y;
+    int st = 0;
+    while ((st + 1) * (st + 2) / 2 <= p) ++st;
+    const int rt = p - st * (st + 1) / 2;
+    const int r0 = rt * TM, s0 = st * TN;
+    double prod[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) prod[a][b] = 1.0;
+    for (int l = 0; l < 3; ++l) {
+      double acc[4][4];
+      gram_tile<TB>(n, M, N, A + l * a_axis, r0, B + l * b_axis, s0, col_stride, q, acc);
+      if (G) {
+        // G[l][q][r][s] (and the mirror for off-diagonal tiles)
+        double* Gq = G + ((size_t)l * gridDim.y + q) * (size_t)M * M;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) {
+            const int r = r0 + ty + 16 * a, s = s0 + tx + 16 * b;
+            if (r < M && s < N) {
+              Gq[(size_t)r * M + s] = acc[a][b];
+              if (rt != st) Gq[(size_t)s * M + r] = acc[a][b];
+            }
+          }
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) prod[a][b] *= acc[a][b];
+    }
+    double sum = 0.0;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int r = r0 + ty + 16 * a;
+      const double w_r = (r < M) ? wr[r] : 0.0;
+      double row = 0.0;
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int s = s0 + tx + 16 * b;
+        row += ((s < N) ? wcol[s] : 0.0) * prod[a][b];
+      }
+      sum += w_r * row;
+    }
+    if (rt != st) sum *= 2.0;
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((tid & 31) == 0) red[tid >> 5] = sum;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < TPB / 32; ++w) s += red[w];
+      partial[(size_t)q * gridDim.x + p] = s;
+    }
+  } else {
+    // blockIdx.x: row tile; blockIdx.y: group of tiles_per_cta column tiles
+    const int r0 = blockIdx.x * TM;
+    const int n_ct = (N + TN - 1) / TN;
+    double rowacc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int ct = blockIdx.y * tiles_per_cta; ct < min(n_ct, (int)(blockIdx.y + 1) * tiles_per_cta); ++ct) {
+      const int s0 = ct * TN;
+      double prod[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) prod[a][b] = 1.0;
+      for (int l = 0; l < 3; ++l) {
+        double acc[4][4];
+        gram_tile<TB>(n, M, N, A + l * a_axis, r0, B + l * b_axis, s0, col_stride, 0, acc);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) prod[a][b] *= acc[a][b];
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int s = s0 + tx + 16 * b;
+          rowacc[a] += ((s < N) ? wcol[s / wcol_div] : 0.0) * prod[a][b];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      double v = rowacc[a];
+      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
+      const int r = r0 + ty + 16 * a;
+      if (tx == 0 && r < M) partial[(size_t)blockIdx.y * M + r] = v;
+    }
+  }
+}
+
+// E_H = h^3 * sum of partials, summed in a fixed order by one block.
+__global__ void finalize_sum_kernel(const double* __restrict__ partial, long long count, double scale,
+                                    double* __restrict__ out) {
+  __shared__ double red[1024 / 32];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < count; i += blockDim.x) s += partial[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+    *out = scale * t;
+  }
+}
+
+// J[t] = h^3 sum_{r in item t} c[r] sum_g rowpart[g][r]
+__global__ void item_reduce_kernel(int n_items, const int* __restrict__ off, const double* __restrict__ c,
+                                   const double* __restrict__ rowpart, int groups, int M, double scale,
+                                   double* __restrict__ J) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_items) return;
+  double s = 0.0;
+  const int r_lo = max(0, min(off[t], M)), r_hi = max(r_lo, min(off[t + 1], M));
+  for (int r = r_lo; r < r_hi; ++r) {
+    double rs = 0.0;
+    for (int g = 0; g < groups; ++g) rs += rowpart[(size_t)g * M + r];
+    s += c[r] * rs;
+  }
+  J[t] = scale * s;
+}
+
+// ---- adjoint --------------------------------------------------------------
+// dU[l][m][i] = sum_{kk} Bl[m][kk] W[l][kk][i],  kk = k'*R_N + q,
+// Bl[m][kk] = 2 h^3 c_m c_k' prod_{l' != l} G[l'][q][m][k'], formed while loading.
+template <typename TB>
+__global__ void __launch_bounds__(TPB)
+adjoint_gemm_kernel(int n, int R_f, int R_N, const double* __restrict__ c, const double* __restrict__ G,
+                    const TB* __restrict__ W, double scale2h3, double* __restrict__ dU) {
+  using Cf = GramCfg<TB>;
+  using TC = typename Cf::TC;
+  constexpr int KC = Cf::KC;
+  __shared__ TC As[KC][TM + 1];
+  __shared__ TC Bs[KC][TN + 1];
+  const int l = blockIdx.z;
+  const int m0 = blockIdx.y * TM, i0 = blockIdx.x * TN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int l1 = (l + 1) % 3, l2 = (l + 2) % 3;
+  const size_t GM = (size_t)R_f * R_f;
+  const TB* Wl = W + (size_t)l * R_f * R_N * n;
+  const int K = R_f * R_N;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += KC) {
+    for (int idx = tid; idx < TM * KC; idx += TPB) {
+      // A tile: rows m, columns kk (kk fastest across threads for G reads along k'? keep simple)
+      const int row = idx / KC, kk = idx % KC;
+      const int m = m0 + row, k = k0 + kk;
+      TC v = TC(0);
+      if (m < R_f && k < K) {
+        const int kp = k / R_N, q = k - kp * R_N;
+        const size_t gi = (size_t)q * GM + (size_t)m * R_f + kp;
+        v = TC(scale2h3 * c[m] * c[kp] * G[(size_t)l1 * R_N * GM + gi] * G[(size_t)l2 * R_N * GM + gi]);
+      }
+      As[kk][row] = v;
+    }
+    for (int idx = tid; idx < TN * KC; idx += TPB) {
+      const int kk = idx / TN, col = idx % TN;
+      const int k = k0 + kk, i = i0 + col;
+      Bs[kk][col] = (k < K && i < n) ? TC(Wl[(size_t)k * n + i]) : TC(0);
+    }
+    __syncthreads();
+    TC part[4][4] = {};
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      TC av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = As[kk][ty + 16 * a];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = Bs[kk][tx + 16 * b];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) part[a][b] = fma(av[a], bv[b], part[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] += double(part[a][b]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int m = m0 + ty + 16 * a, i = i0 + tx + 16 * b;
+      if (m < R_f && i < n) dU[((size_t)l * R_f + m) * n + i] = acc[a][b];
+    }
+}
+
+// dc[m] = 2 h^3 sum_q sum_k' c_k' prod_l G[l][q][m][k']  (one warp per m)
+__global__ void adjoint_coef_kernel(int R_f, int R_N, const double* __restrict__ c,
+                                    const double* __restrict__ G, double scale2h3, double* __restrict__ dc) {
+  const int m = blockIdx.x;
+  const size_t GM = (size_t)R_f * R_f;
+  double s = 0.0;
+  for (int q = 0; q < R_N; ++q)
+    for (int kp = threadIdx.x; kp < R_f; kp += blockDim.x) {
+      const size_t gi = (size_t)q * GM + (size_t)m * R_f + kp;
+      s += c[kp] * G[gi] * G[(size_t)R_N * GM + gi] * G[2 * (size_t)R_N * GM + gi];
+    }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) dc[m] = scale2h3 * s;
+}
+
+// ---------------------------------------------------------------------------
+size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision);
+int check_conv_args(const cpc_kernel* P, int R_f, const void* U, const void* W, int precision,
+                    void* ws, size_t ws_bytes, const char* who);
+int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision, void* ws,
+                 cudaStream_t s);
+
+static int tiles(int x) { return (x + TM - 1) / TM; }
+
+size_t eh_partials(const cpc_kernel* P, int R_f) {
+  const int T = tiles(R_f);
+  return size_t(T) * (T + 1) / 2 * P->R_N;
+}
+
+int launch_eh(const cpc_kernel* P, int R_f, const double* U, const double* c, const void* W,
+              double* G, double* E_H, int precision, double* partial, cudaStream_t s) {
+  const int n = P->n;
+  const int T = tiles(R_f);
+  dim3 grid(T * (T + 1) / 2, P->R_N);
+  const long long a_axis = (long long)R_f * n;
+  const long long b_axis = (long long)R_f * P->R_N * n;
+  if (precision == CPC_FP64)
+    tri_gram_kernel<double, MODE_EH><<<grid, TPB, 0, s>>>(n, R_f, R_f, U, a_axis, static_cast<const double*>(W),
+                                                           b_axis, P->R_N, c, c, 1, partial, G, 0);
+  else
+    tri_gram_kernel<float, MODE_EH><<<grid, TPB, 0, s>>>(n, R_f, R_f, U, a_axis, static_cast<const float*>(W),
+                                                          b_axis, P->R_N, c, c, 1, partial, G, 0);
+  CPC_LAUNCH_CHECK("tri_gram_kernel(EH)");
+  finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, (long long)grid.x * grid.y, P->h * P->h * P->h, E_H);
+  CPC_LAUNCH_CHECK("finalize_sum_kernel");
+  return CPC_OK;
+}
+
+}  // namespace cpc
+
+using namespace cpc;
+
+extern "C" size_t cp_hartree_energy_workspace(const cpc_kernel* P, int R_f, int precision) {
+  if (!P || R_f <= 0) return 0;
+  return cp_convolve_workspace(P, R_f, precision) + align256(sizeof(double) * eh_partials(P, R_f));
+}
+
+extern "C" int cp_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const double* c, void* W,
+                                 double* G, double* E_H, int precision, void* ws, size_t ws_bytes,
+                                 void* stream) {
+  clear_error();
+  int st = check_conv_args(P, R_f, U, W, precision, ws, ws_bytes, "cp_hartree_energy");
+  if (st) return st;
+  if (!c || !E_H) return fail(CPC_ERR_INVALID, "cp_hartree_energy: NULL c or E_H");
+  if (ws_bytes < cp_hartree_energy_workspace(P, R_f, precision))
+    return fail(CPC_ERR_WORKSPACE, "cp_hartree_energy: workspace too small");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = run_convolve(P, R_f, U, W, precision, ws, s);
+  if (st) return st;
+  double* partial = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_f, precision));
+  return launch_eh(P, R_f, U, c, W, G, E_H, precision, partial, s);
+}
+
+extern "C" size_t cp_hartree_energy_from_factors_workspace(const cpc_kernel* P, int R_f) {
+  if (!P || R_f <= 0) return 0;
+  return align256(sizeof(double) * eh_partials(P, R_f));
+}
+
+extern "C" int cp_hartree_energy_from_factors(const cpc_kernel* P, int R_f, const double* U, const double* c,
+                                              const void* W, double* G, double* E_H, int precision, void* ws,
+                                              size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!P || P->kind != CPC_KERNEL_CONV) return fail(CPC_ERR_INVALID, "cp_hartree_energy_from_factors: needs a CONV kernel");
+  if (R_f <= 0 || !U || !c || !W || !E_H) return fail(CPC_ERR_INVALID, "cp_hartree_energy_from_factors: bad arguments");
+  if (precision != CPC_FP64 && precision != CPC_FP32)
+    return fail(CPC_ERR_UNSUPPORTED, "cp_hartree_energy_from_factors: precision form not implemented");
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < cp_hartree_energy_from_factors_workspace(P, R_f))
+    return fail(CPC_ERR_WORKSPACE, "cp_hartree_energy_from_factors: workspace missing, misaligned or too small");
+  return launch_eh(P, R_f, U, c, W, G, E_H, precision, static_cast<double*>(ws), static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int cp_hartree_energy_adjoint(const cpc_kernel* P, int R_f, const double* c, const void* W,
+                                         const double* G, double* dU, double* dc, int precision,
+                                         void* stream) {
+  clear_error();
+  if (!P || P->kind != CPC_KERNEL_CONV) return fail(CPC_ERR_INVALID, "cp_hartree_energy_adjoint: needs a CONV kernel");
+  if (R_f <= 0 || !c || !W || !G || !dU) return fail(CPC_ERR_INVALID, "cp_hartree_energy_adjoint: bad arguments");
+  if (precision != CPC_FP64 && precision != CPC_FP32)
+    return fail(CPC_ERR_UNSUPPORTED, "cp_hartree_energy_adjoint: precision form not implemented");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n = P->n;
+  const double scale = 2.0 * P->h * P->h * P->h;
+  dim3 grid((n + TN - 1) / TN, tiles(R_f), 3);
+  if (precision == CPC_FP64)
+    adjoint_gemm_kernel<double><<<grid, TPB, 0, s>>>(n, R_f, P->R_N, c, G, static_cast<const double*>(W), scale, dU);
+  else
+    adjoint_gemm_kernel<float><<<grid, TPB, 0, s>>>(n, R_f, P->R_N, c, G, static_cast<const float*>(W), scale, dU);
+  CPC_LAUNCH_CHECK("adjoint_gemm_kernel");
+  if (dc) {
+    adjoint_coef_kernel<<<R_f, 32, 0, s>>>(R_f, P->R_N, c, G, scale, dc);
+    CPC_LAUNCH_CHECK("adjoint_coef_kernel");
+  }
+  return CPC_OK;
+}
+
+// ---- Coulomb matrix ---------------------------------------------------------
+namespace cpc {
+static int coulomb_groups(int R_rho, int R_N, int tiles_per_cta) {
+  const int n_ct = tiles(R_rho * R_N);
+  return (n_ct + tiles_per_cta - 1) / tiles_per_cta;
+}
+static const int kCoulombTilesPerCta = 8;
+}  // namespace cpc
+
+extern "C" size_t coulomb_matrix_workspace(const cpc_kernel* P, int n_items, int n_factors, int R_rho,
+                                           int precision) {
+  if (!P || n_items <= 0 || n_factors <= 0 || R_rho <= 0) return 0;
+  const size_t groups = coulomb_groups(R_rho, P->R_N, kCoulombTilesPerCta);
+  return cp_convolve_workspace(P, R_rho, precision) + align256(sizeof(double) * groups * n_factors);
+}
+
+extern "C" int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
+                              const double* c_items, int R_rho, const double* U_rho, const double* c_rho,
+                              void* W_rho, double* J, int precision, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  int st = check_conv_args(P, R_rho, U_rho, W_rho, precision, ws, ws_bytes, "coulomb_matrix");
+  if (st) return st;
+  if (n_items <= 0 || !off || !U_items || !c_items || !c_rho || !J)
+    return fail(CPC_ERR_INVALID, "coulomb_matrix: bad item arguments");
+  if (n_factors <= 0) return fail(CPC_ERR_INVALID, "coulomb_matrix: no item factors");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (ws_bytes < coulomb_matrix_workspace(P, n_items, n_factors, R_rho, precision))
+    return fail(CPC_ERR_WORKSPACE, "coulomb_matrix: workspace too small");
+  st = run_convolve(P, R_rho, U_rho, W_rho, precision, ws, s);
+  if (st) return st;
+  double* rowpart = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_rho, precision));
+  const int n = P->n;
+  const int N = R_rho * P->R_N;
+  const int groups = coulomb_groups(R_rho, P->R_N, kCoulombTilesPerCta);
+  dim3 grid(tiles(n_factors), groups);
+  const long long a_axis = (long long)n_factors * n;
+  const long long b_axis = (long long)N * n;
+  if (precision == CPC_FP64)
+    tri_gram_kernel<double, MODE_ROWS><<<grid, TPB, 0, s>>>(n, n_factors, N, U_items, a_axis,
+        static_cast<const double*>(W_rho), b_axis, 1, nullptr, c_rho, P->R_N, rowpart, nullptr, kCoulombTilesPerCta);
+  else
+    tri_gram_kernel<float, MODE_ROWS><<<grid, TPB, 0, s>>>(n, n_factors, N, U_items, a_axis,
+        static_cast<const float*>(W_rho), b_axis, 1, nullptr, c_rho, P->R_N, rowpart, nullptr, kCoulombTilesPerCta);
+  CPC_LAUNCH_CHECK("tri_gram_kernel(ROWS)");
+  item_reduce_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(n_items, off, c_items, rowpart, groups, n_factors,
+                                                         P->h * P->h * P->h, J);
+  CPC_LAUNCH_CHECK("item_reduce_kernel");
+  return CPC_OK;
+}

@@ -1,0 +1,343 @@
+// Batched 1D convolutions of CP factors with the Newton-kernel vectors
+// (Sec. 2.5, Eq. conv; the V_H factors of Sec. 3.1) by length-2n real FFTs.
+//
+// Each column is zero-padded to 2n real points; a length-2n real transform is
+// an n-point complex transform of the packed pairs (x[2j], x[2j+1]) plus a
+// half-angle post/pre-processing step.  The linear convolution with a kernel
+// given on offsets -(n-1)..n-1 is exact on outputs 0..n-1 under the 2n
+// circular convolution (the wrap-around lands on outputs n..2n-1, which are
+// never formed).
+//
+//   spectra_kernel : float64 forward transforms of factor columns (and of the
+//                    kernel vectors at set-up), stored as n+1 Hermitian bins.
+//   conv_kernel    : per (column, q) item, multiply by the kernel spectrum,
+//                    inverse transform, keep the first n outputs.  One CTA
+//                    holds `slots` transforms in shared memory and walks the
+//                    items in a grid-stride loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "cpc_internal.h"
+#include "fft.cuh"
+
+namespace cpc {
+
+namespace {
+
+constexpr int kMaxLogN = 13;  // n <= 8192 for convolution kernels
+constexpr int kMinLogN = 4;
+
+template <int LOGN> constexpr int pick_logp() { return LOGN <= 4 ? LOGN - 1 : 4; }
+
+template <int LOGN>
+struct Geometry {
+  static constexpr int LOGP = pick_logp<LOGN>();
+  using PL = FftPlan<LOGN, LOGP>;
+  static constexpr int slots = PL::TPF >= 128 ? 1 : 128 / PL::TPF;
+  static constexpr int threads = slots * PL::TPF;
+};
+
+// ---------------------------------------------------------------------------
+// forward spectra (float64).  mode 0: factor columns (zero padded to 2n);
+// mode 1: even kernel vectors p[0..n-1] extended to the 2n circle.
+template <int LOGN>
+__global__ void __launch_bounds__(Geometry<LOGN>::threads)
+spectra_kernel(int mode, const double* __restrict__ src, int ncols, double2* __restrict__ out64,
+               float2* __restrict__ out32, double* __restrict__ re64, float* __restrict__ re32,
+               const double2* __restrict__ hw, const double2* __restrict__ tw) {
+  using G = Geometry<LOGN>;
+  using PL = typename G::PL;
+  constexpr int NC = PL::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* sbuf = reinterpret_cast<double2*>(smem_raw) + (threadIdx.x / PL::TPF) * padded_len(NC);
+  const int slot = threadIdx.x / PL::TPF;
+  const int t = threadIdx.x % PL::TPF;
+  for (int g = blockIdx.x; g * G::slots < ncols; g += gridDim.x) {
+    const int col = g * G::slots + slot;
+    const bool active = col < ncols;
+    const double* x = src + (size_t)(active ? col : ncols - 1) * NC;
+    {
+      double2 v[PL::B1][PL::R1];
+      constexpr int stride = NC / PL::R1, nbf = NC / (PL::R1 * PL::B1);
+#pragma unroll
+      for (int b = 0; b < PL::B1; ++b) {
+        const int j = b * nbf + t;
+#pragma unroll
+        for (int r = 0; r < PL::R1; ++r) {
+          const int f = j + r * stride;  // packed pair (x[2f], x[2f+1])
+          double2 z;
+          if (mode == 0) {
+            z = (2 * f < NC) ? *reinterpret_cast<const double2*>(x + 2 * f) : make_double2(0.0, 0.0);
+          } else {
+            const int m0 = 2 * f, m1 = 2 * f + 1;
+            const double a0 = m0 < NC ? x[m0] : (m0 == NC ? 0.0 : x[2 * NC - m0]);
+            const double a1 = m1 < NC ? x[m1] : x[2 * NC - m1];
+            z = make_double2(a0, a1);
+          }
+          v[b][r] = z;
+        }
+        dft<PL::R1, -1>(v[b]);
+      }
+      pass_store<NC, PL::R1, PL::B1>(sbuf, v, t, 1);
+    }
+    __syncthreads();
+    middle_passes<LOGN, G::LOGP, -1>(sbuf, t, tw);
+    {
+      double2 v[1][PL::P];
+      pass_compute<NC, PL::P, 1, -1>(sbuf, v, t, NC / PL::P, tw);
+      __syncthreads();
+      pass_store<NC, PL::P, 1>(sbuf, v, t, NC / PL::P);
+    }
+    __syncthreads();
+    if (active) {
+      // X[f] = (Z[f] + conj Z[n-f])/2 - (i/2) e^{-2 pi i f/2n} (Z[f] - conj Z[n-f]), f = 0..n
+      for (int f = t; f <= NC; f += PL::TPF) {
+        const double2 Zf = sbuf[pad_index(f & (NC - 1))];
+        const double2 Zr = cconj(sbuf[pad_index((NC - f) & (NC - 1))]);
+        const double2 s = cadd(Zf, Zr), d = csub(Zf, Zr);
+        const double2 w = hw[f];
+        const double2 wd = cmul(w, d);  // e^{-i theta} (Z - conj Z')
+        // -(i/2) * wd = (wd.y/2, -wd.x/2)
+        const double2 X = make_double2(0.5 * s.x + 0.5 * wd.y, 0.5 * s.y - 0.5 * wd.x);
+        const size_t o = (size_t)col * (NC + 1) + f;
+        if (mode == 0) {
+          if (out64) out64[o] = X;
+          if (out32) out32[o] = make_float2(float(X.x), float(X.y));
+        } else {
+          if (re64) re64[o] = X.x;
+          if (re32) re32[o] = float(X.x);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// batched convolution: item = col * R_N + q writes W[item][0..n-1].
+template <typename T, int LOGN>
+__global__ void __launch_bounds__(Geometry<LOGN>::threads)
+conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict__ phat,
+            const typename cvec<T>::type* __restrict__ hw, const typename cvec<T>::type* __restrict__ tw,
+            T* __restrict__ W, int R_N, long long n_items) {
+  using V = typename cvec<T>::type;
+  using G = Geometry<LOGN>;
+  using PL = typename G::PL;
+  constexpr int NC = PL::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int slot = threadIdx.x / PL::TPF;
+  const int t = threadIdx.x % PL::TPF;
+  V* sbuf = reinterpret_cast<V*>(smem_raw) + slot * padded_len(NC);
+  const T scale = T(1) / T(2 * NC);
+  for (long long g = blockIdx.x; g * G::slots < n_items; g += gridDim.x) {
+    const long long item = g * G::slots + slot;
+    const bool active = item < n_items;
+    const long long it = active ? item : n_items - 1;
+    const long long col = it / R_N;
+    const int q = int(it - col * R_N);
+    const V* Uc = Uhat + (size_t)col * (NC + 1);
+    const T* pq = phat + (size_t)q * (NC + 1);
+    {
+      // Z'[f] = (A + B) + i e^{+2 pi i f/2n} (A - B), A = Y[f], B = conj Y[n-f], Y = Uhat * phat
+      V v[PL::B1][PL::R1];
+      constexpr int stride = NC / PL::R1, nbf = NC / (PL::R1 * PL::B1);
+#pragma unroll
+      for (int b = 0; b < PL::B1; ++b) {
+        const int j = b * nbf + t;
+#pragma unroll
+        for (int r = 0; r < PL::R1; ++r) {
+          const int f = j + r * stride;
+          const V uf = __ldg(Uc + f), ur = __ldg(Uc + (NC - f));
+          const T pf = __ldg(pq + f), pr = __ldg(pq + (NC - f));
+          const V A = cmk<V>(uf.x * pf, uf.y * pf);
+          const V B = cmk<V>(ur.x * pr, -ur.y * pr);
+          const V s = cadd(A, B), d = csub(A, B);
+          const V wd = cmulc(d, __ldg(hw + f));  // e^{+i theta} (A - B)
+          v[b][r] = cmk<V>(s.x - wd.y, s.y + wd.x);
+        }
+        dft<PL::R1, +1>(v[b]);
+      }
+      pass_store<NC, PL::R1, PL::B1>(sbuf, v, t, 1);
+    }
+    __syncthreads();
+    middle_passes<LOGN, G::LOGP, +1>(sbuf, t, tw);
+    {
+      V v[1][PL::P];
+      pass_compute<NC, PL::P, 1, +1>(sbuf, v, t, NC / PL::P, tw);
+      if (active) {
+        T* out = W + (size_t)item * NC;
+#pragma unroll
+        for (int r = 0; r < PL::P / 2; ++r) {
+          const int o = t + r * (NC / PL::P);  // complex output o -> reals 2o, 2o+1
+          *reinterpret_cast<V*>(out + 2 * o) = cmk<V>(v[0][r].x * scale, v[0][r].y * scale);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename K>
+int configure(K kern, size_t smem) {
+  CPC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  return CPC_OK;
+}
+
+int sm_count() {
+  static int count = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev);
+    if (count <= 0) count = 1;
+  });
+  return count;
+}
+
+template <int LOGN>
+int launch_spectra(int mode, const double* src, int ncols, double2* o64, float2* o32, double* r64,
+                   float* r32, const cpc_kernel* P, cudaStream_t s) {
+  using G = Geometry<LOGN>;
+  const size_t smem = sizeof(double2) * G::slots * padded_len(1 << LOGN);
+  auto kern = spectra_kernel<LOGN>;
+  int st = configure(kern, smem);
+  if (st) return st;
+  int per_sm = 0;
+  CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::threads, smem));
+  const int groups = (ncols + G::slots - 1) / G::slots;
+  const int grid = std::max(1, std::min(groups, std::max(1, per_sm) * sm_count()));
+  kern<<<grid, G::threads, smem, s>>>(mode, src, ncols, o64, o32, r64, r32, P->d_hw64, P->d_tw64);
+  CPC_LAUNCH_CHECK("spectra_kernel");
+  return CPC_OK;
+}
+
+template <typename T, int LOGN>
+int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, cudaStream_t s) {
+  using G = Geometry<LOGN>;
+  using V = typename cvec<T>::type;
+  const size_t smem = sizeof(V) * G::slots * padded_len(1 << LOGN);
+  auto kern = conv_kernel<T, LOGN>;
+  int st = configure(kern, smem);
+  if (st) return st;
+  int per_sm = 0;
+  CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::threads, smem));
+  const long long n_items = (long long)ncols * P->R_N;
+  const long long groups = (n_items + G::slots - 1) / G::slots;
+  const long long grid = std::max(1LL, std::min(groups, (long long)std::max(1, per_sm) * sm_count()));
+  const T* phat;
+  const V* hw;
+  const V* tw;
+  if constexpr (sizeof(T) == 8) {
+    phat = P->d_phat64; hw = P->d_hw64; tw = P->d_tw64;
+  } else {
+    phat = P->d_phat32; hw = P->d_hw32; tw = P->d_tw32;
+  }
+  kern<<<int(grid), G::threads, smem, s>>>(static_cast<const V*>(Uhat), phat, hw, tw,
+                                           static_cast<T*>(W), P->R_N, n_items);
+  CPC_LAUNCH_CHECK("conv_kernel");
+  return CPC_OK;
+}
+
+template <int LOGN>
+int dispatch_spectra(int logn, int mode, const double* src, int ncols, double2* o64, float2* o32,
+                     double* r64, float* r32, const cpc_kernel* P, cudaStream_t s) {
+  if constexpr (LOGN > kMaxLogN) {
+    return fail(CPC_ERR_UNSUPPORTED, "spectra: n too large");
+  } else {
+    if (logn == LOGN) return launch_spectra<LOGN>(mode, src, ncols, o64, o32, r64, r32, P, s);
+    return dispatch_spectra<LOGN + 1>(logn, mode, src, ncols, o64, o32, r64, r32, P, s);
+  }
+}
+
+template <typename T, int LOGN>
+int dispatch_conv(int logn, const cpc_kernel* P, int ncols, const void* Uhat, void* W, cudaStream_t s) {
+  if constexpr (LOGN > kMaxLogN) {
+    return fail(CPC_ERR_UNSUPPORTED, "conv: n too large");
+  } else {
+    if (logn == LOGN) return launch_conv<T, LOGN>(P, ncols, Uhat, W, s);
+    return dispatch_conv<T, LOGN + 1>(logn, P, ncols, Uhat, W, s);
+  }
+}
+
+}  // namespace
+
+int compute_kernel_spectrum(cpc_kernel* P, cudaStream_t s) {
+  return dispatch_spectra<kMinLogN>(ilog2(P->n), 1, P->d_p, P->R_N, nullptr, nullptr, P->d_phat64,
+                                    P->d_phat32, P, s);
+}
+
+int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uhat64, float2* Uhat32,
+                    cudaStream_t s) {
+  return dispatch_spectra<kMinLogN>(ilog2(P->n), 0, U, ncols, Uhat64, Uhat32, nullptr, nullptr, P, s);
+}
+
+int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W, int precision,
+                          cudaStream_t s) {
+  if (precision == CPC_FP64) return dispatch_conv<double, kMinLogN>(ilog2(P->n), P, ncols, Uhat, W, s);
+  return dispatch_conv<float, kMinLogN>(ilog2(P->n), P, ncols, Uhat, W, s);
+}
+
+size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision) {
+  const size_t bins = size_t(ncols) * (P->n + 1);
+  return align256(bins * (precision == CPC_FP64 ? sizeof(double2) : sizeof(float2)));
+}
+
+}  // namespace cpc
+
+using namespace cpc;
+
+extern "C" size_t cp_convolve_workspace(const cpc_kernel* P, int R_f, int precision) {
+  if (!P || R_f <= 0) return 0;
+  // float32 forms keep a float64 copy of the spectra too (they are formed in float64)
+  size_t b = spectra_bytes(P, 3 * R_f, precision);
+  if (precision != CPC_FP64) b += spectra_bytes(P, 3 * R_f, CPC_FP64);
+  return b;
+}
+
+namespace cpc {
+int check_conv_args(const cpc_kernel* P, int R_f, const void* U, const void* W, int precision,
+                    void* ws, size_t ws_bytes, const char* who) {
+  if (!P) return fail(CPC_ERR_INVALID, std::string(who) + ": NULL kernel");
+  if (P->kind != CPC_KERNEL_CONV) return fail(CPC_ERR_INVALID, std::string(who) + ": needs a CONV kernel");
+  if (R_f <= 0) return fail(CPC_ERR_INVALID, std::string(who) + ": R_f must be positive");
+  if (!U || !W) return fail(CPC_ERR_INVALID, std::string(who) + ": NULL factor pointer");
+  if ((reinterpret_cast<uintptr_t>(U) & 15) || (reinterpret_cast<uintptr_t>(W) & 15))
+    return fail(CPC_ERR_INVALID, std::string(who) + ": U and W must be 16-byte aligned");
+  if (precision != CPC_FP64 && precision != CPC_FP32)
+    return fail(CPC_ERR_UNSUPPORTED, std::string(who) + ": precision form not implemented");
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255))
+    return fail(CPC_ERR_WORKSPACE, std::string(who) + ": workspace NULL or not 256-byte aligned");
+  if (ws_bytes < cp_convolve_workspace(P, R_f, precision))
+    return fail(CPC_ERR_WORKSPACE, std::string(who) + ": workspace too small");
+  return CPC_OK;
+}
+
+int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision, void* ws,
+                 cudaStream_t s) {
+  const int ncols = 3 * R_f;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  double2* h64 = reinterpret_cast<double2*>(w);
+  int st;
+  if (precision == CPC_FP64) {
+    st = forward_spectra(P, ncols, U, h64, nullptr, s);
+    if (st) return st;
+    return convolve_from_spectra(P, ncols, h64, W, precision, s);
+  }
+  float2* h32 = reinterpret_cast<float2*>(w + spectra_bytes(P, ncols, CPC_FP64));
+  st = forward_spectra(P, ncols, U, h64, h32, s);
+  if (st) return st;
+  return convolve_from_spectra(P, ncols, h32, W, precision, s);
+}
+}  // namespace cpc
+
+extern "C" int cp_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision,
+                           void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  int st = check_conv_args(P, R_f, U, W, precision, ws, ws_bytes, "cp_convolve");
+  if (st) return st;
+  return run_convolve(P, R_f, U, W, precision, ws, static_cast<cudaStream_t>(stream));
+}

@@ -1,0 +1,240 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: float64 forms within 1e-10 relative (per-column 2-norm for factor
+matrices, scalar relative for E_H and J, norm-wise for gradients); float32
+forms within the stated bounds below."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from oracle import coulomb as ocoul
+from oracle import cp as ocp
+from oracle import lattice as olat
+from tests.gpu_util import col_rel_err, oracle_conv_kernel, oracle_master_kernel, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def cpc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1504_06289_gb300 as m
+    return m
+
+
+def dev(x, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=dtype, device="cuda")
+
+
+@pytest.mark.parametrize("n,b,M,kind", [(128, 10.0, 20, "conv"), (8192, 20.0, 30, "conv"),
+                                        (16, 2.0, 3, "conv"), (4096, 16.0, 25, "conv"),
+                                        (256, 8.0, 12, "master"), (16384, 64.0, 30, "master")])
+def test_kernel_tables_match_oracle(cpc, n, b, M, kind):
+    P = cpc.make_newton_kernel(n, b, M, kind)
+    t, a, p = P.tables()
+    if kind == "conv":
+        t0, a0, p0 = oracle_conv_kernel(n, b, M)
+    else:
+        t0, a0, p0 = oracle_master_kernel(n, b, M)
+    assert P.R_N == 2 * M + 1
+    assert np.max(np.abs(t / t0 - 1)) < 1e-12
+    assert np.max(np.abs(a / a0 - 1)) < 1e-12
+    # entries relative to each vector's peak (far-tail entries are below 1e-300 of it)
+    peak = np.max(np.abs(p0), axis=1, keepdims=True)
+    assert np.max(np.abs(p - p0) / peak) < 1e-12
+
+
+def test_sampling_matches_oracle(cpc):
+    g = workloads.mixture_for("gauss8_n128", 1)
+    U = cpc.cp_sample_gaussians(128, 10.0, dev(g["a"]), dev(g["X"])).cpu().numpy()
+    U0 = ocp.sample_gaussians(128, 10.0, g["a"], g["X"])
+    assert np.max(np.abs(U - U0)) < 1e-15
+
+
+CASES = [("gauss8_n128", None), ("tiny_n16", dict(n=16, b=2.0, M=3, R_f=1, a_lo=0.5, a_hi=3.0)),
+         ("ragged_n256", dict(n=256, b=6.0, M=12, R_f=70, a_lo=0.3, a_hi=30.0)),
+         ("n1024", dict(n=1024, b=8.0, M=16, R_f=9, a_lo=0.2, a_hi=200.0))]
+
+
+def _case(name, spec, seed=2):
+    if spec is None:
+        cfg = workloads.CONFIGS[name]
+        g = workloads.mixture_for(name, seed)
+        return cfg["n"], cfg["b"], cfg["M"], g
+    g = workloads.gaussian_mixture(spec["R_f"], spec["a_lo"], spec["a_hi"], seed, centre_half=1.0)
+    return spec["n"], spec["b"], spec["M"], g
+
+
+@pytest.mark.parametrize("name,spec", CASES)
+def test_convolution_and_energy_fp64(cpc, name, spec):
+    n, b, M, g = _case(name, spec)
+    h = 2 * b / n
+    P = cpc.make_newton_kernel(n, b, M)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    U = cpc.cp_sample_gaussians(n, b, dev(g["a"]), dev(g["X"]))
+    U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
+    E, W, G = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp64", want_G=True)
+    W0 = ocp.convolve_factors(U0, P0)
+    assert col_rel_err(W.cpu().numpy(), W0) < TOL64
+    G0 = ocp.conv_matrices(U0, W0, P0.shape[0])
+    assert rel(G.cpu().numpy(), G0) < TOL64
+    E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
+    assert abs(E.item() / E0 - 1) < TOL64
+    # cp_convolve alone gives the same factors
+    W2 = cpc.cp_convolve(P, U, "fp64")
+    assert torch.equal(W, W2)
+
+
+@pytest.mark.parametrize("name,spec", CASES[:3])
+def test_convolution_and_energy_fp32(cpc, name, spec):
+    n, b, M, g = _case(name, spec)
+    h = 2 * b / n
+    P = cpc.make_newton_kernel(n, b, M)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    U = cpc.cp_sample_gaussians(n, b, dev(g["a"]), dev(g["X"]))
+    U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
+    E, W, _ = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp32")
+    assert W.dtype == torch.float32
+    W0 = ocp.convolve_factors(U0, P0)
+    assert col_rel_err(W.cpu().numpy(), W0) < 2e-6
+    E0 = ocp.hartree_energy(U0, g["c"], P0, h)
+    assert abs(E.item() / E0 - 1) < 1e-5
+
+
+def test_adjoint_and_parameter_gradients_fp64(cpc):
+    n, b, M = 256, 8.0, 14
+    h = 2 * b / n
+    g = workloads.gaussian_mixture(13, 0.2, 20.0, 7, centre_half=2.0)
+    P = cpc.make_newton_kernel(n, b, M)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    a, X, c = dev(g["a"]), dev(g["X"]), dev(g["c"])
+    U = cpc.cp_sample_gaussians(n, b, a, X)
+    E, W, G = cpc.cp_hartree_energy(P, U, c, "fp64", want_G=True)
+    dU, dc = cpc.cp_hartree_energy_adjoint(P, c, W, G, "fp64")
+    da, dX = cpc.cp_gaussian_param_grad(n, b, a, X, U, dU)
+    U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
+    dU0, dc0 = ocp.hartree_energy_adjoint(U0, g["c"], P0, h)
+    da0, dX0 = ocp.gaussian_param_grad(n, b, g["a"], g["X"], U0, dU0)
+    assert rel(dU.cpu().numpy(), dU0) < TOL64
+    assert rel(dc.cpu().numpy(), dc0) < TOL64
+    assert rel(da.cpu().numpy(), da0) < TOL64
+    assert rel(dX.cpu().numpy(), dX0) < TOL64
+
+
+def test_autograd_function(cpc):
+    n, b, M = 128, 8.0, 12
+    g = workloads.gaussian_mixture(5, 0.3, 5.0, 9, centre_half=2.0)
+    P = cpc.make_newton_kernel(n, b, M)
+    a = dev(g["a"]).requires_grad_()
+    X = dev(g["X"]).requires_grad_()
+    c = dev(g["c"]).requires_grad_()
+    E = cpc.CPHartreeEnergy.apply(a, X, c, P, "fp64")
+    E.backward()
+    # central differences of the library's own energy in a_0 and X_{1,2}
+    with torch.no_grad():
+        for which, idx, grad in (("a", (0,), a.grad), ("X", (1, 2), X.grad), ("c", (3,), c.grad)):
+            base = {"a": a.detach().clone(), "X": X.detach().clone(), "c": c.detach().clone()}
+            step = 1e-5
+            vals = []
+            for sgn in (1, -1):
+                d = {k: v.clone() for k, v in base.items()}
+                d[which][idx] += sgn * step
+                U = cpc.cp_sample_gaussians(n, b, d["a"], d["X"])
+                vals.append(cpc.cp_hartree_energy(P, U, d["c"], "fp64")[0].item())
+            fd = (vals[0] - vals[1]) / (2 * step)
+            assert abs(fd - grad[idx].item()) < 1e-6 * max(1.0, abs(fd)), (which, fd, grad[idx].item())
+
+
+def _basis_case():
+    basis = workloads.basis_set(6, 2, 4, 0.1, 50.0, 3, 1.5, seed=4)
+    return basis
+
+
+def test_coulomb_matrix_fp64(cpc):
+    n, b, M = 256, 10.0, 14
+    basis = _basis_case()
+    nb = len(basis["fn_first"]) - 1
+    items = ocoul.item_list(nb)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    J0, _ = ocoul.coulomb_items(n, b, basis, P0, items)
+    P = cpc.make_newton_kernel(n, b, M)
+    J = _gpu_coulomb(cpc, P, n, b, basis, items, "fp64")
+    assert rel(J, J0) < TOL64
+    assert np.max(np.abs(J - J0) / np.max(np.abs(J0))) < TOL64
+
+
+def _gpu_coulomb(cpc, P, n, b, basis, items, precision):
+    """Build the item and density factors on the GPU (sampling + Hadamard) and run coulomb_matrix."""
+    first = basis["fn_first"]
+    nb = len(first) - 1
+    centre = np.repeat(basis["fn_centre"], np.diff(first), axis=0)
+    F = cpc.cp_sample_gaussians(n, b, dev(basis["prim_alpha"]), dev(centre))
+    d = dev(basis["prim_d"])
+    # density pairs (a <= b within a function), weight w_mu * (1 or 2)
+    pa, pb, sc = [], [], []
+    for mu in range(nb):
+        for x in range(first[mu], first[mu + 1]):
+            for y in range(x, first[mu + 1]):
+                pa.append(x); pb.append(y); sc.append(basis["w"][mu] * (1.0 if x == y else 2.0))
+    U_rho, c_rho = cpc.cp_hadamard_pairs(F, dev(pa, torch.int32), dev(pb, torch.int32), d, dev(sc))
+    ia, ib, off = [], [], [0]
+    for mu, nu in items:
+        for x in range(first[mu], first[mu + 1]):
+            for y in range(first[nu], first[nu + 1]):
+                ia.append(x); ib.append(y)
+        off.append(len(ia))
+    U_it, c_it = cpc.cp_hadamard_pairs(F, dev(ia, torch.int32), dev(ib, torch.int32), d)
+    J, _ = cpc.coulomb_matrix(P, dev(off, torch.int32), U_it, c_it, U_rho, c_rho, precision)
+    return J.cpu().numpy()
+
+
+def test_coulomb_matrix_fp32(cpc):
+    n, b, M = 256, 10.0, 14
+    basis = _basis_case()
+    nb = len(basis["fn_first"]) - 1
+    items = ocoul.item_list(nb)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    J0, _ = ocoul.coulomb_items(n, b, basis, P0, items)
+    P = cpc.make_newton_kernel(n, b, M)
+    J = _gpu_coulomb(cpc, P, n, b, basis, items, "fp32")
+    assert np.max(np.abs(J - J0)) < 1e-5 * np.max(np.abs(J0))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-7)])
+def test_lattice_sum(cpc, precision, tol):
+    n, b, M, L = 1024, 16.0, 20, 8
+    h = 2 * b / n
+    geo = workloads.lattice_geometry(n, L, 32)
+    edges = [geo["edges"], geo["edges"][:5], geo["edges"][2:]]  # ragged per axis
+    P = cpc.make_newton_kernel(n, b, M, "master")
+    _, _, Pm0 = oracle_master_kernel(n, b, M)
+    sub = dev(np.stack([geo["sub_idx"]] * 3), torch.int32)
+    S, V = cpc.lattice_potential_sum(P, edges, sub, precision)
+    S0 = [olat.assembled_vectors(Pm0, e, n) for e in edges]
+    for l in range(3):
+        assert col_rel_err(S[l].cpu().numpy(), S0[l]) < 1e-13
+    V0 = olat.potential_subgrid(S0, h, [geo["sub_idx"]] * 3)
+    assert np.max(np.abs(V.cpu().numpy() / V0 - 1)) < tol
+
+
+def test_invalid_arguments_fail_without_launch(cpc):
+    from paper_1504_06289_gb300 import CpcError
+    with pytest.raises(CpcError):
+        cpc.make_newton_kernel(100, 10.0, 20)          # not a power of two
+    with pytest.raises(CpcError):
+        cpc.make_newton_kernel(16384, 10.0, 20)        # conv limit 8192
+    P = cpc.make_newton_kernel(64, 4.0, 5)
+    U = torch.zeros((3, 2, 64), dtype=torch.float64, device="cuda")
+    with pytest.raises(CpcError):
+        cpc.cp_convolve(P, U, "split")
+    Pm = cpc.make_newton_kernel(64, 4.0, 5, "master")
+    with pytest.raises(CpcError):
+        cpc.cp_convolve(Pm, U, "fp64")                 # wrong kernel kind
+    with pytest.raises(CpcError):
+        cpc.lattice_potential_sum(Pm, [[0, 65], [1], [2]])  # edge beyond n
