@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--seed", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rf", type=int, default=None,
+                    help="override the rank R_f (profiling a smaller case of the same kernels)")
     return ap.parse_args()
 
 
@@ -194,7 +196,7 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "convolutions/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "R_f": cfg["R_f"], "R_N": 2 * M + 1,
+        "config": {"workload": WORKLOAD if not args.rf else f"{WORKLOAD} (R_f={R_f} profiling case)", "n": n, "R_f": cfg["R_f"], "R_N": 2 * M + 1,
                    "sample_per_step": "4 Gaussians x 4 kernel terms x 3 axes (48 direct convolutions)"},
         "cpu_baseline": {"value": value, "unit": "convolutions/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": "48 direct length-8192 convolutions per step"},
@@ -213,6 +215,9 @@ def run_ours(args, ws, rank, local):
     P = cpc.make_newton_kernel(n, b, M, "conv", device=dev)
     R_N = P.R_N
     g = workloads.mixture_for(WORKLOAD, args.seed + rank)
+    if args.rf:
+        R_f = args.rf
+        g = {k: v[:R_f] for k, v in g.items()}
     a_h = torch.tensor(g["a"]).pin_memory()
     X_h = torch.tensor(g["X"]).pin_memory()
     c_h = torch.tensor(g["c"]).pin_memory()
@@ -342,7 +347,7 @@ def run_ours(args, ws, rank, local):
         "metric": METRIC, "value": value, "unit": "convolutions/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n": n, "box": [-b, b], "R_f": R_f, "R_N": R_N,
+        "config": {"workload": WORKLOAD if not args.rf else f"{WORKLOAD} (R_f={R_f} profiling case)", "n": n, "box": [-b, b], "R_f": R_f, "R_N": R_N,
                    "convolutions_per_step": convs_per_step, "precision_form": prec,
                    "l2": "each step writes the V_H factors (%.2f GB), far larger than L2" % (
                        3 * R_f * R_N * n * elem / 1e9)},
