@@ -145,6 +145,27 @@ int cp_hartree_energy_from_factors(const cpc_kernel* P, int R_f, const double* U
                                    const void* W, double* G, double* E_H, int precision, void* ws,
                                    size_t ws_bytes, void* stream);
 
+/* cp_hartree_energy without a workspace argument, for callers that cannot
+ * allocate device memory (a host program that owns a fixed device pool from
+ * start-up, a plug-in living inside another runtime's allocator, a real-time
+ * loop where cudaMalloc's synchronisation and latency are not allowed).  The
+ * paper has no counterpart: this is a packaging variant of the same
+ * computation, with the same arguments as cp_hartree_energy minus ws.
+ * Its scratch is one file-scope device array of 32 MiB, held by every GPU
+ * that loads the library until the process exits; a call needs
+ * cp_hartree_energy_workspace(P, R_f, precision) bytes of it.
+ * Sizes whose requirement exceeds 32 MiB are rejected with
+ * CPC_ERR_UNSUPPORTED and a message naming both sizes; nothing is launched.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current), so make that first call before any
+ * stream capture.  Every call on a device shares the array and sees the last
+ * call's bytes there; the kernels overwrite all scratch they read, so no
+ * clearing is needed, but calls whose work overlaps on the GPU (unordered
+ * streams) race on it.  No cudaMalloc, cudaFree or allocating library call
+ * is made. */
+int cp_hartree_energy_noalloc(const cpc_kernel* P, int R_f, const double* U, const double* c, void* W,
+                              double* G, double* E_H, int precision, void* stream);
+
 /* ---- a7: adjoint of E_H ---------------------------------------------------
  * Derived from Sec. 2.5 Eq. scal and Eq. conv (each Toeplitz factor of p_q is
  * symmetric):

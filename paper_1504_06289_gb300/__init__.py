@@ -22,7 +22,8 @@ from ._abi import KIND, PRECISION, CpcError, check, load
 
 __all__ = [
     "NewtonKernel", "make_newton_kernel", "make_newton_kernel_tables", "cp_sample_gaussians", "cp_hadamard_pairs",
-    "cp_convolve", "cp_hartree_energy", "cp_hartree_energy_from_factors", "cp_hartree_energy_adjoint", "cp_gaussian_param_grad",
+    "cp_convolve", "cp_hartree_energy", "cp_hartree_energy_from_factors",
+    "cp_hartree_energy_noalloc", "cp_hartree_energy_adjoint", "cp_gaussian_param_grad",
     "coulomb_matrix", "lattice_potential_sum", "CPHartreeEnergy", "CpcError",
 ]
 
@@ -190,6 +191,19 @@ def cp_hartree_energy_from_factors(P: NewtonKernel, U: torch.Tensor, c: torch.Te
                                              _prec(precision), _ptr(ws), ws.numel(), _stream(stream)),
           "cp_hartree_energy_from_factors")
     return E, G
+
+
+def cp_hartree_energy_noalloc(P: NewtonKernel, U: torch.Tensor, c: torch.Tensor, W: torch.Tensor,
+                              G: torch.Tensor | None = None, E: torch.Tensor | None = None,
+                              precision: str = "fp64", stream=None) -> torch.Tensor:
+    """cp_hartree_energy for callers that cannot allocate: the caller provides
+    W (and G, E if wanted); the library's fixed 32 MiB device scratch replaces
+    the workspace.  Returns the device scalar E."""
+    if E is None:
+        E = torch.empty((), dtype=torch.float64, device=U.device)
+    check(load().cp_hartree_energy_noalloc(P.handle, U.shape[1], _ptr(U), _ptr(c), _ptr(W), _ptr(G), _ptr(E),
+                                           _prec(precision), _stream(stream)), "cp_hartree_energy_noalloc")
+    return E
 
 
 def cp_hartree_energy_adjoint(P: NewtonKernel, c: torch.Tensor, W: torch.Tensor, G: torch.Tensor,

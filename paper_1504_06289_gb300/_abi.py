@@ -28,6 +28,7 @@ PROTOTYPES = {
     "cp_hartree_energy": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp]),
     "cp_hartree_energy_from_factors_workspace": (sz, [vp, i32]),
     "cp_hartree_energy_from_factors": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp]),
+    "cp_hartree_energy_noalloc": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp]),
     "cp_hartree_energy_adjoint": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp]),
     "cp_gaussian_param_grad": (i32, [i32, f64, i32, vp, vp, vp, vp, vp, vp, vp]),
     "coulomb_matrix_workspace": (sz, [vp, i32, i32, i32, i32]),
