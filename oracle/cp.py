@@ -48,6 +48,15 @@ def conv1d(u: np.ndarray, p: np.ndarray) -> np.ndarray:
     return toeplitz_from_even(p) @ u
 
 
+def conv1d_direct(u: np.ndarray, p: np.ndarray) -> np.ndarray:
+    """The same w = u * p for one column by numpy's direct (O(n^2)) linear
+    convolution with the kernel spread over offsets -(n-1)..n-1: output index
+    i + n - 1 of the full convolution is w[i]."""
+    n = u.shape[0]
+    p_sym = np.concatenate([p[:0:-1], p])  # offsets -(n-1)..n-1
+    return np.convolve(u, p_sym)[n - 1:2 * n - 1]
+
+
 def convolve_factors(U: np.ndarray, P: np.ndarray) -> np.ndarray:
     """W[l, k*R_N + q, :] = U[l, k] * p_q for every axis l, rank k and kernel term q.
 

@@ -208,3 +208,15 @@ def test_closed_form_gradient_self_check():
         Xm = g["X"].copy(); Xm[k, 1] -= 1e-6
         fd = (cf.mixture_energy(g["a"], Xp, g["c"]) - cf.mixture_energy(g["a"], Xm, g["c"])) / 2e-6
         assert abs(fd - dX[k, 1]) < 1e-7 * max(1, abs(dX[k, 1]))
+
+
+def test_single_column_direct_convolution_matches_toeplitz():
+    rng = np.random.default_rng(3)
+    for n in (16, 100, 257):
+        u = rng.standard_normal(n)
+        p = rng.standard_normal(n)
+        w = cp.conv1d_direct(u, p)
+        # brute force from the definition w[i] = sum_j u[j] p[|i-j|]
+        ref = np.array([sum(u[j] * p[abs(i - j)] for j in range(n)) for i in range(n)])
+        assert np.max(np.abs(w - ref)) < 1e-12 * np.max(np.abs(ref))
+        assert np.max(np.abs(cp.conv1d(u, p) - ref)) < 1e-12 * np.max(np.abs(ref))
