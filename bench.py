@@ -226,29 +226,41 @@ def run_ours(args, ws, rank, local):
     lib = cpc.load()
 
     def buffers(prec):
-        W = torch.empty((3, R_f * R_N, n), dtype=torch.float64 if prec == "fp64" else torch.float32, device=dev)
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        W = torch.empty((3, R_f * R_N, n), dtype=dt, device=dev)
         U = torch.empty((3, R_f, n), dtype=torch.float64, device=dev)
+        S = torch.empty((3, R_f, n + 1, 2), dtype=dt, device=dev)
         E = torch.empty((), dtype=torch.float64, device=dev)
-        ws_c = torch.empty(lib.cp_convolve_workspace(P.handle, R_f, cpc._prec(prec)), dtype=torch.uint8, device=dev)
-        ws_g = torch.empty(max(256, lib.cp_hartree_energy_from_factors_workspace(P.handle, R_f)), dtype=torch.uint8,
-                           device=dev)
-        return W, U, E, ws_c, ws_g
+        nb = (lib.cp_hartree_energy_from_factors_workspace(P.handle, R_f) if prec == "fp64"
+              else lib.cp_hartree_energy_from_spectra_workspace(P.handle, R_f))
+        ws_g = torch.empty(max(256, nb), dtype=torch.uint8, device=dev)
+        return W, U, S, E, ws_g
 
     def step(prec, bufs, ev=None):
-        W, U, E, ws_c, ws_g = bufs
-        st = lib.cp_sample_gaussians(n, b, R_f, cpc._ptr(a), cpc._ptr(X), cpc._ptr(U), cpc._stream(stream))
-        cpc.check(st, "sample")
+        """sample -> spectra -> convolutions (V_H factors) -> contraction (E_H), one ABI call each."""
+        W, U, S, E, ws_g = bufs
+        pr = cpc._prec(prec)
+        sp = cpc._stream(stream)
+        cpc.check(lib.cp_sample_gaussians(n, b, R_f, cpc._ptr(a), cpc._ptr(X), cpc._ptr(U), sp), "sample")
         if ev is not None:
             ev[0].record(stream)
-        cpc.check(lib.cp_convolve(P.handle, R_f, cpc._ptr(U), cpc._ptr(W), cpc._prec(prec), cpc._ptr(ws_c),
-                                  ws_c.numel(), cpc._stream(stream)), "cp_convolve")
+        cpc.check(lib.cp_factor_spectra(P.handle, R_f, cpc._ptr(U), cpc._ptr(S), pr, sp), "cp_factor_spectra")
         if ev is not None:
             ev[1].record(stream)
-        cpc.check(lib.cp_hartree_energy_from_factors(P.handle, R_f, cpc._ptr(U), cpc._ptr(c), cpc._ptr(W), None,
-                                                     cpc._ptr(E), cpc._prec(prec), cpc._ptr(ws_g), ws_g.numel(),
-                                                     cpc._stream(stream)), "cp_hartree_energy_from_factors")
+        cpc.check(lib.cp_convolve_from_spectra(P.handle, R_f, cpc._ptr(S), cpc._ptr(W), pr, sp),
+                  "cp_convolve_from_spectra")
         if ev is not None:
             ev[2].record(stream)
+        if prec == "fp64":
+            cpc.check(lib.cp_hartree_energy_from_factors(P.handle, R_f, cpc._ptr(U), cpc._ptr(c), cpc._ptr(W), None,
+                                                         cpc._ptr(E), pr, cpc._ptr(ws_g), ws_g.numel(), sp),
+                      "cp_hartree_energy_from_factors")
+        else:
+            cpc.check(lib.cp_hartree_energy_from_spectra(P.handle, R_f, cpc._ptr(S), cpc._ptr(c), None, cpc._ptr(E),
+                                                         pr, cpc._ptr(ws_g), ws_g.numel(), sp),
+                      "cp_hartree_energy_from_spectra")
+        if ev is not None:
+            ev[3].record(stream)
         return E
 
     prec = args.precision
@@ -256,7 +268,7 @@ def run_ours(args, ws, rank, local):
     for _ in range(args.warmup):
         step(prec, bufs)
     torch.cuda.synchronize(dev)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
         barrier(ws)
@@ -269,9 +281,10 @@ def run_ours(args, ws, rank, local):
         barrier(ws)
     ms_total = start.elapsed_time(stop)
     ms_total = max_over_ranks(ms_total, ws, dev)
-    E_fast = bufs[2].item()
-    conv_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
-    gram_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    E_fast = bufs[3].item()
+    spec_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
+    conv_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
+    gram_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in evs]))
     ms_step = ms_total / args.steps
     convs_per_step = 3 * R_f * R_N
     value = ws * convs_per_step * args.steps / (ms_total * 1e-3)
@@ -300,7 +313,7 @@ def run_ours(args, ws, rank, local):
         b64 = buffers("fp64")
         step("fp64", b64)
         torch.cuda.synchronize(dev)
-        e64 = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.fp64_steps)]
+        e64 = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.fp64_steps)]
         s64, t64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s64.record(stream)
         for k in range(args.fp64_steps):
@@ -308,10 +321,11 @@ def run_ours(args, ws, rank, local):
         t64.record(stream)
         torch.cuda.synchronize(dev)
         ms64 = s64.elapsed_time(t64) / args.fp64_steps
-        E64 = b64[2].item()
+        E64 = b64[3].item()
         fp64 = {"ms_per_step": ms64, "value": convs_per_step / (ms64 * 1e-3),
-                "conv_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in e64])),
-                "contraction_ms": float(np.mean([e[1].elapsed_time(e[2]) for e in e64])),
+                "spectra_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in e64])),
+                "conv_ms": float(np.mean([e[1].elapsed_time(e[2]) for e in e64])),
+                "contraction_ms": float(np.mean([e[2].elapsed_time(e[3]) for e in e64])),
                 "E_H": E64, "rel_err_E_H_of_fast_form": abs(E_fast / E64 - 1)}
         del b64
         torch.cuda.empty_cache()
@@ -325,15 +339,17 @@ def run_ours(args, ws, rank, local):
     # conv kernel algorithmic bytes per step: write all V_H factors, read spectra of U and p
     conv_bytes = 3 * R_f * R_N * n * elem + 3 * R_f * (n + 1) * 2 * elem + R_N * (n + 1) * elem
     conv_gbs = conv_bytes / (conv_ms * 1e-3) / 1e9
-    # contraction: unique Gram entries (symmetric) x 3 axes x R_N, 2 flop per multiply-add over n cells
-    gram_flops = 3 * R_N * (R_f * (R_f + 1) // 2) * n * 2
+    # contraction: unique Gram entries (symmetric) x 3 axes x R_N, 2 flop per multiply-add over
+    # K = 2(n+1) spectral values (float32 form, Parseval) or n cells (float64 form)
+    K_con = 2 * (n + 1) if prec != "fp64" else n
+    gram_flops = 3 * R_N * (R_f * (R_f + 1) // 2) * K_con * 2
     sm_mhz = clk["sm_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak_tf = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12 if prec != "fp64" else None
     gram_tf = gram_flops / (gram_ms * 1e-3) / 1e12
     kernels = {
         "conv_kernel": {"ms": conv_ms, "bound": "hbm", "achieved": conv_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": conv_gbs / hbm_peak, "algorithmic_bytes": conv_bytes},
-        "tri_gram_kernel": {"ms": gram_ms, "bound": "alu", "achieved": gram_tf, "unit": "TFLOP/s",
+        "gemm3_kernel" if prec != "fp64" else "tri_gram_kernel": {"ms": gram_ms, "bound": "alu", "achieved": gram_tf, "unit": "TFLOP/s",
                             "peak": alu_peak_tf, "frac": (gram_tf / alu_peak_tf) if alu_peak_tf else None,
                             "algorithmic_flops": gram_flops,
                             "peak_note": "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x median SM clock"},
@@ -352,13 +368,13 @@ def run_ours(args, ws, rank, local):
                    "l2": "each step writes the V_H factors (%.2f GB), far larger than L2" % (
                        3 * R_f * R_N * n * elem / 1e9)},
         "E_H": E_fast, "E_H_evals_per_s": ws * args.steps / (ms_total * 1e-3),
-        "phases_ms": {"convolve": conv_ms, "contraction": gram_ms},
+        "phases_ms": {"spectra": spec_ms, "convolve": conv_ms, "contraction": gram_ms},
         "kernels": kernels, "roofline": roofline,
         "fp64_gpu": fp64,
         "speedup_vs_fp64_gpu": (fp64["ms_per_step"] / ms_step) if fp64 else None,
         "e2e": {"value": ws * convs_per_step * e2e_steps / e2e_s, "unit": "convolutions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": 5 * args.steps,  # sample, spectra, conv, contraction, final sum
         "clocks": clk,
     }
     if ws == 1 and not args.no_cpu_baseline:

@@ -123,13 +123,27 @@ size_t cp_convolve_workspace(const cpc_kernel* P, int R_f, int precision);
 int cp_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision,
                 void* ws, size_t ws_bytes, void* stream);
 
+/* The two halves of cp_convolve with the factor spectra as an explicit,
+ * caller-owned intermediate.  spec: [3][R_f][n+1] complex bins of the
+ * zero-padded length-2n columns, interleaved (re, im), float64 (CPC_FP64) or
+ * float32 (CPC_FP32: computed in float64, rounded once).  16-byte aligned. */
+int cp_factor_spectra(const cpc_kernel* P, int R_f, const double* U, void* spec, int precision,
+                      void* stream);
+int cp_convolve_from_spectra(const cpc_kernel* P, int R_f, const void* spec, void* W, int precision,
+                             void* stream);
+
 /* ---- a5/a6: convolution matrices and the Hartree energy -------------------
  * G[l][q][k'][k] = sum_i U[l][k'][i] W[l][k*R_N+q][i]   (Sec. 3.2,
  *                  Eq. Factor_Mk_Conv: U^T (p_q * U), symmetric in k', k),
  * E_H = h^3 sum_q sum_{k,k'} c_k c_k' prod_l G[l][q][k'][k]
  *     = h^3 <f, P_R * f>      (Sec. 2.5 Eq. scal with Eq. conv).
  * Runs cp_convolve into W (required: it receives the V_H factors, type as
- * in cp_convolve), then the contraction.  c: [R_f] float64.  G: NULL or
+ * in cp_convolve), then the contraction.  CPC_FP64 contracts U with the
+ * float64 V_H factors.  CPC_FP32 contracts the float32-rounded float64
+ * spectra instead (Parseval on the length-2n circle: G_q[k',k] =
+ * (1/2n) sum_f w_f p^_q[f] Re(U^_k'[f] conj U^_k[f]), w_0 = w_n = 1, else 2),
+ * so E_H does not inherit the float32 FFT error of the V_H factors; float32
+ * products, float32 sums over chunks of 256, float64 final reduction.  c: [R_f] float64.  G: NULL or
  * [3][R_N][R_f][R_f] float64 (needed by the adjoint).  E_H: one float64 on
  * the device.  Workspace: cp_hartree_energy_workspace bytes. */
 size_t cp_hartree_energy_workspace(const cpc_kernel* P, int R_f, int precision);
@@ -138,12 +152,22 @@ int cp_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doubl
                       void* stream);
 
 /* The contraction part of cp_hartree_energy alone: G and E_H from existing
- * V_H factors W (as written by cp_convolve with the same precision).
+ * V_H factors W (as written by cp_convolve with the same precision), in the
+ * spatial form (float32 products on the float32 factors for CPC_FP32).
  * Workspace: cp_hartree_energy_from_factors_workspace bytes. */
 size_t cp_hartree_energy_from_factors_workspace(const cpc_kernel* P, int R_f);
 int cp_hartree_energy_from_factors(const cpc_kernel* P, int R_f, const double* U, const double* c,
                                    const void* W, double* G, double* E_H, int precision, void* ws,
                                    size_t ws_bytes, void* stream);
+
+/* The float32 form's contraction from float32 spectra (as written by
+ * cp_factor_spectra with CPC_FP32): G (may be NULL) and E_H as in
+ * cp_hartree_energy.  precision must be CPC_FP32.
+ * Workspace: cp_hartree_energy_from_spectra_workspace bytes. */
+size_t cp_hartree_energy_from_spectra_workspace(const cpc_kernel* P, int R_f);
+int cp_hartree_energy_from_spectra(const cpc_kernel* P, int R_f, const void* spec, const double* c,
+                                   double* G, double* E_H, int precision, void* ws, size_t ws_bytes,
+                                   void* stream);
 
 /* cp_hartree_energy without a workspace argument, for callers that cannot
  * allocate device memory (a host program that owns a fixed device pool from

@@ -23,6 +23,7 @@ from ._abi import KIND, PRECISION, CpcError, check, load
 __all__ = [
     "NewtonKernel", "make_newton_kernel", "make_newton_kernel_tables", "cp_sample_gaussians", "cp_hadamard_pairs",
     "cp_convolve", "cp_hartree_energy", "cp_hartree_energy_from_factors",
+    "cp_factor_spectra", "cp_convolve_from_spectra", "cp_hartree_energy_from_spectra",
     "cp_hartree_energy_noalloc", "cp_hartree_energy_adjoint", "cp_gaussian_param_grad",
     "coulomb_matrix", "lattice_potential_sum", "CPHartreeEnergy", "CpcError",
 ]
@@ -153,6 +154,44 @@ def cp_convolve(P: NewtonKernel, U: torch.Tensor, precision: str = "fp64", W: to
     check(lib.cp_convolve(P.handle, R_f, _ptr(U), _ptr(W), pr, _ptr(ws), ws.numel(), _stream(stream)),
           "cp_convolve")
     return W
+
+
+def cp_factor_spectra(P: NewtonKernel, U: torch.Tensor, precision: str = "fp64", spec: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+    """Spectra of the zero-padded factor columns, (3, R_f, n+1, 2) as (re, im)."""
+    R_f = U.shape[1]
+    if spec is None:
+        spec = torch.empty((3, R_f, P.n + 1, 2), dtype=_out_dtype(precision), device=U.device)
+    check(load().cp_factor_spectra(P.handle, R_f, _ptr(U), _ptr(spec), _prec(precision), _stream(stream)),
+          "cp_factor_spectra")
+    return spec
+
+
+def cp_convolve_from_spectra(P: NewtonKernel, spec: torch.Tensor, precision: str = "fp64",
+                             W: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """V_H factors from factor spectra (the second half of cp_convolve)."""
+    R_f = spec.shape[1]
+    if W is None:
+        W = torch.empty((3, R_f * P.R_N, P.n), dtype=_out_dtype(precision), device=spec.device)
+    check(load().cp_convolve_from_spectra(P.handle, R_f, _ptr(spec), _ptr(W), _prec(precision), _stream(stream)),
+          "cp_convolve_from_spectra")
+    return W
+
+
+def cp_hartree_energy_from_spectra(P: NewtonKernel, spec: torch.Tensor, c: torch.Tensor, want_G: bool = False,
+                                   ws: torch.Tensor | None = None, E: torch.Tensor | None = None, stream=None):
+    """float32 form: E_H (device scalar) and optionally G from float32 spectra (Parseval)."""
+    lib = load()
+    R_f = spec.shape[1]
+    G = torch.empty((3, P.R_N, R_f, R_f), dtype=torch.float64, device=spec.device) if want_G else None
+    if E is None:
+        E = torch.empty((), dtype=torch.float64, device=spec.device)
+    nb = lib.cp_hartree_energy_from_spectra_workspace(P.handle, R_f)
+    if ws is None or ws.numel() < nb:
+        ws = _workspace(nb, spec.device)
+    check(lib.cp_hartree_energy_from_spectra(P.handle, R_f, _ptr(spec), _ptr(c), _ptr(G), _ptr(E), PRECISION["fp32"],
+                                             _ptr(ws), ws.numel(), _stream(stream)), "cp_hartree_energy_from_spectra")
+    return E, G
 
 
 def cp_hartree_energy(P: NewtonKernel, U: torch.Tensor, c: torch.Tensor, precision: str = "fp64",

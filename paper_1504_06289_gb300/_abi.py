@@ -24,6 +24,10 @@ PROTOTYPES = {
     "cp_hadamard_pairs": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
     "cp_convolve_workspace": (sz, [vp, i32, i32]),
     "cp_convolve": (i32, [vp, i32, vp, vp, i32, vp, sz, vp]),
+    "cp_factor_spectra": (i32, [vp, i32, vp, vp, i32, vp]),
+    "cp_convolve_from_spectra": (i32, [vp, i32, vp, vp, i32, vp]),
+    "cp_hartree_energy_from_spectra_workspace": (sz, [vp, i32]),
+    "cp_hartree_energy_from_spectra": (i32, [vp, i32, vp, vp, vp, vp, i32, vp, sz, vp]),
     "cp_hartree_energy_workspace": (sz, [vp, i32, i32]),
     "cp_hartree_energy": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp]),
     "cp_hartree_energy_from_factors_workspace": (sz, [vp, i32]),

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -32,6 +34,8 @@ struct cpc_kernel {
   float2* d_tw32 = nullptr;
   double2* d_hw64 = nullptr;
   float2* d_hw32 = nullptr;
+  // CONV only: Parseval weights d_q[2f+j] = w_f phat_q[f] / (2n), float32, [R_N][2(n+1)]
+  float* d_specw32 = nullptr;
 };
 
 namespace cpc {
@@ -72,5 +76,14 @@ int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uh
 // batched convolution from spectra
 int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W,
                           int precision, cudaStream_t s);
+
+// float32 contractions (gram32.cu)
+size_t eh32_partials(int R_f, int R_N);
+int build_spectral_weights(const cpc_kernel* P, float* d, cudaStream_t s);
+int launch_eh32(const cpc_kernel* P, int R_f, const double* U, const float* W, const float* S32,
+                const float* dtab, const double* c, double* G, double* partial, cudaStream_t s);
+int launch_rows32(const cpc_kernel* P, int n_factors, const double* U_items, int N, const float* W,
+                  const double* c_rho, double* rowpart, int groups, int tiles_per_cta, cudaStream_t s);
+size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision);
 
 }  // namespace cpc

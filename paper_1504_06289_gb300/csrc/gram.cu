@@ -307,7 +307,18 @@ static int tiles(int x) { return (x + TM - 1) / TM; }
 
 size_t eh_partials(const cpc_kernel* P, int R_f) {
   const int T = tiles(R_f);
-  return size_t(T) * (T + 1) / 2 * P->R_N;
+  return std::max(size_t(T) * (T + 1) / 2 * P->R_N, eh32_partials(R_f, P->R_N));
+}
+
+// E_H from float32 spectra (Parseval contraction), partials in `partial`.
+int launch_eh_spectral(const cpc_kernel* P, int R_f, const float2* spec32, const double* c, double* G,
+                       double* E_H, double* partial, cudaStream_t s) {
+  int st = launch_eh32(P, R_f, nullptr, nullptr, reinterpret_cast<const float*>(spec32), P->d_specw32, c, G,
+                       partial, s);
+  if (st) return st;
+  finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, (long long)eh32_partials(R_f, P->R_N), P->h * P->h * P->h, E_H);
+  CPC_LAUNCH_CHECK("finalize_sum_kernel");
+  return CPC_OK;
 }
 
 int launch_eh(const cpc_kernel* P, int R_f, const double* U, const double* c, const void* W,
@@ -317,16 +328,33 @@ int launch_eh(const cpc_kernel* P, int R_f, const double* U, const double* c, co
   dim3 grid(T * (T + 1) / 2, P->R_N);
   const long long a_axis = (long long)R_f * n;
   const long long b_axis = (long long)R_f * P->R_N * n;
-  if (precision == CPC_FP64)
+  long long count = (long long)grid.x * grid.y;
+  if (precision == CPC_FP64) {
     tri_gram_kernel<double, MODE_EH><<<grid, TPB, 0, s>>>(n, R_f, R_f, U, a_axis, static_cast<const double*>(W),
                                                            b_axis, P->R_N, c, c, 1, partial, G, 0);
-  else
-    tri_gram_kernel<float, MODE_EH><<<grid, TPB, 0, s>>>(n, R_f, R_f, U, a_axis, static_cast<const float*>(W),
-                                                          b_axis, P->R_N, c, c, 1, partial, G, 0);
-  CPC_LAUNCH_CHECK("tri_gram_kernel(EH)");
-  finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, (long long)grid.x * grid.y, P->h * P->h * P->h, E_H);
+    CPC_LAUNCH_CHECK("tri_gram_kernel(EH)");
+  } else {
+    int st = launch_eh32(P, R_f, U, static_cast<const float*>(W), nullptr, nullptr, c, G, partial, s);
+    if (st) return st;
+    count = (long long)eh32_partials(R_f, P->R_N);
+  }
+  finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, count, P->h * P->h * P->h, E_H);
   CPC_LAUNCH_CHECK("finalize_sum_kernel");
   return CPC_OK;
+}
+
+// cp_hartree_energy after argument checks: convolution into W, then the
+// contraction (float64: spatial on W; float32: Parseval on the float32 copy
+// of the float64 spectra that run_convolve leaves at the start of ws).
+int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const double* c, void* W, double* G,
+                       double* E_H, int precision, void* ws, cudaStream_t s) {
+  int st = run_convolve(P, R_f, U, W, precision, ws, s);
+  if (st) return st;
+  double* partial = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_f, precision));
+  if (precision == CPC_FP64) return launch_eh(P, R_f, U, c, W, G, E_H, precision, partial, s);
+  const float2* spec32 = reinterpret_cast<const float2*>(static_cast<unsigned char*>(ws) +
+                                                         spectra_bytes(P, 3 * R_f, CPC_FP64));
+  return launch_eh_spectral(P, R_f, spec32, c, G, E_H, partial, s);
 }
 
 }  // namespace cpc
@@ -347,11 +375,7 @@ extern "C" int cp_hartree_energy(const cpc_kernel* P, int R_f, const double* U, 
   if (!c || !E_H) return fail(CPC_ERR_INVALID, "cp_hartree_energy: NULL c or E_H");
   if (ws_bytes < cp_hartree_energy_workspace(P, R_f, precision))
     return fail(CPC_ERR_WORKSPACE, "cp_hartree_energy: workspace too small");
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  st = run_convolve(P, R_f, U, W, precision, ws, s);
-  if (st) return st;
-  double* partial = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_f, precision));
-  return launch_eh(P, R_f, U, c, W, G, E_H, precision, partial, s);
+  return run_hartree_energy(P, R_f, U, c, W, G, E_H, precision, ws, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" size_t cp_hartree_energy_from_factors_workspace(const cpc_kernel* P, int R_f) {
@@ -436,12 +460,67 @@ extern "C" int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, 
   if (precision == CPC_FP64)
     tri_gram_kernel<double, MODE_ROWS><<<grid, TPB, 0, s>>>(n, n_factors, N, U_items, a_axis,
         static_cast<const double*>(W_rho), b_axis, 1, nullptr, c_rho, P->R_N, rowpart, nullptr, kCoulombTilesPerCta);
-  else
-    tri_gram_kernel<float, MODE_ROWS><<<grid, TPB, 0, s>>>(n, n_factors, N, U_items, a_axis,
-        static_cast<const float*>(W_rho), b_axis, 1, nullptr, c_rho, P->R_N, rowpart, nullptr, kCoulombTilesPerCta);
+  else {
+    st = launch_rows32(P, n_factors, U_items, N, static_cast<const float*>(W_rho), c_rho, rowpart, groups,
+                       kCoulombTilesPerCta, s);
+    if (st) return st;
+  }
   CPC_LAUNCH_CHECK("tri_gram_kernel(ROWS)");
   item_reduce_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(n_items, off, c_items, rowpart, groups, n_factors,
                                                          P->h * P->h * P->h, J);
   CPC_LAUNCH_CHECK("item_reduce_kernel");
   return CPC_OK;
+}
+
+// ---- explicit spectra intermediates ------------------------------------------
+namespace cpc {
+int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uhat64, float2* Uhat32,
+                    cudaStream_t s);
+int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W, int precision,
+                          cudaStream_t s);
+}  // namespace cpc
+
+extern "C" int cp_factor_spectra(const cpc_kernel* P, int R_f, const double* U, void* spec, int precision,
+                                 void* stream) {
+  clear_error();
+  if (!P || P->kind != CPC_KERNEL_CONV || R_f <= 0 || !U || !spec)
+    return fail(CPC_ERR_INVALID, "cp_factor_spectra: bad arguments");
+  if (precision != CPC_FP64 && precision != CPC_FP32)
+    return fail(CPC_ERR_UNSUPPORTED, "cp_factor_spectra: precision form not implemented");
+  if ((reinterpret_cast<uintptr_t>(U) & 15) || (reinterpret_cast<uintptr_t>(spec) & 15))
+    return fail(CPC_ERR_INVALID, "cp_factor_spectra: U and spec must be 16-byte aligned");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (precision == CPC_FP64) return forward_spectra(P, 3 * R_f, U, static_cast<double2*>(spec), nullptr, s);
+  return forward_spectra(P, 3 * R_f, U, nullptr, static_cast<float2*>(spec), s);
+}
+
+extern "C" int cp_convolve_from_spectra(const cpc_kernel* P, int R_f, const void* spec, void* W, int precision,
+                                        void* stream) {
+  clear_error();
+  if (!P || P->kind != CPC_KERNEL_CONV || R_f <= 0 || !spec || !W)
+    return fail(CPC_ERR_INVALID, "cp_convolve_from_spectra: bad arguments");
+  if (precision != CPC_FP64 && precision != CPC_FP32)
+    return fail(CPC_ERR_UNSUPPORTED, "cp_convolve_from_spectra: precision form not implemented");
+  if ((reinterpret_cast<uintptr_t>(W) & 15) || (reinterpret_cast<uintptr_t>(spec) & 15))
+    return fail(CPC_ERR_INVALID, "cp_convolve_from_spectra: spec and W must be 16-byte aligned");
+  return convolve_from_spectra(P, 3 * R_f, spec, W, precision, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" size_t cp_hartree_energy_from_spectra_workspace(const cpc_kernel* P, int R_f) {
+  if (!P || R_f <= 0) return 0;
+  return align256(sizeof(double) * eh32_partials(R_f, P->R_N));
+}
+
+extern "C" int cp_hartree_energy_from_spectra(const cpc_kernel* P, int R_f, const void* spec, const double* c,
+                                              double* G, double* E_H, int precision, void* ws, size_t ws_bytes,
+                                              void* stream) {
+  clear_error();
+  if (!P || P->kind != CPC_KERNEL_CONV || R_f <= 0 || !spec || !c || !E_H)
+    return fail(CPC_ERR_INVALID, "cp_hartree_energy_from_spectra: bad arguments");
+  if (precision != CPC_FP32)
+    return fail(CPC_ERR_UNSUPPORTED, "cp_hartree_energy_from_spectra: only the float32 form contracts spectra");
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < cp_hartree_energy_from_spectra_workspace(P, R_f))
+    return fail(CPC_ERR_WORKSPACE, "cp_hartree_energy_from_spectra: workspace missing, misaligned or too small");
+  return launch_eh_spectral(P, R_f, static_cast<const float2*>(spec), c, G, E_H, static_cast<double*>(ws),
+                            static_cast<cudaStream_t>(stream));
 }

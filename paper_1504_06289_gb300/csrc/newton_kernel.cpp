@@ -279,6 +279,10 @@ int make_newton_kernel(int n, double b, int M, int kind, void* stream, cpc_kerne
     if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: FFT tables"); cleanup(); return st; }
     st = compute_kernel_spectrum(P, s);
     if (st != CPC_OK) { cleanup(); return st; }
+    e = cudaMalloc(&P->d_specw32, sizeof(float) * size_t(P->R_N) * 2 * (n + 1));
+    if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: spectral weights"); cleanup(); return st; }
+    st = build_spectral_weights(P, P->d_specw32, s);
+    if (st != CPC_OK) { cleanup(); return st; }
   }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: synchronize"); cleanup(); return st; }
@@ -316,6 +320,7 @@ int cpc_kernel_free(cpc_kernel* P) {
   cudaFree(P->d_tw32);
   cudaFree(P->d_hw64);
   cudaFree(P->d_hw32);
+  cudaFree(P->d_specw32);
   delete P;
   return CPC_OK;
 }

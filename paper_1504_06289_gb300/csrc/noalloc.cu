@@ -26,10 +26,8 @@ namespace cpc {
 
 int check_conv_args(const cpc_kernel* P, int R_f, const void* U, const void* W, int precision,
                     void* ws, size_t ws_bytes, const char* who);
-int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision, void* ws,
-                 cudaStream_t s);
-int launch_eh(const cpc_kernel* P, int R_f, const double* U, const double* c, const void* W,
-              double* G, double* E_H, int precision, double* partial, cudaStream_t s);
+int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const double* c, void* W, double* G,
+                       double* E_H, int precision, void* ws, cudaStream_t s);
 
 namespace {
 
@@ -81,10 +79,5 @@ extern "C" int cp_hartree_energy_noalloc(const cpc_kernel* P, int R_f, const dou
   if (st) return st;
   st = check_conv_args(P, R_f, U, W, precision, ws, kScratchBytes, "cp_hartree_energy_noalloc");
   if (st) return st;
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  st = run_convolve(P, R_f, U, W, precision, ws, s);
-  if (st) return st;
-  double* partial = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) +
-                                              cp_convolve_workspace(P, R_f, precision));
-  return launch_eh(P, R_f, U, c, W, G, E_H, precision, partial, s);
+  return run_hartree_energy(P, R_f, U, c, W, G, E_H, precision, ws, static_cast<cudaStream_t>(stream));
 }

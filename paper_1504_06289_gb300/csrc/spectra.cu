@@ -29,14 +29,18 @@ namespace {
 constexpr int kMaxLogN = 13;  // n <= 8192 for convolution kernels
 constexpr int kMinLogN = 4;
 
-template <int LOGN> constexpr int pick_logp() { return LOGN <= 4 ? LOGN - 1 : 4; }
+// points per thread: 16 (float64, small n) or 32 (float32, n >= 1024: three passes for n = 8192)
+template <typename T, int LOGN> constexpr int pick_logp() {
+  return LOGN <= 4 ? LOGN - 1 : ((sizeof(T) == 4 && LOGN >= 10) ? 5 : 4);
+}
 
-template <int LOGN>
+template <int LOGN, typename T = double>
 struct Geometry {
-  static constexpr int LOGP = pick_logp<LOGN>();
+  static constexpr int LOGP = pick_logp<T, LOGN>();
   using PL = FftPlan<LOGN, LOGP>;
-  static constexpr int slots = PL::TPF >= 128 ? 1 : 128 / PL::TPF;
+  static constexpr int slots = PL::TPF >= 256 ? 1 : 256 / PL::TPF;
   static constexpr int threads = slots * PL::TPF;
+  static constexpr int min_blocks = threads >= 512 ? 1 : 2;
 };
 
 // ---------------------------------------------------------------------------
@@ -118,12 +122,12 @@ spectra_kernel(int mode, const double* __restrict__ src, int ncols, double2* __r
 // ---------------------------------------------------------------------------
 // batched convolution: item = col * R_N + q writes W[item][0..n-1].
 template <typename T, int LOGN>
-__global__ void __launch_bounds__(Geometry<LOGN>::threads)
+__global__ void __launch_bounds__(Geometry<LOGN, T>::threads, Geometry<LOGN, T>::min_blocks)
 conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict__ phat,
             const typename cvec<T>::type* __restrict__ hw, const typename cvec<T>::type* __restrict__ tw,
             T* __restrict__ W, int R_N, long long n_items) {
   using V = typename cvec<T>::type;
-  using G = Geometry<LOGN>;
+  using G = Geometry<LOGN, T>;
   using PL = typename G::PL;
   constexpr int NC = PL::NC;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -131,7 +135,12 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
   const int t = threadIdx.x % PL::TPF;
   V* sbuf = reinterpret_cast<V*>(smem_raw) + slot * padded_len(NC);
   const T scale = T(1) / T(2 * NC);
-  for (long long g = blockIdx.x; g * G::slots < n_items; g += gridDim.x) {
+  // contiguous group range per CTA: consecutive items share a factor column,
+  // so its spectrum stays in L1 across the kernel terms q
+  const long long n_groups = (n_items + G::slots - 1) / G::slots;
+  const long long g_begin = n_groups * blockIdx.x / gridDim.x;
+  const long long g_end = n_groups * (blockIdx.x + 1) / gridDim.x;
+  for (long long g = g_begin; g < g_end; ++g) {
     const long long item = g * G::slots + slot;
     const bool active = item < n_items;
     const long long it = active ? item : n_items - 1;
@@ -217,7 +226,7 @@ int launch_spectra(int mode, const double* src, int ncols, double2* o64, float2*
 
 template <typename T, int LOGN>
 int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, cudaStream_t s) {
-  using G = Geometry<LOGN>;
+  using G = Geometry<LOGN, T>;
   using V = typename cvec<T>::type;
   const size_t smem = sizeof(V) * G::slots * padded_len(1 << LOGN);
   auto kern = conv_kernel<T, LOGN>;

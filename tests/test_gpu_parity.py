@@ -99,12 +99,25 @@ def test_convolution_and_energy_fp32(cpc, name, spec):
     _, _, P0 = oracle_conv_kernel(n, b, M)
     U = cpc.cp_sample_gaussians(n, b, dev(g["a"]), dev(g["X"]))
     U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
-    E, W, _ = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp32")
+    E, W, G = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp32", want_G=True)
     assert W.dtype == torch.float32
     W0 = ocp.convolve_factors(U0, P0)
     assert col_rel_err(W.cpu().numpy(), W0) < 2e-6
-    E0 = ocp.hartree_energy(U0, g["c"], P0, h)
-    assert abs(E.item() / E0 - 1) < 1e-5
+    G0 = ocp.conv_matrices(U0, W0, P0.shape[0])
+    E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
+    # float32 form target: E_H within 1e-7 of float64
+    assert abs(E.item() / E0 - 1) < 1e-7
+    assert rel(G.cpu().numpy(), G0) < 1e-6
+    # the explicit pipeline gives the same numbers
+    spec = cpc.cp_factor_spectra(P, U, "fp32")
+    W2 = cpc.cp_convolve_from_spectra(P, spec, "fp32")
+    assert torch.equal(W, W2)
+    E2, _ = cpc.cp_hartree_energy_from_spectra(P, spec, dev(g["c"]))
+    assert E2.item() == E.item()
+    # spatial float32 contraction of the float32 factors
+    E3, G3 = cpc.cp_hartree_energy_from_factors(P, U, dev(g["c"]), W, "fp32", want_G=True)
+    assert abs(E3.item() / E0 - 1) < 2e-6
+    assert rel(G3.cpu().numpy(), G0) < 2e-6
 
 
 def test_adjoint_and_parameter_gradients_fp64(cpc):
