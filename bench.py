@@ -44,8 +44,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "split", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="steps of the float64 and split forms timed for comparison (0: skip)")
     ap.add_argument("--seed", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rf", type=int, default=None,
@@ -226,13 +227,12 @@ def run_ours(args, ws, rank, local):
     lib = cpc.load()
 
     def buffers(prec):
-        dt = torch.float64 if prec == "fp64" else torch.float32
+        dt = torch.float32 if prec == "fp32" else torch.float64
         W = torch.empty((3, R_f * R_N, n), dtype=dt, device=dev)
         U = torch.empty((3, R_f, n), dtype=torch.float64, device=dev)
         S = torch.empty((3, R_f, n + 1, 2), dtype=dt, device=dev)
         E = torch.empty((), dtype=torch.float64, device=dev)
-        nb = (lib.cp_hartree_energy_from_factors_workspace(P.handle, R_f) if prec == "fp64"
-              else lib.cp_hartree_energy_from_spectra_workspace(P.handle, R_f))
+        nb = lib.cp_hartree_energy_from_factors_workspace(P.handle, R_f)
         ws_g = torch.empty(max(256, nb), dtype=torch.uint8, device=dev)
         return W, U, S, E, ws_g
 
@@ -251,14 +251,9 @@ def run_ours(args, ws, rank, local):
                   "cp_convolve_from_spectra")
         if ev is not None:
             ev[2].record(stream)
-        if prec == "fp64":
-            cpc.check(lib.cp_hartree_energy_from_factors(P.handle, R_f, cpc._ptr(U), cpc._ptr(c), cpc._ptr(W), None,
-                                                         cpc._ptr(E), pr, cpc._ptr(ws_g), ws_g.numel(), sp),
-                      "cp_hartree_energy_from_factors")
-        else:
-            cpc.check(lib.cp_hartree_energy_from_spectra(P.handle, R_f, cpc._ptr(S), cpc._ptr(c), None, cpc._ptr(E),
-                                                         pr, cpc._ptr(ws_g), ws_g.numel(), sp),
-                      "cp_hartree_energy_from_spectra")
+        cpc.check(lib.cp_hartree_energy_from_factors(P.handle, R_f, cpc._ptr(U), cpc._ptr(c), cpc._ptr(W), None,
+                                                     cpc._ptr(E), pr, cpc._ptr(ws_g), ws_g.numel(), sp),
+                  "cp_hartree_energy_from_factors")
         if ev is not None:
             ev[3].record(stream)
         return E
@@ -305,51 +300,58 @@ def run_ours(args, ws, rank, local):
     e2e_s = max_over_ranks(time.perf_counter() - t0, ws, dev)
     h2d = a_h.numel() * 8 + X_h.numel() * 8 + c_h.numel() * 8
 
-    # plain float64 GPU path on the same GPU (the baseline the reduced-precision form is compared with)
-    fp64 = None
-    if args.fp64_steps > 0 and prec != "fp64":
+    # the other precision forms on the same GPU and inputs: plain float64 (the
+    # baseline) and split (float64 convolutions, float32-product contractions)
+    others = {}
+    if args.fp64_steps > 0:
         del bufs
         torch.cuda.empty_cache()
-        b64 = buffers("fp64")
-        step("fp64", b64)
-        torch.cuda.synchronize(dev)
-        e64 = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.fp64_steps)]
-        s64, t64 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s64.record(stream)
-        for k in range(args.fp64_steps):
-            step("fp64", b64, e64[k])
-        t64.record(stream)
-        torch.cuda.synchronize(dev)
-        ms64 = s64.elapsed_time(t64) / args.fp64_steps
-        E64 = b64[3].item()
-        fp64 = {"ms_per_step": ms64, "value": convs_per_step / (ms64 * 1e-3),
-                "spectra_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in e64])),
-                "conv_ms": float(np.mean([e[1].elapsed_time(e[2]) for e in e64])),
-                "contraction_ms": float(np.mean([e[2].elapsed_time(e[3]) for e in e64])),
-                "E_H": E64, "rel_err_E_H_of_fast_form": abs(E_fast / E64 - 1)}
-        del b64
-        torch.cuda.empty_cache()
+        for form in ("fp64", "split"):
+            if form == prec:
+                continue
+            bf = buffers(form)
+            step(form, bf)
+            torch.cuda.synchronize(dev)
+            eo = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.fp64_steps)]
+            so, to = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            so.record(stream)
+            for k in range(args.fp64_steps):
+                step(form, bf, eo[k])
+            to.record(stream)
+            torch.cuda.synchronize(dev)
+            mso = so.elapsed_time(to) / args.fp64_steps
+            others[form] = {"ms_per_step": mso, "value": convs_per_step / (mso * 1e-3),
+                            "spectra_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in eo])),
+                            "conv_ms": float(np.mean([e[1].elapsed_time(e[2]) for e in eo])),
+                            "contraction_ms": float(np.mean([e[2].elapsed_time(e[3]) for e in eo])),
+                            "E_H": bf[3].item()}
+            del bf
+            torch.cuda.empty_cache()
+        E64 = others.get("fp64", {}).get("E_H", E_fast if prec == "fp64" else None)
+        if E64 is not None:
+            for form, o in others.items():
+                o["rel_err_E_H_vs_fp64_gpu"] = abs(o["E_H"] / E64 - 1)
+    fp64 = others.get("fp64")
 
     if rank != 0:
         return
     peaks, peak_kind = load_peaks()
     hbm_peak = float(peaks["hbm_gbs"])
     clk = clocks.summary()
-    elem = 8 if prec == "fp64" else 4
+    elem = 4 if prec == "fp32" else 8
     # conv kernel algorithmic bytes per step: write all V_H factors, read spectra of U and p
     conv_bytes = 3 * R_f * R_N * n * elem + 3 * R_f * (n + 1) * 2 * elem + R_N * (n + 1) * elem
     conv_gbs = conv_bytes / (conv_ms * 1e-3) / 1e9
     # contraction: unique Gram entries (symmetric) x 3 axes x R_N, 2 flop per multiply-add over
     # K = 2(n+1) spectral values (float32 form, Parseval) or n cells (float64 form)
-    K_con = 2 * (n + 1) if prec != "fp64" else n
-    gram_flops = 3 * R_N * (R_f * (R_f + 1) // 2) * K_con * 2
+    gram_flops = 3 * R_N * (R_f * (R_f + 1) // 2) * n * 2
     sm_mhz = clk["sm_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak_tf = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12 if prec != "fp64" else None
     gram_tf = gram_flops / (gram_ms * 1e-3) / 1e12
     kernels = {
         "conv_kernel": {"ms": conv_ms, "bound": "hbm", "achieved": conv_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": conv_gbs / hbm_peak, "algorithmic_bytes": conv_bytes},
-        "gemm3_kernel" if prec != "fp64" else "tri_gram_kernel": {"ms": gram_ms, "bound": "alu", "achieved": gram_tf, "unit": "TFLOP/s",
+        {"fp32": "gemm3a_kernel", "split": "gemm3_kernel", "fp64": "tri_gram_kernel"}[prec]: {"ms": gram_ms, "bound": "alu", "achieved": gram_tf, "unit": "TFLOP/s",
                             "peak": alu_peak_tf, "frac": (gram_tf / alu_peak_tf) if alu_peak_tf else None,
                             "algorithmic_flops": gram_flops,
                             "peak_note": "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x median SM clock"},
@@ -370,11 +372,13 @@ def run_ours(args, ws, rank, local):
         "E_H": E_fast, "E_H_evals_per_s": ws * args.steps / (ms_total * 1e-3),
         "phases_ms": {"spectra": spec_ms, "convolve": conv_ms, "contraction": gram_ms},
         "kernels": kernels, "roofline": roofline,
-        "fp64_gpu": fp64,
+        "other_forms": others,
+        "rel_err_E_H_vs_fp64_gpu": (abs(E_fast / fp64["E_H"] - 1) if fp64 else 0.0),
         "speedup_vs_fp64_gpu": (fp64["ms_per_step"] / ms_step) if fp64 else None,
         "e2e": {"value": ws * convs_per_step * e2e_steps / e2e_s, "unit": "convolutions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
-        "gpu_launches": 5 * args.steps,  # sample, spectra, conv, contraction, final sum
+        # sample, spectra, conv, [float32 rounding of U,] contraction, final sum
+        "gpu_launches": (6 if prec == "fp32" else 5) * args.steps,
         "clocks": clk,
     }
     if ws == 1 and not args.no_cpu_baseline:

@@ -26,12 +26,15 @@
  *           default stream).  Calls are stream-ordered and do not
  *           synchronise, except make_newton_kernel (which returns with its
  *           tables ready) and the host-side validation before any launch.
- *   Precision: CPC_FP64 computes in float64 throughout; CPC_FP32 runs the
- *           bulk convolutions in float32 (factor outputs stored as float) and
- *           the contractions with float32 products summed in float64;
- *           CPC_SPLIT is reserved for compensated forms and returns
- *           CPC_ERR_UNSUPPORTED where not implemented.  Kernel nodes, weights,
- *           cell integrals and final cross-rank reductions are float64 in
+ *   Precision: CPC_FP64 computes in float64 throughout.  CPC_FP32 runs the
+ *           bulk convolutions in float32 (V_H factors stored as float) and
+ *           the contractions with float32 products, float32 partial sums over
+ *           chunks of 256 cells and float64 cross-tile reductions.  CPC_SPLIT
+ *           keeps the convolutions in float64 (V_H factors stored as double,
+ *           exactly as CPC_FP64) and runs the contractions with float32
+ *           products as in CPC_FP32, so E_H loses only the float32 rounding
+ *           of its operands.  Kernel nodes, weights, cell integrals, spectra
+ *           of the factors and final cross-rank reductions are float64 in
  *           every form.
  *   Errors: every entry point returns CPC_OK (0) or a negative status; no
  *           exception or abort crosses the ABI.  Arguments are validated on
@@ -116,7 +119,7 @@ int cp_hadamard_pairs(int n, int n_in, int n_pairs, const int* pa, const int* pb
  * W[l][k*R_N + q][i] = sum_{j=0}^{n-1} U[l][k][j] * p_q[i - j],  i = 0..n-1,
  * for every axis l, rank k < R_f and kernel term q < R_N of a CONV kernel:
  * the factors of V_H = f * P_R.  U: [3][R_f][n] float64.  W: [3][R_f*R_N][n],
- * float64 for CPC_FP64, float32 for CPC_FP32.  Implemented as length-2n real
+ * float64 for CPC_FP64 and CPC_SPLIT, float32 for CPC_FP32.  Implemented as length-2n real
  * FFT convolutions in the chosen precision (the spectra of U are formed in
  * float64).  Workspace: cp_convolve_workspace bytes. */
 size_t cp_convolve_workspace(const cpc_kernel* P, int R_f, int precision);
@@ -138,12 +141,10 @@ int cp_convolve_from_spectra(const cpc_kernel* P, int R_f, const void* spec, voi
  * E_H = h^3 sum_q sum_{k,k'} c_k c_k' prod_l G[l][q][k'][k]
  *     = h^3 <f, P_R * f>      (Sec. 2.5 Eq. scal with Eq. conv).
  * Runs cp_convolve into W (required: it receives the V_H factors, type as
- * in cp_convolve), then the contraction.  CPC_FP64 contracts U with the
- * float64 V_H factors.  CPC_FP32 contracts the float32-rounded float64
- * spectra instead (Parseval on the length-2n circle: G_q[k',k] =
- * (1/2n) sum_f w_f p^_q[f] Re(U^_k'[f] conj U^_k[f]), w_0 = w_n = 1, else 2),
- * so E_H does not inherit the float32 FFT error of the V_H factors; float32
- * products, float32 sums over chunks of 256, float64 final reduction.  c: [R_f] float64.  G: NULL or
+ * in cp_convolve), then the contraction of U with W: float64 throughout for
+ * CPC_FP64; float32 products of U and W (both rounded to float32 on load for
+ * CPC_SPLIT), float32 sums over chunks of 256 cells, float64 final
+ * reduction for CPC_FP32 and CPC_SPLIT.  c: [R_f] float64.  G: NULL or
  * [3][R_N][R_f][R_f] float64 (needed by the adjoint).  E_H: one float64 on
  * the device.  Workspace: cp_hartree_energy_workspace bytes. */
 size_t cp_hartree_energy_workspace(const cpc_kernel* P, int R_f, int precision);
@@ -160,9 +161,13 @@ int cp_hartree_energy_from_factors(const cpc_kernel* P, int R_f, const double* U
                                    const void* W, double* G, double* E_H, int precision, void* ws,
                                    size_t ws_bytes, void* stream);
 
-/* The float32 form's contraction from float32 spectra (as written by
- * cp_factor_spectra with CPC_FP32): G (may be NULL) and E_H as in
- * cp_hartree_energy.  precision must be CPC_FP32.
+/* E_H without the V_H factors: the convolution matrices by Parseval on the
+ * length-2n circle from float32 spectra (as written by cp_factor_spectra
+ * with CPC_FP32), G_q[k',k] = (1/2n) sum_f w_f p^_q[f] Re(U^_k'[f] conj U^_k[f]),
+ * w_0 = w_n = 1, else 2; float32 products and sums (chunks of 256), float64
+ * final reduction.  G (may be NULL) and E_H as in cp_hartree_energy.  The
+ * spectral sums cancel, so the error is comparable to the spatial float32
+ * form at twice its flops; it needs no V_H factors.  precision: CPC_FP32.
  * Workspace: cp_hartree_energy_from_spectra_workspace bytes. */
 size_t cp_hartree_energy_from_spectra_workspace(const cpc_kernel* P, int R_f);
 int cp_hartree_energy_from_spectra(const cpc_kernel* P, int R_f, const void* spec, const double* c,

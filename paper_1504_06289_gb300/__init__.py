@@ -50,7 +50,8 @@ def _prec(p: str) -> int:
 
 
 def _out_dtype(precision: str):
-    return torch.float64 if precision == "fp64" else torch.float32
+    """Storage type of V_H factors and spectra: float32 only for the fp32 form."""
+    return torch.float32 if precision == "fp32" else torch.float64
 
 
 def _workspace(nbytes: int, device) -> torch.Tensor:

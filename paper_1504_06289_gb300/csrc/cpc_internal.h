@@ -5,6 +5,7 @@
 
 #include <type_traits>
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 #include <string>
@@ -81,9 +82,17 @@ int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void
 size_t eh32_partials(int R_f, int R_N);
 int build_spectral_weights(const cpc_kernel* P, float* d, cudaStream_t s);
 int launch_eh32(const cpc_kernel* P, int R_f, const double* U, const float* W, const float* S32,
-                const float* dtab, const double* c, double* G, double* partial, cudaStream_t s);
+                const float* dtab, const double* c, double* G, double* partial, cudaStream_t s,
+                const double* W64 = nullptr);
 int launch_rows32(const cpc_kernel* P, int n_factors, const double* U_items, int N, const float* W,
-                  const double* c_rho, double* rowpart, int groups, int tiles_per_cta, cudaStream_t s);
+                  const double* c_rho, double* rowpart, int groups, int tiles_per_cta, cudaStream_t s,
+                  const double* W64 = nullptr);
+size_t eh32a_partials(int R_f, int R_N);
+size_t eh32a_u32_bytes(const cpc_kernel* P, int R_f);
+int launch_eh32a(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
+                 double* partial, float* U32, cudaStream_t s);
+// the V_H factors and spectra of CPC_SPLIT are float64, like CPC_FP64
+inline int storage_precision(int precision) { return precision == CPC_FP32 ? CPC_FP32 : CPC_FP64; }
 size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision);
 
 }  // namespace cpc

@@ -307,7 +307,12 @@ static int tiles(int x) { return (x + TM - 1) / TM; }
 
 size_t eh_partials(const cpc_kernel* P, int R_f) {
   const int T = tiles(R_f);
-  return std::max(size_t(T) * (T + 1) / 2 * P->R_N, eh32_partials(R_f, P->R_N));
+  return std::max({size_t(T) * (T + 1) / 2 * P->R_N, eh32_partials(R_f, P->R_N), eh32a_partials(R_f, P->R_N)});
+}
+
+// contraction workspace: partial sums, then (float32 form) a float32 copy of U
+size_t contraction_workspace(const cpc_kernel* P, int R_f) {
+  return align256(sizeof(double) * eh_partials(P, R_f)) + eh32a_u32_bytes(P, R_f);
 }
 
 // E_H from float32 spectra (Parseval contraction), partials in `partial`.
@@ -322,7 +327,8 @@ int launch_eh_spectral(const cpc_kernel* P, int R_f, const float2* spec32, const
 }
 
 int launch_eh(const cpc_kernel* P, int R_f, const double* U, const double* c, const void* W,
-              double* G, double* E_H, int precision, double* partial, cudaStream_t s) {
+              double* G, double* E_H, int precision, void* cws, cudaStream_t s) {
+  double* partial = static_cast<double*>(cws);
   const int n = P->n;
   const int T = tiles(R_f);
   dim3 grid(T * (T + 1) / 2, P->R_N);
@@ -333,10 +339,15 @@ int launch_eh(const cpc_kernel* P, int R_f, const double* U, const double* c, co
     tri_gram_kernel<double, MODE_EH><<<grid, TPB, 0, s>>>(n, R_f, R_f, U, a_axis, static_cast<const double*>(W),
                                                            b_axis, P->R_N, c, c, 1, partial, G, 0);
     CPC_LAUNCH_CHECK("tri_gram_kernel(EH)");
-  } else {
-    int st = launch_eh32(P, R_f, U, static_cast<const float*>(W), nullptr, nullptr, c, G, partial, s);
+  } else if (precision == CPC_SPLIT) {
+    int st = launch_eh32(P, R_f, U, nullptr, nullptr, nullptr, c, G, partial, s, static_cast<const double*>(W));
     if (st) return st;
     count = (long long)eh32_partials(R_f, P->R_N);
+  } else {
+    float* U32 = reinterpret_cast<float*>(static_cast<unsigned char*>(cws) + align256(sizeof(double) * eh_partials(P, R_f)));
+    int st = launch_eh32a(P, R_f, U, static_cast<const float*>(W), c, G, partial, U32, s);
+    if (st) return st;
+    count = (long long)eh32a_partials(R_f, P->R_N);
   }
   finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, count, P->h * P->h * P->h, E_H);
   CPC_LAUNCH_CHECK("finalize_sum_kernel");
@@ -344,17 +355,13 @@ int launch_eh(const cpc_kernel* P, int R_f, const double* U, const double* c, co
 }
 
 // cp_hartree_energy after argument checks: convolution into W, then the
-// contraction (float64: spatial on W; float32: Parseval on the float32 copy
-// of the float64 spectra that run_convolve leaves at the start of ws).
+// spatial contraction of U with W in the form's precision.
 int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const double* c, void* W, double* G,
                        double* E_H, int precision, void* ws, cudaStream_t s) {
   int st = run_convolve(P, R_f, U, W, precision, ws, s);
   if (st) return st;
-  double* partial = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_f, precision));
-  if (precision == CPC_FP64) return launch_eh(P, R_f, U, c, W, G, E_H, precision, partial, s);
-  const float2* spec32 = reinterpret_cast<const float2*>(static_cast<unsigned char*>(ws) +
-                                                         spectra_bytes(P, 3 * R_f, CPC_FP64));
-  return launch_eh_spectral(P, R_f, spec32, c, G, E_H, partial, s);
+  void* cws = static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_f, precision);
+  return launch_eh(P, R_f, U, c, W, G, E_H, precision, cws, s);
 }
 
 }  // namespace cpc
@@ -363,7 +370,7 @@ using namespace cpc;
 
 extern "C" size_t cp_hartree_energy_workspace(const cpc_kernel* P, int R_f, int precision) {
   if (!P || R_f <= 0) return 0;
-  return cp_convolve_workspace(P, R_f, precision) + align256(sizeof(double) * eh_partials(P, R_f));
+  return cp_convolve_workspace(P, R_f, precision) + contraction_workspace(P, R_f);
 }
 
 extern "C" int cp_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const double* c, void* W,
@@ -380,7 +387,7 @@ extern "C" int cp_hartree_energy(const cpc_kernel* P, int R_f, const double* U, 
 
 extern "C" size_t cp_hartree_energy_from_factors_workspace(const cpc_kernel* P, int R_f) {
   if (!P || R_f <= 0) return 0;
-  return align256(sizeof(double) * eh_partials(P, R_f));
+  return contraction_workspace(P, R_f);
 }
 
 extern "C" int cp_hartree_energy_from_factors(const cpc_kernel* P, int R_f, const double* U, const double* c,
@@ -389,11 +396,11 @@ extern "C" int cp_hartree_energy_from_factors(const cpc_kernel* P, int R_f, cons
   clear_error();
   if (!P || P->kind != CPC_KERNEL_CONV) return fail(CPC_ERR_INVALID, "cp_hartree_energy_from_factors: needs a CONV kernel");
   if (R_f <= 0 || !U || !c || !W || !E_H) return fail(CPC_ERR_INVALID, "cp_hartree_energy_from_factors: bad arguments");
-  if (precision != CPC_FP64 && precision != CPC_FP32)
+  if (precision != CPC_FP64 && precision != CPC_FP32 && precision != CPC_SPLIT)
     return fail(CPC_ERR_UNSUPPORTED, "cp_hartree_energy_from_factors: precision form not implemented");
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < cp_hartree_energy_from_factors_workspace(P, R_f))
     return fail(CPC_ERR_WORKSPACE, "cp_hartree_energy_from_factors: workspace missing, misaligned or too small");
-  return launch_eh(P, R_f, U, c, W, G, E_H, precision, static_cast<double*>(ws), static_cast<cudaStream_t>(stream));
+  return launch_eh(P, R_f, U, c, W, G, E_H, precision, ws, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int cp_hartree_energy_adjoint(const cpc_kernel* P, int R_f, const double* c, const void* W,
@@ -402,13 +409,13 @@ extern "C" int cp_hartree_energy_adjoint(const cpc_kernel* P, int R_f, const dou
   clear_error();
   if (!P || P->kind != CPC_KERNEL_CONV) return fail(CPC_ERR_INVALID, "cp_hartree_energy_adjoint: needs a CONV kernel");
   if (R_f <= 0 || !c || !W || !G || !dU) return fail(CPC_ERR_INVALID, "cp_hartree_energy_adjoint: bad arguments");
-  if (precision != CPC_FP64 && precision != CPC_FP32)
+  if (precision != CPC_FP64 && precision != CPC_FP32 && precision != CPC_SPLIT)
     return fail(CPC_ERR_UNSUPPORTED, "cp_hartree_energy_adjoint: precision form not implemented");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n = P->n;
   const double scale = 2.0 * P->h * P->h * P->h;
   dim3 grid((n + TN - 1) / TN, tiles(R_f), 3);
-  if (precision == CPC_FP64)
+  if (storage_precision(precision) == CPC_FP64)
     adjoint_gemm_kernel<double><<<grid, TPB, 0, s>>>(n, R_f, P->R_N, c, G, static_cast<const double*>(W), scale, dU);
   else
     adjoint_gemm_kernel<float><<<grid, TPB, 0, s>>>(n, R_f, P->R_N, c, G, static_cast<const float*>(W), scale, dU);
@@ -460,7 +467,11 @@ extern "C" int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, 
   if (precision == CPC_FP64)
     tri_gram_kernel<double, MODE_ROWS><<<grid, TPB, 0, s>>>(n, n_factors, N, U_items, a_axis,
         static_cast<const double*>(W_rho), b_axis, 1, nullptr, c_rho, P->R_N, rowpart, nullptr, kCoulombTilesPerCta);
-  else {
+  else if (precision == CPC_SPLIT) {
+    st = launch_rows32(P, n_factors, U_items, N, nullptr, c_rho, rowpart, groups, kCoulombTilesPerCta, s,
+                       static_cast<const double*>(W_rho));
+    if (st) return st;
+  } else {
     st = launch_rows32(P, n_factors, U_items, N, static_cast<const float*>(W_rho), c_rho, rowpart, groups,
                        kCoulombTilesPerCta, s);
     if (st) return st;
@@ -485,8 +496,9 @@ extern "C" int cp_factor_spectra(const cpc_kernel* P, int R_f, const double* U, 
   clear_error();
   if (!P || P->kind != CPC_KERNEL_CONV || R_f <= 0 || !U || !spec)
     return fail(CPC_ERR_INVALID, "cp_factor_spectra: bad arguments");
-  if (precision != CPC_FP64 && precision != CPC_FP32)
+  if (precision != CPC_FP64 && precision != CPC_FP32 && precision != CPC_SPLIT)
     return fail(CPC_ERR_UNSUPPORTED, "cp_factor_spectra: precision form not implemented");
+  precision = storage_precision(precision);
   if ((reinterpret_cast<uintptr_t>(U) & 15) || (reinterpret_cast<uintptr_t>(spec) & 15))
     return fail(CPC_ERR_INVALID, "cp_factor_spectra: U and spec must be 16-byte aligned");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -499,8 +511,9 @@ extern "C" int cp_convolve_from_spectra(const cpc_kernel* P, int R_f, const void
   clear_error();
   if (!P || P->kind != CPC_KERNEL_CONV || R_f <= 0 || !spec || !W)
     return fail(CPC_ERR_INVALID, "cp_convolve_from_spectra: bad arguments");
-  if (precision != CPC_FP64 && precision != CPC_FP32)
+  if (precision != CPC_FP64 && precision != CPC_FP32 && precision != CPC_SPLIT)
     return fail(CPC_ERR_UNSUPPORTED, "cp_convolve_from_spectra: precision form not implemented");
+  precision = storage_precision(precision);
   if ((reinterpret_cast<uintptr_t>(W) & 15) || (reinterpret_cast<uintptr_t>(spec) & 15))
     return fail(CPC_ERR_INVALID, "cp_convolve_from_spectra: spec and W must be 16-byte aligned");
   return convolve_from_spectra(P, 3 * R_f, spec, W, precision, static_cast<cudaStream_t>(stream));

@@ -301,6 +301,7 @@ using namespace cpc;
 
 extern "C" size_t cp_convolve_workspace(const cpc_kernel* P, int R_f, int precision) {
   if (!P || R_f <= 0) return 0;
+  precision = storage_precision(precision);
   // float32 forms keep a float64 copy of the spectra too (they are formed in float64)
   size_t b = spectra_bytes(P, 3 * R_f, precision);
   if (precision != CPC_FP64) b += spectra_bytes(P, 3 * R_f, CPC_FP64);
@@ -316,7 +317,7 @@ int check_conv_args(const cpc_kernel* P, int R_f, const void* U, const void* W, 
   if (!U || !W) return fail(CPC_ERR_INVALID, std::string(who) + ": NULL factor pointer");
   if ((reinterpret_cast<uintptr_t>(U) & 15) || (reinterpret_cast<uintptr_t>(W) & 15))
     return fail(CPC_ERR_INVALID, std::string(who) + ": U and W must be 16-byte aligned");
-  if (precision != CPC_FP64 && precision != CPC_FP32)
+  if (precision != CPC_FP64 && precision != CPC_FP32 && precision != CPC_SPLIT)
     return fail(CPC_ERR_UNSUPPORTED, std::string(who) + ": precision form not implemented");
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255))
     return fail(CPC_ERR_WORKSPACE, std::string(who) + ": workspace NULL or not 256-byte aligned");
@@ -328,6 +329,7 @@ int check_conv_args(const cpc_kernel* P, int R_f, const void* U, const void* W, 
 int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision, void* ws,
                  cudaStream_t s) {
   const int ncols = 3 * R_f;
+  precision = storage_precision(precision);
   unsigned char* w = static_cast<unsigned char*>(ws);
   double2* h64 = reinterpret_cast<double2*>(w);
   int st;

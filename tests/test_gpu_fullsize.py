@@ -66,11 +66,15 @@ def test_density600_n8192(cpc):
     assert abs(E64.item() / E_host - 1) < 1e-12
     del W64, G64
     torch.cuda.empty_cache()
-    # float32 form in the bench's configuration
+    # float32 and split forms in the bench's configuration
     E32, W32, _ = cpc.cp_hartree_energy(P, U, c, "fp32")
     cols32 = np.array([W32[l, k * R_N + q].double().cpu().numpy() for l, k, q in picks])
     assert col_rel_err(cols32, np.array(Wref)) < 2e-6
     assert abs(E32.item() / E64.item() - 1) < 5e-7
+    del W32
+    torch.cuda.empty_cache()
+    Es, Ws, _ = cpc.cp_hartree_energy(P, U, c, "split")
+    assert abs(Es.item() / E64.item() - 1) < 1e-7
 
 
 def test_density200_n4096_adjoint(cpc):
