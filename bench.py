@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rf", type=int, default=None,
                     help="override the rank R_f (profiling a smaller case of the same kernels)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    choices=[WORKLOAD, "basis80_n4096", "density200_n4096", "lattice32_n16384"],
+                    help="the default is the headline workload; the others time their own rows")
     return ap.parse_args()
 
 
@@ -386,11 +389,209 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(out), flush=True)
 
 
+def _timed(stream, fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def _line(args, ws, metric, value, unit, ms, dtype, config, **extra):
+    out = {"metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+           "data": "synthetic", "config": config}
+    out.update(extra)
+    print(json.dumps(out), flush=True)
+
+
+def run_coulomb(args, ws, rank, local):
+    """a8: all 3240 Coulomb-matrix entries of basis80_n4096 per step: density and
+    item factors by Hadamard products, V_H factors of rho, persistent contraction
+    (schedule from the autotuner), captured in one CUDA graph and replayed."""
+    import torch
+    import paper_1504_06289_gb300 as cpc
+    from oracle import coulomb as ocoul
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name = "basis80_n4096"
+    cfg = workloads.CONFIGS[name]
+    n, b, M = cfg["n"], cfg["b"], cfg["M"]
+    basis = workloads.basis_for(name, 3 + rank)
+    nb = cfg["n_basis"]
+    P = cpc.make_newton_kernel(n, b, M, device=dev)
+    first = basis["fn_first"]
+    centre = np.repeat(basis["fn_centre"], np.diff(first), axis=0)
+    t = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
+    alpha, cen, d = t(basis["prim_alpha"]), t(centre), t(basis["prim_d"])
+    pa, pb, _ = ocoul.density_pairs(basis)  # index bookkeeping only
+    sc = [basis["w"][mu] * (1.0 if x == y else 2.0)
+          for mu in range(nb) for x in range(first[mu], first[mu + 1]) for y in range(x, first[mu + 1])]
+    items = ocoul.item_list(nb)
+    ia, ib, _, off = ocoul.item_pairs(basis, items)
+    pa_t, pb_t, sc_t = t(pa, torch.int32), t(pb, torch.int32), t(sc)
+    ia_t, ib_t, off_t = t(ia, torch.int32), t(ib, torch.int32), t(off, torch.int32)
+    n_factors, R_rho = len(ia), len(pa)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for prec in (["fp32", "split"] if args.precision != "fp64" else ["fp64"]):
+        F = cpc.cp_sample_gaussians(n, b, alpha, cen)
+        U_rho, c_rho = cpc.cp_hadamard_pairs(F, pa_t, pb_t, d, sc_t)
+        U_it, c_it = cpc.cp_hadamard_pairs(F, ia_t, ib_t, d)
+        J, W_rho = cpc.coulomb_matrix(P, off_t, U_it, c_it, U_rho, c_rho, prec, tiles_per_cta="tune")
+        key = cpc._tune_key(P, n_factors, R_rho, prec, dev)
+        tiles = cpc._tune_lookup(key)["tiles_per_cta"]
+        wsb = torch.empty(cpc.load().coulomb_matrix_workspace(P.handle, len(items), n_factors, R_rho, cpc._prec(prec)),
+                          dtype=torch.uint8, device=dev)
+        def body():
+            cpc.load().cp_sample_gaussians(n, b, len(basis["prim_alpha"]), cpc._ptr(alpha), cpc._ptr(cen),
+                                           cpc._ptr(F), cpc._stream(stream))
+            cpc.load().cp_hadamard_pairs(n, F.shape[1], R_rho, cpc._ptr(pa_t), cpc._ptr(pb_t), cpc._ptr(F),
+                                         cpc._ptr(d), cpc._ptr(sc_t), cpc._ptr(U_rho), cpc._ptr(c_rho),
+                                         cpc._stream(stream))
+            cpc.load().cp_hadamard_pairs(n, F.shape[1], n_factors, cpc._ptr(ia_t), cpc._ptr(ib_t), cpc._ptr(F),
+                                         cpc._ptr(d), None, cpc._ptr(U_it), cpc._ptr(c_it), cpc._stream(stream))
+            cpc.check(cpc.load().coulomb_matrix(P.handle, len(items), cpc._ptr(off_t), n_factors, cpc._ptr(U_it),
+                                                cpc._ptr(c_it), R_rho, cpc._ptr(U_rho), cpc._ptr(c_rho),
+                                                cpc._ptr(W_rho), cpc._ptr(J), cpc._prec(prec), int(tiles),
+                                                cpc._ptr(wsb), wsb.numel(), cpc._stream(stream)), "coulomb_matrix")
+        body()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            body()
+        ms = _timed(stream, g.replay, args.steps, max(1, args.warmup))
+        res[prec] = {"ms_per_step": ms, "tiles_per_cta": tiles, "J_diag_sum_w": float(np.dot(
+            basis["w"], J.cpu().numpy()[[items.index((m, m)) for m in range(nb)]]))}
+        del U_it, W_rho, wsb
+        torch.cuda.empty_cache()
+    if rank != 0:
+        return
+    head = "fp32" if "fp32" in res else "fp64"
+    ms = res[head]["ms_per_step"]
+    flops = 2.0 * 3 * n_factors * R_rho * P.R_N * n
+    clk = 2070.0
+    peak = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12
+    achieved = flops / (ms * 1e-3) / 1e12
+    if "split" in res:
+        res["split"]["rel_diff_E_vs_fp32"] = abs(res["split"]["J_diag_sum_w"] / res["fp32"]["J_diag_sum_w"] - 1)
+    _line(args, ws, "Coulomb-matrix entries/s", ws * len(items) / (ms * 1e-3), "entries/s", ms,
+          "f32" if head == "fp32" else "f64",
+          {"workload": name, "n": n, "items": len(items), "item_factors": n_factors, "R_rho": R_rho, "R_N": P.R_N,
+           "graph": "sample + 2 Hadamard + coulomb_matrix captured in one CUDA graph"},
+          forms=res, roofline={"kernel": "gemm3_kernel(ROWS)+conv", "bound": "alu", "achieved": achieved,
+                               "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                               "note": "whole step; contraction flops 2*3*factors*R_rho*R_N*n"},
+          gpu_launches=None)
+
+
+def run_adjoint(args, ws, rank, local):
+    """a7: forward E_H and its gradients in exponents, centres and coefficients
+    through CPHartreeEnergy (sampling, convolutions, contraction with G, adjoint
+    GEMM, chain rule) for density200_n4096."""
+    import torch
+    import paper_1504_06289_gb300 as cpc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name = "density200_n4096"
+    cfg = workloads.CONFIGS[name]
+    n, b, M, R_f = cfg["n"], cfg["b"], cfg["M"], cfg["R_f"]
+    g = workloads.mixture_for(name, 5 + rank)
+    P = cpc.make_newton_kernel(n, b, M, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for prec in ("fp32", "split", "fp64"):
+        a = torch.tensor(g["a"], device=dev).requires_grad_()
+        X = torch.tensor(g["X"], device=dev).requires_grad_()
+        c = torch.tensor(g["c"], device=dev).requires_grad_()
+        def body():
+            E = cpc.CPHartreeEnergy.apply(a, X, c, P, prec)
+            E.backward()
+            return E
+        ms = _timed(stream, body, args.steps, args.warmup)
+        res[prec] = {"ms_per_step": ms, "E_H": body().item(), "grad_a_norm": float(a.grad.norm())}
+    for prec in ("fp32", "split"):
+        res[prec]["rel_err_E_H_vs_fp64"] = abs(res[prec]["E_H"] / res["fp64"]["E_H"] - 1)
+    if rank != 0:
+        return
+    head = args.precision if args.precision in res else "fp32"
+    ms = res[head]["ms_per_step"]
+    _line(args, ws, "E_H + gradient evaluations/s", ws / (ms * 1e-3), "evaluations/s", ms,
+          {"fp32": "f32", "split": "f64/f32", "fp64": "f64"}[head],
+          {"workload": name, "n": n, "R_f": R_f, "R_N": P.R_N,
+           "parameters": "200 exponents, 600 centre coordinates, 200 coefficients"},
+          forms=res, speedup_vs_fp64_gpu=res["fp64"]["ms_per_step"] / ms)
+
+
+def run_lattice(args, ws, rank, local):
+    """a9/a10: assembled lattice vectors of a 32^3 lattice of unit charges and
+    the potential on the 512^3 sub-grid (lattice32_n16384)."""
+    import torch
+    import paper_1504_06289_gb300 as cpc
+    from oracle import kernel_vectors as okv
+    from oracle import lattice as olat
+    from oracle import sinc as osinc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name = "lattice32_n16384"
+    cfg = workloads.CONFIGS[name]
+    n, b, M, L, sub_n = cfg["n"], cfg["b"], cfg["M"], cfg["L"], cfg["sub"]
+    geo = workloads.lattice_geometry(n, L, sub_n)
+    P = cpc.make_newton_kernel(n, b, M, "master", device=dev)
+    sub = torch.as_tensor(np.stack([geo["sub_idx"]] * 3), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for prec in ("fp64", "fp32"):
+        ms = _timed(stream, lambda: cpc.lattice_potential_sum(P, [geo["edges"]] * 3, sub, prec), args.steps,
+                    args.warmup)
+        res[prec] = {"ms_per_step": ms}
+    if rank != 0:
+        return
+    points = sub_n ** 3
+    head = "fp32" if args.precision == "fp32" else "fp64"
+    ms = res[head]["ms_per_step"]
+    fma = points * P.R_N
+    clk = 2070.0
+    out_bytes = points * (4 if head == "fp32" else 8)
+    # float64 ALU peak from the measured float64 contraction rate is not a unit count; report HBM and ALU both
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        t, w = osinc.master_nodes(n, b, M)
+        Pm = okv.master_kernel_vectors(n, b, t, w)
+        t0 = time.perf_counter()
+        S0 = olat.assembled_vectors(Pm, geo["edges"], n)
+        pts = workloads.check_points(sub_n, 20000, seed=1)
+        olat.potential_on_points([S0] * 3, 2 * b / n, geo["sub_idx"][pts])
+        dt = time.perf_counter() - t0
+        cpu = {"value": 20000 / dt, "unit": "points/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "assembled vectors + 20000 sub-grid points"}
+    _line(args, ws, "lattice potential points/s", ws * points / (ms * 1e-3), "points/s", ms,
+          "f32" if head == "fp32" else "f64",
+          {"workload": name, "n": n, "L": L, "sub_grid": sub_n, "R_N": P.R_N}, forms=res,
+          roofline={"kernel": "subgrid_kernel", "bound": "hbm", "achieved": out_bytes / (ms * 1e-3) / 1e9,
+                    "peak": load_peaks()[0]["hbm_gbs"], "unit": "GB/s",
+                    "frac": out_bytes / (ms * 1e-3) / 1e9 / load_peaks()[0]["hbm_gbs"], "traffic": None,
+                    "alu_fma_per_s": fma / (ms * 1e-3)},
+          cpu_baseline=cpu)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "basis80_n4096":
+        run_coulomb(args, ws, rank, local)
+    elif args.workload == "density200_n4096":
+        run_adjoint(args, ws, rank, local)
+    elif args.workload == "lattice32_n16384":
+        run_lattice(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

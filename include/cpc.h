@@ -225,15 +225,29 @@ int cp_gaussian_param_grad(int n, double b, int R, const double* a, const double
  * [0, n_factors] are clamped, never dereferenced); U_items: [3][n_factors][n];
  * c_items: [n_factors]; U_rho: [3][R_rho][n]; c_rho: [R_rho]; J: [n_items]
  * float64.  Item factors are concatenated into one row space, so items of
- * uneven rank share tiles and no item leaves a tile idle; the contraction runs
- * as one launch over (row tile, column group) work units.
- * Workspace: coulomb_matrix_workspace bytes. */
+ * uneven rank share tiles and no item leaves a tile idle; the contraction is
+ * one persistent launch over (row tile, column group) work units, a column
+ * group being tiles_per_cta consecutive 64-column tiles of the R_rho*R_N V_H
+ * columns (0 = default 8; else a power of two in [4, 128]).  Stream-ordered
+ * and allocation-free, so a sequence of these calls can be captured in a CUDA
+ * graph.  Workspace: coulomb_matrix_workspace bytes (sized for the smallest
+ * tiles_per_cta). */
 size_t coulomb_matrix_workspace(const cpc_kernel* P, int n_items, int n_factors, int R_rho,
                                 int precision);
 int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
                    const double* c_items, int R_rho, const double* U_rho, const double* c_rho,
-                   void* W_rho, double* J, int precision, void* ws, size_t ws_bytes,
+                   void* W_rho, double* J, int precision, int tiles_per_cta, void* ws, size_t ws_bytes,
                    void* stream);
+
+/* Schedule tuner for coulomb_matrix: computes W_rho, then times the
+ * contraction for every tiles_per_cta in {4, 8, ..., 128} on the caller's
+ * data (CUDA events on `stream`; this call synchronises the stream), writes
+ * the fastest to *best_tiles_per_cta (and its time in ms to *best_ms if not
+ * NULL) and leaves J computed with it.  Same arguments as coulomb_matrix. */
+int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* off, int n_factors,
+                        const double* U_items, const double* c_items, int R_rho, const double* U_rho,
+                        const double* c_rho, void* W_rho, double* J, int precision, void* ws,
+                        size_t ws_bytes, void* stream, int* best_tiles_per_cta, float* best_ms);
 
 /* ---- a9/a10: assembled lattice sums (Sec. 5.1, Eq. CoulombLatTensCan) -----
  * With a MASTER kernel p~_q and, per axis l, L[l] charge positions given as

@@ -268,10 +268,58 @@ def cp_gaussian_param_grad(n: int, b: float, a: torch.Tensor, X: torch.Tensor, U
     return da, dX
 
 
+_TUNE_CACHE = None
+
+
+def _tune_cache_path():
+    import os
+    return os.environ.get("CPC_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "cpc_tune.json"))
+
+
+def _tune_key(P, n_factors, R_rho, precision, device):
+    props = torch.cuda.get_device_properties(device)
+    return f"{props.name}|sm{props.multi_processor_count}|n{P.n}|RN{P.R_N}|F{n_factors}|R{R_rho}|{precision}"
+
+
+def _tune_lookup(key):
+    global _TUNE_CACHE
+    import json
+    import os
+    if _TUNE_CACHE is None:
+        try:
+            with open(_tune_cache_path()) as f:
+                _TUNE_CACHE = json.load(f)
+        except (OSError, ValueError):
+            _TUNE_CACHE = {}
+    return _TUNE_CACHE.get(key)
+
+
+def _tune_store(key, value):
+    import json
+    import os
+    _tune_lookup(key)  # loads the cache file on first use
+    _TUNE_CACHE[key] = value
+    path = _tune_cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        tmp = path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(_TUNE_CACHE, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+    except OSError:
+        pass
+
+
 def coulomb_matrix(P: NewtonKernel, off: torch.Tensor, U_items: torch.Tensor, c_items: torch.Tensor,
                    U_rho: torch.Tensor, c_rho: torch.Tensor, precision: str = "fp64",
-                   W_rho: torch.Tensor | None = None, ws: torch.Tensor | None = None, stream=None):
-    """J[t] = <item_t, V_H(rho)> for items in CP form (factor offsets `off`, int32)."""
+                   W_rho: torch.Tensor | None = None, ws: torch.Tensor | None = None, tiles_per_cta=None,
+                   stream=None):
+    """J[t] = <item_t, V_H(rho)> for items in CP form (factor offsets `off`, int32).
+
+    tiles_per_cta: schedule of the persistent contraction; None looks it up in
+    the tuning cache (file CPC_TUNE_CACHE, default ~/.cache/cpc_tune.json) and
+    runs coulomb_matrix_tune on a miss; "tune" forces a new tuning; an int is
+    used as given (0 = library default)."""
     lib = load()
     n_items = off.numel() - 1
     n_factors = U_items.shape[1]
@@ -283,9 +331,21 @@ def coulomb_matrix(P: NewtonKernel, off: torch.Tensor, U_items: torch.Tensor, c_
     nb = lib.coulomb_matrix_workspace(P.handle, n_items, n_factors, R_rho, pr)
     if ws is None or ws.numel() < nb:
         ws = _workspace(nb, U_rho.device)
-    check(lib.coulomb_matrix(P.handle, n_items, _ptr(off), n_factors, _ptr(U_items), _ptr(c_items), R_rho,
-                             _ptr(U_rho), _ptr(c_rho), _ptr(W_rho), _ptr(J), pr, _ptr(ws), ws.numel(),
-                             _stream(stream)), "coulomb_matrix")
+    args = (P.handle, n_items, _ptr(off), n_factors, _ptr(U_items), _ptr(c_items), R_rho, _ptr(U_rho), _ptr(c_rho),
+            _ptr(W_rho), _ptr(J), pr)
+    key = None
+    if tiles_per_cta is None or tiles_per_cta == "tune":
+        key = _tune_key(P, n_factors, R_rho, precision, U_rho.device)
+        cached = _tune_lookup(key) if tiles_per_cta is None else None
+        if cached is not None:
+            tiles_per_cta = int(cached["tiles_per_cta"])
+        else:
+            best, ms = C.c_int(), C.c_float()
+            check(lib.coulomb_matrix_tune(*args, _ptr(ws), ws.numel(), _stream(stream), C.byref(best), C.byref(ms)),
+                  "coulomb_matrix_tune")
+            _tune_store(key, {"tiles_per_cta": best.value, "ms": ms.value})
+            return J, W_rho
+    check(lib.coulomb_matrix(*args, int(tiles_per_cta), _ptr(ws), ws.numel(), _stream(stream)), "coulomb_matrix")
     return J, W_rho
 
 

@@ -36,7 +36,9 @@ PROTOTYPES = {
     "cp_hartree_energy_adjoint": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp]),
     "cp_gaussian_param_grad": (i32, [i32, f64, i32, vp, vp, vp, vp, vp, vp, vp]),
     "coulomb_matrix_workspace": (sz, [vp, i32, i32, i32, i32]),
-    "coulomb_matrix": (i32, [vp, i32, vp, i32, vp, vp, i32, vp, vp, vp, vp, i32, vp, sz, vp]),
+    "coulomb_matrix": (i32, [vp, i32, vp, i32, vp, vp, i32, vp, vp, vp, vp, i32, i32, vp, sz, vp]),
+    "coulomb_matrix_tune": (i32, [vp, i32, vp, i32, vp, vp, i32, vp, vp, vp, vp, i32, vp, sz, vp,
+                                  C.POINTER(C.c_int), C.POINTER(C.c_float)]),
     "lattice_potential_sum": (i32, [vp, vp, vp, vp, i32, vp, vp, i32, vp]),
     "cpc_status_string": (C.c_char_p, [i32]),
     "cpc_last_error": (C.c_char_p, []),

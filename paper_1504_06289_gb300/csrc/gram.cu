@@ -145,11 +145,16 @@ tri_gram_kernel(int n, int M, int N, const double* __restrict__ A, long long a_a
       partial[(size_t)q * gridDim.x + p] = s;
     }
   } else {
-    // blockIdx.x: row tile; blockIdx.y: group of tiles_per_cta column tiles
-    const int r0 = blockIdx.x * TM;
+    // persistent: work unit u = (row tile u % n_rt, column group u / n_rt);
+    // CTAs with neighbouring u share the group's column tiles in L2
+    const int n_rt = (M + TM - 1) / TM;
     const int n_ct = (N + TN - 1) / TN;
+    const int n_groups = (n_ct + tiles_per_cta - 1) / tiles_per_cta;
+    for (long long u = blockIdx.x; u < (long long)n_rt * n_groups; u += gridDim.x) {
+    const int rt = int(u % n_rt), grp = int(u / n_rt);
+    const int r0 = rt * TM;
     double rowacc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int ct = blockIdx.y * tiles_per_cta; ct < min(n_ct, (int)(blockIdx.y + 1) * tiles_per_cta); ++ct) {
+    for (int ct = grp * tiles_per_cta; ct < min(n_ct, (grp + 1) * tiles_per_cta); ++ct) {
       const int s0 = ct * TN;
       double prod[4][4];
 #pragma unroll
@@ -177,7 +182,8 @@ tri_gram_kernel(int n, int M, int N, const double* __restrict__ A, long long a_a
       double v = rowacc[a];
       for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
       const int r = r0 + ty + 16 * a;
-      if (tx == 0 && r < M) partial[(size_t)blockIdx.y * M + r] = v;
+      if (tx == 0 && r < M) partial[(size_t)grp * M + r] = v;
+    }
     }
   }
 }
@@ -428,59 +434,127 @@ extern "C" int cp_hartree_energy_adjoint(const cpc_kernel* P, int R_f, const dou
 }
 
 // ---- Coulomb matrix ---------------------------------------------------------
+// Items are flattened into one row space of n_factors item factors; the
+// contraction runs as a persistent launch over (row tile, column group) work
+// units, a column group being tiles_per_cta consecutive 64-column tiles of
+// the R_rho R_N V_H columns.  tiles_per_cta trades the per-unit row-sum
+// traffic (one partial per row per group) against load balance; the tuner
+// below times the candidates on the caller's data.
 namespace cpc {
+static const int kTilesDefault = 8, kTilesMin = 4, kTilesMax = 128;
 static int coulomb_groups(int R_rho, int R_N, int tiles_per_cta) {
   const int n_ct = tiles(R_rho * R_N);
   return (n_ct + tiles_per_cta - 1) / tiles_per_cta;
 }
-static const int kCoulombTilesPerCta = 8;
+
+// contraction + segmented item reduction, after W_rho holds the V_H factors
+static int coulomb_contract(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
+                            const double* c_items, int R_rho, const double* c_rho, const void* W_rho, double* J,
+                            int precision, int tiles_per_cta, double* rowpart, cudaStream_t s) {
+  const int n = P->n;
+  const int N = R_rho * P->R_N;
+  const int groups = coulomb_groups(R_rho, P->R_N, tiles_per_cta);
+  const long long units = (long long)tiles(n_factors) * groups;
+  const int grid = (int)std::min<long long>(units, 2LL * 152 * 4);
+  const long long a_axis = (long long)n_factors * n;
+  const long long b_axis = (long long)N * n;
+  int st = CPC_OK;
+  if (precision == CPC_FP64) {
+    tri_gram_kernel<double, MODE_ROWS><<<grid, TPB, 0, s>>>(n, n_factors, N, U_items, a_axis,
+        static_cast<const double*>(W_rho), b_axis, 1, nullptr, c_rho, P->R_N, rowpart, nullptr, tiles_per_cta);
+    CPC_LAUNCH_CHECK("tri_gram_kernel(ROWS)");
+  } else if (precision == CPC_SPLIT) {
+    st = launch_rows32(P, n_factors, U_items, N, nullptr, c_rho, rowpart, groups, tiles_per_cta, s,
+                       static_cast<const double*>(W_rho));
+  } else {
+    st = launch_rows32(P, n_factors, U_items, N, static_cast<const float*>(W_rho), c_rho, rowpart, groups,
+                       tiles_per_cta, s);
+  }
+  if (st) return st;
+  item_reduce_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(n_items, off, c_items, rowpart, groups, n_factors,
+                                                         P->h * P->h * P->h, J);
+  CPC_LAUNCH_CHECK("item_reduce_kernel");
+  return CPC_OK;
+}
+
+static int check_coulomb(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
+                         const double* c_items, int R_rho, const double* U_rho, const double* c_rho, void* W_rho,
+                         double* J, int precision, int tiles_per_cta, void* ws, size_t ws_bytes, const char* who) {
+  int st = check_conv_args(P, R_rho, U_rho, W_rho, precision, ws, ws_bytes, who);
+  if (st) return st;
+  if (n_items <= 0 || !off || !U_items || !c_items || !c_rho || !J)
+    return fail(CPC_ERR_INVALID, std::string(who) + ": bad item arguments");
+  if (n_factors <= 0) return fail(CPC_ERR_INVALID, std::string(who) + ": no item factors");
+  if (tiles_per_cta != 0 && (tiles_per_cta < kTilesMin || tiles_per_cta > kTilesMax || (tiles_per_cta & (tiles_per_cta - 1))))
+    return fail(CPC_ERR_INVALID, std::string(who) + ": tiles_per_cta must be 0 or a power of two in [4, 128]");
+  if (ws_bytes < coulomb_matrix_workspace(P, n_items, n_factors, R_rho, precision))
+    return fail(CPC_ERR_WORKSPACE, std::string(who) + ": workspace too small");
+  return CPC_OK;
+}
 }  // namespace cpc
 
 extern "C" size_t coulomb_matrix_workspace(const cpc_kernel* P, int n_items, int n_factors, int R_rho,
                                            int precision) {
   if (!P || n_items <= 0 || n_factors <= 0 || R_rho <= 0) return 0;
-  const size_t groups = coulomb_groups(R_rho, P->R_N, kCoulombTilesPerCta);
+  const size_t groups = coulomb_groups(R_rho, P->R_N, kTilesMin);
   return cp_convolve_workspace(P, R_rho, precision) + align256(sizeof(double) * groups * n_factors);
 }
 
 extern "C" int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
                               const double* c_items, int R_rho, const double* U_rho, const double* c_rho,
-                              void* W_rho, double* J, int precision, void* ws, size_t ws_bytes, void* stream) {
+                              void* W_rho, double* J, int precision, int tiles_per_cta, void* ws, size_t ws_bytes,
+                              void* stream) {
   clear_error();
-  int st = check_conv_args(P, R_rho, U_rho, W_rho, precision, ws, ws_bytes, "coulomb_matrix");
+  int st = check_coulomb(P, n_items, off, n_factors, U_items, c_items, R_rho, U_rho, c_rho, W_rho, J, precision,
+                         tiles_per_cta, ws, ws_bytes, "coulomb_matrix");
   if (st) return st;
-  if (n_items <= 0 || !off || !U_items || !c_items || !c_rho || !J)
-    return fail(CPC_ERR_INVALID, "coulomb_matrix: bad item arguments");
-  if (n_factors <= 0) return fail(CPC_ERR_INVALID, "coulomb_matrix: no item factors");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (ws_bytes < coulomb_matrix_workspace(P, n_items, n_factors, R_rho, precision))
-    return fail(CPC_ERR_WORKSPACE, "coulomb_matrix: workspace too small");
   st = run_convolve(P, R_rho, U_rho, W_rho, precision, ws, s);
   if (st) return st;
   double* rowpart = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_rho, precision));
-  const int n = P->n;
-  const int N = R_rho * P->R_N;
-  const int groups = coulomb_groups(R_rho, P->R_N, kCoulombTilesPerCta);
-  dim3 grid(tiles(n_factors), groups);
-  const long long a_axis = (long long)n_factors * n;
-  const long long b_axis = (long long)N * n;
-  if (precision == CPC_FP64)
-    tri_gram_kernel<double, MODE_ROWS><<<grid, TPB, 0, s>>>(n, n_factors, N, U_items, a_axis,
-        static_cast<const double*>(W_rho), b_axis, 1, nullptr, c_rho, P->R_N, rowpart, nullptr, kCoulombTilesPerCta);
-  else if (precision == CPC_SPLIT) {
-    st = launch_rows32(P, n_factors, U_items, N, nullptr, c_rho, rowpart, groups, kCoulombTilesPerCta, s,
-                       static_cast<const double*>(W_rho));
-    if (st) return st;
-  } else {
-    st = launch_rows32(P, n_factors, U_items, N, static_cast<const float*>(W_rho), c_rho, rowpart, groups,
-                       kCoulombTilesPerCta, s);
-    if (st) return st;
+  return coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision,
+                          tiles_per_cta ? tiles_per_cta : kTilesDefault, rowpart, s);
+}
+
+extern "C" int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* off, int n_factors,
+                                   const double* U_items, const double* c_items, int R_rho, const double* U_rho,
+                                   const double* c_rho, void* W_rho, double* J, int precision, void* ws,
+                                   size_t ws_bytes, void* stream, int* best_tiles_per_cta, float* best_ms) {
+  clear_error();
+  int st = check_coulomb(P, n_items, off, n_factors, U_items, c_items, R_rho, U_rho, c_rho, W_rho, J, precision, 0,
+                         ws, ws_bytes, "coulomb_matrix_tune");
+  if (st) return st;
+  if (!best_tiles_per_cta) return fail(CPC_ERR_INVALID, "coulomb_matrix_tune: NULL best_tiles_per_cta");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = run_convolve(P, R_rho, U_rho, W_rho, precision, ws, s);
+  if (st) return st;
+  double* rowpart = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_rho, precision));
+  cudaEvent_t e0, e1;
+  CPC_CUDA(cudaEventCreate(&e0));
+  CPC_CUDA(cudaEventCreate(&e1));
+  float best = -1.0f;
+  int best_t = kTilesDefault;
+  for (int t = kTilesMin; t <= kTilesMax; t *= 2) {
+    // one untimed launch per candidate, then one timed
+    st = coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, t, rowpart, s);
+    if (st) break;
+    CPC_CUDA(cudaEventRecord(e0, s));
+    st = coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, t, rowpart, s);
+    if (st) break;
+    CPC_CUDA(cudaEventRecord(e1, s));
+    CPC_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    CPC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (best < 0.0f || ms < best) { best = ms; best_t = t; }
   }
-  CPC_LAUNCH_CHECK("tri_gram_kernel(ROWS)");
-  item_reduce_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(n_items, off, c_items, rowpart, groups, n_factors,
-                                                         P->h * P->h * P->h, J);
-  CPC_LAUNCH_CHECK("item_reduce_kernel");
-  return CPC_OK;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  *best_tiles_per_cta = best_t;
+  if (best_ms) *best_ms = best;
+  // leave J computed with the chosen schedule
+  return coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, best_t,
+                          rowpart, s);
 }
 
 // ---- explicit spectra intermediates ------------------------------------------

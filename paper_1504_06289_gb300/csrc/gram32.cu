@@ -252,13 +252,18 @@ gemm3_kernel(Op op, int M, int N, const double* __restrict__ wr, const double* _
       partial[(size_t)q * gridDim.x + blockIdx.x] = s;
     }
   } else {
-    const int r0 = blockIdx.x * BM;
+    // persistent over work units u = (row tile u % n_rt, column group u / n_rt)
+    const int n_rtile = (M + BM - 1) / BM;
     const int n_ct = (N + BN - 1) / BN;
+    const int n_groups = (n_ct + tiles_per_cta - 1) / tiles_per_cta;
+    for (long long u = blockIdx.x; u < (long long)n_rtile * n_groups; u += gridDim.x) {
+    const int rt = int(u % n_rtile), grp = int(u / n_rtile);
+    const int r0 = rt * BM;
     double rowacc[TMR];
 #pragma unroll
     for (int i = 0; i < TMR; ++i) rowacc[i] = 0.0;
-    const int ct_end = min(n_ct, (int)(blockIdx.y + 1) * tiles_per_cta);
-    for (int ct = blockIdx.y * tiles_per_cta; ct < ct_end; ++ct) {
+    const int ct_end = min(n_ct, (grp + 1) * tiles_per_cta);
+    for (int ct = grp * tiles_per_cta; ct < ct_end; ++ct) {
       const int s0 = ct * BN;
       for (int l = 0; l < 3; ++l) {
         float tot[TMR][TNC];
@@ -281,7 +286,9 @@ gemm3_kernel(Op op, int M, int N, const double* __restrict__ wr, const double* _
       double v = rowacc[i];
       for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, 16);
       const int r = r0 + ty * TMR + i;
-      if (tx == 0 && r < M) partial[(size_t)blockIdx.y * M + r] = v;
+      if (tx == 0 && r < M) partial[(size_t)grp * M + r] = v;
+    }
+    __syncthreads();  // prod slots are rewritten by the next unit
     }
   }
 }
@@ -346,7 +353,8 @@ int launch_eh32(const cpc_kernel* P, int R_f, const double* U, const float* W, c
 int launch_rows32(const cpc_kernel* P, int n_factors, const double* U_items, int N, const float* W,
                   const double* c_rho, double* rowpart, int groups, int tiles_per_cta, cudaStream_t s,
                   const double* W64) {
-  dim3 grid((n_factors + g32::BM - 1) / g32::BM, groups);
+  const long long units = (long long)((n_factors + g32::BM - 1) / g32::BM) * groups;
+  const int grid = (int)std::min<long long>(units, 2LL * 152 * 2);
   if (W64) {
     g32::SpatialD op{U_items, W64, (long long)n_factors * P->n, (long long)N * P->n, 1, 0, P->n};
     CPC_CUDA(cudaFuncSetAttribute(g32::gemm3_kernel<g32::SpatialD, 1, true>,

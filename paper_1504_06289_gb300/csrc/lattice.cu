@@ -47,8 +47,9 @@ __global__ void __launch_bounds__(512)
 subgrid_kernel(int n, int R_N, int n_sub, const double* __restrict__ S, const int* __restrict__ sub,
                double inv_h3, TV* __restrict__ V) {
   // thread -> s3; block -> kPairsPerBlock consecutive (s1, s2) pairs, s2 fastest.
-  // ab[pp][q] = S1[q][i1] * S2[q][i2] for the block's pairs, zero-padded in q.
-  __shared__ double ab[kPairsPerBlock][kMaxRNPad];
+  // ab[pp][q] = S1[q][i1] * S2[q][i2] for the block's pairs, zero-padded in q,
+  // formed in float64 and stored in the output's type (no per-term conversion).
+  __shared__ TV ab[kPairsPerBlock][kMaxRNPad];
   const int s3 = threadIdx.x;
   const long long pair0 = (long long)blockIdx.x * kPairsPerBlock;
   const long long n_pairs = (long long)n_sub * n_sub;
@@ -62,7 +63,7 @@ subgrid_kernel(int n, int R_N, int n_sub, const double* __restrict__ S, const in
       const int i1 = clamp_index(sub[s1], n), i2 = clamp_index(sub[n_sub + s2], n);
       v = S[(size_t)q * n + i1] * S[(size_t)(R_N + q) * n + i2];
     }
-    ab[pp][q] = v;
+    ab[pp][q] = TV(v);
   }
   __syncthreads();
   if (s3 >= n_sub) return;
@@ -97,7 +98,7 @@ subgrid_kernel(int n, int R_N, int n_sub, const double* __restrict__ S, const in
       for (int pp = 0; pp < kPairsPerBlock; ++pp)
 #pragma unroll
         for (int j = 0; j < kQChunk; ++j) {
-          const float term = float(ab[pp][q0 + j]) * c[j] - comp[pp];
+          const float term = ab[pp][q0 + j] * c[j] - comp[pp];
           const float t = acc[pp] + term;
           comp[pp] = (t - acc[pp]) - term;
           acc[pp] = t;

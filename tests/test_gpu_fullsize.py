@@ -165,20 +165,20 @@ def test_basis80_n4096_coulomb_matrix(cpc):
     all_items = ocoul.item_list(nb)
     sample = [all_items[int(i)] for i in rng.choice(len(all_items), 10, replace=False)] + [(0, 0), (nb - 1, nb - 1)]
     U_rho, c_rho, U_it, c_it, off = _coulomb_inputs(cpc, n, b, basis, sample)
-    J64, _ = cpc.coulomb_matrix(P, off, U_it, c_it, U_rho, c_rho, "fp64")
+    J64, _ = cpc.coulomb_matrix(P, off, U_it, c_it, U_rho, c_rho, "fp64", tiles_per_cta=0)
     _, _, P0 = oracle_conv_kernel(n, b, M)
     J0 = _oracle_items_streamed(n, b, basis, P0, sample)
     assert np.max(np.abs(J64.cpu().numpy() - J0)) < TOL64 * np.max(np.abs(J0))
     # E_H = sum_mu w_mu J_mu,mu over all diagonal items = h^3 <rho, P rho>
     diag = [(mu, mu) for mu in range(nb)]
     U_rho, c_rho, U_d, c_d, off_d = _coulomb_inputs(cpc, n, b, basis, diag)
-    Jd, _ = cpc.coulomb_matrix(P, off_d, U_d, c_d, U_rho, c_rho, "fp64")
+    Jd, _ = cpc.coulomb_matrix(P, off_d, U_d, c_d, U_rho, c_rho, "fp64", tiles_per_cta=0)
     E_items = float(np.dot(basis["w"], Jd.cpu().numpy()))
     E_direct = cpc.cp_hartree_energy(P, U_rho, c_rho, "fp64")[0].item()
     assert abs(E_items / E_direct - 1) < 1e-10
     # the full matrix (3240 items) in the float32 form, one launch; checked on the sample
     U_rho, c_rho, U_all, c_all, off_all = _coulomb_inputs(cpc, n, b, basis, all_items)
-    J32, _ = cpc.coulomb_matrix(P, off_all, U_all, c_all, U_rho, c_rho, "fp32")
+    J32, _ = cpc.coulomb_matrix(P, off_all, U_all, c_all, U_rho, c_rho, "fp32", tiles_per_cta=0)
     J32 = J32.cpu().numpy()
     idx = [all_items.index(it) for it in sample]
     assert np.max(np.abs(J32[idx] - J0)) < 1e-5 * np.max(np.abs(J0))

@@ -225,8 +225,40 @@ def _gpu_coulomb(cpc, P, n, b, basis, items, precision):
                 ia.append(x); ib.append(y)
         off.append(len(ia))
     U_it, c_it = cpc.cp_hadamard_pairs(F, dev(ia, torch.int32), dev(ib, torch.int32), d)
-    J, _ = cpc.coulomb_matrix(P, dev(off, torch.int32), U_it, c_it, U_rho, c_rho, precision)
+    J, _ = cpc.coulomb_matrix(P, dev(off, torch.int32), U_it, c_it, U_rho, c_rho, precision, tiles_per_cta=0)
     return J.cpu().numpy()
+
+
+def test_coulomb_schedules_agree_and_tuner_caches(cpc, tmp_path, monkeypatch):
+    import json
+    monkeypatch.setenv("CPC_TUNE_CACHE", str(tmp_path / "tune.json"))
+    cpc._TUNE_CACHE = None
+    n, b, M = 128, 10.0, 10
+    basis = _basis_case()
+    nb = len(basis["fn_first"]) - 1
+    items = ocoul.item_list(nb)
+    P = cpc.make_newton_kernel(n, b, M)
+    ref = _gpu_coulomb(cpc, P, n, b, basis, items, "fp64")
+    first = basis["fn_first"]
+    centre = np.repeat(basis["fn_centre"], np.diff(first), axis=0)
+    F = cpc.cp_sample_gaussians(n, b, dev(basis["prim_alpha"]), dev(centre))
+    d = dev(basis["prim_d"])
+    pa, pb, _ = ocoul.density_pairs(basis)
+    sc = [basis["w"][mu] * (1.0 if x == y else 2.0)
+          for mu in range(nb) for x in range(first[mu], first[mu + 1]) for y in range(x, first[mu + 1])]
+    U_rho, c_rho = cpc.cp_hadamard_pairs(F, dev(pa, torch.int32), dev(pb, torch.int32), d, dev(sc))
+    ia, ib, _, off = ocoul.item_pairs(basis, items)
+    U_it, c_it = cpc.cp_hadamard_pairs(F, dev(ia, torch.int32), dev(ib, torch.int32), d)
+    for tiles in (4, 8, 32, 128):
+        J, _ = cpc.coulomb_matrix(P, dev(off, torch.int32), U_it, c_it, U_rho, c_rho, "fp64", tiles_per_cta=tiles)
+        assert np.max(np.abs(J.cpu().numpy() - ref)) < 1e-13 * np.max(np.abs(ref))
+    J, _ = cpc.coulomb_matrix(P, dev(off, torch.int32), U_it, c_it, U_rho, c_rho, "fp64")  # tunes, caches
+    assert np.max(np.abs(J.cpu().numpy() - ref)) < 1e-13 * np.max(np.abs(ref))
+    cache = json.loads((tmp_path / "tune.json").read_text())
+    (entry,) = cache.values()
+    assert entry["tiles_per_cta"] in (4, 8, 16, 32, 64, 128) and entry["ms"] > 0
+    with pytest.raises(cpc.CpcError):
+        cpc.coulomb_matrix(P, dev(off, torch.int32), U_it, c_it, U_rho, c_rho, "fp64", tiles_per_cta=6)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("split", 1e-6)])
