@@ -142,9 +142,14 @@ int cp_convolve_from_spectra(const cpc_kernel* P, int R_f, const void* spec, voi
  *     = h^3 <f, P_R * f>      (Sec. 2.5 Eq. scal with Eq. conv).
  * Runs cp_convolve into W (required: it receives the V_H factors, type as
  * in cp_convolve), then the contraction of U with W: float64 throughout for
- * CPC_FP64; float32 products of U and W (both rounded to float32 on load for
- * CPC_SPLIT), float32 sums over chunks of 256 cells, float64 final
- * reduction for CPC_FP32 and CPC_SPLIT.  c: [R_f] float64.  G: NULL or
+ * CPC_FP64.  CPC_FP32 (n a multiple of 64): on the tensor cores, each row of
+ * U and of the float32 W split exactly into three bf16 integer slices under a
+ * per-row power-of-two scale, the slice products summed exactly per 64-cell
+ * chunk in TMEM and folded into float32 (equivalent to float32 operands and
+ * products); n < 64: float32 products on CUDA cores.  CPC_SPLIT: float32
+ * products of U and W (rounded on load), compensated float32 accumulation.
+ * All forms reduce across tiles in float64.  If a device-side wait of the
+ * tensor-core kernel gives up, E_H is written as NaN.  c: [R_f] float64.  G: NULL or
  * [3][R_N][R_f][R_f] float64 (needed by the adjoint).  E_H: one float64 on
  * the device.  Workspace: cp_hartree_energy_workspace bytes. */
 size_t cp_hartree_energy_workspace(const cpc_kernel* P, int R_f, int precision);
@@ -156,7 +161,7 @@ int cp_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doubl
  * V_H factors W (as written by cp_convolve with the same precision), in the
  * spatial form (float32 products on the float32 factors for CPC_FP32).
  * Workspace: cp_hartree_energy_from_factors_workspace bytes. */
-size_t cp_hartree_energy_from_factors_workspace(const cpc_kernel* P, int R_f);
+size_t cp_hartree_energy_from_factors_workspace(const cpc_kernel* P, int R_f, int precision);
 int cp_hartree_energy_from_factors(const cpc_kernel* P, int R_f, const double* U, const double* c,
                                    const void* W, double* G, double* E_H, int precision, void* ws,
                                    size_t ws_bytes, void* stream);

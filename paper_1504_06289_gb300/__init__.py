@@ -224,7 +224,7 @@ def cp_hartree_energy_from_factors(P: NewtonKernel, U: torch.Tensor, c: torch.Te
     G = torch.empty((3, P.R_N, R_f, R_f), dtype=torch.float64, device=U.device) if want_G else None
     if E is None:
         E = torch.empty((), dtype=torch.float64, device=U.device)
-    nb = lib.cp_hartree_energy_from_factors_workspace(P.handle, R_f)
+    nb = lib.cp_hartree_energy_from_factors_workspace(P.handle, R_f, _prec(precision))
     if ws is None or ws.numel() < nb:
         ws = _workspace(nb, U.device)
     check(lib.cp_hartree_energy_from_factors(P.handle, R_f, _ptr(U), _ptr(c), _ptr(W), _ptr(G), _ptr(E),

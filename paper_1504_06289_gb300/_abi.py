@@ -30,7 +30,7 @@ PROTOTYPES = {
     "cp_hartree_energy_from_spectra": (i32, [vp, i32, vp, vp, vp, vp, i32, vp, sz, vp]),
     "cp_hartree_energy_workspace": (sz, [vp, i32, i32]),
     "cp_hartree_energy": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp]),
-    "cp_hartree_energy_from_factors_workspace": (sz, [vp, i32]),
+    "cp_hartree_energy_from_factors_workspace": (sz, [vp, i32, i32]),
     "cp_hartree_energy_from_factors": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp, sz, vp]),
     "cp_hartree_energy_noalloc": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp]),
     "cp_hartree_energy_adjoint": (i32, [vp, i32, vp, vp, vp, vp, vp, i32, vp]),

@@ -91,6 +91,12 @@ size_t eh32a_partials(int R_f, int R_N);
 size_t eh32a_u32_bytes(const cpc_kernel* P, int R_f);
 int launch_eh32a(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
                  double* partial, float* U32, cudaStream_t s);
+size_t tc_partials(int R_f, int R_N);
+bool tc_supported(const cpc_kernel* P);
+size_t tc_workspace(const cpc_kernel* P, int R_f);
+int* tc_status_ptr(const cpc_kernel* P, int R_f, void* ws);
+int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
+                 double* partial, void* ws, cudaStream_t s);
 // the V_H factors and spectra of CPC_SPLIT are float64, like CPC_FP64
 inline int storage_precision(int precision) { return precision == CPC_FP32 ? CPC_FP32 : CPC_FP64; }
 size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision);

@@ -188,9 +188,10 @@ tri_gram_kernel(int n, int M, int N, const double* __restrict__ A, long long a_a
   }
 }
 
-// E_H = h^3 * sum of partials, summed in a fixed order by one block.
+// E_H = h^3 * sum of partials, summed in a fixed order by one block; NaN when
+// a device-side wait of the contraction gave up (status != 0).
 __global__ void finalize_sum_kernel(const double* __restrict__ partial, long long count, double scale,
-                                    double* __restrict__ out) {
+                                    double* __restrict__ out, const int* __restrict__ status = nullptr) {
   __shared__ double red[1024 / 32];
   double s = 0.0;
   for (long long i = threadIdx.x; i < count; i += blockDim.x) s += partial[i];
@@ -200,7 +201,7 @@ __global__ void finalize_sum_kernel(const double* __restrict__ partial, long lon
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
-    *out = scale * t;
+    *out = (status && *status) ? __longlong_as_double(0x7ff8000000000000LL) : scale * t;
   }
 }
 
@@ -313,12 +314,16 @@ static int tiles(int x) { return (x + TM - 1) / TM; }
 
 size_t eh_partials(const cpc_kernel* P, int R_f) {
   const int T = tiles(R_f);
-  return std::max({size_t(T) * (T + 1) / 2 * P->R_N, eh32_partials(R_f, P->R_N), eh32a_partials(R_f, P->R_N)});
+  return std::max({size_t(T) * (T + 1) / 2 * P->R_N, eh32_partials(R_f, P->R_N), eh32a_partials(R_f, P->R_N),
+                   tc_partials(R_f, P->R_N)});
 }
 
-// contraction workspace: partial sums, then (float32 form) a float32 copy of U
-size_t contraction_workspace(const cpc_kernel* P, int R_f) {
-  return align256(sizeof(double) * eh_partials(P, R_f)) + eh32a_u32_bytes(P, R_f);
+// contraction workspace: partial sums; float32 form: a float32 copy of U (CUDA-core
+// kernel, n < 64) or the bf16 slices, exponents and status word of the tensor-core kernel
+size_t contraction_workspace(const cpc_kernel* P, int R_f, int precision) {
+  size_t b = align256(sizeof(double) * eh_partials(P, R_f));
+  if (precision == CPC_FP32) b += tc_supported(P) ? tc_workspace(P, R_f) : eh32a_u32_bytes(P, R_f);
+  return b;
 }
 
 // E_H from float32 spectra (Parseval contraction), partials in `partial`.
@@ -349,6 +354,14 @@ int launch_eh(const cpc_kernel* P, int R_f, const double* U, const double* c, co
     int st = launch_eh32(P, R_f, U, nullptr, nullptr, nullptr, c, G, partial, s, static_cast<const double*>(W));
     if (st) return st;
     count = (long long)eh32_partials(R_f, P->R_N);
+  } else if (tc_supported(P)) {
+    void* tws = static_cast<unsigned char*>(cws) + align256(sizeof(double) * eh_partials(P, R_f));
+    int st = launch_eh_tc(P, R_f, U, static_cast<const float*>(W), c, G, partial, tws, s);
+    if (st) return st;
+    finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, (long long)tc_partials(R_f, P->R_N), P->h * P->h * P->h, E_H,
+                                           tc_status_ptr(P, R_f, tws));
+    CPC_LAUNCH_CHECK("finalize_sum_kernel");
+    return CPC_OK;
   } else {
     float* U32 = reinterpret_cast<float*>(static_cast<unsigned char*>(cws) + align256(sizeof(double) * eh_partials(P, R_f)));
     int st = launch_eh32a(P, R_f, U, static_cast<const float*>(W), c, G, partial, U32, s);
@@ -376,7 +389,7 @@ using namespace cpc;
 
 extern "C" size_t cp_hartree_energy_workspace(const cpc_kernel* P, int R_f, int precision) {
   if (!P || R_f <= 0) return 0;
-  return cp_convolve_workspace(P, R_f, precision) + contraction_workspace(P, R_f);
+  return cp_convolve_workspace(P, R_f, precision) + contraction_workspace(P, R_f, precision);
 }
 
 extern "C" int cp_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const double* c, void* W,
@@ -391,9 +404,9 @@ extern "C" int cp_hartree_energy(const cpc_kernel* P, int R_f, const double* U, 
   return run_hartree_energy(P, R_f, U, c, W, G, E_H, precision, ws, static_cast<cudaStream_t>(stream));
 }
 
-extern "C" size_t cp_hartree_energy_from_factors_workspace(const cpc_kernel* P, int R_f) {
+extern "C" size_t cp_hartree_energy_from_factors_workspace(const cpc_kernel* P, int R_f, int precision) {
   if (!P || R_f <= 0) return 0;
-  return contraction_workspace(P, R_f);
+  return contraction_workspace(P, R_f, precision);
 }
 
 extern "C" int cp_hartree_energy_from_factors(const cpc_kernel* P, int R_f, const double* U, const double* c,
@@ -404,7 +417,8 @@ extern "C" int cp_hartree_energy_from_factors(const cpc_kernel* P, int R_f, cons
   if (R_f <= 0 || !U || !c || !W || !E_H) return fail(CPC_ERR_INVALID, "cp_hartree_energy_from_factors: bad arguments");
   if (precision != CPC_FP64 && precision != CPC_FP32 && precision != CPC_SPLIT)
     return fail(CPC_ERR_UNSUPPORTED, "cp_hartree_energy_from_factors: precision form not implemented");
-  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) || ws_bytes < cp_hartree_energy_from_factors_workspace(P, R_f))
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) ||
+      ws_bytes < cp_hartree_energy_from_factors_workspace(P, R_f, precision))
     return fail(CPC_ERR_WORKSPACE, "cp_hartree_energy_from_factors: workspace missing, misaligned or too small");
   return launch_eh(P, R_f, U, c, W, G, E_H, precision, ws, static_cast<cudaStream_t>(stream));
 }
