@@ -12,14 +12,15 @@
 // dropping the a+b >= 3 terms (below float32 rounding of the operands).  Over
 // 128 cells every S_g is an integer below 2^24, so the bf16 MMAs accumulate
 // exactly in TMEM whatever the tensor core's rounding; every 128 cells the
-// accumulators are folded into float32 registers (round to nearest).
+// accumulators are folded into a compensated float32 sum (TwoSum) per entry.
 //
-// Tiles: 128 rows of U (M) x 64 columns of W (N), 128 threads (one TMEM lane
-// per row).  One thread streams the operand slices with TMA
-// (cp.async.bulk.tensor, 128-byte swizzle, completion counted on an
-// mbarrier) through 3 shared-memory stages and issues the MMAs; two TMEM
-// accumulator sets alternate so the readout of chunk t-1 by all threads
-// overlaps the MMAs of chunk t.  The three axes run as one stream of chunks.
+// Tiles: a CTA pair (2-CTA cluster, cta_group::2) computes 256 rows of U (M)
+// x 128 rows of W (N) for one kernel term; each CTA streams its 128 U rows and
+// 64 W rows with TMA (cp.async.bulk.tensor, 128-byte swizzle, completion
+// counted on an mbarrier) through 3 shared-memory stages, and one thread of
+// the even CTA issues the MMAs for both.  Sixteen warps per CTA read the
+// accumulators after every two chunks; the three axes run as one stream of
+// chunks and the running product over axes stays in TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -33,25 +34,44 @@
 namespace cpc {
 namespace tc {
 
-constexpr int BM = 128, BN = 64, BKC = 64;  // chunk of 64 cells = one 128-byte bf16 row
-constexpr int THREADS = 160, STAGES = 3;  // 4 reader warps + 1 TMA/MMA warp
-constexpr uint32_t A_SLICE_BYTES = BM * 128, B_SLICE_BYTES = BN * 128;
-constexpr uint32_t STAGE_BYTES = 3 * A_SLICE_BYTES + 3 * B_SLICE_BYTES;  // 73728
-constexpr uint32_t TMEM_COLS = 512;  // 2 sets x 3 groups x 64, then the product over axes
-constexpr uint32_t PROD_COL = 2 * 3 * BN;
-constexpr size_t kSmemBytes = size_t(STAGES) * STAGE_BYTES + 1024 + 256;
+constexpr int BM = 128;      // U rows per CTA (M = 256 per CTA pair)
+constexpr int BN = 128;      // W rows (output columns) per pair tile
+constexpr int BNH = BN / 2;  // W rows loaded by each CTA of the pair
+constexpr int BKC = 64;      // chunk of 64 cells = one 128-byte bf16 row
+constexpr int READERS = 16;  // accumulator reader warps: lane quadrant x column quarter
+constexpr int BNW = BN / 4;  // columns read by one reader warp
+constexpr int THREADS = (READERS + 1) * 32;  // + one TMA/MMA warp
+constexpr int STAGES = 3;
+constexpr uint32_t A_SLICE_BYTES = BM * 128, B_SLICE_BYTES = BNH * 128;
+constexpr uint32_t STAGE_BYTES = 3 * A_SLICE_BYTES + 3 * B_SLICE_BYTES;  // 72 KB per CTA
+constexpr uint32_t TMEM_COLS = 512;  // 3 groups x 128 columns, then the product over axes
+constexpr uint32_t PROD_COL = 3 * BN;
+// stages, alignment slack, barriers, then per-column exponents (3 axes) and coefficients
+constexpr size_t kColBytes = 3 * BN * sizeof(int) + BN * sizeof(double);
+constexpr size_t kSmemBytes = size_t(STAGES) * STAGE_BYTES + 1024 + 256 + kColBytes;
 constexpr long kSpinLimit = 20000000;
 
 // x -> (s0, s1, s2) with one exponent per row (2^e > max |x| over the row):
 // one CTA of 256 threads per row, the row read once into registers
-// (n / 256 values per thread, n a multiple of 1024 or handled by a tail).
+// (n / 256 values per thread, rounded up).
+//
+// Source rows are (l, s, q) of a [3][R_f][R_N][n] array (R_N = 1 for U).
+// Slices are written chunk-blocked, so that the rows of one operand tile
+// (64 consecutive s, one 64-cell chunk) are one contiguous block:
+//   out[k][G = l*R_N + q][t][s][i % 64],  t = i / 64,  k = slice.
 template <typename TS, int VPT>
-__global__ void __launch_bounds__(256) slice_rows_kernel(const TS* __restrict__ src, long long rows, int n,
-                                                         __nv_bfloat16* __restrict__ out, long long slice_stride,
-                                                         int* __restrict__ expo) {
+__global__ void __launch_bounds__(256) slice_rows_kernel(const TS* __restrict__ src, long long rows, int n, int R_f,
+                                                         int R_N, __nv_bfloat16* __restrict__ out,
+                                                         long long slice_stride, int* __restrict__ expo) {
   __shared__ float red[8];
+  const int T = n >> 6;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
     const TS* x = src + row * n;
+    const long long per_l = (long long)R_f * R_N;
+    const int l = (int)(row / per_l);
+    const int rem = (int)(row - l * per_l);
+    const int srow = rem / R_N, q = rem - srow * R_N;
+    __nv_bfloat16* ob = out + ((long long)(l * R_N + q) * T * R_f + srow) * 64;
     float v[VPT];
     float m = 0.0f;
 #pragma unroll
@@ -78,7 +98,7 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const TS* __restrict__ 
       const float b = (a - s0) * 256.0f;    // exact
       const float s1 = rintf(b);
       const float s2 = rintf((b - s1) * 256.0f);
-      __nv_bfloat16* o = out + row * n + i;
+      __nv_bfloat16* o = ob + (long long)(i >> 6) * R_f * 64 + (i & 63);
       o[0] = __float2bfloat16_rn(s0);
       o[slice_stride] = __float2bfloat16_rn(s1);
       o[2 * slice_stride] = __float2bfloat16_rn(s2);
@@ -97,18 +117,14 @@ struct Args {
   int* status;
 };
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t mbar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(mbar)
-      : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+// 5D tiled TMA load into this CTA's shared memory; the innermost coordinate is
+// always 0 (16-byte aligned); the mbarrier may be the peer CTA's (cta_group::2)
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c1, int c2, int c3,
                                             uint32_t mbar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, {%2, %3, %4, %5, %6}], [%7];\n" ::"r"(
           dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(0), "r"(mbar)
       : "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
@@ -116,21 +132,21 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
 }
 
 // chunk tt of the stream (axis tt / T, cells (tt % T) * 64 ..) into stage tt % STAGES
+// of this CTA; completion is counted on the even CTA's barrier (cluster address)
 __device__ __forceinline__ void issue_stage(const CUtensorMap* mapA, const CUtensorMap* mapB, const Args& g,
-                                            uint32_t sbase, uint32_t fullbar, int tt, int T, int q, int r0, int s0) {
-  const int l = tt / T, k0 = (tt % T) * BKC;
+                                            uint32_t sbase, uint32_t fullbar_cluster, int tt, int T, int q, int r0,
+                                            int sb0) {
+  const int l = tt / T, t = tt % T;
   const uint32_t stage = sbase + (tt % STAGES) * STAGE_BYTES;
-  mbar_expect_tx(fullbar, STAGE_BYTES);
-#pragma unroll
-  for (int a = 0; a < 3; ++a)  // A rows: slice a, axis l, rows r0.. (dim 1 = a*3R_f + l*R_f + r)
-    tma_load_2d(stage + a * A_SLICE_BYTES, mapA, k0, (a * 3 + l) * g.R_f + r0, fullbar);
-#pragma unroll
-  for (int b = 0; b < 3; ++b)  // B rows: slice b, axis l, columns s0.., term q (dims: cell, q, b*3R_f + l*R_f + s)
-    tma_load_3d(stage + 3 * A_SLICE_BYTES + b * B_SLICE_BYTES, mapB, k0, q, (b * 3 + l) * g.R_f + s0, fullbar);
+  // all three slices of each operand tile in one copy: A dims (cell, r, t, l, slice),
+  // B dims (cell, s, t, l*R_N + q, slice); rows past R_f read as zeros
+  tma_load_5d(stage, mapA, r0, t, l, fullbar_cluster);
+  tma_load_5d(stage + 3 * A_SLICE_BYTES, mapB, sb0, t, l * g.R_N + q, fullbar_cluster);
 }
 
+// the 6 slice-pair products of one chunk for the CTA pair (M = 256, N = 128)
 __device__ __forceinline__ void issue_mmas(uint32_t stage, uint32_t tacc, uint32_t accumulate) {
-  constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN);
+  constexpr uint32_t idesc = umma::idesc_bf16_f32(2 * BM, BN);
   const uint32_t a0 = stage, b0 = stage + 3 * A_SLICE_BYTES;
   // group g accumulates the slice pairs (a, b) with a + b = g
 #pragma unroll
@@ -143,7 +159,7 @@ __device__ __forceinline__ void issue_mmas(uint32_t stage, uint32_t tacc, uint32
       for (int kk = 0; kk < BKC / 16; ++kk) {
         const uint64_t ad = umma::desc_k_sw128(a0 + a * A_SLICE_BYTES + kk * 32);
         const uint64_t bd = umma::desc_k_sw128(b0 + b * B_SLICE_BYTES + kk * 32);
-        umma::mma_bf16(tacc + g * BN, ad, bd, idesc, acc);
+        umma::mma_bf16_pair(tacc + g * BN, ad, bd, idesc, acc);
         acc = 1;
       }
     }
@@ -166,14 +182,20 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, v
   return false;
 }
 
-// Warps 0-3 read the accumulators (one TMEM lane per thread); warp 4 (lane 0)
-// streams the operands with TMA and issues the MMAs.  Two consecutive 64-cell
-// chunks accumulate into the same TMEM set (every group sum stays an integer
-// below 2^24 over 128 cells, so it is exact), which halves the readouts.
-// Barriers: full[stage] (TMA bytes landed), sfree[stage] (the MMAs reading
-// a stage finished), done[set] (both chunks of a pair accumulated),
-// free[set] (the four reader warps took the set out of TMEM).
-__global__ void __launch_bounds__(THREADS, 1)
+// One CTA pair (a 2-CTA cluster) per tile of 256 U rows x 128 W rows of one
+// kernel term q.  Both CTAs stream their half of the operands (128 U rows, 64
+// W rows) with TMA into their own shared memory and count the bytes on the
+// even CTA's full barrier; one thread of the even CTA issues the pair MMAs
+// (each CTA's TMEM receives its 128 rows x 128 columns).  In each CTA, warps
+// 0-15 read the accumulators (warp w: TMEM lanes 32 (w % 4).., columns
+// 32 (w / 4)..), warp 16 drives the copies.  Two consecutive 64-cell chunks
+// accumulate before each readout (every group sum stays an integer below
+// 2^24 over 128 cells, so it is exact).
+// Barriers: full[stage] (even CTA: both halves landed), sfree[stage] (both
+// CTAs: the MMAs reading a stage finished), done (both CTAs: a pair of
+// chunks accumulated), freeb (even CTA: the 32 reader warps of the pair
+// took the accumulators out of TMEM).
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
 gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Args g) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = umma::smem_u32(smem_raw);
@@ -182,102 +204,144 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const uint32_t sbase = raw + pad;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);  // [STAGES]
   uint64_t* sfree = full + STAGES;                                             // [STAGES]
-  uint64_t* done = sfree + STAGES;                                             // [2]
-  uint64_t* freeb = done + 2;                                                  // [2]
-  uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(freeb + 2);
+  uint64_t* done = sfree + STAGES;                                             // [1]
+  uint64_t* freeb = done + 1;                                                  // [1]
+  uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(freeb + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_ptr + 1);
+  double* col_c = reinterpret_cast<double*>(smem + STAGES * STAGE_BYTES + 256);  // [BN]
+  int* col_e = reinterpret_cast<int*>(col_c + BN);                              // [3][BN]
   __shared__ double red[THREADS / 32];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t rank = umma::cluster_ctarank();
   const int q = blockIdx.y;
   const int n_ct = (g.R_f + BN - 1) / BN;
-  const int rt = blockIdx.x / n_ct, ct = blockIdx.x % n_ct;
-  const int r0 = rt * BM, s0 = ct * BN;
-  if (r0 > s0 + BN - 1) {  // entirely below the diagonal of the symmetric sum
+  const int pair = blockIdx.x >> 1;
+  const int rp = pair / n_ct, ct = pair % n_ct;
+  const int r0p = rp * 2 * BM, s0 = ct * BN;
+  if (r0p > s0 + BN - 1) {  // the whole pair tile lies below the diagonal: both CTAs leave
     if (tid == 0) g.partial[(size_t)q * gridDim.x + blockIdx.x] = 0.0;
     return;
   }
-  if (warp == 0) umma::tmem_alloc(tmem_ptr, TMEM_COLS);
-  if (tid == 0) {
+  const int r0 = r0p + int(rank) * BM, sb0 = s0 + int(rank) * BNH;
+  // the tile's column coefficients and row exponents of W, once
+  for (int i = tid; i < 4 * BN; i += THREADS) {
+    const int j = i % BN, s = s0 + j;
+    if (i < BN) col_c[j] = (s < g.R_f) ? g.c[s] : 0.0;
+    else col_e[i - BN] = (s < g.R_f) ? g.eB[((long long)(i / BN - 1) * g.R_f + s) * g.R_N + q] : 0;
+  }
+  if (warp == 0) umma::tmem_alloc_pair(tmem_ptr, TMEM_COLS);
+  if (tid == 32) {
     for (int i = 0; i < STAGES; ++i) {
       umma::mbar_init(&full[i], 1);
       umma::mbar_init(&sfree[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
-      umma::mbar_init(&done[i], 1);
-      umma::mbar_init(&freeb[i], 4);
-    }
+    umma::mbar_init(done, 1);
+    umma::mbar_init(freeb, 2 * READERS);
     *abort_flag = 0;
     umma::mbar_fence_init();
   }
   umma::fence_before();
   __syncthreads();
+  umma::cluster_sync();  // the peer's barriers are initialised before any copy or arrive reaches them
   umma::fence_after();
   const uint32_t tbase = *tmem_ptr;
   const int T = g.n / BKC, TT = 3 * T;  // chunks (T even)
-  const int PP = TT / 2, PA = T / 2;    // pairs in all, per axis
+  const int PP = TT / 2, PA = T / 2;    // pairs of chunks in all, per axis
+  const uint32_t freeb_even = umma::mapa(umma::smem_u32(freeb), 0);
   double sum = 0.0;
 
-  if (warp == 4) {
+  if (warp == READERS) {
     if (lane == 0) {
-      for (int tt = 0; tt < STAGES - 1 && tt < TT; ++tt)
-        issue_stage(&mapA, &mapB, g, sbase, umma::smem_u32(&full[tt % STAGES]), tt, T, q, r0, s0);
-      for (int tt = 0; tt < TT; ++tt) {
-        const int pp = tt >> 1, set = pp & 1;
-        if (!wait_or_abort(&full[tt % STAGES], (tt / STAGES) & 1, abort_flag)) break;
-        if ((tt & 1) == 0 && pp >= 2 && !wait_or_abort(&freeb[set], ((pp - 2) >> 1) & 1, abort_flag)) break;
-        umma::fence_after();
-        issue_mmas(sbase + (tt % STAGES) * STAGE_BYTES, tbase + set * 3 * BN, (tt & 1) ? 1u : 0u);
-        umma::mma_commit(&sfree[tt % STAGES]);
-        if (tt & 1) umma::mma_commit(&done[set]);
-        const int tn = tt + STAGES - 1;
-        if (tn < TT) {
-          // stage tn % STAGES last held chunk tt - 1: wait until its MMAs finished
+      auto fullc = [&](int tt) { return umma::mapa(umma::smem_u32(&full[tt % STAGES]), 0); };
+      if (rank == 0) {
+        for (int tt = 0; tt < STAGES - 1 && tt < TT; ++tt) {
+          mbar_expect_tx(umma::smem_u32(&full[tt]), 2 * STAGE_BYTES);
+          issue_stage(&mapA, &mapB, g, sbase, fullc(tt), tt, T, q, r0, sb0);
+        }
+        for (int tt = 0; tt < TT; ++tt) {
+          const int pp = tt >> 1;
+          if (!wait_or_abort(&full[tt % STAGES], (tt / STAGES) & 1, abort_flag)) break;
+          if ((tt & 1) == 0 && pp >= 1 && !wait_or_abort(freeb, (pp - 1) & 1, abort_flag)) break;
+          umma::fence_after();
+          issue_mmas(sbase + (tt % STAGES) * STAGE_BYTES, tbase, (tt & 1) ? 1u : 0u);
+          umma::mma_commit_pair(&sfree[tt % STAGES]);
+          if (tt & 1) umma::mma_commit_pair(done);
+          const int tn = tt + STAGES - 1;
+          if (tn < TT) {
+            // stage tn % STAGES last held chunk tt - 1: wait until its MMAs finished
+            if (tt >= 1 && !wait_or_abort(&sfree[(tt - 1) % STAGES], ((tt - 1) / STAGES) & 1, abort_flag)) break;
+            mbar_expect_tx(umma::smem_u32(&full[tn % STAGES]), 2 * STAGE_BYTES);
+            issue_stage(&mapA, &mapB, g, sbase, fullc(tn), tn, T, q, r0, sb0);
+          }
+        }
+      } else {
+        for (int tt = 0; tt < STAGES - 1 && tt < TT; ++tt) issue_stage(&mapA, &mapB, g, sbase, fullc(tt), tt, T, q, r0, sb0);
+        for (int tt = 0; tt + STAGES - 1 < TT; ++tt) {
+          const int tn = tt + STAGES - 1;
           if (tt >= 1 && !wait_or_abort(&sfree[(tt - 1) % STAGES], ((tt - 1) / STAGES) & 1, abort_flag)) break;
-          issue_stage(&mapA, &mapB, g, sbase, umma::smem_u32(&full[tn % STAGES]), tn, T, q, r0, s0);
+          issue_stage(&mapA, &mapB, g, sbase, fullc(tn), tn, T, q, r0, sb0);
         }
       }
+      // drain: every commit of the pair has arrived on this CTA's stage barriers
+      // before the CTA can leave
+      if (!*abort_flag)
+        for (int tt = (TT > STAGES ? TT - STAGES : 0); tt < TT; ++tt)
+          if (!wait_or_abort(&sfree[tt % STAGES], (tt / STAGES) & 1, abort_flag)) break;
     }
   } else {
-    const int r = r0 + tid;  // this thread's row and TMEM lane
-    const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * warp) << 16);
-    // running sum of an axis as an unevaluated pair tot + lo (TwoSum per fold)
-    float tot[BN], lo[BN];
+    const int quad = warp & 3, part = warp >> 2;
+    const int r = r0 + 32 * quad + lane;  // this thread's row and TMEM lane
+    const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * quad) << 16) + part * BNW;
+    const int sh0 = s0 + part * BNW;  // first column of this warp
+    // running sum of an axis as an unevaluated pair tot + lo (TwoSum per fold);
+    // |lo| stays near 2^-24 |tot|, so lo is kept in bf16 (two per register):
+    // its own rounding is then below 2^-32 |tot|
+    float tot[BNW];
+    __nv_bfloat162 lo[BNW / 2];
 #pragma unroll
-    for (int j = 0; j < BN; ++j) { tot[j] = 0.0f; lo[j] = 0.0f; }
+    for (int j = 0; j < BNW; ++j) tot[j] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < BNW / 2; ++j) lo[j] = __float2bfloat162_rn(0.0f);
     double row = 0.0;
     bool ok = true;
     for (int pp = 0; pp < PP && ok; ++pp) {
-      const int set = pp & 1;
-      if (!wait_or_abort(&done[set], (pp >> 1) & 1, abort_flag)) { ok = false; break; }
+      if (!wait_or_abort(done, pp & 1, abort_flag)) { ok = false; break; }
       umma::fence_after();
 #pragma unroll
-      for (int cb = 0; cb < BN / 16; ++cb) {
-        float v0[16], v1[16], v2[16];
-        const uint32_t col = set * 3 * BN + cb * 16;
-        umma::tmem_ld16(lane_base + col, v0);
-        umma::tmem_ld16(lane_base + col + BN, v1);
-        umma::tmem_ld16(lane_base + col + 2 * BN, v2);
+      for (int cb = 0; cb < BNW / 8; ++cb) {
+        float v0[8], v1[8], v2[8];
+        const uint32_t col = cb * 8;
+        umma::tmem_ld8(lane_base + col, v0);
+        umma::tmem_ld8(lane_base + col + BN, v1);
+        umma::tmem_ld8(lane_base + col + 2 * BN, v2);
         umma::tmem_ld_wait();
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float v = fmaf(v2[j], 1.0f / 65536.0f, fmaf(v1[j], 1.0f / 256.0f, v0[j]));
-          float& t = tot[cb * 16 + j];
-          const float sm = t + v, bb = sm - t;
-          lo[cb * 16 + j] += (t - (sm - bb)) + (v - bb);
-          t = sm;
+        for (int j = 0; j < 8; j += 2) {
+          float e[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float v = fmaf(v2[j + h], 1.0f / 65536.0f, fmaf(v1[j + h], 1.0f / 256.0f, v0[j + h]));
+            float& t = tot[cb * 8 + j + h];
+            const float sm = t + v, bb = sm - t;
+            e[h] = (t - (sm - bb)) + (v - bb);
+            t = sm;
+          }
+          __nv_bfloat162& L = lo[(cb * 8 + j) / 2];
+          const float2 f = __bfloat1622float2(L);
+          L = __floats2bfloat162_rn(f.x + e[0], f.y + e[1]);
         }
       }
       umma::fence_before();
       __syncwarp();
-      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(umma::smem_u32(&freeb[set])));
+      if (lane == 0) umma::mbar_arrive_cluster(freeb_even);
       if (pp % PA == PA - 1) {
         // axis l finished: G_l = 2^(e_r + e_s - 16) (tot + lo); the running
         // product over axes lives in TMEM columns PROD_COL.. between axes
         const int l = pp / PA;
         const int er = (r < g.R_f) ? g.eA[l * g.R_f + r] : 0;
 #pragma unroll
-        for (int cb = 0; cb < BN / 16; ++cb) {
+        for (int cb = 0; cb < BNW / 16; ++cb) {
           float pv[16];
           if (l > 0) {
             umma::tmem_ld16(lane_base + PROD_COL + cb * 16, pv);
@@ -285,11 +349,13 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           }
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj) {
-            const int j = cb * 16 + jj, s = s0 + j;
-            const int es = (s < g.R_f) ? __ldg(g.eB + ((long long)l * g.R_f + s) * g.R_N + q) : 0;
-            const float Gv = ldexpf(tot[j] + lo[j], er + es - 16);
+            const int j = cb * 16 + jj, s = sh0 + j;
+            const int es = col_e[l * BN + part * BNW + j];
+            const __nv_bfloat162 L = lo[j / 2];
+            const float lj = (j & 1) ? __high2float(L) : __low2float(L);
+            const float Gv = ldexpf(tot[j] + lj, er + es - 16);
             tot[j] = 0.0f;
-            lo[j] = 0.0f;
+            if (j & 1) lo[j / 2] = __float2bfloat162_rn(0.0f);
             const bool in = r < g.R_f && s < g.R_f && r <= s;
             if (g.G && in) {
               double* Gq = g.G + ((size_t)l * gridDim.y + q) * (size_t)g.R_f * g.R_f;
@@ -298,7 +364,7 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             }
             const float pr = (l > 0) ? pv[jj] * Gv : Gv;
             pv[jj] = pr;
-            if (l == 2 && in) row += (r == s ? 1.0 : 2.0) * g.c[s] * double(pr);
+            if (l == 2 && in) row += (r == s ? 1.0 : 2.0) * col_c[part * BNW + j] * double(pr);
           }
           if (l < 2) {
             umma::tmem_st16(lane_base + PROD_COL + cb * 16, pv);
@@ -319,23 +385,24 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     g.partial[(size_t)q * gridDim.x + blockIdx.x] = s;
     if (*abort_flag) atomicExch(g.status, 1);
   }
+  umma::cluster_sync();  // neither CTA leaves (or frees TMEM) while the pair still works
   if (warp == 0) {
     umma::fence_after();
-    umma::tmem_dealloc(tbase, TMEM_COLS);
+    umma::tmem_dealloc_pair(tbase, TMEM_COLS);
   }
 }
 
 template <typename TS>
-int launch_slice(const TS* src, long long rows, int n, __nv_bfloat16* out, long long slice_stride, int* expo,
-                 cudaStream_t s) {
+int launch_slice(const TS* src, long long rows, int n, int R_f, int R_N, __nv_bfloat16* out, long long slice_stride,
+                 int* expo, cudaStream_t s) {
   const unsigned grid = (unsigned)std::min<long long>(rows, 1 << 20);
   switch ((n + 255) / 256) {
-    case 1: slice_rows_kernel<TS, 1><<<grid, 256, 0, s>>>(src, rows, n, out, slice_stride, expo); break;
-    case 2: slice_rows_kernel<TS, 2><<<grid, 256, 0, s>>>(src, rows, n, out, slice_stride, expo); break;
-    case 4: slice_rows_kernel<TS, 4><<<grid, 256, 0, s>>>(src, rows, n, out, slice_stride, expo); break;
-    case 8: slice_rows_kernel<TS, 8><<<grid, 256, 0, s>>>(src, rows, n, out, slice_stride, expo); break;
-    case 16: slice_rows_kernel<TS, 16><<<grid, 256, 0, s>>>(src, rows, n, out, slice_stride, expo); break;
-    case 32: slice_rows_kernel<TS, 32><<<grid, 256, 0, s>>>(src, rows, n, out, slice_stride, expo); break;
+    case 1: slice_rows_kernel<TS, 1><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
+    case 2: slice_rows_kernel<TS, 2><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
+    case 4: slice_rows_kernel<TS, 4><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
+    case 8: slice_rows_kernel<TS, 8><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
+    case 16: slice_rows_kernel<TS, 16><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
+    case 32: slice_rows_kernel<TS, 32><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
     default: return fail(CPC_ERR_UNSUPPORTED, "tensor-core contraction: n must be a power of two up to 8192");
   }
   CPC_LAUNCH_CHECK("slice_rows_kernel");
@@ -344,9 +411,10 @@ int launch_slice(const TS* src, long long rows, int n, __nv_bfloat16* out, long 
 
 }  // namespace tc
 
+// one partial per CTA: 2 CTAs per (256-row, 128-column) pair tile and kernel term
 size_t tc_partials(int R_f, int R_N) {
-  const int n_rt = (R_f + tc::BM - 1) / tc::BM, n_ct = (R_f + tc::BN - 1) / tc::BN;
-  return size_t(n_rt) * n_ct * R_N;
+  const int n_rp = (R_f + 2 * tc::BM - 1) / (2 * tc::BM), n_ct = (R_f + tc::BN - 1) / tc::BN;
+  return size_t(2) * n_rp * n_ct * R_N;
 }
 
 // two 64-cell chunks per accumulation: n a multiple of 128
@@ -396,35 +464,37 @@ int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, 
   int* status = tc_status_ptr(P, R_f, ws);
   CPC_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
   const long long arows = 3LL * R_f, brows = 3LL * R_f * R_N;
-  int st0 = tc::launch_slice(U, arows, n, As, a / 3, eA, s);
+  int st0 = tc::launch_slice(U, arows, n, R_f, 1, As, a / 3, eA, s);
   if (st0) return st0;
-  st0 = tc::launch_slice(W, brows, n, Bs, b / 3, eB, s);
+  st0 = tc::launch_slice(W, brows, n, R_f, R_N, Bs, b / 3, eB, s);
   if (st0) return st0;
 
   EncodeTiledFn enc;
   int st = encode_fn(&enc);
   if (st) return st;
   CUtensorMap mapA, mapB;
+  const int T = n / tc::BKC;
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   {
-    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)9 * R_f};
-    const cuuint64_t strides[1] = {(cuuint64_t)n * 2};
-    const cuuint32_t box[2] = {tc::BKC, tc::BM};
-    const cuuint32_t estr[2] = {1, 1};
-    if (enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, As, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    // [slice 3][l 3][t T][r R_f][64 cells]
+    const cuuint64_t dims[5] = {64, (cuuint64_t)R_f, (cuuint64_t)T, 3, 3};
+    const cuuint64_t row = 128, strides[4] = {row, row * R_f, row * R_f * T, row * R_f * T * 3};
+    const cuuint32_t box[5] = {tc::BKC, tc::BM, 1, 1, 3};
+    if (enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, As, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(CPC_ERR_CUDA, "tensor map for the U slices");
   }
   {
-    const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)R_N, (cuuint64_t)9 * R_f};
-    const cuuint64_t strides[2] = {(cuuint64_t)n * 2, (cuuint64_t)R_N * n * 2};
-    const cuuint32_t box[3] = {tc::BKC, 1, tc::BN};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    if (enc(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, Bs, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    // [slice 3][l*R_N + q][t T][s R_f][64 cells]
+    const cuuint64_t dims[5] = {64, (cuuint64_t)R_f, (cuuint64_t)T, (cuuint64_t)3 * R_N, 3};
+    const cuuint64_t row = 128, strides[4] = {row, row * R_f, row * R_f * T, row * R_f * T * 3 * R_N};
+    const cuuint32_t box[5] = {tc::BKC, tc::BNH, 1, 1, 3};
+    if (enc(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, Bs, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(CPC_ERR_CUDA, "tensor map for the V_H factor slices");
   }
-  const int n_rt = (R_f + tc::BM - 1) / tc::BM, n_ct = (R_f + tc::BN - 1) / tc::BN;
-  dim3 grid(n_rt * n_ct, R_N);
+  const int n_rp = (R_f + 2 * tc::BM - 1) / (2 * tc::BM), n_ct = (R_f + tc::BN - 1) / tc::BN;
+  dim3 grid(2 * n_rp * n_ct, R_N);  // clusters of 2 along x
   tc::Args args{eA, eB, R_f, R_N, n, c, partial, G, status};
   CPC_CUDA(cudaFuncSetAttribute(tc::gemm3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc::kSmemBytes)));
   tc::gemm3_tc_kernel<<<grid, tc::THREADS, tc::kSmemBytes, s>>>(mapA, mapB, args);
