@@ -288,13 +288,16 @@ def run_ours(args, ws, rank, local):
     with ClockSampler(local) as clocks:
         barrier(ws)
         torch.cuda.synchronize(dev)
+        cpc.kernel_timing(True)  # events around the library's main kernels, on their stream
         start.record(stream)
         for k in range(args.steps):
             step(prec, bufs, evs[k])
         stop.record(stream)
         torch.cuda.synchronize(dev)
+        cpc.kernel_timing(False)
         barrier(ws)
     ms_total = start.elapsed_time(stop)
+    kt = {k: cpc.kernel_timing_read(k) for k in ("conv_kernel", "slice_rows_kernel", "gemm3_tc_kernel")}
     ms_total = max_over_ranks(ms_total, ws, dev)
     E_fast = bufs[3].item()
     spec_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
@@ -362,20 +365,48 @@ def run_ours(args, ws, rank, local):
     # conv kernel algorithmic bytes per step: write all V_H factors, read spectra of U and p
     conv_bytes = 3 * R_f * R_N * n * elem + 3 * R_f * (n + 1) * 2 * elem + R_N * (n + 1) * elem
     conv_gbs = conv_bytes / (conv_ms * 1e-3) / 1e9
-    # contraction: unique Gram entries (symmetric) x 3 axes x R_N, 2 flop per multiply-add over
-    # K = 2(n+1) spectral values (float32 form, Parseval) or n cells (float64 form)
+    # contraction: unique Gram entries (symmetric) x 3 axes x R_N x n cells, 2 flop per multiply-add
     gram_flops = 3 * R_N * (R_f * (R_f + 1) // 2) * n * 2
     sm_mhz = clk["sm_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak_tf = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12 if prec != "fp64" else None
-    gram_tf = gram_flops / (gram_ms * 1e-3) / 1e12
+
+    def per_launch(name, fallback_ms):
+        tot, cnt = kt.get(name, (0.0, 0))
+        return (tot / cnt, cnt) if cnt else (fallback_ms, 0)
+
+    conv_k_ms, _ = per_launch("conv_kernel", conv_ms)
+    conv_gbs = conv_bytes / (conv_k_ms * 1e-3) / 1e9
     kernels = {
-        "conv_kernel": {"ms": conv_ms, "bound": "hbm", "achieved": conv_gbs, "peak": hbm_peak, "unit": "GB/s",
+        "conv_kernel": {"ms": conv_k_ms, "bound": "hbm", "achieved": conv_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": conv_gbs / hbm_peak, "algorithmic_bytes": conv_bytes},
-        {"fp32": "gemm3_tc_kernel", "split": "gemm3_kernel", "fp64": "tri_gram_kernel"}[prec]: {"ms": gram_ms, "bound": "alu", "achieved": gram_tf, "unit": "TFLOP/s",
-                            "peak": alu_peak_tf, "frac": (gram_tf / alu_peak_tf) if alu_peak_tf else None,
-                            "algorithmic_flops": gram_flops,
-                            "peak_note": "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x median SM clock"},
     }
+    if prec == "fp32":
+        # tensor-core form: each row of U and W split exactly into 3 bf16 slices;
+        # 6 slice products (a + b <= 2) per multiply-add of the float32 contraction
+        tc_ms, _ = per_launch("gemm3_tc_kernel", gram_ms)
+        tc_flops = 6 * gram_flops
+        tc_tf = tc_flops / (tc_ms * 1e-3) / 1e12
+        bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+        kernels["gemm3_tc_kernel"] = {"ms": tc_ms, "bound": "tensor", "achieved": tc_tf, "peak": bf16_peak,
+                                      "unit": "TFLOP/s", "frac": tc_tf / bf16_peak,
+                                      "algorithmic_flops": tc_flops,
+                                      "peak_note": "bf16 dense burst (cuBLAS), " + peak_kind,
+                                      "fp32_equivalent_TFLOP/s": gram_flops / (tc_ms * 1e-3) / 1e12}
+        # slicing: 2 launches per step (U rows, W rows): read float64 U / float32 W, write 3 bf16 slices
+        sl_tot, sl_cnt = kt.get("slice_rows_kernel", (0.0, 0))
+        sl_ms = sl_tot / max(1, sl_cnt) * 2
+        sl_bytes = 3 * R_f * n * (8 + 6) + 3 * R_f * R_N * n * (4 + 6)
+        kernels["slice_rows_kernel"] = {"ms": sl_ms, "bound": "hbm", "achieved": sl_bytes / (sl_ms * 1e-3) / 1e9,
+                                        "peak": hbm_peak, "unit": "GB/s",
+                                        "frac": sl_bytes / (sl_ms * 1e-3) / 1e9 / hbm_peak,
+                                        "algorithmic_bytes": sl_bytes, "note": "two launches per step, ms summed"}
+    else:
+        gram_tf = gram_flops / (gram_ms * 1e-3) / 1e12
+        kernels[{"split": "gemm3_kernel", "fp64": "tri_gram_kernel"}[prec]] = {
+            "ms": gram_ms, "bound": "alu", "achieved": gram_tf, "unit": "TFLOP/s",
+            "peak": alu_peak_tf, "frac": (gram_tf / alu_peak_tf) if alu_peak_tf else None,
+            "algorithmic_flops": gram_flops,
+            "peak_note": "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x median SM clock"}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
     if args.rf is None:
@@ -383,7 +414,7 @@ def run_ours(args, ws, rank, local):
             kd["traffic"] = recorded_traffic(kname)
     roofline = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"],
                 "unit": d["unit"], "frac": d["frac"], "traffic": d.get("traffic"),
-                "peak_source": peak_kind if d["bound"] == "hbm" else "derived (unit counts x clock)"}
+                "peak_source": peak_kind if d["bound"] in ("hbm", "tensor") else "derived (unit counts x clock)"}
     out = {
         "metric": METRIC, "value": value, "unit": "convolutions/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -400,8 +431,8 @@ def run_ours(args, ws, rank, local):
         "speedup_vs_fp64_gpu": (fp64["ms_per_step"] / ms_step) if fp64 else None,
         "e2e": {"value": ws * convs_per_step * e2e_steps / e2e_s, "unit": "convolutions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
-        # sample, spectra, conv, [float32 rounding of U,] contraction, final sum
-        "gpu_launches": (6 if prec == "fp32" else 5) * args.steps,
+        # sample, spectra, conv, [slice U, slice W,] contraction, final sum
+        "gpu_launches": (7 if prec == "fp32" else 5) * args.steps,
         "clocks": clk,
     }
     if ws == 1 and not args.no_cpu_baseline:

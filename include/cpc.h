@@ -142,11 +142,12 @@ int cp_convolve_from_spectra(const cpc_kernel* P, int R_f, const void* spec, voi
  *     = h^3 <f, P_R * f>      (Sec. 2.5 Eq. scal with Eq. conv).
  * Runs cp_convolve into W (required: it receives the V_H factors, type as
  * in cp_convolve), then the contraction of U with W: float64 throughout for
- * CPC_FP64.  CPC_FP32 (n a multiple of 64): on the tensor cores, each row of
- * U and of the float32 W split exactly into three bf16 integer slices under a
- * per-row power-of-two scale, the slice products summed exactly per 64-cell
- * chunk in TMEM and folded into float32 (equivalent to float32 operands and
- * products); n < 64: float32 products on CUDA cores.  CPC_SPLIT: float32
+ * CPC_FP64.  CPC_FP32 (n a multiple of 128): on the tensor cores, each row
+ * of U and of the float32 W split exactly into three bf16 integer slices under
+ * a per-row power-of-two scale, the slice products summed exactly over
+ * 128-cell chunks in TMEM and folded into a compensated float32 sum per entry
+ * (at least as accurate as float32 operands with float32 products); other n:
+ * float32 products on CUDA cores.  CPC_SPLIT: float32
  * products of U and W (rounded on load), compensated float32 accumulation.
  * All forms reduce across tiles in float64.  If a device-side wait of the
  * tensor-core kernel gives up, E_H is written as NaN.  c: [R_f] float64.  G: NULL or
@@ -270,6 +271,20 @@ int lattice_potential_sum(const cpc_kernel* master, const int* L, const int* edg
                           int n_sub, const int* sub, void* V, int precision, void* stream);
 
 /* ---- status -------------------------------------------------------------- */
+/* ---- kernel timing (measurement support; the paper has no counterpart) -----
+ * While enabled, every launch of conv_kernel, slice_rows_kernel and
+ * gemm3_tc_kernel is bracketed by two CUDA events recorded on the stream the
+ * kernel is launched on (up to 8192 launches; later ones go unrecorded).
+ * cpc_kernel_timing(1) creates the events on first use and clears earlier
+ * records; cpc_kernel_timing(0) stops recording and keeps the records.
+ * cpc_kernel_timing_read(name, total_ms, launches) waits for the recorded
+ * events of that kernel name and returns their summed device time (ms) and
+ * count (0 and 0 for an unknown name).  Host-side only; not for use inside a
+ * stream capture.  Returns CPC_OK, CPC_ERR_INVALID (null argument) or
+ * CPC_ERR_CUDA. */
+int cpc_kernel_timing(int enable);
+int cpc_kernel_timing_read(const char* kernel, double* total_ms, int* launches);
+
 const char* cpc_status_string(int status);
 /* Message of the most recent failure in this thread ("" if none). */
 const char* cpc_last_error(void);

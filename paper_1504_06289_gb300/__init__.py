@@ -387,3 +387,16 @@ class CPHartreeEnergy(torch.autograd.Function):
         dU, dc = cp_hartree_energy_adjoint(P, c, ctx.W, ctx.G, ctx.precision)
         da, dX = cp_gaussian_param_grad(P.n, P.b, a, X, ctx.U, dU)
         return gE * da, gE * dX, gE * dc, None, None
+
+
+def kernel_timing(enable: bool) -> None:
+    """Start (clearing earlier records) or stop CUDA-event timing of the
+    library's main kernels (conv_kernel, slice_rows_kernel, gemm3_tc_kernel)."""
+    check(load().cpc_kernel_timing(1 if enable else 0), "cpc_kernel_timing")
+
+
+def kernel_timing_read(kernel: str):
+    """(total device ms, launches) recorded for `kernel` since timing was enabled."""
+    ms, cnt = C.c_double(), C.c_int()
+    check(load().cpc_kernel_timing_read(kernel.encode(), C.byref(ms), C.byref(cnt)), "cpc_kernel_timing_read")
+    return ms.value, cnt.value

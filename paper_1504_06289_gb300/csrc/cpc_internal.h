@@ -43,6 +43,11 @@ namespace cpc {
 
 // error reporting (thread-local message)
 int fail(int status, const std::string& msg);
+
+// optional CUDA-event timing of selected kernel launches (timing.cpp)
+bool timing_on();
+int timing_begin(const char* name, cudaStream_t s);  // -1 when not recording
+void timing_end(int slot, cudaStream_t s);
 int cuda_fail(cudaError_t e, const char* what);
 void clear_error();
 

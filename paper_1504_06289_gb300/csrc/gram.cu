@@ -319,7 +319,8 @@ size_t eh_partials(const cpc_kernel* P, int R_f) {
 }
 
 // contraction workspace: partial sums; float32 form: a float32 copy of U (CUDA-core
-// kernel, n < 64) or the bf16 slices, exponents and status word of the tensor-core kernel
+// kernel, n not a multiple of 128) or the bf16 slices, exponents and status word of
+// the tensor-core kernel
 size_t contraction_workspace(const cpc_kernel* P, int R_f, int precision) {
   size_t b = align256(sizeof(double) * eh_partials(P, R_f));
   if (precision == CPC_FP32) b += tc_supported(P) ? tc_workspace(P, R_f) : eh32a_u32_bytes(P, R_f);

@@ -396,6 +396,7 @@ template <typename TS>
 int launch_slice(const TS* src, long long rows, int n, int R_f, int R_N, __nv_bfloat16* out, long long slice_stride,
                  int* expo, cudaStream_t s) {
   const unsigned grid = (unsigned)std::min<long long>(rows, 1 << 20);
+  const int slot = timing_begin("slice_rows_kernel", s);
   switch ((n + 255) / 256) {
     case 1: slice_rows_kernel<TS, 1><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
     case 2: slice_rows_kernel<TS, 2><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
@@ -403,8 +404,11 @@ int launch_slice(const TS* src, long long rows, int n, int R_f, int R_N, __nv_bf
     case 8: slice_rows_kernel<TS, 8><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
     case 16: slice_rows_kernel<TS, 16><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
     case 32: slice_rows_kernel<TS, 32><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
-    default: return fail(CPC_ERR_UNSUPPORTED, "tensor-core contraction: n must be a power of two up to 8192");
+    default:
+      timing_end(slot, s);
+      return fail(CPC_ERR_UNSUPPORTED, "tensor-core contraction: n must be a power of two up to 8192");
   }
+  timing_end(slot, s);
   CPC_LAUNCH_CHECK("slice_rows_kernel");
   return CPC_OK;
 }
@@ -497,7 +501,9 @@ int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, 
   dim3 grid(2 * n_rp * n_ct, R_N);  // clusters of 2 along x
   tc::Args args{eA, eB, R_f, R_N, n, c, partial, G, status};
   CPC_CUDA(cudaFuncSetAttribute(tc::gemm3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc::kSmemBytes)));
+  const int slot = timing_begin("gemm3_tc_kernel", s);
   tc::gemm3_tc_kernel<<<grid, tc::THREADS, tc::kSmemBytes, s>>>(mapA, mapB, args);
+  timing_end(slot, s);
   CPC_LAUNCH_CHECK("gemm3_tc_kernel");
   return CPC_OK;
 }

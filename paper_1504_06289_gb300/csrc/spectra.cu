@@ -245,8 +245,10 @@ int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, cudaS
   } else {
     phat = P->d_phat32; hw = P->d_hw32; tw = P->d_tw32;
   }
+  const int slot = timing_begin("conv_kernel", s);
   kern<<<int(grid), G::threads, smem, s>>>(static_cast<const V*>(Uhat), phat, hw, tw,
                                            static_cast<T*>(W), P->R_N, n_items);
+  timing_end(slot, s);
   CPC_LAUNCH_CHECK("conv_kernel");
   return CPC_OK;
 }
