@@ -250,32 +250,24 @@ def run_ours(args, ws, rank, local):
         dt = torch.float32 if prec == "fp32" else torch.float64
         W = torch.empty((3, R_f * R_N, n), dtype=dt, device=dev)
         U = torch.empty((3, R_f, n), dtype=torch.float64, device=dev)
-        S = torch.empty((3, R_f, n + 1, 2), dtype=dt, device=dev)
         E = torch.empty((), dtype=torch.float64, device=dev)
-        nb = lib.cp_hartree_energy_from_factors_workspace(P.handle, R_f, cpc._prec(prec))
+        nb = lib.cp_hartree_energy_workspace(P.handle, R_f, cpc._prec(prec))
         ws_g = torch.empty(max(256, nb), dtype=torch.uint8, device=dev)
-        return W, U, S, E, ws_g
+        return W, U, E, ws_g
 
     def step(prec, bufs, ev=None):
-        """sample -> spectra -> convolutions (V_H factors) -> contraction (E_H), one ABI call each."""
-        W, U, S, E, ws_g = bufs
+        """sample -> cp_hartree_energy (spectra, convolutions = V_H factors W, contraction = E_H):
+        two ABI calls; per-kernel times come from the library's event timing."""
+        W, U, E, ws_g = bufs
         pr = cpc._prec(prec)
         sp = cpc._stream(stream)
         cpc.check(lib.cp_sample_gaussians(n, b, R_f, cpc._ptr(a), cpc._ptr(X), cpc._ptr(U), sp), "sample")
         if ev is not None:
             ev[0].record(stream)
-        cpc.check(lib.cp_factor_spectra(P.handle, R_f, cpc._ptr(U), cpc._ptr(S), pr, sp), "cp_factor_spectra")
+        cpc.check(lib.cp_hartree_energy(P.handle, R_f, cpc._ptr(U), cpc._ptr(c), cpc._ptr(W), None, cpc._ptr(E),
+                                        pr, cpc._ptr(ws_g), ws_g.numel(), sp), "cp_hartree_energy")
         if ev is not None:
             ev[1].record(stream)
-        cpc.check(lib.cp_convolve_from_spectra(P.handle, R_f, cpc._ptr(S), cpc._ptr(W), pr, sp),
-                  "cp_convolve_from_spectra")
-        if ev is not None:
-            ev[2].record(stream)
-        cpc.check(lib.cp_hartree_energy_from_factors(P.handle, R_f, cpc._ptr(U), cpc._ptr(c), cpc._ptr(W), None,
-                                                     cpc._ptr(E), pr, cpc._ptr(ws_g), ws_g.numel(), sp),
-                  "cp_hartree_energy_from_factors")
-        if ev is not None:
-            ev[3].record(stream)
         return E
 
     prec = args.precision
@@ -283,7 +275,7 @@ def run_ours(args, ws, rank, local):
     for _ in range(args.warmup):
         step(prec, bufs)
     torch.cuda.synchronize(dev)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clocks:
         barrier(ws)
@@ -297,12 +289,14 @@ def run_ours(args, ws, rank, local):
         cpc.kernel_timing(False)
         barrier(ws)
     ms_total = start.elapsed_time(stop)
-    kt = {k: cpc.kernel_timing_read(k) for k in ("conv_kernel", "slice_rows_kernel", "gemm3_tc_kernel")}
+    kt = {k: cpc.kernel_timing_read(k)
+          for k in ("spectra_kernel", "conv_kernel", "slice_rows_kernel", "gemm3_tc_kernel")}
     ms_total = max_over_ranks(ms_total, ws, dev)
-    E_fast = bufs[3].item()
-    spec_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))
-    conv_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in evs]))
-    gram_ms = float(np.mean([e[2].elapsed_time(e[3]) for e in evs]))
+    E_fast = bufs[2].item()
+    energy_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))  # the cp_hartree_energy call
+    spec_ms = kt["spectra_kernel"][0] / max(1, kt["spectra_kernel"][1])
+    conv_ms = kt["conv_kernel"][0] / max(1, kt["conv_kernel"][1])
+    gram_ms = energy_ms - spec_ms - conv_ms  # slicing of U, contraction, final sum
     ms_step = ms_total / args.steps
     convs_per_step = 3 * R_f * R_N
     value = ws * convs_per_step * args.steps / (ms_total * 1e-3)
@@ -335,19 +329,23 @@ def run_ours(args, ws, rank, local):
             bf = buffers(form)
             step(form, bf)
             torch.cuda.synchronize(dev)
-            eo = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.fp64_steps)]
+            eo = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.fp64_steps)]
             so, to = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            cpc.kernel_timing(True)
             so.record(stream)
             for k in range(args.fp64_steps):
                 step(form, bf, eo[k])
             to.record(stream)
             torch.cuda.synchronize(dev)
+            cpc.kernel_timing(False)
             mso = so.elapsed_time(to) / args.fp64_steps
+            kto = {k: cpc.kernel_timing_read(k) for k in ("spectra_kernel", "conv_kernel")}
+            sp_o = kto["spectra_kernel"][0] / max(1, kto["spectra_kernel"][1])
+            cv_o = kto["conv_kernel"][0] / max(1, kto["conv_kernel"][1])
+            en_o = float(np.mean([e[0].elapsed_time(e[1]) for e in eo]))
             others[form] = {"ms_per_step": mso, "value": convs_per_step / (mso * 1e-3),
-                            "spectra_ms": float(np.mean([e[0].elapsed_time(e[1]) for e in eo])),
-                            "conv_ms": float(np.mean([e[1].elapsed_time(e[2]) for e in eo])),
-                            "contraction_ms": float(np.mean([e[2].elapsed_time(e[3]) for e in eo])),
-                            "E_H": bf[3].item()}
+                            "spectra_ms": sp_o, "conv_ms": cv_o, "contraction_ms": en_o - sp_o - cv_o,
+                            "E_H": bf[2].item()}
             del bf
             torch.cuda.empty_cache()
         E64 = others.get("fp64", {}).get("E_H", E_fast if prec == "fp64" else None)
@@ -362,8 +360,10 @@ def run_ours(args, ws, rank, local):
     hbm_peak = float(peaks["hbm_gbs"])
     clk = clocks.summary()
     elem = 4 if prec == "fp32" else 8
-    # conv kernel algorithmic bytes per step: write all V_H factors, read spectra of U and p
-    conv_bytes = 3 * R_f * R_N * n * elem + 3 * R_f * (n + 1) * 2 * elem + R_N * (n + 1) * elem
+    # conv kernel algorithmic bytes per step: write all V_H factors (float32 form: and their
+    # three bf16 slices for the tensor-core contraction), read spectra of U and p
+    out_elem = elem + (6 if prec == "fp32" else 0)
+    conv_bytes = 3 * R_f * R_N * n * out_elem + 3 * R_f * (n + 1) * 2 * elem + R_N * (n + 1) * elem
     conv_gbs = conv_bytes / (conv_ms * 1e-3) / 1e9
     # contraction: unique Gram entries (symmetric) x 3 axes x R_N x n cells, 2 flop per multiply-add
     gram_flops = 3 * R_N * (R_f * (R_f + 1) // 2) * n * 2
@@ -392,14 +392,14 @@ def run_ours(args, ws, rank, local):
                                       "algorithmic_flops": tc_flops,
                                       "peak_note": "bf16 dense burst (cuBLAS), " + peak_kind,
                                       "fp32_equivalent_TFLOP/s": gram_flops / (tc_ms * 1e-3) / 1e12}
-        # slicing: 2 launches per step (U rows, W rows): read float64 U / float32 W, write 3 bf16 slices
+        # slicing of U (the W slices come out of the convolution): read float64, write 3 bf16 slices
         sl_tot, sl_cnt = kt.get("slice_rows_kernel", (0.0, 0))
-        sl_ms = sl_tot / max(1, sl_cnt) * 2
-        sl_bytes = 3 * R_f * n * (8 + 6) + 3 * R_f * R_N * n * (4 + 6)
+        sl_ms = sl_tot / max(1, sl_cnt)
+        sl_bytes = 3 * R_f * n * (8 + 6)
         kernels["slice_rows_kernel"] = {"ms": sl_ms, "bound": "hbm", "achieved": sl_bytes / (sl_ms * 1e-3) / 1e9,
                                         "peak": hbm_peak, "unit": "GB/s",
                                         "frac": sl_bytes / (sl_ms * 1e-3) / 1e9 / hbm_peak,
-                                        "algorithmic_bytes": sl_bytes, "note": "two launches per step, ms summed"}
+                                        "algorithmic_bytes": sl_bytes}
     else:
         gram_tf = gram_flops / (gram_ms * 1e-3) / 1e12
         kernels[{"split": "gemm3_kernel", "fp64": "tri_gram_kernel"}[prec]] = {
@@ -431,8 +431,8 @@ def run_ours(args, ws, rank, local):
         "speedup_vs_fp64_gpu": (fp64["ms_per_step"] / ms_step) if fp64 else None,
         "e2e": {"value": ws * convs_per_step * e2e_steps / e2e_s, "unit": "convolutions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
-        # sample, spectra, conv, [slice U, slice W,] contraction, final sum
-        "gpu_launches": (7 if prec == "fp32" else 5) * args.steps,
+        # sample, spectra, conv (+ W slices), [slice U,] contraction, final sum
+        "gpu_launches": (6 if prec == "fp32" else 5) * args.steps,
         "clocks": clk,
     }
     if ws == 1 and not args.no_cpu_baseline:

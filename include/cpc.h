@@ -144,10 +144,11 @@ int cp_convolve_from_spectra(const cpc_kernel* P, int R_f, const void* spec, voi
  * in cp_convolve), then the contraction of U with W: float64 throughout for
  * CPC_FP64.  CPC_FP32 (n a multiple of 128): on the tensor cores, each row
  * of U and of the float32 W split exactly into three bf16 integer slices under
- * a per-row power-of-two scale, the slice products summed exactly over
- * 128-cell chunks in TMEM and folded into a compensated float32 sum per entry
- * (at least as accurate as float32 operands with float32 products); other n:
- * float32 products on CUDA cores.  CPC_SPLIT: float32
+ * a per-row power-of-two scale (the convolution writes W's slices in the same
+ * pass as W), the slice products summed exactly over 128-cell chunks in TMEM
+ * and folded into a compensated float32 sum per entry (at least as accurate
+ * as float32 operands with float32 products); other n: float32 products on
+ * CUDA cores.  CPC_SPLIT: float32
  * products of U and W (rounded on load), compensated float32 accumulation.
  * All forms reduce across tiles in float64.  If a device-side wait of the
  * tensor-core kernel gives up, E_H is written as NaN.  c: [R_f] float64.  G: NULL or
@@ -272,8 +273,8 @@ int lattice_potential_sum(const cpc_kernel* master, const int* L, const int* edg
 
 /* ---- status -------------------------------------------------------------- */
 /* ---- kernel timing (measurement support; the paper has no counterpart) -----
- * While enabled, every launch of conv_kernel, slice_rows_kernel and
- * gemm3_tc_kernel is bracketed by two CUDA events recorded on the stream the
+ * While enabled, every launch of spectra_kernel, conv_kernel,
+ * slice_rows_kernel and gemm3_tc_kernel is bracketed by two CUDA events recorded on the stream the
  * kernel is launched on (up to 8192 launches; later ones go unrecorded).
  * cpc_kernel_timing(1) creates the events on first use and clears earlier
  * records; cpc_kernel_timing(0) stops recording and keeps the records.

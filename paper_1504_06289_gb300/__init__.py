@@ -391,7 +391,8 @@ class CPHartreeEnergy(torch.autograd.Function):
 
 def kernel_timing(enable: bool) -> None:
     """Start (clearing earlier records) or stop CUDA-event timing of the
-    library's main kernels (conv_kernel, slice_rows_kernel, gemm3_tc_kernel)."""
+    library's main kernels (spectra_kernel, conv_kernel, slice_rows_kernel,
+    gemm3_tc_kernel)."""
     check(load().cpc_kernel_timing(1 if enable else 0), "cpc_kernel_timing")
 
 

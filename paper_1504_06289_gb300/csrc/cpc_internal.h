@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -82,6 +83,10 @@ int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uh
 // batched convolution from spectra
 int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W,
                           int precision, cudaStream_t s);
+// float32 convolution that also writes the tensor-core contraction's W slices
+// and row exponents (same values as slicing W afterwards); n >= 128
+int convolve_from_spectra_sliced(const cpc_kernel* P, int R_f, const float2* Uhat32, float* W,
+                                 __nv_bfloat16* slices, long long slice_stride, int* expo, cudaStream_t s);
 
 // float32 contractions (gram32.cu)
 size_t eh32_partials(int R_f, int R_N);
@@ -100,8 +105,11 @@ size_t tc_partials(int R_f, int R_N);
 bool tc_supported(const cpc_kernel* P);
 size_t tc_workspace(const cpc_kernel* P, int R_f);
 int* tc_status_ptr(const cpc_kernel* P, int R_f, void* ws);
+// where a convolution writes the W slices for launch_eh_tc(..., w_sliced = true)
+void tc_w_slices(const cpc_kernel* P, int R_f, void* ws, __nv_bfloat16** slices, long long* slice_stride,
+                 int** expo);
 int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
-                 double* partial, void* ws, cudaStream_t s);
+                 double* partial, void* ws, cudaStream_t s, bool w_sliced = false);
 // the V_H factors and spectra of CPC_SPLIT are float64, like CPC_FP64
 inline int storage_precision(int precision) { return precision == CPC_FP32 ? CPC_FP32 : CPC_FP64; }
 size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision);

@@ -378,9 +378,32 @@ int launch_eh(const cpc_kernel* P, int R_f, const double* U, const double* c, co
 // spatial contraction of U with W in the form's precision.
 int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const double* c, void* W, double* G,
                        double* E_H, int precision, void* ws, cudaStream_t s) {
+  void* cws = static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_f, precision);
+  if (precision == CPC_FP32 && tc_supported(P)) {
+    // the convolution writes W and, in the same pass, the W slices of the
+    // tensor-core contraction (no second pass over W)
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    double2* h64 = reinterpret_cast<double2*>(w);
+    float2* h32 = reinterpret_cast<float2*>(w + spectra_bytes(P, 3 * R_f, CPC_FP64));
+    int st = forward_spectra(P, 3 * R_f, U, h64, h32, s);
+    if (st) return st;
+    void* tws = static_cast<unsigned char*>(cws) + align256(sizeof(double) * eh_partials(P, R_f));
+    __nv_bfloat16* sl;
+    long long sl_stride;
+    int* ex;
+    tc_w_slices(P, R_f, tws, &sl, &sl_stride, &ex);
+    st = convolve_from_spectra_sliced(P, R_f, h32, static_cast<float*>(W), sl, sl_stride, ex, s);
+    if (st) return st;
+    double* partial = static_cast<double*>(cws);
+    st = launch_eh_tc(P, R_f, U, static_cast<const float*>(W), c, G, partial, tws, s, true);
+    if (st) return st;
+    finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, (long long)tc_partials(R_f, P->R_N), P->h * P->h * P->h, E_H,
+                                           tc_status_ptr(P, R_f, tws));
+    CPC_LAUNCH_CHECK("finalize_sum_kernel");
+    return CPC_OK;
+  }
   int st = run_convolve(P, R_f, U, W, precision, ws, s);
   if (st) return st;
-  void* cws = static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_f, precision);
   return launch_eh(P, R_f, U, c, W, G, E_H, precision, cws, s);
 }
 

@@ -456,8 +456,17 @@ static int encode_fn(EncodeTiledFn* out) {
   return CPC_OK;
 }
 
+void tc_w_slices(const cpc_kernel* P, int R_f, void* ws, __nv_bfloat16** slices, long long* slice_stride,
+                 int** expo) {
+  const size_t a = size_t(3) * 3 * R_f * P->n, b = size_t(3) * 3 * R_f * P->R_N * P->n;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  *slices = reinterpret_cast<__nv_bfloat16*>(w + align256(2 * a));
+  *slice_stride = (long long)(b / 3);
+  *expo = reinterpret_cast<int*>(w + align256(2 * a) + align256(2 * b) + align256(4 * size_t(3) * R_f));
+}
+
 int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
-                 double* partial, void* ws, cudaStream_t s) {
+                 double* partial, void* ws, cudaStream_t s, bool w_sliced) {
   const int n = P->n, R_N = P->R_N;
   const size_t a = size_t(3) * 3 * R_f * n, b = size_t(3) * 3 * R_f * R_N * n;
   unsigned char* w = static_cast<unsigned char*>(ws);
@@ -470,8 +479,10 @@ int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, 
   const long long arows = 3LL * R_f, brows = 3LL * R_f * R_N;
   int st0 = tc::launch_slice(U, arows, n, R_f, 1, As, a / 3, eA, s);
   if (st0) return st0;
-  st0 = tc::launch_slice(W, brows, n, R_f, R_N, Bs, b / 3, eB, s);
-  if (st0) return st0;
+  if (!w_sliced) {  // else the convolution already wrote them (convolve_from_spectra_sliced)
+    st0 = tc::launch_slice(W, brows, n, R_f, R_N, Bs, b / 3, eB, s);
+    if (st0) return st0;
+  }
 
   EncodeTiledFn enc;
   int st = encode_fn(&enc);

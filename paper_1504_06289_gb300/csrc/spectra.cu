@@ -14,6 +14,7 @@
 //                    inverse transform, keep the first n outputs.  One CTA
 //                    holds `slots` transforms in shared memory and walks the
 //                    items in a grid-stride loop.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -119,13 +120,78 @@ spectra_kernel(int mode, const double* __restrict__ src, int ncols, double2* __r
   }
 }
 
+// Optional second output of the float32 convolution: the exact bf16 slices
+// of each output row (the operand format of the tensor-core contraction,
+// csrc/gram_tc.cu), written in the same chunk-blocked layout and with the
+// same arithmetic as slice_rows_kernel, so the result is bit-identical.
+struct SliceOut {
+  __nv_bfloat16* out;      // [3 slices][3 R_N][n/64][R_f][64]
+  long long slice_stride;  // elements between slices
+  int* expo;               // [3 R_f R_N] row exponents, row = item
+  int R_f;
+};
+
+// Row maximum over the TPF threads of one transform, then the three slices of
+// each of this thread's outputs (reals 2o, 2o+1, o = t + r NC/P, r < P/2).
+template <typename PL>
+__device__ __forceinline__ void slice_epilogue(const float2* v, const SliceOut& so, long long item, bool active,
+                                               int slot, int t, int R_N) {
+  constexpr int NC = PL::NC, TPF = PL::TPF;
+  __shared__ float red[32];  // per-warp maxima (transforms of >= 32 threads)
+  float m = 0.0f;
+#pragma unroll
+  for (int r = 0; r < PL::P / 2; ++r) m = fmaxf(m, fmaxf(fabsf(v[r].x), fabsf(v[r].y)));
+  // within a warp: lanes of the same transform (TPF lanes, or all 32)
+  constexpr int LW = TPF < 32 ? TPF : 32;
+#pragma unroll
+  for (int o = LW / 2; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if constexpr (TPF > 32) {
+    // a transform spans TPF / 32 whole warps: combine them
+    constexpr int WPF = TPF / 32;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = red[slot * WPF];
+#pragma unroll
+    for (int w = 1; w < WPF; ++w) m = fmaxf(m, red[slot * WPF + w]);
+    __syncthreads();  // red[] is reused by the next item
+  }
+  if (!active) return;
+  int e = 0;
+  if (m > 0.0f) frexpf(m, &e);
+  if (t == 0) so.expo[item] = e;
+  const long long col = item / R_N;
+  const int q = int(item - col * R_N);
+  const int l = int(col / so.R_f), srow = int(col - (long long)l * so.R_f);
+  constexpr int T = NC / 64;
+  __nv_bfloat16* ob = so.out + ((long long)(l * R_N + q) * T * so.R_f + srow) * 64;
+#pragma unroll
+  for (int r = 0; r < PL::P / 2; ++r) {
+    const int i = 2 * (t + r * (NC / PL::P));  // even: the pair (i, i+1) stays in one 64-cell chunk
+    float sl[3][2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float a = ldexpf(h ? v[r].y : v[r].x, 8 - e);  // |a| < 256
+      const float s0 = rintf(a);
+      const float b = (a - s0) * 256.0f;  // exact
+      const float s1 = rintf(b);
+      sl[0][h] = s0;
+      sl[1][h] = s1;
+      sl[2][h] = rintf((b - s1) * 256.0f);
+    }
+    __nv_bfloat16* o = ob + (long long)(i >> 6) * so.R_f * 64 + (i & 63);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      *reinterpret_cast<__nv_bfloat162*>(o + k * so.slice_stride) = __floats2bfloat162_rn(sl[k][0], sl[k][1]);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // batched convolution: item = col * R_N + q writes W[item][0..n-1].
-template <typename T, int LOGN>
+template <typename T, int LOGN, bool SLICE>
 __global__ void __launch_bounds__(Geometry<LOGN, T>::threads, Geometry<LOGN, T>::min_blocks)
 conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict__ phat,
             const typename cvec<T>::type* __restrict__ hw, const typename cvec<T>::type* __restrict__ tw,
-            T* __restrict__ W, int R_N, long long n_items) {
+            T* __restrict__ W, int R_N, long long n_items, SliceOut so) {
   using V = typename cvec<T>::type;
   using G = Geometry<LOGN, T>;
   using PL = typename G::PL;
@@ -175,14 +241,17 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
     {
       V v[1][PL::P];
       pass_compute<NC, PL::P, 1, +1>(sbuf, v, t, NC / PL::P, tw);
+#pragma unroll
+      for (int r = 0; r < PL::P / 2; ++r) v[0][r] = cmk<V>(v[0][r].x * scale, v[0][r].y * scale);
       if (active) {
         T* out = W + (size_t)item * NC;
 #pragma unroll
         for (int r = 0; r < PL::P / 2; ++r) {
           const int o = t + r * (NC / PL::P);  // complex output o -> reals 2o, 2o+1
-          *reinterpret_cast<V*>(out + 2 * o) = cmk<V>(v[0][r].x * scale, v[0][r].y * scale);
+          *reinterpret_cast<V*>(out + 2 * o) = v[0][r];
         }
       }
+      if constexpr (SLICE) slice_epilogue<PL>(v[0], so, item, active, slot, t, R_N);
     }
     __syncthreads();
   }
@@ -219,17 +288,19 @@ int launch_spectra(int mode, const double* src, int ncols, double2* o64, float2*
   CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::threads, smem));
   const int groups = (ncols + G::slots - 1) / G::slots;
   const int grid = std::max(1, std::min(groups, std::max(1, per_sm) * sm_count()));
+  const int slot = timing_begin("spectra_kernel", s);
   kern<<<grid, G::threads, smem, s>>>(mode, src, ncols, o64, o32, r64, r32, P->d_hw64, P->d_tw64);
+  timing_end(slot, s);
   CPC_LAUNCH_CHECK("spectra_kernel");
   return CPC_OK;
 }
 
-template <typename T, int LOGN>
-int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, cudaStream_t s) {
+template <typename T, int LOGN, bool SLICE>
+int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const SliceOut& so, cudaStream_t s) {
   using G = Geometry<LOGN, T>;
   using V = typename cvec<T>::type;
   const size_t smem = sizeof(V) * G::slots * padded_len(1 << LOGN);
-  auto kern = conv_kernel<T, LOGN>;
+  auto kern = conv_kernel<T, LOGN, SLICE>;
   int st = configure(kern, smem);
   if (st) return st;
   int per_sm = 0;
@@ -247,7 +318,7 @@ int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, cudaS
   }
   const int slot = timing_begin("conv_kernel", s);
   kern<<<int(grid), G::threads, smem, s>>>(static_cast<const V*>(Uhat), phat, hw, tw,
-                                           static_cast<T*>(W), P->R_N, n_items);
+                                           static_cast<T*>(W), P->R_N, n_items, so);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("conv_kernel");
   return CPC_OK;
@@ -264,13 +335,18 @@ int dispatch_spectra(int logn, int mode, const double* src, int ncols, double2* 
   }
 }
 
-template <typename T, int LOGN>
-int dispatch_conv(int logn, const cpc_kernel* P, int ncols, const void* Uhat, void* W, cudaStream_t s) {
+template <typename T, int LOGN, bool SLICE>
+int dispatch_conv(int logn, const cpc_kernel* P, int ncols, const void* Uhat, void* W, const SliceOut& so,
+                  cudaStream_t s) {
   if constexpr (LOGN > kMaxLogN) {
     return fail(CPC_ERR_UNSUPPORTED, "conv: n too large");
   } else {
-    if (logn == LOGN) return launch_conv<T, LOGN>(P, ncols, Uhat, W, s);
-    return dispatch_conv<T, LOGN + 1>(logn, P, ncols, Uhat, W, s);
+    if constexpr (SLICE && LOGN < 7) {
+      if (logn == LOGN) return fail(CPC_ERR_UNSUPPORTED, "sliced conv: n must be at least 128");
+    } else {
+      if (logn == LOGN) return launch_conv<T, LOGN, SLICE>(P, ncols, Uhat, W, so, s);
+    }
+    return dispatch_conv<T, LOGN + 1, SLICE>(logn, P, ncols, Uhat, W, so, s);
   }
 }
 
@@ -288,8 +364,16 @@ int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uh
 
 int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W, int precision,
                           cudaStream_t s) {
-  if (precision == CPC_FP64) return dispatch_conv<double, kMinLogN>(ilog2(P->n), P, ncols, Uhat, W, s);
-  return dispatch_conv<float, kMinLogN>(ilog2(P->n), P, ncols, Uhat, W, s);
+  const SliceOut none{nullptr, 0, nullptr, 0};
+  if (precision == CPC_FP64)
+    return dispatch_conv<double, kMinLogN, false>(ilog2(P->n), P, ncols, Uhat, W, none, s);
+  return dispatch_conv<float, kMinLogN, false>(ilog2(P->n), P, ncols, Uhat, W, none, s);
+}
+
+int convolve_from_spectra_sliced(const cpc_kernel* P, int R_f, const float2* Uhat32, float* W,
+                                 __nv_bfloat16* slices, long long slice_stride, int* expo, cudaStream_t s) {
+  const SliceOut so{slices, slice_stride, expo, R_f};
+  return dispatch_conv<float, kMinLogN, true>(ilog2(P->n), P, 3 * R_f, Uhat32, W, so, s);
 }
 
 size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision) {
