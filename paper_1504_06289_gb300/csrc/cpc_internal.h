@@ -34,6 +34,8 @@ struct cpc_kernel {
   // half-angle table hw[f] = exp(-2 pi i f / (2n)), f <= n.
   double2* d_tw64 = nullptr;
   float2* d_tw32 = nullptr;
+  double2* d_twp64 = nullptr;  // per-pass twiddle tables of the FFT plans (fft.cuh)
+  float2* d_twp32 = nullptr;
   double2* d_hw64 = nullptr;
   float2* d_hw32 = nullptr;
   // CONV only: Parseval weights d_q[2f+j] = w_f phat_q[f] / (2n), float32, [R_N][2(n+1)]
@@ -75,6 +77,7 @@ void build_twiddles(int n, std::vector<double>& tw_re, std::vector<double>& tw_i
                     std::vector<double>& hw_re, std::vector<double>& hw_im);
 
 // device-side builders (spectra.cu)
+int build_pass_twiddles(cpc_kernel* P, cudaStream_t s);
 int compute_kernel_spectrum(cpc_kernel* P, cudaStream_t s);
 
 // spectra of U columns into workspace (float64 and/or float32 copies)

@@ -110,18 +110,54 @@ struct FftPlan {
   static_assert(LOGN >= LOGP, "FFT smaller than one thread's points");
 };
 
-// Twiddle: x * w^e for w = exp(-2 pi i / NC) (SIGN < 0) or its conjugate.
+// Twiddle: x * w^e for w = exp(-2 pi i / NC) (SIGN < 0) or its conjugate;
+// `k` indexes the pass table (below), which holds w^e.
 template <int SIGN, typename V>
-__device__ __forceinline__ V twiddle(V x, const V* __restrict__ tw, int e) {
-  V w = __ldg(tw + e);
+__device__ __forceinline__ V twiddle(V x, const V* __restrict__ twp, int k) {
+  V w = __ldg(twp + k);
   return SIGN > 0 ? cmulc(x, w) : cmul(x, w);
+}
+
+// Pass tables.  Pass p >= 1 of a plan (Ns = R1 P^(p-1) butterfly groups,
+// radix P) multiplies point r of butterfly j by w^((j mod Ns) (NC/(Ns P)) r).
+// Its table stores these values at (r-1) Ns + (j mod Ns), so that the lanes
+// of a warp (consecutive j) read consecutive entries; the tables of passes
+// 1..NP-1 follow each other (offset of pass p: sum over earlier passes of
+// (P-1) Ns).  The entries are copies of the flat table w^e, e = 0..NC-1.
+template <int LOGN, int LOGP>
+__host__ __device__ constexpr int pass_table_offset(int p) {
+  using PL = FftPlan<LOGN, LOGP>;
+  int off = 0, Ns = PL::R1;
+  for (int q = 1; q < p; ++q) { off += (PL::P - 1) * Ns; Ns *= PL::P; }
+  return off;
+}
+template <int LOGN, int LOGP>
+__host__ __device__ constexpr int pass_table_size() {
+  return pass_table_offset<LOGN, LOGP>(FftPlan<LOGN, LOGP>::NP);
+}
+// flat-table exponent of entry k of the pass tables (inverse of the layout above)
+template <int LOGN, int LOGP>
+__host__ __device__ inline int pass_table_exponent(int k) {
+  using PL = FftPlan<LOGN, LOGP>;
+  int Ns = PL::R1;
+  for (int p = 1; p < PL::NP; ++p) {
+    const int sz = (PL::P - 1) * Ns;
+    if (k < sz) {
+      const int r = k / Ns + 1, m = k % Ns;
+      return m * (PL::NC / (Ns * PL::P)) * r;
+    }
+    k -= sz;
+    Ns *= PL::P;
+  }
+  return 0;
 }
 
 // Load + twiddle + DFT of one pass from the padded shared buffer.
 // Butterfly j of this thread: j = b * (NC / (R*B)) + t; points j + r NC/R.
+// twp: this pass's table (unused when Ns == 1).
 template <int NC, int R, int B, int SIGN, typename V>
 __device__ __forceinline__ void pass_compute(const V* sbuf, V (&v)[B][R], int t, int Ns,
-                                             const V* __restrict__ tw) {
+                                             const V* __restrict__ twp) {
   constexpr int stride = NC / R;
   constexpr int nbf = NC / (R * B);
 #pragma unroll
@@ -130,9 +166,9 @@ __device__ __forceinline__ void pass_compute(const V* sbuf, V (&v)[B][R], int t,
 #pragma unroll
     for (int r = 0; r < R; ++r) v[b][r] = sbuf[pad_index(j + r * stride)];
     if (Ns > 1) {
-      const int e0 = (j & (Ns - 1)) * (NC / (Ns * R));
+      const int m = j & (Ns - 1);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[b][r] = twiddle<SIGN>(v[b][r], tw, e0 * r);
+      for (int r = 1; r < R; ++r) v[b][r] = twiddle<SIGN>(v[b][r], twp, (r - 1) * Ns + m);
     }
     dft<R, SIGN>(v[b]);
   }
@@ -153,17 +189,20 @@ __device__ __forceinline__ void pass_store(V* sbuf, const V (&v)[B][R], int t, i
 
 // Middle passes 2..NP-1 (radix P, one butterfly per thread): smem -> smem.
 // Enter with the first pass stored; leave with pass NP-1 stored and synced.
+// tw: the plan's pass tables; the last pass uses tw + pass_table_offset(NP-1).
 template <int LOGN, int LOGP, int SIGN, typename V>
 __device__ __forceinline__ void middle_passes(V* sbuf, int t, const V* __restrict__ tw) {
   using PL = FftPlan<LOGN, LOGP>;
   int Ns = PL::R1;
+  const V* twp = tw;
 #pragma unroll 1
   for (int p = 1; p < PL::NP - 1; ++p) {
     V v[1][PL::P];
-    pass_compute<PL::NC, PL::P, 1, SIGN>(sbuf, v, t, Ns, tw);
+    pass_compute<PL::NC, PL::P, 1, SIGN>(sbuf, v, t, Ns, twp);
     __syncthreads();
     pass_store<PL::NC, PL::P, 1>(sbuf, v, t, Ns);
     __syncthreads();
+    twp += (PL::P - 1) * Ns;
     Ns *= PL::P;
   }
 }

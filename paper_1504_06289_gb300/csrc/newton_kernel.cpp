@@ -276,7 +276,11 @@ int make_newton_kernel(int n, double b, int M, int kind, void* stream, cpc_kerne
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->d_tw32, tw32.data(), sizeof(float2) * n, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->d_hw64, hw64.data(), sizeof(double2) * (n + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->d_hw32, hw32.data(), sizeof(float2) * (n + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_twp64, sizeof(double2) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_twp32, sizeof(float2) * n);
     if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: FFT tables"); cleanup(); return st; }
+    st = build_pass_twiddles(P, s);
+    if (st != CPC_OK) { cleanup(); return st; }
     st = compute_kernel_spectrum(P, s);
     if (st != CPC_OK) { cleanup(); return st; }
     e = cudaMalloc(&P->d_specw32, sizeof(float) * size_t(P->R_N) * 2 * (n + 1));
@@ -318,6 +322,8 @@ int cpc_kernel_free(cpc_kernel* P) {
   cudaFree(P->d_phat32);
   cudaFree(P->d_tw64);
   cudaFree(P->d_tw32);
+  cudaFree(P->d_twp64);
+  cudaFree(P->d_twp32);
   cudaFree(P->d_hw64);
   cudaFree(P->d_hw32);
   cudaFree(P->d_specw32);

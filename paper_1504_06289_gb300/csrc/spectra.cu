@@ -91,7 +91,7 @@ spectra_kernel(int mode, const double* __restrict__ src, int ncols, double2* __r
     middle_passes<LOGN, G::LOGP, -1>(sbuf, t, tw);
     {
       double2 v[1][PL::P];
-      pass_compute<NC, PL::P, 1, -1>(sbuf, v, t, NC / PL::P, tw);
+      pass_compute<NC, PL::P, 1, -1>(sbuf, v, t, NC / PL::P, tw + pass_table_offset<LOGN, G::LOGP>(PL::NP - 1));
       __syncthreads();
       pass_store<NC, PL::P, 1>(sbuf, v, t, NC / PL::P);
     }
@@ -240,7 +240,7 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
     middle_passes<LOGN, G::LOGP, +1>(sbuf, t, tw);
     {
       V v[1][PL::P];
-      pass_compute<NC, PL::P, 1, +1>(sbuf, v, t, NC / PL::P, tw);
+      pass_compute<NC, PL::P, 1, +1>(sbuf, v, t, NC / PL::P, tw + pass_table_offset<LOGN, G::LOGP>(PL::NP - 1));
 #pragma unroll
       for (int r = 0; r < PL::P / 2; ++r) v[0][r] = cmk<V>(v[0][r].x * scale, v[0][r].y * scale);
       if (active) {
@@ -289,7 +289,7 @@ int launch_spectra(int mode, const double* src, int ncols, double2* o64, float2*
   const int groups = (ncols + G::slots - 1) / G::slots;
   const int grid = std::max(1, std::min(groups, std::max(1, per_sm) * sm_count()));
   const int slot = timing_begin("spectra_kernel", s);
-  kern<<<grid, G::threads, smem, s>>>(mode, src, ncols, o64, o32, r64, r32, P->d_hw64, P->d_tw64);
+  kern<<<grid, G::threads, smem, s>>>(mode, src, ncols, o64, o32, r64, r32, P->d_hw64, P->d_twp64);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("spectra_kernel");
   return CPC_OK;
@@ -312,9 +312,9 @@ int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const
   const V* hw;
   const V* tw;
   if constexpr (sizeof(T) == 8) {
-    phat = P->d_phat64; hw = P->d_hw64; tw = P->d_tw64;
+    phat = P->d_phat64; hw = P->d_hw64; tw = P->d_twp64;
   } else {
-    phat = P->d_phat32; hw = P->d_hw32; tw = P->d_tw32;
+    phat = P->d_phat32; hw = P->d_hw32; tw = P->d_twp32;
   }
   const int slot = timing_begin("conv_kernel", s);
   kern<<<int(grid), G::threads, smem, s>>>(static_cast<const V*>(Uhat), phat, hw, tw,
@@ -351,6 +351,40 @@ int dispatch_conv(int logn, const cpc_kernel* P, int ncols, const void* Uhat, vo
 }
 
 }  // namespace
+
+template <int LOGN, int LOGP, typename V>
+__global__ void pass_table_kernel(const V* __restrict__ flat, V* __restrict__ out) {
+  constexpr int N = pass_table_size<LOGN, LOGP>();
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x)
+    out[k] = flat[pass_table_exponent<LOGN, LOGP>(k)];
+}
+
+template <int LOGN>
+int launch_pass_tables(cpc_kernel* P, cudaStream_t s) {
+  constexpr int L64 = Geometry<LOGN, double>::LOGP, L32 = Geometry<LOGN, float>::LOGP;
+  static_assert(pass_table_size<LOGN, L64>() <= (1 << LOGN) && pass_table_size<LOGN, L32>() <= (1 << LOGN),
+                "pass tables fit in n entries");
+  pass_table_kernel<LOGN, L64><<<8, 256, 0, s>>>(P->d_tw64, P->d_twp64);
+  pass_table_kernel<LOGN, L32><<<8, 256, 0, s>>>(P->d_tw32, P->d_twp32);
+  CPC_LAUNCH_CHECK("pass_table_kernel");
+  return CPC_OK;
+}
+
+template <int LOGN>
+int dispatch_pass_tables(int logn, cpc_kernel* P, cudaStream_t s) {
+  if constexpr (LOGN > kMaxLogN) {
+    return fail(CPC_ERR_UNSUPPORTED, "pass tables: n too large");
+  } else {
+    if (logn == LOGN) return launch_pass_tables<LOGN>(P, s);
+    return dispatch_pass_tables<LOGN + 1>(logn, P, s);
+  }
+}
+
+// per-pass twiddle tables of the float64 and float32 plans (n entries each,
+// allocated by the caller), built from the flat tables
+int build_pass_twiddles(cpc_kernel* P, cudaStream_t s) {
+  return dispatch_pass_tables<kMinLogN>(ilog2(P->n), P, s);
+}
 
 int compute_kernel_spectrum(cpc_kernel* P, cudaStream_t s) {
   return dispatch_spectra<kMinLogN>(ilog2(P->n), 1, P->d_p, P->R_N, nullptr, nullptr, P->d_phat64,
