@@ -519,7 +519,15 @@ def run_coulomb(args, ws, rank, local):
         with torch.cuda.graph(g, stream=stream):
             body()
         ms = _timed(stream, g.replay, args.steps, max(1, args.warmup))
-        res[prec] = {"ms_per_step": ms, "tiles_per_cta": tiles, "J_diag_sum_w": float(np.dot(
+        # per-kernel device times: one more (uncaptured) step with the library's event timing on
+        torch.cuda.synchronize()
+        cpc.kernel_timing(True)
+        body()
+        torch.cuda.synchronize()
+        cpc.kernel_timing(False)
+        kms = {k: cpc.kernel_timing_read(k)[0] for k in ("spectra_kernel", "conv_kernel", "slice_rows_kernel",
+                                                           "gemm3_tc_kernel")}
+        res[prec] = {"ms_per_step": ms, "tiles_per_cta": tiles, "kernel_ms": kms, "J_diag_sum_w": float(np.dot(
             basis["w"], J.cpu().numpy()[[items.index((m, m)) for m in range(nb)]]))}
         del U_it, W_rho, wsb
         torch.cuda.empty_cache()
@@ -527,20 +535,33 @@ def run_coulomb(args, ws, rank, local):
         return
     head = "fp32" if "fp32" in res else "fp64"
     ms = res[head]["ms_per_step"]
-    flops = 2.0 * 3 * n_factors * R_rho * P.R_N * n
-    clk = 2070.0
-    peak = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12
-    achieved = flops / (ms * 1e-3) / 1e12
+    flops = 2.0 * 3 * n_factors * R_rho * P.R_N * n  # contraction multiply-adds x 2
+    peaks, peak_kind = load_peaks()
     if "split" in res:
         res["split"]["rel_diff_E_vs_fp32"] = abs(res["split"]["J_diag_sum_w"] / res["fp32"]["J_diag_sum_w"] - 1)
+    tc_ms = res[head]["kernel_ms"].get("gemm3_tc_kernel", 0.0)
+    if head == "fp32" and tc_ms > 0:
+        # tensor-core form: 6 bf16 slice products per float32 multiply-add
+        achieved = 6 * flops / (tc_ms * 1e-3) / 1e12
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        roof = {"kernel": "gemm3_tc_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "kernel_ms": tc_ms, "fp32_equivalent_TFLOP/s": flops / (tc_ms * 1e-3) / 1e12,
+                "note": "bf16 slice-product flops 6 x 2*3*factors*R_rho*R_N*n per launch / event time"}
+        launches = 9  # sample, 2 Hadamard, spectra, conv, slice items, slice W, contraction, item sums
+    else:
+        clk = 2070.0
+        peak = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12
+        achieved = flops / (ms * 1e-3) / 1e12
+        roof = {"kernel": "gemm3_kernel(ROWS)+conv", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "note": "whole step; contraction flops 2*3*factors*R_rho*R_N*n"}
+        launches = None
     _line(args, ws, "Coulomb-matrix entries/s", ws * len(items) / (ms * 1e-3), "entries/s", ms,
           "f32" if head == "fp32" else "f64",
           {"workload": name, "n": n, "items": len(items), "item_factors": n_factors, "R_rho": R_rho, "R_N": P.R_N,
            "graph": "sample + 2 Hadamard + coulomb_matrix captured in one CUDA graph"},
-          forms=res, roofline={"kernel": "gemm3_kernel(ROWS)+conv", "bound": "alu", "achieved": achieved,
-                               "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                               "note": "whole step; contraction flops 2*3*factors*R_rho*R_N*n"},
-          gpu_launches=None)
+          forms=res, roofline=roof, gpu_launches=launches * args.steps if launches else None)
 
 
 def run_adjoint(args, ws, rank, local):

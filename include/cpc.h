@@ -232,13 +232,19 @@ int cp_gaussian_param_grad(int n, double b, int R, const double* a, const double
  * [0, n_factors] are clamped, never dereferenced); U_items: [3][n_factors][n];
  * c_items: [n_factors]; U_rho: [3][R_rho][n]; c_rho: [R_rho]; J: [n_items]
  * float64.  Item factors are concatenated into one row space, so items of
- * uneven rank share tiles and no item leaves a tile idle; the contraction is
- * one persistent launch over (row tile, column group) work units, a column
- * group being tiles_per_cta consecutive 64-column tiles of the R_rho*R_N V_H
- * columns (0 = default 8; else a power of two in [4, 128]).  Stream-ordered
- * and allocation-free, so a sequence of these calls can be captured in a CUDA
- * graph.  Workspace: coulomb_matrix_workspace bytes (sized for the smallest
- * tiles_per_cta). */
+ * uneven rank share tiles and no item leaves a tile idle.  CPC_FP64, CPC_SPLIT
+ * (and CPC_FP32 when n is not a multiple of 128): one persistent launch over
+ * (row tile, column group) work units, a column group being tiles_per_cta
+ * consecutive 64-column tiles of the R_rho*R_N V_H columns (0 = default 8;
+ * else a power of two in [4, 128]).  CPC_FP32 with n a multiple of 128: the
+ * tensor-core contraction of cp_hartree_energy (exact bf16 slices of the item
+ * factors and of the float32 W_rho) on tiles of 256 item factors x 128 rho
+ * factors per kernel term, tiles_per_cta unused; if one of its device-side
+ * waits gives up, J is written as NaN.  Stream-ordered and allocation-free, so
+ * a sequence of these calls can be captured in a CUDA graph.  Workspace:
+ * coulomb_matrix_workspace bytes (sized for the smallest tiles_per_cta; for
+ * the tensor-core form it holds the bf16 slices, 18 n (n_factors + R_rho R_N)
+ * bytes). */
 size_t coulomb_matrix_workspace(const cpc_kernel* P, int n_items, int n_factors, int R_rho,
                                 int precision);
 int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
@@ -250,7 +256,9 @@ int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, int n_facto
  * contraction for every tiles_per_cta in {4, 8, ..., 128} on the caller's
  * data (CUDA events on `stream`; this call synchronises the stream), writes
  * the fastest to *best_tiles_per_cta (and its time in ms to *best_ms if not
- * NULL) and leaves J computed with it.  Same arguments as coulomb_matrix. */
+ * NULL) and leaves J computed with it.  The tensor-core form has no
+ * schedule parameter: it is timed once and the default is reported.  Same
+ * arguments as coulomb_matrix. */
 int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* off, int n_factors,
                         const double* U_items, const double* c_items, int R_rho, const double* U_rho,
                         const double* c_rho, void* W_rho, double* J, int precision, void* ws,

@@ -108,6 +108,12 @@ size_t tc_partials(int R_f, int R_N);
 bool tc_supported(const cpc_kernel* P);
 size_t tc_workspace(const cpc_kernel* P, int R_f);
 int* tc_status_ptr(const cpc_kernel* P, int R_f, void* ws);
+// tensor-core Coulomb-matrix rows (M item factors against Ns rho factors)
+size_t tc_rows_workspace(const cpc_kernel* P, int M, int Ns);
+size_t tc_rows_groups(const cpc_kernel* P, int Ns);
+int* tc_rows_status_ptr(const cpc_kernel* P, int M, int Ns, void* ws);
+int launch_rows_tc(const cpc_kernel* P, int M, const double* U_items, int Ns, const float* W_rho,
+                   const double* c_rho, double* rowpart, void* ws, cudaStream_t s);
 // where a convolution writes the W slices for launch_eh_tc(..., w_sliced = true)
 void tc_w_slices(const cpc_kernel* P, int R_f, void* ws, __nv_bfloat16** slices, long long* slice_stride,
                  int** expo);

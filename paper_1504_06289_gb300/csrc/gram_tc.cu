@@ -48,7 +48,8 @@ constexpr uint32_t TMEM_COLS = 512;  // 3 groups x 128 columns, then the product
 constexpr uint32_t PROD_COL = 3 * BN;
 // stages, alignment slack, barriers, then per-column exponents (3 axes) and coefficients
 constexpr size_t kColBytes = 3 * BN * sizeof(int) + BN * sizeof(double);
-constexpr size_t kSmemBytes = size_t(STAGES) * STAGE_BYTES + 1024 + 256 + kColBytes;
+constexpr size_t kRowBytes = 4 * BM * sizeof(double);  // rows mode: the 4 column quarters of each row
+constexpr size_t kSmemBytes = size_t(STAGES) * STAGE_BYTES + 1024 + 256 + kColBytes + kRowBytes;
 constexpr long kSpinLimit = 20000000;
 
 // x -> (s0, s1, s2) with one exponent per row (2^e > max |x| over the row):
@@ -108,12 +109,14 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const TS* __restrict__ 
 }
 
 struct Args {
-  const int* eA;           // [3 * R_f] row exponents of U, row l*R_f + r
-  const int* eB;           // [3 * R_f * R_N] row exponents of W, row (l*R_f + s)*R_N + q
-  int R_f, R_N, n;
-  const double* c;
-  double* partial;
-  double* G;
+  const int* eA;           // [3 * M] row exponents of the A rows (U or item factors), row l*M + r
+  const int* eB;           // [3 * Ns * R_N] row exponents of W, row (l*Ns + s)*R_N + q
+  int M, Ns, R_N, n;       // A rows, W factor columns, kernel terms, cells
+  int rows_mode;           // 0: E_H (M == Ns, symmetric, upper triangle); 1: per-row sums
+  const double* c;         // E_H: coefficients of rows and columns
+  const double* c_col;     // column coefficients c_s
+  double* partial;         // E_H: one sum per CTA; rows mode: [(q * n_ct + ct) * M + r]
+  double* G;               // E_H only (may be NULL)
   int* status;
 };
 
@@ -210,16 +213,17 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_ptr + 1);
   double* col_c = reinterpret_cast<double*>(smem + STAGES * STAGE_BYTES + 256);  // [BN]
   int* col_e = reinterpret_cast<int*>(col_c + BN);                              // [3][BN]
+  double* row_q = reinterpret_cast<double*>(col_e + 3 * BN);                    // [4][BM]
   __shared__ double red[THREADS / 32];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t rank = umma::cluster_ctarank();
   const int q = blockIdx.y;
-  const int n_ct = (g.R_f + BN - 1) / BN;
+  const int n_ct = (g.Ns + BN - 1) / BN;
   const int pair = blockIdx.x >> 1;
   const int rp = pair / n_ct, ct = pair % n_ct;
   const int r0p = rp * 2 * BM, s0 = ct * BN;
-  if (r0p > s0 + BN - 1) {  // the whole pair tile lies below the diagonal: both CTAs leave
+  if (!g.rows_mode && r0p > s0 + BN - 1) {  // the whole pair tile lies below the diagonal: both CTAs leave
     if (tid == 0) g.partial[(size_t)q * gridDim.x + blockIdx.x] = 0.0;
     return;
   }
@@ -227,8 +231,8 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   // the tile's column coefficients and row exponents of W, once
   for (int i = tid; i < 4 * BN; i += THREADS) {
     const int j = i % BN, s = s0 + j;
-    if (i < BN) col_c[j] = (s < g.R_f) ? g.c[s] : 0.0;
-    else col_e[i - BN] = (s < g.R_f) ? g.eB[((long long)(i / BN - 1) * g.R_f + s) * g.R_N + q] : 0;
+    if (i < BN) col_c[j] = (s < g.Ns) ? g.c_col[s] : 0.0;
+    else col_e[i - BN] = (s < g.Ns) ? g.eB[((long long)(i / BN - 1) * g.Ns + s) * g.R_N + q] : 0;
   }
   if (warp == 0) umma::tmem_alloc_pair(tmem_ptr, TMEM_COLS);
   if (tid == 32) {
@@ -339,7 +343,7 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         // axis l finished: G_l = 2^(e_r + e_s - 16) (tot + lo); the running
         // product over axes lives in TMEM columns PROD_COL.. between axes
         const int l = pp / PA;
-        const int er = (r < g.R_f) ? g.eA[l * g.R_f + r] : 0;
+        const int er = (r < g.M) ? g.eA[l * g.M + r] : 0;
 #pragma unroll
         for (int cb = 0; cb < BNW / 16; ++cb) {
           float pv[16];
@@ -356,15 +360,18 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             const float Gv = ldexpf(tot[j] + lj, er + es - 16);
             tot[j] = 0.0f;
             if (j & 1) lo[j / 2] = __float2bfloat162_rn(0.0f);
-            const bool in = r < g.R_f && s < g.R_f && r <= s;
+            const bool in = r < g.M && s < g.Ns && (g.rows_mode || r <= s);
             if (g.G && in) {
-              double* Gq = g.G + ((size_t)l * gridDim.y + q) * (size_t)g.R_f * g.R_f;
-              Gq[(size_t)r * g.R_f + s] = Gv;
-              Gq[(size_t)s * g.R_f + r] = Gv;
+              double* Gq = g.G + ((size_t)l * gridDim.y + q) * (size_t)g.M * g.M;
+              Gq[(size_t)r * g.M + s] = Gv;
+              Gq[(size_t)s * g.M + r] = Gv;
             }
             const float pr = (l > 0) ? pv[jj] * Gv : Gv;
             pv[jj] = pr;
-            if (l == 2 && in) row += (r == s ? 1.0 : 2.0) * col_c[part * BNW + j] * double(pr);
+            if (l == 2 && in) {
+              const double wgt = (g.rows_mode || r == s) ? 1.0 : 2.0;  // E_H: off-diagonal pairs twice
+              row += wgt * col_c[part * BNW + j] * double(pr);
+            }
           }
           if (l < 2) {
             umma::tmem_st16(lane_base + PROD_COL + cb * 16, pv);
@@ -373,13 +380,20 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         }
       }
     }
-    if (ok && r < g.R_f) sum = g.c[r] * row;
+    if (g.rows_mode) row_q[part * BM + 32 * quad + lane] = ok ? row : 0.0;
+    else if (ok && r < g.M) sum = g.c[r] * row;
   }
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if (lane == 0) red[warp] = sum;
   umma::fence_before();
   __syncthreads();
-  if (tid == 0) {
+  if (g.rows_mode) {
+    // row sums of this CTA's 128 rows over the tile's 128 columns
+    if (tid < BM && r0 + tid < g.M)
+      g.partial[((size_t)q * n_ct + ct) * g.M + r0 + tid] =
+          row_q[tid] + row_q[BM + tid] + row_q[2 * BM + tid] + row_q[3 * BM + tid];
+    if (tid == 0 && *abort_flag) atomicExch(g.status, 1);
+  } else if (tid == 0) {
     double s = 0.0;
     for (int w = 0; w < THREADS / 32; ++w) s += red[w];
     g.partial[(size_t)q * gridDim.x + blockIdx.x] = s;
@@ -424,16 +438,36 @@ size_t tc_partials(int R_f, int R_N) {
 // two 64-cell chunks per accumulation: n a multiple of 128
 bool tc_supported(const cpc_kernel* P) { return P->n >= 2 * tc::BKC && P->n % (2 * tc::BKC) == 0; }
 
-// bytes: A slices, B slices, row exponents of A and B, status word (each 256-aligned)
-size_t tc_workspace(const cpc_kernel* P, int R_f) {
-  const size_t a = size_t(3) * 3 * R_f * P->n, b = size_t(3) * 3 * R_f * P->R_N * P->n;
-  return align256(2 * a) + align256(2 * b) + align256(4 * size_t(3) * R_f) + align256(4 * size_t(3) * R_f * P->R_N) +
-         256;
+namespace {
+// workspace of the tensor-core contraction of M A rows against Ns R_N W rows:
+// A slices, W slices, row exponents of A and W, status word (each 256-aligned)
+struct TcLayout {
+  size_t a, b;  // slice elements of A and W (all 3 slices, 3 axes)
+  size_t off_b, off_ea, off_eb, off_status, total;
+};
+TcLayout tc_layout(const cpc_kernel* P, int M, int Ns) {
+  TcLayout L;
+  L.a = size_t(3) * 3 * M * P->n;
+  L.b = size_t(3) * 3 * size_t(Ns) * P->R_N * P->n;
+  L.off_b = align256(2 * L.a);
+  L.off_ea = L.off_b + align256(2 * L.b);
+  L.off_eb = L.off_ea + align256(4 * size_t(3) * M);
+  L.off_status = L.off_eb + align256(4 * size_t(3) * Ns * P->R_N);
+  L.total = L.off_status + 256;
+  return L;
 }
+}  // namespace
 
-// status (int) at the end of the tc workspace
+size_t tc_workspace(const cpc_kernel* P, int R_f) { return tc_layout(P, R_f, R_f).total; }
+size_t tc_rows_workspace(const cpc_kernel* P, int M, int Ns) { return tc_layout(P, M, Ns).total; }
+size_t tc_rows_groups(const cpc_kernel* P, int Ns) { return size_t((Ns + tc::BN - 1) / tc::BN) * P->R_N; }
+
+// status (int) of the tc workspace
 int* tc_status_ptr(const cpc_kernel* P, int R_f, void* ws) {
-  return reinterpret_cast<int*>(static_cast<unsigned char*>(ws) + tc_workspace(P, R_f) - 256);
+  return reinterpret_cast<int*>(static_cast<unsigned char*>(ws) + tc_layout(P, R_f, R_f).off_status);
+}
+int* tc_rows_status_ptr(const cpc_kernel* P, int M, int Ns, void* ws) {
+  return reinterpret_cast<int*>(static_cast<unsigned char*>(ws) + tc_layout(P, M, Ns).off_status);
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -458,29 +492,31 @@ static int encode_fn(EncodeTiledFn* out) {
 
 void tc_w_slices(const cpc_kernel* P, int R_f, void* ws, __nv_bfloat16** slices, long long* slice_stride,
                  int** expo) {
-  const size_t a = size_t(3) * 3 * R_f * P->n, b = size_t(3) * 3 * R_f * P->R_N * P->n;
+  const TcLayout L = tc_layout(P, R_f, R_f);
   unsigned char* w = static_cast<unsigned char*>(ws);
-  *slices = reinterpret_cast<__nv_bfloat16*>(w + align256(2 * a));
-  *slice_stride = (long long)(b / 3);
-  *expo = reinterpret_cast<int*>(w + align256(2 * a) + align256(2 * b) + align256(4 * size_t(3) * R_f));
+  *slices = reinterpret_cast<__nv_bfloat16*>(w + L.off_b);
+  *slice_stride = (long long)(L.b / 3);
+  *expo = reinterpret_cast<int*>(w + L.off_eb);
 }
 
-int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
-                 double* partial, void* ws, cudaStream_t s, bool w_sliced) {
+namespace {
+// slices (unless W is already sliced), tensor maps and the launch
+int launch_tc(const cpc_kernel* P, int M, int Ns, const double* U, const float* W, const double* c,
+              const double* c_col, double* G, double* partial, void* ws, cudaStream_t s, bool w_sliced,
+              int rows_mode) {
   const int n = P->n, R_N = P->R_N;
-  const size_t a = size_t(3) * 3 * R_f * n, b = size_t(3) * 3 * R_f * R_N * n;
+  const TcLayout L = tc_layout(P, M, Ns);
   unsigned char* w = static_cast<unsigned char*>(ws);
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(w);
-  __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(w + align256(2 * a));
-  int* eA = reinterpret_cast<int*>(w + align256(2 * a) + align256(2 * b));
-  int* eB = reinterpret_cast<int*>(w + align256(2 * a) + align256(2 * b) + align256(4 * size_t(3) * R_f));
-  int* status = tc_status_ptr(P, R_f, ws);
+  __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(w + L.off_b);
+  int* eA = reinterpret_cast<int*>(w + L.off_ea);
+  int* eB = reinterpret_cast<int*>(w + L.off_eb);
+  int* status = reinterpret_cast<int*>(w + L.off_status);
   CPC_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
-  const long long arows = 3LL * R_f, brows = 3LL * R_f * R_N;
-  int st0 = tc::launch_slice(U, arows, n, R_f, 1, As, a / 3, eA, s);
+  int st0 = tc::launch_slice(U, 3LL * M, n, M, 1, As, (long long)(L.a / 3), eA, s);
   if (st0) return st0;
   if (!w_sliced) {  // else the convolution already wrote them (convolve_from_spectra_sliced)
-    st0 = tc::launch_slice(W, brows, n, R_f, R_N, Bs, b / 3, eB, s);
+    st0 = tc::launch_slice(W, 3LL * Ns * R_N, n, Ns, R_N, Bs, (long long)(L.b / 3), eB, s);
     if (st0) return st0;
   }
 
@@ -491,32 +527,47 @@ int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, 
   const int T = n / tc::BKC;
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   {
-    // [slice 3][l 3][t T][r R_f][64 cells]
-    const cuuint64_t dims[5] = {64, (cuuint64_t)R_f, (cuuint64_t)T, 3, 3};
-    const cuuint64_t row = 128, strides[4] = {row, row * R_f, row * R_f * T, row * R_f * T * 3};
+    // [slice 3][l 3][t T][r M][64 cells]
+    const cuuint64_t dims[5] = {64, (cuuint64_t)M, (cuuint64_t)T, 3, 3};
+    const cuuint64_t row = 128, strides[4] = {row, row * M, row * M * T, row * M * T * 3};
     const cuuint32_t box[5] = {tc::BKC, tc::BM, 1, 1, 3};
     if (enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, As, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(CPC_ERR_CUDA, "tensor map for the U slices");
   }
   {
-    // [slice 3][l*R_N + q][t T][s R_f][64 cells]
-    const cuuint64_t dims[5] = {64, (cuuint64_t)R_f, (cuuint64_t)T, (cuuint64_t)3 * R_N, 3};
-    const cuuint64_t row = 128, strides[4] = {row, row * R_f, row * R_f * T, row * R_f * T * 3 * R_N};
+    // [slice 3][l*R_N + q][t T][s Ns][64 cells]
+    const cuuint64_t dims[5] = {64, (cuuint64_t)Ns, (cuuint64_t)T, (cuuint64_t)3 * R_N, 3};
+    const cuuint64_t row = 128, strides[4] = {row, row * Ns, row * Ns * T, row * Ns * T * 3 * R_N};
     const cuuint32_t box[5] = {tc::BKC, tc::BNH, 1, 1, 3};
     if (enc(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, Bs, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(CPC_ERR_CUDA, "tensor map for the V_H factor slices");
   }
-  const int n_rp = (R_f + 2 * tc::BM - 1) / (2 * tc::BM), n_ct = (R_f + tc::BN - 1) / tc::BN;
-  dim3 grid(2 * n_rp * n_ct, R_N);  // clusters of 2 along x
-  tc::Args args{eA, eB, R_f, R_N, n, c, partial, G, status};
+  const int n_rp = (M + 2 * tc::BM - 1) / (2 * tc::BM), n_ct = (Ns + tc::BN - 1) / tc::BN;
+  const long long gx = 2LL * n_rp * n_ct;
+  if (gx > 0x7fffffffLL || R_N > 65535) return fail(CPC_ERR_UNSUPPORTED, "tensor-core contraction: grid too large");
+  dim3 grid((unsigned)gx, R_N);  // clusters of 2 along x
+  tc::Args args{eA, eB, M, Ns, R_N, n, rows_mode, c, c_col, partial, G, status};
   CPC_CUDA(cudaFuncSetAttribute(tc::gemm3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc::kSmemBytes)));
   const int slot = timing_begin("gemm3_tc_kernel", s);
   tc::gemm3_tc_kernel<<<grid, tc::THREADS, tc::kSmemBytes, s>>>(mapA, mapB, args);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("gemm3_tc_kernel");
   return CPC_OK;
+}
+}  // namespace
+
+int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
+                 double* partial, void* ws, cudaStream_t s, bool w_sliced) {
+  return launch_tc(P, R_f, R_f, U, W, c, c, G, partial, ws, s, w_sliced, 0);
+}
+
+// Coulomb-matrix rows: rowpart[(q * n_ct + ct) * M + r] = sum over the 128
+// columns s of tile ct of c_s prod_l G_l[r][s, q] (M item factors, Ns = R_rho)
+int launch_rows_tc(const cpc_kernel* P, int M, const double* U_items, int Ns, const float* W_rho,
+                   const double* c_rho, double* rowpart, void* ws, cudaStream_t s) {
+  return launch_tc(P, M, Ns, U_items, W_rho, nullptr, c_rho, nullptr, rowpart, ws, s, false, 1);
 }
 
 }  // namespace cpc
