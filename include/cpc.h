@@ -275,14 +275,19 @@ int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* off, int n_
  * first), each in [0, n]; sub: device int32 [3][n_sub] in [0, n) (entries
  * outside are clamped), 1 <= n_sub <= 512.  R_N <= 129.
  * S: [3][R_N][n] float64.  V: n_sub^3 float64 (CPC_FP64) or float32
- * (CPC_FP32: float32 products with a float32 compensated sum). */
+ * (CPC_FP32: for R_N <= 64 on the tensor cores, the pair products S1 S2 and
+ * S3 rounded to float32, each row of them split exactly into four bf16
+ * integer slices under a per-row power of two, slice products summed exactly
+ * in TMEM and folded into float32 once per value; a device-side wait that
+ * gives up writes NaN; for R_N > 64 float32 products with a float32
+ * compensated sum). */
 int lattice_potential_sum(const cpc_kernel* master, const int* L, const int* edges, double* S,
                           int n_sub, const int* sub, void* V, int precision, void* stream);
 
 /* ---- status -------------------------------------------------------------- */
 /* ---- kernel timing (measurement support; the paper has no counterpart) -----
  * While enabled, every launch of spectra_kernel, conv_kernel,
- * slice_rows_kernel and gemm3_tc_kernel is bracketed by two CUDA events recorded on the stream the
+ * slice_rows_kernel, gemm3_tc_kernel and subgrid_tc_kernel is bracketed by two CUDA events recorded on the stream the
  * kernel is launched on (up to 8192 launches; later ones go unrecorded).
  * cpc_kernel_timing(1) creates the events on first use and clears earlier
  * records; cpc_kernel_timing(0) stops recording and keeps the records.

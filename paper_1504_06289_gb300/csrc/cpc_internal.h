@@ -40,6 +40,10 @@ struct cpc_kernel {
   float2* d_hw32 = nullptr;
   // CONV only: Parseval weights d_q[2f+j] = w_f phat_q[f] / (2n), float32, [R_N][2(n+1)]
   float* d_specw32 = nullptr;
+  // MASTER kernels: scratch of the tensor-core sub-grid evaluation (the bf16
+  // slices of the S3 rows, pre-swizzled per 64-point sub-tile, and their
+  // exponents); calls on unordered streams sharing one kernel race on it
+  unsigned char* d_lat = nullptr;
 };
 
 namespace cpc {
@@ -78,6 +82,7 @@ void build_twiddles(int n, std::vector<double>& tw_re, std::vector<double>& tw_i
 
 // device-side builders (spectra.cu)
 int build_pass_twiddles(cpc_kernel* P, cudaStream_t s);
+size_t lattice_scratch_bytes();
 int compute_kernel_spectrum(cpc_kernel* P, cudaStream_t s);
 
 // spectra of U columns into workspace (float64 and/or float32 copies)

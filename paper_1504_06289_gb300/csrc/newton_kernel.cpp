@@ -259,6 +259,10 @@ int make_newton_kernel(int n, double b, int M, int kind, void* stream, cpc_kerne
   cudaError_t e = cudaMalloc(&P->d_p, sizeof(double) * P->p.size());
   if (e == cudaSuccess) e = cudaMemcpyAsync(P->d_p, P->p.data(), sizeof(double) * P->p.size(), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: table upload"); cleanup(); return st; }
+  if (master) {
+    e = cudaMalloc(&P->d_lat, lattice_scratch_bytes());
+    if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: lattice scratch"); cleanup(); return st; }
+  }
   if (!master) {
     std::vector<double> twr, twi, hwr, hwi;
     build_twiddles(n, twr, twi, hwr, hwi);
@@ -327,6 +331,7 @@ int cpc_kernel_free(cpc_kernel* P) {
   cudaFree(P->d_hw64);
   cudaFree(P->d_hw32);
   cudaFree(P->d_specw32);
+  cudaFree(P->d_lat);
   delete P;
   return CPC_OK;
 }
