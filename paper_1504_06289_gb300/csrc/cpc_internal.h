@@ -36,6 +36,8 @@ struct cpc_kernel {
   float2* d_tw32 = nullptr;
   double2* d_twp64 = nullptr;  // per-pass twiddle tables of the FFT plans (fft.cuh)
   float2* d_twp32 = nullptr;
+  void* d_twp32_lo = nullptr;  // __half2: 2^24 (exact - float32) of each float32 pass-table entry
+  void* d_hw32_lo = nullptr;   // the same for the half-angle table
   double2* d_hw64 = nullptr;
   float2* d_hw32 = nullptr;
   // CONV only: Parseval weights d_q[2f+j] = w_f phat_q[f] / (2n), float32, [R_N][2(n+1)]

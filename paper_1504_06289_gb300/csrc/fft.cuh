@@ -9,6 +9,7 @@
 // passes do not collide in shared-memory banks.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace cpc {
@@ -55,22 +56,57 @@ __device__ __forceinline__ V root(int k) {
   return cmk<V>(T(c), T(SIGN * s));
 }
 
+// float32 transforms carry each rounded constant's error as a second term
+// (c = c_hi + c_lo): a handful of constants and table twiddles enter every
+// transform, so without the second term their rounding errors do not average
+// out and bias the result (about 1e-7 relative at n = 8192).
+
+// x * (c + i s) for c, s known in double; float32: compensated
+template <typename V>
+__device__ __forceinline__ V cmul_const(V x, double c, double s) {
+  using T = decltype(V::x);
+  if constexpr (sizeof(T) == 4) {
+    const float ch = float(c), sh = float(s);
+    const float cl = float(c - double(ch)), sl = float(s - double(sh));
+    const float re = fmaf(x.x, ch, fmaf(-x.y, sh, fmaf(x.x, cl, -x.y * sl)));
+    const float im = fmaf(x.x, sh, fmaf(x.y, ch, fmaf(x.x, sl, x.y * cl)));
+    return cmk<V>(re, im);
+  } else {
+    return cmul(x, cmk<V>(T(c), T(s)));
+  }
+}
+
+// a / sqrt2 (float32: compensated)
+template <typename T>
+__device__ __forceinline__ T div_sqrt2(T a) {
+  constexpr double r = 0.70710678118654752440;
+  if constexpr (sizeof(T) == 4) {
+    constexpr float rh = float(r), rl = float(r - double(float(r)));
+    return fmaf(a, rh, a * rl);
+  } else {
+    return T(r) * a;
+  }
+}
+
 // x * exp(SIGN 2 pi i k / R), with the trivial angles special-cased (k is a
 // compile-time constant after unrolling, so the branches fold away).
 template <typename V, int R, int SIGN>
 __device__ __forceinline__ V rotate(V x, int k) {
-  using T = decltype(V::x);
   if (k == 0) return x;
   if (4 * k == R) return mul_si<SIGN>(x);
   if (8 * k == R) {  // (1 + SIGN i)/sqrt2
-    const T r = T(0.70710678118654752440);
-    return SIGN > 0 ? cmk<V>(r * (x.x - x.y), r * (x.x + x.y)) : cmk<V>(r * (x.x + x.y), r * (x.y - x.x));
+    return SIGN > 0 ? cmk<V>(div_sqrt2(x.x - x.y), div_sqrt2(x.x + x.y))
+                    : cmk<V>(div_sqrt2(x.x + x.y), div_sqrt2(x.y - x.x));
   }
   if (8 * k == 3 * R) {  // (-1 + SIGN i)/sqrt2
-    const T r = T(0.70710678118654752440);
-    return SIGN > 0 ? cmk<V>(-r * (x.x + x.y), r * (x.x - x.y)) : cmk<V>(r * (x.y - x.x), -r * (x.x + x.y));
+    return SIGN > 0 ? cmk<V>(-div_sqrt2(x.x + x.y), div_sqrt2(x.x - x.y))
+                    : cmk<V>(div_sqrt2(x.y - x.x), -div_sqrt2(x.x + x.y));
   }
-  return cmul(x, root<V, R, SIGN>(k));
+  const int j = k * (32 / R);  // angle 2 pi j / 32, j in [0, 16)
+  double c, s;
+  if (j <= 8) { c = c32(j); s = c32(8 - j); }          // [0, pi/2]
+  else { c = -c32(16 - j); s = c32(j - 8); }            // (pi/2, pi)
+  return cmul_const(x, c, SIGN * s);
 }
 
 // In-register DFT of size R (power of two, R <= 32), unnormalised,
@@ -111,11 +147,21 @@ struct FftPlan {
 };
 
 // Twiddle: x * w^e for w = exp(-2 pi i / NC) (SIGN < 0) or its conjugate;
-// `k` indexes the pass table (below), which holds w^e.
+// `k` indexes the pass table (below), which holds w^e.  float32 tables come
+// with a second table of the rounding errors, 2^24 (w^e - fl(w^e)) in fp16.
 template <int SIGN, typename V>
-__device__ __forceinline__ V twiddle(V x, const V* __restrict__ twp, int k) {
+__device__ __forceinline__ V twiddle(V x, const V* __restrict__ twp, const __half2* __restrict__ twl, int k) {
   V w = __ldg(twp + k);
-  return SIGN > 0 ? cmulc(x, w) : cmul(x, w);
+  if constexpr (sizeof(decltype(V::x)) == 4) {
+    const float2 l = __half22float2(__ldg(twl + k));
+    const float lx = l.x * (1.0f / 16777216.0f), ly = (SIGN > 0 ? -l.y : l.y) * (1.0f / 16777216.0f);
+    const float wy = SIGN > 0 ? -w.y : w.y;
+    const float re = fmaf(x.x, w.x, fmaf(-x.y, wy, fmaf(x.x, lx, -x.y * ly)));
+    const float im = fmaf(x.x, wy, fmaf(x.y, w.x, fmaf(x.x, ly, x.y * lx)));
+    return cmk<V>(re, im);
+  } else {
+    return SIGN > 0 ? cmulc(x, w) : cmul(x, w);
+  }
 }
 
 // Pass tables.  Pass p >= 1 of a plan (Ns = R1 P^(p-1) butterfly groups,
@@ -157,7 +203,7 @@ __host__ __device__ inline int pass_table_exponent(int k) {
 // twp: this pass's table (unused when Ns == 1).
 template <int NC, int R, int B, int SIGN, typename V>
 __device__ __forceinline__ void pass_compute(const V* sbuf, V (&v)[B][R], int t, int Ns,
-                                             const V* __restrict__ twp) {
+                                             const V* __restrict__ twp, const __half2* __restrict__ twl) {
   constexpr int stride = NC / R;
   constexpr int nbf = NC / (R * B);
 #pragma unroll
@@ -168,7 +214,7 @@ __device__ __forceinline__ void pass_compute(const V* sbuf, V (&v)[B][R], int t,
     if (Ns > 1) {
       const int m = j & (Ns - 1);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[b][r] = twiddle<SIGN>(v[b][r], twp, (r - 1) * Ns + m);
+      for (int r = 1; r < R; ++r) v[b][r] = twiddle<SIGN>(v[b][r], twp, twl, (r - 1) * Ns + m);
     }
     dft<R, SIGN>(v[b]);
   }
@@ -189,20 +235,24 @@ __device__ __forceinline__ void pass_store(V* sbuf, const V (&v)[B][R], int t, i
 
 // Middle passes 2..NP-1 (radix P, one butterfly per thread): smem -> smem.
 // Enter with the first pass stored; leave with pass NP-1 stored and synced.
-// tw: the plan's pass tables; the last pass uses tw + pass_table_offset(NP-1).
+// tw (twl): the plan's pass tables (float32: and their error tables); the
+// last pass uses tw + pass_table_offset(NP-1).
 template <int LOGN, int LOGP, int SIGN, typename V>
-__device__ __forceinline__ void middle_passes(V* sbuf, int t, const V* __restrict__ tw) {
+__device__ __forceinline__ void middle_passes(V* sbuf, int t, const V* __restrict__ tw,
+                                              const __half2* __restrict__ twl) {
   using PL = FftPlan<LOGN, LOGP>;
   int Ns = PL::R1;
   const V* twp = tw;
+  const __half2* twlp = twl;
 #pragma unroll 1
   for (int p = 1; p < PL::NP - 1; ++p) {
     V v[1][PL::P];
-    pass_compute<PL::NC, PL::P, 1, SIGN>(sbuf, v, t, Ns, twp);
+    pass_compute<PL::NC, PL::P, 1, SIGN>(sbuf, v, t, Ns, twp, twlp);
     __syncthreads();
     pass_store<PL::NC, PL::P, 1>(sbuf, v, t, Ns);
     __syncthreads();
     twp += (PL::P - 1) * Ns;
+    twlp += (PL::P - 1) * Ns;
     Ns *= PL::P;
   }
 }

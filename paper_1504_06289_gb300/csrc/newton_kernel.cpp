@@ -282,6 +282,8 @@ int make_newton_kernel(int n, double b, int M, int kind, void* stream, cpc_kerne
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->d_hw32, hw32.data(), sizeof(float2) * (n + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMalloc(&P->d_twp64, sizeof(double2) * n);
     if (e == cudaSuccess) e = cudaMalloc(&P->d_twp32, sizeof(float2) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_twp32_lo, 4 * size_t(n));
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_hw32_lo, 4 * size_t(n + 1));
     if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: FFT tables"); cleanup(); return st; }
     st = build_pass_twiddles(P, s);
     if (st != CPC_OK) { cleanup(); return st; }
@@ -328,6 +330,8 @@ int cpc_kernel_free(cpc_kernel* P) {
   cudaFree(P->d_tw32);
   cudaFree(P->d_twp64);
   cudaFree(P->d_twp32);
+  cudaFree(P->d_twp32_lo);
+  cudaFree(P->d_hw32_lo);
   cudaFree(P->d_hw64);
   cudaFree(P->d_hw32);
   cudaFree(P->d_specw32);

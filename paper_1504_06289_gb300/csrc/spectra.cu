@@ -15,6 +15,7 @@
 //                    holds `slots` transforms in shared memory and walks the
 //                    items in a grid-stride loop.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -88,10 +89,11 @@ spectra_kernel(int mode, const double* __restrict__ src, int ncols, double2* __r
       pass_store<NC, PL::R1, PL::B1>(sbuf, v, t, 1);
     }
     __syncthreads();
-    middle_passes<LOGN, G::LOGP, -1>(sbuf, t, tw);
+    middle_passes<LOGN, G::LOGP, -1>(sbuf, t, tw, nullptr);
     {
       double2 v[1][PL::P];
-      pass_compute<NC, PL::P, 1, -1>(sbuf, v, t, NC / PL::P, tw + pass_table_offset<LOGN, G::LOGP>(PL::NP - 1));
+      pass_compute<NC, PL::P, 1, -1>(sbuf, v, t, NC / PL::P, tw + pass_table_offset<LOGN, G::LOGP>(PL::NP - 1),
+                                     nullptr);
       __syncthreads();
       pass_store<NC, PL::P, 1>(sbuf, v, t, NC / PL::P);
     }
@@ -191,6 +193,7 @@ template <typename T, int LOGN, bool SLICE>
 __global__ void __launch_bounds__(Geometry<LOGN, T>::threads, Geometry<LOGN, T>::min_blocks)
 conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict__ phat,
             const typename cvec<T>::type* __restrict__ hw, const typename cvec<T>::type* __restrict__ tw,
+            const __half2* __restrict__ hwl, const __half2* __restrict__ twl,
             T* __restrict__ W, int R_N, long long n_items, SliceOut so) {
   using V = typename cvec<T>::type;
   using G = Geometry<LOGN, T>;
@@ -229,7 +232,7 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
           const V A = cmk<V>(uf.x * pf, uf.y * pf);
           const V B = cmk<V>(ur.x * pr, -ur.y * pr);
           const V s = cadd(A, B), d = csub(A, B);
-          const V wd = cmulc(d, __ldg(hw + f));  // e^{+i theta} (A - B)
+          const V wd = twiddle<+1>(d, hw, hwl, f);  // e^{+i theta} (A - B)
           v[b][r] = cmk<V>(s.x - wd.y, s.y + wd.x);
         }
         dft<PL::R1, +1>(v[b]);
@@ -237,10 +240,11 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
       pass_store<NC, PL::R1, PL::B1>(sbuf, v, t, 1);
     }
     __syncthreads();
-    middle_passes<LOGN, G::LOGP, +1>(sbuf, t, tw);
+    middle_passes<LOGN, G::LOGP, +1>(sbuf, t, tw, twl);
     {
       V v[1][PL::P];
-      pass_compute<NC, PL::P, 1, +1>(sbuf, v, t, NC / PL::P, tw + pass_table_offset<LOGN, G::LOGP>(PL::NP - 1));
+      pass_compute<NC, PL::P, 1, +1>(sbuf, v, t, NC / PL::P, tw + pass_table_offset<LOGN, G::LOGP>(PL::NP - 1),
+                                     twl ? twl + pass_table_offset<LOGN, G::LOGP>(PL::NP - 1) : nullptr);
 #pragma unroll
       for (int r = 0; r < PL::P / 2; ++r) v[0][r] = cmk<V>(v[0][r].x * scale, v[0][r].y * scale);
       if (active) {
@@ -311,13 +315,17 @@ int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const
   const T* phat;
   const V* hw;
   const V* tw;
+  const __half2* hwl = nullptr;
+  const __half2* twl = nullptr;
   if constexpr (sizeof(T) == 8) {
     phat = P->d_phat64; hw = P->d_hw64; tw = P->d_twp64;
   } else {
     phat = P->d_phat32; hw = P->d_hw32; tw = P->d_twp32;
+    hwl = static_cast<const __half2*>(P->d_hw32_lo);
+    twl = static_cast<const __half2*>(P->d_twp32_lo);
   }
   const int slot = timing_begin("conv_kernel", s);
-  kern<<<int(grid), G::threads, smem, s>>>(static_cast<const V*>(Uhat), phat, hw, tw,
+  kern<<<int(grid), G::threads, smem, s>>>(static_cast<const V*>(Uhat), phat, hw, tw, hwl, twl,
                                            static_cast<T*>(W), P->R_N, n_items, so);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("conv_kernel");
@@ -353,10 +361,25 @@ int dispatch_conv(int logn, const cpc_kernel* P, int ncols, const void* Uhat, vo
 }  // namespace
 
 template <int LOGN, int LOGP, typename V>
-__global__ void pass_table_kernel(const V* __restrict__ flat, V* __restrict__ out) {
+__global__ void pass_table_kernel(const V* __restrict__ flat, V* __restrict__ out,
+                                  const double2* __restrict__ flat64, __half2* __restrict__ err) {
   constexpr int N = pass_table_size<LOGN, LOGP>();
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x)
-    out[k] = flat[pass_table_exponent<LOGN, LOGP>(k)];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < N; k += gridDim.x * blockDim.x) {
+    const int e = pass_table_exponent<LOGN, LOGP>(k);
+    out[k] = flat[e];
+    if (err) {  // 2^24 (exact - float32) of each entry
+      const double2 w = flat64[e];
+      err[k] = __floats2half2_rn(float((w.x - double(flat[e].x)) * 16777216.0),
+                                 float((w.y - double(flat[e].y)) * 16777216.0));
+    }
+  }
+}
+
+__global__ void error_table_kernel(const double2* __restrict__ w64, const float2* __restrict__ w32, int count,
+                                   __half2* __restrict__ err) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x)
+    err[k] = __floats2half2_rn(float((w64[k].x - double(w32[k].x)) * 16777216.0),
+                               float((w64[k].y - double(w32[k].y)) * 16777216.0));
 }
 
 template <int LOGN>
@@ -364,8 +387,10 @@ int launch_pass_tables(cpc_kernel* P, cudaStream_t s) {
   constexpr int L64 = Geometry<LOGN, double>::LOGP, L32 = Geometry<LOGN, float>::LOGP;
   static_assert(pass_table_size<LOGN, L64>() <= (1 << LOGN) && pass_table_size<LOGN, L32>() <= (1 << LOGN),
                 "pass tables fit in n entries");
-  pass_table_kernel<LOGN, L64><<<8, 256, 0, s>>>(P->d_tw64, P->d_twp64);
-  pass_table_kernel<LOGN, L32><<<8, 256, 0, s>>>(P->d_tw32, P->d_twp32);
+  pass_table_kernel<LOGN, L64><<<8, 256, 0, s>>>(P->d_tw64, P->d_twp64, nullptr, nullptr);
+  pass_table_kernel<LOGN, L32><<<8, 256, 0, s>>>(P->d_tw32, P->d_twp32, P->d_tw64,
+                                                 static_cast<__half2*>(P->d_twp32_lo));
+  error_table_kernel<<<8, 256, 0, s>>>(P->d_hw64, P->d_hw32, P->n + 1, static_cast<__half2*>(P->d_hw32_lo));
   CPC_LAUNCH_CHECK("pass_table_kernel");
   return CPC_OK;
 }
