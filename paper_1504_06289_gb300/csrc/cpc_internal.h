@@ -38,6 +38,7 @@ struct cpc_kernel {
   float2* d_twp32 = nullptr;
   void* d_twp32_lo = nullptr;  // __half2: 2^24 (exact - float32) of each float32 pass-table entry
   void* d_hw32_lo = nullptr;   // the same for the half-angle table
+  void* d_pp32 = nullptr;      // float2 [R_N][n]: kernel-term pairs (p^[f], p^[n-f])
   double2* d_hw64 = nullptr;
   float2* d_hw32 = nullptr;
   // CONV only: Parseval weights d_q[2f+j] = w_f phat_q[f] / (2n), float32, [R_N][2(n+1)]
@@ -93,10 +94,15 @@ int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uh
 // batched convolution from spectra
 int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W,
                           int precision, cudaStream_t s);
-// float32 convolution that also writes the tensor-core contraction's W slices
-// and row exponents (same values as slicing W afterwards); n >= 128
-int convolve_from_spectra_sliced(const cpc_kernel* P, int R_f, const float2* Uhat32, float* W,
-                                 __nv_bfloat16* slices, long long slice_stride, int* expo, cudaStream_t s);
+// float32 convolution operands (X1, X2) from float64 transforms of U, and the
+// convolutions from them (also writing the tensor-core contraction's W
+// slices and row exponents, n >= 128, in the _sliced form)
+int forward_operands32(const cpc_kernel* P, int ncols, const double* U, void* X, cudaStream_t s);
+size_t operands32_bytes(const cpc_kernel* P, int ncols);
+int convolve_operands32(const cpc_kernel* P, int ncols, const void* X, float* W, cudaStream_t s);
+int convolve_operands32_sliced(const cpc_kernel* P, int R_f, const void* X, float* W, __nv_bfloat16* slices,
+                               long long slice_stride, int* expo, cudaStream_t s);
+int build_kernel_pairs(cpc_kernel* P, cudaStream_t s);
 
 // float32 contractions (gram32.cu)
 size_t eh32_partials(int R_f, int R_N);

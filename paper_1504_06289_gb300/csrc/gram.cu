@@ -383,17 +383,15 @@ int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doub
   if (precision == CPC_FP32 && tc_supported(P)) {
     // the convolution writes W and, in the same pass, the W slices of the
     // tensor-core contraction (no second pass over W)
-    unsigned char* w = static_cast<unsigned char*>(ws);
-    double2* h64 = reinterpret_cast<double2*>(w);
-    float2* h32 = reinterpret_cast<float2*>(w + spectra_bytes(P, 3 * R_f, CPC_FP64));
-    int st = forward_spectra(P, 3 * R_f, U, h64, h32, s);
+    void* X = ws;  // float32 convolution operands, in the float64-spectra part of the workspace
+    int st = forward_operands32(P, 3 * R_f, U, X, s);
     if (st) return st;
     void* tws = static_cast<unsigned char*>(cws) + align256(sizeof(double) * eh_partials(P, R_f));
     __nv_bfloat16* sl;
     long long sl_stride;
     int* ex;
     tc_w_slices(P, R_f, tws, &sl, &sl_stride, &ex);
-    st = convolve_from_spectra_sliced(P, R_f, h32, static_cast<float*>(W), sl, sl_stride, ex, s);
+    st = convolve_operands32_sliced(P, R_f, X, static_cast<float*>(W), sl, sl_stride, ex, s);
     if (st) return st;
     double* partial = static_cast<double*>(cws);
     st = launch_eh_tc(P, R_f, U, static_cast<const float*>(W), c, G, partial, tws, s, true);

@@ -284,10 +284,13 @@ int make_newton_kernel(int n, double b, int M, int kind, void* stream, cpc_kerne
     if (e == cudaSuccess) e = cudaMalloc(&P->d_twp32, sizeof(float2) * n);
     if (e == cudaSuccess) e = cudaMalloc(&P->d_twp32_lo, 4 * size_t(n));
     if (e == cudaSuccess) e = cudaMalloc(&P->d_hw32_lo, 4 * size_t(n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_pp32, sizeof(float2) * size_t(P->R_N) * n);
     if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: FFT tables"); cleanup(); return st; }
     st = build_pass_twiddles(P, s);
     if (st != CPC_OK) { cleanup(); return st; }
     st = compute_kernel_spectrum(P, s);
+    if (st != CPC_OK) { cleanup(); return st; }
+    st = build_kernel_pairs(P, s);
     if (st != CPC_OK) { cleanup(); return st; }
     e = cudaMalloc(&P->d_specw32, sizeof(float) * size_t(P->R_N) * 2 * (n + 1));
     if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: spectral weights"); cleanup(); return st; }
@@ -332,6 +335,7 @@ int cpc_kernel_free(cpc_kernel* P) {
   cudaFree(P->d_twp32);
   cudaFree(P->d_twp32_lo);
   cudaFree(P->d_hw32_lo);
+  cudaFree(P->d_pp32);
   cudaFree(P->d_hw64);
   cudaFree(P->d_hw32);
   cudaFree(P->d_specw32);

@@ -47,12 +47,16 @@ struct Geometry {
 
 // ---------------------------------------------------------------------------
 // forward spectra (float64).  mode 0: factor columns (zero padded to 2n);
-// mode 1: even kernel vectors p[0..n-1] extended to the 2n circle.
+// mode 1: even kernel vectors p[0..n-1] extended to the 2n circle;
+// mode 2: factor columns, written as the float32 convolution operands
+//   X1[f] = U^[f] (1 + i e^{i theta_f}),  X2[f] = conj(U^[n-f]) (1 - i e^{i theta_f}),
+//   theta_f = pi f / n, f = 0..n-1 (out4[col][f] = (X1, X2)), so that the
+//   convolution's packed spectrum is Z[f] = p^[f] X1[f] + p^[n-f] X2[f].
 template <int LOGN>
 __global__ void __launch_bounds__(Geometry<LOGN>::threads)
 spectra_kernel(int mode, const double* __restrict__ src, int ncols, double2* __restrict__ out64,
                float2* __restrict__ out32, double* __restrict__ re64, float* __restrict__ re32,
-               const double2* __restrict__ hw, const double2* __restrict__ tw) {
+               const double2* __restrict__ hw, const double2* __restrict__ tw, float4* __restrict__ out4) {
   using G = Geometry<LOGN>;
   using PL = typename G::PL;
   constexpr int NC = PL::NC;
@@ -74,7 +78,7 @@ spectra_kernel(int mode, const double* __restrict__ src, int ncols, double2* __r
         for (int r = 0; r < PL::R1; ++r) {
           const int f = j + r * stride;  // packed pair (x[2f], x[2f+1])
           double2 z;
-          if (mode == 0) {
+          if (mode != 1) {
             z = (2 * f < NC) ? *reinterpret_cast<const double2*>(x + 2 * f) : make_double2(0.0, 0.0);
           } else {
             const int m0 = 2 * f, m1 = 2 * f + 1;
@@ -98,8 +102,29 @@ spectra_kernel(int mode, const double* __restrict__ src, int ncols, double2* __r
       pass_store<NC, PL::P, 1>(sbuf, v, t, NC / PL::P);
     }
     __syncthreads();
-    if (active) {
-      // X[f] = (Z[f] + conj Z[n-f])/2 - (i/2) e^{-2 pi i f/2n} (Z[f] - conj Z[n-f]), f = 0..n
+    // X[f] = (Z[f] + conj Z[n-f])/2 - (i/2) e^{-2 pi i f/2n} (Z[f] - conj Z[n-f]), f = 0..n
+    auto bin = [&](int f) {
+      const double2 Zf = sbuf[pad_index(f & (NC - 1))];
+      const double2 Zr = cconj(sbuf[pad_index((NC - f) & (NC - 1))]);
+      const double2 s = cadd(Zf, Zr), d = csub(Zf, Zr);
+      const double2 wd = cmul(hw[f], d);  // e^{-i theta} (Z - conj Z')
+      return make_double2(0.5 * s.x + 0.5 * wd.y, 0.5 * s.y - 0.5 * wd.x);
+    };
+    if (active && mode == 2) {
+      // bins f and n-f give the operands at both f and n-f: one pair per step
+      auto operands = [&](int f, double2 Uf, double2 Un) {  // Un = U^[n-f]
+        const double2 E = cconj(hw[f]);             // e^{+i theta_f}
+        const double2 iE = make_double2(-E.y, E.x);  // i e^{+i theta_f}
+        const double2 X1 = cmul(Uf, make_double2(1.0 + iE.x, iE.y));
+        const double2 X2 = cmul(cconj(Un), make_double2(1.0 - iE.x, -iE.y));
+        out4[(size_t)col * NC + f] = make_float4(float(X1.x), float(X1.y), float(X2.x), float(X2.y));
+      };
+      for (int f = t; f <= NC / 2; f += PL::TPF) {
+        const double2 Uf = bin(f), Un = bin(NC - f);
+        operands(f, Uf, Un);
+        if (f > 0 && 2 * f < NC) operands(NC - f, Un, Uf);
+      }
+    } else if (active) {
       for (int f = t; f <= NC; f += PL::TPF) {
         const double2 Zf = sbuf[pad_index(f & (NC - 1))];
         const double2 Zr = cconj(sbuf[pad_index((NC - f) & (NC - 1))]);
@@ -189,7 +214,11 @@ __device__ __forceinline__ void slice_epilogue(const float2* v, const SliceOut& 
 
 // ---------------------------------------------------------------------------
 // batched convolution: item = col * R_N + q writes W[item][0..n-1].
-template <typename T, int LOGN, bool SLICE>
+// XIN: the factor spectra come as the float32 operands (X1, X2) of
+// spectra_kernel mode 2 (`Uhat` points at float4 [cols][n]) and `phat` at
+// the kernel-term pairs (p^[f], p^[n-f]) as float2 [R_N][n]; the packed
+// spectrum is then Z[f] = p^[f] X1[f] + p^[n-f] X2[f] (no half-angle step).
+template <typename T, int LOGN, bool SLICE, bool XIN = false>
 __global__ void __launch_bounds__(Geometry<LOGN, T>::threads, Geometry<LOGN, T>::min_blocks)
 conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict__ phat,
             const typename cvec<T>::type* __restrict__ hw, const typename cvec<T>::type* __restrict__ tw,
@@ -227,6 +256,12 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
 #pragma unroll
         for (int r = 0; r < PL::R1; ++r) {
           const int f = j + r * stride;
+          if constexpr (XIN) {
+            const float4 x = __ldg(reinterpret_cast<const float4*>(Uhat) + (size_t)col * NC + f);
+            const float2 pp = __ldg(reinterpret_cast<const float2*>(phat) + (size_t)q * NC + f);
+            v[b][r] = cmk<V>(fmaf(pp.x, x.x, pp.y * x.z), fmaf(pp.x, x.y, pp.y * x.w));
+            continue;
+          }
           const V uf = __ldg(Uc + f), ur = __ldg(Uc + (NC - f));
           const T pf = __ldg(pq + f), pr = __ldg(pq + (NC - f));
           const V A = cmk<V>(uf.x * pf, uf.y * pf);
@@ -282,7 +317,7 @@ int sm_count() {
 
 template <int LOGN>
 int launch_spectra(int mode, const double* src, int ncols, double2* o64, float2* o32, double* r64,
-                   float* r32, const cpc_kernel* P, cudaStream_t s) {
+                   float* r32, const cpc_kernel* P, cudaStream_t s, float4* o4 = nullptr) {
   using G = Geometry<LOGN>;
   const size_t smem = sizeof(double2) * G::slots * padded_len(1 << LOGN);
   auto kern = spectra_kernel<LOGN>;
@@ -293,18 +328,18 @@ int launch_spectra(int mode, const double* src, int ncols, double2* o64, float2*
   const int groups = (ncols + G::slots - 1) / G::slots;
   const int grid = std::max(1, std::min(groups, std::max(1, per_sm) * sm_count()));
   const int slot = timing_begin("spectra_kernel", s);
-  kern<<<grid, G::threads, smem, s>>>(mode, src, ncols, o64, o32, r64, r32, P->d_hw64, P->d_twp64);
+  kern<<<grid, G::threads, smem, s>>>(mode, src, ncols, o64, o32, r64, r32, P->d_hw64, P->d_twp64, o4);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("spectra_kernel");
   return CPC_OK;
 }
 
-template <typename T, int LOGN, bool SLICE>
+template <typename T, int LOGN, bool SLICE, bool XIN>
 int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const SliceOut& so, cudaStream_t s) {
   using G = Geometry<LOGN, T>;
   using V = typename cvec<T>::type;
   const size_t smem = sizeof(V) * G::slots * padded_len(1 << LOGN);
-  auto kern = conv_kernel<T, LOGN, SLICE>;
+  auto kern = conv_kernel<T, LOGN, SLICE, XIN>;
   int st = configure(kern, smem);
   if (st) return st;
   int per_sm = 0;
@@ -320,7 +355,8 @@ int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const
   if constexpr (sizeof(T) == 8) {
     phat = P->d_phat64; hw = P->d_hw64; tw = P->d_twp64;
   } else {
-    phat = P->d_phat32; hw = P->d_hw32; tw = P->d_twp32;
+    phat = XIN ? reinterpret_cast<const T*>(P->d_pp32) : P->d_phat32;
+    hw = P->d_hw32; tw = P->d_twp32;
     hwl = static_cast<const __half2*>(P->d_hw32_lo);
     twl = static_cast<const __half2*>(P->d_twp32_lo);
   }
@@ -334,16 +370,26 @@ int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const
 
 template <int LOGN>
 int dispatch_spectra(int logn, int mode, const double* src, int ncols, double2* o64, float2* o32,
-                     double* r64, float* r32, const cpc_kernel* P, cudaStream_t s) {
+                     double* r64, float* r32, const cpc_kernel* P, cudaStream_t s, float4* o4 = nullptr) {
   if constexpr (LOGN > kMaxLogN) {
     return fail(CPC_ERR_UNSUPPORTED, "spectra: n too large");
   } else {
-    if (logn == LOGN) return launch_spectra<LOGN>(mode, src, ncols, o64, o32, r64, r32, P, s);
-    return dispatch_spectra<LOGN + 1>(logn, mode, src, ncols, o64, o32, r64, r32, P, s);
+    if (logn == LOGN) return launch_spectra<LOGN>(mode, src, ncols, o64, o32, r64, r32, P, s, o4);
+    return dispatch_spectra<LOGN + 1>(logn, mode, src, ncols, o64, o32, r64, r32, P, s, o4);
   }
 }
 
-template <typename T, int LOGN, bool SLICE>
+// kernel-term pairs (p^[f], p^[n-f]), f = 0..n-1, float32 [R_N][n]
+__global__ void kernel_pairs_kernel(const double* __restrict__ phat64, int R_N, int n, float2* __restrict__ pp) {
+  const long long total = (long long)R_N * n;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total; k += (long long)gridDim.x * blockDim.x) {
+    const int q = int(k / n), f = int(k % n);
+    const double* ph = phat64 + (size_t)q * (n + 1);
+    pp[k] = make_float2(float(ph[f]), float(ph[n - f]));
+  }
+}
+
+template <typename T, int LOGN, bool SLICE, bool XIN = false>
 int dispatch_conv(int logn, const cpc_kernel* P, int ncols, const void* Uhat, void* W, const SliceOut& so,
                   cudaStream_t s) {
   if constexpr (LOGN > kMaxLogN) {
@@ -352,9 +398,9 @@ int dispatch_conv(int logn, const cpc_kernel* P, int ncols, const void* Uhat, vo
     if constexpr (SLICE && LOGN < 7) {
       if (logn == LOGN) return fail(CPC_ERR_UNSUPPORTED, "sliced conv: n must be at least 128");
     } else {
-      if (logn == LOGN) return launch_conv<T, LOGN, SLICE>(P, ncols, Uhat, W, so, s);
+      if (logn == LOGN) return launch_conv<T, LOGN, SLICE, XIN>(P, ncols, Uhat, W, so, s);
     }
-    return dispatch_conv<T, LOGN + 1, SLICE>(logn, P, ncols, Uhat, W, so, s);
+    return dispatch_conv<T, LOGN + 1, SLICE, XIN>(logn, P, ncols, Uhat, W, so, s);
   }
 }
 
@@ -421,6 +467,19 @@ int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uh
   return dispatch_spectra<kMinLogN>(ilog2(P->n), 0, U, ncols, Uhat64, Uhat32, nullptr, nullptr, P, s);
 }
 
+int forward_operands32(const cpc_kernel* P, int ncols, const double* U, void* X, cudaStream_t s) {
+  return dispatch_spectra<kMinLogN>(ilog2(P->n), 2, U, ncols, nullptr, nullptr, nullptr, nullptr, P, s,
+                                    static_cast<float4*>(X));
+}
+
+size_t operands32_bytes(const cpc_kernel* P, int ncols) { return align256(size_t(ncols) * P->n * sizeof(float4)); }
+
+int build_kernel_pairs(cpc_kernel* P, cudaStream_t s) {
+  kernel_pairs_kernel<<<64, 256, 0, s>>>(P->d_phat64, P->R_N, P->n, static_cast<float2*>(P->d_pp32));
+  CPC_LAUNCH_CHECK("kernel_pairs_kernel");
+  return CPC_OK;
+}
+
 int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W, int precision,
                           cudaStream_t s) {
   const SliceOut none{nullptr, 0, nullptr, 0};
@@ -429,10 +488,15 @@ int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void
   return dispatch_conv<float, kMinLogN, false>(ilog2(P->n), P, ncols, Uhat, W, none, s);
 }
 
-int convolve_from_spectra_sliced(const cpc_kernel* P, int R_f, const float2* Uhat32, float* W,
-                                 __nv_bfloat16* slices, long long slice_stride, int* expo, cudaStream_t s) {
+int convolve_operands32(const cpc_kernel* P, int ncols, const void* X, float* W, cudaStream_t s) {
+  const SliceOut none{nullptr, 0, nullptr, 0};
+  return dispatch_conv<float, kMinLogN, false, true>(ilog2(P->n), P, ncols, X, W, none, s);
+}
+
+int convolve_operands32_sliced(const cpc_kernel* P, int R_f, const void* X, float* W, __nv_bfloat16* slices,
+                               long long slice_stride, int* expo, cudaStream_t s) {
   const SliceOut so{slices, slice_stride, expo, R_f};
-  return dispatch_conv<float, kMinLogN, true>(ilog2(P->n), P, 3 * R_f, Uhat32, W, so, s);
+  return dispatch_conv<float, kMinLogN, true, true>(ilog2(P->n), P, 3 * R_f, X, W, so, s);
 }
 
 size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision) {
@@ -483,10 +547,11 @@ int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int pre
     if (st) return st;
     return convolve_from_spectra(P, ncols, h64, W, precision, s);
   }
-  float2* h32 = reinterpret_cast<float2*>(w + spectra_bytes(P, ncols, CPC_FP64));
-  st = forward_spectra(P, ncols, U, h64, h32, s);
+  // float32: the convolution operands straight from the float64 transforms
+  // (they fit in the float64-spectra part of the workspace)
+  st = forward_operands32(P, ncols, U, h64, s);
   if (st) return st;
-  return convolve_from_spectra(P, ncols, h32, W, precision, s);
+  return convolve_operands32(P, ncols, h64, static_cast<float*>(W), s);
 }
 }  // namespace cpc
 
