@@ -70,7 +70,9 @@ def test_density600_n8192(cpc):
     E32, W32, _ = cpc.cp_hartree_energy(P, U, c, "fp32")
     cols32 = np.array([W32[l, k * R_N + q].double().cpu().numpy() for l, k, q in picks])
     assert col_rel_err(cols32, np.array(Wref)) < 2e-6
-    assert abs(E32.item() / E64.item() - 1) < 5e-7
+    # the stated bound of the float32 form (compensated float32 FFT, exact
+    # tensor-core contraction): 1e-7 relative on E_H
+    assert abs(E32.item() / E64.item() - 1) < 1e-7
     del W32
     torch.cuda.empty_cache()
     Es, Ws, _ = cpc.cp_hartree_energy(P, U, c, "split")
@@ -117,6 +119,7 @@ def test_density200_n4096_adjoint(cpc):
             assert abs(fd - ref) < 1e-6 * scale, (which, k, fd, ref)
     # float32 form of the adjoint
     E32, W32, G32 = cpc.cp_hartree_energy(P, U, c, "fp32", want_G=True)
+    assert abs(E32.item() / E.item() - 1) < 1e-7
     dU32, dc32 = cpc.cp_hartree_energy_adjoint(P, c, W32, G32, "fp32")
     assert rel(dU32.cpu().numpy(), dU0) < 1e-5
     assert rel(dc32.cpu().numpy(), dc0) < 1e-5
