@@ -588,18 +588,35 @@ def run_adjoint(args, ws, rank, local):
             E.backward()
             return E
         ms = _timed(stream, body, args.steps, args.warmup)
-        res[prec] = {"ms_per_step": ms, "E_H": body().item(), "grad_a_norm": float(a.grad.norm())}
+        torch.cuda.synchronize()
+        cpc.kernel_timing(True)
+        E_last = body().item()
+        torch.cuda.synchronize()
+        cpc.kernel_timing(False)
+        kms = {k: cpc.kernel_timing_read(k)[0] for k in ("spectra_kernel", "conv_kernel", "slice_rows_kernel",
+                                                           "gemm3_tc_kernel", "adjoint_gemm_kernel")}
+        res[prec] = {"ms_per_step": ms, "E_H": E_last, "grad_a_norm": float(a.grad.norm()), "kernel_ms": kms}
     for prec in ("fp32", "split"):
         res[prec]["rel_err_E_H_vs_fp64"] = abs(res[prec]["E_H"] / res["fp64"]["E_H"] - 1)
     if rank != 0:
         return
     head = args.precision if args.precision in res else "fp32"
     ms = res[head]["ms_per_step"]
+    # dominant kernel of the backward pass: dU^l = B^l W^l, 2 flop per multiply-add,
+    # 3 axes x R_f rows x (R_f R_N) x n; float32 CUDA-core peak from unit counts
+    adj_ms = res[head]["kernel_ms"].get("adjoint_gemm_kernel", 0.0)
+    adj_flops = 2.0 * 3 * R_f * R_f * P.R_N * n
+    peak = SMS * FP32_LANES * 2 * 2070.0 * 1e6 / 1e12
+    roof = ({"kernel": "adjoint_gemm_kernel", "bound": "alu", "kernel_ms": adj_ms,
+             "achieved": adj_flops / (adj_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+             "frac": adj_flops / (adj_ms * 1e-3) / 1e12 / peak, "traffic": None,
+             "peak_note": "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x 2070 MHz"}
+            if head == "fp32" and adj_ms > 0 else None)
     _line(args, ws, "E_H + gradient evaluations/s", ws / (ms * 1e-3), "evaluations/s", ms,
           {"fp32": "f32", "split": "f64/f32", "fp64": "f64"}[head],
           {"workload": name, "n": n, "R_f": R_f, "R_N": P.R_N,
            "parameters": "200 exponents, 600 centre coordinates, 200 coefficients"},
-          forms=res, speedup_vs_fp64_gpu=res["fp64"]["ms_per_step"] / ms)
+          forms=res, speedup_vs_fp64_gpu=res["fp64"]["ms_per_step"] / ms, roofline=roof)
 
 
 def run_lattice(args, ws, rank, local):

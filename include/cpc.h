@@ -287,7 +287,8 @@ int lattice_potential_sum(const cpc_kernel* master, const int* L, const int* edg
 /* ---- status -------------------------------------------------------------- */
 /* ---- kernel timing (measurement support; the paper has no counterpart) -----
  * While enabled, every launch of spectra_kernel, conv_kernel,
- * slice_rows_kernel, gemm3_tc_kernel and subgrid_tc_kernel is bracketed by two CUDA events recorded on the stream the
+ * slice_rows_kernel, gemm3_tc_kernel, subgrid_tc_kernel and
+ * adjoint_gemm_kernel is bracketed by two CUDA events recorded on the stream the
  * kernel is launched on (up to 8192 launches; later ones go unrecorded).
  * cpc_kernel_timing(1) creates the events on first use and clears earlier
  * records; cpc_kernel_timing(0) stops recording and keeps the records.

@@ -458,10 +458,12 @@ extern "C" int cp_hartree_energy_adjoint(const cpc_kernel* P, int R_f, const dou
   const int n = P->n;
   const double scale = 2.0 * P->h * P->h * P->h;
   dim3 grid((n + TN - 1) / TN, tiles(R_f), 3);
+  const int slot = timing_begin("adjoint_gemm_kernel", s);
   if (storage_precision(precision) == CPC_FP64)
     adjoint_gemm_kernel<double><<<grid, TPB, 0, s>>>(n, R_f, P->R_N, c, G, static_cast<const double*>(W), scale, dU);
   else
     adjoint_gemm_kernel<float><<<grid, TPB, 0, s>>>(n, R_f, P->R_N, c, G, static_cast<const float*>(W), scale, dU);
+  timing_end(slot, s);
   CPC_LAUNCH_CHECK("adjoint_gemm_kernel");
   if (dc) {
     adjoint_coef_kernel<<<R_f, 32, 0, s>>>(R_f, P->R_N, c, G, scale, dc);
