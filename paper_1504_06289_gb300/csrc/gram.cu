@@ -222,6 +222,119 @@ __global__ void item_reduce_kernel(int n_items, const int* __restrict__ off, con
   J[t] = (status && *status) ? __longlong_as_double(0x7ff8000000000000LL) : scale * s;
 }
 
+// float32 form of the adjoint GEMM.  The K sum runs q-major (kk = (q, k')),
+// so the A tile Bl[m][k'] for one q is read along k' (contiguous in G); A is
+// formed as float(G1 G2) times float32 coefficients cached in shared memory;
+// each K chunk of 32 is summed in float32 and folded into a float32 total
+// per output (compensated when COMP).  Tile TM m x TN i with RT x CT outputs
+// per thread (rows RT ty.., columns CT tx.., the W tile read as float4).
+namespace adj32 {
+constexpr int KC = 32, THREADS = 256;
+constexpr int TM = 40, TN = 128, RT = 5, CT = 4;  // 40 rows: R_f = 200 splits without a ragged tile
+constexpr bool COMP = true;
+constexpr int MAXRF = 1024;  // coefficients cached in shared memory
+static_assert((TM / RT) * (TN / CT) == THREADS, "thread tiling");
+__global__ void __launch_bounds__(THREADS)
+adjoint32_kernel(int n, int R_f, int R_N, const double* __restrict__ c, const double* __restrict__ G,
+                 const float* __restrict__ W, float scale2h3, double* __restrict__ dU) {
+  __shared__ float As[KC][TM + 1];  // written along kk (padded: no bank conflicts)
+  __shared__ __align__(16) float Bs[KC][TN];
+  __shared__ float cf[MAXRF];
+  const int l = blockIdx.z;
+  const int m0 = blockIdx.y * TM, i0 = blockIdx.x * TN;
+  const int tid = threadIdx.x;
+  constexpr int NTX = TN / CT;
+  const int tx = tid % NTX, ty = tid / NTX;
+  const int l1 = (l + 1) % 3, l2 = (l + 2) % 3;
+  const size_t GM = (size_t)R_f * R_f;
+  const float* Wl = W + (size_t)l * R_f * R_N * n;
+  for (int k = tid; k < R_f && k < MAXRF; k += THREADS) cf[k] = float(c[k]);
+  __syncthreads();
+  float tot[RT][CT], lo[RT][CT];
+#pragma unroll
+  for (int a = 0; a < RT; ++a)
+#pragma unroll
+    for (int b = 0; b < CT; ++b) { tot[a][b] = 0.0f; lo[a][b] = 0.0f; }
+  for (int q = 0; q < R_N; ++q) {
+    const double* G1 = G + ((size_t)l1 * R_N + q) * GM;
+    const double* G2 = G + ((size_t)l2 * R_N + q) * GM;
+    for (int kp0 = 0; kp0 < R_f; kp0 += KC) {
+      // A tile: As[kk][row] = 2 h^3 c_m c_k' G1[m][k'] G2[m][k'], k' = kp0 + kk (contiguous per row)
+      for (int idx = tid; idx < TM * KC; idx += THREADS) {
+        const int row = idx / KC, kk = idx % KC;
+        const int m = m0 + row, kp = kp0 + kk;
+        float v = 0.0f;
+        if (m < R_f && kp < R_f) {
+          const size_t gi = (size_t)m * R_f + kp;
+          v = (scale2h3 * cf[m] * cf[kp]) * float(G1[gi] * G2[gi]);
+        }
+        As[kk][row] = v;
+      }
+      // B tile: W rows k' R_N + q, columns i0.. (float4 per thread)
+      for (int idx = tid; idx < KC * TN / 4; idx += THREADS) {
+        const int kk = idx / (TN / 4), c4 = idx % (TN / 4);
+        const int kp = kp0 + kk, i = i0 + 4 * c4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kp < R_f) {
+          const float* row = Wl + ((size_t)kp * R_N + q) * n;
+          if (i + 3 < n) v = *reinterpret_cast<const float4*>(row + i);
+          else {
+            if (i < n) v.x = row[i];
+            if (i + 1 < n) v.y = row[i + 1];
+            if (i + 2 < n) v.z = row[i + 2];
+          }
+        }
+        *reinterpret_cast<float4*>(&Bs[kk][4 * c4]) = v;
+      }
+      __syncthreads();
+      float part[RT][CT];
+#pragma unroll
+      for (int a = 0; a < RT; ++a)
+#pragma unroll
+        for (int b = 0; b < CT; ++b) part[a][b] = 0.0f;
+#pragma unroll
+      for (int kk = 0; kk < KC; ++kk) {
+        float ar[RT], br[CT];
+#pragma unroll
+        for (int a = 0; a < RT; ++a) ar[a] = As[kk][RT * ty + a];
+#pragma unroll
+        for (int b = 0; b < CT; b += 4) {
+          const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][CT * tx + b]);
+          br[b] = bv.x; br[b + 1] = bv.y; br[b + 2] = bv.z; br[b + 3] = bv.w;
+        }
+#pragma unroll
+        for (int a = 0; a < RT; ++a)
+#pragma unroll
+          for (int b = 0; b < CT; ++b) part[a][b] = fmaf(ar[a], br[b], part[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < RT; ++a)
+#pragma unroll
+        for (int b = 0; b < CT; ++b) {
+          if constexpr (COMP) {
+            const float t = tot[a][b], v = part[a][b], sm = t + v, bb = sm - t;
+            lo[a][b] += (t - (sm - bb)) + (v - bb);
+            tot[a][b] = sm;
+          } else {
+            tot[a][b] += part[a][b];
+          }
+        }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < RT; ++a) {
+    const int m = m0 + RT * ty + a;
+    if (m >= R_f) continue;
+#pragma unroll
+    for (int b = 0; b < CT; ++b) {
+      const int i = i0 + CT * tx + b;
+      if (i < n) dU[((size_t)l * R_f + m) * n + i] = double(tot[a][b]) + double(lo[a][b]);
+    }
+  }
+}
+}  // namespace adj32
+
 // ---- adjoint --------------------------------------------------------------
 // dU[l][m][i] = sum_{kk} Bl[m][kk] W[l][kk][i],  kk = k'*R_N + q,
 // Bl[m][kk] = 2 h^3 c_m c_k' prod_{l' != l} G[l'][q][m][k'], formed while loading.
@@ -459,10 +572,13 @@ extern "C" int cp_hartree_energy_adjoint(const cpc_kernel* P, int R_f, const dou
   const double scale = 2.0 * P->h * P->h * P->h;
   dim3 grid((n + TN - 1) / TN, tiles(R_f), 3);
   const int slot = timing_begin("adjoint_gemm_kernel", s);
-  if (storage_precision(precision) == CPC_FP64)
+  if (storage_precision(precision) == CPC_FP64) {
     adjoint_gemm_kernel<double><<<grid, TPB, 0, s>>>(n, R_f, P->R_N, c, G, static_cast<const double*>(W), scale, dU);
-  else
-    adjoint_gemm_kernel<float><<<grid, TPB, 0, s>>>(n, R_f, P->R_N, c, G, static_cast<const float*>(W), scale, dU);
+  } else {
+    dim3 g32((n + adj32::TN - 1) / adj32::TN, (R_f + adj32::TM - 1) / adj32::TM, 3);
+    adj32::adjoint32_kernel<<<g32, adj32::THREADS, 0, s>>>(n, R_f, P->R_N, c, G, static_cast<const float*>(W),
+                                                          float(scale), dU);
+  }
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("adjoint_gemm_kernel");
   if (dc) {
