@@ -206,14 +206,38 @@ __device__ __forceinline__ void slice_epilogue(const float2* v, const SliceOut& 
       sl[2][h] = rintf((b - s1) * 256.0f);
     }
     __nv_bfloat16* o = ob + (long long)(i >> 6) * so.R_f * 64 + (i & 63);
+    // streaming stores (evict first): the outputs must not push the reused
+    // operand spectra out of L2
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-      *reinterpret_cast<__nv_bfloat162*>(o + k * so.slice_stride) = __floats2bfloat162_rn(sl[k][0], sl[k][1]);
+    for (int k = 0; k < 3; ++k) {
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(sl[k][0], sl[k][1]);
+      __stcs(reinterpret_cast<unsigned int*>(o + k * so.slice_stride), *reinterpret_cast<const unsigned int*>(&b2));
+    }
   }
 }
 
 // ---------------------------------------------------------------------------
 // batched convolution: item = col * R_N + q writes W[item][0..n-1].
+// loads that ask L2 to keep the line (the convolution operands are read once
+// per kernel term while the output stream passes through L2)
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ float4 ld_keep4(const float4* a, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;\n"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(a), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float2 ld_keep2(const float2* a, uint64_t pol) {
+  float2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;\n" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol));
+  return v;
+}
+
 // XIN: the factor spectra come as the float32 operands (X1, X2) of
 // spectra_kernel mode 2 (`Uhat` points at float4 [cols][n]) and `phat` at
 // the kernel-term pairs (p^[f], p^[n-f]) as float2 [R_N][n]; the packed
@@ -233,6 +257,7 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
   const int t = threadIdx.x % PL::TPF;
   V* sbuf = reinterpret_cast<V*>(smem_raw) + slot * padded_len(NC);
   const T scale = T(1) / T(2 * NC);
+  const uint64_t keep = l2_evict_last();  // operands are reused by the R_N kernel terms of a column
   // contiguous group range per CTA: consecutive items share a factor column,
   // so its spectrum stays in L1 across the kernel terms q
   const long long n_groups = (n_items + G::slots - 1) / G::slots;
@@ -257,8 +282,8 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
         for (int r = 0; r < PL::R1; ++r) {
           const int f = j + r * stride;
           if constexpr (XIN) {
-            const float4 x = __ldg(reinterpret_cast<const float4*>(Uhat) + (size_t)col * NC + f);
-            const float2 pp = __ldg(reinterpret_cast<const float2*>(phat) + (size_t)q * NC + f);
+            const float4 x = ld_keep4(reinterpret_cast<const float4*>(Uhat) + (size_t)col * NC + f, keep);
+            const float2 pp = ld_keep2(reinterpret_cast<const float2*>(phat) + (size_t)q * NC + f, keep);
             v[b][r] = cmk<V>(fmaf(pp.x, x.x, pp.y * x.z), fmaf(pp.x, x.y, pp.y * x.w));
             continue;
           }
@@ -287,7 +312,7 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
 #pragma unroll
         for (int r = 0; r < PL::P / 2; ++r) {
           const int o = t + r * (NC / PL::P);  // complex output o -> reals 2o, 2o+1
-          *reinterpret_cast<V*>(out + 2 * o) = v[0][r];
+          __stcs(reinterpret_cast<V*>(out + 2 * o), v[0][r]);  // streaming store (see slice_epilogue)
         }
       }
       if constexpr (SLICE) slice_epilogue<PL>(v[0], so, item, active, slot, t, R_N);
