@@ -147,6 +147,82 @@ spectra_kernel(int mode, const double* __restrict__ src, int ncols, double2* __r
   }
 }
 
+// Float32 forward transform for the float32 form's convolution operands
+// (the output of spectra_kernel mode 2), with the float32 plan and the
+// compensated constants and twiddles of fft.cuh; inputs rounded to float32
+// once; the operand factors (1 +- i e^{i theta}) formed in float64.
+template <int LOGN>
+__global__ void __launch_bounds__(Geometry<LOGN, float>::threads)
+spectra32_kernel(const double* __restrict__ src, int ncols, const float2* __restrict__ hw,
+                 const __half2* __restrict__ hwl, const double2* __restrict__ hw64, const float2* __restrict__ tw,
+                 const __half2* __restrict__ twl, float4* __restrict__ out4) {
+  using G = Geometry<LOGN, float>;
+  using PL = typename G::PL;
+  constexpr int NC = PL::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* sbuf = reinterpret_cast<float2*>(smem_raw) + (threadIdx.x / PL::TPF) * padded_len(NC);
+  const int slot = threadIdx.x / PL::TPF;
+  const int t = threadIdx.x % PL::TPF;
+  for (int g = blockIdx.x; g * G::slots < ncols; g += gridDim.x) {
+    const int col = g * G::slots + slot;
+    const bool active = col < ncols;
+    const double* x = src + (size_t)(active ? col : ncols - 1) * NC;
+    {
+      float2 v[PL::B1][PL::R1];
+      constexpr int stride = NC / PL::R1, nbf = NC / (PL::R1 * PL::B1);
+#pragma unroll
+      for (int b = 0; b < PL::B1; ++b) {
+        const int j = b * nbf + t;
+#pragma unroll
+        for (int r = 0; r < PL::R1; ++r) {
+          const int f = j + r * stride;  // packed pair (x[2f], x[2f+1]), zero beyond n
+          if (2 * f < NC) {
+            const double2 z = *reinterpret_cast<const double2*>(x + 2 * f);
+            v[b][r] = make_float2(float(z.x), float(z.y));
+          } else {
+            v[b][r] = make_float2(0.0f, 0.0f);
+          }
+        }
+        dft<PL::R1, -1>(v[b]);
+      }
+      pass_store<NC, PL::R1, PL::B1>(sbuf, v, t, 1);
+    }
+    __syncthreads();
+    middle_passes<LOGN, G::LOGP, -1>(sbuf, t, tw, twl);
+    {
+      float2 v[1][PL::P];
+      constexpr int off = pass_table_offset<LOGN, G::LOGP>(PL::NP - 1);
+      pass_compute<NC, PL::P, 1, -1>(sbuf, v, t, NC / PL::P, tw + off, twl + off);
+      __syncthreads();
+      pass_store<NC, PL::P, 1>(sbuf, v, t, NC / PL::P);
+    }
+    __syncthreads();
+    if (active) {
+      // U^[f] = (Z[f] + conj Z[n-f])/2 - (i/2) e^{-i theta} (Z[f] - conj Z[n-f])
+      auto bin = [&](int f) {
+        const float2 Zf = sbuf[pad_index(f & (NC - 1))];
+        const float2 Zr = cconj(sbuf[pad_index((NC - f) & (NC - 1))]);
+        const float2 sm = cadd(Zf, Zr), d = csub(Zf, Zr);
+        const float2 wd = twiddle<-1>(d, hw, hwl, f);  // e^{-i theta} (Z - conj Z'), compensated
+        return make_float2(0.5f * sm.x + 0.5f * wd.y, 0.5f * sm.y - 0.5f * wd.x);
+      };
+      auto operands = [&](int f, float2 Uf, float2 Un) {  // Un = U^[n-f]
+        const double2 E = hw64[f];                         // e^{-i theta}; e^{+i theta} = conj
+        const float2 a1 = make_float2(float(1.0 + E.y), float(E.x));   // 1 + i e^{+i theta}
+        const float2 a2 = make_float2(float(1.0 - E.y), float(-E.x));  // 1 - i e^{+i theta}
+        const float2 X1 = cmul(Uf, a1), X2 = cmul(cconj(Un), a2);
+        out4[(size_t)col * NC + f] = make_float4(X1.x, X1.y, X2.x, X2.y);
+      };
+      for (int f = t; f <= NC / 2; f += PL::TPF) {
+        const float2 Uf = bin(f), Un = bin(NC - f);
+        operands(f, Uf, Un);
+        if (f > 0 && 2 * f < NC) operands(NC - f, Un, Uf);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Optional second output of the float32 convolution: the exact bf16 slices
 // of each output row (the operand format of the tensor-core contraction,
 // csrc/gram_tc.cu), written in the same chunk-blocked layout and with the
@@ -404,6 +480,35 @@ int dispatch_spectra(int logn, int mode, const double* src, int ncols, double2* 
   }
 }
 
+template <int LOGN>
+int launch_spectra32(const double* src, int ncols, float4* o4, const cpc_kernel* P, cudaStream_t s) {
+  using G = Geometry<LOGN, float>;
+  const size_t smem = sizeof(float2) * G::slots * padded_len(1 << LOGN);
+  auto kern = spectra32_kernel<LOGN>;
+  int st = configure(kern, smem);
+  if (st) return st;
+  int per_sm = 0;
+  CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::threads, smem));
+  const int groups = (ncols + G::slots - 1) / G::slots;
+  const int grid = std::max(1, std::min(groups, std::max(1, per_sm) * sm_count()));
+  const int slot = timing_begin("spectra_kernel", s);
+  kern<<<grid, G::threads, smem, s>>>(src, ncols, P->d_hw32, static_cast<const __half2*>(P->d_hw32_lo), P->d_hw64,
+                                      P->d_twp32, static_cast<const __half2*>(P->d_twp32_lo), o4);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("spectra32_kernel");
+  return CPC_OK;
+}
+
+template <int LOGN>
+int dispatch_spectra32(int logn, const double* src, int ncols, float4* o4, const cpc_kernel* P, cudaStream_t s) {
+  if constexpr (LOGN > kMaxLogN) {
+    return fail(CPC_ERR_UNSUPPORTED, "spectra: n too large");
+  } else {
+    if (logn == LOGN) return launch_spectra32<LOGN>(src, ncols, o4, P, s);
+    return dispatch_spectra32<LOGN + 1>(logn, src, ncols, o4, P, s);
+  }
+}
+
 // kernel-term pairs (p^[f], p^[n-f]), f = 0..n-1, float32 [R_N][n]
 __global__ void kernel_pairs_kernel(const double* __restrict__ phat64, int R_N, int n, float2* __restrict__ pp) {
   const long long total = (long long)R_N * n;
@@ -493,8 +598,7 @@ int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uh
 }
 
 int forward_operands32(const cpc_kernel* P, int ncols, const double* U, void* X, cudaStream_t s) {
-  return dispatch_spectra<kMinLogN>(ilog2(P->n), 2, U, ncols, nullptr, nullptr, nullptr, nullptr, P, s,
-                                    static_cast<float4*>(X));
+  return dispatch_spectra32<kMinLogN>(ilog2(P->n), U, ncols, static_cast<float4*>(X), P, s);
 }
 
 size_t operands32_bytes(const cpc_kernel* P, int ncols) { return align256(size_t(ncols) * P->n * sizeof(float4)); }
