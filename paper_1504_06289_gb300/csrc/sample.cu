@@ -14,7 +14,10 @@ __global__ void sample_kernel(int n, double b, double h, int R, const double* __
   if (i >= n) return;
   const double x = -b + (i + 0.5) * h;
   const double d = x - X[3 * k + l];
-  U[((size_t)l * R + k) * n + i] = exp(-a[k] * d * d);
+  const double e = a[k] * d * d;
+  // exp(-e) is exactly 0 in float64 beyond e = 745.2 (below the smallest
+  // subnormal): skip the call there (most cells of a narrow Gaussian)
+  U[((size_t)l * R + k) * n + i] = (e > 746.0) ? 0.0 : exp(-e);
 }
 
 __global__ void hadamard_kernel(int n, int n_in, int n_pairs, const int* __restrict__ pa,
