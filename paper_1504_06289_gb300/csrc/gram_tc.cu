@@ -10,16 +10,17 @@
 // bf16 (exact).  A product of two rows is
 //   2^(e_r + e_s - 16) * (S0 + S1 2^-8 + S2 2^-16),  S_g = sum_{a+b=g} sum_i s_a s_b,
 // dropping the a+b >= 3 terms (below float32 rounding of the operands).  Over
-// 128 cells every S_g is an integer below 2^24, so the bf16 MMAs accumulate
-// exactly in TMEM whatever the tensor core's rounding; every 128 cells the
-// accumulators are folded into a compensated float32 sum (TwoSum) per entry.
+// 192 cells every S_g is an integer below 2^24 (at most 192 * 81920 =
+// 1.57e7 for S_2), so the bf16 MMAs accumulate exactly in TMEM whatever the
+// tensor core's rounding; every 192 cells the accumulators are folded into a
+// compensated float32 sum (TwoSum) per entry.
 //
 // Tiles: a CTA pair (2-CTA cluster, cta_group::2) computes 256 rows of U (M)
 // x 128 rows of W (N) for one kernel term; each CTA streams its 128 U rows and
 // 64 W rows with TMA (cp.async.bulk.tensor, 128-byte swizzle, completion
 // counted on an mbarrier) through 3 shared-memory stages, and one thread of
 // the even CTA issues the MMAs for both.  Sixteen warps per CTA read the
-// accumulators after every two chunks; the three axes run as one stream of
+// accumulators after every three chunks; the three axes run as one stream of
 // chunks and the running product over axes stays in TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -42,6 +43,7 @@ constexpr int READERS = 16;  // accumulator reader warps: lane quadrant x column
 constexpr int BNW = BN / 4;  // columns read by one reader warp
 constexpr int THREADS = (READERS + 1) * 32;  // + one TMA/MMA warp
 constexpr int STAGES = 3;
+constexpr int GROUP = 3;  // 64-cell chunks per TMEM accumulation: every group sum over 192 cells < 2^24
 constexpr uint32_t A_SLICE_BYTES = BM * 128, B_SLICE_BYTES = BNH * 128;
 constexpr uint32_t STAGE_BYTES = 3 * A_SLICE_BYTES + 3 * B_SLICE_BYTES;  // 72 KB per CTA
 constexpr uint32_t TMEM_COLS = 512;  // 3 groups x 128 columns, then the product over axes
@@ -191,11 +193,11 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, v
 // even CTA's full barrier; one thread of the even CTA issues the pair MMAs
 // (each CTA's TMEM receives its 128 rows x 128 columns).  In each CTA, warps
 // 0-15 read the accumulators (warp w: TMEM lanes 32 (w % 4).., columns
-// 32 (w / 4)..), warp 16 drives the copies.  Two consecutive 64-cell chunks
-// accumulate before each readout (every group sum stays an integer below
-// 2^24 over 128 cells, so it is exact).
+// 32 (w / 4)..), warp 16 drives the copies.  Up to GROUP = 3 consecutive
+// 64-cell chunks accumulate before each readout (every group sum stays an
+// integer below 2^24 over 192 cells, so it is exact).
 // Barriers: full[stage] (even CTA: both halves landed), sfree[stage] (both
-// CTAs: the MMAs reading a stage finished), done (both CTAs: a pair of
+// CTAs: the MMAs reading a stage finished), done (both CTAs: a group of
 // chunks accumulated), freeb (even CTA: the 32 reader warps of the pair
 // took the accumulators out of TMEM).
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
@@ -251,7 +253,9 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   umma::fence_after();
   const uint32_t tbase = *tmem_ptr;
   const int T = g.n / BKC, TT = 3 * T;  // chunks (T even)
-  const int PP = TT / 2, PA = T / 2;    // pairs of chunks in all, per axis
+  // chunks accumulate in TMEM in groups of up to GROUP (the last group of an
+  // axis may be shorter); GA groups per axis, 3 GA in all
+  const int GA = (T + GROUP - 1) / GROUP;
   const uint32_t freeb_even = umma::mapa(umma::smem_u32(freeb), 0);
   double sum = 0.0;
 
@@ -264,13 +268,14 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           issue_stage(&mapA, &mapB, g, sbase, fullc(tt), tt, T, q, r0, sb0);
         }
         for (int tt = 0; tt < TT; ++tt) {
-          const int pp = tt >> 1;
+          const int t = tt % T, gi = (tt / T) * GA + t / GROUP;  // group of this chunk
+          const bool first = (t % GROUP == 0), last = (t % GROUP == GROUP - 1) || (t == T - 1);
           if (!wait_or_abort(&full[tt % STAGES], (tt / STAGES) & 1, abort_flag)) break;
-          if ((tt & 1) == 0 && pp >= 1 && !wait_or_abort(freeb, (pp - 1) & 1, abort_flag)) break;
+          if (first && gi >= 1 && !wait_or_abort(freeb, (gi - 1) & 1, abort_flag)) break;
           umma::fence_after();
-          issue_mmas(sbase + (tt % STAGES) * STAGE_BYTES, tbase, (tt & 1) ? 1u : 0u);
+          issue_mmas(sbase + (tt % STAGES) * STAGE_BYTES, tbase, first ? 0u : 1u);
           umma::mma_commit_pair(&sfree[tt % STAGES]);
-          if (tt & 1) umma::mma_commit_pair(done);
+          if (last) umma::mma_commit_pair(done);
           const int tn = tt + STAGES - 1;
           if (tn < TT) {
             // stage tn % STAGES last held chunk tt - 1: wait until its MMAs finished
@@ -309,8 +314,8 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     for (int j = 0; j < BNW / 2; ++j) lo[j] = __float2bfloat162_rn(0.0f);
     double row = 0.0;
     bool ok = true;
-    for (int pp = 0; pp < PP && ok; ++pp) {
-      if (!wait_or_abort(done, pp & 1, abort_flag)) { ok = false; break; }
+    for (int gi = 0; gi < 3 * GA && ok; ++gi) {
+      if (!wait_or_abort(done, gi & 1, abort_flag)) { ok = false; break; }
       umma::fence_after();
 #pragma unroll
       for (int cb = 0; cb < BNW / 8; ++cb) {
@@ -339,10 +344,10 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       umma::fence_before();
       __syncwarp();
       if (lane == 0) umma::mbar_arrive_cluster(freeb_even);
-      if (pp % PA == PA - 1) {
+      if (gi % GA == GA - 1) {
         // axis l finished: G_l = 2^(e_r + e_s - 16) (tot + lo); the running
         // product over axes lives in TMEM columns PROD_COL.. between axes
-        const int l = pp / PA;
+        const int l = gi / GA;
         const int er = (r < g.M) ? g.eA[l * g.M + r] : 0;
 #pragma unroll
         for (int cb = 0; cb < BNW / 16; ++cb) {
@@ -435,7 +440,7 @@ size_t tc_partials(int R_f, int R_N) {
   return size_t(2) * n_rp * n_ct * R_N;
 }
 
-// two 64-cell chunks per accumulation: n a multiple of 128
+// n a multiple of 128 (the convolution that writes the W slices needs n >= 128)
 bool tc_supported(const cpc_kernel* P) { return P->n >= 2 * tc::BKC && P->n % (2 * tc::BKC) == 0; }
 
 namespace {
