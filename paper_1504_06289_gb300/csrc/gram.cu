@@ -225,20 +225,29 @@ __global__ void item_reduce_kernel(int n_items, const int* __restrict__ off, con
 // float32 form of the adjoint GEMM.  The K sum runs q-major (kk = (q, k')),
 // so the A tile Bl[m][k'] for one q is read along k' (contiguous in G); A is
 // formed as float(G1 G2) times float32 coefficients cached in shared memory;
-// each K chunk of 32 is summed in float32 and folded into a float32 total
-// per output (compensated when COMP).  Tile TM m x TN i with RT x CT outputs
-// per thread (rows RT ty.., columns CT tx.., the W tile read as float4).
+// each K chunk of 32 is summed in float32 and folded into a compensated
+// float32 total per output.  Tile TM m x TN i with RT x CT outputs per thread
+// (rows RT ty.., columns CT tx..).  Software pipeline: while chunk c is
+// multiplied out of one shared-memory buffer, the W tile of chunk c+1 lands in
+// the other by cp.async and its G values wait in registers.
 namespace adj32 {
 constexpr int KC = 32, THREADS = 256;
 constexpr int TM = 40, TN = 128, RT = 5, CT = 4;  // 40 rows: R_f = 200 splits without a ragged tile
-constexpr bool COMP = true;
-constexpr int MAXRF = 1024;  // coefficients cached in shared memory
+constexpr int MAXRF = 1024;                       // coefficients cached in shared memory
+constexpr int AE = (TM * KC + THREADS - 1) / THREADS;    // A elements per thread
+constexpr int BE = (KC * TN / 4 + THREADS - 1) / THREADS;  // B float4 per thread
 static_assert((TM / RT) * (TN / CT) == THREADS, "thread tiling");
+
+__device__ __forceinline__ void cp_async16(float* sdst, const float* gsrc) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(sdst))),
+               "l"(gsrc));
+}
+
 __global__ void __launch_bounds__(THREADS)
 adjoint32_kernel(int n, int R_f, int R_N, const double* __restrict__ c, const double* __restrict__ G,
                  const float* __restrict__ W, float scale2h3, double* __restrict__ dU) {
-  __shared__ float As[KC][TM + 1];  // written along kk (padded: no bank conflicts)
-  __shared__ __align__(16) float Bs[KC][TN];
+  __shared__ float As[2][KC][TM + 1];  // written along kk (padded: no bank conflicts)
+  __shared__ __align__(16) float Bs[2][KC][TN];
   __shared__ float cf[MAXRF];
   const int l = blockIdx.z;
   const int m0 = blockIdx.y * TM, i0 = blockIdx.x * TN;
@@ -249,78 +258,110 @@ adjoint32_kernel(int n, int R_f, int R_N, const double* __restrict__ c, const do
   const size_t GM = (size_t)R_f * R_f;
   const float* Wl = W + (size_t)l * R_f * R_N * n;
   for (int k = tid; k < R_f && k < MAXRF; k += THREADS) cf[k] = float(c[k]);
-  __syncthreads();
+  const int NKP = (R_f + KC - 1) / KC, NCH = R_N * NKP;
+
+  double g1[AE], g2[AE];
+  // raw G values of chunk ch into registers (zero outside)
+  auto load_a = [&](int ch) {
+    const int q = ch / NKP, kp0 = (ch % NKP) * KC;
+    const double* G1 = G + ((size_t)l1 * R_N + q) * GM;
+    const double* G2 = G + ((size_t)l2 * R_N + q) * GM;
+#pragma unroll
+    for (int e = 0; e < AE; ++e) {
+      const int idx = tid + e * THREADS;
+      const int row = idx / KC, kk = idx % KC;
+      const int m = m0 + row, kp = kp0 + kk;
+      const bool ok = idx < TM * KC && m < R_f && kp < R_f;
+      const size_t gi = (size_t)m * R_f + kp;
+      g1[e] = ok ? G1[gi] : 0.0;
+      g2[e] = ok ? G2[gi] : 0.0;
+    }
+  };
+  // A tile of chunk ch from the registers: As[buf][kk][row] = 2 h^3 c_m c_k' G1 G2
+  auto store_a = [&](int ch, int buf) {
+    const int kp0 = (ch % NKP) * KC;
+#pragma unroll
+    for (int e = 0; e < AE; ++e) {
+      const int idx = tid + e * THREADS;
+      if (idx >= TM * KC) break;
+      const int row = idx / KC, kk = idx % KC;
+      const int m = m0 + row, kp = kp0 + kk;
+      As[buf][kk][row] = (m < R_f && kp < R_f) ? (scale2h3 * cf[m] * cf[kp]) * float(g1[e] * g2[e]) : 0.0f;
+    }
+  };
+  // W tile of chunk ch: rows k' R_N + q, columns i0.. (cp.async where whole, zeros or scalars elsewhere)
+  auto load_b = [&](int ch, int buf) {
+    const int q = ch / NKP, kp0 = (ch % NKP) * KC;
+#pragma unroll
+    for (int e = 0; e < BE; ++e) {
+      const int idx = tid + e * THREADS;
+      if (idx >= KC * TN / 4) break;
+      const int kk = idx / (TN / 4), c4 = idx % (TN / 4);
+      const int kp = kp0 + kk, i = i0 + 4 * c4;
+      float* dst = &Bs[buf][kk][4 * c4];
+      if (kp < R_f && i + 3 < n && (n & 3) == 0) {
+        cp_async16(dst, Wl + ((size_t)kp * R_N + q) * n + i);
+      } else {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (kp < R_f) {
+          const float* row = Wl + ((size_t)kp * R_N + q) * n;
+          if (i < n) v.x = row[i];
+          if (i + 1 < n) v.y = row[i + 1];
+          if (i + 2 < n) v.z = row[i + 2];
+          if (i + 3 < n) v.w = row[i + 3];
+        }
+        *reinterpret_cast<float4*>(dst) = v;
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+
   float tot[RT][CT], lo[RT][CT];
 #pragma unroll
   for (int a = 0; a < RT; ++a)
 #pragma unroll
     for (int b = 0; b < CT; ++b) { tot[a][b] = 0.0f; lo[a][b] = 0.0f; }
-  for (int q = 0; q < R_N; ++q) {
-    const double* G1 = G + ((size_t)l1 * R_N + q) * GM;
-    const double* G2 = G + ((size_t)l2 * R_N + q) * GM;
-    for (int kp0 = 0; kp0 < R_f; kp0 += KC) {
-      // A tile: As[kk][row] = 2 h^3 c_m c_k' G1[m][k'] G2[m][k'], k' = kp0 + kk (contiguous per row)
-      for (int idx = tid; idx < TM * KC; idx += THREADS) {
-        const int row = idx / KC, kk = idx % KC;
-        const int m = m0 + row, kp = kp0 + kk;
-        float v = 0.0f;
-        if (m < R_f && kp < R_f) {
-          const size_t gi = (size_t)m * R_f + kp;
-          v = (scale2h3 * cf[m] * cf[kp]) * float(G1[gi] * G2[gi]);
-        }
-        As[kk][row] = v;
-      }
-      // B tile: W rows k' R_N + q, columns i0.. (float4 per thread)
-      for (int idx = tid; idx < KC * TN / 4; idx += THREADS) {
-        const int kk = idx / (TN / 4), c4 = idx % (TN / 4);
-        const int kp = kp0 + kk, i = i0 + 4 * c4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (kp < R_f) {
-          const float* row = Wl + ((size_t)kp * R_N + q) * n;
-          if (i + 3 < n) v = *reinterpret_cast<const float4*>(row + i);
-          else {
-            if (i < n) v.x = row[i];
-            if (i + 1 < n) v.y = row[i + 1];
-            if (i + 2 < n) v.z = row[i + 2];
-          }
-        }
-        *reinterpret_cast<float4*>(&Bs[kk][4 * c4]) = v;
-      }
-      __syncthreads();
-      float part[RT][CT];
-#pragma unroll
-      for (int a = 0; a < RT; ++a)
-#pragma unroll
-        for (int b = 0; b < CT; ++b) part[a][b] = 0.0f;
-#pragma unroll
-      for (int kk = 0; kk < KC; ++kk) {
-        float ar[RT], br[CT];
-#pragma unroll
-        for (int a = 0; a < RT; ++a) ar[a] = As[kk][RT * ty + a];
-#pragma unroll
-        for (int b = 0; b < CT; b += 4) {
-          const float4 bv = *reinterpret_cast<const float4*>(&Bs[kk][CT * tx + b]);
-          br[b] = bv.x; br[b + 1] = bv.y; br[b + 2] = bv.z; br[b + 3] = bv.w;
-        }
-#pragma unroll
-        for (int a = 0; a < RT; ++a)
-#pragma unroll
-          for (int b = 0; b < CT; ++b) part[a][b] = fmaf(ar[a], br[b], part[a][b]);
-      }
-#pragma unroll
-      for (int a = 0; a < RT; ++a)
-#pragma unroll
-        for (int b = 0; b < CT; ++b) {
-          if constexpr (COMP) {
-            const float t = tot[a][b], v = part[a][b], sm = t + v, bb = sm - t;
-            lo[a][b] += (t - (sm - bb)) + (v - bb);
-            tot[a][b] = sm;
-          } else {
-            tot[a][b] += part[a][b];
-          }
-        }
-      __syncthreads();
+  __syncthreads();  // cf
+  load_a(0);
+  load_b(0, 0);
+  store_a(0, 0);
+  asm volatile("cp.async.wait_all;\n" ::);
+  __syncthreads();
+  for (int ch = 0; ch < NCH; ++ch) {
+    const int buf = ch & 1;
+    const bool more = ch + 1 < NCH;
+    if (more) {
+      load_b(ch + 1, buf ^ 1);
+      load_a(ch + 1);
     }
+    float part[RT][CT];
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+      for (int b = 0; b < CT; ++b) part[a][b] = 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      float ar[RT];
+#pragma unroll
+      for (int a = 0; a < RT; ++a) ar[a] = As[buf][kk][RT * ty + a];
+      const float4 bv = *reinterpret_cast<const float4*>(&Bs[buf][kk][CT * tx]);
+      const float br[CT] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+      for (int a = 0; a < RT; ++a)
+#pragma unroll
+        for (int b = 0; b < CT; ++b) part[a][b] = fmaf(ar[a], br[b], part[a][b]);
+    }
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+      for (int b = 0; b < CT; ++b) {
+        const float t = tot[a][b], v = part[a][b], sm = t + v, bb = sm - t;
+        lo[a][b] += (t - (sm - bb)) + (v - bb);
+        tot[a][b] = sm;
+      }
+    if (more) store_a(ch + 1, buf ^ 1);
+    asm volatile("cp.async.wait_all;\n" ::);
+    __syncthreads();
   }
 #pragma unroll
   for (int a = 0; a < RT; ++a) {
