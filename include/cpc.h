@@ -145,7 +145,8 @@ int cp_convolve_from_spectra(const cpc_kernel* P, int R_f, const void* spec, voi
  * CPC_FP64.  CPC_FP32 (n a multiple of 128): on the tensor cores, each row
  * of U and of the float32 W split exactly into three bf16 integer slices under
  * a per-row power-of-two scale (the convolution writes W's slices in the same
- * pass as W), the slice products summed exactly over 192-cell chunks in TMEM
+ * pass as W), the slice products summed in TMEM over 256-cell chunks (the
+ * two leading slice groups exactly)
  * and folded into a compensated float32 sum per entry (at least as accurate
  * as float32 operands with float32 products); other n: float32 products on
  * CUDA cores.  CPC_SPLIT: float32

@@ -10,17 +10,19 @@
 // bf16 (exact).  A product of two rows is
 //   2^(e_r + e_s - 16) * (S0 + S1 2^-8 + S2 2^-16),  S_g = sum_{a+b=g} sum_i s_a s_b,
 // dropping the a+b >= 3 terms (below float32 rounding of the operands).  Over
-// 192 cells every S_g is an integer below 2^24 (at most 192 * 81920 =
-// 1.57e7 for S_2), so the bf16 MMAs accumulate exactly in TMEM whatever the
-// tensor core's rounding; every 192 cells the accumulators are folded into a
-// compensated float32 sum (TwoSum) per entry.
+// 256 cells S_0 and S_1 are integers of magnitude at most 2^24 (256 * 2^16
+// each), so the bf16 MMAs accumulate them exactly in TMEM whatever the tensor
+// core's rounding; S_2 (at most 256 * 81920 = 2.1e7) may pass 2^24, where a
+// float32 accumulation step can round by 2^-24 of S_2, i.e. below 2^-38 of the
+// 2^(e_r+e_s) scale of the entry.  Every 256 cells the accumulators are folded
+// into a compensated float32 sum (TwoSum) per entry.
 //
 // Tiles: a CTA pair (2-CTA cluster, cta_group::2) computes 256 rows of U (M)
 // x 128 rows of W (N) for one kernel term; each CTA streams its 128 U rows and
 // 64 W rows with TMA (cp.async.bulk.tensor, 128-byte swizzle, completion
 // counted on an mbarrier) through 3 shared-memory stages, and one thread of
 // the even CTA issues the MMAs for both.  Sixteen warps per CTA read the
-// accumulators after every three chunks; the three axes run as one stream of
+// accumulators after every four chunks; the three axes run as one stream of
 // chunks and the running product over axes stays in TMEM.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -38,12 +40,13 @@ namespace tc {
 constexpr int BM = 128;      // U rows per CTA (M = 256 per CTA pair)
 constexpr int BN = 128;      // W rows (output columns) per pair tile
 constexpr int BNH = BN / 2;  // W rows loaded by each CTA of the pair
+static_assert(BM == BN, "the symmetric E_H tiling uses square 128 x 128 blocks");
 constexpr int BKC = 64;      // chunk of 64 cells = one 128-byte bf16 row
 constexpr int READERS = 16;  // accumulator reader warps: lane quadrant x column quarter
 constexpr int BNW = BN / 4;  // columns read by one reader warp
 constexpr int THREADS = (READERS + 1) * 32;  // + one TMA/MMA warp
 constexpr int STAGES = 3;
-constexpr int GROUP = 3;  // 64-cell chunks per TMEM accumulation: every group sum over 192 cells < 2^24
+constexpr int GROUP = 4;  // 64-cell chunks per TMEM accumulation: S_0, S_1 over 256 cells stay within 2^24
 constexpr uint32_t A_SLICE_BYTES = BM * 128, B_SLICE_BYTES = BNH * 128;
 constexpr uint32_t STAGE_BYTES = 3 * A_SLICE_BYTES + 3 * B_SLICE_BYTES;  // 72 KB per CTA
 constexpr uint32_t TMEM_COLS = 512;  // 3 groups x 128 columns, then the product over axes
@@ -108,6 +111,53 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const TS* __restrict__ 
     }
     __syncthreads();  // red[] reused by the next row
   }
+}
+
+// E_H tiling of the symmetric Gram.  With nb = ceil(R_f / 128) blocks per
+// side, the blocks {i, c}, i <= c, of 128 rows x 128 columns are what E_H
+// needs; a CTA pair computes two blocks that share a column block.  Column c
+// starts with its diagonal block and the blocks of rows i < c; walking
+// c = nb-1 .. 1, a column with an odd count hands its block {c-1, c} to column
+// c-1, where it is computed as rows c, columns c-1 (the transpose, equal by
+// symmetry).  Every column but column 0 then holds an even count, so at most
+// one CTA pair has a single block (about nb^2 / 4 pairs instead of the
+// nb/2 x nb of a 256 x 128 tiling of the upper triangle).
+__host__ __device__ inline int eh_pair_tiles(int nb) {
+  int carry = 0, total = 0;
+  for (int c = nb - 1; c >= 0; --c) {
+    const int cnt = c + 1 + carry;
+    const int out = (c > 0 && (cnt & 1)) ? 1 : 0;
+    total += (cnt - out + 1) / 2;
+    carry = out;
+  }
+  return total;
+}
+// row blocks (rb0, rb1; rb1 = -1: none) and column block of pair tile pt
+__host__ __device__ inline void eh_pair_tile(int nb, int pt, int* rb0, int* rb1, int* cb) {
+  int carry = 0, base = 0;
+  for (int c = nb - 1; c >= 0; --c) {
+    const int cnt = c + 1 + carry;
+    const int out = (c > 0 && (cnt & 1)) ? 1 : 0;
+    const int np = (cnt - out + 1) / 2;
+    if (pt < base + np) {
+      // rows of column c: 0..c without c-1 when handed on, then c+1 when received
+      const int len_main = out ? c : c + 1;
+      auto elem = [&](int e) {
+        if (e < len_main) return (out && e >= c - 1) ? e + 1 : e;
+        return (carry && e == len_main) ? c + 1 : -1;
+      };
+      const int e = 2 * (pt - base);
+      *rb0 = elem(e);
+      *rb1 = elem(e + 1);
+      *cb = c;
+      return;
+    }
+    base += np;
+    carry = out;
+  }
+  *rb0 = -1;
+  *rb1 = -1;
+  *cb = 0;
 }
 
 struct Args {
@@ -193,9 +243,9 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, v
 // even CTA's full barrier; one thread of the even CTA issues the pair MMAs
 // (each CTA's TMEM receives its 128 rows x 128 columns).  In each CTA, warps
 // 0-15 read the accumulators (warp w: TMEM lanes 32 (w % 4).., columns
-// 32 (w / 4)..), warp 16 drives the copies.  Up to GROUP = 3 consecutive
-// 64-cell chunks accumulate before each readout (every group sum stays an
-// integer below 2^24 over 192 cells, so it is exact).
+// 32 (w / 4)..), warp 16 drives the copies.  Up to GROUP = 4 consecutive
+// 64-cell chunks accumulate before each readout (S_0 and S_1 stay integers of
+// magnitude at most 2^24 over 256 cells, so they are exact).
 // Barriers: full[stage] (even CTA: both halves landed), sfree[stage] (both
 // CTAs: the MMAs reading a stage finished), done (both CTAs: a group of
 // chunks accumulated), freeb (even CTA: the 32 reader warps of the pair
@@ -223,13 +273,19 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const int q = blockIdx.y;
   const int n_ct = (g.Ns + BN - 1) / BN;
   const int pair = blockIdx.x >> 1;
-  const int rp = pair / n_ct, ct = pair % n_ct;
-  const int r0p = rp * 2 * BM, s0 = ct * BN;
-  if (!g.rows_mode && r0p > s0 + BN - 1) {  // the whole pair tile lies below the diagonal: both CTAs leave
-    if (tid == 0) g.partial[(size_t)q * gridDim.x + blockIdx.x] = 0.0;
-    return;
+  int ct, r0;
+  if (g.rows_mode) {  // rectangular: 256-row x 128-column pair tiles
+    const int rp = pair / n_ct;
+    ct = pair % n_ct;
+    r0 = rp * 2 * BM + int(rank) * BM;
+  } else {  // symmetric: two 128 x 128 blocks of one column block (above)
+    int rb0, rb1;
+    eh_pair_tile(n_ct, pair, &rb0, &rb1, &ct);
+    const int rb = rank ? rb1 : rb0;
+    r0 = (rb >= 0 ? rb : n_ct) * BM;  // no block: rows past R_f (read as zeros, never counted)
   }
-  const int r0 = r0p + int(rank) * BM, sb0 = s0 + int(rank) * BNH;
+  const int s0 = ct * BN, sb0 = s0 + int(rank) * BNH;
+  const bool diag = !g.rows_mode && r0 == s0;  // a diagonal block: only r <= s counts
   // the tile's column coefficients and row exponents of W, once
   for (int i = tid; i < 4 * BN; i += THREADS) {
     const int j = i % BN, s = s0 + j;
@@ -365,7 +421,7 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             const float Gv = ldexpf(tot[j] + lj, er + es - 16);
             tot[j] = 0.0f;
             if (j & 1) lo[j / 2] = __float2bfloat162_rn(0.0f);
-            const bool in = r < g.M && s < g.Ns && (g.rows_mode || r <= s);
+            const bool in = r < g.M && s < g.Ns && (!diag || r <= s);
             if (g.G && in) {
               double* Gq = g.G + ((size_t)l * gridDim.y + q) * (size_t)g.M * g.M;
               Gq[(size_t)r * g.M + s] = Gv;
@@ -434,10 +490,9 @@ int launch_slice(const TS* src, long long rows, int n, int R_f, int R_N, __nv_bf
 
 }  // namespace tc
 
-// one partial per CTA: 2 CTAs per (256-row, 128-column) pair tile and kernel term
+// one partial per CTA: 2 CTAs per pair tile of the symmetric tiling and kernel term
 size_t tc_partials(int R_f, int R_N) {
-  const int n_rp = (R_f + 2 * tc::BM - 1) / (2 * tc::BM), n_ct = (R_f + tc::BN - 1) / tc::BN;
-  return size_t(2) * n_rp * n_ct * R_N;
+  return size_t(2) * tc::eh_pair_tiles((R_f + tc::BN - 1) / tc::BN) * R_N;
 }
 
 // n a multiple of 128 (the convolution that writes the W slices needs n >= 128)
@@ -550,7 +605,7 @@ int launch_tc(const cpc_kernel* P, int M, int Ns, const double* U, const float* 
       return fail(CPC_ERR_CUDA, "tensor map for the V_H factor slices");
   }
   const int n_rp = (M + 2 * tc::BM - 1) / (2 * tc::BM), n_ct = (Ns + tc::BN - 1) / tc::BN;
-  const long long gx = 2LL * n_rp * n_ct;
+  const long long gx = rows_mode ? 2LL * n_rp * n_ct : 2LL * tc::eh_pair_tiles(n_ct);
   if (gx > 0x7fffffffLL || R_N > 65535) return fail(CPC_ERR_UNSUPPORTED, "tensor-core contraction: grid too large");
   dim3 grid((unsigned)gx, R_N);  // clusters of 2 along x
   tc::Args args{eA, eB, M, Ns, R_N, n, rows_mode, c, c_col, partial, G, status};

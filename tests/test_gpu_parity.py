@@ -122,6 +122,28 @@ def test_convolution_and_energy_fp32(cpc, name, spec):
     assert rel(G2.cpu().numpy(), G0) < 2e-6
 
 
+@pytest.mark.parametrize("R_f", [129, 300, 400, 520])
+def test_fp32_tensor_core_block_tilings(cpc, R_f):
+    # the tensor-core E_H contraction pairs the 128 x 128 blocks of the
+    # symmetric Gram by column block, some of them transposed, one possibly
+    # alone: 2..5 blocks per side with ragged edges, every G entry compared
+    n, b, M = 256, 6.0, 8
+    h = 2 * b / n
+    g = workloads.gaussian_mixture(R_f, 0.3, 30.0, 5, centre_half=1.0)
+    P = cpc.make_newton_kernel(n, b, M)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    U = cpc.cp_sample_gaussians(n, b, dev(g["a"]), dev(g["X"]))
+    U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
+    E, W, G = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp32", want_G=True)
+    W0 = ocp.convolve_factors(U0, P0)
+    G0 = ocp.conv_matrices(U0, W0, P0.shape[0])
+    E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
+    assert abs(E.item() / E0 - 1) < 5e-7
+    Gh = G.cpu().numpy()
+    assert rel(Gh, G0) < 2e-6
+    assert np.array_equal(Gh, np.swapaxes(Gh, 2, 3))
+
+
 @pytest.mark.parametrize("name,spec", CASES[:3])
 def test_convolution_and_energy_split(cpc, name, spec):
     # float64 convolutions, float32-product contractions
