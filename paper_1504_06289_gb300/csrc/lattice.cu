@@ -10,13 +10,16 @@
 //                     terms with a compensated (Kahan) float32 sum.  Sub-grid
 //                     indices outside [0, n) are clamped, never dereferenced.
 //   subgrid_tc_kernel : the float32 form on the tensor cores when R_N <= 64:
-//                     V[(s1,s2)][s3] is a product of a (pairs x q) matrix
-//                     A = S1 * S2 and a (q x s3) matrix B = S3, each row split
-//                     exactly into four bf16 integer slices under a per-row
-//                     power of two (a published error-free splitting, the
-//                     "Ozaki scheme"); the slice products are summed exactly
-//                     in TMEM (every group sum over 64 q is an integer below
-//                     2^24) and folded into float32 once per output.
+//                     V[(s1,s2)][s3] is a product of a (s3 x q) matrix S3 and
+//                     a (q x pairs) matrix S1 * S2 (the MMA's M runs over s3,
+//                     so that stores are coalesced), each row split exactly
+//                     into four bf16 integer slices under a per-row power of
+//                     two (a published error-free splitting, the "Ozaki
+//                     scheme"); the slice products are summed exactly in TMEM
+//                     (every group sum over 64 q is an integer below 2^24) and
+//                     folded into float32 once per output.  prep_kernel slices
+//                     the S3 rows and gathers the S1, S2 sub-grid values once
+//                     per call.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -122,32 +125,49 @@ subgrid_kernel(int n, int R_N, int n_sub, const double* __restrict__ S, const in
 
 // ---- tensor-core float32 form -------------------------------------------------
 namespace lat {
-constexpr int BM = 128;      // (s1, s2) pairs per CTA, one TMEM lane each
-constexpr int BN = 64;       // s3 points per sub-tile
+// V[(s1,s2)][s3] as D = A B^T per sub-tile: A = the S3 rows of 128 sub-grid
+// points s3 (the MMA's M, one TMEM lane each, so that a warp's 32 lanes hold
+// 32 consecutive s3 and every store of a warp writes 128 contiguous bytes),
+// B = the products a_q = S1[q][i1] S2[q][i2] of 64 (s1, s2) pairs (the MMA's N).
+constexpr int BM = 128;      // s3 points per sub-tile (TMEM lanes)
+constexpr int NP = 64;       // (s1, s2) pairs per CTA (TMEM columns per slice group)
 constexpr int NSL = 4;       // slices: x = 2^e (s0 2^-8 + s1 2^-16 + s2 2^-24 + s3 2^-32)
-constexpr int THREADS = 128;
-constexpr uint32_t A_SLICE = BM * 128, B_SLICE = BN * 128;  // rows of 64 bf16 (128 bytes)
-constexpr uint32_t TMEM_COLS = 256;                         // NSL groups x BN columns
-constexpr size_t kSmemBytes = size_t(NSL) * (A_SLICE + B_SLICE) + 1024 + 64;
+constexpr int THREADS = 256;        // 8 warps: lane quadrant x column half of the accumulators
+constexpr int PREP_THREADS = BM;    // one S3 row per thread
+constexpr uint32_t A_SLICE = BM * 128, B_SLICE = NP * 128;  // rows of 64 bf16 (128 bytes)
+constexpr uint32_t TMEM_COLS = NSL * NP;                    // 256
 constexpr long kSpinLimit = 20000000;
+constexpr int kMaxSub = 512;
+constexpr int kMaxTiles = kMaxSub / BM;
+constexpr size_t kATileBytes = size_t(NSL) * A_SLICE;  // 64 KB per sub-tile
+constexpr size_t kSmemBytes = kATileBytes + size_t(NSL) * B_SLICE + 1024 + 64 + 2 * NP * sizeof(int);
+// per-call scratch of the MASTER kernel: the S3 rows sliced per sub-tile, their
+// exponents, and the S1, S2 values of the sub-grid gathered q-contiguous
+constexpr size_t kExpOff = kMaxTiles * kATileBytes;
+constexpr size_t kGathOff = kExpOff + kMaxSub * sizeof(int);
+constexpr size_t kScratchBytes = kGathOff + size_t(2) * kMaxSub * 64 * sizeof(double);
 
-// row of 64 values (q = 0..63) -> NSL bf16 slices in 128-byte-swizzled K-major
-// rows at `base` (slice k at base + k * slice_bytes); returns the row exponent
-__device__ __forceinline__ int slice_row(const float (&x)[64], uint8_t* base, uint32_t slice_bytes, int row) {
-  float m = 0.0f;
+// NCH 16-byte chunks (8 values each, chunks c0 .. c0+NCH-1 of a 64-value row)
+// -> NSL bf16 slices under the row exponent e (|x| < 2^e), written into
+// 128-byte-swizzled K-major rows at `base` (slice k at base + k * slice_bytes)
+// 2^k as a float, k in [-126, 127]
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+
+template <int NCH>
+__device__ __forceinline__ void slice_chunks(const float* x, int e, uint8_t* base, uint32_t slice_bytes, int row,
+                                             int c0) {
+  // x 2^(8-e) by one exact multiplication while 2^(8-e) is a normal float
+  const bool fast = e > -100 && e < 100;
+  const float sc = fast ? pow2f(8 - e) : 0.0f;
 #pragma unroll
-  for (int q = 0; q < 64; ++q) m = fmaxf(m, fabsf(x[q]));
-  int e = 0;
-  if (m > 0.0f) frexpf(m, &e);  // |x| < 2^e
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {  // 16-byte chunk c holds q = 8c .. 8c+7
+  for (int c = 0; c < NCH; ++c) {
     uint32_t w[NSL][4];
 #pragma unroll
     for (int h = 0; h < 8; h += 2) {
       float sl[NSL][2];
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
-        float a = ldexpf(x[8 * c + h + u], 8 - e);  // |a| < 256
+        float a = fast ? x[8 * c + h + u] * sc : ldexpf(x[8 * c + h + u], 8 - e);  // |a| < 256
 #pragma unroll
         for (int k = 0; k < NSL; ++k) {
           const float r = rintf(a);
@@ -161,32 +181,51 @@ __device__ __forceinline__ int slice_row(const float (&x)[64], uint8_t* base, ui
         w[k][h / 2] = *reinterpret_cast<const uint32_t*>(&b2);
       }
     }
-    const uint32_t off = umma::sw128_offset(row, c * 16);
+    const uint32_t off = umma::sw128_offset(row, (c0 + c) * 16);
 #pragma unroll
     for (int k = 0; k < NSL; ++k)
       *reinterpret_cast<uint4*>(base + k * slice_bytes + off) = make_uint4(w[k][0], w[k][1], w[k][2], w[k][3]);
   }
+}
+
+__device__ __forceinline__ int row_exponent(float m) {
+  int e = 0;
+  if (m > 0.0f) frexpf(m, &e);  // m < 2^e
   return e;
 }
 
-constexpr int kMaxTiles = 512 / BN;                          // n_sub <= 512
-constexpr size_t kBTileBytes = size_t(NSL) * B_SLICE;          // 32 KB per sub-tile
-constexpr size_t kScratchBytes = kMaxTiles * kBTileBytes + 512 * sizeof(int);
-
-// B rows (b_q = S3[q][i3], s3 = 0..n_sub-1) sliced once per call into the
-// kernel's scratch: sub-tile j at j * 32 KB, slice k at + k * 8 KB, rows in the
-// 128-byte-swizzled layout the MMA reads; exponents after the tiles.
-__global__ void __launch_bounds__(BN)
-slice_b_kernel(int n, int R_N, int n_sub, const double* __restrict__ S, const int* __restrict__ sub,
-               unsigned char* __restrict__ scratch) {
-  const int t = threadIdx.x, j = blockIdx.x, s3 = j * BN + t;
-  const bool ok = s3 < n_sub;
-  const int i3 = clamp_index(sub[2 * n_sub + (ok ? s3 : 0)], n);
-  float x[64];
+// Once per call.  blockIdx.y == 0: the S3 rows of sub-tile blockIdx.x sliced
+// into the scratch (tile j at j * 64 KB, slice k at + k * 16 KB) with their
+// exponents; blockIdx.y == 1, 2: the S1 (S2) values of the tile's sub-grid
+// points gathered as rows g[s][q] (float64, zero for q >= R_N).
+__global__ void __launch_bounds__(PREP_THREADS)
+prep_kernel(int n, int R_N, int n_sub, const double* __restrict__ S, const int* __restrict__ sub,
+            unsigned char* __restrict__ scratch) {
+  const int t = threadIdx.x, j = blockIdx.x;
+  if (blockIdx.y == 0) {
+    const int s3 = j * BM + t;  // < kMaxSub
+    const bool ok = s3 < n_sub;
+    const int i3 = clamp_index(sub[2 * n_sub + (ok ? s3 : 0)], n);
+    float x[64];
+    float m = 0.0f;
 #pragma unroll
-  for (int q = 0; q < 64; ++q) x[q] = (ok && q < R_N) ? float(S[(size_t)(2 * R_N + q) * n + i3]) : 0.0f;
-  const int e = slice_row(x, scratch + (size_t)j * kBTileBytes, B_SLICE, t);
-  reinterpret_cast<int*>(scratch + kMaxTiles * kBTileBytes)[s3 < 512 ? s3 : 511] = ok ? e : 0;
+    for (int q = 0; q < 64; ++q) {
+      x[q] = (ok && q < R_N) ? float(S[(size_t)(2 * R_N + q) * n + i3]) : 0.0f;
+      m = fmaxf(m, fabsf(x[q]));
+    }
+    const int e = row_exponent(m);
+    slice_chunks<8>(x, e, scratch + (size_t)j * kATileBytes, A_SLICE, t, 0);
+    reinterpret_cast<int*>(scratch + kExpOff)[s3] = ok ? e : 0;
+  } else {
+    const int l = blockIdx.y - 1;
+    double* g = reinterpret_cast<double*>(scratch + kGathOff) + (size_t)l * kMaxSub * 64;
+    for (int idx = t; idx < BM * 64; idx += PREP_THREADS) {
+      const int s = j * BM + idx / 64, q = idx % 64;
+      double v = 0.0;
+      if (s < n_sub && q < R_N) v = S[(size_t)(l * R_N + q) * n + clamp_index(sub[l * n_sub + s], n)];
+      g[(size_t)s * 64 + q] = v;
+    }
+  }
 }
 
 __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
@@ -194,61 +233,88 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                "l"(src), "r"(bytes), "r"(mbar)
                : "memory");
 }
+__device__ __forceinline__ void load_tile(uint32_t dst, const unsigned char* scratch, int j, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(umma::smem_u32(bar)),
+               "r"(uint32_t(kATileBytes))
+               : "memory");
+  bulk_load(dst, scratch + (size_t)j * kATileBytes, uint32_t(kATileBytes), umma::smem_u32(bar));
+}
 
-__global__ void __launch_bounds__(THREADS)
-subgrid_tc_kernel(int n, int R_N, int n_sub, const double* __restrict__ S, const int* __restrict__ sub,
-                  float inv_h3, const unsigned char* __restrict__ scratch, float* __restrict__ V) {
+// One CTA per 64 consecutive (s1, s2) pairs; it slices their products into
+// shared memory once, then walks the sub-tiles of 128 s3 points: the tile's
+// S3 slices arrive by one bulk copy (the next one during the fold), one thread
+// issues the 10 slice-pair products per 16-q step, and eight warps (TMEM lane
+// quadrant x half of the 64 columns) fold the four TMEM groups into float32
+// and store V[(s1,s2)][s3].
+__global__ void __launch_bounds__(THREADS, 2)
+subgrid_tc_kernel(int n_sub, float inv_h3, const unsigned char* __restrict__ scratch, float* __restrict__ V) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = umma::smem_u32(smem_raw);
   const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
   uint8_t* smem = smem_raw + pad;
-  const uint32_t sA = raw + pad, sB = sA + NSL * A_SLICE;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + NSL * (A_SLICE + B_SLICE));  // MMA done
-  uint64_t* bbar = mbar + 1;                                                          // B tile landed
-  uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(bbar + 1);
-  const int* eB = reinterpret_cast<const int*>(scratch + kMaxTiles * kBTileBytes);
+  const uint32_t sA = raw + pad, sB = sA + uint32_t(kATileBytes);
+  uint8_t* smemB = smem + kATileBytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kATileBytes + NSL * B_SLICE);  // MMAs done
+  uint64_t* abar = mbar + 1;                                                          // S3 tile landed
+  uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(abar + 1);
+  int* eP = reinterpret_cast<int*>(smem + kATileBytes + NSL * B_SLICE + 64);  // exponents of the pair rows
+  float* fP = reinterpret_cast<float*>(eP + NP);  // 2^eP, or 0 outside the fast range
+  const int* eS = reinterpret_cast<const int*>(scratch + kExpOff);
+  const double* g1 = reinterpret_cast<const double*>(scratch + kGathOff);
+  const double* g2 = g1 + (size_t)kMaxSub * 64;
 
   const int t = threadIdx.x, warp = t >> 5;
   const long long n_pairs = (long long)n_sub * n_sub;
-  const long long p = (long long)blockIdx.x * BM + t;  // this thread's pair and TMEM lane
-  // A row: a_q = S1[q][i1] S2[q][i2] (float64 product, rounded once), q >= R_N zero
-  int eA;
-  {
-    float x[64];
-    const bool ok = p < n_pairs;
-    const int s1 = ok ? int(p / n_sub) : 0, s2 = ok ? int(p % n_sub) : 0;
-    const int i1 = clamp_index(sub[s1], n), i2 = clamp_index(sub[n_sub + s2], n);
-#pragma unroll
-    for (int q = 0; q < 64; ++q)
-      x[q] = (ok && q < R_N) ? float(S[(size_t)q * n + i1] * S[(size_t)(R_N + q) * n + i2]) : 0.0f;
-    eA = slice_row(x, smem, A_SLICE, t);
-  }
-  if (warp == 0) umma::tmem_alloc(tmem_ptr, TMEM_COLS);
+  const long long pair0 = (long long)blockIdx.x * NP;
+  const int n_tiles = (n_sub + BM - 1) / BM;
   if (t == 0) {
     umma::mbar_init(mbar, 1);
-    umma::mbar_init(bbar, 1);
+    umma::mbar_init(abar, 1);
     umma::mbar_fence_init();
   }
+  __syncthreads();
+  if (t == 0) load_tile(sA, scratch, 0, abar);  // lands while the pair rows are formed
+  {
+    // pair row k = t / 4, quarter h = t % 4 (q = 16 h .. 16 h + 15):
+    // a_q = S1[q][i1] S2[q][i2] (float64 product, rounded once)
+    const int k = t >> 2, h = t & 3;
+    const long long p = pair0 + k;
+    const bool ok = p < n_pairs;
+    const int s1 = ok ? int(p / n_sub) : 0, s2 = ok ? int(p % n_sub) : 0;
+    const double2* r1 = reinterpret_cast<const double2*>(g1 + (size_t)s1 * 64 + 16 * h);
+    const double2* r2 = reinterpret_cast<const double2*>(g2 + (size_t)s2 * 64 + 16 * h);
+    float x[16];
+    float m = 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const double2 a = __ldg(r1 + u), b = __ldg(r2 + u);
+      x[2 * u] = ok ? float(a.x * b.x) : 0.0f;
+      x[2 * u + 1] = ok ? float(a.y * b.y) : 0.0f;
+      m = fmaxf(m, fmaxf(fabsf(x[2 * u]), fabsf(x[2 * u + 1])));
+    }
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));  // the row's other quarters
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+    const int e = row_exponent(m);
+    slice_chunks<2>(x, e, smemB, B_SLICE, k, 2 * h);
+    if (h == 0) {
+      eP[k] = e;
+      fP[k] = (e > -100 && e < 100) ? pow2f(e) : 0.0f;
+    }
+  }
+  if (warp == 0) umma::tmem_alloc(tmem_ptr, TMEM_COLS);
+  umma::fence_proxy_async();  // the B slices (generic-proxy writes) -> tensor-core reads
   umma::fence_before();
   __syncthreads();
   umma::fence_after();
   const uint32_t tbase = *tmem_ptr;
-  const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * warp) << 16);
-  constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, BN);
+  const int quad = warp & 3, half = warp >> 2;  // TMEM lanes 32 quad.., columns 32 half..
+  const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * quad) << 16) + half * (NP / 2);
+  constexpr uint32_t idesc = umma::idesc_bf16_f32(BM, NP);
   bool ok_wait = true;
-  const int n_tiles = (n_sub + BN - 1) / BN;
-  umma::fence_proxy_async();  // the A slices (generic-proxy writes) -> tensor-core reads
-  __syncthreads();
   for (int j = 0; j < n_tiles; ++j) {
-    // the sub-tile's B slices (sliced once per call by slice_b_kernel): one bulk copy
+    ok_wait = ok_wait && umma::mbar_wait(abar, j & 1, kSpinLimit);
     if (t == 0) {
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(umma::smem_u32(bbar)),
-                   "r"(uint32_t(kBTileBytes))
-                   : "memory");
-      bulk_load(sB, scratch + (size_t)j * kBTileBytes, uint32_t(kBTileBytes), umma::smem_u32(bbar));
-    }
-    ok_wait = ok_wait && umma::mbar_wait(bbar, j & 1, kSpinLimit);
-    if (t == 0) {
+      umma::fence_after();
       // group g accumulates the slice pairs (a, b) with a + b = g
 #pragma unroll
       for (int g = 0; g < NSL; ++g) {
@@ -258,7 +324,7 @@ subgrid_tc_kernel(int n, int R_N, int n_sub, const double* __restrict__ S, const
           const int b = g - a;
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {
-            umma::mma_bf16(tbase + g * BN, umma::desc_k_sw128(sA + a * A_SLICE + kk * 32),
+            umma::mma_bf16(tbase + g * NP, umma::desc_k_sw128(sA + a * A_SLICE + kk * 32),
                            umma::desc_k_sw128(sB + b * B_SLICE + kk * 32), idesc, acc);
             acc = 1;
           }
@@ -268,39 +334,40 @@ subgrid_tc_kernel(int n, int R_N, int n_sub, const double* __restrict__ S, const
     }
     ok_wait = ok_wait && umma::mbar_wait(mbar, j & 1, kSpinLimit);
     umma::fence_after();
-    // fold: v = (S0 + S1 2^-8 + S2 2^-16 + S3 2^-24) 2^(eA + eB - 16) h^-3
+    __syncthreads();  // every thread has passed its wait on this phase of abar
+    // the MMAs have read this tile's S3 slices: the next tile's come during the fold
+    if (t == 0 && j + 1 < n_tiles && ok_wait) load_tile(sA, scratch, j + 1, abar);
+    // fold: v = (S0 + S1 2^-8 + S2 2^-16 + S3 2^-24) 2^(e3 + ep - 16) h^-3, the
+    // power of two applied as two exact multiplications in the normal range
+    const int s3 = j * BM + 32 * quad + (t & 31);
+    const bool s_ok = s3 < n_sub;
+    const int e3 = s_ok ? __ldg(eS + s3) : 0;
+    const bool fast3 = e3 > -100 && e3 < 100;
+    const float f3 = ldexpf(inv_h3, e3 - 16);
 #pragma unroll
-    for (int cb = 0; cb < BN / 16; ++cb) {
-      float v0[16], v1[16], v2[16], v3[16];
-      umma::tmem_ld16(lane_base + cb * 16, v0);
-      umma::tmem_ld16(lane_base + BN + cb * 16, v1);
-      umma::tmem_ld16(lane_base + 2 * BN + cb * 16, v2);
-      umma::tmem_ld16(lane_base + 3 * BN + cb * 16, v3);
+    for (int cb = 0; cb < NP / 16; ++cb) {
+      float v0[8], v1[8], v2[8], v3[8];
+      umma::tmem_ld8(lane_base + cb * 8, v0);
+      umma::tmem_ld8(lane_base + NP + cb * 8, v1);
+      umma::tmem_ld8(lane_base + 2 * NP + cb * 8, v2);
+      umma::tmem_ld8(lane_base + 3 * NP + cb * 8, v3);
       umma::tmem_ld_wait();
-      const int c0 = j * BN + cb * 16;
-      if (p < n_pairs && c0 < n_sub) {
-        float val[16];
+      if (s_ok) {
 #pragma unroll
-        for (int u = 0; u < 16; ++u) {
+        for (int u = 0; u < 8; ++u) {
+          const int k = half * (NP / 2) + cb * 8 + u;
+          const long long p = pair0 + k;
           const float f = fmaf(v3[u], 1.0f / 16777216.0f,
                                fmaf(v2[u], 1.0f / 65536.0f, fmaf(v1[u], 1.0f / 256.0f, v0[u])));
-          const int e = (c0 + u < n_sub) ? __ldg(eB + c0 + u) : 0;
-          val[u] = ok_wait ? ldexpf(f, eA + e - 16) * inv_h3 : __int_as_float(0x7fc00000);
-        }
-        float* out = V + p * n_sub + c0;
-        if ((n_sub & 15) == 0) {  // 16 values, 64-byte aligned: four 16-byte stores
-#pragma unroll
-          for (int u = 0; u < 16; u += 4)
-            *reinterpret_cast<float4*>(out + u) = make_float4(val[u], val[u + 1], val[u + 2], val[u + 3]);
-        } else {
-#pragma unroll
-          for (int u = 0; u < 16; ++u)
-            if (c0 + u < n_sub) out[u] = val[u];
+          const float fp = fP[k];
+          float val = (fast3 && fp != 0.0f) ? (f * fp) * f3 : ldexpf(f, e3 + eP[k] - 16) * inv_h3;
+          if (!ok_wait) val = __int_as_float(0x7fc00000);
+          if (p < n_pairs) __stcs(V + p * n_sub + s3, val);  // a warp writes 32 consecutive s3
         }
       }
     }
     umma::fence_before();
-    __syncthreads();  // B slices and TMEM are rewritten by the next sub-tile
+    __syncthreads();  // TMEM is rewritten by the next tile's MMAs
     umma::fence_after();
   }
   if (warp == 0) umma::tmem_dealloc(tbase, TMEM_COLS);
@@ -355,14 +422,14 @@ extern "C" int lattice_potential_sum(const cpc_kernel* P, const int* L, const in
   const double inv_h3 = 1.0 / (P->h * P->h * P->h);
   if (precision == CPC_FP64) return launch_subgrid<double>(n, P->R_N, n_sub, S, sub, inv_h3, V, s);
   if (P->R_N <= 64) {  // tensor cores
-    const long long blocks = ((long long)n_sub * n_sub + lat::BM - 1) / lat::BM;
+    const long long blocks = ((long long)n_sub * n_sub + lat::NP - 1) / lat::NP;
     CPC_CUDA(cudaFuncSetAttribute(lat::subgrid_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   int(lat::kSmemBytes)));
-    lat::slice_b_kernel<<<(n_sub + lat::BN - 1) / lat::BN, lat::BN, 0, s>>>(n, P->R_N, n_sub, S, sub, P->d_lat);
-    CPC_LAUNCH_CHECK("slice_b_kernel");
+    lat::prep_kernel<<<dim3((n_sub + lat::BM - 1) / lat::BM, 3), lat::PREP_THREADS, 0, s>>>(n, P->R_N, n_sub, S, sub,
+                                                                                     P->d_lat);
+    CPC_LAUNCH_CHECK("lattice prep_kernel");
     const int slot = timing_begin("subgrid_tc_kernel", s);
-    lat::subgrid_tc_kernel<<<(unsigned)blocks, lat::THREADS, lat::kSmemBytes, s>>>(n, P->R_N, n_sub, S, sub,
-                                                                                   float(inv_h3), P->d_lat,
+    lat::subgrid_tc_kernel<<<(unsigned)blocks, lat::THREADS, lat::kSmemBytes, s>>>(n_sub, float(inv_h3), P->d_lat,
                                                                                    static_cast<float*>(V));
     timing_end(slot, s);
     CPC_LAUNCH_CHECK("subgrid_tc_kernel");
