@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "cpc_internal.h"
+#include "pow2.cuh"
 #include "umma.cuh"
 
 namespace cpc {
@@ -150,9 +151,6 @@ constexpr size_t kScratchBytes = kGathOff + size_t(2) * kMaxSub * 64 * sizeof(do
 // NCH 16-byte chunks (8 values each, chunks c0 .. c0+NCH-1 of a 64-value row)
 // -> NSL bf16 slices under the row exponent e (|x| < 2^e), written into
 // 128-byte-swizzled K-major rows at `base` (slice k at base + k * slice_bytes)
-// 2^k as a float, k in [-126, 127]
-__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
-
 template <int NCH>
 __device__ __forceinline__ void slice_chunks(const float* x, int e, uint8_t* base, uint32_t slice_bytes, int row,
                                              int c0) {
