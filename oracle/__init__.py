@@ -19,7 +19,9 @@ Modules and the passages they follow (Khoromskaia & Khoromskij, arXiv:1504.06289
                       giving E_H, and its adjoint.
 * ``coulomb``         Coulomb matrix J_{mu nu} = <G_mu . G_nu, V_H> (Sec. 3.1).
 * ``lattice``         assembled lattice sums (Sec. 5.1, Eqs. CoulombLattice,
-                      CoulombLatTensCan) and their evaluation on a sub-grid.
+                      CoulombLatTensCan), their evaluation on a sub-grid, and the
+                      interaction energy of the lattice charges (Sec. 5.3,
+                      Eqs. EnergyLatSum, EnergyLattice).
 * ``closed_forms``    analytic Gaussian Coulomb results used only to pin the
                       oracle (not part of the method).
 
