@@ -99,8 +99,13 @@ def interaction_energy_tensor(Pm: np.ndarray, edges: list, n: int, h: float, Z: 
     T = []
     for e in edges:
         e = np.asarray(e, dtype=np.int64)
-        s = assembled_vectors(Pm, e, n)
-        T.append(0.5 * (s[:, e - 1] + s[:, e]).sum(axis=1))
+        # the assembled vectors traced at the 2L cells around the points
+        # (the same sums over k as assembled_vectors, at those cells only)
+        cells = np.concatenate([e - 1, e])
+        s = np.zeros((Pm.shape[0], len(cells)))
+        for ek in e:
+            s += Pm[:, cells - ek + n]
+        T.append(0.5 * s.sum(axis=1))
     t0 = 0.5 * (Pm[:, n - 1] + Pm[:, n])
     count = float(len(edges[0]) * len(edges[1]) * len(edges[2]))
     lattice_sum = float(np.sum(T[0] * T[1] * T[2]))
