@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--rf", type=int, default=None,
                     help="override the rank R_f (profiling a smaller case of the same kernels)")
     ap.add_argument("--workload", default=WORKLOAD,
-                    choices=[WORKLOAD, "basis80_n4096", "density200_n4096", "lattice32_n16384"],
+                    choices=[WORKLOAD, "basis80_n4096", "density200_n4096", "lattice32_n16384",
+                             "lattice_energy256_n16384"],
                     help="the default is the headline workload; the others time their own rows")
     return ap.parse_args()
 
@@ -684,6 +685,69 @@ def run_lattice(args, ws, rank, local):
           cpu_baseline=cpu)
 
 
+def run_lattice_energy(args, ws, rank, local):
+    """f1: interaction energy of a 256^3 hydrogen lattice (charges 2 bohr apart,
+    64 cells) by the traced tensor lattice sum with the singular-point
+    correction (Sec. 5.3, Eq. EnergyLattice); float64, one E_L per step."""
+    import torch
+    import paper_1504_06289_gb300 as cpc
+    from oracle import kernel_vectors as okv
+    from oracle import lattice as olat
+    from oracle import sinc as osinc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name = "lattice_energy256_n16384"
+    cfg = workloads.CONFIGS[name]
+    n, b, M, L, cells = cfg["n"], cfg["b"], cfg["M"], cfg["L"], cfg["cells"]
+    h = 2 * b / n
+    edges = [workloads.lattice_energy_edges(n, L, cells)] * 3
+    P = cpc.make_newton_kernel(n, b, M, "master", device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ms = _timed(stream, lambda: cpc.lattice_interaction_energy(P, edges), args.steps, args.warmup)
+    torch.cuda.synchronize()
+    cpc.kernel_timing(True)
+    E = cpc.lattice_interaction_energy(P, edges)
+    torch.cuda.synchronize()
+    cpc.kernel_timing(False)
+    k_ms, k_n = cpc.kernel_timing_read("lattice_energy_kernel")
+    p_ms, _ = cpc.kernel_timing_read("lattice_pairs_kernel")
+    # end to end: host edge lists in, E_L read back, every step
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_val = cpc.lattice_interaction_energy(P, edges).item()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    if rank != 0:
+        return
+    # per axis, q and distinct difference d: p~[d-1] + p~[d] and one multiply-add
+    n_diff = sum(len(np.unique(np.subtract.outer(e.astype(np.int64), e))) for e in edges)
+    flops = 3 * P.R_N * n_diff
+    fp64_peak = 1250.0  # GFLOP/s: the nominal float64 rate of GB300
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        t, w = osinc.master_nodes(n, b, M)
+        Pm = okv.master_kernel_vectors(n, b, t, w)
+        t0 = time.perf_counter()
+        E0 = olat.interaction_energy_tensor(Pm, edges, n, h)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / dt, "unit": "evaluations/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "one E_L of the same lattice (traced tensor sum, master vectors given)",
+               "rel_diff": abs(E.item() / E0 - 1)}
+    _line(args, ws, "lattice interaction energy evaluations/s", ws / (ms * 1e-3), "evaluations/s", ms, "f64",
+          {"workload": name, "n": n, "L": L, "cells_per_spacing": cells, "R_N": P.R_N},
+          E_L=E.item(), E_L_direct=olat.interaction_energy_direct(edges, h),
+          kernel_ms={"lattice_pairs_kernel": p_ms, "lattice_energy_kernel": k_ms},
+          e2e={"value": 1e3 / e2e_ms, "unit": "evaluations/s", "h2d_bytes_per_step": 4 * 3 * L,
+               "d2h_bytes_per_step": 8},
+          roofline={"kernel": "lattice_energy_kernel", "bound": "alu", "kernel_ms": k_ms,
+                    "achieved": flops / (k_ms * 1e-3) / 1e9 if k_n else None, "peak": fp64_peak,
+                    "unit": "GFLOP/s", "frac": flops / (k_ms * 1e-3) / 1e9 / fp64_peak if k_n else None,
+                    "traffic": None, "note": "float64 flops of the traced sums over the distinct differences "
+                                             "per launch / event time (a microsecond launch: latency-bound); "
+                                             "peak: nominal GB300 float64 rate"},
+          gpu_launches=2 * args.steps, cpu_baseline=cpu)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -695,6 +759,8 @@ def main():
         run_adjoint(args, ws, rank, local)
     elif args.workload == "lattice32_n16384":
         run_lattice(args, ws, rank, local)
+    elif args.workload == "lattice_energy256_n16384":
+        run_lattice_energy(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -285,11 +285,34 @@ int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* off, int n_
 int lattice_potential_sum(const cpc_kernel* master, const int* L, const int* edges, double* S,
                           int n_sub, const int* sub, void* V, int precision, void* stream);
 
+/* Interaction energy of equal charges Z on the tensor lattice of grid-cell
+ * edges (Sec. 5.3): the sum E_L = 1/2 sum_{k != j} Z^2 / |x_k - x_j|
+ * (Eq. EnergyLatSum) as the rank-R_N lattice sum traced at the lattice points
+ * with the singular-point correction (Eq. EnergyLattice):
+ *   E_L = Z^2 h^-3 / 2 sum_q (prod_l T_q^(l) - L[0] L[1] L[2] t0_q^3),
+ *   T_q^(l) = 1/2 sum_{j,k < L[l]} (p~_q[e_j - e_k - 1] + p~_q[e_j - e_k]),
+ *   t0_q = (p~_q[-1] + p~_q[0]) / 2,
+ * in float64 (the pairs of each axis counted once per difference d = e_j - e_k,
+ * then O(R_N) work per distinct d): a charge at edge e is the corner shared by the
+ * cells e-1 and e of each axis, and the tensor value at a lattice point is
+ * read as the mean over those 8 cells (a cube of edge 2h centred on the point,
+ * whose mean of the harmonic 1/r has no second-order error).  Accurate when
+ * the charges are many cells apart (about 30 or more).  master: a MASTER
+ * kernel; L: host int32[3], each in [0, 256]; edges: host int32 array of
+ * L[0]+L[1]+L[2] entries (axis 0 first), each in [1, n-1]; Z finite; E_L:
+ * device float64, written once.  Uses the kernel's scratch (calls on
+ * unordered streams sharing one kernel race on it).  Returns CPC_OK,
+ * CPC_ERR_INVALID (not a MASTER kernel, NULL argument, edge out of range,
+ * Z not finite), CPC_ERR_UNSUPPORTED (L out of range) or CPC_ERR_CUDA; no
+ * launch happens on an error. */
+int lattice_interaction_energy(const cpc_kernel* master, const int* L, const int* edges, double Z,
+                               double* E_L, void* stream);
+
 /* ---- status -------------------------------------------------------------- */
 /* ---- kernel timing (measurement support; the paper has no counterpart) -----
  * While enabled, every launch of spectra_kernel, conv_kernel,
- * slice_rows_kernel, gemm3_tc_kernel, subgrid_tc_kernel and
- * adjoint_gemm_kernel is bracketed by two CUDA events recorded on the stream the
+ * slice_rows_kernel, gemm3_tc_kernel, subgrid_tc_kernel, lattice_pairs_kernel,
+ * lattice_energy_kernel and adjoint_gemm_kernel is bracketed by two CUDA events recorded on the stream the
  * kernel is launched on (up to 8192 launches; later ones go unrecorded).
  * cpc_kernel_timing(1) creates the events on first use and clears earlier
  * records; cpc_kernel_timing(0) stops recording and keeps the records.

@@ -25,7 +25,7 @@ __all__ = [
     "cp_convolve", "cp_hartree_energy", "cp_hartree_energy_from_factors",
     "cp_factor_spectra", "cp_convolve_from_spectra", "cp_hartree_energy_from_spectra",
     "cp_hartree_energy_noalloc", "cp_hartree_energy_adjoint", "cp_gaussian_param_grad",
-    "coulomb_matrix", "lattice_potential_sum", "CPHartreeEnergy", "CpcError",
+    "coulomb_matrix", "lattice_potential_sum", "lattice_interaction_energy", "CPHartreeEnergy", "CpcError",
 ]
 
 
@@ -366,6 +366,19 @@ def lattice_potential_sum(P: NewtonKernel, edges, sub: torch.Tensor | None = Non
     check(lib.lattice_potential_sum(P.handle, L, flat.ctypes.data, _ptr(S), n_sub, _ptr(sub), _ptr(V),
                                     _prec(precision), _stream(stream)), "lattice_potential_sum")
     return S, V
+
+
+def lattice_interaction_energy(P: NewtonKernel, edges, Z: float = 1.0, stream=None) -> torch.Tensor:
+    """Interaction energy E_L of equal charges Z at the grid-cell edges `edges`
+    (three int arrays, each entry in [1, n-1]) of a MASTER kernel (Sec. 5.3,
+    Eq. EnergyLattice): a 0-d float64 device tensor."""
+    lib = load()
+    L = (C.c_int * 3)(*[len(e) for e in edges])
+    flat = np.ascontiguousarray(np.concatenate([np.asarray(e, dtype=np.int32) for e in edges]))
+    E = torch.empty((), dtype=torch.float64, device=P.device)
+    check(lib.lattice_interaction_energy(P.handle, L, flat.ctypes.data, float(Z), _ptr(E), _stream(stream)),
+          "lattice_interaction_energy")
+    return E
 
 
 class CPHartreeEnergy(torch.autograd.Function):

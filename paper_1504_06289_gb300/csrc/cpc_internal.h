@@ -85,7 +85,7 @@ void build_twiddles(int n, std::vector<double>& tw_re, std::vector<double>& tw_i
 
 // device-side builders (spectra.cu)
 int build_pass_twiddles(cpc_kernel* P, cudaStream_t s);
-size_t lattice_scratch_bytes();
+size_t lattice_scratch_bytes(int n);
 int compute_kernel_spectrum(cpc_kernel* P, cudaStream_t s);
 
 // spectra of U columns into workspace (float64 and/or float32 copies)

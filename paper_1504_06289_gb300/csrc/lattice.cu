@@ -21,6 +21,9 @@
 //                     the S3 rows and gathers the S1, S2 sub-grid values once
 //                     per call.
 #include <cuda_bf16.h>
+#include <algorithm>
+#include <atomic>
+#include <cmath>
 #include <cuda_runtime.h>
 
 #include "cpc_internal.h"
@@ -372,7 +375,127 @@ subgrid_tc_kernel(int n_sub, float inv_h3, const unsigned char* __restrict__ scr
 }
 }  // namespace lat
 
-size_t lattice_scratch_bytes() { return lat::kScratchBytes; }
+// the MASTER kernel's scratch: the sub-grid evaluation's (above), or the
+// interaction energy's [3][R_N] axis sums (and list lengths) in the first
+// 4 KB, then per axis a histogram of 2n bins and a list of up to 2n
+// (d, count) pairs, whichever is larger
+constexpr size_t kEnergyListOff = 4096;
+size_t lattice_scratch_bytes(int n) {
+  return std::max(lat::kScratchBytes, kEnergyListOff + size_t(3) * 2 * n * 3 * sizeof(int));
+}
+
+// ---- interaction energy of the lattice charges (Sec. 5.3, Eq. EnergyLattice) ----
+// A charge sits at the grid-cell edge e, the corner of the cells e-1 and e of
+// each axis; the potential sum traced at a lattice point is the mean of those
+// 8 cells (the doubled lattice of the traced 2L sub-tensor).  Per axis,
+//   T_q = 1/2 sum_{j,k} (p~_q[e_j - e_k - 1] + p~_q[e_j - e_k])
+//       = 1/2 sum_d c(d) (p~_q[d - 1] + p~_q[d]),
+// c(d) the number of point pairs of the axis at difference d, the same for
+// every q.  lattice_pairs_kernel counts the pairs of one slice of the L^2 in a
+// shared-memory histogram over the 2n possible d and adds its nonzero bins to
+// the axis histogram; lattice_diffs_kernel lists the nonzero bins in order of
+// d; lattice_energy_kernel (block q, l) sums over that list.  A regular
+// lattice of L points has 2L-1 differences, so the work per q is O(L).
+constexpr int kPairChunks = 32;
+constexpr int kPairThreads = 1024;
+constexpr int kEnergyThreads = 128;
+
+__global__ void __launch_bounds__(kPairThreads)
+lattice_pairs_kernel(int n, Edges ed, int* __restrict__ ghist) {
+  extern __shared__ int hist[];  // [2n]: c(d) at d + n
+  __shared__ int se[kMaxLattice];
+  const int c = blockIdx.x, l = blockIdx.y, t = threadIdx.x, nb = 2 * n;
+  int base = 0;
+  for (int a = 0; a < l; ++a) base += ed.count[a];
+  const int L = ed.count[l];
+  const int pairs = L * L, chunk = (pairs + kPairChunks - 1) / kPairChunks;
+  const int p0 = c * chunk, p1 = min(pairs, p0 + chunk);
+  if (p0 >= p1) return;  // nothing in this slice (uniform over the block)
+  for (int i = t; i < nb; i += kPairThreads) hist[i] = 0;
+  for (int i = t; i < L; i += kPairThreads) se[i] = ed.e[base + i];
+  __syncthreads();
+  for (int p = p0 + t; p < p1; p += kPairThreads)
+    atomicAdd(&hist[se[p / L] - se[p % L] + n], 1);  // d + n in [2, 2n-2]
+  __syncthreads();
+  int* gh = ghist + (size_t)l * nb;
+  for (int i = t; i < nb; i += kPairThreads)
+    if (hist[i]) atomicAdd(&gh[i], hist[i]);
+}
+
+// the nonzero bins of axis blockIdx.x in order of d, as pairs (d, c(d))
+__global__ void __launch_bounds__(kPairThreads)
+lattice_diffs_kernel(int n, const int* __restrict__ ghist, int* __restrict__ list, int* __restrict__ list_len) {
+  __shared__ int wsum[kPairThreads / 32];
+  const int l = blockIdx.x, t = threadIdx.x, nb = 2 * n;
+  const int* gh = ghist + (size_t)l * nb;
+  // thread t owns bins [t * per, (t+1) * per)
+  const int per = (nb + kPairThreads - 1) / kPairThreads;
+  const int b0 = t * per, b1 = min(nb, b0 + per);
+  int cnt = 0;
+  for (int i = b0; i < b1; ++i) cnt += gh[i] != 0;
+  // exclusive scan of cnt over the block
+  int incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if ((t & 31) >= o) incl += v;
+  }
+  if ((t & 31) == 31) wsum[t >> 5] = incl;
+  __syncthreads();
+  int off = incl - cnt;
+  for (int w = 0; w < (t >> 5); ++w) off += wsum[w];
+  int* out = list + (size_t)l * 2 * nb;  // up to 2n pairs
+  for (int i = b0; i < b1; ++i) {
+    const int v = gh[i];
+    if (v) {
+      out[2 * off] = i - n;
+      out[2 * off + 1] = v;
+      ++off;
+    }
+  }
+  if (t == kPairThreads - 1) list_len[l] = off;
+}
+
+__global__ void __launch_bounds__(kEnergyThreads)
+lattice_energy_kernel(int n, int R_N, const double* __restrict__ Pm, const int* __restrict__ list,
+                      const int* __restrict__ list_len, double* __restrict__ T) {
+  __shared__ double red[kEnergyThreads / 32];
+  const int q = blockIdx.x, l = blockIdx.y, t = threadIdx.x;
+  const double* row = Pm + (size_t)q * 2 * n + n;  // row[j] = p~_q[j], j in [-n, n)
+  const int* dl = list + (size_t)l * 4 * n;
+  const int len = list_len[l];
+  double s = 0.0;
+  for (int i = t; i < len; i += kEnergyThreads) {
+    const int d = dl[2 * i];  // in [-(n-2), n-2]
+    s = fma(double(dl[2 * i + 1]), row[d - 1] + row[d], s);
+  }
+  // fixed-order reduction: the same sum on every call
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((t & 31) == 0) red[t >> 5] = s;
+  __syncthreads();
+  if (t == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < kEnergyThreads / 32; ++w) tot += red[w];
+    T[(size_t)l * R_N + q] = 0.5 * tot;
+  }
+}
+
+// E_L = Z^2 h^-3 / 2 sum_q (prod_l T[l][q] - L1 L2 L3 t0_q^3), summed in order
+// of q; products and the difference rounded separately (no fused multiply-add),
+// so that a single charge gives exactly 0
+__global__ void lattice_energy_sum_kernel(int n, int R_N, const double* __restrict__ Pm, const double* __restrict__ T,
+                                          double count, double scale, double* __restrict__ E) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < R_N; ++q) {
+      const double* row = Pm + (size_t)q * 2 * n + n;
+      const double t0 = 0.5 * (row[-1] + row[0]);
+      const double lat = __dmul_rn(__dmul_rn(T[q], T[R_N + q]), T[2 * R_N + q]);
+      const double self = __dmul_rn(count, __dmul_rn(__dmul_rn(t0, t0), t0));
+      s = __dadd_rn(s, __dsub_rn(lat, self));
+    }
+    *E = __dmul_rn(scale, s);
+  }
+}
 
 template <typename TV>
 int launch_subgrid(int n, int R_N, int n_sub, const double* S, const int* sub, double inv_h3, void* V,
@@ -434,4 +557,57 @@ extern "C" int lattice_potential_sum(const cpc_kernel* P, const int* L, const in
     return CPC_OK;
   }
   return launch_subgrid<float>(n, P->R_N, n_sub, S, sub, inv_h3, V, s);
+}
+
+extern "C" int lattice_interaction_energy(const cpc_kernel* P, const int* L, const int* edges, double Z, double* E_L,
+                                          void* stream) {
+  clear_error();
+  if (!P || P->kind != CPC_KERNEL_MASTER)
+    return fail(CPC_ERR_INVALID, "lattice_interaction_energy: needs a MASTER kernel");
+  if (!L || !edges || !E_L) return fail(CPC_ERR_INVALID, "lattice_interaction_energy: NULL argument");
+  if (!std::isfinite(Z)) return fail(CPC_ERR_INVALID, "lattice_interaction_energy: Z must be finite");
+  const int n = P->n;
+  Edges ed;
+  int total = 0;
+  for (int l = 0; l < 3; ++l) {
+    if (L[l] < 0 || L[l] > kMaxLattice)
+      return fail(CPC_ERR_UNSUPPORTED, "lattice_interaction_energy: L per axis must be in [0, 256]");
+    ed.count[l] = L[l];
+    for (int k = 0; k < L[l]; ++k) {
+      const int e = edges[total + k];
+      if (e < 1 || e > n - 1)
+        return fail(CPC_ERR_INVALID, "lattice_interaction_energy: edge index outside [1, n-1]");
+      ed.e[total + k] = e;
+    }
+    total += L[l];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // scratch: T [3][R_N] doubles and the list lengths, then the histograms
+  // [3][2n] and the difference lists [3][2n][2]
+  double* T = reinterpret_cast<double*>(P->d_lat);
+  int* list_len = reinterpret_cast<int*>(P->d_lat + kEnergyListOff) - 4;
+  int* ghist = reinterpret_cast<int*>(P->d_lat + kEnergyListOff);
+  int* list = ghist + size_t(3) * 2 * n;
+  const size_t hist_bytes = size_t(2) * n * sizeof(int);
+  CPC_CUDA(cudaMemsetAsync(ghist, 0, 3 * hist_bytes, s));
+  static std::atomic<int> pairs_smem{0};  // dynamic shared memory already allowed for lattice_pairs_kernel
+  if (int(hist_bytes) > pairs_smem.load()) {
+    CPC_CUDA(cudaFuncSetAttribute(lattice_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(hist_bytes)));
+    pairs_smem.store(int(hist_bytes));
+  }
+  const int pslot = timing_begin("lattice_pairs_kernel", s);
+  lattice_pairs_kernel<<<dim3(kPairChunks, 3), kPairThreads, hist_bytes, s>>>(n, ed, ghist);
+  timing_end(pslot, s);
+  CPC_LAUNCH_CHECK("lattice_pairs_kernel");
+  lattice_diffs_kernel<<<3, kPairThreads, 0, s>>>(n, ghist, list, list_len);
+  CPC_LAUNCH_CHECK("lattice_diffs_kernel");
+  const int slot = timing_begin("lattice_energy_kernel", s);
+  lattice_energy_kernel<<<dim3(P->R_N, 3), kEnergyThreads, 0, s>>>(n, P->R_N, P->d_p, list, list_len, T);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("lattice_energy_kernel");
+  const double count = double(L[0]) * double(L[1]) * double(L[2]);
+  const double scale = 0.5 * Z * Z / (P->h * P->h * P->h);
+  lattice_energy_sum_kernel<<<1, 32, 0, s>>>(n, P->R_N, P->d_p, T, count, scale, E_L);
+  CPC_LAUNCH_CHECK("lattice_energy_sum_kernel");
+  return CPC_OK;
 }

@@ -260,7 +260,7 @@ int make_newton_kernel(int n, double b, int M, int kind, void* stream, cpc_kerne
   if (e == cudaSuccess) e = cudaMemcpyAsync(P->d_p, P->p.data(), sizeof(double) * P->p.size(), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: table upload"); cleanup(); return st; }
   if (master) {
-    e = cudaMalloc(&P->d_lat, lattice_scratch_bytes());
+    e = cudaMalloc(&P->d_lat, lattice_scratch_bytes(n));
     if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: lattice scratch"); cleanup(); return st; }
   }
   if (!master) {

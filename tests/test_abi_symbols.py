@@ -23,10 +23,10 @@ def lib():
     return ctypes.CDLL(LIB)
 
 
-def test_header_declares_the_five_entry_points():
+def test_header_declares_the_main_entry_points():
     names = declared()
     for n in ("make_newton_kernel", "cp_convolve", "cp_hartree_energy", "coulomb_matrix",
-              "lattice_potential_sum"):
+              "lattice_potential_sum", "lattice_interaction_energy"):
         assert n in names
 
 

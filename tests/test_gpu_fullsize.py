@@ -215,3 +215,19 @@ def test_lattice32_n16384(cpc, precision, tol):
     Q = np.array(np.meshgrid(q, q, q, indexing="ij")).reshape(3, -1).T
     ref = np.array([np.sum(1.0 / np.linalg.norm(Q - xi, axis=1)) for xi in x])
     assert np.max(np.abs(Vs / ref - 1)) < 5e-5
+
+
+@pytest.mark.parametrize("name", ["lattice_energy24_n4096", "lattice_energy256_n16384"])
+def test_lattice_interaction_energy_fullsize(cpc, name):
+    # hydrogen lattices of the printed energy table (Sec. 5.3): 24^3 and 256^3
+    # charges 2 bohr apart; the device sum against the oracle's traced tensor
+    # sum and against the direct sum of Eq. EnergyLatSum
+    cfg = workloads.CONFIGS[name]
+    n, b, M, L, cells = cfg["n"], cfg["b"], cfg["M"], cfg["L"], cfg["cells"]
+    h = 2 * b / n
+    edges = [workloads.lattice_energy_edges(n, L, cells)] * 3
+    P = cpc.make_newton_kernel(n, b, M, "master")
+    E = cpc.lattice_interaction_energy(P, edges).item()
+    _, _, Pm0 = oracle_master_kernel(n, b, M)
+    assert abs(E / olat.interaction_energy_tensor(Pm0, edges, n, h) - 1) < 1e-12
+    assert abs(E / olat.interaction_energy_direct(edges, h) - 1) < 2e-8

@@ -315,6 +315,34 @@ def test_lattice_sum(cpc, precision, tol):
     assert np.max(np.abs(V.cpu().numpy() / V0 - 1)) < tol
 
 
+def test_lattice_interaction_energy(cpc):
+    # Sec. 5.3 Eq. EnergyLattice: the device sum against the oracle's traced
+    # tensor sum on the same master kernel, and against the direct sum
+    n, b, M = 512, 16.0, 64
+    h = 2 * b / n
+    P = cpc.make_newton_kernel(n, b, M, "master")
+    _, _, Pm0 = oracle_master_kernel(n, b, M)
+    cube = workloads.lattice_energy_edges(n, 8, 32)
+    cases = [([cube] * 3, 1.0), ([np.array([40, 97, 130]), np.array([60, 100, 200, 333, 400]),
+                                  np.array([250, 300])], 2.0),
+             ([cube, cube[:3], cube[1:7]], 0.5)]
+    for edges, Z in cases:
+        E = cpc.lattice_interaction_energy(P, edges, Z).item()
+        E0 = olat.interaction_energy_tensor(Pm0, edges, n, h, Z)
+        assert abs(E / E0 - 1) < 1e-12
+        assert abs(E / olat.interaction_energy_direct(edges, h, Z) - 1) < 5e-8
+    # one charge: the singular-point correction cancels the traced sum exactly
+    assert cpc.lattice_interaction_energy(P, [[100], [7], [511]]).item() == 0.0
+    # no charges along an axis
+    assert cpc.lattice_interaction_energy(P, [cube, [], cube]).item() == 0.0
+    from paper_1504_06289_gb300 import CpcError
+    for bad in ([[0], [5], [5]], [[5], [512], [5]]):  # edges must lie in [1, n-1]
+        with pytest.raises(CpcError):
+            cpc.lattice_interaction_energy(P, bad)
+    with pytest.raises(CpcError):
+        cpc.lattice_interaction_energy(cpc.make_newton_kernel(64, 4.0, 5), [[5], [5], [5]])  # CONV kernel
+
+
 def test_invalid_arguments_fail_without_launch(cpc):
     from paper_1504_06289_gb300 import CpcError
     with pytest.raises(CpcError):

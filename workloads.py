@@ -36,6 +36,9 @@ CONFIGS = {
     # 32^3 lattice of unit charges with spacing 4 bohr, 16384^3 grid, 512^3 sub-grid.
     "lattice32_n16384": dict(n=16384, b=64.0, M=30, L=32, spacing=4.0, sub=512,
                              n_check=1000),
+    # interaction energy of hydrogen lattices, 2 bohr apart (128 or 64 cells)
+    "lattice_energy24_n4096": dict(n=4096, b=32.0, M=64, L=24, cells=128),
+    "lattice_energy256_n16384": dict(n=16384, b=256.0, M=64, L=256, cells=64),
 }
 
 
@@ -135,6 +138,14 @@ def lattice_geometry(n: int, L: int, sub: int) -> dict:
     stride = n // sub
     sub_idx = (stride // 2 + stride * np.arange(sub)).astype(np.int32)
     return dict(edges=edges, sub_idx=sub_idx)
+
+
+def lattice_energy_edges(n: int, L: int, cells: int) -> np.ndarray:
+    """Grid-cell edges of L charges ``cells`` cells apart, centred in the n-cell box."""
+    off = (n - (L - 1) * cells) // 2
+    if off < 1:
+        raise ValueError("lattice does not fit the box")
+    return (off + cells * np.arange(L)).astype(np.int32)
 
 
 def check_points(sub: int, count: int, seed: int) -> np.ndarray:
