@@ -22,6 +22,8 @@ Modules and the passages they follow (Khoromskaia & Khoromskij, arXiv:1504.06289
                       CoulombLatTensCan), their evaluation on a sub-grid, and the
                       interaction energy of the lattice charges (Sec. 5.3,
                       Eqs. EnergyLatSum, EnergyLattice).
+* ``nuclear``         nuclear potential of a molecule by windowed shifts of the
+                      master kernel and its Galerkin matrix (Sec. 3.3).
 * ``closed_forms``    analytic Gaussian Coulomb results used only to pin the
                       oracle (not part of the method).
 

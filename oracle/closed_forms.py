@@ -5,6 +5,8 @@ method; these are textbook integrals the discrete method must approach as the
 grid is refined and M grows.
 
 * potential of exp(-a |y - A|^2):  (pi/a)^{3/2} erf(sqrt(a) r) / r,  r = |x - A|
+* nuclear attraction of exp(-a|x-A|^2) by a unit charge at C:
+  -(2 pi / a) F0(a |A - C|^2)
 * Coulomb integral of exp(-a|x-A|^2) and exp(-b|y-B|^2):
   2 pi^{5/2} / (a b sqrt(a+b)) * F0(a b/(a+b) |A - B|^2),
   F0(T) = (1/2) sqrt(pi/T) erf(sqrt(T)), F0(0) = 1  (the s-type Boys function).
@@ -73,3 +75,11 @@ def mixture_energy_grad(a, X, c):
     Mfull = pref * F0
     dc = 2.0 * Mfull @ c
     return da, dX, dc
+
+
+def nuclear_attraction(a, A, C) -> np.ndarray:
+    """-(a|C): integral of exp(-a |x - A|^2) / |x - C| over R^3, negated
+    (attraction by a unit charge at C): -(2 pi / a) F0(a |A - C|^2)."""
+    a = np.asarray(a, dtype=np.float64)
+    d2 = np.sum(np.square(np.asarray(A) - np.asarray(C)), axis=-1)
+    return -2.0 * math.pi / a * boys0(a * d2)
