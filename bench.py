@@ -53,7 +53,7 @@ def parse():
                     help="override the rank R_f (profiling a smaller case of the same kernels)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "basis80_n4096", "density200_n4096", "lattice32_n16384",
-                             "lattice_energy256_n16384"],
+                             "lattice_energy256_n16384", "nuclear80_n4096"],
                     help="the default is the headline workload; the others time their own rows")
     return ap.parse_args()
 
@@ -685,6 +685,82 @@ def run_lattice(args, ws, rank, local):
           cpu_baseline=cpu)
 
 
+def run_nuclear(args, ws, rank, local):
+    """f3: the nuclear-attraction matrix (3240 entries) of the 80-function basis:
+    master kernel windowed onto 10 nuclei (Sec. 3.3) and contracted with the
+    item factors; the item factors are built once (the Coulomb workload's)."""
+    import torch
+    import paper_1504_06289_gb300 as cpc
+    from oracle import coulomb as ocoul
+    from oracle import kernel_vectors as okv
+    from oracle import nuclear as onuc
+    from oracle import sinc as osinc
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name = "nuclear80_n4096"
+    cfg = workloads.CONFIGS[name]
+    n, b, M = cfg["n"], cfg["b"], cfg["M"]
+    basis = workloads.basis_for(name, 3 + rank)
+    nb = cfg["n_basis"]
+    nuc, Z = workloads.nuclei_for(basis, n, b, 5 + rank)
+    P = cpc.make_newton_kernel(n, b, M, "master", device=dev)
+    first = basis["fn_first"]
+    centre = np.repeat(basis["fn_centre"], np.diff(first), axis=0)
+    t = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
+    items = ocoul.item_list(nb)
+    ia, ib, _, off = ocoul.item_pairs(basis, items)
+    G = cpc.cp_sample_gaussians(n, b, t(basis["prim_alpha"]), t(centre))
+    U_it, c_it = cpc.cp_hadamard_pairs(G, t(ia, torch.int32), t(ib, torch.int32), t(basis["prim_d"]))
+    off_t, Z_t = t(off, torch.int32), t(Z)
+    n_factors, n_nuc = U_it.shape[1], nuc.shape[1]
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    for prec, steps in (("fp32", args.steps), ("fp64", max(1, min(args.steps, 3)))):
+        V, F = cpc.nuclear_matrix(P, off_t, U_it, c_it, nuc, Z_t, prec)
+        wsb = torch.empty(max(256, cpc.load().nuclear_matrix_workspace(P.handle, len(items), n_factors, n_nuc,
+                                                                        cpc._prec(prec))), dtype=torch.uint8,
+                          device=dev)
+        ms = _timed(stream, lambda: cpc.nuclear_matrix(P, off_t, U_it, c_it, nuc, Z_t, prec, F=F, ws=wsb), steps,
+                    max(1, min(args.warmup, 3)))
+        torch.cuda.synchronize()
+        cpc.kernel_timing(True)
+        V, _ = cpc.nuclear_matrix(P, off_t, U_it, c_it, nuc, Z_t, prec, F=F, ws=wsb)
+        torch.cuda.synchronize()
+        cpc.kernel_timing(False)
+        res[prec] = {"ms_per_step": ms, "kernel_ms": {k: cpc.kernel_timing_read(k)[0]
+                                                      for k in ("slice_rows_kernel", "gemm3_tc_kernel")},
+                     "V_trace": float(V.cpu().numpy()[[items.index((m, m)) for m in range(nb)]].sum())}
+        del F, wsb
+        torch.cuda.empty_cache()
+    if rank != 0:
+        return
+    res["fp32"]["rel_diff_trace_vs_fp64"] = abs(res["fp32"]["V_trace"] / res["fp64"]["V_trace"] - 1)
+    ms = res["fp32"]["ms_per_step"]
+    flops = 2.0 * 3 * n_factors * n_nuc * P.R_N * n
+    peaks, peak_kind = load_peaks()
+    tc_ms = res["fp32"]["kernel_ms"]["gemm3_tc_kernel"]
+    achieved = 6 * flops / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        tq, wq = osinc.master_nodes(n, b, M)
+        Pm = okv.master_kernel_vectors(n, b, tq, wq)
+        sample = items[:40]
+        t0 = time.perf_counter()
+        onuc.nuclear_items(n, b, basis, Pm, sample, nuc, Z)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(sample) / dt, "unit": "entries/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "the first 40 items (factors, windows and products formed per call)"}
+    _line(args, ws, "nuclear-attraction matrix entries/s", ws * len(items) / (ms * 1e-3), "entries/s", ms, "f32",
+          {"workload": name, "n": n, "items": len(items), "item_factors": n_factors, "nuclei": n_nuc, "R_N": P.R_N},
+          forms=res,
+          roofline={"kernel": "gemm3_tc_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
+                    "peak_source": peak_kind, "kernel_ms": tc_ms,
+                    "note": "bf16 slice-product flops 6 x 2*3*factors*nuclei*R_N*n per launch / event time"},
+          gpu_launches=6 * args.steps, cpu_baseline=cpu)
+
+
 def run_lattice_energy(args, ws, rank, local):
     """f1: interaction energy of a 256^3 hydrogen lattice (charges 2 bohr apart,
     64 cells) by the traced tensor lattice sum with the singular-point
@@ -761,6 +837,8 @@ def main():
         run_lattice(args, ws, rank, local)
     elif args.workload == "lattice_energy256_n16384":
         run_lattice_energy(args, ws, rank, local)
+    elif args.workload == "nuclear80_n4096":
+        run_nuclear(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

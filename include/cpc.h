@@ -253,6 +253,32 @@ int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, int n_facto
                    void* W_rho, double* J, int precision, int tiles_per_cta, void* ws, size_t ws_bytes,
                    void* stream);
 
+/* Galerkin matrix of the nuclear potential over product functions (Sec. 3.3):
+ * the reference Newton kernel of a MASTER kernel shifted onto each nucleus
+ * by the rank-1 windowing operator,
+ *   F[l][a R_N + q][i] = p~_q[i - nuc_edges[l][a]],  i = 0..n-1
+ * (computed here into F), gives P_c = sum_a Z[a] sum_q prod_l F[l][a R_N + q]
+ * (h^3 times V_c = -sum Z_a / |x - a_a| at the cell centres, up to the sign),
+ * and
+ *   V[t] = -sum_{r in item t} c_items[r] sum_a Z[a] sum_q prod_l <u_r^(l), F[l][a R_N + q]>
+ * = -<G_k . G_m, P_c> for item t = (k, m) given as the CP factors of
+ * G_k . G_m (as in coulomb_matrix).  A nucleus sits at the grid-cell edge
+ * nuc_edges[l][a] of each axis (x = -b + e h).  off, U_items, c_items: as in
+ * coulomb_matrix; n_nuc in [1, 256] with n_nuc R_N <= 65535; nuc_edges: host
+ * int32 [3][n_nuc] in [0, n]; Z: device float64 [n_nuc]; F: [3][n_nuc R_N][n]
+ * float64 (CPC_FP64, CPC_SPLIT) or float32 (CPC_FP32); V: device float64
+ * [n_items].  The contraction is coulomb_matrix's for each form over the
+ * n_nuc R_N columns (a, q), the product over axes being per column (the
+ * tensor-core form for CPC_FP32 with n a multiple of 128; a device-side wait
+ * that gives up writes NaN).  Workspace: nuclear_matrix_workspace bytes,
+ * 256-byte aligned.  Returns CPC_OK, CPC_ERR_INVALID (not a MASTER kernel,
+ * NULL or misaligned pointer, edge out of range), CPC_ERR_UNSUPPORTED,
+ * CPC_ERR_WORKSPACE or CPC_ERR_CUDA; no launch happens on an argument error. */
+size_t nuclear_matrix_workspace(const cpc_kernel* master, int n_items, int n_factors, int n_nuc, int precision);
+int nuclear_matrix(const cpc_kernel* master, int n_items, const int* off, int n_factors, const double* U_items,
+                   const double* c_items, int n_nuc, const int* nuc_edges, const double* Z, void* F, double* V,
+                   int precision, void* ws, size_t ws_bytes, void* stream);
+
 /* Schedule tuner for coulomb_matrix: computes W_rho, then times the
  * contraction for every tiles_per_cta in {4, 8, ..., 128} on the caller's
  * data (CUDA events on `stream`; this call synchronises the stream), writes

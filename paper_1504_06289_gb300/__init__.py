@@ -25,7 +25,7 @@ __all__ = [
     "cp_convolve", "cp_hartree_energy", "cp_hartree_energy_from_factors",
     "cp_factor_spectra", "cp_convolve_from_spectra", "cp_hartree_energy_from_spectra",
     "cp_hartree_energy_noalloc", "cp_hartree_energy_adjoint", "cp_gaussian_param_grad",
-    "coulomb_matrix", "lattice_potential_sum", "lattice_interaction_energy", "CPHartreeEnergy", "CpcError",
+    "coulomb_matrix", "nuclear_matrix", "lattice_potential_sum", "lattice_interaction_energy", "CPHartreeEnergy", "CpcError",
 ]
 
 
@@ -347,6 +347,30 @@ def coulomb_matrix(P: NewtonKernel, off: torch.Tensor, U_items: torch.Tensor, c_
             return J, W_rho
     check(lib.coulomb_matrix(*args, int(tiles_per_cta), _ptr(ws), ws.numel(), _stream(stream)), "coulomb_matrix")
     return J, W_rho
+
+
+def nuclear_matrix(P: NewtonKernel, off: torch.Tensor, U_items: torch.Tensor, c_items: torch.Tensor, nuc_edges,
+                   Z: torch.Tensor, precision: str = "fp64", F: torch.Tensor | None = None,
+                   ws: torch.Tensor | None = None, stream=None):
+    """V[t] = -<item_t, P_c> with P_c the master kernel P shifted onto nuclei at
+    the grid-cell edges `nuc_edges` (3, n_nuc) with charges Z (Sec. 3.3).
+    Returns (V, F), F the windowed nuclear factors (3, n_nuc R_N, n)."""
+    lib = load()
+    n_items = off.numel() - 1
+    n_factors = U_items.shape[1]
+    e = np.ascontiguousarray(np.asarray(nuc_edges, dtype=np.int32).reshape(3, -1))
+    n_nuc = e.shape[1]
+    pr = _prec(precision)
+    if F is None:
+        F = torch.empty((3, n_nuc * P.R_N, P.n), dtype=_out_dtype(precision), device=U_items.device)
+    V = torch.empty(n_items, dtype=torch.float64, device=U_items.device)
+    nb = lib.nuclear_matrix_workspace(P.handle, n_items, n_factors, n_nuc, pr)
+    if ws is None or ws.numel() < nb:
+        ws = _workspace(nb, U_items.device)
+    check(lib.nuclear_matrix(P.handle, n_items, _ptr(off), n_factors, _ptr(U_items), _ptr(c_items), n_nuc,
+                             e.ctypes.data, _ptr(Z), _ptr(F), _ptr(V), pr, _ptr(ws), ws.numel(), _stream(stream)),
+          "nuclear_matrix")
+    return V, F
 
 
 def lattice_potential_sum(P: NewtonKernel, edges, sub: torch.Tensor | None = None, precision: str = "fp64",

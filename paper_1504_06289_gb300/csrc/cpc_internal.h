@@ -86,6 +86,9 @@ void build_twiddles(int n, std::vector<double>& tw_re, std::vector<double>& tw_i
 // device-side builders (spectra.cu)
 int build_pass_twiddles(cpc_kernel* P, cudaStream_t s);
 size_t lattice_scratch_bytes(int n);
+// nuclear factors F[l][a R_N + q][i] = p~_q[i - edges[l n_nuc + a]] of a MASTER
+// kernel (edges: host int32 [3][n_nuc] in [0, n]), float64 or float32 (lattice.cu)
+int launch_window(const cpc_kernel* P, int n_nuc, const int* edges, void* F, bool fp32, cudaStream_t s);
 int compute_kernel_spectrum(cpc_kernel* P, cudaStream_t s);
 
 // spectra of U columns into workspace (float64 and/or float32 copies)

@@ -644,9 +644,10 @@ static int coulomb_groups(int R_rho, int R_N, int tiles_per_cta) {
 }
 
 // contraction + segmented item reduction, after W_rho holds the V_H factors
+// J[t] = scale sum_{r in item t} c_items[r] sum_m c_rho[m] sum_q prod_l <u_r^(l), W_rho[l][m R_N + q]>
 static int coulomb_contract(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
                             const double* c_items, int R_rho, const double* c_rho, const void* W_rho, double* J,
-                            int precision, int tiles_per_cta, double* rowpart, cudaStream_t s) {
+                            int precision, int tiles_per_cta, double* rowpart, cudaStream_t s, double scale) {
   const int n = P->n;
   const int N = R_rho * P->R_N;
   const int groups = coulomb_groups(R_rho, P->R_N, tiles_per_cta);
@@ -670,8 +671,7 @@ static int coulomb_contract(const cpc_kernel* P, int n_items, const int* off, in
     st = launch_rows_tc(P, n_factors, U_items, R_rho, static_cast<const float*>(W_rho), c_rho, rowpart, tws, s);
     if (st) return st;
     item_reduce_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(n_items, off, c_items, rowpart, tgroups, n_factors,
-                                                           P->h * P->h * P->h, J,
-                                                           tc_rows_status_ptr(P, n_factors, R_rho, tws));
+                                                           scale, J, tc_rows_status_ptr(P, n_factors, R_rho, tws));
     CPC_LAUNCH_CHECK("item_reduce_kernel");
     return CPC_OK;
   } else {
@@ -680,7 +680,7 @@ static int coulomb_contract(const cpc_kernel* P, int n_items, const int* off, in
   }
   if (st) return st;
   item_reduce_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(n_items, off, c_items, rowpart, groups, n_factors,
-                                                         P->h * P->h * P->h, J);
+                                                         scale, J);
   CPC_LAUNCH_CHECK("item_reduce_kernel");
   return CPC_OK;
 }
@@ -725,7 +725,7 @@ extern "C" int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, 
   if (st) return st;
   double* rowpart = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_rho, precision));
   return coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision,
-                          tiles_per_cta ? tiles_per_cta : kTilesDefault, rowpart, s);
+                          tiles_per_cta ? tiles_per_cta : kTilesDefault, rowpart, s, P->h * P->h * P->h);
 }
 
 extern "C" int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* off, int n_factors,
@@ -751,10 +751,10 @@ extern "C" int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* 
   const bool fixed = (precision == CPC_FP32 && tc_supported(P));
   for (int t = fixed ? kTilesDefault : kTilesMin; t <= (fixed ? kTilesDefault : kTilesMax); t *= 2) {
     // one untimed launch per candidate, then one timed
-    st = coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, t, rowpart, s);
+    st = coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, t, rowpart, s, P->h * P->h * P->h);
     if (st) break;
     CPC_CUDA(cudaEventRecord(e0, s));
-    st = coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, t, rowpart, s);
+    st = coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, t, rowpart, s, P->h * P->h * P->h);
     if (st) break;
     CPC_CUDA(cudaEventRecord(e1, s));
     CPC_CUDA(cudaEventSynchronize(e1));
@@ -770,7 +770,74 @@ extern "C" int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* 
   if (fixed) return CPC_OK;  // J already holds the timed run's result
   // leave J computed with the chosen schedule
   return coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, best_t,
-                          rowpart, s);
+                          rowpart, s, P->h * P->h * P->h);
+}
+
+// ---- nuclear potential and its Galerkin matrix (Sec. 3.3) ---------------------
+// V[t] = -sum_{r in item t} c_items[r] sum_a Z[a] sum_q prod_l <u_r^(l), F[l][a R_N + q]>,
+// F the master kernel windowed onto each nucleus (launch_window).  The product
+// over axes is taken per column m = a R_N + q, so this is the Coulomb
+// contraction over n_nuc R_N columns of one term each (a kernel view with
+// R_N = 1, the charge of column m being Z[m / R_N]) and the scale -1 in place
+// of h^3 (the Galerkin vectors already carry h^3).  Folding q into the
+// columns fills the 128-column tiles of the tensor-core form (10 nuclei x 51
+// terms: 4 tiles of one term instead of one 10-column tile per term).
+__global__ void expand_charges_kernel(int n_nuc, int R_N, const double* __restrict__ Z, double* __restrict__ Zq) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < n_nuc * R_N) Zq[m] = Z[m / R_N];
+}
+
+static cpc_kernel column_view(const cpc_kernel* P) {
+  cpc_kernel Q;  // only the sizes the contraction reads; no tables
+  Q.n = P->n;
+  Q.b = P->b;
+  Q.h = P->h;
+  Q.kind = P->kind;
+  Q.len = P->len;
+  Q.R_N = 1;
+  return Q;
+}
+
+static size_t nuclear_contract_bytes(const cpc_kernel* Q, int n_factors, int N, int precision) {
+  if (precision == CPC_FP32 && tc_supported(Q))
+    return align256(sizeof(double) * tc_rows_groups(Q, N) * n_factors) + tc_rows_workspace(Q, n_factors, N);
+  return align256(sizeof(double) * coulomb_groups(N, 1, kTilesMin) * n_factors);
+}
+
+extern "C" size_t nuclear_matrix_workspace(const cpc_kernel* P, int n_items, int n_factors, int n_nuc,
+                                           int precision) {
+  if (!P || n_items <= 0 || n_factors <= 0 || n_nuc <= 0) return 0;
+  const cpc_kernel Q = column_view(P);
+  const int N = n_nuc * P->R_N;
+  return align256(sizeof(double) * N) + nuclear_contract_bytes(&Q, n_factors, N, precision);
+}
+
+extern "C" int nuclear_matrix(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
+                              const double* c_items, int n_nuc, const int* nuc_edges, const double* Z, void* F,
+                              double* V, int precision, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  if (!P || P->kind != CPC_KERNEL_MASTER) return fail(CPC_ERR_INVALID, "nuclear_matrix: needs a MASTER kernel");
+  if (n_items <= 0 || n_factors <= 0 || !off || !U_items || !c_items || !nuc_edges || !Z || !F || !V)
+    return fail(CPC_ERR_INVALID, "nuclear_matrix: bad arguments");
+  if ((reinterpret_cast<uintptr_t>(U_items) & 15) || (reinterpret_cast<uintptr_t>(F) & 15))
+    return fail(CPC_ERR_INVALID, "nuclear_matrix: U_items and F must be 16-byte aligned");
+  if (precision != CPC_FP64 && precision != CPC_FP32 && precision != CPC_SPLIT)
+    return fail(CPC_ERR_UNSUPPORTED, "nuclear_matrix: precision form not implemented");
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255))
+    return fail(CPC_ERR_WORKSPACE, "nuclear_matrix: workspace NULL or not 256-byte aligned");
+  if (ws_bytes < nuclear_matrix_workspace(P, n_items, n_factors, n_nuc, precision))
+    return fail(CPC_ERR_WORKSPACE, "nuclear_matrix: workspace too small");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int st = launch_window(P, n_nuc, nuc_edges, F, storage_precision(precision) == CPC_FP32, s);
+  if (st) return st;
+  const int N = n_nuc * P->R_N;
+  double* Zq = static_cast<double*>(ws);
+  expand_charges_kernel<<<(N + 255) / 256, 256, 0, s>>>(n_nuc, P->R_N, Z, Zq);
+  CPC_LAUNCH_CHECK("expand_charges_kernel");
+  double* rowpart = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + align256(sizeof(double) * N));
+  const cpc_kernel Q = column_view(P);
+  return coulomb_contract(&Q, n_items, off, n_factors, U_items, c_items, N, Zq, F, V, precision, kTilesDefault,
+                          rowpart, s, -1.0);
 }
 
 // ---- explicit spectra intermediates ------------------------------------------

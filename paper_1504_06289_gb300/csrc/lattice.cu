@@ -384,6 +384,40 @@ size_t lattice_scratch_bytes(int n) {
   return std::max(lat::kScratchBytes, kEnergyListOff + size_t(3) * 2 * n * 3 * sizeof(int));
 }
 
+// ---- nuclear potential by windowed shifts of the master kernel (Sec. 3.3) ----
+// F[l][a R_N + q][i] = p~_q[i - e[l][a]], i = 0..n-1: the master vector of
+// term q shifted onto nucleus a (at the grid-cell edge e[l][a] of axis l) and
+// windowed onto the n-cell box; float64, or rounded to float32.
+template <typename T>
+__global__ void window_kernel(int n, int R_N, int n_nuc, const double* __restrict__ Pm, Edges ed,
+                              T* __restrict__ F) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = blockIdx.y, l = blockIdx.z;
+  if (i >= n) return;
+  const int a = row / R_N, q = row - a * R_N;
+  const int e = ed.e[l * n_nuc + a];  // in [0, n]: i - e in [-n, n-1]
+  F[((size_t)l * n_nuc * R_N + row) * n + i] = T(Pm[(size_t)q * 2 * n + n + i - e]);
+}
+
+int launch_window(const cpc_kernel* P, int n_nuc, const int* edges, void* F, bool fp32, cudaStream_t s) {
+  if (n_nuc < 1 || n_nuc > kMaxLattice) return fail(CPC_ERR_UNSUPPORTED, "nuclear factors: 1..256 nuclei");
+  if ((long long)n_nuc * P->R_N > 65535) return fail(CPC_ERR_UNSUPPORTED, "nuclear factors: too many columns");
+  Edges ed;
+  for (int l = 0; l < 3; ++l) {
+    ed.count[l] = n_nuc;
+    for (int a = 0; a < n_nuc; ++a) {
+      const int e = edges[l * n_nuc + a];
+      if (e < 0 || e > P->n) return fail(CPC_ERR_INVALID, "nuclear factors: edge index outside [0, n]");
+      ed.e[l * n_nuc + a] = e;
+    }
+  }
+  const dim3 grid((P->n + 255) / 256, n_nuc * P->R_N, 3);
+  if (fp32) window_kernel<float><<<grid, 256, 0, s>>>(P->n, P->R_N, n_nuc, P->d_p, ed, static_cast<float*>(F));
+  else window_kernel<double><<<grid, 256, 0, s>>>(P->n, P->R_N, n_nuc, P->d_p, ed, static_cast<double*>(F));
+  CPC_LAUNCH_CHECK("window_kernel");
+  return CPC_OK;
+}
+
 // ---- interaction energy of the lattice charges (Sec. 5.3, Eq. EnergyLattice) ----
 // A charge sits at the grid-cell edge e, the corner of the cells e-1 and e of
 // each axis; the potential sum traced at a lattice point is the mean of those

@@ -231,3 +231,30 @@ def test_lattice_interaction_energy_fullsize(cpc, name):
     _, _, Pm0 = oracle_master_kernel(n, b, M)
     assert abs(E / olat.interaction_energy_tensor(Pm0, edges, n, h) - 1) < 1e-12
     assert abs(E / olat.interaction_energy_direct(edges, h) - 1) < 2e-8
+
+
+def test_nuclear80_n4096_nuclear_matrix(cpc):
+    # Sec. 3.3: all 3240 nuclear-attraction entries of the 80-function basis
+    # (10 nuclei) in the float32 form, and a sample in float64, against the oracle
+    from oracle import nuclear as onuc
+    name = "nuclear80_n4096"
+    cfg = workloads.CONFIGS[name]
+    n, b, M = cfg["n"], cfg["b"], cfg["M"]
+    basis = workloads.basis_for(name, 3)
+    nb = cfg["n_basis"]
+    nuc, Z = workloads.nuclei_for(basis, n, b, 5)
+    P = cpc.make_newton_kernel(n, b, M, "master")
+    _, _, Pm0 = oracle_master_kernel(n, b, M)
+    rng = np.random.default_rng(4)
+    all_items = ocoul.item_list(nb)
+    sample = [all_items[int(i)] for i in rng.choice(len(all_items), 12, replace=False)] + [(0, 0), (nb - 1, nb - 1)]
+    V0 = onuc.nuclear_items(n, b, basis, Pm0, sample, nuc, Z)
+    _, _, U_s, c_s, off_s = _coulomb_inputs(cpc, n, b, basis, sample)
+    V64, _ = cpc.nuclear_matrix(P, off_s, U_s, c_s, nuc, dev(Z), "fp64")
+    assert np.max(np.abs(V64.cpu().numpy() - V0)) < TOL64 * np.max(np.abs(V0))
+    _, _, U_all, c_all, off_all = _coulomb_inputs(cpc, n, b, basis, all_items)
+    V32, _ = cpc.nuclear_matrix(P, off_all, U_all, c_all, nuc, dev(Z), "fp32")
+    V32 = V32.cpu().numpy()
+    idx = [all_items.index(it) for it in sample]
+    assert np.max(np.abs(V32[idx] - V0)) < 1e-5 * np.max(np.abs(V0))
+    assert np.all(np.isfinite(V32))

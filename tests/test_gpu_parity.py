@@ -315,6 +315,40 @@ def test_lattice_sum(cpc, precision, tol):
     assert np.max(np.abs(V.cpu().numpy() / V0 - 1)) < tol
 
 
+@pytest.mark.parametrize("n,precision,tol", [(256, "fp64", TOL64), (256, "split", 1e-6), (256, "fp32", 1e-5),
+                                           (64, "fp32", 1e-5)])
+def test_nuclear_matrix(cpc, n, precision, tol):
+    # Sec. 3.3: the master kernel windowed onto three nuclei, contracted with
+    # the item factors (the tensor-core form for n = 256, CUDA cores for n = 64)
+    from oracle import nuclear as onuc
+    b, M = 10.0, 14
+    basis = _basis_case()
+    nb = len(basis["fn_first"]) - 1
+    items = ocoul.item_list(nb)
+    first = basis["fn_first"]
+    nuc = np.array([[n // 2 - 7, n // 2 + 3, n // 2 + 11], [n // 2, n // 2 - 5, n // 2 + 2],
+                    [n // 2 + 4, n // 2 - 9, n // 2]], dtype=np.int32)
+    Z = np.array([1.0, 6.0, 8.0])
+    P = cpc.make_newton_kernel(n, b, M, "master")
+    _, _, Pm0 = oracle_master_kernel(n, b, M)
+    V0 = onuc.nuclear_items(n, b, basis, Pm0, items, nuc, Z)
+    centre = np.repeat(basis["fn_centre"], np.diff(first), axis=0)
+    G = cpc.cp_sample_gaussians(n, b, dev(basis["prim_alpha"]), dev(centre))
+    ia, ib, _, off = ocoul.item_pairs(basis, items)
+    U_it, c_it = cpc.cp_hadamard_pairs(G, dev(ia, torch.int32), dev(ib, torch.int32), dev(basis["prim_d"]))
+    V, F = cpc.nuclear_matrix(P, dev(off, torch.int32), U_it, c_it, nuc, dev(Z), precision)
+    V = V.cpu().numpy()
+    assert np.max(np.abs(V - V0)) < tol * np.max(np.abs(V0))
+    F0 = np.stack([onuc.windowed_factors(Pm0, nuc[l], n) for l in range(3)])
+    Fd = F.double().cpu().numpy()
+    assert np.max(np.abs(Fd - F0)) < (1e-7 if precision == "fp32" else 1e-13) * np.max(np.abs(F0))
+    from paper_1504_06289_gb300 import CpcError
+    with pytest.raises(CpcError):
+        cpc.nuclear_matrix(P, dev(off, torch.int32), U_it, c_it, np.array([[0], [n + 1], [3]]), dev(Z[:1]))
+    with pytest.raises(CpcError):
+        cpc.nuclear_matrix(cpc.make_newton_kernel(64, 4.0, 5), dev(off, torch.int32), U_it, c_it, nuc, dev(Z))
+
+
 def test_lattice_interaction_energy(cpc):
     # Sec. 5.3 Eq. EnergyLattice: the device sum against the oracle's traced
     # tensor sum on the same master kernel, and against the direct sum

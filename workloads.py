@@ -36,6 +36,10 @@ CONFIGS = {
     # 32^3 lattice of unit charges with spacing 4 bohr, 16384^3 grid, 512^3 sub-grid.
     "lattice32_n16384": dict(n=16384, b=64.0, M=30, L=32, spacing=4.0, sub=512,
                              n_check=1000),
+    # nuclear-attraction matrix over the basis80_n4096 products: nuclei at the
+    # 10 basis centres (rounded to grid-cell edges), charges 1..8, master kernel M=25
+    "nuclear80_n4096": dict(n=4096, b=20.0, M=25, n_basis=80, prim_lo=3, prim_hi=6,
+                            a_lo=0.05, a_hi=2000.0, centres=10, centre_half=3.0),
     # interaction energy of hydrogen lattices, 2 bohr apart (128 or 64 cells)
     "lattice_energy24_n4096": dict(n=4096, b=32.0, M=64, L=24, cells=128),
     "lattice_energy256_n16384": dict(n=16384, b=256.0, M=64, L=256, cells=64),
@@ -138,6 +142,16 @@ def lattice_geometry(n: int, L: int, sub: int) -> dict:
     stride = n // sub
     sub_idx = (stride // 2 + stride * np.arange(sub)).astype(np.int32)
     return dict(edges=edges, sub_idx=sub_idx)
+
+
+def nuclei_for(basis: dict, n: int, b: float, seed: int):
+    """Nuclei at the distinct basis centres, each moved to the nearest grid-cell
+    edge (x = -b + e h): edges (3, N) int32 and charges Z (N,) in 1..8."""
+    C = np.unique(np.asarray(basis["fn_centre"]), axis=0)
+    h = 2.0 * b / n
+    e = np.clip(np.rint((C + b) / h), 0, n).astype(np.int32).T
+    Z = rng(seed).integers(1, 9, size=C.shape[0]).astype(np.float64)
+    return np.ascontiguousarray(e), Z
 
 
 def lattice_energy_edges(n: int, L: int, cells: int) -> np.ndarray:
