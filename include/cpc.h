@@ -291,6 +291,42 @@ int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* off, int n_
                         const double* c_rho, void* W_rho, double* J, int precision, void* ws,
                         size_t ws_bytes, void* stream, int* best_tiles_per_cta, float* best_ms);
 
+/* ---- two-electron integrals: 1D density fitting + truncated Cholesky (Sec. 3.2) ----
+ * For N_b s-type primitive Gaussians with sampled factors U_prims [3][n_b][n]
+ * (device float64, cp_sample_gaussians) and n_pairs pairs P = (pa[P], pb[P])
+ * (device int32, entries in [0, n_b)), the side matrices
+ * G^(l)[i, P] = U_prims[l][pa[P]][i] U_prims[l][pb[P]][i] are fitted per axis
+ * (Eq. 1DDensFit) by a truncated Cholesky factorisation with diagonal
+ * pivoting of G G^T, stopped when the largest remaining diagonal is
+ * <= tol_df times the largest initial one or after max_rank_df (<= 128)
+ * steps: G ~ U V^T with U = L L[I,:]^{-1} and V = G[I,:]^T (I the pivots).
+ * With M_k^(l) = U^(l)T (p_k * U^(l)) (Eq. Factor_Mk_Conv; P a CONV kernel),
+ * the TEI matrix b_{P,P'} = <G_P, P_R * G_P'> (Eq. TEI_tens) is
+ *   B = h^3 sum_k (Hadamard over l) V^(l) M_k^(l) V^(l)T,
+ * whose diagonal and pivot columns drive the same truncated Cholesky
+ * factorisation (tol_b, max_rank_b <= n_pairs): B ~ L L^T.  Output: L
+ * [max_rank_b][n_pairs] device float64 (column s of L at L + s n_pairs, zero
+ * beyond the rank) and ranks device int32[4] = (R_1, R_2, R_3, R_B).  The
+ * pivot loops run on the device (no host synchronisation); float64
+ * throughout.  Workspace: tei_cholesky_workspace bytes, 256-byte aligned.
+ * Returns CPC_OK, CPC_ERR_INVALID (not a CONV kernel, bad pointer or size,
+ * negative tolerance), CPC_ERR_UNSUPPORTED (max_rank_df > 128),
+ * CPC_ERR_WORKSPACE or CPC_ERR_CUDA. */
+size_t tei_cholesky_workspace(const cpc_kernel* P, int n_pairs, int max_rank_b);
+int tei_cholesky(const cpc_kernel* P, int n_b, const double* U_prims, int n_pairs, const int* pa, const int* pb,
+                 double tol_df, double tol_b, int max_rank_df, int max_rank_b, double* L, int* ranks, void* ws,
+                 size_t ws_bytes, void* stream);
+
+/* Coulomb matrix of a density matrix D (device float64 [n_b][n_b],
+ * symmetric) from the TEI factor of tei_cholesky (Sec. 3.2):
+ *   J[P] = sum_{P'} b_{P,P'} (2 - delta_{pa pb}) D[pa[P']][pb[P']]  ~  (L (L^T d))[P]
+ * for every pair P (J: device float64 [n_pairs]; with all pairs mu <= nu,
+ * J[P] = J_{pa[P] pb[P]}).  L, ranks: as written by tei_cholesky.  Workspace:
+ * 256-byte aligned, at least align256(8 n_pairs) + 8 max_rank_b bytes.
+ * Returns CPC_OK, CPC_ERR_INVALID, CPC_ERR_WORKSPACE or CPC_ERR_CUDA. */
+int tei_coulomb(int n_b, int n_pairs, const int* pa, const int* pb, int max_rank_b, const double* L,
+                const int* ranks, const double* D, double* J, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- a9/a10: assembled lattice sums (Sec. 5.1, Eq. CoulombLatTensCan) -----
  * With a MASTER kernel p~_q and, per axis l, L[l] charge positions given as
  * grid-cell edge indices e[l][k] in [0, n] (a charge at x = -b + e h):

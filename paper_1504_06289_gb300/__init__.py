@@ -25,7 +25,7 @@ __all__ = [
     "cp_convolve", "cp_hartree_energy", "cp_hartree_energy_from_factors",
     "cp_factor_spectra", "cp_convolve_from_spectra", "cp_hartree_energy_from_spectra",
     "cp_hartree_energy_noalloc", "cp_hartree_energy_adjoint", "cp_gaussian_param_grad",
-    "coulomb_matrix", "nuclear_matrix", "lattice_potential_sum", "lattice_interaction_energy", "CPHartreeEnergy", "CpcError",
+    "coulomb_matrix", "nuclear_matrix", "tei_cholesky", "tei_coulomb", "lattice_potential_sum", "lattice_interaction_energy", "CPHartreeEnergy", "CpcError",
 ]
 
 
@@ -371,6 +371,37 @@ def nuclear_matrix(P: NewtonKernel, off: torch.Tensor, U_items: torch.Tensor, c_
                              e.ctypes.data, _ptr(Z), _ptr(F), _ptr(V), pr, _ptr(ws), ws.numel(), _stream(stream)),
           "nuclear_matrix")
     return V, F
+
+
+def tei_cholesky(P: NewtonKernel, U_prims: torch.Tensor, pa: torch.Tensor, pb: torch.Tensor, tol_df: float = 1e-12,
+                 tol_b: float = 1e-10, max_rank_df: int = 128, max_rank_b: int | None = None, stream=None):
+    """Truncated Cholesky factor of the TEI matrix over the pairs (pa, pb) of
+    primitive Gaussians with sampled factors U_prims (3, n_b, n), via 1D
+    density fitting (Sec. 3.2).  Returns (L (max_rank_b, n_pairs), ranks
+    (4,) int32 device: the fitted ranks of the three axes and the rank of L)."""
+    lib = load()
+    n_b, n_pairs = U_prims.shape[1], pa.numel()
+    if max_rank_b is None:
+        max_rank_b = n_pairs
+    L = torch.empty((max_rank_b, n_pairs), dtype=torch.float64, device=U_prims.device)
+    ranks = torch.zeros(4, dtype=torch.int32, device=U_prims.device)
+    ws = _workspace(lib.tei_cholesky_workspace(P.handle, n_pairs, max_rank_b), U_prims.device)
+    check(lib.tei_cholesky(P.handle, n_b, _ptr(U_prims), n_pairs, _ptr(pa), _ptr(pb), float(tol_df), float(tol_b),
+                           int(max_rank_df), int(max_rank_b), _ptr(L), _ptr(ranks), _ptr(ws), ws.numel(),
+                           _stream(stream)), "tei_cholesky")
+    return L, ranks
+
+
+def tei_coulomb(L: torch.Tensor, ranks: torch.Tensor, pa: torch.Tensor, pb: torch.Tensor, D: torch.Tensor,
+                stream=None) -> torch.Tensor:
+    """J over the pairs for the density matrix D (n_b, n_b) from tei_cholesky's factor."""
+    lib = load()
+    n_b, n_pairs, max_rank_b = D.shape[0], pa.numel(), L.shape[0]
+    J = torch.empty(n_pairs, dtype=torch.float64, device=L.device)
+    ws = _workspace(((8 * n_pairs + 255) // 256) * 256 + 8 * max_rank_b, L.device)
+    check(lib.tei_coulomb(n_b, n_pairs, _ptr(pa), _ptr(pb), max_rank_b, _ptr(L), _ptr(ranks), _ptr(D), _ptr(J),
+                          _ptr(ws), ws.numel(), _stream(stream)), "tei_coulomb")
+    return J
 
 
 def lattice_potential_sum(P: NewtonKernel, edges, sub: torch.Tensor | None = None, precision: str = "fp64",

@@ -258,3 +258,46 @@ def test_nuclear80_n4096_nuclear_matrix(cpc):
     idx = [all_items.index(it) for it in sample]
     assert np.max(np.abs(V32[idx] - V0)) < 1e-5 * np.max(np.abs(V0))
     assert np.all(np.isfinite(V32))
+
+
+def test_tei80_n4096_cholesky(cpc):
+    # Sec. 3.2 at full size: 80 s primitives (3240 pairs) on the 4096 grid;
+    # J(D) for a diagonal and a random symmetric D against the oracle's own
+    # density fitting and Cholesky (each within its truncation), and the
+    # diagonal-density J against the Coulomb-matrix path of the library
+    from oracle import tei as otei
+    name = "tei80_n4096"
+    cfg = workloads.CONFIGS[name]
+    n, b, M, nb = cfg["n"], cfg["b"], cfg["M"], cfg["n_prims"]
+    h = 2 * b / n
+    g = workloads.gaussian_mixture(nb, cfg["a_lo"], cfg["a_hi"], 11, centres=cfg["centres"],
+                                   cluster_radius=cfg["cluster_radius"])
+    P = cpc.make_newton_kernel(n, b, M)
+    U = cpc.cp_sample_gaussians(n, b, dev(g["a"]), dev(g["X"]))
+    pa0, pb0 = otei.pair_list(nb)
+    pa, pb = dev(pa0, torch.int32), dev(pb0, torch.int32)
+    L, ranks = cpc.tei_cholesky(P, U, pa, pb, cfg["tol_df"], 1e-8, 128, cfg["max_rank_b"])
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
+    L0, *_ = otei.tei_cholesky(U0, P0, h, pa0, pb0, cfg["tol_df"], 1e-8, 128, cfg["max_rank_b"])
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((nb, nb))
+    w = rng.uniform(0.0, 2.0, nb)
+    for D in (np.diag(w), X + X.T):
+        J = cpc.tei_coulomb(L, ranks, pa, pb, dev(D)).cpu().numpy()
+        J0 = otei.coulomb_from_cholesky(L0, D, pa0, pb0)
+        assert np.max(np.abs(J - J0)) < 1e-6 * np.max(np.abs(J0))
+    # the same J for D = diag(w) from the Coulomb-matrix path (V_H factors of
+    # rho = sum w g^2, no density fitting, no Cholesky)
+    d1 = dev(np.ones(nb))
+    idx = dev(np.arange(nb), torch.int32)
+    U_rho, c_rho = cpc.cp_hadamard_pairs(U, idx, idx, d1, dev(w))
+    U_it, c_it = cpc.cp_hadamard_pairs(U, pa, pb, d1)
+    off = dev(np.arange(len(pa0) + 1), torch.int32)
+    Jc, _ = cpc.coulomb_matrix(P, off, U_it, c_it, U_rho, c_rho, "fp64", tiles_per_cta=0)
+    Jd = cpc.tei_coulomb(L, ranks, pa, pb, dev(np.diag(w))).cpu().numpy()
+    Jc = Jc.cpu().numpy()
+    # set by the density fitting at tol_df = 1e-14 (the oracle measures
+    # 1.5e-7 of max |J|; 1.3e-6 at tol_df = 1e-12), not by the Cholesky
+    # truncation (tol_b = 1e-8: at most 8e-7 of max |J| here)
+    assert np.max(np.abs(Jd - Jc)) < 1e-6 * np.max(np.abs(Jc))

@@ -349,6 +349,44 @@ def test_nuclear_matrix(cpc, n, precision, tol):
         cpc.nuclear_matrix(cpc.make_newton_kernel(64, 4.0, 5), dev(off, torch.int32), U_it, c_it, nuc, dev(Z))
 
 
+def test_tei_cholesky_and_coulomb(cpc):
+    # Sec. 3.2: 1D density fitting, TEI matrix from its factors, truncated
+    # Cholesky, J(D); L is compared through L L^T (the pivot order may differ
+    # where two diagonals agree to rounding) and through J(D)
+    from oracle import tei as otei
+    n, b, M, nb = 128, 6.0, 16, 5
+    h = 2 * b / n
+    g = workloads.gaussian_mixture(nb, 0.4, 3.0, 7, centre_half=1.0)
+    P = cpc.make_newton_kernel(n, b, M)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
+    pa0, pb0 = otei.pair_list(nb)
+    L0, piv0, Uf0, Vf0, Mf0 = otei.tei_cholesky(U0, P0, h, pa0, pb0, 1e-13, 1e-12, 128, 64)
+    B0 = np.stack([otei.tei_column(Vf0, Mf0, h, j) for j in range(len(pa0))], axis=1)
+    U = cpc.cp_sample_gaussians(n, b, dev(g["a"]), dev(g["X"]))
+    pa, pb = dev(pa0, torch.int32), dev(pb0, torch.int32)
+    L, ranks = cpc.tei_cholesky(P, U, pa, pb, 1e-13, 1e-12, 128, 15)
+    rk = ranks.cpu().numpy()
+    assert list(rk[:3]) == [u.shape[1] for u in Uf0] and rk[3] == L0.shape[1]
+    Lh = L.cpu().numpy()[:rk[3]].T
+    assert np.max(np.abs(Lh @ Lh.T - B0)) < 1e-9 * np.max(np.abs(B0))
+    assert np.all(L.cpu().numpy()[rk[3]:] == 0.0)
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((nb, nb))
+    for D in (np.diag(np.linspace(0.5, 1.5, nb)), X + X.T):
+        J = cpc.tei_coulomb(L, ranks, pa, pb, dev(D)).cpu().numpy()
+        J0 = otei.coulomb_from_cholesky(L0, D, pa0, pb0)
+        assert np.max(np.abs(J - J0)) < 1e-9 * np.max(np.abs(J0))
+    # a truncated factorisation stops at its rank cap
+    L2, r2 = cpc.tei_cholesky(P, U, pa, pb, 1e-13, 1e-12, 4, 6)
+    assert list(r2.cpu().numpy()) == [4, 4, 4, 6]
+    from paper_1504_06289_gb300 import CpcError
+    with pytest.raises(CpcError):
+        cpc.tei_cholesky(P, U, pa, pb, max_rank_df=129)
+    with pytest.raises(CpcError):
+        cpc.tei_cholesky(cpc.make_newton_kernel(n, b, M, "master"), U, pa, pb)
+
+
 def test_lattice_interaction_energy(cpc):
     # Sec. 5.3 Eq. EnergyLattice: the device sum against the oracle's traced
     # tensor sum on the same master kernel, and against the direct sum

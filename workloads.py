@@ -40,6 +40,10 @@ CONFIGS = {
     # 10 basis centres (rounded to grid-cell edges), charges 1..8, master kernel M=25
     "nuclear80_n4096": dict(n=4096, b=20.0, M=25, n_basis=80, prim_lo=3, prim_hi=6,
                             a_lo=0.05, a_hi=2000.0, centres=10, centre_half=3.0),
+    # two-electron integrals of 80 s primitives at 10 centres (1D density
+    # fitting + truncated Cholesky of the TEI matrix)
+    "tei80_n4096": dict(n=4096, b=20.0, M=25, n_prims=80, a_lo=0.3, a_hi=30.0, centres=10,
+                        cluster_radius=3.0, tol_df=1e-14, tol_b=1e-10, max_rank_b=512),
     # interaction energy of hydrogen lattices, 2 bohr apart (128 or 64 cells)
     "lattice_energy24_n4096": dict(n=4096, b=32.0, M=64, L=24, cells=128),
     "lattice_energy256_n16384": dict(n=16384, b=256.0, M=64, L=256, cells=64),
