@@ -53,7 +53,7 @@ def parse():
                     help="override the rank R_f (profiling a smaller case of the same kernels)")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "basis80_n4096", "density200_n4096", "lattice32_n16384",
-                             "lattice_energy256_n16384", "nuclear80_n4096"],
+                             "lattice_energy256_n16384", "nuclear80_n4096", "tei80_n4096"],
                     help="the default is the headline workload; the others time their own rows")
     return ap.parse_args()
 
@@ -761,6 +761,88 @@ def run_nuclear(args, ws, rank, local):
           gpu_launches=6 * args.steps, cpu_baseline=cpu)
 
 
+def run_tei(args, ws, rank, local):
+    """f2: two-electron integrals of 80 s primitives (3240 pairs): 1D density
+    fitting, convolution matrices, truncated Cholesky of the TEI matrix and
+    J(D) for one density matrix per step (Sec. 3.2); float64."""
+    import torch
+    import paper_1504_06289_gb300 as cpc
+    from oracle import coulomb as ocoul
+    from oracle import cp as ocp
+    from oracle import kernel_vectors as okv
+    from oracle import sinc as osinc
+    from oracle import tei as otei
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    name = "tei80_n4096"
+    cfg = workloads.CONFIGS[name]
+    n, b, M, nb = cfg["n"], cfg["b"], cfg["M"], cfg["n_prims"]
+    g = workloads.gaussian_mixture(nb, cfg["a_lo"], cfg["a_hi"], 11 + rank, centres=cfg["centres"],
+                                   cluster_radius=cfg["cluster_radius"])
+    P = cpc.make_newton_kernel(n, b, M, device=dev)
+    t = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
+    U = cpc.cp_sample_gaussians(n, b, t(g["a"]), t(g["X"]))
+    pa0, pb0 = otei.pair_list(nb)
+    pa, pb = t(pa0, torch.int32), t(pb0, torch.int32)
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((nb, nb))
+    D = t(X + X.T)
+    w = rng.uniform(0.0, 2.0, nb)
+    stream = torch.cuda.current_stream(dev)
+    def step():
+        L, ranks = cpc.tei_cholesky(P, U, pa, pb, cfg["tol_df"], cfg["tol_b"], 128, cfg["max_rank_b"])
+        return cpc.tei_coulomb(L, ranks, pa, pb, D), L, ranks
+    ms = _timed(stream, step, args.steps, max(1, min(args.warmup, 3)))
+    torch.cuda.synchronize()
+    cpc.kernel_timing(True)
+    J, L, ranks = step()
+    torch.cuda.synchronize()
+    cpc.kernel_timing(False)
+    phases = {k: cpc.kernel_timing_read(k)[0] for k in ("tei_fit", "tei_conv_matrices", "tei_factor", "conv_kernel")}
+    rk = [int(x) for x in ranks.cpu().numpy()]
+    # the diagonal-density J against the Coulomb-matrix path (no fitting, no Cholesky)
+    d1, idx = t(np.ones(nb)), t(np.arange(nb), torch.int32)
+    U_rho, c_rho = cpc.cp_hadamard_pairs(U, idx, idx, d1, t(w))
+    U_it, c_it = cpc.cp_hadamard_pairs(U, pa, pb, d1)
+    Jc, _ = cpc.coulomb_matrix(P, t(np.arange(len(pa0) + 1), torch.int32), U_it, c_it, U_rho, c_rho, "fp64",
+                               tiles_per_cta=0)
+    Jd = cpc.tei_coulomb(L, ranks, pa, pb, t(np.diag(w)))
+    rel_vs_coulomb = float((Jd - Jc).abs().max() / Jc.abs().max())
+    if rank != 0:
+        return
+    # float64 work of the factor phase: the TEI diagonal (3 R_N sum_l R_l^2 per pair)
+    # and per pivot column 3 R_N (R_l^2 + n_pairs R_l) multiply-adds, plus the rank-s updates
+    R_N, npair = P.R_N, len(pa0)
+    RB = rk[3]
+    fl = 2.0 * (R_N * npair * sum(r * r for r in rk[:3]) + RB * R_N * sum(r * r + npair * r for r in rk[:3])
+                + npair * RB * RB / 2.0)
+    fp64_peak = 1250.0
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        tq, wq = osinc.conv_nodes(n, b, M)
+        P0 = okv.conv_kernel_vectors(n, b, tq, wq)
+        U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
+        t0 = time.perf_counter()
+        otei.density_fit(otei.side_matrix(U0[0], pa0, pb0), cfg["tol_df"], 128)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 1.0 / (3 * dt), "unit": "factorisations/s (fitting stage of one axis x 3, lower bound)",
+               "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "the 1D density fitting of one axis (A = G G^T and its truncated Cholesky), times 3"}
+    _line(args, ws, "TEI factorisations + J(D)/s", ws / (ms * 1e-3), "factorisations/s", ms, "f64",
+          {"workload": name, "n": n, "primitives": nb, "pairs": npair, "R_N": R_N, "tol_df": cfg["tol_df"],
+           "tol_b": cfg["tol_b"]},
+          ranks={"fit": rk[:3], "tei": RB}, phases_ms=phases, rel_diff_J_vs_coulomb_path=rel_vs_coulomb,
+          roofline={"kernel": "tei_factor (pick, pivot-column and update kernels)", "bound": "alu",
+                    "kernel_ms": phases["tei_factor"],
+                    "achieved": fl / (phases["tei_factor"] * 1e-3) / 1e9 if phases["tei_factor"] else None,
+                    "peak": fp64_peak, "unit": "GFLOP/s",
+                    "frac": fl / (phases["tei_factor"] * 1e-3) / 1e9 / fp64_peak if phases["tei_factor"] else None,
+                    "traffic": None,
+                    "note": "float64 multiply-adds x 2 of the TEI diagonal, pivot columns and updates / phase time; "
+                            "peak: nominal GB300 float64 rate"},
+          gpu_launches=None, cpu_baseline=cpu)
+
+
 def run_lattice_energy(args, ws, rank, local):
     """f1: interaction energy of a 256^3 hydrogen lattice (charges 2 bohr apart,
     64 cells) by the traced tensor lattice sum with the singular-point
@@ -839,6 +921,8 @@ def main():
         run_lattice_energy(args, ws, rank, local)
     elif args.workload == "nuclear80_n4096":
         run_nuclear(args, ws, rank, local)
+    elif args.workload == "tei80_n4096":
+        run_tei(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

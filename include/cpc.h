@@ -374,7 +374,8 @@ int lattice_interaction_energy(const cpc_kernel* master, const int* L, const int
 /* ---- kernel timing (measurement support; the paper has no counterpart) -----
  * While enabled, every launch of spectra_kernel, conv_kernel,
  * slice_rows_kernel, gemm3_tc_kernel, subgrid_tc_kernel, lattice_pairs_kernel,
- * lattice_energy_kernel and adjoint_gemm_kernel is bracketed by two CUDA events recorded on the stream the
+ * lattice_energy_kernel and adjoint_gemm_kernel, and each phase of
+ * tei_cholesky (tei_fit, tei_conv_matrices, tei_factor), is bracketed by two CUDA events recorded on the stream the
  * kernel is launched on (up to 8192 launches; later ones go unrecorded).
  * cpc_kernel_timing(1) creates the events on first use and clears earlier
  * records; cpc_kernel_timing(0) stops recording and keeps the records.

@@ -106,42 +106,62 @@ __global__ void __launch_bounds__(kPickThreads) pick_kernel(int N, const double*
   }
 }
 
-// c[i] = A[i, p] = sum_P G[i, P] G[p, P], p the pivot of step s
-__global__ void __launch_bounds__(kThreads)
+// c[i] = A[i, p] = sum_P G[i, P] G[p, P], p the pivot of step s; block of
+// 32 points x 8 pair groups (pairs P = g mod 8), summed in a fixed order
+constexpr int kRows = 32, kGroups = 8;
+__global__ void __launch_bounds__(kRows * kGroups)
 side_column_kernel(int n, int n_pairs, const double* __restrict__ U, const int* __restrict__ pa,
                    const int* __restrict__ pb, const CholState* st, const int* __restrict__ piv, int s,
                    double* __restrict__ c) {
   if (st->done) return;
   __shared__ double gp[kPairChunk];
+  __shared__ double red[kGroups][kRows];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kRows + tx;
   const int p = piv[s];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * kRows + tx;
   double acc = 0.0;
   for (int P0 = 0; P0 < n_pairs; P0 += kPairChunk) {
     const int cnt = min(kPairChunk, n_pairs - P0);
     __syncthreads();
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x)
+    for (int k = tid; k < cnt; k += kRows * kGroups)
       gp[k] = U[(size_t)pa[P0 + k] * n + p] * U[(size_t)pb[P0 + k] * n + p];
     __syncthreads();
     if (i < n)
-      for (int k = 0; k < cnt; ++k) acc += U[(size_t)pa[P0 + k] * n + i] * U[(size_t)pb[P0 + k] * n + i] * gp[k];
+      for (int k = ty; k < cnt; k += kGroups)
+        acc += U[(size_t)pa[P0 + k] * n + i] * U[(size_t)pb[P0 + k] * n + i] * gp[k];
   }
-  if (i < n) c[i] = acc;
+  red[ty][tx] = acc;
+  __syncthreads();
+  if (ty == 0 && i < n) {
+    double t = 0.0;
+    for (int g = 0; g < kGroups; ++g) t += red[g][tx];
+    c[i] = t;
+  }
 }
 
 // column s of L from the pivot column c: L[s][i] = (c[i] - sum_{t<s} L[t][i] L[t][p]) / sqrt(d_p),
-// and the remaining diagonal d[i] -= L[s][i]^2
-__global__ void __launch_bounds__(kThreads)
+// and the remaining diagonal d[i] -= L[s][i]^2; block of 32 rows x 8 groups of
+// earlier columns (t = g mod 8), summed in a fixed order
+__global__ void __launch_bounds__(kRows * kGroups)
 update_kernel(int N, int s, size_t ld, double* __restrict__ L, const double* __restrict__ c, double* __restrict__ d,
               const CholState* st, const int* __restrict__ piv) {
   if (st->done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
+  __shared__ double red[kGroups][kRows];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * kRows + tx;
   const int p = piv[s];
-  double v = c[i];
-  for (int t = 0; t < s; ++t) v -= L[t * ld + i] * L[t * ld + p];
-  const double l = v / sqrt(st->dp);
-  L[s * ld + i] = l;
-  d[i] -= l * l;
+  double acc = 0.0;
+  if (i < N)
+    for (int t = ty; t < s; t += kGroups) acc += L[t * ld + i] * L[t * ld + p];
+  red[ty][tx] = acc;
+  __syncthreads();
+  if (ty == 0 && i < N) {
+    double v = c[i];
+    for (int g = 0; g < kGroups; ++g) v -= red[g][tx];
+    const double l = v / sqrt(st->dp);
+    L[s * ld + i] = l;
+    d[i] -= l * l;
+  }
 }
 
 // U[u][i] = (L L[I, :]^{-1})[i][u] for u < rank (backward substitution over u,
@@ -175,36 +195,50 @@ __global__ void pivot_rows_kernel(int n, int n_pairs, int R_max, const double* _
   V[k] = v;
 }
 
-// B[i][i] = h^3 sum_k prod_l V_l[i] M_l[k] V_l[i]^T
-__global__ void __launch_bounds__(kThreads)
-tei_diag_kernel(int n_pairs, int R_max, int R_N, const double* __restrict__ V, const double* __restrict__ M,
-                const CholState* fit, double h3, double* __restrict__ d) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_pairs) return;
-  double tot = 0.0;
-  for (int k = 0; k < R_N; ++k) {
-    double prod = 1.0;
-    for (int l = 0; l < 3; ++l) {
-      const int r = fit[l].rank;
-      const double* v = V + ((size_t)l * n_pairs + i) * R_max;
-      const double* Mk = M + ((size_t)l * R_N + k) * R_max * R_max;
-      double q = 0.0;
-      for (int a = 0; a < r; ++a) {
-        double row = 0.0;
-        for (int b2 = 0; b2 < r; ++b2) row += Mk[(size_t)a * R_max + b2] * v[b2];
-        q += v[a] * row;
-      }
-      prod *= q;
-    }
-    tot += prod;
-  }
-  d[i] = h3 * tot;
+// threads (k, i): 64 kernel terms (k = tx, tx + 64, ...) x 16 pairs per block;
+// the sum over k is reduced in a fixed order
+constexpr int kTermThreads = 64, kPairRows = 16;
+
+__device__ __forceinline__ double reduce_terms(double acc, double (*red)[2], int tx, int ty) {
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((tx & 31) == 0) red[ty][tx >> 5] = acc;
+  __syncthreads();
+  return red[ty][0] + red[ty][1];
 }
 
-// w[l][k][a] = sum_b M_l[k][a][b] V_l[j][b], j the pivot of step s; block (k, l)
+// B[i][i] = h^3 sum_k prod_l V_l[i] M_l[k] V_l[i]^T
+__global__ void __launch_bounds__(kTermThreads * kPairRows)
+tei_diag_kernel(int n_pairs, int R_max, int R_N, const double* __restrict__ V, const double* __restrict__ M,
+                const CholState* fit, double h3, double* __restrict__ d) {
+  __shared__ double red[kPairRows][2];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * kPairRows + ty;
+  double acc = 0.0;
+  if (i < n_pairs)
+    for (int k = tx; k < R_N; k += kTermThreads) {
+      double prod = 1.0;
+      for (int l = 0; l < 3; ++l) {
+        const int r = fit[l].rank;
+        const double* v = V + ((size_t)l * n_pairs + i) * R_max;
+        const double* Mk = M + ((size_t)l * R_N + k) * R_max * R_max;
+        double q = 0.0;
+        for (int a = 0; a < r; ++a) {
+          double row = 0.0;
+          for (int b2 = 0; b2 < r; ++b2) row += Mk[(size_t)a * R_max + b2] * v[b2];
+          q += v[a] * row;
+        }
+        prod *= q;
+      }
+      acc += prod;
+    }
+  const double tot = reduce_terms(acc, red, tx, ty);
+  if (tx == 0 && i < n_pairs) d[i] = h3 * tot;
+}
+
+// wT[l][a][k] = sum_b M_l[k][a][b] V_l[j][b], j the pivot of step s; block (k, l)
 __global__ void tei_w_kernel(int n_pairs, int R_max, int R_N, const double* __restrict__ V,
                              const double* __restrict__ M, const CholState* fit, const CholState* st,
-                             const int* __restrict__ piv, int s, double* __restrict__ w) {
+                             const int* __restrict__ piv, int s, double* __restrict__ wT) {
   if (st->done) return;
   const int k = blockIdx.x, l = blockIdx.y, a = threadIdx.x;
   if (a >= R_max) return;
@@ -215,30 +249,33 @@ __global__ void tei_w_kernel(int n_pairs, int R_max, int R_N, const double* __re
   double acc = 0.0;
   if (a < r)
     for (int b2 = 0; b2 < r; ++b2) acc += Mk[(size_t)a * R_max + b2] * v[b2];
-  w[((size_t)l * R_N + k) * R_max + a] = acc;
+  wT[((size_t)l * R_max + a) * R_N + k] = acc;
 }
 
 // c[i] = B[i][j] = h^3 sum_k prod_l V_l[i] . w[l][k]
-__global__ void __launch_bounds__(kThreads)
-tei_column_kernel(int n_pairs, int R_max, int R_N, const double* __restrict__ V, const double* __restrict__ w,
+__global__ void __launch_bounds__(kTermThreads * kPairRows)
+tei_column_kernel(int n_pairs, int R_max, int R_N, const double* __restrict__ V, const double* __restrict__ wT,
                   const CholState* fit, const CholState* st, double h3, double* __restrict__ c) {
   if (st->done) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_pairs) return;
-  double tot = 0.0;
-  for (int k = 0; k < R_N; ++k) {
-    double prod = 1.0;
-    for (int l = 0; l < 3; ++l) {
-      const int r = fit[l].rank;
-      const double* v = V + ((size_t)l * n_pairs + i) * R_max;
-      const double* wk = w + ((size_t)l * R_N + k) * R_max;
-      double q = 0.0;
-      for (int a = 0; a < r; ++a) q += v[a] * wk[a];
-      prod *= q;
+  __shared__ double red[kPairRows][2];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = blockIdx.x * kPairRows + ty;
+  double acc = 0.0;
+  if (i < n_pairs)
+    for (int k = tx; k < R_N; k += kTermThreads) {
+      double prod = 1.0;
+      for (int l = 0; l < 3; ++l) {
+        const int r = fit[l].rank;
+        const double* v = V + ((size_t)l * n_pairs + i) * R_max;
+        const double* w = wT + (size_t)l * R_max * R_N + k;
+        double q = 0.0;
+        for (int a = 0; a < r; ++a) q += v[a] * w[(size_t)a * R_N];
+        prod *= q;
+      }
+      acc += prod;
     }
-    tot += prod;
-  }
-  c[i] = h3 * tot;
+  const double tot = reduce_terms(acc, red, tx, ty);
+  if (tx == 0 && i < n_pairs) c[i] = h3 * tot;
 }
 
 __global__ void ranks_kernel(const CholState* fit, const CholState* st, int* __restrict__ ranks) {
@@ -365,6 +402,7 @@ extern "C" int tei_cholesky(const cpc_kernel* P, int n_b, const double* U_prims,
   const int n = P->n, R = tei::kMaxRankDF, RN = P->R_N;
   const int T = tei::kThreads;
   // 1. density fitting per axis
+  const int t_fit = timing_begin("tei_fit", s);
   for (int l = 0; l < 3; ++l) {
     const double* Ul = U_prims + (size_t)l * n_b * n;
     int* pv = piv_fit + l * R;
@@ -372,8 +410,10 @@ extern "C" int tei_cholesky(const cpc_kernel* P, int n_b, const double* U_prims,
     tei::init_state_kernel<<<1, tei::kPickThreads, 0, s>>>(n, dA, tol_df, st + l);
     for (int step = 0; step < max_rank_df; ++step) {
       tei::pick_kernel<<<1, tei::kPickThreads, 0, s>>>(n, dA, step, st + l, pv);
-      tei::side_column_kernel<<<(n + T - 1) / T, T, 0, s>>>(n, n_pairs, Ul, pa, pb, st + l, pv, step, c);
-      tei::update_kernel<<<(n + T - 1) / T, T, 0, s>>>(n, step, size_t(n), LA, c, dA, st + l, pv);
+      tei::side_column_kernel<<<(n + tei::kRows - 1) / tei::kRows, dim3(tei::kRows, tei::kGroups), 0, s>>>(
+          n, n_pairs, Ul, pa, pb, st + l, pv, step, c);
+      tei::update_kernel<<<(n + tei::kRows - 1) / tei::kRows, dim3(tei::kRows, tei::kGroups), 0, s>>>(
+          n, step, size_t(n), LA, c, dA, st + l, pv);
     }
     tei::fit_solve_kernel<<<(n + T - 1) / T, T, 0, s>>>(n, R, LA, pv, st + l, Uf + (size_t)l * R * n);
     const long long nv = (long long)n_pairs * R;
@@ -381,24 +421,32 @@ extern "C" int tei_cholesky(const cpc_kernel* P, int n_b, const double* U_prims,
                                                                      V + (size_t)l * n_pairs * R);
     CPC_LAUNCH_CHECK("tei_cholesky: density fitting");
   }
+  timing_end(t_fit, s);
   // 2. convolution matrices M_k^(l) = U^T (p_k * U)
+  const int t_conv = timing_begin("tei_conv_matrices", s);
   CPC_CUDA(cudaMemsetAsync(czero, 0, R * sizeof(double), s));
   int st2 = cp_hartree_energy(P, R, Uf, czero, W, M, E, CPC_FP64, at(Ly.hws), cp_hartree_energy_workspace(P, R, CPC_FP64),
                               stream);
+  timing_end(t_conv, s);
   if (st2) return st2;
   // 3. TEI diagonal and truncated Cholesky
+  const int t_fac = timing_begin("tei_factor", s);
   const double h3 = P->h * P->h * P->h;
   tei::CholState* sb = st + 3;
-  tei::tei_diag_kernel<<<(n_pairs + T - 1) / T, T, 0, s>>>(n_pairs, R, RN, V, M, st, h3, dB);
+  const dim3 tb(tei::kTermThreads, tei::kPairRows);
+  const unsigned tg = (n_pairs + tei::kPairRows - 1) / tei::kPairRows;
+  tei::tei_diag_kernel<<<tg, tb, 0, s>>>(n_pairs, R, RN, V, M, st, h3, dB);
   tei::init_state_kernel<<<1, tei::kPickThreads, 0, s>>>(n_pairs, dB, tol_b, sb);
   CPC_CUDA(cudaMemsetAsync(L, 0, sizeof(double) * (size_t)max_rank_b * n_pairs, s));
   for (int step = 0; step < max_rank_b; ++step) {
     tei::pick_kernel<<<1, tei::kPickThreads, 0, s>>>(n_pairs, dB, step, sb, piv_b);
     tei::tei_w_kernel<<<dim3(RN, 3), R, 0, s>>>(n_pairs, R, RN, V, M, st, sb, piv_b, step, wv);
-    tei::tei_column_kernel<<<(n_pairs + T - 1) / T, T, 0, s>>>(n_pairs, R, RN, V, wv, st, sb, h3, c);
-    tei::update_kernel<<<(n_pairs + T - 1) / T, T, 0, s>>>(n_pairs, step, size_t(n_pairs), L, c, dB, sb, piv_b);
+    tei::tei_column_kernel<<<tg, tb, 0, s>>>(n_pairs, R, RN, V, wv, st, sb, h3, c);
+    tei::update_kernel<<<(n_pairs + tei::kRows - 1) / tei::kRows, dim3(tei::kRows, tei::kGroups), 0, s>>>(
+        n_pairs, step, size_t(n_pairs), L, c, dB, sb, piv_b);
   }
   tei::ranks_kernel<<<1, 32, 0, s>>>(st, sb, ranks);
+  timing_end(t_fac, s);
   CPC_LAUNCH_CHECK("tei_cholesky: TEI factorisation");
   return CPC_OK;
 }
