@@ -22,6 +22,9 @@ Modules and the passages they follow (Khoromskaia & Khoromskij, arXiv:1504.06289
                       CoulombLatTensCan), their evaluation on a sub-grid, and the
                       interaction energy of the lattice charges (Sec. 5.3,
                       Eqs. EnergyLatSum, EnergyLattice).
+* ``tei``             two-electron integrals by 1D density fitting and a
+                      truncated Cholesky factorisation of the TEI matrix, and
+                      J(D) for a density matrix (Sec. 3.2).
 * ``nuclear``         nuclear potential of a molecule by windowed shifts of the
                       master kernel and its Galerkin matrix (Sec. 3.3).
 * ``closed_forms``    analytic Gaussian Coulomb results used only to pin the
