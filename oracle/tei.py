@@ -25,6 +25,11 @@ The steps follow the paper's order:
    J_{mu nu} = sum_{kappa, lambda} b_{mu nu, kappa lambda} D_{kappa lambda}
              = (L (L^T d))_{mu nu},  d_{kappa lambda} = (2 - delta_{kappa lambda}) D_{kappa lambda}
    over the pairs kappa <= lambda.
+5. The exchange matrix: the exchange operator of Sec. 3.1,
+   K_km,a = <G_k . phi_a, (G_m . phi_a) * P_R> with phi_a = sum_mu c_{mu a} G_mu,
+   summed over the orbitals a with D = sum_a c_a c_a^T, is
+   K_km = sum_{mu nu} D_{mu nu} b_{k mu, m nu}; with B ~ L L^T,
+   K = sum_s X_s D X_s^T, X_s[k, mu] = L[(k mu), s] (the pair of g_k g_mu).
 """
 from __future__ import annotations
 
@@ -137,3 +142,35 @@ def coulomb_from_cholesky(L: np.ndarray, D: np.ndarray, pa, pb) -> np.ndarray:
     """J over the pairs (step 4)."""
     d = np.where(pa == pb, 1.0, 2.0) * D[pa, pb]
     return L @ (L.T @ d)
+
+
+def pair_index(nb: int, pa: np.ndarray, pb: np.ndarray) -> np.ndarray:
+    """(nb, nb) map of (kappa, lambda) to the pair holding g_kappa g_lambda (either order), -1 if none."""
+    idx = -np.ones((nb, nb), dtype=np.int64)
+    idx[pa, pb] = np.arange(len(pa))
+    idx[pb, pa] = np.arange(len(pa))
+    return idx
+
+
+def exchange_from_tei(B: np.ndarray, D: np.ndarray, pa, pb) -> np.ndarray:
+    """Exchange matrix K_km = sum_a K_km,a = sum_{mu nu} D_{mu nu} (k mu | m nu) (Sec. 3.1, the
+    exchange operator K_km,a with the orbitals summed into D = sum_a c_a c_a^T), from a TEI
+    matrix B over the pairs."""
+    nb = D.shape[0]
+    idx = pair_index(nb, pa, pb)
+    K = np.zeros((nb, nb))
+    for k in range(nb):
+        for m in range(nb):
+            K[k, m] = float(np.sum(B[np.ix_(idx[k], idx[m])] * D))
+    return K
+
+
+def exchange_from_cholesky(L: np.ndarray, D: np.ndarray, pa, pb) -> np.ndarray:
+    """The same from B ~ L L^T: K = sum_s X_s D X_s^T with X_s[k, mu] = L[(k mu), s]."""
+    nb = D.shape[0]
+    idx = pair_index(nb, pa, pb)
+    K = np.zeros((nb, nb))
+    for s in range(L.shape[1]):
+        X = L[idx, s]
+        K += X @ D @ X.T
+    return K

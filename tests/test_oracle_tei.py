@@ -108,3 +108,35 @@ def test_coulomb_matrix_of_a_diagonal_density_agrees_with_the_product_form():
     items = list(zip(pa.tolist(), pb.tolist()))
     J0, _ = coulomb.coulomb_items(n, b, basis, P, items)
     assert np.max(np.abs(J - J0)) < 1e-7 * np.max(np.abs(J0))
+
+
+def test_exchange_matrix_against_analytic_integrals_and_the_factor():
+    # K_km = sum_{mu nu} D_{mu nu} (k mu | m nu): from the direct TEI matrix
+    # (converging to the analytic integrals) and from B ~ L L^T
+    b, M, nb = 6.0, 20, 4
+    a, X = _prims(nb, 13)
+    pa, pb = tei.pair_list(nb)
+    rng = np.random.default_rng(1)
+    C = rng.standard_normal((nb, 2))
+    D = C @ C.T  # two orbitals
+    def eri(k, mu, m, nu):
+        p, q = a[k] + a[mu], a[m] + a[nu]
+        K1 = math.exp(-a[k] * a[mu] / p * float(np.sum((X[k] - X[mu]) ** 2)))
+        K2 = math.exp(-a[m] * a[nu] / q * float(np.sum((X[m] - X[nu]) ** 2)))
+        P1, P2 = (a[k] * X[k] + a[mu] * X[mu]) / p, (a[m] * X[m] + a[nu] * X[nu]) / q
+        return K1 * K2 * float(cf.coulomb_pair(p, P1, q, P2))
+    K0 = np.array([[sum(D[mu, nu] * eri(k, mu, m, nu) for mu in range(nb) for nu in range(nb))
+                    for m in range(nb)] for k in range(nb)])
+    errs = []
+    for n in (64, 128):
+        h = 2 * b / n
+        U = cp.sample_gaussians(n, b, a, X)
+        P = _kernel(n, b, M)
+        Bd = tei.tei_matrix_direct(U, P, h, pa, pb)
+        K = tei.exchange_from_tei(Bd, D, pa, pb)
+        errs.append(np.max(np.abs(K - K0)) / np.max(np.abs(K0)))
+        L, *_ = tei.tei_cholesky(U, P, h, pa, pb, 1e-13, 1e-13, 128, len(pa))
+        Kc = tei.exchange_from_cholesky(L, D, pa, pb)
+        assert np.max(np.abs(Kc - K)) < 1e-7 * np.max(np.abs(K))
+        assert np.allclose(Kc, Kc.T, rtol=0, atol=1e-12 * np.max(np.abs(Kc)))
+    assert errs[1] < 2e-3 and errs[0] / errs[1] > 3.0
