@@ -762,9 +762,9 @@ def run_nuclear(args, ws, rank, local):
 
 
 def run_tei(args, ws, rank, local):
-    """f2: two-electron integrals of 80 s primitives (3240 pairs): 1D density
-    fitting, convolution matrices, truncated Cholesky of the TEI matrix and
-    J(D) for one density matrix per step (Sec. 3.2); float64."""
+    """f2/f4: two-electron integrals of 80 s primitives (3240 pairs): 1D density
+    fitting, convolution matrices, truncated Cholesky of the TEI matrix, and
+    J(D) and K(D) for one density matrix per step (Secs. 3.1, 3.2); float64."""
     import torch
     import paper_1504_06289_gb300 as cpc
     from oracle import coulomb as ocoul
@@ -791,6 +791,7 @@ def run_tei(args, ws, rank, local):
     stream = torch.cuda.current_stream(dev)
     def step():
         L, ranks = cpc.tei_cholesky(P, U, pa, pb, cfg["tol_df"], cfg["tol_b"], 128, cfg["max_rank_b"])
+        cpc.tei_exchange(L, ranks, pa, pb, D)
         return cpc.tei_coulomb(L, ranks, pa, pb, D), L, ranks
     ms = _timed(stream, step, args.steps, max(1, min(args.warmup, 3)))
     torch.cuda.synchronize()
@@ -828,7 +829,7 @@ def run_tei(args, ws, rank, local):
         cpu = {"value": 1.0 / (3 * dt), "unit": "factorisations/s (fitting stage of one axis x 3, lower bound)",
                "cores": os.cpu_count(), "kind": "oracle",
                "sample": "the 1D density fitting of one axis (A = G G^T and its truncated Cholesky), times 3"}
-    _line(args, ws, "TEI factorisations + J(D)/s", ws / (ms * 1e-3), "factorisations/s", ms, "f64",
+    _line(args, ws, "TEI factorisations + J(D) + K(D)/s", ws / (ms * 1e-3), "factorisations/s", ms, "f64",
           {"workload": name, "n": n, "primitives": nb, "pairs": npair, "R_N": R_N, "tol_df": cfg["tol_df"],
            "tol_b": cfg["tol_b"]},
           ranks={"fit": rk[:3], "tei": RB}, phases_ms=phases, rel_diff_J_vs_coulomb_path=rel_vs_coulomb,

@@ -327,6 +327,19 @@ int tei_cholesky(const cpc_kernel* P, int n_b, const double* U_prims, int n_pair
 int tei_coulomb(int n_b, int n_pairs, const int* pa, const int* pb, int max_rank_b, const double* L,
                 const int* ranks, const double* D, double* J, void* ws, size_t ws_bytes, void* stream);
 
+/* Exchange matrix of a density matrix D from the TEI factor (Sec. 3.1, the
+ * exchange operator K_km,a = <G_k . phi_a, (G_m . phi_a) * P_R> summed over the
+ * orbitals phi_a = sum_mu c_{mu a} g_mu, D = sum_a c_a c_a^T):
+ *   K[k][m] = sum_{mu,nu} D[mu][nu] b_{(k mu),(m nu)}  ~  sum_{s < R_B} (X_s D X_s^T)[k][m],
+ *   X_s[k][mu] = L[s][pair of g_k g_mu]
+ * (a product g_k g_mu with no pair in (pa, pb) contributes 0).  n_b <= 1024;
+ * D, K: device float64 [n_b][n_b]; L, ranks as written by tei_cholesky.
+ * Workspace: tei_exchange_workspace(n_b, max_rank_b) bytes, 256-byte
+ * aligned.  Returns CPC_OK, CPC_ERR_INVALID, CPC_ERR_WORKSPACE or CPC_ERR_CUDA. */
+size_t tei_exchange_workspace(int n_b, int max_rank_b);
+int tei_exchange(int n_b, int n_pairs, const int* pa, const int* pb, int max_rank_b, const double* L,
+                 const int* ranks, const double* D, double* K, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- a9/a10: assembled lattice sums (Sec. 5.1, Eq. CoulombLatTensCan) -----
  * With a MASTER kernel p~_q and, per axis l, L[l] charge positions given as
  * grid-cell edge indices e[l][k] in [0, n] (a charge at x = -b + e h):

@@ -25,7 +25,7 @@ __all__ = [
     "cp_convolve", "cp_hartree_energy", "cp_hartree_energy_from_factors",
     "cp_factor_spectra", "cp_convolve_from_spectra", "cp_hartree_energy_from_spectra",
     "cp_hartree_energy_noalloc", "cp_hartree_energy_adjoint", "cp_gaussian_param_grad",
-    "coulomb_matrix", "nuclear_matrix", "tei_cholesky", "tei_coulomb", "lattice_potential_sum", "lattice_interaction_energy", "CPHartreeEnergy", "CpcError",
+    "coulomb_matrix", "nuclear_matrix", "tei_cholesky", "tei_coulomb", "tei_exchange", "lattice_potential_sum", "lattice_interaction_energy", "CPHartreeEnergy", "CpcError",
 ]
 
 
@@ -402,6 +402,18 @@ def tei_coulomb(L: torch.Tensor, ranks: torch.Tensor, pa: torch.Tensor, pb: torc
     check(lib.tei_coulomb(n_b, n_pairs, _ptr(pa), _ptr(pb), max_rank_b, _ptr(L), _ptr(ranks), _ptr(D), _ptr(J),
                           _ptr(ws), ws.numel(), _stream(stream)), "tei_coulomb")
     return J
+
+
+def tei_exchange(L: torch.Tensor, ranks: torch.Tensor, pa: torch.Tensor, pb: torch.Tensor, D: torch.Tensor,
+                 stream=None) -> torch.Tensor:
+    """Exchange matrix K (n_b, n_b) of the density matrix D from tei_cholesky's factor."""
+    lib = load()
+    n_b, n_pairs, max_rank_b = D.shape[0], pa.numel(), L.shape[0]
+    K = torch.empty((n_b, n_b), dtype=torch.float64, device=L.device)
+    ws = _workspace(lib.tei_exchange_workspace(n_b, max_rank_b), L.device)
+    check(lib.tei_exchange(n_b, n_pairs, _ptr(pa), _ptr(pb), max_rank_b, _ptr(L), _ptr(ranks), _ptr(D), _ptr(K),
+                           _ptr(ws), ws.numel(), _stream(stream)), "tei_exchange")
+    return K
 
 
 def lattice_potential_sum(P: NewtonKernel, edges, sub: torch.Tensor | None = None, precision: str = "fp64",

@@ -45,6 +45,8 @@ PROTOTYPES = {
     "tei_cholesky_workspace": (sz, [vp, i32, i32]),
     "tei_cholesky": (i32, [vp, i32, vp, i32, vp, vp, f64, f64, i32, i32, vp, vp, vp, sz, vp]),
     "tei_coulomb": (i32, [i32, i32, vp, vp, i32, vp, vp, vp, vp, vp, sz, vp]),
+    "tei_exchange_workspace": (sz, [i32, i32]),
+    "tei_exchange": (i32, [i32, i32, vp, vp, i32, vp, vp, vp, vp, vp, sz, vp]),
     "nuclear_matrix": (i32, [vp, i32, vp, i32, vp, vp, i32, vp, vp, vp, vp, i32, vp, sz, vp]),
     "cpc_kernel_timing": (i32, [i32]),
     "cpc_kernel_timing_read": (i32, [C.c_char_p, P_f64, P_i32]),

@@ -328,6 +328,52 @@ __global__ void l_t_kernel(int n_pairs, const double* __restrict__ L, const doub
   J[P] = acc;
 }
 
+// ---- K(D) ------------------------------------------------------------------
+// map[k][m] = the pair holding g_k g_m (either order), -1 if none
+__global__ void pair_map_kernel(int n_b, int n_pairs, const int* __restrict__ pa, const int* __restrict__ pb,
+                                int* __restrict__ map) {
+  const int P = blockIdx.x * blockDim.x + threadIdx.x;
+  if (P >= n_pairs) return;
+  const int a = pa[P], b = pb[P];
+  if (a < 0 || a >= n_b || b < 0 || b >= n_b) return;  // outside the basis: no entry
+  map[(size_t)a * n_b + b] = P;
+  map[(size_t)b * n_b + a] = P;
+}
+
+// Z[s][k][nu] = sum_mu X_s[k][mu] D[mu][nu], X_s[k][mu] = L[s][map[k][mu]]; block (s, k)
+__global__ void exchange_z_kernel(int n_b, int n_pairs, const double* __restrict__ L, const int* __restrict__ map,
+                                  const int* __restrict__ ranks, const double* __restrict__ D,
+                                  double* __restrict__ Z) {
+  const int s = blockIdx.x, k = blockIdx.y, nu = threadIdx.x;
+  if (s >= ranks[3] || nu >= n_b) return;
+  const double* Ls = L + (size_t)s * n_pairs;
+  double acc = 0.0;
+  for (int mu = 0; mu < n_b; ++mu) {
+    const int P = map[(size_t)k * n_b + mu];
+    if (P >= 0) acc += Ls[P] * D[(size_t)mu * n_b + nu];
+  }
+  Z[((size_t)s * n_b + k) * n_b + nu] = acc;
+}
+
+// K[k][m] = sum_{s < R_B} sum_nu Z[s][k][nu] X_s[m][nu]
+__global__ void exchange_k_kernel(int n_b, int n_pairs, const double* __restrict__ L, const int* __restrict__ map,
+                                  const int* __restrict__ ranks, const double* __restrict__ Z,
+                                  double* __restrict__ K) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x, k = blockIdx.y;
+  if (m >= n_b) return;
+  const int r = ranks[3];
+  double acc = 0.0;
+  for (int s = 0; s < r; ++s) {
+    const double* Ls = L + (size_t)s * n_pairs;
+    const double* z = Z + ((size_t)s * n_b + k) * n_b;
+    for (int nu = 0; nu < n_b; ++nu) {
+      const int P = map[(size_t)m * n_b + nu];
+      if (P >= 0) acc += z[nu] * Ls[P];
+    }
+  }
+  K[(size_t)k * n_b + m] = acc;
+}
+
 // workspace layout
 struct Layout {
   size_t state, piv_fit, piv_b, dA, LA, c, Uf, V, M, W, hws, czero, E, dB, w, total;
@@ -468,5 +514,31 @@ extern "C" int tei_coulomb(int n_b, int n_pairs, const int* pa, const int* pb, i
   tei::lt_d_kernel<<<max_rank_b, T, 0, s>>>(n_pairs, L, dv, ranks, t);
   tei::l_t_kernel<<<(n_pairs + T - 1) / T, T, 0, s>>>(n_pairs, L, t, ranks, J);
   CPC_LAUNCH_CHECK("tei_coulomb");
+  return CPC_OK;
+}
+
+extern "C" size_t tei_exchange_workspace(int n_b, int max_rank_b) {
+  if (n_b <= 0 || max_rank_b <= 0) return 0;
+  return align256(sizeof(int) * (size_t)n_b * n_b) + sizeof(double) * (size_t)max_rank_b * n_b * n_b;
+}
+
+extern "C" int tei_exchange(int n_b, int n_pairs, const int* pa, const int* pb, int max_rank_b, const double* L,
+                            const int* ranks, const double* D, double* K, void* ws, size_t ws_bytes, void* stream) {
+  clear_error();
+  if (n_b <= 0 || n_b > 1024 || n_pairs <= 0 || max_rank_b <= 0 || !pa || !pb || !L || !ranks || !D || !K)
+    return fail(CPC_ERR_INVALID, "tei_exchange: bad arguments");
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255))
+    return fail(CPC_ERR_WORKSPACE, "tei_exchange: workspace NULL or not 256-byte aligned");
+  if (ws_bytes < tei_exchange_workspace(n_b, max_rank_b))
+    return fail(CPC_ERR_WORKSPACE, "tei_exchange: workspace too small");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* map = static_cast<int*>(ws);
+  double* Z = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + align256(sizeof(int) * (size_t)n_b * n_b));
+  CPC_CUDA(cudaMemsetAsync(map, 0xff, sizeof(int) * (size_t)n_b * n_b, s));  // -1
+  const int T = tei::kThreads;
+  tei::pair_map_kernel<<<(n_pairs + T - 1) / T, T, 0, s>>>(n_b, n_pairs, pa, pb, map);
+  tei::exchange_z_kernel<<<dim3(max_rank_b, n_b), ((n_b + 31) / 32) * 32, 0, s>>>(n_b, n_pairs, L, map, ranks, D, Z);
+  tei::exchange_k_kernel<<<dim3((n_b + 127) / 128, n_b), 128, 0, s>>>(n_b, n_pairs, L, map, ranks, Z, K);
+  CPC_LAUNCH_CHECK("tei_exchange");
   return CPC_OK;
 }

@@ -287,6 +287,9 @@ def test_tei80_n4096_cholesky(cpc):
         J = cpc.tei_coulomb(L, ranks, pa, pb, dev(D)).cpu().numpy()
         J0 = otei.coulomb_from_cholesky(L0, D, pa0, pb0)
         assert np.max(np.abs(J - J0)) < 1e-6 * np.max(np.abs(J0))
+        K = cpc.tei_exchange(L, ranks, pa, pb, dev(D)).cpu().numpy()
+        K0 = otei.exchange_from_cholesky(L0, D, pa0, pb0)
+        assert np.max(np.abs(K - K0)) < 1e-6 * np.max(np.abs(K0))
     # the same J for D = diag(w) from the Coulomb-matrix path (V_H factors of
     # rho = sum w g^2, no density fitting, no Cholesky)
     d1 = dev(np.ones(nb))

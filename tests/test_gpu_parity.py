@@ -377,6 +377,12 @@ def test_tei_cholesky_and_coulomb(cpc):
         J = cpc.tei_coulomb(L, ranks, pa, pb, dev(D)).cpu().numpy()
         J0 = otei.coulomb_from_cholesky(L0, D, pa0, pb0)
         assert np.max(np.abs(J - J0)) < 1e-9 * np.max(np.abs(J0))
+    # exchange: K = sum_{mu nu} D (k mu | m nu) from the factor
+    C = rng.standard_normal((nb, 2))
+    Dk = C @ C.T
+    K = cpc.tei_exchange(L, ranks, pa, pb, dev(Dk)).cpu().numpy()
+    K0 = otei.exchange_from_cholesky(L0, Dk, pa0, pb0)
+    assert np.max(np.abs(K - K0)) < 1e-9 * np.max(np.abs(K0))
     # a truncated factorisation stops at its rank cap
     L2, r2 = cpc.tei_cholesky(P, U, pa, pb, 1e-13, 1e-12, 4, 6)
     assert list(r2.cpu().numpy()) == [4, 4, 4, 6]
