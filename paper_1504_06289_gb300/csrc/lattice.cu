@@ -456,37 +456,41 @@ lattice_pairs_kernel(int n, Edges ed, int* __restrict__ ghist) {
     if (hist[i]) atomicAdd(&gh[i], hist[i]);
 }
 
-// the nonzero bins of axis blockIdx.x in order of d, as pairs (d, c(d))
+// the nonzero bins of axis blockIdx.x in order of d, as pairs (d, c(d)):
+// chunks of 1024 consecutive bins (coalesced), each thread's position from a
+// warp ballot and a block scan of the warp counts
 __global__ void __launch_bounds__(kPairThreads)
 lattice_diffs_kernel(int n, const int* __restrict__ ghist, int* __restrict__ list, int* __restrict__ list_len) {
-  __shared__ int wsum[kPairThreads / 32];
-  const int l = blockIdx.x, t = threadIdx.x, nb = 2 * n;
+  __shared__ int wcount[kPairThreads / 32];
+  __shared__ int woff[kPairThreads / 32 + 1];
+  const int l = blockIdx.x, t = threadIdx.x, lane = t & 31, warp = t >> 5, nb = 2 * n;
   const int* gh = ghist + (size_t)l * nb;
-  // thread t owns bins [t * per, (t+1) * per)
-  const int per = (nb + kPairThreads - 1) / kPairThreads;
-  const int b0 = t * per, b1 = min(nb, b0 + per);
-  int cnt = 0;
-  for (int i = b0; i < b1; ++i) cnt += gh[i] != 0;
-  // exclusive scan of cnt over the block
-  int incl = cnt;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-    if ((t & 31) >= o) incl += v;
-  }
-  if ((t & 31) == 31) wsum[t >> 5] = incl;
-  __syncthreads();
-  int off = incl - cnt;
-  for (int w = 0; w < (t >> 5); ++w) off += wsum[w];
   int* out = list + (size_t)l * 2 * nb;  // up to 2n pairs
-  for (int i = b0; i < b1; ++i) {
-    const int v = gh[i];
-    if (v) {
-      out[2 * off] = i - n;
-      out[2 * off + 1] = v;
-      ++off;
+  int base = 0;
+  for (int c0 = 0; c0 < nb; c0 += kPairThreads) {
+    const int i = c0 + t;
+    const int v = (i < nb) ? gh[i] : 0;
+    const unsigned ball = __ballot_sync(0xffffffffu, v != 0);
+    if (lane == 0) wcount[warp] = __popc(ball);
+    __syncthreads();
+    if (t == 0) {
+      int acc = 0;
+      for (int w = 0; w < kPairThreads / 32; ++w) {
+        woff[w] = acc;
+        acc += wcount[w];
+      }
+      woff[kPairThreads / 32] = acc;
     }
+    __syncthreads();
+    if (v) {
+      const int pos = base + woff[warp] + __popc(ball & ((1u << lane) - 1u));
+      out[2 * pos] = i - n;
+      out[2 * pos + 1] = v;
+    }
+    base += woff[kPairThreads / 32];
+    __syncthreads();  // wcount and woff are rewritten by the next chunk
   }
-  if (t == kPairThreads - 1) list_len[l] = off;
+  if (t == 0) list_len[l] = base;
 }
 
 __global__ void __launch_bounds__(kEnergyThreads)
@@ -513,20 +517,23 @@ lattice_energy_kernel(int n, int R_N, const double* __restrict__ Pm, const int* 
   }
 }
 
-// E_L = Z^2 h^-3 / 2 sum_q (prod_l T[l][q] - L1 L2 L3 t0_q^3), summed in order
-// of q; products and the difference rounded separately (no fused multiply-add),
-// so that a single charge gives exactly 0
+// E_L = Z^2 h^-3 / 2 sum_q (prod_l T[l][q] - L1 L2 L3 t0_q^3): the terms in
+// parallel, their sum in order of q; products and the difference rounded
+// separately (no fused multiply-add), so that a single charge gives exactly 0
 __global__ void lattice_energy_sum_kernel(int n, int R_N, const double* __restrict__ Pm, const double* __restrict__ T,
                                           double count, double scale, double* __restrict__ E) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
+  __shared__ double term[kMaxRN];
+  for (int q = threadIdx.x; q < R_N; q += blockDim.x) {
+    const double* row = Pm + (size_t)q * 2 * n + n;
+    const double t0 = 0.5 * (row[-1] + row[0]);
+    const double lat = __dmul_rn(__dmul_rn(T[q], T[R_N + q]), T[2 * R_N + q]);
+    const double self = __dmul_rn(count, __dmul_rn(__dmul_rn(t0, t0), t0));
+    term[q] = __dsub_rn(lat, self);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     double s = 0.0;
-    for (int q = 0; q < R_N; ++q) {
-      const double* row = Pm + (size_t)q * 2 * n + n;
-      const double t0 = 0.5 * (row[-1] + row[0]);
-      const double lat = __dmul_rn(__dmul_rn(T[q], T[R_N + q]), T[2 * R_N + q]);
-      const double self = __dmul_rn(count, __dmul_rn(__dmul_rn(t0, t0), t0));
-      s = __dadd_rn(s, __dsub_rn(lat, self));
-    }
+    for (int q = 0; q < R_N; ++q) s = __dadd_rn(s, term[q]);
     *E = __dmul_rn(scale, s);
   }
 }
@@ -641,7 +648,7 @@ extern "C" int lattice_interaction_energy(const cpc_kernel* P, const int* L, con
   CPC_LAUNCH_CHECK("lattice_energy_kernel");
   const double count = double(L[0]) * double(L[1]) * double(L[2]);
   const double scale = 0.5 * Z * Z / (P->h * P->h * P->h);
-  lattice_energy_sum_kernel<<<1, 32, 0, s>>>(n, P->R_N, P->d_p, T, count, scale, E_L);
+  lattice_energy_sum_kernel<<<1, 128, 0, s>>>(n, P->R_N, P->d_p, T, count, scale, E_L);
   CPC_LAUNCH_CHECK("lattice_energy_sum_kernel");
   return CPC_OK;
 }
