@@ -218,7 +218,8 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "convolutions/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if not args.rf else f"{WORKLOAD} (R_f={R_f} profiling case)", "n": n, "R_f": cfg["R_f"], "R_N": 2 * M + 1,
+        "config": {"workload": WORKLOAD if not args.rf else f"{WORKLOAD} (R_f={args.rf} profiling case)", "n": n,
+                   "R_f": cfg["R_f"], "R_N": 2 * M + 1,
                    "sample_per_step": "4 Gaussians x 4 kernel terms x 3 axes (48 direct convolutions)"},
         "cpu_baseline": {"value": value, "unit": "convolutions/s", "cores": os.cpu_count(), "kind": "oracle",
                          "sample": "48 direct length-8192 convolutions per step"},
