@@ -345,6 +345,11 @@ subgrid_tc_kernel(int n_sub, float inv_h3, const unsigned char* __restrict__ scr
     const int e3 = s_ok ? __ldg(eS + s3) : 0;
     const bool fast3 = e3 > -100 && e3 < 100;
     const float f3 = ldexpf(inv_h3, e3 - 16);
+    // this warp's 32 pairs start at prow0; every store of a warp writes 32
+    // consecutive s3 of one pair
+    const long long prow0 = pair0 + half * (NP / 2);
+    const bool full = prow0 + NP / 2 <= n_pairs;
+    float* vrow = V + prow0 * n_sub + s3;
 #pragma unroll
     for (int cb = 0; cb < NP / 16; ++cb) {
       float v0[8], v1[8], v2[8], v3[8];
@@ -354,16 +359,33 @@ subgrid_tc_kernel(int n_sub, float inv_h3, const unsigned char* __restrict__ scr
       umma::tmem_ld8(lane_base + 3 * NP + cb * 8, v3);
       umma::tmem_ld_wait();
       if (s_ok) {
+        const int kb = half * (NP / 2) + cb * 8;
+        const float4 fa = *reinterpret_cast<const float4*>(fP + kb);
+        const float4 fb = *reinterpret_cast<const float4*>(fP + kb + 4);
+        const float fpv[8] = {fa.x, fa.y, fa.z, fa.w, fb.x, fb.y, fb.z, fb.w};
+        bool fast = fast3;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int k = half * (NP / 2) + cb * 8 + u;
-          const long long p = pair0 + k;
-          const float f = fmaf(v3[u], 1.0f / 16777216.0f,
-                               fmaf(v2[u], 1.0f / 65536.0f, fmaf(v1[u], 1.0f / 256.0f, v0[u])));
-          const float fp = fP[k];
-          float val = (fast3 && fp != 0.0f) ? (f * fp) * f3 : ldexpf(f, e3 + eP[k] - 16) * inv_h3;
-          if (!ok_wait) val = __int_as_float(0x7fc00000);
-          if (p < n_pairs) __stcs(V + p * n_sub + s3, val);  // a warp writes 32 consecutive s3
+        for (int u = 0; u < 8; ++u) fast = fast && fpv[u] != 0.0f;
+        float val[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          val[u] = fmaf(v3[u], 1.0f / 16777216.0f, fmaf(v2[u], 1.0f / 65536.0f, fmaf(v1[u], 1.0f / 256.0f, v0[u])));
+        if (fast) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) val[u] = (val[u] * fpv[u]) * f3;
+        } else {
+          for (int u = 0; u < 8; ++u) val[u] = ldexpf(val[u], e3 + eP[kb + u] - 16) * inv_h3;
+        }
+        if (!ok_wait)
+#pragma unroll
+          for (int u = 0; u < 8; ++u) val[u] = __int_as_float(0x7fc00000);
+        float* vp = vrow + (size_t)(cb * 8) * n_sub;
+        if (full) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) __stcs(vp + u * n_sub, val[u]);
+        } else {
+          for (int u = 0; u < 8; ++u)
+            if (prow0 + cb * 8 + u < n_pairs) __stcs(vp + u * n_sub, val[u]);
         }
       }
     }
