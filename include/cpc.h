@@ -239,8 +239,9 @@ int cp_gaussian_param_grad(int n, double b, int R, const double* a, const double
  * consecutive 64-column tiles of the R_rho*R_N V_H columns (0 = default 8;
  * else a power of two in [4, 128]).  CPC_FP32 with n a multiple of 128: the
  * tensor-core contraction of cp_hartree_energy (exact bf16 slices of the item
- * factors and of the float32 W_rho) on tiles of 256 item factors x 128 rho
- * factors per kernel term, tiles_per_cta unused; if one of its device-side
+ * factors and of the float32 W_rho) with the R_rho R_N columns (m, q) taken
+ * as one-term factors, on tiles of 256 item factors x 128 columns,
+ * tiles_per_cta unused; if one of its device-side
  * waits gives up, J is written as NaN.  Stream-ordered and allocation-free, so
  * a sequence of these calls can be captured in a CUDA graph.  Workspace:
  * coulomb_matrix_workspace bytes (sized for the smallest tiles_per_cta; for

@@ -643,6 +643,37 @@ static int coulomb_groups(int R_rho, int R_N, int tiles_per_cta) {
   return (n_ct + tiles_per_cta - 1) / tiles_per_cta;
 }
 
+// c_col[m R_N + q] = c_rho[m]: the coefficient of each (factor, term) column
+__global__ void expand_coef_kernel(int R_rho, int R_N, const double* __restrict__ c, double* __restrict__ cq) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < R_rho * R_N) cq[m] = c[m / R_N];
+}
+
+// a view of P with one kernel term: the tensor-core rows form then takes the
+// R_rho R_N columns (m, q) as factors of one term each, so that they fill its
+// 128-column tiles (the product over axes is per column either way)
+static cpc_kernel column_view(const cpc_kernel* P) {
+  cpc_kernel Q;  // only the sizes the contraction reads; no tables
+  Q.n = P->n;
+  Q.b = P->b;
+  Q.h = P->h;
+  Q.kind = P->kind;
+  Q.len = P->len;
+  Q.R_N = 1;
+  return Q;
+}
+
+// workspace of coulomb_contract (after the convolution's)
+static size_t contract_bytes(const cpc_kernel* P, int n_factors, int R_rho, int precision) {
+  if (precision == CPC_FP32 && tc_supported(P)) {
+    const cpc_kernel Q = column_view(P);
+    const int Nc = R_rho * P->R_N;
+    return align256(sizeof(double) * Nc) + align256(sizeof(double) * tc_rows_groups(&Q, Nc) * n_factors) +
+           tc_rows_workspace(&Q, n_factors, Nc);
+  }
+  return align256(sizeof(double) * coulomb_groups(R_rho, P->R_N, kTilesMin) * n_factors);
+}
+
 // contraction + segmented item reduction, after W_rho holds the V_H factors
 // J[t] = scale sum_{r in item t} c_items[r] sum_m c_rho[m] sum_q prod_l <u_r^(l), W_rho[l][m R_N + q]>
 static int coulomb_contract(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
@@ -664,14 +695,21 @@ static int coulomb_contract(const cpc_kernel* P, int n_items, const int* off, in
     st = launch_rows32(P, n_factors, U_items, N, nullptr, c_rho, rowpart, groups, tiles_per_cta, s,
                        static_cast<const double*>(W_rho));
   } else if (tc_supported(P)) {
-    // tensor cores: one row partial per (kernel term, 128-column tile); the
-    // tensor-core workspace follows the row partials
-    const int tgroups = (int)tc_rows_groups(P, R_rho);
-    void* tws = reinterpret_cast<unsigned char*>(rowpart) + align256(sizeof(double) * (size_t)tgroups * n_factors);
-    st = launch_rows_tc(P, n_factors, U_items, R_rho, static_cast<const float*>(W_rho), c_rho, rowpart, tws, s);
+    // tensor cores over the R_rho R_N columns (m, q) as one-term factors:
+    // workspace = column coefficients, one row partial per 128-column tile,
+    // then the tensor-core slices
+    const cpc_kernel Q = column_view(P);
+    const int Nc = R_rho * P->R_N;
+    double* cq = rowpart;
+    double* rp = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(rowpart) + align256(sizeof(double) * Nc));
+    expand_coef_kernel<<<(Nc + 255) / 256, 256, 0, s>>>(R_rho, P->R_N, c_rho, cq);
+    CPC_LAUNCH_CHECK("expand_coef_kernel");
+    const int tgroups = (int)tc_rows_groups(&Q, Nc);
+    void* tws = reinterpret_cast<unsigned char*>(rp) + align256(sizeof(double) * (size_t)tgroups * n_factors);
+    st = launch_rows_tc(&Q, n_factors, U_items, Nc, static_cast<const float*>(W_rho), cq, rp, tws, s);
     if (st) return st;
-    item_reduce_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(n_items, off, c_items, rowpart, tgroups, n_factors,
-                                                           scale, J, tc_rows_status_ptr(P, n_factors, R_rho, tws));
+    item_reduce_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(n_items, off, c_items, rp, tgroups, n_factors, scale, J,
+                                                           tc_rows_status_ptr(&Q, n_factors, Nc, tws));
     CPC_LAUNCH_CHECK("item_reduce_kernel");
     return CPC_OK;
   } else {
@@ -704,12 +742,7 @@ static int check_coulomb(const cpc_kernel* P, int n_items, const int* off, int n
 extern "C" size_t coulomb_matrix_workspace(const cpc_kernel* P, int n_items, int n_factors, int R_rho,
                                            int precision) {
   if (!P || n_items <= 0 || n_factors <= 0 || R_rho <= 0) return 0;
-  if (precision == CPC_FP32 && tc_supported(P))  // row partials, then the tensor-core slices
-    return cp_convolve_workspace(P, R_rho, precision) +
-           align256(sizeof(double) * tc_rows_groups(P, R_rho) * n_factors) +
-           tc_rows_workspace(P, n_factors, R_rho);
-  const size_t groups = coulomb_groups(R_rho, P->R_N, kTilesMin);
-  return cp_convolve_workspace(P, R_rho, precision) + align256(sizeof(double) * groups * n_factors);
+  return cp_convolve_workspace(P, R_rho, precision) + contract_bytes(P, n_factors, R_rho, precision);
 }
 
 extern "C" int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
@@ -775,41 +808,16 @@ extern "C" int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* 
 
 // ---- nuclear potential and its Galerkin matrix (Sec. 3.3) ---------------------
 // V[t] = -sum_{r in item t} c_items[r] sum_a Z[a] sum_q prod_l <u_r^(l), F[l][a R_N + q]>,
-// F the master kernel windowed onto each nucleus (launch_window).  The product
-// over axes is taken per column m = a R_N + q, so this is the Coulomb
-// contraction over n_nuc R_N columns of one term each (a kernel view with
-// R_N = 1, the charge of column m being Z[m / R_N]) and the scale -1 in place
-// of h^3 (the Galerkin vectors already carry h^3).  Folding q into the
-// columns fills the 128-column tiles of the tensor-core form (10 nuclei x 51
-// terms: 4 tiles of one term instead of one 10-column tile per term).
-__global__ void expand_charges_kernel(int n_nuc, int R_N, const double* __restrict__ Z, double* __restrict__ Zq) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m < n_nuc * R_N) Zq[m] = Z[m / R_N];
-}
-
-static cpc_kernel column_view(const cpc_kernel* P) {
-  cpc_kernel Q;  // only the sizes the contraction reads; no tables
-  Q.n = P->n;
-  Q.b = P->b;
-  Q.h = P->h;
-  Q.kind = P->kind;
-  Q.len = P->len;
-  Q.R_N = 1;
-  return Q;
-}
-
-static size_t nuclear_contract_bytes(const cpc_kernel* Q, int n_factors, int N, int precision) {
-  if (precision == CPC_FP32 && tc_supported(Q))
-    return align256(sizeof(double) * tc_rows_groups(Q, N) * n_factors) + tc_rows_workspace(Q, n_factors, N);
-  return align256(sizeof(double) * coulomb_groups(N, 1, kTilesMin) * n_factors);
-}
-
+// F the master kernel windowed onto each nucleus (launch_window): the Coulomb
+// contraction with the nuclear factors in place of the V_H factors, the
+// charges as their coefficients, and the scale -1 in place of h^3 (the
+// Galerkin vectors already carry h^3).  In the tensor-core form the (a, q)
+// columns are folded into one-term factors (10 nuclei x 51 terms: 4 tiles
+// instead of one 10-column tile per term).
 extern "C" size_t nuclear_matrix_workspace(const cpc_kernel* P, int n_items, int n_factors, int n_nuc,
                                            int precision) {
   if (!P || n_items <= 0 || n_factors <= 0 || n_nuc <= 0) return 0;
-  const cpc_kernel Q = column_view(P);
-  const int N = n_nuc * P->R_N;
-  return align256(sizeof(double) * N) + nuclear_contract_bytes(&Q, n_factors, N, precision);
+  return contract_bytes(P, n_factors, n_nuc, precision);
 }
 
 extern "C" int nuclear_matrix(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
@@ -830,14 +838,8 @@ extern "C" int nuclear_matrix(const cpc_kernel* P, int n_items, const int* off, 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int st = launch_window(P, n_nuc, nuc_edges, F, storage_precision(precision) == CPC_FP32, s);
   if (st) return st;
-  const int N = n_nuc * P->R_N;
-  double* Zq = static_cast<double*>(ws);
-  expand_charges_kernel<<<(N + 255) / 256, 256, 0, s>>>(n_nuc, P->R_N, Z, Zq);
-  CPC_LAUNCH_CHECK("expand_charges_kernel");
-  double* rowpart = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + align256(sizeof(double) * N));
-  const cpc_kernel Q = column_view(P);
-  return coulomb_contract(&Q, n_items, off, n_factors, U_items, c_items, N, Zq, F, V, precision, kTilesDefault,
-                          rowpart, s, -1.0);
+  return coulomb_contract(P, n_items, off, n_factors, U_items, c_items, n_nuc, Z, F, V, precision, kTilesDefault,
+                          static_cast<double*>(ws), s, -1.0);
 }
 
 // ---- explicit spectra intermediates ------------------------------------------
