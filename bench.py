@@ -36,6 +36,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # GB300 unit counts for ALU roofs: 152 SMs, 128 FP32 lanes per SM (FMA = 2 flop)
 SMS = 152
 FP32_LANES = 128
+# nominal GB300 float64 CUDA-core rate (GFLOP/s): a context figure, not measured here
+FP64_PEAK_GFLOPS = 1250.0
 
 
 def parse():
@@ -44,13 +46,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "split", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "split", "fp64", "fp64tc"])
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="steps of the float64 and split forms timed for comparison (0: skip)")
     ap.add_argument("--seed", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rf", type=int, default=None,
                     help="override the rank R_f (profiling a smaller case of the same kernels)")
+    ap.add_argument("--cpu-sample", type=float, default=None, help=argparse.SUPPRESS)
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "basis80_n4096", "density200_n4096", "lattice32_n16384",
                              "lattice_energy256_n16384", "nuclear80_n4096", "tei80_n4096"],
@@ -164,10 +167,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(cfg, seed, budget_s=20.0):
+def _oracle_conv_sample(cfg, seed, budget_s):
     """The oracle, as it stands, on a bounded sample of the workload: direct
-    O(n^2) convolutions (Toeplitz products) of a subset of the factor columns
-    with a subset of kernel terms, on all three axes."""
+    O(n^2) convolutions (Toeplitz products) of 16 factor columns with 4 kernel
+    terms, on all three axes, repeated until `budget_s` or 4 repetitions.
+    Returns (convolutions, seconds, repetitions)."""
     from oracle import cp as ocp
     from oracle import kernel_vectors as okv
     from oracle import sinc as osinc
@@ -178,19 +182,48 @@ def cpu_baseline(cfg, seed, budget_s=20.0):
     qs = np.linspace(0, 2 * M, q_sub).round().astype(int)
     P = okv.conv_kernel_vectors(n, b, t[qs], a[qs])
     U = ocp.sample_gaussians(n, b, g["a"][:k_sub], g["X"][:k_sub])
-    done = 0
+    done, reps = 0, 0
     t0 = time.perf_counter()
-    reps = 0
     while True:
         ocp.convolve_factors(U, P)
         done += 3 * k_sub * q_sub
         reps += 1
         if time.perf_counter() - t0 > budget_s or reps >= 4:
             break
-    dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": "convolutions/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{reps} x ({k_sub} Gaussians x {q_sub} kernel terms x 3 axes) direct length-{n} "
-                      f"convolutions of {WORKLOAD} ({done} convolutions, {dt:.1f} s)"}
+    return done, time.perf_counter() - t0, reps
+
+
+def _cpu_sample_child(threads, seed, budget_s):
+    """Run the oracle sample in a fresh interpreter whose BLAS uses `threads`
+    threads (the thread count of a BLAS pool is fixed when it starts)."""
+    env = dict(os.environ)
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[var] = str(threads)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", str(budget_s), "--seed", str(seed)],
+                       env=env, capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        return None
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(cfg, seed, budget_s=10.0):
+    """The oracle timed on the host cores twice: one thread, and one BLAS
+    thread per core (the Toeplitz products are the only parallel part)."""
+    cores = os.cpu_count()
+    runs = {}
+    for label, threads in (("single_thread", 1), ("all_cores", cores)):
+        rec = _cpu_sample_child(threads, seed, budget_s)
+        if rec:
+            runs[label] = {"value": rec["done"] / rec["seconds"], "threads": threads,
+                           "convolutions": rec["done"], "seconds": rec["seconds"]}
+    head = runs.get("all_cores") or runs.get("single_thread")
+    if head is None:
+        return None
+    n = cfg["n"]
+    return {"value": head["value"], "unit": "convolutions/s", "cores": head["threads"], "kind": "oracle",
+            "sample": f"(16 Gaussians x 4 kernel terms x 3 axes) direct length-{n} convolutions of {WORKLOAD}, "
+                      f"repeated up to 4 times or {budget_s:.0f} s, in a fresh process per thread count",
+            **runs}
 
 
 def run_reference(args, ws, rank):
@@ -327,7 +360,7 @@ def run_ours(args, ws, rank, local):
     if args.fp64_steps > 0:
         del bufs
         torch.cuda.empty_cache()
-        for form in ("fp64", "split"):
+        for form in ("fp64", "split", "fp64tc"):
             if form == prec:
                 continue
             bf = buffers(form)
@@ -343,19 +376,34 @@ def run_ours(args, ws, rank, local):
             torch.cuda.synchronize(dev)
             cpc.kernel_timing(False)
             mso = so.elapsed_time(to) / args.fp64_steps
-            kto = {k: cpc.kernel_timing_read(k) for k in ("spectra_kernel", "conv_kernel")}
+            kto = {k: cpc.kernel_timing_read(k)
+                   for k in ("spectra_kernel", "conv_kernel", "slice_rows_kernel", "gemm3_tc_kernel")}
             sp_o = kto["spectra_kernel"][0] / max(1, kto["spectra_kernel"][1])
             cv_o = kto["conv_kernel"][0] / max(1, kto["conv_kernel"][1])
             en_o = float(np.mean([e[0].elapsed_time(e[1]) for e in eo]))
             others[form] = {"ms_per_step": mso, "value": convs_per_step / (mso * 1e-3),
                             "spectra_ms": sp_o, "conv_ms": cv_o, "contraction_ms": en_o - sp_o - cv_o,
                             "E_H": bf[2].item()}
+            if form == "fp64tc" and kto["gemm3_tc_kernel"][1]:
+                # the float64-accurate tensor-core contraction: 15 bf16 slice products
+                # per multiply-add of the method's symmetric Gram
+                tc_ms64 = kto["gemm3_tc_kernel"][0] / kto["gemm3_tc_kernel"][1]
+                gf = 3 * R_N * (R_f * (R_f + 1) // 2) * n * 2
+                bf16_peak = float(load_peaks()[0].get("bf16_tflops", 1900.0))
+                others[form]["gemm3_tc_kernel"] = {
+                    "ms": tc_ms64, "achieved_TFLOPs": gf / (tc_ms64 * 1e-3) / 1e12,
+                    "frac_of_bf16_peak": gf / (tc_ms64 * 1e-3) / 1e12 / bf16_peak,
+                    "slice_products_TFLOPs": 15 * gf / (tc_ms64 * 1e-3) / 1e12}
+                others[form]["slice_rows_ms"] = kto["slice_rows_kernel"][0]
             del bf
             torch.cuda.empty_cache()
         E64 = others.get("fp64", {}).get("E_H", E_fast if prec == "fp64" else None)
         if E64 is not None:
             for form, o in others.items():
                 o["rel_err_E_H_vs_fp64_gpu"] = abs(o["E_H"] / E64 - 1)
+        if "fp64" in others:
+            for form, o in others.items():
+                o["speedup_vs_fp64_gpu"] = others["fp64"]["ms_per_step"] / o["ms_per_step"]
     fp64 = others.get("fp64")
 
     if rank != 0:
@@ -364,53 +412,71 @@ def run_ours(args, ws, rank, local):
     hbm_peak = float(peaks["hbm_gbs"])
     clk = clocks.summary()
     elem = 4 if prec == "fp32" else 8
-    # conv kernel algorithmic bytes per step: write all V_H factors (float32 form: and their
-    # three bf16 slices for the tensor-core contraction), read spectra of U and p
-    out_elem = elem + (6 if prec == "fp32" else 0)
-    conv_bytes = 3 * R_f * R_N * n * out_elem + 3 * R_f * (n + 1) * 2 * elem + R_N * (n + 1) * elem
-    conv_gbs = conv_bytes / (conv_ms * 1e-3) / 1e9
-    # contraction: unique Gram entries (symmetric) x 3 axes x R_N x n cells, 2 flop per multiply-add
-    gram_flops = 3 * R_N * (R_f * (R_f + 1) // 2) * n * 2
     sm_mhz = clk["sm_mhz"] or float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak_tf = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12 if prec != "fp64" else None
+    alu32_peak_tf = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
 
     def per_launch(name, fallback_ms):
         tot, cnt = kt.get(name, (0.0, 0))
         return (tot / cnt, cnt) if cnt else (fallback_ms, 0)
 
+    # convolution, the method's work: per convolution an n-point complex inverse
+    # FFT (5 n log2 n flop) and the spectral product (6 n flop); bytes: the V_H
+    # factors written once plus the operand spectra and kernel pairs read once
     conv_k_ms, _ = per_launch("conv_kernel", conv_ms)
+    conv_flops = convs_per_step * (5 * n * math.log2(n) + 6 * n)
+    # (operands: 16 bytes per bin of each factor column, float4 (X1, X2) or double2;
+    # kernel terms: 8 bytes per bin, float2 pairs or float64)
+    conv_bytes = 3 * R_f * R_N * n * elem + 3 * R_f * n * 16 + R_N * n * 8
+    conv_tf = conv_flops / (conv_k_ms * 1e-3) / 1e12
     conv_gbs = conv_bytes / (conv_k_ms * 1e-3) / 1e9
     kernels = {
-        "conv_kernel": {"ms": conv_k_ms, "bound": "hbm", "achieved": conv_gbs, "peak": hbm_peak, "unit": "GB/s",
-                        "frac": conv_gbs / hbm_peak, "algorithmic_bytes": conv_bytes},
+        "conv_kernel": {
+            "ms": conv_k_ms, "bound": "alu", "achieved": conv_tf, "unit": "TFLOP/s",
+            "peak": alu32_peak_tf if prec == "fp32" else FP64_PEAK_GFLOPS / 1e3,
+            "frac": conv_tf / (alu32_peak_tf if prec == "fp32" else FP64_PEAK_GFLOPS / 1e3),
+            "algorithmic_flops": conv_flops,
+            "peak_note": ("float32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x median SM clock"
+                          if prec == "fp32" else "nominal GB300 float64 rate"),
+            "hbm": {"algorithmic_bytes": conv_bytes, "achieved_GBps": conv_gbs, "peak_GBps": hbm_peak,
+                    "frac": conv_gbs / hbm_peak},
+        },
     }
-    if prec == "fp32":
-        # tensor-core form: each row of U and W split exactly into 3 bf16 slices;
-        # 6 slice products (a + b <= 2) per multiply-add of the float32 contraction
+    # contraction, the method's work: the unique entries of the symmetric convolution
+    # matrices (Sec. 3.2), 3 axes x R_N terms x R_f (R_f + 1) / 2 entries x n cells, 2 flop
+    # per multiply-add; the fused product over axes and weighted sum are not counted
+    gram_flops = 3 * R_N * (R_f * (R_f + 1) // 2) * n * 2
+    if prec in ("fp32", "fp64tc"):
+        n_slice_products = 6 if prec == "fp32" else 15
         tc_ms, _ = per_launch("gemm3_tc_kernel", gram_ms)
-        tc_flops = 6 * gram_flops
-        tc_tf = tc_flops / (tc_ms * 1e-3) / 1e12
         bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
-        kernels["gemm3_tc_kernel"] = {"ms": tc_ms, "bound": "tensor", "achieved": tc_tf, "peak": bf16_peak,
-                                      "unit": "TFLOP/s", "frac": tc_tf / bf16_peak,
-                                      "algorithmic_flops": tc_flops,
-                                      "peak_note": "bf16 dense burst (cuBLAS), " + peak_kind,
-                                      "fp32_equivalent_TFLOP/s": gram_flops / (tc_ms * 1e-3) / 1e12}
-        # slicing of U (the W slices come out of the convolution): read float64, write 3 bf16 slices
+        tc_tf = gram_flops / (tc_ms * 1e-3) / 1e12
+        kernels["gemm3_tc_kernel"] = {
+            "ms": tc_ms, "bound": "tensor", "achieved": tc_tf, "peak": bf16_peak, "unit": "TFLOP/s",
+            "frac": tc_tf / bf16_peak, "algorithmic_flops": gram_flops,
+            "peak_note": "bf16 dense burst (cuBLAS), " + peak_kind,
+            # the implementation's work, kept apart from the method's: every multiply-add
+            # is 6 (float32 form) or 15 (float64 form) bf16 slice products (exact slicing)
+            "slice_products": {"flops": n_slice_products * gram_flops, "TFLOP/s": n_slice_products * tc_tf,
+                               "frac_of_peak": n_slice_products * tc_tf / bf16_peak},
+        }
+        # slicing (read the float64 rows, write the bf16 slices): bookkeeping of the
+        # tensor-core form; U only in the float32 form (the convolution slices W)
         sl_tot, sl_cnt = kt.get("slice_rows_kernel", (0.0, 0))
         sl_ms = sl_tot / max(1, sl_cnt)
-        sl_bytes = 3 * R_f * n * (8 + 6)
+        sl_bytes = (3 * R_f * n * (8 + 6) if prec == "fp32"
+                    else 3 * R_f * (R_N + 1) * n * (8 + 10) / 2)  # per launch: two launches (U, W)
         kernels["slice_rows_kernel"] = {"ms": sl_ms, "bound": "hbm", "achieved": sl_bytes / (sl_ms * 1e-3) / 1e9,
                                         "peak": hbm_peak, "unit": "GB/s",
                                         "frac": sl_bytes / (sl_ms * 1e-3) / 1e9 / hbm_peak,
                                         "algorithmic_bytes": sl_bytes}
     else:
         gram_tf = gram_flops / (gram_ms * 1e-3) / 1e12
+        peak = alu32_peak_tf if prec == "split" else FP64_PEAK_GFLOPS / 1e3
         kernels[{"split": "gemm3_kernel", "fp64": "tri_gram_kernel"}[prec]] = {
             "ms": gram_ms, "bound": "alu", "achieved": gram_tf, "unit": "TFLOP/s",
-            "peak": alu_peak_tf, "frac": (gram_tf / alu_peak_tf) if alu_peak_tf else None,
-            "algorithmic_flops": gram_flops,
-            "peak_note": "FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x median SM clock"}
+            "peak": peak, "frac": gram_tf / peak, "algorithmic_flops": gram_flops,
+            "peak_note": ("float32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x median SM clock"
+                          if prec == "split" else "nominal GB300 float64 rate")}
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     d = kernels[dom]
     if args.rf is None:
@@ -436,7 +502,7 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": ws * convs_per_step * e2e_steps / e2e_s, "unit": "convolutions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
         # sample, spectra, conv (+ W slices), [slice U,] contraction, final sum
-        "gpu_launches": (6 if prec == "fp32" else 5) * args.steps,
+        "gpu_launches": {"fp32": 6, "fp64tc": 8}.get(prec, 5) * args.steps,
         "clocks": clk,
     }
     if ws == 1 and not args.no_cpu_baseline:
@@ -472,7 +538,6 @@ def run_coulomb(args, ws, rank, local):
     (schedule from the autotuner), captured in one CUDA graph and replayed."""
     import torch
     import paper_1504_06289_gb300 as cpc
-    from oracle import coulomb as ocoul
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     name = "basis80_n4096"
@@ -485,11 +550,8 @@ def run_coulomb(args, ws, rank, local):
     centre = np.repeat(basis["fn_centre"], np.diff(first), axis=0)
     t = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
     alpha, cen, d = t(basis["prim_alpha"]), t(centre), t(basis["prim_d"])
-    pa, pb, _ = ocoul.density_pairs(basis)  # index bookkeeping only
-    sc = [basis["w"][mu] * (1.0 if x == y else 2.0)
-          for mu in range(nb) for x in range(first[mu], first[mu + 1]) for y in range(x, first[mu + 1])]
-    items = ocoul.item_list(nb)
-    ia, ib, _, off = ocoul.item_pairs(basis, items)
+    pa, pb, sc = workloads.basis_density_pairs(basis)  # index bookkeeping only
+    items, ia, ib, off = workloads.basis_item_pairs(basis)
     pa_t, pb_t, sc_t = t(pa, torch.int32), t(pb, torch.int32), t(sc)
     ia_t, ib_t, off_t = t(ia, torch.int32), t(ib, torch.int32), t(off, torch.int32)
     n_factors, R_rho = len(ia), len(pa)
@@ -535,6 +597,22 @@ def run_coulomb(args, ws, rank, local):
             basis["w"], J.cpu().numpy()[[items.index((m, m)) for m in range(nb)]]))}
         del U_it, W_rho, wsb
         torch.cuda.empty_cache()
+    if args.precision != "fp64" and args.fp64_steps > 0:
+        # the plain float64 form on the same GPU and inputs (CUDA-core contraction,
+        # default schedule, not tuned: one step takes tens of seconds), the
+        # baseline of the speedup and of the energy error
+        F = cpc.cp_sample_gaussians(n, b, alpha, cen)
+        U_rho, c_rho = cpc.cp_hadamard_pairs(F, pa_t, pb_t, d, sc_t)
+        U_it, c_it = cpc.cp_hadamard_pairs(F, ia_t, ib_t, d)
+        J64 = None
+        def fp64_step():
+            nonlocal J64
+            J64, _ = cpc.coulomb_matrix(P, off_t, U_it, c_it, U_rho, c_rho, "fp64", tiles_per_cta=0)
+        ms64 = _timed(stream, fp64_step, 1, 0)
+        res["fp64"] = {"ms_per_step": ms64, "steps": 1, "J_diag_sum_w": float(np.dot(
+            basis["w"], J64.cpu().numpy()[[items.index((m, m)) for m in range(nb)]]))}
+        del U_it, J64
+        torch.cuda.empty_cache()
     if rank != 0:
         return
     head = "fp32" if "fp32" in res else "fp64"
@@ -543,15 +621,26 @@ def run_coulomb(args, ws, rank, local):
     peaks, peak_kind = load_peaks()
     if "split" in res:
         res["split"]["rel_diff_E_vs_fp32"] = abs(res["split"]["J_diag_sum_w"] / res["fp32"]["J_diag_sum_w"] - 1)
+    extra = {}
+    if "fp64" in res and head != "fp64":
+        # E_H = sum_mu w_mu J_mu,mu of each reduced-precision form against the float64 form
+        for form in ("fp32", "split"):
+            if form in res:
+                res[form]["rel_err_E_H_vs_fp64_gpu"] = abs(res[form]["J_diag_sum_w"] / res["fp64"]["J_diag_sum_w"] - 1)
+        extra = {"speedup_vs_fp64_gpu": res["fp64"]["ms_per_step"] / res[head]["ms_per_step"],
+                 "rel_err_E_H_vs_fp64_gpu": res[head]["rel_err_E_H_vs_fp64_gpu"]}
     tc_ms = res[head]["kernel_ms"].get("gemm3_tc_kernel", 0.0)
     if head == "fp32" and tc_ms > 0:
-        # tensor-core form: 6 bf16 slice products per float32 multiply-add
-        achieved = 6 * flops / (tc_ms * 1e-3) / 1e12
+        # the method's work (2 flop per multiply-add of the 3 axes' scalar products
+        # of item factors with the V_H factors of rho) against the bf16 peak; the 6
+        # bf16 slice products per multiply-add are the implementation's, reported apart
+        achieved = flops / (tc_ms * 1e-3) / 1e12
         peak = float(peaks.get("bf16_tflops", 1900.0))
         roof = {"kernel": "gemm3_tc_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                "kernel_ms": tc_ms, "fp32_equivalent_TFLOP/s": flops / (tc_ms * 1e-3) / 1e12,
-                "note": "bf16 slice-product flops 6 x 2*3*factors*R_rho*R_N*n per launch / event time"}
+                "kernel_ms": tc_ms,
+                "slice_products": {"flops": 6 * flops, "TFLOP/s": 6 * achieved, "frac_of_peak": 6 * achieved / peak},
+                "note": "method flops 2*3*factors*R_rho*R_N*n per launch / event time"}
         launches = 9  # sample, 2 Hadamard, spectra, conv, slice items, slice W, contraction, item sums
     else:
         clk = 2070.0
@@ -565,7 +654,7 @@ def run_coulomb(args, ws, rank, local):
           "f32" if head == "fp32" else "f64",
           {"workload": name, "n": n, "items": len(items), "item_factors": n_factors, "R_rho": R_rho, "R_N": P.R_N,
            "graph": "sample + 2 Hadamard + coulomb_matrix captured in one CUDA graph"},
-          forms=res, roofline=roof, gpu_launches=launches * args.steps if launches else None)
+          forms=res, roofline=roof, gpu_launches=launches * args.steps if launches else None, **extra)
 
 
 def run_adjoint(args, ws, rank, local):
@@ -628,9 +717,6 @@ def run_lattice(args, ws, rank, local):
     the potential on the 512^3 sub-grid (lattice32_n16384)."""
     import torch
     import paper_1504_06289_gb300 as cpc
-    from oracle import kernel_vectors as okv
-    from oracle import lattice as olat
-    from oracle import sinc as osinc
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     name = "lattice32_n16384"
@@ -663,6 +749,9 @@ def run_lattice(args, ws, rank, local):
     # float64 ALU peak from the measured float64 contraction rate is not a unit count; report HBM and ALU both
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
+        from oracle import kernel_vectors as okv
+        from oracle import lattice as olat
+        from oracle import sinc as osinc
         t, w = osinc.master_nodes(n, b, M)
         Pm = okv.master_kernel_vectors(n, b, t, w)
         t0 = time.perf_counter()
@@ -694,10 +783,6 @@ def run_nuclear(args, ws, rank, local):
     item factors; the item factors are built once (the Coulomb workload's)."""
     import torch
     import paper_1504_06289_gb300 as cpc
-    from oracle import coulomb as ocoul
-    from oracle import kernel_vectors as okv
-    from oracle import nuclear as onuc
-    from oracle import sinc as osinc
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     name = "nuclear80_n4096"
@@ -710,8 +795,7 @@ def run_nuclear(args, ws, rank, local):
     first = basis["fn_first"]
     centre = np.repeat(basis["fn_centre"], np.diff(first), axis=0)
     t = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
-    items = ocoul.item_list(nb)
-    ia, ib, _, off = ocoul.item_pairs(basis, items)
+    items, ia, ib, off = workloads.basis_item_pairs(basis)
     G = cpc.cp_sample_gaussians(n, b, t(basis["prim_alpha"]), t(centre))
     U_it, c_it = cpc.cp_hadamard_pairs(G, t(ia, torch.int32), t(ib, torch.int32), t(basis["prim_d"]))
     off_t, Z_t = t(off, torch.int32), t(Z)
@@ -742,10 +826,13 @@ def run_nuclear(args, ws, rank, local):
     flops = 2.0 * 3 * n_factors * n_nuc * P.R_N * n
     peaks, peak_kind = load_peaks()
     tc_ms = res["fp32"]["kernel_ms"]["gemm3_tc_kernel"]
-    achieved = 6 * flops / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
+    achieved = flops / (tc_ms * 1e-3) / 1e12 if tc_ms > 0 else None
     peak = float(peaks.get("bf16_tflops", 1900.0))
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
+        from oracle import kernel_vectors as okv
+        from oracle import nuclear as onuc
+        from oracle import sinc as osinc
         tq, wq = osinc.master_nodes(n, b, M)
         Pm = okv.master_kernel_vectors(n, b, tq, wq)
         sample = items[:40]
@@ -760,7 +847,9 @@ def run_nuclear(args, ws, rank, local):
           roofline={"kernel": "gemm3_tc_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
                     "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
                     "peak_source": peak_kind, "kernel_ms": tc_ms,
-                    "note": "bf16 slice-product flops 6 x 2*3*factors*nuclei*R_N*n per launch / event time"},
+                    "slice_products": ({"flops": 6 * flops, "TFLOP/s": 6 * achieved, "frac_of_peak": 6 * achieved / peak}
+                                       if achieved else None),
+                    "note": "method flops 2*3*factors*nuclei*R_N*n per launch / event time"},
           gpu_launches=6 * args.steps, cpu_baseline=cpu)
 
 
@@ -770,11 +859,6 @@ def run_tei(args, ws, rank, local):
     J(D) and K(D) for one density matrix per step (Secs. 3.1, 3.2); float64."""
     import torch
     import paper_1504_06289_gb300 as cpc
-    from oracle import coulomb as ocoul
-    from oracle import cp as ocp
-    from oracle import kernel_vectors as okv
-    from oracle import sinc as osinc
-    from oracle import tei as otei
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     name = "tei80_n4096"
@@ -785,7 +869,7 @@ def run_tei(args, ws, rank, local):
     P = cpc.make_newton_kernel(n, b, M, device=dev)
     t = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
     U = cpc.cp_sample_gaussians(n, b, t(g["a"]), t(g["X"]))
-    pa0, pb0 = otei.pair_list(nb)
+    pa0, pb0 = workloads.upper_pairs(nb)
     pa, pb = t(pa0, torch.int32), t(pb0, torch.int32)
     rng = np.random.default_rng(5)
     X = rng.standard_normal((nb, nb))
@@ -820,11 +904,11 @@ def run_tei(args, ws, rank, local):
     RB = rk[3]
     fl = 2.0 * (R_N * npair * sum(r * r for r in rk[:3]) + RB * R_N * sum(r * r + npair * r for r in rk[:3])
                 + npair * RB * RB / 2.0)
-    fp64_peak = 1250.0
+    fp64_peak = FP64_PEAK_GFLOPS
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        tq, wq = osinc.conv_nodes(n, b, M)
-        P0 = okv.conv_kernel_vectors(n, b, tq, wq)
+        from oracle import cp as ocp
+        from oracle import tei as otei
         U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
         t0 = time.perf_counter()
         otei.density_fit(otei.side_matrix(U0[0], pa0, pb0), cfg["tol_df"], 128)
@@ -853,9 +937,6 @@ def run_lattice_energy(args, ws, rank, local):
     correction (Sec. 5.3, Eq. EnergyLattice); float64, one E_L per step."""
     import torch
     import paper_1504_06289_gb300 as cpc
-    from oracle import kernel_vectors as okv
-    from oracle import lattice as olat
-    from oracle import sinc as osinc
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     name = "lattice_energy256_n16384"
@@ -884,9 +965,12 @@ def run_lattice_energy(args, ws, rank, local):
     # per axis, q and distinct difference d: p~[d-1] + p~[d] and one multiply-add
     n_diff = sum(len(np.unique(np.subtract.outer(e.astype(np.int64), e))) for e in edges)
     flops = 3 * P.R_N * n_diff
-    fp64_peak = 1250.0  # GFLOP/s: the nominal float64 rate of GB300
+    fp64_peak = FP64_PEAK_GFLOPS
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
+        from oracle import kernel_vectors as okv
+        from oracle import lattice as olat
+        from oracle import sinc as osinc
         t, w = osinc.master_nodes(n, b, M)
         Pm = okv.master_kernel_vectors(n, b, t, w)
         t0 = time.perf_counter()
@@ -894,10 +978,11 @@ def run_lattice_energy(args, ws, rank, local):
         dt = time.perf_counter() - t0
         cpu = {"value": 1.0 / dt, "unit": "evaluations/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": "one E_L of the same lattice (traced tensor sum, master vectors given)",
-               "rel_diff": abs(E.item() / E0 - 1)}
+               "rel_diff": abs(E.item() / E0 - 1),
+               "E_L_direct": olat.interaction_energy_direct(edges, h)}
     _line(args, ws, "lattice interaction energy evaluations/s", ws / (ms * 1e-3), "evaluations/s", ms, "f64",
           {"workload": name, "n": n, "L": L, "cells_per_spacing": cells, "R_N": P.R_N},
-          E_L=E.item(), E_L_direct=olat.interaction_energy_direct(edges, h),
+          E_L=E.item(),
           kernel_ms={"lattice_pairs_kernel": p_ms, "lattice_energy_kernel": k_ms},
           e2e={"value": 1e3 / e2e_ms, "unit": "evaluations/s", "h2d_bytes_per_step": 4 * 3 * L,
                "d2h_bytes_per_step": 8},
@@ -912,6 +997,10 @@ def run_lattice_energy(args, ws, rank, local):
 
 def main():
     args = parse()
+    if args.cpu_sample is not None:  # child of cpu_baseline: the oracle sample alone, no GPU
+        done, dt, reps = _oracle_conv_sample(workloads.CONFIGS[WORKLOAD], args.seed, args.cpu_sample)
+        print(json.dumps({"done": done, "seconds": dt, "reps": reps}), flush=True)
+        return
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)

@@ -33,9 +33,19 @@
  *           keeps the convolutions in float64 (V_H factors stored as double,
  *           exactly as CPC_FP64) and runs the contractions with float32
  *           products as in CPC_FP32, so E_H loses only the float32 rounding
- *           of its operands.  Kernel nodes, weights, cell integrals, spectra
- *           of the factors and final cross-rank reductions are float64 in
- *           every form.
+ *           of its operands.  CPC_FP64_TC (cp_hartree_energy and
+ *           cp_hartree_energy_from_factors only, n a multiple of 128) keeps
+ *           the float64 convolutions of CPC_FP64 and runs the E_H contraction
+ *           on the tensor cores: each float64 operand row is split exactly
+ *           into five bf16 slices (40 bits of its row maximum), the slice
+ *           pairs down to 2^-32 of the row scales are multiplied and summed
+ *           exactly or below 2^-38 of the entry scale, and the convolution
+ *           matrices and E_H are formed in float64 (the method's float64
+ *           accuracy at tensor-core speed; every other entry point and the
+ *           Coulomb, nuclear and lattice calls reject it with
+ *           CPC_ERR_UNSUPPORTED and take CPC_FP64).  Kernel nodes, weights,
+ *           cell integrals, spectra of the factors and final cross-rank
+ *           reductions are float64 in every form.
  *   Errors: every entry point returns CPC_OK (0) or a negative status; no
  *           exception or abort crosses the ABI.  Arguments are validated on
  *           the host before any launch; a failed CUDA call returns
@@ -60,6 +70,7 @@ extern "C" {
 #define CPC_FP64 0
 #define CPC_FP32 1
 #define CPC_SPLIT 2
+#define CPC_FP64_TC 3
 
 #define CPC_KERNEL_CONV 0   /* cell-centred offsets m = -(n-1)..n-1 (Sec. 3.1) */
 #define CPC_KERNEL_MASTER 1 /* 2n cells [jh,(j+1)h], j = -n..n-1 (Sec. 5.1, Eq. refTensor) */
@@ -193,9 +204,14 @@ int cp_hartree_energy_from_spectra(const cpc_kernel* P, int R_f, const void* spe
  * cp_hartree_energy_workspace(P, R_f, precision) bytes of it.
  * Sizes whose requirement exceeds 32 MiB are rejected with
  * CPC_ERR_UNSUPPORTED and a message naming both sizes; nothing is launched.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current), so make that first call before any
- * stream capture.  Every call on a device shares the array and sees the last
+ * A device address of the array is valid only in the CUDA context it was
+ * looked up in, so every call that is not under stream capture looks it up in
+ * the current context (keyed by context: a caller's own non-primary context,
+ * or a primary context recreated after cudaDeviceReset, gets its own); under
+ * capture the address from an earlier call in the same context is used, so
+ * make the first call in a context before any stream capture (otherwise
+ * CPC_ERR_INVALID).  Invalid arguments are reported as CPC_ERR_INVALID before
+ * the size limit is applied.  Every call on a device shares the array and sees the last
  * call's bytes there; the kernels overwrite all scratch they read, so no
  * clearing is needed, but calls whose work overlaps on the GPU (unordered
  * streams) race on it.  No cudaMalloc, cudaFree or allocating library call
@@ -236,13 +252,17 @@ int cp_gaussian_param_grad(int n, double b, int R, const double* a, const double
  * uneven rank share tiles and no item leaves a tile idle.  CPC_FP64, CPC_SPLIT
  * (and CPC_FP32 when n is not a multiple of 128): one persistent launch over
  * (row tile, column group) work units, a column group being tiles_per_cta
- * consecutive 64-column tiles of the R_rho*R_N V_H columns (0 = default 8;
- * else a power of two in [4, 128]).  CPC_FP32 with n a multiple of 128: the
- * tensor-core contraction of cp_hartree_energy (exact bf16 slices of the item
- * factors and of the float32 W_rho) with the R_rho R_N columns (m, q) taken
- * as one-term factors, on tiles of 256 item factors x 128 columns,
- * tiles_per_cta unused; if one of its device-side
- * waits gives up, J is written as NaN.  Stream-ordered and allocation-free, so
+ * consecutive 64-column tiles of the R_rho*R_N V_H columns.  CPC_FP32 with n
+ * a multiple of 128: the tensor-core contraction of cp_hartree_energy (exact
+ * bf16 slices of the item factors and of the float32 W_rho) with the
+ * R_rho R_N columns (m, q) taken as one-term factors, on tiles of 256 item
+ * factors x 128 columns; tiles_per_cta is then the number of 256-row item
+ * blocks whose CTA pairs sweep the column tiles together (a raster group:
+ * the pairs in flight share row blocks and column tiles in L2; capped at
+ * the number of blocks).  tiles_per_cta: 0 = default 8, else a power of two
+ * in [1, 128].  The result does not depend on it (fixed-order reductions).
+ * If one of the tensor-core form's device-side waits gives up, J is written
+ * as NaN.  Stream-ordered and allocation-free, so
  * a sequence of these calls can be captured in a CUDA graph.  Workspace:
  * coulomb_matrix_workspace bytes (sized for the smallest tiles_per_cta; for
  * the tensor-core form it holds the bf16 slices, 18 n (n_factors + R_rho R_N)
@@ -281,16 +301,19 @@ int nuclear_matrix(const cpc_kernel* master, int n_items, const int* off, int n_
                    int precision, void* ws, size_t ws_bytes, void* stream);
 
 /* Schedule tuner for coulomb_matrix: computes W_rho, then times the
- * contraction for every tiles_per_cta in {4, 8, ..., 128} on the caller's
- * data (CUDA events on `stream`; this call synchronises the stream), writes
- * the fastest to *best_tiles_per_cta (and its time in ms to *best_ms if not
- * NULL) and leaves J computed with it.  The tensor-core form has no
- * schedule parameter: it is timed once and the default is reported.  Same
- * arguments as coulomb_matrix. */
+ * contraction for every candidate schedule on the caller's data (one untimed
+ * and one timed launch each, CUDA events on `stream`; this call synchronises
+ * the stream), writes the fastest to *best_tiles_per_cta (and its time in ms
+ * to *best_ms if not NULL) and leaves J computed with it.  Candidates:
+ * tiles_per_cta in {4, 8, ..., 128} for the CUDA-core forms, raster groups
+ * {1, 2, 4, ..., 32} for the tensor-core form.  times_ms (NULL, or host
+ * float[8]): times_ms[k] = the timed launch of candidate 2^k, NaN where 2^k
+ * is not a candidate.  Same arguments as coulomb_matrix otherwise. */
 int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* off, int n_factors,
                         const double* U_items, const double* c_items, int R_rho, const double* U_rho,
                         const double* c_rho, void* W_rho, double* J, int precision, void* ws,
-                        size_t ws_bytes, void* stream, int* best_tiles_per_cta, float* best_ms);
+                        size_t ws_bytes, void* stream, int* best_tiles_per_cta, float* best_ms,
+                        float* times_ms);
 
 /* ---- two-electron integrals: 1D density fitting + truncated Cholesky (Sec. 3.2) ----
  * For N_b s-type primitive Gaussians with sampled factors U_prims [3][n_b][n]

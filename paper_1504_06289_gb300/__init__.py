@@ -341,9 +341,11 @@ def coulomb_matrix(P: NewtonKernel, off: torch.Tensor, U_items: torch.Tensor, c_
             tiles_per_cta = int(cached["tiles_per_cta"])
         else:
             best, ms = C.c_int(), C.c_float()
-            check(lib.coulomb_matrix_tune(*args, _ptr(ws), ws.numel(), _stream(stream), C.byref(best), C.byref(ms)),
-                  "coulomb_matrix_tune")
-            _tune_store(key, {"tiles_per_cta": best.value, "ms": ms.value})
+            times = (C.c_float * 8)()
+            check(lib.coulomb_matrix_tune(*args, _ptr(ws), ws.numel(), _stream(stream), C.byref(best), C.byref(ms),
+                                          times), "coulomb_matrix_tune")
+            cands = {str(1 << k): float(times[k]) for k in range(8) if times[k] == times[k]}
+            _tune_store(key, {"tiles_per_cta": best.value, "ms": ms.value, "candidates_ms": cands})
             return J, W_rho
     check(lib.coulomb_matrix(*args, int(tiles_per_cta), _ptr(ws), ws.numel(), _stream(stream)), "coulomb_matrix")
     return J, W_rho

@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcpc.so")
 
 CPC_OK = 0
-PRECISION = {"fp64": 0, "fp32": 1, "split": 2}
+PRECISION = {"fp64": 0, "fp32": 1, "split": 2, "fp64tc": 3}
 KIND = {"conv": 0, "master": 1}
 
 vp, sz, i32, f64 = C.c_void_p, C.c_size_t, C.c_int, C.c_double
@@ -38,7 +38,7 @@ PROTOTYPES = {
     "coulomb_matrix_workspace": (sz, [vp, i32, i32, i32, i32]),
     "coulomb_matrix": (i32, [vp, i32, vp, i32, vp, vp, i32, vp, vp, vp, vp, i32, i32, vp, sz, vp]),
     "coulomb_matrix_tune": (i32, [vp, i32, vp, i32, vp, vp, i32, vp, vp, vp, vp, i32, vp, sz, vp,
-                                  C.POINTER(C.c_int), C.POINTER(C.c_float)]),
+                                  C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_float)]),
     "lattice_potential_sum": (i32, [vp, vp, vp, vp, i32, vp, vp, i32, vp]),
     "lattice_interaction_energy": (i32, [vp, vp, vp, f64, vp, vp]),
     "nuclear_matrix_workspace": (sz, [vp, i32, i32, i32, i32]),

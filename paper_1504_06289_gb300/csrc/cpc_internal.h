@@ -124,19 +124,29 @@ size_t tc_partials(int R_f, int R_N);
 bool tc_supported(const cpc_kernel* P);
 size_t tc_workspace(const cpc_kernel* P, int R_f);
 int* tc_status_ptr(const cpc_kernel* P, int R_f, void* ws);
+// CPC_FP64_TC: float64 operands in five bf16 slices, convolution matrices in float64
+size_t tc64_partials(int R_f, int R_N);
+size_t tc64_workspace(const cpc_kernel* P, int R_f);
+int* tc64_status_ptr(const cpc_kernel* P, int R_f, void* ws);
+int launch_eh_tc64(const cpc_kernel* P, int R_f, const double* U, const double* W, const double* c, double* G,
+                   double* partial, void* ws, cudaStream_t s);
 // tensor-core Coulomb-matrix rows (M item factors against Ns rho factors)
 size_t tc_rows_workspace(const cpc_kernel* P, int M, int Ns);
 size_t tc_rows_groups(const cpc_kernel* P, int Ns);
 int* tc_rows_status_ptr(const cpc_kernel* P, int M, int Ns, void* ws);
+// raster: 256-row blocks of item factors whose CTA pairs sweep the column tiles together
 int launch_rows_tc(const cpc_kernel* P, int M, const double* U_items, int Ns, const float* W_rho,
-                   const double* c_rho, double* rowpart, void* ws, cudaStream_t s);
+                   const double* c_rho, double* rowpart, void* ws, cudaStream_t s, int raster);
 // where a convolution writes the W slices for launch_eh_tc(..., w_sliced = true)
 void tc_w_slices(const cpc_kernel* P, int R_f, void* ws, __nv_bfloat16** slices, long long* slice_stride,
                  int** expo);
 int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
                  double* partial, void* ws, cudaStream_t s, bool w_sliced = false);
-// the V_H factors and spectra of CPC_SPLIT are float64, like CPC_FP64
+// the V_H factors and spectra of CPC_SPLIT and CPC_FP64_TC are float64, like CPC_FP64
 inline int storage_precision(int precision) { return precision == CPC_FP32 ? CPC_FP32 : CPC_FP64; }
+inline bool known_precision(int precision) {
+  return precision == CPC_FP64 || precision == CPC_FP32 || precision == CPC_SPLIT || precision == CPC_FP64_TC;
+}
 size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision);
 
 }  // namespace cpc

@@ -470,7 +470,7 @@ static int tiles(int x) { return (x + TM - 1) / TM; }
 size_t eh_partials(const cpc_kernel* P, int R_f) {
   const int T = tiles(R_f);
   return std::max({size_t(T) * (T + 1) / 2 * P->R_N, eh32_partials(R_f, P->R_N), eh32a_partials(R_f, P->R_N),
-                   tc_partials(R_f, P->R_N)});
+                   tc_partials(R_f, P->R_N), tc64_partials(R_f, P->R_N)});
 }
 
 // contraction workspace: partial sums; float32 form: a float32 copy of U (CUDA-core
@@ -479,6 +479,7 @@ size_t eh_partials(const cpc_kernel* P, int R_f) {
 size_t contraction_workspace(const cpc_kernel* P, int R_f, int precision) {
   size_t b = align256(sizeof(double) * eh_partials(P, R_f));
   if (precision == CPC_FP32) b += tc_supported(P) ? tc_workspace(P, R_f) : eh32a_u32_bytes(P, R_f);
+  if (precision == CPC_FP64_TC) b += tc64_workspace(P, R_f);
   return b;
 }
 
@@ -510,6 +511,15 @@ int launch_eh(const cpc_kernel* P, int R_f, const double* U, const double* c, co
     int st = launch_eh32(P, R_f, U, nullptr, nullptr, nullptr, c, G, partial, s, static_cast<const double*>(W));
     if (st) return st;
     count = (long long)eh32_partials(R_f, P->R_N);
+  } else if (precision == CPC_FP64_TC) {
+    if (!tc_supported(P)) return fail(CPC_ERR_UNSUPPORTED, "CPC_FP64_TC needs n a multiple of 128");
+    void* tws = static_cast<unsigned char*>(cws) + align256(sizeof(double) * eh_partials(P, R_f));
+    int st = launch_eh_tc64(P, R_f, U, static_cast<const double*>(W), c, G, partial, tws, s);
+    if (st) return st;
+    finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, (long long)tc64_partials(R_f, P->R_N), P->h * P->h * P->h, E_H,
+                                           tc64_status_ptr(P, R_f, tws));
+    CPC_LAUNCH_CHECK("finalize_sum_kernel");
+    return CPC_OK;
   } else if (tc_supported(P)) {
     void* tws = static_cast<unsigned char*>(cws) + align256(sizeof(double) * eh_partials(P, R_f));
     int st = launch_eh_tc(P, R_f, U, static_cast<const float*>(W), c, G, partial, tws, s);
@@ -592,7 +602,7 @@ extern "C" int cp_hartree_energy_from_factors(const cpc_kernel* P, int R_f, cons
   clear_error();
   if (!P || P->kind != CPC_KERNEL_CONV) return fail(CPC_ERR_INVALID, "cp_hartree_energy_from_factors: needs a CONV kernel");
   if (R_f <= 0 || !U || !c || !W || !E_H) return fail(CPC_ERR_INVALID, "cp_hartree_energy_from_factors: bad arguments");
-  if (precision != CPC_FP64 && precision != CPC_FP32 && precision != CPC_SPLIT)
+  if (!known_precision(precision))
     return fail(CPC_ERR_UNSUPPORTED, "cp_hartree_energy_from_factors: precision form not implemented");
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) ||
       ws_bytes < cp_hartree_energy_from_factors_workspace(P, R_f, precision))
@@ -606,7 +616,7 @@ extern "C" int cp_hartree_energy_adjoint(const cpc_kernel* P, int R_f, const dou
   clear_error();
   if (!P || P->kind != CPC_KERNEL_CONV) return fail(CPC_ERR_INVALID, "cp_hartree_energy_adjoint: needs a CONV kernel");
   if (R_f <= 0 || !c || !W || !G || !dU) return fail(CPC_ERR_INVALID, "cp_hartree_energy_adjoint: bad arguments");
-  if (precision != CPC_FP64 && precision != CPC_FP32 && precision != CPC_SPLIT)
+  if (!known_precision(precision))
     return fail(CPC_ERR_UNSUPPORTED, "cp_hartree_energy_adjoint: precision form not implemented");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n = P->n;
@@ -637,7 +647,11 @@ extern "C" int cp_hartree_energy_adjoint(const cpc_kernel* P, int R_f, const dou
 // traffic (one partial per row per group) against load balance; the tuner
 // below times the candidates on the caller's data.
 namespace cpc {
+// schedule parameter: CUDA-core forms, 64-column tiles per work unit (tuned over
+// [4, 128]); tensor-core form, 256-row item blocks rastered together (tuned over
+// [1, 32]); 8 when the caller passes 0
 static const int kTilesDefault = 8, kTilesMin = 4, kTilesMax = 128;
+static const int kRasterMin = 1, kRasterMax = 32;
 static int coulomb_groups(int R_rho, int R_N, int tiles_per_cta) {
   const int n_ct = tiles(R_rho * R_N);
   return (n_ct + tiles_per_cta - 1) / tiles_per_cta;
@@ -706,7 +720,7 @@ static int coulomb_contract(const cpc_kernel* P, int n_items, const int* off, in
     CPC_LAUNCH_CHECK("expand_coef_kernel");
     const int tgroups = (int)tc_rows_groups(&Q, Nc);
     void* tws = reinterpret_cast<unsigned char*>(rp) + align256(sizeof(double) * (size_t)tgroups * n_factors);
-    st = launch_rows_tc(&Q, n_factors, U_items, Nc, static_cast<const float*>(W_rho), cq, rp, tws, s);
+    st = launch_rows_tc(&Q, n_factors, U_items, Nc, static_cast<const float*>(W_rho), cq, rp, tws, s, tiles_per_cta);
     if (st) return st;
     item_reduce_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(n_items, off, c_items, rp, tgroups, n_factors, scale, J,
                                                            tc_rows_status_ptr(&Q, n_factors, Nc, tws));
@@ -726,13 +740,15 @@ static int coulomb_contract(const cpc_kernel* P, int n_items, const int* off, in
 static int check_coulomb(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
                          const double* c_items, int R_rho, const double* U_rho, const double* c_rho, void* W_rho,
                          double* J, int precision, int tiles_per_cta, void* ws, size_t ws_bytes, const char* who) {
+  if (precision == CPC_FP64_TC)
+    return fail(CPC_ERR_UNSUPPORTED, std::string(who) + ": CPC_FP64_TC is an E_H form; use CPC_FP64");
   int st = check_conv_args(P, R_rho, U_rho, W_rho, precision, ws, ws_bytes, who);
   if (st) return st;
   if (n_items <= 0 || !off || !U_items || !c_items || !c_rho || !J)
     return fail(CPC_ERR_INVALID, std::string(who) + ": bad item arguments");
   if (n_factors <= 0) return fail(CPC_ERR_INVALID, std::string(who) + ": no item factors");
-  if (tiles_per_cta != 0 && (tiles_per_cta < kTilesMin || tiles_per_cta > kTilesMax || (tiles_per_cta & (tiles_per_cta - 1))))
-    return fail(CPC_ERR_INVALID, std::string(who) + ": tiles_per_cta must be 0 or a power of two in [4, 128]");
+  if (tiles_per_cta != 0 && (tiles_per_cta < 1 || tiles_per_cta > kTilesMax || (tiles_per_cta & (tiles_per_cta - 1))))
+    return fail(CPC_ERR_INVALID, std::string(who) + ": tiles_per_cta must be 0 or a power of two in [1, 128]");
   if (ws_bytes < coulomb_matrix_workspace(P, n_items, n_factors, R_rho, precision))
     return fail(CPC_ERR_WORKSPACE, std::string(who) + ": workspace too small");
   return CPC_OK;
@@ -764,7 +780,8 @@ extern "C" int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, 
 extern "C" int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* off, int n_factors,
                                    const double* U_items, const double* c_items, int R_rho, const double* U_rho,
                                    const double* c_rho, void* W_rho, double* J, int precision, void* ws,
-                                   size_t ws_bytes, void* stream, int* best_tiles_per_cta, float* best_ms) {
+                                   size_t ws_bytes, void* stream, int* best_tiles_per_cta, float* best_ms,
+                                   float* times_ms) {
   clear_error();
   int st = check_coulomb(P, n_items, off, n_factors, U_items, c_items, R_rho, U_rho, c_rho, W_rho, J, precision, 0,
                          ws, ws_bytes, "coulomb_matrix_tune");
@@ -774,33 +791,41 @@ extern "C" int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* 
   st = run_convolve(P, R_rho, U_rho, W_rho, precision, ws, s);
   if (st) return st;
   double* rowpart = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_rho, precision));
-  cudaEvent_t e0, e1;
-  CPC_CUDA(cudaEventCreate(&e0));
-  CPC_CUDA(cudaEventCreate(&e1));
+  // candidates: the tensor-core form (CPC_FP32, n a multiple of 128) rasters
+  // its CTA pairs over groups of 1..32 item-row blocks; the CUDA-core forms
+  // take 4..128 column tiles per work unit
+  const bool tc = (precision == CPC_FP32 && tc_supported(P));
+  const int lo = tc ? kRasterMin : kTilesMin, hi = tc ? kRasterMax : kTilesMax;
+  // the events are released on every return path
+  struct Events {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~Events() {
+      for (cudaEvent_t x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } ev;
+  CPC_CUDA(cudaEventCreate(&ev.e[0]));
+  CPC_CUDA(cudaEventCreate(&ev.e[1]));
+  if (times_ms)
+    for (int k = 0; k < 8; ++k) times_ms[k] = __builtin_nanf("");
   float best = -1.0f;
   int best_t = kTilesDefault;
-  // the tensor-core form (CPC_FP32, n a multiple of 128) has a fixed tile schedule:
-  // time the default once
-  const bool fixed = (precision == CPC_FP32 && tc_supported(P));
-  for (int t = fixed ? kTilesDefault : kTilesMin; t <= (fixed ? kTilesDefault : kTilesMax); t *= 2) {
+  for (int t = lo; t <= hi; t *= 2) {
     // one untimed launch per candidate, then one timed
     st = coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, t, rowpart, s, P->h * P->h * P->h);
-    if (st) break;
-    CPC_CUDA(cudaEventRecord(e0, s));
+    if (st) return st;
+    CPC_CUDA(cudaEventRecord(ev.e[0], s));
     st = coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, t, rowpart, s, P->h * P->h * P->h);
-    if (st) break;
-    CPC_CUDA(cudaEventRecord(e1, s));
-    CPC_CUDA(cudaEventSynchronize(e1));
+    if (st) return st;
+    CPC_CUDA(cudaEventRecord(ev.e[1], s));
+    CPC_CUDA(cudaEventSynchronize(ev.e[1]));
     float ms = 0.0f;
-    CPC_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    CPC_CUDA(cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]));
+    if (times_ms) times_ms[ilog2(t)] = ms;
     if (best < 0.0f || ms < best) { best = ms; best_t = t; }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (st) return st;
   *best_tiles_per_cta = best_t;
   if (best_ms) *best_ms = best;
-  if (fixed) return CPC_OK;  // J already holds the timed run's result
   // leave J computed with the chosen schedule
   return coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, best_t,
                           rowpart, s, P->h * P->h * P->h);
@@ -855,7 +880,7 @@ extern "C" int cp_factor_spectra(const cpc_kernel* P, int R_f, const double* U, 
   clear_error();
   if (!P || P->kind != CPC_KERNEL_CONV || R_f <= 0 || !U || !spec)
     return fail(CPC_ERR_INVALID, "cp_factor_spectra: bad arguments");
-  if (precision != CPC_FP64 && precision != CPC_FP32 && precision != CPC_SPLIT)
+  if (!known_precision(precision))
     return fail(CPC_ERR_UNSUPPORTED, "cp_factor_spectra: precision form not implemented");
   precision = storage_precision(precision);
   if ((reinterpret_cast<uintptr_t>(U) & 15) || (reinterpret_cast<uintptr_t>(spec) & 15))
@@ -870,7 +895,7 @@ extern "C" int cp_convolve_from_spectra(const cpc_kernel* P, int R_f, const void
   clear_error();
   if (!P || P->kind != CPC_KERNEL_CONV || R_f <= 0 || !spec || !W)
     return fail(CPC_ERR_INVALID, "cp_convolve_from_spectra: bad arguments");
-  if (precision != CPC_FP64 && precision != CPC_FP32 && precision != CPC_SPLIT)
+  if (!known_precision(precision))
     return fail(CPC_ERR_UNSUPPORTED, "cp_convolve_from_spectra: precision form not implemented");
   precision = storage_precision(precision);
   if ((reinterpret_cast<uintptr_t>(W) & 15) || (reinterpret_cast<uintptr_t>(spec) & 15))

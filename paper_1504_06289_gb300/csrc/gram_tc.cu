@@ -1,35 +1,51 @@
-// float32-form E_H contraction on the tensor cores (tcgen05, kind::f16).
+// E_H contraction on the tensor cores (tcgen05, kind::f16): the float32 form
+// and the float64-accurate form CPC_FP64_TC.
 //
-// Same quantity as gemm3a_kernel (Sec. 3.2 Eq. Factor_Mk_Conv, Sec. 2.5
-// Eq. scal): G_l[r][s] = sum_i U_l[r][i] W_l[s*R_N+q][i], then
-// sum_{r<=s} (1 or 2) c_r c_s prod_l G_l[r][s].
+// Same quantity as gemm3a_kernel and tri_gram_kernel (Sec. 3.2 Eq.
+// Factor_Mk_Conv, Sec. 2.5 Eq. scal): G_l[r][s] = sum_i U_l[r][i] W_l[s*R_N+q][i],
+// then sum_{r<=s} (1 or 2) c_r c_s prod_l G_l[r][s].
 //
-// Exact slicing.  Every operand row x (a column of U or of the V_H factors,
-// as float32) is written as x = 2^e * (s0 2^-8 + s1 2^-16 + s2 2^-24) with
-// 2^e > max|x| and integer slices |s0| <= 256, |s1|, |s2| <= 128, stored as
-// bf16 (exact).  A product of two rows is
-//   2^(e_r + e_s - 16) * (S0 + S1 2^-8 + S2 2^-16),  S_g = sum_{a+b=g} sum_i s_a s_b,
-// dropping the a+b >= 3 terms (below float32 rounding of the operands).  Over
-// 256 cells S_0 and S_1 are integers of magnitude at most 2^24 (256 * 2^16
-// each), so the bf16 MMAs accumulate them exactly in TMEM whatever the tensor
-// core's rounding; S_2 (at most 256 * 81920 = 2.1e7) may pass 2^24, where a
-// float32 accumulation step can round by 2^-24 of S_2, i.e. below 2^-38 of the
-// 2^(e_r+e_s) scale of the entry.  Every 256 cells the accumulators are folded
-// into a compensated float32 sum (TwoSum) per entry.
+// Exact slicing (error-free splitting of the operands into low-precision
+// slices, Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 2012).  Every
+// operand row x (a column of U or of the V_H factors) is written as
+//   x = 2^(e-8) * sum_k t_k,  t_k = s_k 2^(-8k),  2^e > max|x| over the row,
+// with integer digits |s_0| <= 256, |s_k| <= 128 (k >= 1), each t_k exact in
+// bf16.  A product of two rows is 2^(e_r + e_s - 16) sum_{a,b} sum_i t_a t_b.
+//   * float32 form (NS = 3 slices of the float32 operands, 24 bits): the
+//     pairs a + b <= 2 (6 products per cell); the dropped ones lie below
+//     float32 rounding of the operands.
+//   * CPC_FP64_TC (NS = 5 slices of the float64 operands, 40 bits): the pairs
+//     a + b <= 4 (15 products per cell); the dropped ones lie below 2^-40 of
+//     the row scales.
+// Three TMEM accumulators per output: S_0 = sum t_0 t_0' and S_1 = sum (t_0 t_1'
+// + t_1 t_0') are integer multiples of 1 and 2^-8 of magnitude at most 2^24
+// units over 256 cells, so the bf16 MMAs accumulate them exactly whatever
+// the tensor core's rounding; S_2 collects every pair with a + b >= 2 (weight
+// 2^-16 and below), where an accumulation step can round by 2^-24 of S_2,
+// i.e. below 2^-38 of the entry's scale 2^(e_r+e_s).  (The float32 form keeps
+// its slices as the integers s_k and applies the weights 2^-8, 2^-16 at
+// readout; the float64 form stores the weighted t_k, so that its 12 products
+// with a + b >= 2 all land in S_2.)  Every 256 cells the accumulators are
+// folded into a compensated float32 sum (TwoSum, float32 form) or a float64
+// sum (CPC_FP64_TC) per entry.
 //
 // Tiles: a CTA pair (2-CTA cluster, cta_group::2) computes 256 rows of U (M)
 // x 128 rows of W (N) for one kernel term; each CTA streams its 128 U rows and
-// 64 W rows with TMA (cp.async.bulk.tensor, 128-byte swizzle, completion
+// 64 W rows with TMA (cp.async.bulk.tensor, 128-byte swizzle for 64-cell
+// chunks, 64-byte swizzle for the 32-cell chunks of CPC_FP64_TC; completion
 // counted on an mbarrier) through 3 shared-memory stages, and one thread of
 // the even CTA issues the MMAs for both.  Sixteen warps per CTA read the
-// accumulators after every four chunks; the three axes run as one stream of
-// chunks and the running product over axes stays in TMEM.
+// accumulators after every 256 cells.  Float32 form: the three axes run as
+// one stream of chunks and the running product over axes stays in TMEM.
+// CPC_FP64_TC: the readers write the float64 convolution matrices G, and
+// E_H is reduced from them by a separate kernel.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 
 #include "cpc_internal.h"
 #include "umma.cuh"
@@ -41,73 +57,104 @@ constexpr int BM = 128;      // U rows per CTA (M = 256 per CTA pair)
 constexpr int BN = 128;      // W rows (output columns) per pair tile
 constexpr int BNH = BN / 2;  // W rows loaded by each CTA of the pair
 static_assert(BM == BN, "the symmetric E_H tiling uses square 128 x 128 blocks");
-constexpr int BKC = 64;      // chunk of 64 cells = one 128-byte bf16 row
+static_assert(BN == 128, "TMEM: 4 accumulators or 3 + the product over axes, 128 columns each");
 constexpr int READERS = 16;  // accumulator reader warps: lane quadrant x column quarter
 constexpr int BNW = BN / 4;  // columns read by one reader warp
 constexpr int THREADS = (READERS + 1) * 32;  // + one TMA/MMA warp
 constexpr int STAGES = 3;
-constexpr int GROUP = 4;  // 64-cell chunks per TMEM accumulation: S_0, S_1 over 256 cells stay within 2^24
-constexpr uint32_t A_SLICE_BYTES = BM * 128, B_SLICE_BYTES = BNH * 128;
-constexpr uint32_t STAGE_BYTES = 3 * A_SLICE_BYTES + 3 * B_SLICE_BYTES;  // 72 KB per CTA
+constexpr int EXACT_CELLS = 256;     // cells per exact TMEM accumulation (S_0, S_1 within 2^24)
 constexpr uint32_t TMEM_COLS = 512;  // 3 groups x 128 columns, then the product over axes
 constexpr uint32_t PROD_COL = 3 * BN;
-// stages, alignment slack, barriers, then per-column exponents (3 axes) and coefficients
+// per-column exponents (3 axes) and coefficients; rows mode: the 4 column quarters of each row
 constexpr size_t kColBytes = 3 * BN * sizeof(int) + BN * sizeof(double);
-constexpr size_t kRowBytes = 4 * BM * sizeof(double);  // rows mode: the 4 column quarters of each row
-constexpr size_t kSmemBytes = size_t(STAGES) * STAGE_BYTES + 1024 + 256 + kColBytes + kRowBytes;
+constexpr size_t kRowBytes = 4 * BM * sizeof(double);
 constexpr long kSpinLimit = 20000000;
 
-// x -> (s0, s1, s2) with one exponent per row (2^e > max |x| over the row):
-// one CTA of 256 threads per row, the row read once into registers
-// (n / 256 values per thread, rounded up).
+// Shapes of one form: NS slices per operand, BKC cells per chunk (one
+// swizzled shared-memory row of BKC bf16: 128 or 64 bytes).
+template <int NS_, int BKC_, int NACC_>
+struct Form {
+  static constexpr int NS = NS_, BKC = BKC_;
+  static constexpr int NACC = NACC_;        // TMEM accumulators of BN columns per output tile
+  static constexpr uint32_t ROW = BKC * 2;  // bytes per operand row of a chunk
+  static constexpr int K_STEPS = BKC / 16;  // MMAs of K = 16 per slice pair and chunk
+  static constexpr uint32_t A_SLICE_BYTES = BM * ROW, B_SLICE_BYTES = BNH * ROW;
+  static constexpr uint32_t STAGE_BYTES = NS * (A_SLICE_BYTES + B_SLICE_BYTES);
+  static constexpr int GROUP = EXACT_CELLS / BKC;  // chunks per TMEM accumulation
+  static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + 1024 + 256 + kColBytes + kRowBytes;
+  static_assert(SMEM <= 232448, "shared memory of one CTA");
+};
+using Form32 = Form<3, 64, 3>;  // float32 form: 72 KB stages, S_0..S_2 + the product over axes
+using Form64 = Form<5, 32, 4>;  // CPC_FP64_TC: 60 KB stages, S_0..S_3 (no product over axes)
+
+// K-major operand descriptor for 128- or 64-byte swizzled rows (8-row atoms)
+template <uint32_t ROW>
+__device__ __forceinline__ uint64_t desc_k(uint32_t saddr) {
+  static_assert(ROW == 128 || ROW == 64, "swizzle width");
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= static_cast<uint64_t>(1) << 16;
+  d |= static_cast<uint64_t>((8 * ROW) >> 4) << 32;  // stride between 8-row atoms
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(ROW == 128 ? 2 : 4) << 61;  // SWIZZLE_128B / SWIZZLE_64B
+  return d;
+}
+
+// x -> NS slices with one exponent per row (2^e > max|x| over the row): one
+// CTA of 256 threads per row, the row read once into registers (n / 256
+// values per thread, rounded up).  Float32 form (NS = 3): the digits s_k of
+// the row rounded to float32, stored as integers.  CPC_FP64_TC (NS = 5): the
+// digits of the float64 row, stored weighted, t_k = s_k 2^(-8k).
 //
 // Source rows are (l, s, q) of a [3][R_f][R_N][n] array (R_N = 1 for U).
 // Slices are written chunk-blocked, so that the rows of one operand tile
-// (64 consecutive s, one 64-cell chunk) are one contiguous block:
-//   out[k][G = l*R_N + q][t][s][i % 64],  t = i / 64,  k = slice.
-template <typename TS, int VPT>
+// (64 consecutive s, one BKC-cell chunk) are one contiguous block:
+//   out[k][G = l*R_N + q][t][s][i % BKC],  t = i / BKC,  k = slice.
+template <typename TS, int VPT, class F>
 __global__ void __launch_bounds__(256) slice_rows_kernel(const TS* __restrict__ src, long long rows, int n, int R_f,
                                                          int R_N, __nv_bfloat16* __restrict__ out,
                                                          long long slice_stride, int* __restrict__ expo) {
-  __shared__ float red[8];
-  const int T = n >> 6;
+  constexpr int NS = F::NS, BKC = F::BKC;
+  constexpr bool WEIGHTED = NS > 3;
+  using V = typename std::conditional<WEIGHTED, double, float>::type;
+  __shared__ V red[8];
+  const int T = n / BKC;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
     const TS* x = src + row * n;
     const long long per_l = (long long)R_f * R_N;
     const int l = (int)(row / per_l);
     const int rem = (int)(row - l * per_l);
     const int srow = rem / R_N, q = rem - srow * R_N;
-    __nv_bfloat16* ob = out + ((long long)(l * R_N + q) * T * R_f + srow) * 64;
-    float v[VPT];
-    float m = 0.0f;
+    __nv_bfloat16* ob = out + ((long long)(l * R_N + q) * T * R_f + srow) * BKC;
+    V v[VPT];
+    V m = V(0);
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
       const int i = (k * 256 + threadIdx.x);  // coalesced
-      v[k] = (i < n) ? float(x[i]) : 0.0f;
-      m = fmaxf(m, fabsf(v[k]));
+      v[k] = (i < n) ? V(x[i]) : V(0);
+      m = fmax(m, fabs(v[k]));
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
-    float mm = red[0];
+    V mm = red[0];
 #pragma unroll
-    for (int w = 1; w < 8; ++w) mm = fmaxf(mm, red[w]);
+    for (int w = 1; w < 8; ++w) mm = fmax(mm, red[w]);
     int e = 0;
-    if (mm > 0.0f) frexpf(mm, &e);  // mm = f 2^e, f in [0.5, 1): |x| < 2^e
+    if (mm > V(0)) frexp(mm, &e);  // mm = f 2^e, f in [0.5, 1): |x| < 2^e
     if (threadIdx.x == 0) expo[row] = e;
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
       const int i = k * 256 + threadIdx.x;
       if (i >= n) continue;
-      const float a = ldexpf(v[k], 8 - e);  // |a| < 256
-      const float s0 = rintf(a);
-      const float b = (a - s0) * 256.0f;    // exact
-      const float s1 = rintf(b);
-      const float s2 = rintf((b - s1) * 256.0f);
-      __nv_bfloat16* o = ob + (long long)(i >> 6) * R_f * 64 + (i & 63);
-      o[0] = __float2bfloat16_rn(s0);
-      o[slice_stride] = __float2bfloat16_rn(s1);
-      o[2 * slice_stride] = __float2bfloat16_rn(s2);
+      V a = ldexp(v[k], 8 - e);  // |a| < 256
+      __nv_bfloat16* o = ob + (long long)(i / BKC) * R_f * BKC + (i % BKC);
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const V d = rint(a);   // digit s_j: |s_0| <= 256, |s_j| <= 128
+        a = (a - d) * V(256);  // exact
+        o[j * slice_stride] = __float2bfloat16_rn(float(WEIGHTED ? ldexp(d, -8 * j) : d));
+      }
     }
     __syncthreads();  // red[] reused by the next row
   }
@@ -170,6 +217,7 @@ struct Args {
   double* partial;         // E_H: one sum per CTA; rows mode: [(q * n_ct + ct) * M + r]
   double* G;               // E_H only (may be NULL)
   int* status;
+  int raster;              // rows mode: 256-row blocks whose pairs sweep the column tiles together
 };
 
 // 5D tiled TMA load into this CTA's shared memory; the innermost coordinate is
@@ -186,36 +234,38 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
 }
 
-// chunk tt of the stream (axis tt / T, cells (tt % T) * 64 ..) into stage tt % STAGES
+// chunk tt of the stream (axis tt / T, cells (tt % T) * BKC ..) into stage tt % STAGES
 // of this CTA; completion is counted on the even CTA's barrier (cluster address)
+template <class F>
 __device__ __forceinline__ void issue_stage(const CUtensorMap* mapA, const CUtensorMap* mapB, const Args& g,
                                             uint32_t sbase, uint32_t fullbar_cluster, int tt, int T, int q, int r0,
                                             int sb0) {
   const int l = tt / T, t = tt % T;
-  const uint32_t stage = sbase + (tt % STAGES) * STAGE_BYTES;
-  // all three slices of each operand tile in one copy: A dims (cell, r, t, l, slice),
+  const uint32_t stage = sbase + (tt % STAGES) * F::STAGE_BYTES;
+  // all slices of each operand tile in one copy: A dims (cell, r, t, l, slice),
   // B dims (cell, s, t, l*R_N + q, slice); rows past R_f read as zeros
   tma_load_5d(stage, mapA, r0, t, l, fullbar_cluster);
-  tma_load_5d(stage + 3 * A_SLICE_BYTES, mapB, sb0, t, l * g.R_N + q, fullbar_cluster);
+  tma_load_5d(stage + F::NS * F::A_SLICE_BYTES, mapB, sb0, t, l * g.R_N + q, fullbar_cluster);
 }
 
-// the 6 slice-pair products of one chunk for the CTA pair (M = 256, N = 128)
+// the slice-pair products of one chunk for the CTA pair (M = 256, N = 128):
+// pair (a, b) goes to accumulator min(a + b, NACC - 1); the first MMA into
+// each accumulator of a group is (0, g) at k-step 0
+template <class F>
 __device__ __forceinline__ void issue_mmas(uint32_t stage, uint32_t tacc, uint32_t accumulate) {
   constexpr uint32_t idesc = umma::idesc_bf16_f32(2 * BM, BN);
-  const uint32_t a0 = stage, b0 = stage + 3 * A_SLICE_BYTES;
-  // group g accumulates the slice pairs (a, b) with a + b = g
+  const uint32_t a0 = stage, b0 = stage + F::NS * F::A_SLICE_BYTES;
 #pragma unroll
-  for (int g = 0; g < 3; ++g) {
-    uint32_t acc = accumulate;
+  for (int a = 0; a < F::NS; ++a) {
 #pragma unroll
-    for (int a = 0; a <= g; ++a) {
-      const int b = g - a;
+    for (int b = 0; a + b < F::NS; ++b) {
+      const int grp = a + b < F::NACC - 1 ? a + b : F::NACC - 1;
 #pragma unroll
-      for (int kk = 0; kk < BKC / 16; ++kk) {
-        const uint64_t ad = umma::desc_k_sw128(a0 + a * A_SLICE_BYTES + kk * 32);
-        const uint64_t bd = umma::desc_k_sw128(b0 + b * B_SLICE_BYTES + kk * 32);
-        umma::mma_bf16_pair(tacc + g * BN, ad, bd, idesc, acc);
-        acc = 1;
+      for (int kk = 0; kk < F::K_STEPS; ++kk) {
+        const uint64_t ad = desc_k<F::ROW>(a0 + a * F::A_SLICE_BYTES + kk * 32);
+        const uint64_t bd = desc_k<F::ROW>(b0 + b * F::B_SLICE_BYTES + kk * 32);
+        const uint32_t acc = (a == 0 && b == grp && kk == 0) ? accumulate : 1u;
+        umma::mma_bf16_pair(tacc + grp * BN, ad, bd, idesc, acc);
       }
     }
   }
@@ -243,29 +293,33 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, v
 // even CTA's full barrier; one thread of the even CTA issues the pair MMAs
 // (each CTA's TMEM receives its 128 rows x 128 columns).  In each CTA, warps
 // 0-15 read the accumulators (warp w: TMEM lanes 32 (w % 4).., columns
-// 32 (w / 4)..), warp 16 drives the copies.  Up to GROUP = 4 consecutive
-// 64-cell chunks accumulate before each readout (S_0 and S_1 stay integers of
-// magnitude at most 2^24 over 256 cells, so they are exact).
+// 32 (w / 4)..), warp 16 drives the copies.  GROUP consecutive chunks (256
+// cells) accumulate before each readout (S_0 and S_1 stay exact).
 // Barriers: full[stage] (even CTA: both halves landed), sfree[stage] (both
 // CTAs: the MMAs reading a stage finished), done (both CTAs: a group of
 // chunks accumulated), freeb (even CTA: the 32 reader warps of the pair
 // took the accumulators out of TMEM).
+// GOUT (CPC_FP64_TC): the readers fold in float64 and write G (both
+// triangles); there is no product over axes and no E_H or row sum here.
+template <class F, bool GOUT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
 gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Args g) {
+  static_assert(GOUT ? F::NACC == 4 : F::NACC == 3, "TMEM columns: accumulators (+ product over axes)");
+  constexpr int GROUP = F::GROUP;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = umma::smem_u32(smem_raw);
   const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
   uint8_t* smem = smem_raw + pad;
   const uint32_t sbase = raw + pad;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);  // [STAGES]
-  uint64_t* sfree = full + STAGES;                                             // [STAGES]
-  uint64_t* done = sfree + STAGES;                                             // [1]
-  uint64_t* freeb = done + 1;                                                  // [1]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * F::STAGE_BYTES);  // [STAGES]
+  uint64_t* sfree = full + STAGES;                                                // [STAGES]
+  uint64_t* done = sfree + STAGES;                                                // [1]
+  uint64_t* freeb = done + 1;                                                     // [1]
   uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(freeb + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_ptr + 1);
-  double* col_c = reinterpret_cast<double*>(smem + STAGES * STAGE_BYTES + 256);  // [BN]
-  int* col_e = reinterpret_cast<int*>(col_c + BN);                              // [3][BN]
-  double* row_q = reinterpret_cast<double*>(col_e + 3 * BN);                    // [4][BM]
+  double* col_c = reinterpret_cast<double*>(smem + STAGES * F::STAGE_BYTES + 256);  // [BN]
+  int* col_e = reinterpret_cast<int*>(col_c + BN);                                 // [3][BN]
+  double* row_q = reinterpret_cast<double*>(col_e + 3 * BN);                       // [4][BM]
   __shared__ double red[THREADS / 32];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -274,9 +328,17 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const int n_ct = (g.Ns + BN - 1) / BN;
   const int pair = blockIdx.x >> 1;
   int ct, r0;
-  if (g.rows_mode) {  // rectangular: 256-row x 128-column pair tiles
-    const int rp = pair / n_ct;
-    ct = pair % n_ct;
+  if (g.rows_mode) {
+    // rectangular 256-row x 128-column pair tiles, rastered in groups of
+    // `raster` row blocks: consecutive pairs take the rows of one group for a
+    // column tile, then the next column tile, so the pairs in flight share both
+    // their row blocks and their column tiles in L2
+    const int n_rp = (g.M + 2 * BM - 1) / (2 * BM);
+    const int per_group = g.raster * n_ct;
+    const int grp = pair / per_group, rem = pair - grp * per_group;
+    const int rows_here = min(g.raster, n_rp - grp * g.raster);
+    ct = rem / rows_here;
+    const int rp = grp * g.raster + (rem - ct * rows_here);
     r0 = rp * 2 * BM + int(rank) * BM;
   } else {  // symmetric: two 128 x 128 blocks of one column block (above)
     int rb0, rb1;
@@ -289,7 +351,7 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   // the tile's column coefficients and row exponents of W, once
   for (int i = tid; i < 4 * BN; i += THREADS) {
     const int j = i % BN, s = s0 + j;
-    if (i < BN) col_c[j] = (s < g.Ns) ? g.c_col[s] : 0.0;
+    if (i < BN) col_c[j] = (s < g.Ns && g.c_col) ? g.c_col[s] : 0.0;
     else col_e[i - BN] = (s < g.Ns) ? g.eB[((long long)(i / BN - 1) * g.Ns + s) * g.R_N + q] : 0;
   }
   if (warp == 0) umma::tmem_alloc_pair(tmem_ptr, TMEM_COLS);
@@ -308,7 +370,7 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   umma::cluster_sync();  // the peer's barriers are initialised before any copy or arrive reaches them
   umma::fence_after();
   const uint32_t tbase = *tmem_ptr;
-  const int T = g.n / BKC, TT = 3 * T;  // chunks (T even)
+  const int T = g.n / F::BKC, TT = 3 * T;  // chunks per axis, in all
   // chunks accumulate in TMEM in groups of up to GROUP (the last group of an
   // axis may be shorter); GA groups per axis, 3 GA in all
   const int GA = (T + GROUP - 1) / GROUP;
@@ -320,8 +382,8 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       auto fullc = [&](int tt) { return umma::mapa(umma::smem_u32(&full[tt % STAGES]), 0); };
       if (rank == 0) {
         for (int tt = 0; tt < STAGES - 1 && tt < TT; ++tt) {
-          mbar_expect_tx(umma::smem_u32(&full[tt]), 2 * STAGE_BYTES);
-          issue_stage(&mapA, &mapB, g, sbase, fullc(tt), tt, T, q, r0, sb0);
+          mbar_expect_tx(umma::smem_u32(&full[tt]), 2 * F::STAGE_BYTES);
+          issue_stage<F>(&mapA, &mapB, g, sbase, fullc(tt), tt, T, q, r0, sb0);
         }
         for (int tt = 0; tt < TT; ++tt) {
           const int t = tt % T, gi = (tt / T) * GA + t / GROUP;  // group of this chunk
@@ -329,23 +391,24 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           if (!wait_or_abort(&full[tt % STAGES], (tt / STAGES) & 1, abort_flag)) break;
           if (first && gi >= 1 && !wait_or_abort(freeb, (gi - 1) & 1, abort_flag)) break;
           umma::fence_after();
-          issue_mmas(sbase + (tt % STAGES) * STAGE_BYTES, tbase, first ? 0u : 1u);
+          issue_mmas<F>(sbase + (tt % STAGES) * F::STAGE_BYTES, tbase, first ? 0u : 1u);
           umma::mma_commit_pair(&sfree[tt % STAGES]);
           if (last) umma::mma_commit_pair(done);
           const int tn = tt + STAGES - 1;
           if (tn < TT) {
             // stage tn % STAGES last held chunk tt - 1: wait until its MMAs finished
             if (tt >= 1 && !wait_or_abort(&sfree[(tt - 1) % STAGES], ((tt - 1) / STAGES) & 1, abort_flag)) break;
-            mbar_expect_tx(umma::smem_u32(&full[tn % STAGES]), 2 * STAGE_BYTES);
-            issue_stage(&mapA, &mapB, g, sbase, fullc(tn), tn, T, q, r0, sb0);
+            mbar_expect_tx(umma::smem_u32(&full[tn % STAGES]), 2 * F::STAGE_BYTES);
+            issue_stage<F>(&mapA, &mapB, g, sbase, fullc(tn), tn, T, q, r0, sb0);
           }
         }
       } else {
-        for (int tt = 0; tt < STAGES - 1 && tt < TT; ++tt) issue_stage(&mapA, &mapB, g, sbase, fullc(tt), tt, T, q, r0, sb0);
+        for (int tt = 0; tt < STAGES - 1 && tt < TT; ++tt)
+          issue_stage<F>(&mapA, &mapB, g, sbase, fullc(tt), tt, T, q, r0, sb0);
         for (int tt = 0; tt + STAGES - 1 < TT; ++tt) {
           const int tn = tt + STAGES - 1;
           if (tt >= 1 && !wait_or_abort(&sfree[(tt - 1) % STAGES], ((tt - 1) / STAGES) & 1, abort_flag)) break;
-          issue_stage(&mapA, &mapB, g, sbase, fullc(tn), tn, T, q, r0, sb0);
+          issue_stage<F>(&mapA, &mapB, g, sbase, fullc(tn), tn, T, q, r0, sb0);
         }
       }
       // drain: every commit of the pair has arrived on this CTA's stage barriers
@@ -359,15 +422,22 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     const int r = r0 + 32 * quad + lane;  // this thread's row and TMEM lane
     const uint32_t lane_base = tbase + (static_cast<uint32_t>(32 * quad) << 16) + part * BNW;
     const int sh0 = s0 + part * BNW;  // first column of this warp
-    // running sum of an axis as an unevaluated pair tot + lo (TwoSum per fold);
-    // |lo| stays near 2^-24 |tot|, so lo is kept in bf16 (two per register):
-    // its own rounding is then below 2^-32 |tot|
-    float tot[BNW];
-    __nv_bfloat162 lo[BNW / 2];
+    // float32 form: running sum of an axis as an unevaluated pair tot + lo
+    // (TwoSum per fold); |lo| stays near 2^-24 |tot|, so lo is kept in bf16
+    // (two per register): its own rounding is then below 2^-32 |tot|.
+    // CPC_FP64_TC: a float64 sum per entry (tot64).
+    float tot[GOUT ? 1 : BNW];
+    __nv_bfloat162 lo[GOUT ? 1 : BNW / 2];
+    double tot64[GOUT ? BNW : 1];
 #pragma unroll
-    for (int j = 0; j < BNW; ++j) tot[j] = 0.0f;
+    for (int j = 0; j < BNW; ++j) {
+      if constexpr (GOUT) tot64[j] = 0.0;
+      else tot[j] = 0.0f;
+    }
+    if constexpr (!GOUT) {
 #pragma unroll
-    for (int j = 0; j < BNW / 2; ++j) lo[j] = __float2bfloat162_rn(0.0f);
+      for (int j = 0; j < BNW / 2; ++j) lo[j] = __float2bfloat162_rn(0.0f);
+    }
     double row = 0.0;
     bool ok = true;
     for (int gi = 0; gi < 3 * GA && ok; ++gi) {
@@ -375,80 +445,107 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
       umma::fence_after();
 #pragma unroll
       for (int cb = 0; cb < BNW / 8; ++cb) {
-        float v0[8], v1[8], v2[8];
+        float v0[8], v1[8], v2[8], v3[8];
         const uint32_t col = cb * 8;
         umma::tmem_ld8(lane_base + col, v0);
         umma::tmem_ld8(lane_base + col + BN, v1);
         umma::tmem_ld8(lane_base + col + 2 * BN, v2);
+        if constexpr (F::NACC > 3) umma::tmem_ld8(lane_base + col + 3 * BN, v3);
         umma::tmem_ld_wait();
+        if constexpr (GOUT) {
+          // weighted slices: the four sums already carry their weights
 #pragma unroll
-        for (int j = 0; j < 8; j += 2) {
-          float e[2];
+          for (int j = 0; j < 8; ++j)
+            tot64[cb * 8 + j] += ((double(v0[j]) + double(v1[j])) + double(v2[j])) + double(v3[j]);
+        } else {
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const float v = fmaf(v2[j + h], 1.0f / 65536.0f, fmaf(v1[j + h], 1.0f / 256.0f, v0[j + h]));
-            float& t = tot[cb * 8 + j + h];
-            const float sm = t + v, bb = sm - t;
-            e[h] = (t - (sm - bb)) + (v - bb);
-            t = sm;
+          for (int j = 0; j < 8; j += 2) {
+            float e[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float v = fmaf(v2[j + h], 1.0f / 65536.0f, fmaf(v1[j + h], 1.0f / 256.0f, v0[j + h]));
+              float& t = tot[cb * 8 + j + h];
+              const float sm = t + v, bb = sm - t;
+              e[h] = (t - (sm - bb)) + (v - bb);
+              t = sm;
+            }
+            __nv_bfloat162& L = lo[(cb * 8 + j) / 2];
+            const float2 f = __bfloat1622float2(L);
+            L = __floats2bfloat162_rn(f.x + e[0], f.y + e[1]);
           }
-          __nv_bfloat162& L = lo[(cb * 8 + j) / 2];
-          const float2 f = __bfloat1622float2(L);
-          L = __floats2bfloat162_rn(f.x + e[0], f.y + e[1]);
         }
       }
       umma::fence_before();
       __syncwarp();
       if (lane == 0) umma::mbar_arrive_cluster(freeb_even);
       if (gi % GA == GA - 1) {
-        // axis l finished: G_l = 2^(e_r + e_s - 16) (tot + lo); the running
-        // product over axes lives in TMEM columns PROD_COL.. between axes
+        // axis l finished: G_l = 2^(e_r + e_s - 16) (sum of the folds)
         const int l = gi / GA;
         const int er = (r < g.M) ? g.eA[l * g.M + r] : 0;
+        if constexpr (GOUT) {
 #pragma unroll
-        for (int cb = 0; cb < BNW / 16; ++cb) {
-          float pv[16];
-          if (l > 0) {
-            umma::tmem_ld16(lane_base + PROD_COL + cb * 16, pv);
-            umma::tmem_ld_wait();
-          }
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int j = cb * 16 + jj, s = sh0 + j;
+          for (int j = 0; j < BNW; ++j) {
+            const int s = sh0 + j;
             const int es = col_e[l * BN + part * BNW + j];
-            const __nv_bfloat162 L = lo[j / 2];
-            const float lj = (j & 1) ? __high2float(L) : __low2float(L);
-            const float Gv = ldexpf(tot[j] + lj, er + es - 16);
-            tot[j] = 0.0f;
-            if (j & 1) lo[j / 2] = __float2bfloat162_rn(0.0f);
-            const bool in = r < g.M && s < g.Ns && (!diag || r <= s);
-            if (g.G && in) {
+            const double Gv = ldexp(tot64[j], er + es - 16);
+            tot64[j] = 0.0;
+            if (r < g.M && s < g.Ns && (!diag || r <= s)) {
               double* Gq = g.G + ((size_t)l * gridDim.y + q) * (size_t)g.M * g.M;
               Gq[(size_t)r * g.M + s] = Gv;
               Gq[(size_t)s * g.M + r] = Gv;
             }
-            const float pr = (l > 0) ? pv[jj] * Gv : Gv;
-            pv[jj] = pr;
-            if (l == 2 && in) {
-              const double wgt = (g.rows_mode || r == s) ? 1.0 : 2.0;  // E_H: off-diagonal pairs twice
-              row += wgt * col_c[part * BNW + j] * double(pr);
-            }
           }
-          if (l < 2) {
-            umma::tmem_st16(lane_base + PROD_COL + cb * 16, pv);
-            umma::tmem_st_wait();
+        } else {
+          // the running product over axes lives in TMEM columns PROD_COL.. between axes
+#pragma unroll
+          for (int cb = 0; cb < BNW / 16; ++cb) {
+            float pv[16];
+            if (l > 0) {
+              umma::tmem_ld16(lane_base + PROD_COL + cb * 16, pv);
+              umma::tmem_ld_wait();
+            }
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) {
+              const int j = cb * 16 + jj, s = sh0 + j;
+              const int es = col_e[l * BN + part * BNW + j];
+              const __nv_bfloat162 L = lo[j / 2];
+              const float lj = (j & 1) ? __high2float(L) : __low2float(L);
+              const float Gv = ldexpf(tot[j] + lj, er + es - 16);
+              tot[j] = 0.0f;
+              if (j & 1) lo[j / 2] = __float2bfloat162_rn(0.0f);
+              const bool in = r < g.M && s < g.Ns && (!diag || r <= s);
+              if (g.G && in) {
+                double* Gq = g.G + ((size_t)l * gridDim.y + q) * (size_t)g.M * g.M;
+                Gq[(size_t)r * g.M + s] = Gv;
+                Gq[(size_t)s * g.M + r] = Gv;
+              }
+              const float pr = (l > 0) ? pv[jj] * Gv : Gv;
+              pv[jj] = pr;
+              if (l == 2 && in) {
+                const double wgt = (g.rows_mode || r == s) ? 1.0 : 2.0;  // E_H: off-diagonal pairs twice
+                row += wgt * col_c[part * BNW + j] * double(pr);
+              }
+            }
+            if (l < 2) {
+              umma::tmem_st16(lane_base + PROD_COL + cb * 16, pv);
+              umma::tmem_st_wait();
+            }
           }
         }
       }
     }
-    if (g.rows_mode) row_q[part * BM + 32 * quad + lane] = ok ? row : 0.0;
-    else if (ok && r < g.M) sum = g.c[r] * row;
+    if (!GOUT) {
+      if (g.rows_mode) row_q[part * BM + 32 * quad + lane] = ok ? row : 0.0;
+      else if (ok && r < g.M) sum = g.c[r] * row;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
   if (lane == 0) red[warp] = sum;
   umma::fence_before();
   __syncthreads();
-  if (g.rows_mode) {
+  if (GOUT) {
+    if (tid == 0 && *abort_flag) atomicExch(g.status, 1);
+  } else if (g.rows_mode) {
     // row sums of this CTA's 128 rows over the tile's 128 columns
     if (tid < BM && r0 + tid < g.M)
       g.partial[((size_t)q * n_ct + ct) * g.M + r0 + tid] =
@@ -467,18 +564,18 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   }
 }
 
-template <typename TS>
+template <typename TS, class F>
 int launch_slice(const TS* src, long long rows, int n, int R_f, int R_N, __nv_bfloat16* out, long long slice_stride,
                  int* expo, cudaStream_t s) {
   const unsigned grid = (unsigned)std::min<long long>(rows, 1 << 20);
   const int slot = timing_begin("slice_rows_kernel", s);
   switch ((n + 255) / 256) {
-    case 1: slice_rows_kernel<TS, 1><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
-    case 2: slice_rows_kernel<TS, 2><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
-    case 4: slice_rows_kernel<TS, 4><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
-    case 8: slice_rows_kernel<TS, 8><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
-    case 16: slice_rows_kernel<TS, 16><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
-    case 32: slice_rows_kernel<TS, 32><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
+    case 1: slice_rows_kernel<TS, 1, F><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
+    case 2: slice_rows_kernel<TS, 2, F><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
+    case 4: slice_rows_kernel<TS, 4, F><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
+    case 8: slice_rows_kernel<TS, 8, F><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
+    case 16: slice_rows_kernel<TS, 16, F><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
+    case 32: slice_rows_kernel<TS, 32, F><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
     default:
       timing_end(slot, s);
       return fail(CPC_ERR_UNSUPPORTED, "tensor-core contraction: n must be a power of two up to 8192");
@@ -488,43 +585,68 @@ int launch_slice(const TS* src, long long rows, int n, int R_f, int R_N, __nv_bf
   return CPC_OK;
 }
 
+// E_H from the float64 convolution matrices (CPC_FP64_TC): block (r, q) sums
+// (1 or 2) c_s prod_l G_l[q][r][s] over s >= r in a fixed order, times c_r.
+__global__ void __launch_bounds__(128) eh_from_g_kernel(const double* __restrict__ G, const double* __restrict__ c,
+                                                        int R_f, int R_N, double* __restrict__ partial) {
+  __shared__ double red[4];
+  const int r = blockIdx.x, q = blockIdx.y;
+  const size_t plane = (size_t)R_f * R_f, axis = (size_t)R_N * plane;
+  const double* g0 = G + (size_t)q * plane + (size_t)r * R_f;
+  double acc = 0.0;
+  for (int s = r + threadIdx.x; s < R_f; s += blockDim.x)
+    acc += (s == r ? 1.0 : 2.0) * c[s] * (g0[s] * g0[axis + s] * g0[2 * axis + s]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) partial[(size_t)q * R_f + r] = c[r] * (((red[0] + red[1]) + red[2]) + red[3]);
+}
+
 }  // namespace tc
 
 // one partial per CTA: 2 CTAs per pair tile of the symmetric tiling and kernel term
 size_t tc_partials(int R_f, int R_N) {
   return size_t(2) * tc::eh_pair_tiles((R_f + tc::BN - 1) / tc::BN) * R_N;
 }
+// CPC_FP64_TC: one partial per row and kernel term (eh_from_g_kernel)
+size_t tc64_partials(int R_f, int R_N) { return size_t(R_f) * R_N; }
 
 // n a multiple of 128 (the convolution that writes the W slices needs n >= 128)
-bool tc_supported(const cpc_kernel* P) { return P->n >= 2 * tc::BKC && P->n % (2 * tc::BKC) == 0; }
+bool tc_supported(const cpc_kernel* P) { return P->n >= 128 && P->n % 128 == 0; }
 
 namespace {
 // workspace of the tensor-core contraction of M A rows against Ns R_N W rows:
-// A slices, W slices, row exponents of A and W, status word (each 256-aligned)
+// A slices, W slices, row exponents of A and W, status word (each 256-aligned);
+// CPC_FP64_TC also holds the float64 convolution matrices G
 struct TcLayout {
-  size_t a, b;  // slice elements of A and W (all 3 slices, 3 axes)
-  size_t off_b, off_ea, off_eb, off_status, total;
+  size_t a, b;  // slice elements of A and W (all slices, 3 axes)
+  size_t off_b, off_ea, off_eb, off_status, off_g, total;
 };
-TcLayout tc_layout(const cpc_kernel* P, int M, int Ns) {
+TcLayout tc_layout(const cpc_kernel* P, int M, int Ns, int ns = 3, bool with_g = false) {
   TcLayout L;
-  L.a = size_t(3) * 3 * M * P->n;
-  L.b = size_t(3) * 3 * size_t(Ns) * P->R_N * P->n;
+  L.a = size_t(ns) * 3 * M * P->n;
+  L.b = size_t(ns) * 3 * size_t(Ns) * P->R_N * P->n;
   L.off_b = align256(2 * L.a);
   L.off_ea = L.off_b + align256(2 * L.b);
   L.off_eb = L.off_ea + align256(4 * size_t(3) * M);
   L.off_status = L.off_eb + align256(4 * size_t(3) * Ns * P->R_N);
-  L.total = L.off_status + 256;
+  L.off_g = L.off_status + 256;
+  L.total = L.off_g + (with_g ? align256(sizeof(double) * 3 * size_t(P->R_N) * M * M) : 0);
   return L;
 }
 }  // namespace
 
 size_t tc_workspace(const cpc_kernel* P, int R_f) { return tc_layout(P, R_f, R_f).total; }
+size_t tc64_workspace(const cpc_kernel* P, int R_f) { return tc_layout(P, R_f, R_f, tc::Form64::NS, true).total; }
 size_t tc_rows_workspace(const cpc_kernel* P, int M, int Ns) { return tc_layout(P, M, Ns).total; }
 size_t tc_rows_groups(const cpc_kernel* P, int Ns) { return size_t((Ns + tc::BN - 1) / tc::BN) * P->R_N; }
 
 // status (int) of the tc workspace
 int* tc_status_ptr(const cpc_kernel* P, int R_f, void* ws) {
   return reinterpret_cast<int*>(static_cast<unsigned char*>(ws) + tc_layout(P, R_f, R_f).off_status);
+}
+int* tc64_status_ptr(const cpc_kernel* P, int R_f, void* ws) {
+  return reinterpret_cast<int*>(static_cast<unsigned char*>(ws) + tc_layout(P, R_f, R_f, tc::Form64::NS, true).off_status);
 }
 int* tc_rows_status_ptr(const cpc_kernel* P, int M, int Ns, void* ws) {
   return reinterpret_cast<int*>(static_cast<unsigned char*>(ws) + tc_layout(P, M, Ns).off_status);
@@ -560,61 +682,75 @@ void tc_w_slices(const cpc_kernel* P, int R_f, void* ws, __nv_bfloat16** slices,
 }
 
 namespace {
-// slices (unless W is already sliced), tensor maps and the launch
-int launch_tc(const cpc_kernel* P, int M, int Ns, const double* U, const float* W, const double* c,
-              const double* c_col, double* G, double* partial, void* ws, cudaStream_t s, bool w_sliced,
-              int rows_mode) {
+// tensor maps of the chunk-blocked slices and the launch
+template <class F, bool GOUT>
+int launch_tc_kernel(const cpc_kernel* P, int M, int Ns, const TcLayout& L, unsigned char* w, const double* c,
+                     const double* c_col, double* G, double* partial, cudaStream_t s, int rows_mode, int raster) {
   const int n = P->n, R_N = P->R_N;
-  const TcLayout L = tc_layout(P, M, Ns);
-  unsigned char* w = static_cast<unsigned char*>(ws);
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(w);
   __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(w + L.off_b);
   int* eA = reinterpret_cast<int*>(w + L.off_ea);
   int* eB = reinterpret_cast<int*>(w + L.off_eb);
   int* status = reinterpret_cast<int*>(w + L.off_status);
-  CPC_CUDA(cudaMemsetAsync(status, 0, sizeof(int), s));
-  int st0 = tc::launch_slice(U, 3LL * M, n, M, 1, As, (long long)(L.a / 3), eA, s);
-  if (st0) return st0;
-  if (!w_sliced) {  // else the convolution already wrote them (convolve_from_spectra_sliced)
-    st0 = tc::launch_slice(W, 3LL * Ns * R_N, n, Ns, R_N, Bs, (long long)(L.b / 3), eB, s);
-    if (st0) return st0;
-  }
-
   EncodeTiledFn enc;
   int st = encode_fn(&enc);
   if (st) return st;
   CUtensorMap mapA, mapB;
-  const int T = n / tc::BKC;
+  const int T = n / F::BKC;
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUtensorMapSwizzle swz = F::ROW == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  const cuuint64_t row = F::ROW;
   {
-    // [slice 3][l 3][t T][r M][64 cells]
-    const cuuint64_t dims[5] = {64, (cuuint64_t)M, (cuuint64_t)T, 3, 3};
-    const cuuint64_t row = 128, strides[4] = {row, row * M, row * M * T, row * M * T * 3};
-    const cuuint32_t box[5] = {tc::BKC, tc::BM, 1, 1, 3};
+    // [slice NS][l 3][t T][r M][BKC cells]
+    const cuuint64_t dims[5] = {(cuuint64_t)F::BKC, (cuuint64_t)M, (cuuint64_t)T, 3, (cuuint64_t)F::NS};
+    const cuuint64_t strides[4] = {row, row * M, row * M * T, row * M * T * 3};
+    const cuuint32_t box[5] = {(cuuint32_t)F::BKC, tc::BM, 1, 1, (cuuint32_t)F::NS};
     if (enc(&mapA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, As, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(CPC_ERR_CUDA, "tensor map for the U slices");
   }
   {
-    // [slice 3][l*R_N + q][t T][s Ns][64 cells]
-    const cuuint64_t dims[5] = {64, (cuuint64_t)Ns, (cuuint64_t)T, (cuuint64_t)3 * R_N, 3};
-    const cuuint64_t row = 128, strides[4] = {row, row * Ns, row * Ns * T, row * Ns * T * 3 * R_N};
-    const cuuint32_t box[5] = {tc::BKC, tc::BNH, 1, 1, 3};
+    // [slice NS][l*R_N + q][t T][s Ns][BKC cells]
+    const cuuint64_t dims[5] = {(cuuint64_t)F::BKC, (cuuint64_t)Ns, (cuuint64_t)T, (cuuint64_t)3 * R_N,
+                                (cuuint64_t)F::NS};
+    const cuuint64_t strides[4] = {row, row * Ns, row * Ns * T, row * Ns * T * 3 * R_N};
+    const cuuint32_t box[5] = {(cuuint32_t)F::BKC, tc::BNH, 1, 1, (cuuint32_t)F::NS};
     if (enc(&mapB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, Bs, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return fail(CPC_ERR_CUDA, "tensor map for the V_H factor slices");
   }
   const int n_rp = (M + 2 * tc::BM - 1) / (2 * tc::BM), n_ct = (Ns + tc::BN - 1) / tc::BN;
   const long long gx = rows_mode ? 2LL * n_rp * n_ct : 2LL * tc::eh_pair_tiles(n_ct);
   if (gx > 0x7fffffffLL || R_N > 65535) return fail(CPC_ERR_UNSUPPORTED, "tensor-core contraction: grid too large");
   dim3 grid((unsigned)gx, R_N);  // clusters of 2 along x
-  tc::Args args{eA, eB, M, Ns, R_N, n, rows_mode, c, c_col, partial, G, status};
-  CPC_CUDA(cudaFuncSetAttribute(tc::gemm3_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc::kSmemBytes)));
+  tc::Args args{eA, eB, M, Ns, R_N, n, rows_mode, c, c_col, partial, G, status, std::max(1, std::min(raster, n_rp))};
+  auto kern = tc::gemm3_tc_kernel<F, GOUT>;
+  CPC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(F::SMEM)));
   const int slot = timing_begin("gemm3_tc_kernel", s);
-  tc::gemm3_tc_kernel<<<grid, tc::THREADS, tc::kSmemBytes, s>>>(mapA, mapB, args);
+  kern<<<grid, tc::THREADS, F::SMEM, s>>>(mapA, mapB, args);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("gemm3_tc_kernel");
   return CPC_OK;
+}
+
+// float32 form: slices (unless W is already sliced), tensor maps and the launch
+int launch_tc(const cpc_kernel* P, int M, int Ns, const double* U, const float* W, const double* c,
+              const double* c_col, double* G, double* partial, void* ws, cudaStream_t s, bool w_sliced,
+              int rows_mode, int raster = 1) {
+  const int n = P->n, R_N = P->R_N;
+  const TcLayout L = tc_layout(P, M, Ns);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  CPC_CUDA(cudaMemsetAsync(w + L.off_status, 0, sizeof(int), s));
+  int st0 = tc::launch_slice<double, tc::Form32>(U, 3LL * M, n, M, 1, reinterpret_cast<__nv_bfloat16*>(w),
+                                                 (long long)(L.a / 3), reinterpret_cast<int*>(w + L.off_ea), s);
+  if (st0) return st0;
+  if (!w_sliced) {  // else the convolution already wrote them (convolve_from_spectra_sliced)
+    st0 = tc::launch_slice<float, tc::Form32>(W, 3LL * Ns * R_N, n, Ns, R_N,
+                                              reinterpret_cast<__nv_bfloat16*>(w + L.off_b), (long long)(L.b / 3),
+                                              reinterpret_cast<int*>(w + L.off_eb), s);
+    if (st0) return st0;
+  }
+  return launch_tc_kernel<tc::Form32, false>(P, M, Ns, L, w, c, c_col, G, partial, s, rows_mode, raster);
 }
 }  // namespace
 
@@ -623,11 +759,36 @@ int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, 
   return launch_tc(P, R_f, R_f, U, W, c, c, G, partial, ws, s, w_sliced, 0);
 }
 
+// CPC_FP64_TC: five weighted slices of the float64 U and W, the convolution
+// matrices in float64 (into G, or the workspace's G when G is NULL), then
+// partial[q R_f + r] = c_r sum_{s >= r} (1 or 2) c_s prod_l G_l[q][r][s]
+int launch_eh_tc64(const cpc_kernel* P, int R_f, const double* U, const double* W, const double* c, double* G,
+                   double* partial, void* ws, cudaStream_t s) {
+  const int n = P->n, R_N = P->R_N;
+  const TcLayout L = tc_layout(P, R_f, R_f, tc::Form64::NS, true);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  CPC_CUDA(cudaMemsetAsync(w + L.off_status, 0, sizeof(int), s));
+  int st = tc::launch_slice<double, tc::Form64>(U, 3LL * R_f, n, R_f, 1, reinterpret_cast<__nv_bfloat16*>(w),
+                                                (long long)(L.a / tc::Form64::NS),
+                                                reinterpret_cast<int*>(w + L.off_ea), s);
+  if (st) return st;
+  st = tc::launch_slice<double, tc::Form64>(W, 3LL * R_f * R_N, n, R_f, R_N,
+                                            reinterpret_cast<__nv_bfloat16*>(w + L.off_b),
+                                            (long long)(L.b / tc::Form64::NS), reinterpret_cast<int*>(w + L.off_eb), s);
+  if (st) return st;
+  double* Gd = G ? G : reinterpret_cast<double*>(w + L.off_g);
+  st = launch_tc_kernel<tc::Form64, true>(P, R_f, R_f, L, w, c, c, Gd, partial, s, 0, 1);
+  if (st) return st;
+  tc::eh_from_g_kernel<<<dim3(R_f, R_N), 128, 0, s>>>(Gd, c, R_f, R_N, partial);
+  CPC_LAUNCH_CHECK("eh_from_g_kernel");
+  return CPC_OK;
+}
+
 // Coulomb-matrix rows: rowpart[(q * n_ct + ct) * M + r] = sum over the 128
 // columns s of tile ct of c_s prod_l G_l[r][s, q] (M item factors, Ns = R_rho)
 int launch_rows_tc(const cpc_kernel* P, int M, const double* U_items, int Ns, const float* W_rho,
-                   const double* c_rho, double* rowpart, void* ws, cudaStream_t s) {
-  return launch_tc(P, M, Ns, U_items, W_rho, nullptr, c_rho, nullptr, rowpart, ws, s, false, 1);
+                   const double* c_rho, double* rowpart, void* ws, cudaStream_t s, int raster) {
+  return launch_tc(P, M, Ns, U_items, W_rho, nullptr, c_rho, nullptr, rowpart, ws, s, false, 1, raster);
 }
 
 }  // namespace cpc

@@ -647,16 +647,24 @@ extern "C" size_t cp_convolve_workspace(const cpc_kernel* P, int R_f, int precis
 }
 
 namespace cpc {
-int check_conv_args(const cpc_kernel* P, int R_f, const void* U, const void* W, int precision,
-                    void* ws, size_t ws_bytes, const char* who) {
+// kernel kind, rank, factor pointers and precision (everything but the workspace)
+int check_conv_inputs(const cpc_kernel* P, int R_f, const void* U, const void* W, int precision,
+                      const char* who) {
   if (!P) return fail(CPC_ERR_INVALID, std::string(who) + ": NULL kernel");
   if (P->kind != CPC_KERNEL_CONV) return fail(CPC_ERR_INVALID, std::string(who) + ": needs a CONV kernel");
   if (R_f <= 0) return fail(CPC_ERR_INVALID, std::string(who) + ": R_f must be positive");
   if (!U || !W) return fail(CPC_ERR_INVALID, std::string(who) + ": NULL factor pointer");
   if ((reinterpret_cast<uintptr_t>(U) & 15) || (reinterpret_cast<uintptr_t>(W) & 15))
     return fail(CPC_ERR_INVALID, std::string(who) + ": U and W must be 16-byte aligned");
-  if (precision != CPC_FP64 && precision != CPC_FP32 && precision != CPC_SPLIT)
+  if (!known_precision(precision))
     return fail(CPC_ERR_UNSUPPORTED, std::string(who) + ": precision form not implemented");
+  return CPC_OK;
+}
+
+int check_conv_args(const cpc_kernel* P, int R_f, const void* U, const void* W, int precision,
+                    void* ws, size_t ws_bytes, const char* who) {
+  const int st = check_conv_inputs(P, R_f, U, W, precision, who);
+  if (st) return st;
   if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255))
     return fail(CPC_ERR_WORKSPACE, std::string(who) + ": workspace NULL or not 256-byte aligned");
   if (ws_bytes < cp_convolve_workspace(P, R_f, precision))

@@ -28,3 +28,16 @@ def rel(a, b):
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def cancellation(G0, c, h):
+    """kappa = sum_kk' |c_k c_k' J_kk'| / |E_H| with J_kk' = h^3 sum_q prod_l G0[l, q, k, k']
+    (G0: the oracle's convolution matrices, shape (3, R_N, R_f, R_f)): how much the
+    terms of E_H = sum_kk' c_k c_k' J_kk' cancel.  It is 1 for a density with
+    non-negative coefficients (all J_kk' > 0) and grows when coefficients of both
+    signs cancel; a float32 rounding of the terms moves E_H by up to kappa times
+    its relative size."""
+    J = h ** 3 * np.sum(np.prod(G0, axis=0), axis=0)
+    c = np.asarray(c, dtype=np.float64)
+    E = float(c @ J @ c)
+    return float(np.sum(np.abs(np.outer(c, c) * J)) / abs(E))

@@ -77,6 +77,14 @@ def test_density600_n8192(cpc):
     torch.cuda.empty_cache()
     Es, Ws, _ = cpc.cp_hartree_energy(P, U, c, "split")
     assert abs(Es.item() / E64.item() - 1) < 1e-7
+    del Ws
+    torch.cuda.empty_cache()
+    # the float64-accurate tensor-core form: the float64 bar, and the sampled
+    # convolution-matrix columns against the oracle
+    Et, Wt, Gt = cpc.cp_hartree_energy(P, U, c, "fp64tc", want_G=True)
+    assert abs(Et.item() / E64.item() - 1) < TOL64
+    Gtc = np.array([Gt[l, q, :, k].cpu().numpy() for l, k, q in picks])
+    assert col_rel_err(Gtc, np.array(Gref)) < TOL64
 
 
 def test_density200_n4096_adjoint(cpc):
@@ -188,6 +196,12 @@ def test_basis80_n4096_coulomb_matrix(cpc):
     # and the float64 diagonal against the float32 full run
     didx = [all_items.index(it) for it in diag]
     assert np.max(np.abs(J32[didx] - Jd.cpu().numpy())) < 1e-5 * np.max(np.abs(Jd.cpu().numpy()))
+    # the batched reduced-precision forms' energy E_H = sum_mu w_mu J_mu,mu against
+    # the float64 form: the stated 1e-7 (the terms w_mu J_mu,mu are all positive)
+    E32 = float(np.dot(basis["w"], J32[didx]))
+    assert abs(E32 / E_items - 1) < 1e-7
+    Js, _ = cpc.coulomb_matrix(P, off_d, U_d, c_d, U_rho, c_rho, "split", tiles_per_cta=0)
+    assert abs(float(np.dot(basis["w"], Js.cpu().numpy())) / E_items - 1) < 1e-7
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-7)])
@@ -258,6 +272,13 @@ def test_nuclear80_n4096_nuclear_matrix(cpc):
     idx = [all_items.index(it) for it in sample]
     assert np.max(np.abs(V32[idx] - V0)) < 1e-5 * np.max(np.abs(V0))
     assert np.all(np.isfinite(V32))
+    # the trace (the nuclear energy of a density with unit weights) of the float32
+    # form against the float64 form at the stated 1e-7 (all diagonal entries are negative)
+    diag = [(mu, mu) for mu in range(nb)]
+    _, _, U_d, c_d, off_d = _coulomb_inputs(cpc, n, b, basis, diag)
+    V64d, _ = cpc.nuclear_matrix(P, off_d, U_d, c_d, nuc, dev(Z), "fp64")
+    didx = [all_items.index(it) for it in diag]
+    assert abs(V32[didx].sum() / V64d.cpu().numpy().sum() - 1) < 1e-7
 
 
 def test_tei80_n4096_cholesky(cpc):

@@ -2,7 +2,14 @@
 
 Bars: float64 forms within 1e-10 relative (per-column 2-norm for factor
 matrices, scalar relative for E_H and J, norm-wise for gradients); float32
-forms within the stated bounds below."""
+forms within the stated bounds below.
+
+The reduced-precision bound on E_H is 1e-7 of the absolute sum of its terms,
+sum_kk' |c_k c_k' J_kk'| = kappa |E_H| (see gpu_util.cancellation): float32
+roundings perturb the terms, which cancel in E_H when the coefficients of the
+density have both signs.  For kappa = 1 (a density with non-negative
+coefficients) it is 1e-7 relative; the cases below with kappa < 4 are held to
+1e-7 relative as well."""
 import math
 
 import numpy as np
@@ -13,11 +20,18 @@ import workloads
 from oracle import coulomb as ocoul
 from oracle import cp as ocp
 from oracle import lattice as olat
-from tests.gpu_util import col_rel_err, oracle_conv_kernel, oracle_master_kernel, rel
+from tests.gpu_util import cancellation, col_rel_err, oracle_conv_kernel, oracle_master_kernel, rel
 
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-10
+# reduced-precision forms: |dE_H| <= EH_TOL * kappa * |E_H|
+EH_TOL = 1e-7
+# the Parseval form (E_H from float32 spectra): its spectral terms also cancel
+# in each Gram entry (two Gaussians at different centres give oscillating
+# spectral products whose sum is small), which amplifies the float32
+# rounding of the spectra; measured up to 1.75e-7 kappa
+EH_TOL_SPECTRAL = 3e-7
 
 
 @pytest.fixture(scope="module")
@@ -105,8 +119,11 @@ def test_convolution_and_energy_fp32(cpc, name, spec):
     assert col_rel_err(W.cpu().numpy(), W0) < 2e-6
     G0 = ocp.conv_matrices(U0, W0, P0.shape[0])
     E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
-    # float32 form: float32 FFT and float32 products (stated bound 5e-7 on E_H)
-    assert abs(E.item() / E0 - 1) < 5e-7
+    kappa = cancellation(G0, g["c"], h)
+    # float32 form: compensated float32 FFT, tensor-core contraction exact on
+    # the float32 operands; these densities cancel little (kappa < 4)
+    assert kappa < 4
+    assert abs(E.item() / E0 - 1) < EH_TOL
     assert rel(G.cpu().numpy(), G0) < 2e-6
     # the convolve entry point gives the same factors; the explicit pipeline
     # (float32 spectra, half-angle step in float32) agrees to float32 rounding
@@ -118,8 +135,66 @@ def test_convolution_and_energy_fp32(cpc, name, spec):
     assert E3.item() == E.item()
     # energy from the spectra alone (Parseval), no V_H factors
     E2, G2 = cpc.cp_hartree_energy_from_spectra(P, spec, dev(g["c"]), want_G=True)
-    assert abs(E2.item() / E0 - 1) < 5e-7
+    assert abs(E2.item() / E0 - 1) < EH_TOL_SPECTRAL * kappa
     assert rel(G2.cpu().numpy(), G0) < 2e-6
+
+
+@pytest.mark.parametrize("name,spec", [CASES[0], CASES[2], CASES[3]])
+def test_convolution_and_energy_fp64tc(cpc, name, spec):
+    # float64 convolutions (the same V_H factors as CPC_FP64) and the
+    # tensor-core contraction of five exact bf16 slices per float64 operand:
+    # held to the float64 bar against the oracle
+    n, b, M, g = _case(name, spec)
+    h = 2 * b / n
+    P = cpc.make_newton_kernel(n, b, M)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    U = cpc.cp_sample_gaussians(n, b, dev(g["a"]), dev(g["X"]))
+    U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
+    E, W, G = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp64tc", want_G=True)
+    assert W.dtype == torch.float64
+    assert torch.equal(W, cpc.cp_convolve(P, U, "fp64"))
+    W0 = ocp.convolve_factors(U0, P0)
+    G0 = ocp.conv_matrices(U0, W0, P0.shape[0])
+    E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
+    assert abs(E.item() / E0 - 1) < TOL64
+    assert rel(G.cpu().numpy(), G0) < TOL64
+    # without G requested the matrices go to the workspace: same energy
+    E2, _, _ = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp64tc")
+    assert E2.item() == E.item()
+    # the float64 adjoint takes these G and W
+    dU, dc = cpc.cp_hartree_energy_adjoint(P, dev(g["c"]), W, G, "fp64tc")
+    dU0, dc0 = ocp.hartree_energy_adjoint(U0, g["c"], P0, h)
+    assert rel(dU.cpu().numpy(), dU0) < TOL64 and rel(dc.cpu().numpy(), dc0) < TOL64
+
+
+def test_fp64tc_rejected_where_not_implemented(cpc):
+    P = cpc.make_newton_kernel(64, 5.0, 6)  # n not a multiple of 128
+    g = workloads.gaussian_mixture(3, 0.5, 5.0, 3, centre_half=1.0)
+    U = cpc.cp_sample_gaussians(64, 5.0, dev(g["a"]), dev(g["X"]))
+    with pytest.raises(cpc.CpcError, match="multiple of 128"):
+        cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp64tc")
+
+
+@pytest.mark.parametrize("R_f", [129, 300, 400, 520])
+def test_fp64tc_tensor_core_block_tilings(cpc, R_f):
+    # the float64 tensor-core form on the same ragged symmetric tilings
+    n, b, M = 256, 6.0, 8
+    h = 2 * b / n
+    g = workloads.gaussian_mixture(R_f, 0.3, 30.0, 5, centre_half=1.0)
+    P = cpc.make_newton_kernel(n, b, M)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    U = cpc.cp_sample_gaussians(n, b, dev(g["a"]), dev(g["X"]))
+    U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
+    E, W, G = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp64tc", want_G=True)
+    W0 = ocp.convolve_factors(U0, P0)
+    G0 = ocp.conv_matrices(U0, W0, P0.shape[0])
+    E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
+    # E_H of these densities cancels strongly (kappa 13..260): the bound is
+    # taken relative to the sum of |terms|, as for the float32 form
+    assert abs(E.item() / E0 - 1) < TOL64 * cancellation(G0, g["c"], h)
+    Gh = G.cpu().numpy()
+    assert rel(Gh, G0) < TOL64
+    assert np.array_equal(Gh, np.swapaxes(Gh, 2, 3))
 
 
 @pytest.mark.parametrize("R_f", [129, 300, 400, 520])
@@ -138,7 +213,10 @@ def test_fp32_tensor_core_block_tilings(cpc, R_f):
     W0 = ocp.convolve_factors(U0, P0)
     G0 = ocp.conv_matrices(U0, W0, P0.shape[0])
     E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
-    assert abs(E.item() / E0 - 1) < 5e-7
+    # random-sign coefficients of up to 520 Gaussians cancel strongly here
+    # (kappa 13..260), so the bound is taken relative to the sum of |terms|
+    kappa = cancellation(G0, g["c"], h)
+    assert abs(E.item() / E0 - 1) < EH_TOL * kappa
     Gh = G.cpu().numpy()
     assert rel(Gh, G0) < 2e-6
     assert np.array_equal(Gh, np.swapaxes(Gh, 2, 3))
@@ -159,7 +237,7 @@ def test_convolution_and_energy_split(cpc, name, spec):
     assert col_rel_err(W.cpu().numpy(), W0) < TOL64
     G0 = ocp.conv_matrices(U0, W0, P0.shape[0])
     E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
-    assert abs(E.item() / E0 - 1) < 1e-7
+    assert abs(E.item() / E0 - 1) < EH_TOL * max(1.0, cancellation(G0, g["c"], h))
     assert rel(G.cpu().numpy(), G0) < 1e-6
     dU, dc = cpc.cp_hartree_energy_adjoint(P, dev(g["c"]), W, G, "split")
     dU0, dc0 = ocp.hartree_energy_adjoint(U0, g["c"], P0, h)
@@ -281,8 +359,24 @@ def test_coulomb_schedules_agree_and_tuner_caches(cpc, tmp_path, monkeypatch):
     cache = json.loads((tmp_path / "tune.json").read_text())
     (entry,) = cache.values()
     assert entry["tiles_per_cta"] in (4, 8, 16, 32, 64, 128) and entry["ms"] > 0
+    assert sorted(int(k) for k in entry["candidates_ms"]) == [4, 8, 16, 32, 64, 128]
     with pytest.raises(cpc.CpcError):
         cpc.coulomb_matrix(P, dev(off, torch.int32), U_it, c_it, U_rho, c_rho, "fp64", tiles_per_cta=6)
+    # the tensor-core form (float32, n a multiple of 128): every raster group
+    # gives the same J bit for bit (fixed-order reductions), and the tuner
+    # times all six candidates and caches them
+    U_rho32, c_rho32 = U_rho, c_rho
+    J32 = [cpc.coulomb_matrix(P, dev(off, torch.int32), U_it, c_it, U_rho32, c_rho32, "fp32",
+                              tiles_per_cta=r)[0].cpu().numpy() for r in (1, 2, 8, 32)]
+    for Jr in J32[1:]:
+        assert np.array_equal(Jr, J32[0])
+    assert np.max(np.abs(J32[0] - ref)) < 1e-5 * np.max(np.abs(ref))
+    Jt, _ = cpc.coulomb_matrix(P, dev(off, torch.int32), U_it, c_it, U_rho32, c_rho32, "fp32")  # tunes, caches
+    assert np.array_equal(Jt.cpu().numpy(), J32[0])
+    cache = json.loads((tmp_path / "tune.json").read_text())
+    (e32,) = [v for k, v in cache.items() if k.endswith("|fp32")]
+    assert sorted(int(k) for k in e32["candidates_ms"]) == [1, 2, 4, 8, 16, 32]
+    assert e32["tiles_per_cta"] in (1, 2, 4, 8, 16, 32) and all(t > 0 for t in e32["candidates_ms"].values())
 
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("split", 1e-6)])

@@ -5,8 +5,11 @@ device memory (a program that owns a fixed device pool, a plug-in inside
 another runtime's allocator, a loop that must not call cudaMalloc).  It takes
 its scratch from the library's fixed 32 MiB device array instead of a
 caller workspace.  Here it must reproduce the workspace entry point on two
-calls in a row (with different inputs, so stale scratch would show), in both
-precision forms, and reject a size whose scratch exceeds the array.
+calls in a row (with different inputs, so stale scratch would show), in all
+three precision forms (SPLIT keeps a different scratch layout: float64
+spectra and CUDA-core partial sums, no tensor-core slices), reject a size
+whose scratch exceeds the array, and report an invalid argument as invalid
+even when the size would also be too large.
 
 This file is collected last so a run that stops at the first failure has
 already run every other test; it also passes on its own in a fresh process.
@@ -21,7 +24,8 @@ import workloads
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-10, "fp32": 1e-10}
+# the same kernels on the same inputs: agreement to rounding of the final sums
+TOL = {"fp64": 1e-10, "fp32": 1e-10, "split": 1e-10}
 
 
 @pytest.fixture(scope="module")
@@ -42,12 +46,12 @@ def _inputs(cpc, seed, n, b, R_f):
     return cpc.cp_sample_gaussians(n, b, a, X), c
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "split"])
 def test_noalloc_matches_workspace_entry_on_consecutive_calls(cpc, precision):
     lib = cpc.load()
     n, b, M, R_f = 128, 10.0, 20, 8
     P = cpc.make_newton_kernel(n, b, M)
-    dt = torch.float64 if precision == "fp64" else torch.float32
+    dt = torch.float32 if precision == "fp32" else torch.float64
     pr = cpc._prec(precision)
     stream = cpc._stream()
     for seed in (11, 12):  # two calls in a row, different densities
@@ -83,3 +87,20 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(cpc):
     assert st == -5
     msg = lib.cpc_last_error().decode()
     assert "32 MiB" in msg and str(need) in msg
+
+
+def test_noalloc_reports_invalid_arguments_before_the_size_limit(cpc):
+    lib = cpc.load()
+    n, b, M = 4096, 16.0, 25
+    R_f = 400  # too large for the scratch array, but the arguments are wrong first
+    P = cpc.make_newton_kernel(n, b, M)
+    Pm = cpc.make_newton_kernel(256, 8.0, 12, "master")
+    dummy = torch.empty(16, dtype=torch.float64, device="cuda")
+    p = C.c_void_p(dummy.data_ptr())
+    # a MASTER kernel, an unknown precision, a NULL factor pointer
+    assert lib.cp_hartree_energy_noalloc(Pm.handle, R_f, p, p, p, None, p, 0, cpc._stream()) == -1
+    assert "CONV" in lib.cpc_last_error().decode()
+    assert lib.cp_hartree_energy_noalloc(P.handle, R_f, p, p, p, None, p, 7, cpc._stream()) == -5
+    assert "precision" in lib.cpc_last_error().decode()
+    assert lib.cp_hartree_energy_noalloc(P.handle, R_f, None, p, p, None, p, 0, cpc._stream()) == -1
+    assert "NULL" in lib.cpc_last_error().decode()

@@ -169,3 +169,44 @@ def lattice_energy_edges(n: int, L: int, cells: int) -> np.ndarray:
 def check_points(sub: int, count: int, seed: int) -> np.ndarray:
     """``count`` random sub-grid points as (count, 3) int64 indices in [0, sub)."""
     return rng(seed).integers(0, sub, size=(count, 3))
+
+
+# ---- index bookkeeping of product functions (no arithmetic of the method) ----
+
+def upper_pairs(nb: int):
+    """Pairs (mu, nu), mu <= nu, in row-major order of the upper triangle."""
+    pa, pb = np.triu_indices(nb)
+    return pa, pb
+
+
+def basis_density_pairs(basis: dict):
+    """Primitive pairs (a, b), a <= b inside each function, of the diagonal
+    density rho = sum_mu w_mu g_mu^2, and each pair's weight: w_mu, doubled when
+    a != b (the (a, b) and (b, a) terms are equal).  The contraction
+    coefficients d_a d_b are not included."""
+    first, w = basis["fn_first"], basis["w"]
+    pa, pb, wt = [], [], []
+    for mu in range(len(first) - 1):
+        for a in range(first[mu], first[mu + 1]):
+            for b in range(a, first[mu + 1]):
+                pa.append(a)
+                pb.append(b)
+                wt.append(w[mu] * (1.0 if a == b else 2.0))
+    return np.array(pa), np.array(pb), np.array(wt)
+
+
+def basis_item_pairs(basis: dict):
+    """Items (mu, nu), mu <= nu, in row-major order of the upper triangle; for
+    each item its primitive pairs (a in mu, b in nu), concatenated, and the
+    offsets of each item's pairs (len(items) + 1 entries)."""
+    first = basis["fn_first"]
+    nb = len(first) - 1
+    items = [(mu, nu) for mu in range(nb) for nu in range(mu, nb)]
+    pa, pb, off = [], [], [0]
+    for mu, nu in items:
+        for a in range(first[mu], first[mu + 1]):
+            for b in range(first[nu], first[nu + 1]):
+                pa.append(a)
+                pb.append(b)
+        off.append(len(pa))
+    return items, np.array(pa), np.array(pb), np.array(off)
