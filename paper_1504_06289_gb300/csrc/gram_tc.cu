@@ -8,26 +8,34 @@
 // Exact slicing (error-free splitting of the operands into low-precision
 // slices, Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 2012).  Every
 // operand row x (a column of U or of the V_H factors) is written as
-//   x = 2^(e-8) * sum_k t_k,  t_k = s_k 2^(-8k),  2^e > max|x| over the row,
-// with integer digits |s_0| <= 256, |s_k| <= 128 (k >= 1), each t_k exact in
-// bf16.  A product of two rows is 2^(e_r + e_s - 16) sum_{a,b} sum_i t_a t_b.
-//   * float32 form (NS = 3 slices of the float32 operands, 24 bits): the
-//     pairs a + b <= 2 (6 products per cell); the dropped ones lie below
-//     float32 rounding of the operands.
-//   * CPC_FP64_TC (NS = 5 slices of the float64 operands, 40 bits): the pairs
-//     a + b <= 4 (15 products per cell); the dropped ones lie below 2^-40 of
-//     the row scales.
-// Three TMEM accumulators per output: S_0 = sum t_0 t_0' and S_1 = sum (t_0 t_1'
-// + t_1 t_0') are integer multiples of 1 and 2^-8 of magnitude at most 2^24
-// units over 256 cells, so the bf16 MMAs accumulate them exactly whatever
-// the tensor core's rounding; S_2 collects every pair with a + b >= 2 (weight
-// 2^-16 and below), where an accumulation step can round by 2^-24 of S_2,
-// i.e. below 2^-38 of the entry's scale 2^(e_r+e_s).  (The float32 form keeps
-// its slices as the integers s_k and applies the weights 2^-8, 2^-16 at
-// readout; the float64 form stores the weighted t_k, so that its 12 products
-// with a + b >= 2 all land in S_2.)  Every 256 cells the accumulators are
-// folded into a compensated float32 sum (TwoSum, float32 form) or a float64
-// sum (CPC_FP64_TC) per entry.
+//   x = 2^(e-8) * sum_k t_k,  t_k = s_k 2^(-8k),
+// with integer digits s_k, each t_k exact in bf16.  A product of two rows is
+// 2^(e_r + e_s - 16) sum_{a,b} sum_i t_a t_b.
+//   * float32 form (NS = 3 slices of the float32 operands): U rows with
+//     2^e > max|x|, |s_0| <= 256, |s_1|, |s_2| <= 128 (24 bits, error <=
+//     2^-24 max|x|); W rows with balanced digits, 2^e > 2 max|x| and
+//     |s_k| <= 128 for every k (23 bits, error <= 2^-23 max|x|, below the
+//     float32 FFT's own error).  The pairs a + b <= 2 (6 products per cell);
+//     the dropped ones lie below float32 rounding of the operands.  Three
+//     TMEM accumulators per output: S_0 = sum s_0 s_0' (<= 2^15 per cell) is
+//     an integer of magnitude at most 2^24 over 512 cells, exact in the bf16
+//     MMAs whatever the tensor core's rounding; S_1 = sum (s_0 s_1' + s_1 s_0')
+//     (<= 1.5 x 2^15 per cell, its digits being rounding remainders of both
+//     signs) stays below 2^24 unless nearly every cell carries maximal digits
+//     of one sign, and otherwise rounds by at most one unit (weight 2^-8) per
+//     step: 2^-26 of the entry scale after the 64 steps of 512 cells; S_2
+//     (a + b = 2, weight 2^-16) rounds by at most two units per step, 2^-39 of
+//     the entry scale.  The weights 2^-8, 2^-16 are applied at readout, every
+//     512 cells, into a compensated float32 sum (TwoSum) per entry.
+//   * CPC_FP64_TC (NS = 5 slices of the float64 operands): 2^e > max|x|,
+//     |s_0| <= 256, |s_k| <= 128 (40 bits of the row maximum); the pairs
+//     a + b <= 4 (15 products per cell), the dropped ones below 2^-40 of the
+//     row scales.  The slices are stored weighted (t_k), so each product
+//     carries its weight; four accumulators per output: S_0 and S_1 exact over
+//     256 cells as above (<= 2^16 and 1.5 x 2^15 per cell), S_2 (a + b = 2,
+//     at most 5 x 2^22 units of 2^-16: one unit of rounding per step, 2^-40 of
+//     the entry scale) and S_3 (a + b = 3, 4; weight <= 2^-24); folded into a
+//     float64 sum per entry every 256 cells.
 //
 // Tiles: a CTA pair (2-CTA cluster, cta_group::2) computes 256 rows of U (M)
 // x 128 rows of W (N) for one kernel term; each CTA streams its 128 U rows and
@@ -35,7 +43,7 @@
 // chunks, 64-byte swizzle for the 32-cell chunks of CPC_FP64_TC; completion
 // counted on an mbarrier) through 3 shared-memory stages, and one thread of
 // the even CTA issues the MMAs for both.  Sixteen warps per CTA read the
-// accumulators after every 256 cells.  Float32 form: the three axes run as
+// accumulators after every 512 (float32 form) or 256 cells.  Float32 form: the three axes run as
 // one stream of chunks and the running product over axes stays in TMEM.
 // CPC_FP64_TC: the readers write the float64 convolution matrices G, and
 // E_H is reduced from them by a separate kernel.
@@ -45,6 +53,7 @@
 
 #include <cstdint>
 #include <mutex>
+#include <string>
 #include <type_traits>
 
 #include "cpc_internal.h"
@@ -61,8 +70,6 @@ static_assert(BN == 128, "TMEM: 4 accumulators or 3 + the product over axes, 128
 constexpr int READERS = 16;  // accumulator reader warps: lane quadrant x column quarter
 constexpr int BNW = BN / 4;  // columns read by one reader warp
 constexpr int THREADS = (READERS + 1) * 32;  // + one TMA/MMA warp
-constexpr int STAGES = 3;
-constexpr int EXACT_CELLS = 256;     // cells per exact TMEM accumulation (S_0, S_1 within 2^24)
 constexpr uint32_t TMEM_COLS = 512;  // 3 groups x 128 columns, then the product over axes
 constexpr uint32_t PROD_COL = 3 * BN;
 // per-column exponents (3 axes) and coefficients; rows mode: the 4 column quarters of each row
@@ -72,20 +79,31 @@ constexpr long kSpinLimit = 20000000;
 
 // Shapes of one form: NS slices per operand, BKC cells per chunk (one
 // swizzled shared-memory row of BKC bf16: 128 or 64 bytes).
-template <int NS_, int BKC_, int NACC_>
+template <int NS_, int BKC_, int NACC_, int STAGES_, bool BAL_>
 struct Form {
   static constexpr int NS = NS_, BKC = BKC_;
   static constexpr int NACC = NACC_;        // TMEM accumulators of BN columns per output tile
+  static constexpr int STAGES = STAGES_;    // shared-memory stages of one chunk each
+  static constexpr bool BAL = BAL_;         // balanced digits of W (the B operand): 2^e > 2 max|x|, |s_0| <= 128
+  // cells per TMEM accumulation (S_0 exact, S_1 within 2^24 but for extreme data)
+  static constexpr int EXACT_CELLS = BAL ? 512 : 256;
   static constexpr uint32_t ROW = BKC * 2;  // bytes per operand row of a chunk
   static constexpr int K_STEPS = BKC / 16;  // MMAs of K = 16 per slice pair and chunk
   static constexpr uint32_t A_SLICE_BYTES = BM * ROW, B_SLICE_BYTES = BNH * ROW;
   static constexpr uint32_t STAGE_BYTES = NS * (A_SLICE_BYTES + B_SLICE_BYTES);
   static constexpr int GROUP = EXACT_CELLS / BKC;  // chunks per TMEM accumulation
-  static constexpr size_t SMEM = size_t(STAGES) * STAGE_BYTES + 1024 + 256 + kColBytes + kRowBytes;
+  static constexpr size_t SMEM = size_t(STAGES_) * STAGE_BYTES + 1024 + 256 + kColBytes + kRowBytes;
   static_assert(SMEM <= 232448, "shared memory of one CTA");
+  static_assert((2 * STAGES + 3) * 8 <= 256, "barriers fit before the column data");
 };
-using Form32 = Form<3, 64, 3>;  // float32 form: 72 KB stages, S_0..S_2 + the product over axes
-using Form64 = Form<5, 32, 4>;  // CPC_FP64_TC: 60 KB stages, S_0..S_3 (no product over axes)
+// float32 form: 3 stages of 64-cell chunks (72 KB), S_0..S_2 + the product over
+// axes, balanced digits of W (readout every 512 cells; 12% faster than every
+// 256 cells at density600_n8192).  (6 stages of 32-cell
+// chunks, 36 KB, measured 32% slower at density600_n8192 and 30% slower in
+// the Coulomb rows mode.)
+using Form32 = Form<3, 64, 3, 3, true>;
+// CPC_FP64_TC: 3 stages of 32-cell chunks (60 KB), S_0..S_3 (no product over axes)
+using Form64 = Form<5, 32, 4, 3, false>;
 
 // K-major operand descriptor for 128- or 64-byte swizzled rows (8-row atoms)
 template <uint32_t ROW>
@@ -100,24 +118,24 @@ __device__ __forceinline__ uint64_t desc_k(uint32_t saddr) {
   return d;
 }
 
-// x -> NS slices with one exponent per row (2^e > max|x| over the row): one
-// CTA of 256 threads per row, the row read once into registers (n / 256
-// values per thread, rounded up).  Float32 form (NS = 3): the digits s_k of
-// the row rounded to float32, stored as integers.  CPC_FP64_TC (NS = 5): the
-// digits of the float64 row, stored weighted, t_k = s_k 2^(-8k).
+// Float32 form: x -> 3 slices with one exponent per row: one CTA of 256
+// threads per row (several CTAs per SM keep rows in flight across each CTA's
+// row barrier; one 1024-thread CTA per SM measured 2x slower), the row read
+// once into registers (n / 256 values per thread, rounded up), rounded to
+// float32, then its digits s_k stored as integers; BAL:
+// balanced digits (2^e > 2 max|x|, the W operand), else 2^e > max|x| (U).
 //
 // Source rows are (l, s, q) of a [3][R_f][R_N][n] array (R_N = 1 for U).
 // Slices are written chunk-blocked, so that the rows of one operand tile
 // (64 consecutive s, one BKC-cell chunk) are one contiguous block:
 //   out[k][G = l*R_N + q][t][s][i % BKC],  t = i / BKC,  k = slice.
-template <typename TS, int VPT, class F>
-__global__ void __launch_bounds__(256) slice_rows_kernel(const TS* __restrict__ src, long long rows, int n, int R_f,
+template <typename TS, int VPT, class F, int TPB, bool BAL>
+__global__ void __launch_bounds__(TPB) slice_rows_kernel(const TS* __restrict__ src, long long rows, int n, int R_f,
                                                          int R_N, __nv_bfloat16* __restrict__ out,
                                                          long long slice_stride, int* __restrict__ expo) {
   constexpr int NS = F::NS, BKC = F::BKC;
-  constexpr bool WEIGHTED = NS > 3;
-  using V = typename std::conditional<WEIGHTED, double, float>::type;
-  __shared__ V red[8];
+  static_assert(NS == 3, "float32 form: three slices");
+  __shared__ float red[TPB / 32];
   const int T = n / BKC;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
     const TS* x = src + row * n;
@@ -126,34 +144,40 @@ __global__ void __launch_bounds__(256) slice_rows_kernel(const TS* __restrict__ 
     const int rem = (int)(row - l * per_l);
     const int srow = rem / R_N, q = rem - srow * R_N;
     __nv_bfloat16* ob = out + ((long long)(l * R_N + q) * T * R_f + srow) * BKC;
-    V v[VPT];
-    V m = V(0);
+    float v[VPT];
+    float m = 0.0f;
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
-      const int i = (k * 256 + threadIdx.x);  // coalesced
-      v[k] = (i < n) ? V(x[i]) : V(0);
-      m = fmax(m, fabs(v[k]));
+      const int i = (k * TPB + threadIdx.x);  // coalesced
+      v[k] = (i < n) ? float(x[i]) : 0.0f;
+      m = fmaxf(m, fabsf(v[k]));
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
-    V mm = red[0];
+    float mm = red[0];
 #pragma unroll
-    for (int w = 1; w < 8; ++w) mm = fmax(mm, red[w]);
+    for (int w = 1; w < TPB / 32; ++w) mm = fmaxf(mm, red[w]);
     int e = 0;
-    if (mm > V(0)) frexp(mm, &e);  // mm = f 2^e, f in [0.5, 1): |x| < 2^e
+    if (mm > 0.0f) {
+      frexpf(mm, &e);  // mm = f 2^e, f in [0.5, 1): |x| < 2^e
+      if (BAL) e += 1;  // balanced digits: |x| < 2^(e-1)
+    }
     if (threadIdx.x == 0) expo[row] = e;
+    // 2^(8-e) as two exact multiplies by normal powers of two (as the convolution's epilogue)
+    const int k1 = (8 - e) / 2, k2 = (8 - e) - k1;
+    const float sc1 = __int_as_float((127 + k1) << 23), sc2 = __int_as_float((127 + k2) << 23);
 #pragma unroll
     for (int k = 0; k < VPT; ++k) {
-      const int i = k * 256 + threadIdx.x;
+      const int i = k * TPB + threadIdx.x;
       if (i >= n) continue;
-      V a = ldexp(v[k], 8 - e);  // |a| < 256
       __nv_bfloat16* o = ob + (long long)(i / BKC) * R_f * BKC + (i % BKC);
+      float a = (v[k] * sc1) * sc2;  // |a| < 256 (balanced: 128)
 #pragma unroll
       for (int j = 0; j < NS; ++j) {
-        const V d = rint(a);   // digit s_j: |s_0| <= 256, |s_j| <= 128
-        a = (a - d) * V(256);  // exact
-        o[j * slice_stride] = __float2bfloat16_rn(float(WEIGHTED ? ldexp(d, -8 * j) : d));
+        const float d = rintf(a);  // digit s_j: |s_0| <= 256 (balanced: 128), |s_j| <= 128
+        a = (a - d) * 256.0f;      // exact
+        o[j * slice_stride] = __float2bfloat16_rn(d);
       }
     }
     __syncthreads();  // red[] reused by the next row
@@ -233,15 +257,12 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
 __device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
 }
-
-// chunk tt of the stream (axis tt / T, cells (tt % T) * BKC ..) into stage tt % STAGES
-// of this CTA; completion is counted on the even CTA's barrier (cluster address)
 template <class F>
 __device__ __forceinline__ void issue_stage(const CUtensorMap* mapA, const CUtensorMap* mapB, const Args& g,
                                             uint32_t sbase, uint32_t fullbar_cluster, int tt, int T, int q, int r0,
                                             int sb0) {
   const int l = tt / T, t = tt % T;
-  const uint32_t stage = sbase + (tt % STAGES) * F::STAGE_BYTES;
+  const uint32_t stage = sbase + (tt % F::STAGES) * F::STAGE_BYTES;
   // all slices of each operand tile in one copy: A dims (cell, r, t, l, slice),
   // B dims (cell, s, t, l*R_N + q, slice); rows past R_f read as zeros
   tma_load_5d(stage, mapA, r0, t, l, fullbar_cluster);
@@ -294,33 +315,39 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, v
 // (each CTA's TMEM receives its 128 rows x 128 columns).  In each CTA, warps
 // 0-15 read the accumulators (warp w: TMEM lanes 32 (w % 4).., columns
 // 32 (w / 4)..), warp 16 drives the copies.  GROUP consecutive chunks (256
-// cells) accumulate before each readout (S_0 and S_1 stay exact).
+// or 512 cells) accumulate before each readout (S_0 and S_1 stay exact).
 // Barriers: full[stage] (even CTA: both halves landed), sfree[stage] (both
 // CTAs: the MMAs reading a stage finished), done (both CTAs: a group of
 // chunks accumulated), freeb (even CTA: the 32 reader warps of the pair
 // took the accumulators out of TMEM).
 // GOUT (CPC_FP64_TC): the readers fold in float64 and write G (both
 // triangles); there is no product over axes and no E_H or row sum here.
+// register cap: each of the SM's four sub-partitions holds 16K registers and
+// a block's warps are spread over them, so the 17 warps put 5 on one: at most
+// 16384 / (5 x 32) = 102 registers per thread, 96 in steps of 8 (104 and 120
+// did not launch); with the cap ptxas spills 40-108 bytes instead of the
+// 144-168 bytes it chose under __launch_bounds__(544, 1)
 template <class F, bool GOUT>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+__global__ void __cluster_dims__(2, 1, 1) __maxnreg__(96)
 gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Args g) {
   static_assert(GOUT ? F::NACC == 4 : F::NACC == 3, "TMEM columns: accumulators (+ product over axes)");
   constexpr int GROUP = F::GROUP;
+  constexpr int NT = THREADS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   const uint32_t raw = umma::smem_u32(smem_raw);
   const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
   uint8_t* smem = smem_raw + pad;
   const uint32_t sbase = raw + pad;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * F::STAGE_BYTES);  // [STAGES]
-  uint64_t* sfree = full + STAGES;                                                // [STAGES]
-  uint64_t* done = sfree + STAGES;                                                // [1]
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + F::STAGES * F::STAGE_BYTES);  // [F::STAGES]
+  uint64_t* sfree = full + F::STAGES;                                                // [F::STAGES]
+  uint64_t* done = sfree + F::STAGES;                                                // [1]
   uint64_t* freeb = done + 1;                                                     // [1]
   uint32_t* tmem_ptr = reinterpret_cast<uint32_t*>(freeb + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_ptr + 1);
-  double* col_c = reinterpret_cast<double*>(smem + STAGES * F::STAGE_BYTES + 256);  // [BN]
+  double* col_c = reinterpret_cast<double*>(smem + F::STAGES * F::STAGE_BYTES + 256);  // [BN]
   int* col_e = reinterpret_cast<int*>(col_c + BN);                                 // [3][BN]
   double* row_q = reinterpret_cast<double*>(col_e + 3 * BN);                       // [4][BM]
-  __shared__ double red[THREADS / 32];
+  __shared__ double red[NT / 32];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t rank = umma::cluster_ctarank();
@@ -349,14 +376,14 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const int s0 = ct * BN, sb0 = s0 + int(rank) * BNH;
   const bool diag = !g.rows_mode && r0 == s0;  // a diagonal block: only r <= s counts
   // the tile's column coefficients and row exponents of W, once
-  for (int i = tid; i < 4 * BN; i += THREADS) {
+  for (int i = tid; i < 4 * BN; i += NT) {
     const int j = i % BN, s = s0 + j;
     if (i < BN) col_c[j] = (s < g.Ns && g.c_col) ? g.c_col[s] : 0.0;
     else col_e[i - BN] = (s < g.Ns) ? g.eB[((long long)(i / BN - 1) * g.Ns + s) * g.R_N + q] : 0;
   }
   if (warp == 0) umma::tmem_alloc_pair(tmem_ptr, TMEM_COLS);
   if (tid == 32) {
-    for (int i = 0; i < STAGES; ++i) {
+    for (int i = 0; i < F::STAGES; ++i) {
       umma::mbar_init(&full[i], 1);
       umma::mbar_init(&sfree[i], 1);
     }
@@ -379,43 +406,43 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 
   if (warp == READERS) {
     if (lane == 0) {
-      auto fullc = [&](int tt) { return umma::mapa(umma::smem_u32(&full[tt % STAGES]), 0); };
+      // both CTAs' copies count on the even CTA's full barrier, which expects both halves
+      auto load = [&](int tt) {
+        if (rank == 0) mbar_expect_tx(umma::smem_u32(&full[tt % F::STAGES]), 2 * F::STAGE_BYTES);
+        issue_stage<F>(&mapA, &mapB, g, sbase, umma::mapa(umma::smem_u32(&full[tt % F::STAGES]), 0), tt, T, q,
+                       r0, sb0);
+      };
       if (rank == 0) {
-        for (int tt = 0; tt < STAGES - 1 && tt < TT; ++tt) {
-          mbar_expect_tx(umma::smem_u32(&full[tt]), 2 * F::STAGE_BYTES);
-          issue_stage<F>(&mapA, &mapB, g, sbase, fullc(tt), tt, T, q, r0, sb0);
-        }
+        for (int tt = 0; tt < F::STAGES - 1 && tt < TT; ++tt) load(tt);
         for (int tt = 0; tt < TT; ++tt) {
           const int t = tt % T, gi = (tt / T) * GA + t / GROUP;  // group of this chunk
           const bool first = (t % GROUP == 0), last = (t % GROUP == GROUP - 1) || (t == T - 1);
-          if (!wait_or_abort(&full[tt % STAGES], (tt / STAGES) & 1, abort_flag)) break;
+          if (!wait_or_abort(&full[tt % F::STAGES], (tt / F::STAGES) & 1, abort_flag)) break;
           if (first && gi >= 1 && !wait_or_abort(freeb, (gi - 1) & 1, abort_flag)) break;
           umma::fence_after();
-          issue_mmas<F>(sbase + (tt % STAGES) * F::STAGE_BYTES, tbase, first ? 0u : 1u);
-          umma::mma_commit_pair(&sfree[tt % STAGES]);
+          issue_mmas<F>(sbase + (tt % F::STAGES) * F::STAGE_BYTES, tbase, first ? 0u : 1u);
+          umma::mma_commit_pair(&sfree[tt % F::STAGES]);
           if (last) umma::mma_commit_pair(done);
-          const int tn = tt + STAGES - 1;
+          const int tn = tt + F::STAGES - 1;
           if (tn < TT) {
-            // stage tn % STAGES last held chunk tt - 1: wait until its MMAs finished
-            if (tt >= 1 && !wait_or_abort(&sfree[(tt - 1) % STAGES], ((tt - 1) / STAGES) & 1, abort_flag)) break;
-            mbar_expect_tx(umma::smem_u32(&full[tn % STAGES]), 2 * F::STAGE_BYTES);
-            issue_stage<F>(&mapA, &mapB, g, sbase, fullc(tn), tn, T, q, r0, sb0);
+            // stage tn % F::STAGES last held chunk tt - 1: wait until its MMAs finished
+            if (tt >= 1 && !wait_or_abort(&sfree[(tt - 1) % F::STAGES], ((tt - 1) / F::STAGES) & 1, abort_flag)) break;
+            load(tn);
           }
         }
       } else {
-        for (int tt = 0; tt < STAGES - 1 && tt < TT; ++tt)
-          issue_stage<F>(&mapA, &mapB, g, sbase, fullc(tt), tt, T, q, r0, sb0);
-        for (int tt = 0; tt + STAGES - 1 < TT; ++tt) {
-          const int tn = tt + STAGES - 1;
-          if (tt >= 1 && !wait_or_abort(&sfree[(tt - 1) % STAGES], ((tt - 1) / STAGES) & 1, abort_flag)) break;
-          issue_stage<F>(&mapA, &mapB, g, sbase, fullc(tn), tn, T, q, r0, sb0);
+        for (int tt = 0; tt < F::STAGES - 1 && tt < TT; ++tt) load(tt);
+        for (int tt = 0; tt + F::STAGES - 1 < TT; ++tt) {
+          const int tn = tt + F::STAGES - 1;
+          if (tt >= 1 && !wait_or_abort(&sfree[(tt - 1) % F::STAGES], ((tt - 1) / F::STAGES) & 1, abort_flag)) break;
+          load(tn);
         }
       }
       // drain: every commit of the pair has arrived on this CTA's stage barriers
       // before the CTA can leave
       if (!*abort_flag)
-        for (int tt = (TT > STAGES ? TT - STAGES : 0); tt < TT; ++tt)
-          if (!wait_or_abort(&sfree[tt % STAGES], (tt / STAGES) & 1, abort_flag)) break;
+        for (int tt = (TT > F::STAGES ? TT - F::STAGES : 0); tt < TT; ++tt)
+          if (!wait_or_abort(&sfree[tt % F::STAGES], (tt / F::STAGES) & 1, abort_flag)) break;
     }
   } else {
     const int quad = warp & 3, part = warp >> 2;
@@ -553,7 +580,7 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     if (tid == 0 && *abort_flag) atomicExch(g.status, 1);
   } else if (tid == 0) {
     double s = 0.0;
-    for (int w = 0; w < THREADS / 32; ++w) s += red[w];
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
     g.partial[(size_t)q * gridDim.x + blockIdx.x] = s;
     if (*abort_flag) atomicExch(g.status, 1);
   }
@@ -564,24 +591,123 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   }
 }
 
-template <typename TS, class F>
+// BAL: balanced digits (the W operand of the float32 form)
+template <typename TS, class F, bool BAL>
 int launch_slice(const TS* src, long long rows, int n, int R_f, int R_N, __nv_bfloat16* out, long long slice_stride,
                  int* expo, cudaStream_t s) {
   const unsigned grid = (unsigned)std::min<long long>(rows, 1 << 20);
   const int slot = timing_begin("slice_rows_kernel", s);
-  switch ((n + 255) / 256) {
-    case 1: slice_rows_kernel<TS, 1, F><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
-    case 2: slice_rows_kernel<TS, 2, F><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
-    case 4: slice_rows_kernel<TS, 4, F><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
-    case 8: slice_rows_kernel<TS, 8, F><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
-    case 16: slice_rows_kernel<TS, 16, F><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
-    case 32: slice_rows_kernel<TS, 32, F><<<grid, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo); break;
+#define CPC_SLICE(VPT, TPB) \
+  slice_rows_kernel<TS, VPT, F, TPB, BAL><<<grid, TPB, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo)
+  switch (n) {
+    case 128: CPC_SLICE(1, 256); break;
+    case 256: CPC_SLICE(1, 256); break;
+    case 512: CPC_SLICE(2, 256); break;
+    case 1024: CPC_SLICE(4, 256); break;
+    case 2048: CPC_SLICE(8, 256); break;
+    case 4096: CPC_SLICE(16, 256); break;
+    case 8192: CPC_SLICE(32, 256); break;
     default:
       timing_end(slot, s);
-      return fail(CPC_ERR_UNSUPPORTED, "tensor-core contraction: n must be a power of two up to 8192");
+      return fail(CPC_ERR_UNSUPPORTED, "tensor-core contraction: n must be a power of two in [128, 8192]");
   }
+#undef CPC_SLICE
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("slice_rows_kernel");
+  return CPC_OK;
+}
+
+// CPC_FP64_TC slicing in two streaming passes (the per-row reduction and the
+// digits in one kernel left a CTA per row waiting on its loads).
+// Pass 1: expo[row] = e with 2^e > max|x| over the row (frexp convention),
+// from the largest biased exponent field of the row's float64 values
+// (0 for a row of zeros or subnormals); 256 threads per row, rows grid-strided.
+__global__ void __launch_bounds__(256) row_exponent64_kernel(const double* __restrict__ src, long long rows, int n,
+                                                             int* __restrict__ expo) {
+  __shared__ int red[8];
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    const double2* x = reinterpret_cast<const double2*>(src + row * n);
+    int m = 0;
+    for (int i = threadIdx.x; i < n / 2; i += 256) {
+      const double2 v = x[i];
+      m = max(m, max(int((__double_as_longlong(v.x) >> 52) & 0x7FF), int((__double_as_longlong(v.y) >> 52) & 0x7FF)));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int mm = red[0];
+      for (int w = 1; w < 8; ++w) mm = max(mm, red[w]);
+      expo[row] = mm ? mm - 1022 : 0;
+    }
+    __syncthreads();
+  }
+}
+
+// Pass 2: the five weighted digits t_k = s_k 2^(-8k) of each float64 value,
+// by integer arithmetic on its bit pattern (the float64 pipe of this GPU is
+// slow): A = |x| 2^(40-e) rounded to an integer (half up; |x 2^(40-e) - A|
+// <= 1/2, i.e. 2^-41 of 2^e), split into balanced base-256 digits s_4..s_1 in
+// [-128, 127] and the leading s_0 in [0, 256], all with the sign of x (values
+// below the float64 normal range count as zero).  Two neighbouring cells per
+// thread (one 4-byte store per slice), elements grid-strided over all rows;
+// the output layout is slice_rows_kernel's.
+template <int BKC>
+__global__ void __launch_bounds__(256) slice64_kernel(const double* __restrict__ src, long long rows, int n, int R_f,
+                                                      int R_N, __nv_bfloat16* __restrict__ out, long long slice_stride,
+                                                      const int* __restrict__ expo) {
+  constexpr int NS = 5;
+  const int T = n / BKC;
+  const long long pairs = rows * (n / 2);
+  for (long long p = blockIdx.x * 256LL + threadIdx.x; p < pairs; p += gridDim.x * 256LL) {
+    const long long i2 = 2 * p;
+    const long long row = i2 / n;
+    const int i = int(i2 - row * n);  // even cell index
+    const long long per_l = (long long)R_f * R_N;
+    const int l = (int)(row / per_l);
+    const int rem = (int)(row - l * per_l);
+    const int srow = rem / R_N, q = rem - srow * R_N;
+    const int e = expo[row];
+    const double2 v = *reinterpret_cast<const double2*>(src + i2);
+    float t[2][NS];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(h ? v.y : v.x));
+      const int ex = int((bits >> 52) & 0x7FF);
+      const int sh = 1035 + e - ex;
+      long long A = 0;
+      if (ex != 0 && sh < 64) {
+        const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+        A = (long long)((mant + (1ull << (sh - 1))) >> sh);
+      }
+      const float sgn = (bits >> 63) ? -1.0f : 1.0f;
+      const unsigned long long B = (unsigned long long)A + 0x80808080ull;
+      const unsigned lo = (unsigned)B;
+      t[h][0] = sgn * float(int(B >> 32));
+#pragma unroll
+      for (int j = 1; j < NS; ++j)
+        t[h][j] = sgn * float(int((lo >> (8 * (NS - 1 - j))) & 255u) - 128) * __int_as_float((127 - 8 * j) << 23);
+    }
+    __nv_bfloat16* o = out + ((long long)(l * R_N + q) * T * R_f + srow) * BKC + (long long)(i / BKC) * R_f * BKC +
+                       (i % BKC);
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(t[0][j], t[1][j]);
+      *reinterpret_cast<__nv_bfloat162*>(o + j * slice_stride) = b2;
+    }
+  }
+}
+
+int launch_slice64(const double* src, long long rows, int n, int R_f, int R_N, __nv_bfloat16* out,
+                   long long slice_stride, int* expo, cudaStream_t s) {
+  const int slot = timing_begin("slice_rows_kernel", s);
+  const unsigned g1 = (unsigned)std::min<long long>(rows, 152LL * 8 * 4);
+  row_exponent64_kernel<<<g1, 256, 0, s>>>(src, rows, n, expo);
+  const long long pairs = rows * (n / 2);
+  const unsigned g2 = (unsigned)std::min<long long>((pairs + 255) / 256, 152LL * 8 * 16);
+  slice64_kernel<Form64::BKC><<<g2, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("slice64_kernel");
   return CPC_OK;
 }
 
@@ -616,22 +742,22 @@ bool tc_supported(const cpc_kernel* P) { return P->n >= 128 && P->n % 128 == 0; 
 
 namespace {
 // workspace of the tensor-core contraction of M A rows against Ns R_N W rows:
-// A slices, W slices, row exponents of A and W, status word (each 256-aligned);
-// CPC_FP64_TC also holds the float64 convolution matrices G
+// A slices, row exponents of A and W, status word, (CPC_FP64_TC: the float64
+// convolution matrices G,) then the W slices (each 256-aligned)
 struct TcLayout {
   size_t a, b;  // slice elements of A and W (all slices, 3 axes)
-  size_t off_b, off_ea, off_eb, off_status, off_g, total;
+  size_t off_ea, off_eb, off_status, off_g, off_b, total;
 };
 TcLayout tc_layout(const cpc_kernel* P, int M, int Ns, int ns = 3, bool with_g = false) {
   TcLayout L;
   L.a = size_t(ns) * 3 * M * P->n;
   L.b = size_t(ns) * 3 * size_t(Ns) * P->R_N * P->n;
-  L.off_b = align256(2 * L.a);
-  L.off_ea = L.off_b + align256(2 * L.b);
+  L.off_ea = align256(2 * L.a);
   L.off_eb = L.off_ea + align256(4 * size_t(3) * M);
   L.off_status = L.off_eb + align256(4 * size_t(3) * Ns * P->R_N);
   L.off_g = L.off_status + 256;
-  L.total = L.off_g + (with_g ? align256(sizeof(double) * 3 * size_t(P->R_N) * M * M) : 0);
+  L.off_b = L.off_g + (with_g ? align256(sizeof(double) * 3 * size_t(P->R_N) * M * M) : 0);
+  L.total = L.off_b + align256(2 * L.b);
   return L;
 }
 }  // namespace
@@ -726,6 +852,15 @@ int launch_tc_kernel(const cpc_kernel* P, int M, int Ns, const TcLayout& L, unsi
   tc::Args args{eA, eB, M, Ns, R_N, n, rows_mode, c, c_col, partial, G, status, std::max(1, std::min(raster, n_rp))};
   auto kern = tc::gemm3_tc_kernel<F, GOUT>;
   CPC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(F::SMEM)));
+  {
+    // the block must fit the register file at this kernel's register count
+    cudaFuncAttributes fa;
+    CPC_CUDA(cudaFuncGetAttributes(&fa, kern));
+    if (fa.maxThreadsPerBlock < tc::THREADS)
+      return fail(CPC_ERR_CUDA, "gemm3_tc_kernel: " + std::to_string(fa.numRegs) + " registers per thread allow " +
+                                    std::to_string(fa.maxThreadsPerBlock) + " threads per block, the kernel needs " +
+                                    std::to_string(tc::THREADS));
+  }
   const int slot = timing_begin("gemm3_tc_kernel", s);
   kern<<<grid, tc::THREADS, F::SMEM, s>>>(mapA, mapB, args);
   timing_end(slot, s);
@@ -733,24 +868,30 @@ int launch_tc_kernel(const cpc_kernel* P, int M, int Ns, const TcLayout& L, unsi
   return CPC_OK;
 }
 
-// float32 form: slices (unless W is already sliced), tensor maps and the launch
-int launch_tc(const cpc_kernel* P, int M, int Ns, const double* U, const float* W, const double* c,
-              const double* c_col, double* G, double* partial, void* ws, cudaStream_t s, bool w_sliced,
-              int rows_mode, int raster = 1) {
+// float32 form: slices (unless the convolution already wrote W's), tensor maps and the launch
+template <class F>
+int launch_tc_form(const cpc_kernel* P, int M, int Ns, const double* U, const float* W, const double* c,
+                   const double* c_col, double* G, double* partial, void* ws, cudaStream_t s, bool w_sliced,
+                   int rows_mode, int raster) {
   const int n = P->n, R_N = P->R_N;
   const TcLayout L = tc_layout(P, M, Ns);
   unsigned char* w = static_cast<unsigned char*>(ws);
   CPC_CUDA(cudaMemsetAsync(w + L.off_status, 0, sizeof(int), s));
-  int st0 = tc::launch_slice<double, tc::Form32>(U, 3LL * M, n, M, 1, reinterpret_cast<__nv_bfloat16*>(w),
-                                                 (long long)(L.a / 3), reinterpret_cast<int*>(w + L.off_ea), s);
+  int st0 = tc::launch_slice<double, F, false>(U, 3LL * M, n, M, 1, reinterpret_cast<__nv_bfloat16*>(w),
+                                               (long long)(L.a / 3), reinterpret_cast<int*>(w + L.off_ea), s);
   if (st0) return st0;
-  if (!w_sliced) {  // else the convolution already wrote them (convolve_from_spectra_sliced)
-    st0 = tc::launch_slice<float, tc::Form32>(W, 3LL * Ns * R_N, n, Ns, R_N,
-                                              reinterpret_cast<__nv_bfloat16*>(w + L.off_b), (long long)(L.b / 3),
-                                              reinterpret_cast<int*>(w + L.off_eb), s);
+  if (!w_sliced) {  // else the convolution already wrote them (convolve_operands32_sliced)
+    st0 = tc::launch_slice<float, F, F::BAL>(W, 3LL * Ns * R_N, n, Ns, R_N,
+                                             reinterpret_cast<__nv_bfloat16*>(w + L.off_b), (long long)(L.b / 3),
+                                             reinterpret_cast<int*>(w + L.off_eb), s);
     if (st0) return st0;
   }
-  return launch_tc_kernel<tc::Form32, false>(P, M, Ns, L, w, c, c_col, G, partial, s, rows_mode, raster);
+  return launch_tc_kernel<F, false>(P, M, Ns, L, w, c, c_col, G, partial, s, rows_mode, raster);
+}
+int launch_tc(const cpc_kernel* P, int M, int Ns, const double* U, const float* W, const double* c,
+              const double* c_col, double* G, double* partial, void* ws, cudaStream_t s, bool w_sliced,
+              int rows_mode, int raster = 1) {
+  return launch_tc_form<tc::Form32>(P, M, Ns, U, W, c, c_col, G, partial, ws, s, w_sliced, rows_mode, raster);
 }
 }  // namespace
 
@@ -768,13 +909,11 @@ int launch_eh_tc64(const cpc_kernel* P, int R_f, const double* U, const double* 
   const TcLayout L = tc_layout(P, R_f, R_f, tc::Form64::NS, true);
   unsigned char* w = static_cast<unsigned char*>(ws);
   CPC_CUDA(cudaMemsetAsync(w + L.off_status, 0, sizeof(int), s));
-  int st = tc::launch_slice<double, tc::Form64>(U, 3LL * R_f, n, R_f, 1, reinterpret_cast<__nv_bfloat16*>(w),
-                                                (long long)(L.a / tc::Form64::NS),
-                                                reinterpret_cast<int*>(w + L.off_ea), s);
+  int st = tc::launch_slice64(U, 3LL * R_f, n, R_f, 1, reinterpret_cast<__nv_bfloat16*>(w),
+                              (long long)(L.a / tc::Form64::NS), reinterpret_cast<int*>(w + L.off_ea), s);
   if (st) return st;
-  st = tc::launch_slice<double, tc::Form64>(W, 3LL * R_f * R_N, n, R_f, R_N,
-                                            reinterpret_cast<__nv_bfloat16*>(w + L.off_b),
-                                            (long long)(L.b / tc::Form64::NS), reinterpret_cast<int*>(w + L.off_eb), s);
+  st = tc::launch_slice64(W, 3LL * R_f * R_N, n, R_f, R_N, reinterpret_cast<__nv_bfloat16*>(w + L.off_b),
+                          (long long)(L.b / tc::Form64::NS), reinterpret_cast<int*>(w + L.off_eb), s);
   if (st) return st;
   double* Gd = G ? G : reinterpret_cast<double*>(w + L.off_g);
   st = launch_tc_kernel<tc::Form64, true>(P, R_f, R_f, L, w, c, c, Gd, partial, s, 0, 1);

@@ -259,21 +259,30 @@ __device__ __forceinline__ void slice_epilogue(const float2* v, const SliceOut& 
     __syncthreads();  // red[] is reused by the next item
   }
   if (!active) return;
+  // balanced digits of the float32 form's W operand: 2^e > 2 max|x|
   int e = 0;
-  if (m > 0.0f) frexpf(m, &e);
+  if (m > 0.0f) {
+    frexpf(m, &e);
+    e += 1;
+  }
   if (t == 0) so.expo[item] = e;
   const long long col = item / R_N;
   const int q = int(item - col * R_N);
   const int l = int(col / so.R_f), srow = int(col - (long long)l * so.R_f);
   constexpr int T = NC / 64;
   __nv_bfloat16* ob = so.out + ((long long)(l * R_N + q) * T * so.R_f + srow) * 64;
+  // 2^(8-e) as two normal powers of two (here e is in [-147, 129]):
+  // two exact multiplies per value instead of ldexpf (a value whose first
+  // product would fall below the normal range is below the last digit)
+  const int k1 = (8 - e) / 2, k2 = (8 - e) - k1;
+  const float sc1 = __int_as_float((127 + k1) << 23), sc2 = __int_as_float((127 + k2) << 23);
 #pragma unroll
   for (int r = 0; r < PL::P / 2; ++r) {
     const int i = 2 * (t + r * (NC / PL::P));  // even: the pair (i, i+1) stays in one 64-cell chunk
     float sl[3][2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const float a = ldexpf(h ? v[r].y : v[r].x, 8 - e);  // |a| < 256
+      const float a = ((h ? v[r].y : v[r].x) * sc1) * sc2;  // |a| < 128
       const float s0 = rintf(a);
       const float b = (a - s0) * 256.0f;  // exact
       const float s1 = rintf(b);
