@@ -394,7 +394,7 @@ def run_ours(args, ws, rank, local):
                     "ms": tc_ms64, "achieved_TFLOPs": gf / (tc_ms64 * 1e-3) / 1e12,
                     "frac_of_bf16_peak": gf / (tc_ms64 * 1e-3) / 1e12 / bf16_peak,
                     "slice_products_TFLOPs": 15 * gf / (tc_ms64 * 1e-3) / 1e12}
-                others[form]["slice_rows_ms"] = kto["slice_rows_kernel"][0]
+                others[form]["slice_ms_per_step"] = kto["slice_rows_kernel"][0] / args.fp64_steps
             del bf
             torch.cuda.empty_cache()
         E64 = others.get("fp64", {}).get("E_H", E_fast if prec == "fp64" else None)

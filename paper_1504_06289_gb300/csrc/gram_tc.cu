@@ -34,8 +34,8 @@
 //     carries its weight; four accumulators per output: S_0 and S_1 exact over
 //     256 cells as above (<= 2^16 and 1.5 x 2^15 per cell), S_2 (a + b = 2,
 //     at most 5 x 2^22 units of 2^-16: one unit of rounding per step, 2^-40 of
-//     the entry scale) and S_3 (a + b = 3, 4; weight <= 2^-24); folded into a
-//     float64 sum per entry every 256 cells.
+//     the entry scale) and S_3 (a + b = 3, 4; weight <= 2^-24); folded every
+//     256 cells into an unevaluated float pair per entry (TwoSum, ~48 bits).
 //
 // Tiles: a CTA pair (2-CTA cluster, cta_group::2) computes 256 rows of U (M)
 // x 128 rows of W (N) for one kernel term; each CTA streams its 128 U rows and
@@ -452,14 +452,17 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
     // float32 form: running sum of an axis as an unevaluated pair tot + lo
     // (TwoSum per fold); |lo| stays near 2^-24 |tot|, so lo is kept in bf16
     // (two per register): its own rounding is then below 2^-32 |tot|.
-    // CPC_FP64_TC: a float64 sum per entry (tot64).
-    float tot[GOUT ? 1 : BNW];
+    // CPC_FP64_TC: an unevaluated float pair hi + lo per entry (TwoSum of each
+    // of the four group sums into hi, the rounding errors summed in lo: about
+    // 48 bits, and float32 arithmetic; this GPU's float64 rate made a float64
+    // fold as slow as the MMAs it folds).
+    float tot[BNW];
     __nv_bfloat162 lo[GOUT ? 1 : BNW / 2];
-    double tot64[GOUT ? BNW : 1];
+    float lo32[GOUT ? BNW : 1];
 #pragma unroll
     for (int j = 0; j < BNW; ++j) {
-      if constexpr (GOUT) tot64[j] = 0.0;
-      else tot[j] = 0.0f;
+      tot[j] = 0.0f;
+      if constexpr (GOUT) lo32[j] = 0.0f;
     }
     if constexpr (!GOUT) {
 #pragma unroll
@@ -482,8 +485,18 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
         if constexpr (GOUT) {
           // weighted slices: the four sums already carry their weights
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            tot64[cb * 8 + j] += ((double(v0[j]) + double(v1[j])) + double(v2[j])) + double(v3[j]);
+          for (int j = 0; j < 8; ++j) {
+            float& t = tot[cb * 8 + j];
+            float e = 0.0f;
+            const float vs[4] = {v0[j], v1[j], v2[j], v3[j]};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float sm = t + vs[k], bb = sm - t;
+              e += (t - (sm - bb)) + (vs[k] - bb);
+              t = sm;
+            }
+            lo32[cb * 8 + j] += e;
+          }
         } else {
 #pragma unroll
           for (int j = 0; j < 8; j += 2) {
@@ -514,8 +527,9 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
           for (int j = 0; j < BNW; ++j) {
             const int s = sh0 + j;
             const int es = col_e[l * BN + part * BNW + j];
-            const double Gv = ldexp(tot64[j], er + es - 16);
-            tot64[j] = 0.0;
+            const double Gv = ldexp(double(tot[j]) + double(lo32[j]), er + es - 16);
+            tot[j] = 0.0f;
+            lo32[j] = 0.0f;
             if (r < g.M && s < g.Ns && (!diag || r <= s)) {
               double* Gq = g.G + ((size_t)l * gridDim.y + q) * (size_t)g.M * g.M;
               Gq[(size_t)r * g.M + s] = Gv;
@@ -649,51 +663,51 @@ __global__ void __launch_bounds__(256) row_exponent64_kernel(const double* __res
 // slow): A = |x| 2^(40-e) rounded to an integer (half up; |x 2^(40-e) - A|
 // <= 1/2, i.e. 2^-41 of 2^e), split into balanced base-256 digits s_4..s_1 in
 // [-128, 127] and the leading s_0 in [0, 256], all with the sign of x (values
-// below the float64 normal range count as zero).  Two neighbouring cells per
-// thread (one 4-byte store per slice), elements grid-strided over all rows;
-// the output layout is slice_rows_kernel's.
+// below the float64 normal range count as zero).  A block per row (rows
+// grid-strided, the row's place in the layout found once), two neighbouring
+// cells per thread and step (one 4-byte store per slice); the output layout
+// is slice_rows_kernel's.
 template <int BKC>
 __global__ void __launch_bounds__(256) slice64_kernel(const double* __restrict__ src, long long rows, int n, int R_f,
                                                       int R_N, __nv_bfloat16* __restrict__ out, long long slice_stride,
                                                       const int* __restrict__ expo) {
   constexpr int NS = 5;
   const int T = n / BKC;
-  const long long pairs = rows * (n / 2);
-  for (long long p = blockIdx.x * 256LL + threadIdx.x; p < pairs; p += gridDim.x * 256LL) {
-    const long long i2 = 2 * p;
-    const long long row = i2 / n;
-    const int i = int(i2 - row * n);  // even cell index
+  for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+    // the row's place in the chunk-blocked layout, once per row
     const long long per_l = (long long)R_f * R_N;
     const int l = (int)(row / per_l);
     const int rem = (int)(row - l * per_l);
     const int srow = rem / R_N, q = rem - srow * R_N;
     const int e = expo[row];
-    const double2 v = *reinterpret_cast<const double2*>(src + i2);
-    float t[2][NS];
+    const double2* x = reinterpret_cast<const double2*>(src + row * n);
+    __nv_bfloat16* ob = out + ((long long)(l * R_N + q) * T * R_f + srow) * BKC;
+    for (int p = threadIdx.x; p < n / 2; p += 256) {
+      const int i = 2 * p;  // even cell: the pair stays in one chunk
+      const double2 v = x[p];
+      float t[2][NS];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(h ? v.y : v.x));
-      const int ex = int((bits >> 52) & 0x7FF);
-      const int sh = 1035 + e - ex;
-      long long A = 0;
-      if (ex != 0 && sh < 64) {
-        const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-        A = (long long)((mant + (1ull << (sh - 1))) >> sh);
+      for (int h = 0; h < 2; ++h) {
+        const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(h ? v.y : v.x));
+        const int ex = int((bits >> 52) & 0x7FF);
+        const int sh = 1035 + e - ex;
+        long long A = 0;
+        if (ex != 0 && sh < 64) {
+          const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+          A = (long long)((mant + (1ull << (sh - 1))) >> sh);
+        }
+        const float sgn = (bits >> 63) ? -1.0f : 1.0f;
+        const unsigned long long B = (unsigned long long)A + 0x80808080ull;
+        const unsigned lo = (unsigned)B;
+        t[h][0] = sgn * float(int(B >> 32));
+#pragma unroll
+        for (int j = 1; j < NS; ++j)
+          t[h][j] = sgn * float(int((lo >> (8 * (NS - 1 - j))) & 255u) - 128) * __int_as_float((127 - 8 * j) << 23);
       }
-      const float sgn = (bits >> 63) ? -1.0f : 1.0f;
-      const unsigned long long B = (unsigned long long)A + 0x80808080ull;
-      const unsigned lo = (unsigned)B;
-      t[h][0] = sgn * float(int(B >> 32));
+      __nv_bfloat16* o = ob + (i / BKC) * (long long)R_f * BKC + (i % BKC);
 #pragma unroll
-      for (int j = 1; j < NS; ++j)
-        t[h][j] = sgn * float(int((lo >> (8 * (NS - 1 - j))) & 255u) - 128) * __int_as_float((127 - 8 * j) << 23);
-    }
-    __nv_bfloat16* o = out + ((long long)(l * R_N + q) * T * R_f + srow) * BKC + (long long)(i / BKC) * R_f * BKC +
-                       (i % BKC);
-#pragma unroll
-    for (int j = 0; j < NS; ++j) {
-      const __nv_bfloat162 b2 = __floats2bfloat162_rn(t[0][j], t[1][j]);
-      *reinterpret_cast<__nv_bfloat162*>(o + j * slice_stride) = b2;
+      for (int j = 0; j < NS; ++j)
+        *reinterpret_cast<__nv_bfloat162*>(o + j * slice_stride) = __floats2bfloat162_rn(t[0][j], t[1][j]);
     }
   }
 }
@@ -703,8 +717,7 @@ int launch_slice64(const double* src, long long rows, int n, int R_f, int R_N, _
   const int slot = timing_begin("slice_rows_kernel", s);
   const unsigned g1 = (unsigned)std::min<long long>(rows, 152LL * 8 * 4);
   row_exponent64_kernel<<<g1, 256, 0, s>>>(src, rows, n, expo);
-  const long long pairs = rows * (n / 2);
-  const unsigned g2 = (unsigned)std::min<long long>((pairs + 255) / 256, 152LL * 8 * 16);
+  const unsigned g2 = (unsigned)std::min<long long>(rows, 152LL * 8 * 4);
   slice64_kernel<Form64::BKC><<<g2, 256, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("slice64_kernel");
