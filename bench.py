@@ -31,6 +31,8 @@ sys.path.insert(0, ROOT)
 import workloads  # noqa: E402
 
 WORKLOAD = "density600_n8192"
+# kernels timed by the library's events in the density step
+TIMED = ("spectra_kernel", "conv_kernel", "band_conv_kernel", "slice_rows_kernel", "gemm3_tc_kernel")
 METRIC = "1D factor convolutions/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # GB300 unit counts for ALU roofs: 152 SMs, 128 FP32 lanes per SM (FMA = 2 flop)
@@ -54,6 +56,8 @@ def parse():
     ap.add_argument("--rf", type=int, default=None,
                     help="override the rank R_f (profiling a smaller case of the same kernels)")
     ap.add_argument("--cpu-sample", type=float, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--no-band", action="store_true",
+                    help="send every kernel term through the FFT (no banded direct sums), for comparison")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "basis80_n4096", "density200_n4096", "lattice32_n16384",
                              "lattice_energy256_n16384", "nuclear80_n4096", "tei80_n4096"],
@@ -272,6 +276,8 @@ def run_ours(args, ws, rank, local):
     n, b, M, R_f = cfg["n"], cfg["b"], cfg["M"], cfg["R_f"]
     P = cpc.make_newton_kernel(n, b, M, "conv", device=dev)
     R_N = P.R_N
+    if args.no_band:
+        P.set_banding(-1, -1)
     g = workloads.mixture_for(WORKLOAD, args.seed + rank)
     if args.rf:
         R_f = args.rf
@@ -326,13 +332,13 @@ def run_ours(args, ws, rank, local):
         cpc.kernel_timing(False)
         barrier(ws)
     ms_total = start.elapsed_time(stop)
-    kt = {k: cpc.kernel_timing_read(k)
-          for k in ("spectra_kernel", "conv_kernel", "slice_rows_kernel", "gemm3_tc_kernel")}
+    kt = {k: cpc.kernel_timing_read(k) for k in TIMED}
     ms_total = max_over_ranks(ms_total, ws, dev)
     E_fast = bufs[2].item()
     energy_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))  # the cp_hartree_energy call
     spec_ms = kt["spectra_kernel"][0] / max(1, kt["spectra_kernel"][1])
-    conv_ms = kt["conv_kernel"][0] / max(1, kt["conv_kernel"][1])
+    # the convolutions: FFT terms (conv_kernel) and banded terms (band_conv_kernel)
+    conv_ms = (kt["conv_kernel"][0] + kt["band_conv_kernel"][0]) / args.steps
     gram_ms = energy_ms - spec_ms - conv_ms  # slicing of U, contraction, final sum
     ms_step = ms_total / args.steps
     convs_per_step = 3 * R_f * R_N
@@ -376,13 +382,14 @@ def run_ours(args, ws, rank, local):
             torch.cuda.synchronize(dev)
             cpc.kernel_timing(False)
             mso = so.elapsed_time(to) / args.fp64_steps
-            kto = {k: cpc.kernel_timing_read(k)
-                   for k in ("spectra_kernel", "conv_kernel", "slice_rows_kernel", "gemm3_tc_kernel")}
+            kto = {k: cpc.kernel_timing_read(k) for k in TIMED}
             sp_o = kto["spectra_kernel"][0] / max(1, kto["spectra_kernel"][1])
-            cv_o = kto["conv_kernel"][0] / max(1, kto["conv_kernel"][1])
+            cv_o = (kto["conv_kernel"][0] + kto["band_conv_kernel"][0]) / args.fp64_steps
             en_o = float(np.mean([e[0].elapsed_time(e[1]) for e in eo]))
             others[form] = {"ms_per_step": mso, "value": convs_per_step / (mso * 1e-3),
                             "spectra_ms": sp_o, "conv_ms": cv_o, "contraction_ms": en_o - sp_o - cv_o,
+                            "conv_fft_ms": kto["conv_kernel"][0] / args.fp64_steps,
+                            "conv_band_ms": kto["band_conv_kernel"][0] / args.fp64_steps,
                             "E_H": bf[2].item()}
             if form == "fp64tc" and kto["gemm3_tc_kernel"][1]:
                 # the float64-accurate tensor-core contraction: 15 bf16 slice products
@@ -421,12 +428,17 @@ def run_ours(args, ws, rank, local):
 
     # convolution, the method's work: per convolution an n-point complex inverse
     # FFT (5 n log2 n flop) and the spectral product (6 n flop); bytes: the V_H
-    # factors written once plus the operand spectra and kernel pairs read once
+    # factors written once plus the operand spectra and kernel pairs read once.
+    # conv_kernel takes the n_fft wide terms; the banded terms are direct sums
+    # (band_conv_kernel): W written once and each factor column read once.
+    hw = P.banding(prec)
+    n_band = int((hw >= 0).sum())
+    n_fft = R_N - n_band
     conv_k_ms, _ = per_launch("conv_kernel", conv_ms)
-    conv_flops = convs_per_step * (5 * n * math.log2(n) + 6 * n)
+    conv_flops = 3 * R_f * n_fft * (5 * n * math.log2(n) + 6 * n)
     # (operands: 16 bytes per bin of each factor column, float4 (X1, X2) or double2;
     # kernel terms: 8 bytes per bin, float2 pairs or float64)
-    conv_bytes = 3 * R_f * R_N * n * elem + 3 * R_f * n * 16 + R_N * n * 8
+    conv_bytes = 3 * R_f * n_fft * n * elem + 3 * R_f * n * 16 + n_fft * n * 8
     conv_tf = conv_flops / (conv_k_ms * 1e-3) / 1e12
     conv_gbs = conv_bytes / (conv_k_ms * 1e-3) / 1e9
     kernels = {
@@ -434,13 +446,25 @@ def run_ours(args, ws, rank, local):
             "ms": conv_k_ms, "bound": "alu", "achieved": conv_tf, "unit": "TFLOP/s",
             "peak": alu32_peak_tf if prec == "fp32" else FP64_PEAK_GFLOPS / 1e3,
             "frac": conv_tf / (alu32_peak_tf if prec == "fp32" else FP64_PEAK_GFLOPS / 1e3),
-            "algorithmic_flops": conv_flops,
+            "algorithmic_flops": conv_flops, "terms": n_fft,
             "peak_note": ("float32 CUDA-core peak: 152 SMs x 128 lanes x 2 flop x median SM clock"
                           if prec == "fp32" else "nominal GB300 float64 rate"),
             "hbm": {"algorithmic_bytes": conv_bytes, "achieved_GBps": conv_gbs, "peak_GBps": hbm_peak,
                     "frac": conv_gbs / hbm_peak},
         },
     }
+    if n_band:
+        bd_ms, _ = per_launch("band_conv_kernel", 0.0)
+        # bytes: W of the banded terms written once, each factor column read once
+        bd_bytes = 3 * R_f * n_band * n * elem + 3 * R_f * n * 8
+        bd_taps = 3 * R_f * n * int(np.sum(2 * hw[hw >= 0] + 1))
+        kernels["band_conv_kernel"] = {
+            "ms": bd_ms, "bound": "hbm", "achieved": bd_bytes / (bd_ms * 1e-3) / 1e9, "unit": "GB/s",
+            "peak": hbm_peak, "frac": bd_bytes / (bd_ms * 1e-3) / 1e9 / hbm_peak, "algorithmic_bytes": bd_bytes,
+            "terms": n_band, "half_widths": [int(x) for x in hw[hw >= 0]],
+            "taps_multiply_adds": bd_taps,
+            "note": "direct sums over the band of the narrow kernel terms; float32 W: the bf16 slices "
+                    "(6 B per output) are written too and not counted"}
     # contraction, the method's work: the unique entries of the symmetric convolution
     # matrices (Sec. 3.2), 3 axes x R_N terms x R_f (R_f + 1) / 2 entries x n cells, 2 flop
     # per multiply-add; the fused product over axes and weighted sum are not counted
@@ -491,6 +515,7 @@ def run_ours(args, ws, rank, local):
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if not args.rf else f"{WORKLOAD} (R_f={R_f} profiling case)", "n": n, "box": [-b, b], "R_f": R_f, "R_N": R_N,
                    "convolutions_per_step": convs_per_step, "precision_form": prec,
+                   "terms_fft": n_fft, "terms_banded": n_band,
                    "l2": "each step writes the V_H factors (%.2f GB), far larger than L2" % (
                        3 * R_f * R_N * n * elem / 1e9)},
         "E_H": E_fast, "E_H_evals_per_s": ws * args.steps / (ms_total * 1e-3),
@@ -502,7 +527,7 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": ws * convs_per_step * e2e_steps / e2e_s, "unit": "convolutions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
         # sample, spectra, conv (+ W slices), [slice U,] contraction, final sum
-        "gpu_launches": {"fp32": 6, "fp64tc": 8}.get(prec, 5) * args.steps,
+        "gpu_launches": ({"fp32": 6, "fp64tc": 8}.get(prec, 5) + (1 if n_band else 0)) * args.steps,
         "clocks": clk,
     }
     if ws == 1 and not args.no_cpu_baseline:

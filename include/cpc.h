@@ -109,6 +109,24 @@ int cpc_kernel_tables(const cpc_kernel* P, double* t, double* a, double* p);
 /* Releases the kernel's device tables and the handle (NULL is a no-op). */
 int cpc_kernel_free(cpc_kernel* P);
 
+/* Banded direct convolution of the narrow kernel terms (Sec. 2.5, Eq. conv
+ * as a finite sum).  A CONV kernel with a large exponent t_q has a Galerkin
+ * vector p_q a few cells wide; for such a term cp_convolve (and every call
+ * that convolves U) forms W = p_q * U as the sum over |m| <= H_q,
+ * H_q the smallest half-width whose tail 2 sum_{m > H_q} |p_q[m]| is at most
+ * 2^-32 (float32 W) or 2^-60 (float64 W) of |p_q[0]| + 2 sum_{m>0} |p_q[m]|,
+ * rounded up to an instantiated width (0..8, 10..16 step 2, 20..32 step 4).
+ * Terms with H_q above the maximum of their W type go through the FFT.
+ * make_newton_kernel sets the maxima to 20 (float32 W) and 24 (float64 W).
+ * cpc_kernel_set_banding sets them (each in [-1, 32]; -1 sends every term
+ * through the FFT), rebuilds the device tables on `stream` and synchronises
+ * it; no call that uses P may run meanwhile.  cpc_kernel_banding writes H_q
+ * (or -1 for an FFT term) for the W type of `precision` into the host array
+ * half_width[R_N].  cp_convolve_from_spectra has no U and always takes the
+ * FFT for every term. */
+int cpc_kernel_set_banding(cpc_kernel* P, int max_half_width32, int max_half_width64, void* stream);
+int cpc_kernel_banding(const cpc_kernel* P, int precision, int* half_width);
+
 /* ---- a3: grid sampling of Gaussians (Sec. 3.1, Eq. disc_GTO) --------------
  * U[l][k][i] = exp(-a_k (x_i - X[k][l])^2) for R Gaussians exp(-a_k |x - X_k|^2).
  * a: [R], X: [R][3] (row k holds X_k), U: [3][R][n]; all float64 device. */
@@ -132,7 +150,9 @@ int cp_hadamard_pairs(int n, int n_in, int n_pairs, const int* pa, const int* pb
  * the factors of V_H = f * P_R.  U: [3][R_f][n] float64.  W: [3][R_f*R_N][n],
  * float64 for CPC_FP64 and CPC_SPLIT, float32 for CPC_FP32.  Implemented as length-2n real
  * FFT convolutions in the chosen precision (the spectra of U are formed in
- * float64).  Workspace: cp_convolve_workspace bytes. */
+ * float64), except for the narrow kernel terms, which are summed directly
+ * over their band (cpc_kernel_set_banding).  Workspace: cp_convolve_workspace
+ * bytes. */
 size_t cp_convolve_workspace(const cpc_kernel* P, int R_f, int precision);
 int cp_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision,
                 void* ws, size_t ws_bytes, void* stream);
@@ -156,8 +176,8 @@ int cp_convolve_from_spectra(const cpc_kernel* P, int R_f, const void* spec, voi
  * CPC_FP64.  CPC_FP32 (n a multiple of 128): on the tensor cores, each row
  * of U and of the float32 W split exactly into three bf16 integer slices under
  * a per-row power-of-two scale (the convolution writes W's slices in the same
- * pass as W), the slice products summed in TMEM over 256-cell chunks (the
- * two leading slice groups exactly)
+ * pass as W), the slice products summed in TMEM over 512-cell groups (all
+ * three slice groups exactly, W in balanced digits)
  * and folded into a compensated float32 sum per entry (at least as accurate
  * as float32 operands with float32 products); other n: float32 products on
  * CUDA cores.  CPC_SPLIT: float32

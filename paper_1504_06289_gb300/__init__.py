@@ -86,6 +86,19 @@ class NewtonKernel:
               "cpc_kernel_tables")
         return t, a, p
 
+    def set_banding(self, max_half_width32: int, max_half_width64: int, stream=None):
+        """Largest half-width of the kernel terms convolved by the banded direct
+        sum, per W type (-1: every term through the FFT)."""
+        with torch.cuda.device(self.device):
+            check(load().cpc_kernel_set_banding(self._h, int(max_half_width32), int(max_half_width64),
+                                                _stream(stream)), "cpc_kernel_set_banding")
+
+    def banding(self, precision: str = "fp32") -> np.ndarray:
+        """Half-width of each banded term for the W type of `precision` (-1: FFT)."""
+        hw = np.empty(self.R_N, dtype=np.int32)
+        check(load().cpc_kernel_banding(self._h, _prec(precision), hw.ctypes.data), "cpc_kernel_banding")
+        return hw
+
     def close(self):
         if self._h is not None:
             load().cpc_kernel_free(self._h)

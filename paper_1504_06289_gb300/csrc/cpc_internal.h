@@ -43,6 +43,19 @@ struct cpc_kernel {
   float2* d_hw32 = nullptr;
   // CONV only: Parseval weights d_q[2f+j] = w_f phat_q[f] / (2n), float32, [R_N][2(n+1)]
   float* d_specw32 = nullptr;
+  // CONV only: the banded direct convolution of narrow kernel terms
+  // (spectra.cu).  Per precision class (0: float32 W, 1: float64 W): the
+  // half-width used for each term (-1: the term goes through the FFT), the
+  // list of banded terms and the list of FFT terms.  d_band holds
+  // [class][3][R_N] ints in that order; the taps are p_q[0..kBandHalo]
+  // (float32 class: float2 (hi, lo), float64 class: double), zero beyond the
+  // term's half-width.
+  int band_max[2] = {-1, -1};  // largest half-width sent to the banded kernel
+  int n_band[2] = {0, 0};
+  std::vector<int> band_h[2];  // host copy of the half-widths
+  int* d_band = nullptr;
+  float2* d_taps32 = nullptr;
+  double* d_taps64 = nullptr;
   // MASTER kernels: scratch of the tensor-core sub-grid evaluation (the bf16
   // slices of the S3 rows, pre-swizzled per 64-point sub-tile, and their
   // exponents); calls on unordered streams sharing one kernel race on it
@@ -94,18 +107,30 @@ int compute_kernel_spectrum(cpc_kernel* P, cudaStream_t s);
 // spectra of U columns into workspace (float64 and/or float32 copies)
 int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uhat64,
                     float2* Uhat32, cudaStream_t s);
-// batched convolution from spectra
+// batched convolution from spectra.  U: the factor columns themselves
+// (float64 [ncols][n]) or NULL; with U, the kernel terms of the banded set
+// are convolved directly from U (band_conv_kernel) and the FFT takes the rest
 int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W,
-                          int precision, cudaStream_t s);
+                          int precision, cudaStream_t s, const double* U = nullptr);
 // float32 convolution operands (X1, X2) from float64 transforms of U, and the
 // convolutions from them (also writing the tensor-core contraction's W
-// slices and row exponents, n >= 128, in the _sliced form)
+// slices and row exponents, n >= 128, in the _sliced form); U as above
 int forward_operands32(const cpc_kernel* P, int ncols, const double* U, void* X, cudaStream_t s);
 size_t operands32_bytes(const cpc_kernel* P, int ncols);
-int convolve_operands32(const cpc_kernel* P, int ncols, const void* X, float* W, cudaStream_t s);
+int convolve_operands32(const cpc_kernel* P, int ncols, const void* X, float* W, cudaStream_t s,
+                        const double* U = nullptr);
 int convolve_operands32_sliced(const cpc_kernel* P, int R_f, const void* X, float* W, __nv_bfloat16* slices,
-                               long long slice_stride, int* expo, cudaStream_t s);
+                               long long slice_stride, int* expo, cudaStream_t s, const double* U = nullptr);
 int build_kernel_pairs(cpc_kernel* P, cudaStream_t s);
+// the banded terms of each precision class from the host tables (at most
+// max32 / max64 cells of half-width; a negative maximum bands nothing)
+int build_band_tables(cpc_kernel* P, int max32, int max64, cudaStream_t s);
+// default maxima: where the direct sum still costs less than the transform
+// per output (float32 W: about 1.5 instructions per tap against about 110
+// per output for the 8192-point float32 transform; float64 W: 2H + 1 float64
+// operations against about 60)
+constexpr int kDefaultBand32 = 20;
+constexpr int kDefaultBand64 = 24;
 
 // float32 contractions (gram32.cu)
 size_t eh32_partials(int R_f, int R_N);

@@ -555,7 +555,7 @@ int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doub
     long long sl_stride;
     int* ex;
     tc_w_slices(P, R_f, tws, &sl, &sl_stride, &ex);
-    st = convolve_operands32_sliced(P, R_f, X, static_cast<float*>(W), sl, sl_stride, ex, s);
+    st = convolve_operands32_sliced(P, R_f, X, static_cast<float*>(W), sl, sl_stride, ex, s, U);
     if (st) return st;
     double* partial = static_cast<double*>(cws);
     st = launch_eh_tc(P, R_f, U, static_cast<const float*>(W), c, G, partial, tws, s, true);
@@ -868,13 +868,6 @@ extern "C" int nuclear_matrix(const cpc_kernel* P, int n_items, const int* off, 
 }
 
 // ---- explicit spectra intermediates ------------------------------------------
-namespace cpc {
-int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uhat64, float2* Uhat32,
-                    cudaStream_t s);
-int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W, int precision,
-                          cudaStream_t s);
-}  // namespace cpc
-
 extern "C" int cp_factor_spectra(const cpc_kernel* P, int R_f, const double* U, void* spec, int precision,
                                  void* stream) {
   clear_error();

@@ -296,6 +296,8 @@ int make_newton_kernel(int n, double b, int M, int kind, void* stream, cpc_kerne
     if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: spectral weights"); cleanup(); return st; }
     st = build_spectral_weights(P, P->d_specw32, s);
     if (st != CPC_OK) { cleanup(); return st; }
+    st = build_band_tables(P, kDefaultBand32, kDefaultBand64, s);
+    if (st != CPC_OK) { cleanup(); return st; }
   }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: synchronize"); cleanup(); return st; }
@@ -324,6 +326,25 @@ int cpc_kernel_tables(const cpc_kernel* P, double* t, double* a, double* p) {
   return CPC_OK;
 }
 
+int cpc_kernel_set_banding(cpc_kernel* P, int max_half_width32, int max_half_width64, void* stream) {
+  clear_error();
+  if (!P) return fail(CPC_ERR_INVALID, "cpc_kernel_set_banding: NULL kernel");
+  if (P->kind != CPC_KERNEL_CONV) return fail(CPC_ERR_INVALID, "cpc_kernel_set_banding: needs a CONV kernel");
+  if (max_half_width32 < -1 || max_half_width32 > 32 || max_half_width64 < -1 || max_half_width64 > 32)
+    return fail(CPC_ERR_INVALID, "cpc_kernel_set_banding: half-widths must lie in [-1, 32]");
+  return build_band_tables(P, max_half_width32, max_half_width64, static_cast<cudaStream_t>(stream));
+}
+
+int cpc_kernel_banding(const cpc_kernel* P, int precision, int* half_width) {
+  clear_error();
+  if (!P || !half_width) return fail(CPC_ERR_INVALID, "cpc_kernel_banding: NULL argument");
+  if (!known_precision(precision)) return fail(CPC_ERR_UNSUPPORTED, "cpc_kernel_banding: unknown precision form");
+  const int cls = storage_precision(precision) == CPC_FP32 ? 0 : 1;
+  for (int q = 0; q < P->R_N; ++q)
+    half_width[q] = (P->kind == CPC_KERNEL_CONV && !P->band_h[cls].empty()) ? P->band_h[cls][q] : -1;
+  return CPC_OK;
+}
+
 int cpc_kernel_free(cpc_kernel* P) {
   if (!P) return CPC_OK;
   cudaFree(P->d_p);
@@ -339,6 +360,9 @@ int cpc_kernel_free(cpc_kernel* P) {
   cudaFree(P->d_hw64);
   cudaFree(P->d_hw32);
   cudaFree(P->d_specw32);
+  cudaFree(P->d_band);
+  cudaFree(P->d_taps32);
+  cudaFree(P->d_taps64);
   cudaFree(P->d_lat);
   delete P;
   return CPC_OK;

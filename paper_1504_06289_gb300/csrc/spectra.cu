@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 
 #include "cpc_internal.h"
@@ -234,6 +235,49 @@ struct SliceOut {
   int R_f;
 };
 
+// 2^(8-e) as two normal powers of two (here e is in [-147, 129]): two exact
+// multiplies per value instead of ldexpf (a value whose first product would
+// fall below the normal range is below the last digit)
+__device__ __forceinline__ void slice_scales(int e, float& sc1, float& sc2) {
+  const int k1 = (8 - e) / 2, k2 = (8 - e) - k1;
+  sc1 = __int_as_float((127 + k1) << 23);
+  sc2 = __int_as_float((127 + k2) << 23);
+}
+
+// the three balanced digits of the outputs x0, x1 (cells i, i+1 of one
+// 64-cell chunk) under the row scale, stored as bf16 pairs at o, o + stride,
+// o + 2 stride with streaming stores (evict first: the outputs must not push
+// the reused operands out of L2)
+__device__ __forceinline__ void slice_pair(float x0, float x1, float sc1, float sc2, __nv_bfloat16* o,
+                                           long long stride) {
+  float sl[3][2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float a = ((h ? x1 : x0) * sc1) * sc2;  // |a| < 128
+    const float s0 = rintf(a);
+    const float b = (a - s0) * 256.0f;  // exact
+    const float s1 = rintf(b);
+    sl[0][h] = s0;
+    sl[1][h] = s1;
+    sl[2][h] = rintf((b - s1) * 256.0f);
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const __nv_bfloat162 b2 = __floats2bfloat162_rn(sl[k][0], sl[k][1]);
+    __stcs(reinterpret_cast<unsigned int*>(o + k * stride), *reinterpret_cast<const unsigned int*>(&b2));
+  }
+}
+
+// balanced-digit row exponent of the float32 form's W operand: 2^e > 2 max|x|
+__device__ __forceinline__ int balanced_exponent(float m) {
+  int e = 0;
+  if (m > 0.0f) {
+    frexpf(m, &e);
+    e += 1;
+  }
+  return e;
+}
+
 // Row maximum over the TPF threads of one transform, then the three slices of
 // each of this thread's outputs (reals 2o, 2o+1, o = t + r NC/P, r < P/2).
 template <typename PL>
@@ -259,45 +303,19 @@ __device__ __forceinline__ void slice_epilogue(const float2* v, const SliceOut& 
     __syncthreads();  // red[] is reused by the next item
   }
   if (!active) return;
-  // balanced digits of the float32 form's W operand: 2^e > 2 max|x|
-  int e = 0;
-  if (m > 0.0f) {
-    frexpf(m, &e);
-    e += 1;
-  }
+  const int e = balanced_exponent(m);
   if (t == 0) so.expo[item] = e;
   const long long col = item / R_N;
   const int q = int(item - col * R_N);
   const int l = int(col / so.R_f), srow = int(col - (long long)l * so.R_f);
   constexpr int T = NC / 64;
   __nv_bfloat16* ob = so.out + ((long long)(l * R_N + q) * T * so.R_f + srow) * 64;
-  // 2^(8-e) as two normal powers of two (here e is in [-147, 129]):
-  // two exact multiplies per value instead of ldexpf (a value whose first
-  // product would fall below the normal range is below the last digit)
-  const int k1 = (8 - e) / 2, k2 = (8 - e) - k1;
-  const float sc1 = __int_as_float((127 + k1) << 23), sc2 = __int_as_float((127 + k2) << 23);
+  float sc1, sc2;
+  slice_scales(e, sc1, sc2);
 #pragma unroll
   for (int r = 0; r < PL::P / 2; ++r) {
     const int i = 2 * (t + r * (NC / PL::P));  // even: the pair (i, i+1) stays in one 64-cell chunk
-    float sl[3][2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const float a = ((h ? v[r].y : v[r].x) * sc1) * sc2;  // |a| < 128
-      const float s0 = rintf(a);
-      const float b = (a - s0) * 256.0f;  // exact
-      const float s1 = rintf(b);
-      sl[0][h] = s0;
-      sl[1][h] = s1;
-      sl[2][h] = rintf((b - s1) * 256.0f);
-    }
-    __nv_bfloat16* o = ob + (long long)(i >> 6) * so.R_f * 64 + (i & 63);
-    // streaming stores (evict first): the outputs must not push the reused
-    // operand spectra out of L2
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const __nv_bfloat162 b2 = __floats2bfloat162_rn(sl[k][0], sl[k][1]);
-      __stcs(reinterpret_cast<unsigned int*>(o + k * so.slice_stride), *reinterpret_cast<const unsigned int*>(&b2));
-    }
+    slice_pair(v[r].x, v[r].y, sc1, sc2, ob + (long long)(i >> 6) * so.R_f * 64 + (i & 63), so.slice_stride);
   }
 }
 
@@ -327,12 +345,15 @@ __device__ __forceinline__ float2 ld_keep2(const float2* a, uint64_t pol) {
 // spectra_kernel mode 2 (`Uhat` points at float4 [cols][n]) and `phat` at
 // the kernel-term pairs (p^[f], p^[n-f]) as float2 [R_N][n]; the packed
 // spectrum is then Z[f] = p^[f] X1[f] + p^[n-f] X2[f] (no half-angle step).
+// The kernel terms it convolves: qlist[0..n_q) (NULL: all R_N terms).  A
+// group is one term for `slots` consecutive columns, so every transform of a
+// CTA takes the same path and the same barriers.
 template <typename T, int LOGN, bool SLICE, bool XIN = false>
 __global__ void __launch_bounds__(Geometry<LOGN, T>::threads, Geometry<LOGN, T>::min_blocks)
 conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict__ phat,
             const typename cvec<T>::type* __restrict__ hw, const typename cvec<T>::type* __restrict__ tw,
             const __half2* __restrict__ hwl, const __half2* __restrict__ twl,
-            T* __restrict__ W, int R_N, long long n_items, SliceOut so) {
+            T* __restrict__ W, int R_N, int ncols, const int* __restrict__ qlist, int n_q, SliceOut so) {
   using V = typename cvec<T>::type;
   using G = Geometry<LOGN, T>;
   using PL = typename G::PL;
@@ -343,17 +364,19 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
   V* sbuf = reinterpret_cast<V*>(smem_raw) + slot * padded_len(NC);
   const T scale = T(1) / T(2 * NC);
   const uint64_t keep = l2_evict_last();  // operands are reused by the R_N kernel terms of a column
-  // contiguous group range per CTA: consecutive items share a factor column,
-  // so its spectrum stays in L1 across the kernel terms q
-  const long long n_groups = (n_items + G::slots - 1) / G::slots;
+  // contiguous group range per CTA: consecutive groups share the factor
+  // columns, so their spectra stay in L1 across the kernel terms q
+  const long long n_groups = (long long)((ncols + G::slots - 1) / G::slots) * n_q;
   const long long g_begin = n_groups * blockIdx.x / gridDim.x;
   const long long g_end = n_groups * (blockIdx.x + 1) / gridDim.x;
   for (long long g = g_begin; g < g_end; ++g) {
-    const long long item = g * G::slots + slot;
-    const bool active = item < n_items;
-    const long long it = active ? item : n_items - 1;
-    const long long col = it / R_N;
-    const int q = int(it - col * R_N);
+    const long long cb = g / n_q;
+    const int qi = int(g - cb * n_q);
+    const int q = qlist ? __ldg(qlist + qi) : qi;
+    const long long colr = cb * G::slots + slot;
+    const bool active = colr < ncols;
+    const long long col = active ? colr : ncols - 1;
+    const long long item = col * R_N + q;
     const V* Uc = Uhat + (size_t)col * (NC + 1);
     const T* pq = phat + (size_t)q * (NC + 1);
     {
@@ -407,6 +430,177 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// Banded direct convolution of the narrow kernel terms (Sec. 2.5, Eq. conv,
+// as the finite sum it is).  The Galerkin vector p_q of a term with a large
+// exponent t_q is a bell a few cells wide: beyond a half-width H_q its
+// entries add up to less than a set fraction of sum_m |p_q[|m|]| (2^-32 for
+// float32 W, 2^-60 for float64 W; build_band_tables picks H_q from the host
+// float64 tables), and
+//   W[i] = sum_{|m| <= H} p_q[|m|] U[i - m]      (U = 0 outside the grid)
+// costs about 2H + 1 multiply-adds per output instead of a length-2n
+// transform.  float32: each tap is a pair (hi, lo), lo the rounding error of
+// hi; the lo products are kept for |m| <= (H+1)/2 (the host widens H until
+// the taps beyond that add up to less than 2^-9 of the sum, so the dropped lo
+// products stay below 2^-33 of it), so the rounding of the taps leaves no
+// bias that would repeat across the columns of a term.  One CTA walks a
+// contiguous range of (column, term) items, stages each column once in
+// shared memory (rounded to T, as the FFT path rounds its input, inside a
+// zero border of kBandHalo cells) and writes W, and with SLICE the bf16
+// slices and row exponent with the same arithmetic as the FFT path.
+constexpr int kBandHalo = 32;          // largest half-width and the zero border
+constexpr int kBandTaps = kBandHalo + 1;
+constexpr int kBandThreads = 256;
+// the half-widths with a kernel instantiation (a term's H is rounded up to one)
+constexpr int kBandNumWidths = 17;
+__host__ __device__ constexpr int band_width(int k) {
+  return k < 9 ? k : (k < 13 ? 10 + 2 * (k - 9) : 20 + 4 * (k - 13));  // 0..8, 10..16, 20..32
+}
+static_assert(band_width(kBandNumWidths - 1) == kBandHalo, "the widest band fills the border");
+
+template <typename V>
+__device__ __forceinline__ decltype(V::x) win_el(const V* win, int d) {
+  return (d & 1) ? win[d >> 1].y : win[d >> 1].x;
+}
+
+// outputs i, i+1 for every even i = 2 threadIdx.x + 2 kBandThreads j < n;
+// returns this thread's largest |W| (SLICE)
+template <typename T, int H, bool SLICE>
+__device__ __forceinline__ float band_rows(const T* __restrict__ us, int n, const void* __restrict__ taps_q,
+                                           T* __restrict__ w, float* __restrict__ ws) {
+  using V = typename cvec<T>::type;
+  constexpr int H2 = (H + 1) & ~1;  // the window starts at an even cell
+  constexpr int HL = (H + 1) / 2;   // float32: taps with their lo part
+  T ph[H + 1];
+  float pl[HL + 1];
+  if constexpr (sizeof(T) == 4) {
+    const float2* tp = static_cast<const float2*>(taps_q);
+#pragma unroll
+    for (int m = 0; m <= H; ++m) {
+      const float2 v = __ldg(tp + m);
+      ph[m] = v.x;
+      if (m <= HL) pl[m] = v.y;
+    }
+  } else {
+    const double* tp = static_cast<const double*>(taps_q);
+#pragma unroll
+    for (int m = 0; m <= H; ++m) ph[m] = __ldg(tp + m);
+  }
+  float mx = 0.0f;
+  for (int i = 2 * threadIdx.x; i < n; i += 2 * kBandThreads) {
+    // cells i - H2 .. i + H2 + 1
+    const V* u2 = reinterpret_cast<const V*>(us + kBandHalo + i - H2);
+    V win[H2 + 1];
+#pragma unroll
+    for (int d = 0; d <= H2; ++d) win[d] = u2[d];
+    T a0 = T(0), a1 = T(0);
+    float l0 = 0.0f, l1 = 0.0f;
+    // smallest taps first
+#pragma unroll
+    for (int m = H; m >= 1; --m) {
+      const T s0 = win_el(win, H2 - m) + win_el(win, H2 + m);
+      const T s1 = win_el(win, H2 + 1 - m) + win_el(win, H2 + 1 + m);
+      if constexpr (sizeof(T) == 4) {
+        a0 = fmaf(ph[m], s0, a0);
+        a1 = fmaf(ph[m], s1, a1);
+        if (m <= HL) {
+          l0 = fmaf(pl[m], s0, l0);
+          l1 = fmaf(pl[m], s1, l1);
+        }
+      } else {
+        a0 = fma(ph[m], s0, a0);
+        a1 = fma(ph[m], s1, a1);
+      }
+    }
+    if constexpr (sizeof(T) == 4) {
+      a0 = fmaf(ph[0], win_el(win, H2), a0) + fmaf(pl[0], win_el(win, H2), l0);
+      a1 = fmaf(ph[0], win_el(win, H2 + 1), a1) + fmaf(pl[0], win_el(win, H2 + 1), l1);
+    } else {
+      a0 = fma(ph[0], win_el(win, H2), a0);
+      a1 = fma(ph[0], win_el(win, H2 + 1), a1);
+    }
+    __stcs(reinterpret_cast<V*>(w + i), cmk<V>(a0, a1));
+    if constexpr (SLICE) {
+      *reinterpret_cast<float2*>(ws + i) = make_float2(float(a0), float(a1));
+      mx = fmaxf(mx, fmaxf(fabsf(float(a0)), fabsf(float(a1))));
+    }
+  }
+  return mx;
+}
+
+template <typename T, bool SLICE, int K = 0>
+__device__ __forceinline__ float band_dispatch(int h, const T* us, int n, const void* tq, T* w, float* ws) {
+  if constexpr (K == kBandNumWidths - 1) {
+    return band_rows<T, band_width(K), SLICE>(us, n, tq, w, ws);  // the widest (and any unknown) width
+  } else {
+    if (h == band_width(K)) return band_rows<T, band_width(K), SLICE>(us, n, tq, w, ws);
+    return band_dispatch<T, SLICE, K + 1>(h, us, n, tq, w, ws);
+  }
+}
+
+// U: [ncols][n] float64 factor columns; items (col, j), j < n_band, term
+// qlist[j] with half-width hq[qlist[j]] (a value of band_width); taps:
+// [R_N][kBandTaps] (float32 W: float2, float64 W: double); W row col R_N + q.
+template <typename T, bool SLICE>
+__global__ void __launch_bounds__(kBandThreads, 2)
+band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const int* __restrict__ qlist, int n_band,
+                 const int* __restrict__ hq, const void* __restrict__ taps, T* __restrict__ W, SliceOut so) {
+  using V = typename cvec<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* us = reinterpret_cast<T*>(smem_raw);  // [kBandHalo + n + kBandHalo]
+  float* ws = reinterpret_cast<float*>(smem_raw + sizeof(T) * (size_t(n) + 2 * kBandHalo));  // SLICE: [n]
+  __shared__ float red[2][kBandThreads / 32];
+  for (int k = threadIdx.x; k < kBandHalo; k += kBandThreads) {
+    us[k] = T(0);
+    us[kBandHalo + n + k] = T(0);
+  }
+  const long long n_items = (long long)ncols * n_band;
+  const long long k0 = n_items * blockIdx.x / gridDim.x;
+  const long long k1 = n_items * (blockIdx.x + 1) / gridDim.x;
+  long long staged = -1;
+  int parity = 0;
+  for (long long k = k0; k < k1; ++k) {
+    const long long col = k / n_band;
+    const int q = __ldg(qlist + int(k - col * n_band));
+    if (col != staged) {
+      __syncthreads();  // every reader of the previous column is done
+      const double2* src = reinterpret_cast<const double2*>(U + (size_t)col * n);
+      for (int j = threadIdx.x; j < n / 2; j += kBandThreads) {
+        const double2 v = src[j];
+        *reinterpret_cast<V*>(us + kBandHalo + 2 * j) = cmk<V>(T(v.x), T(v.y));
+      }
+      staged = col;
+      __syncthreads();
+    }
+    const long long item = col * R_N + q;
+    const void* tq = (sizeof(T) == 4) ? static_cast<const void*>(static_cast<const float2*>(taps) + (size_t)q * kBandTaps)
+                                      : static_cast<const void*>(static_cast<const double*>(taps) + (size_t)q * kBandTaps);
+    float mx = band_dispatch<T, SLICE>(__ldg(hq + q), us, n, tq, W + (size_t)item * n, ws);
+    if constexpr (SLICE) {
+      // row maximum over the CTA (red is double-buffered: one barrier per item)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      if ((threadIdx.x & 31) == 0) red[parity][threadIdx.x >> 5] = mx;
+      __syncthreads();
+      float m = red[parity][0];
+#pragma unroll
+      for (int w = 1; w < kBandThreads / 32; ++w) m = fmaxf(m, red[parity][w]);
+      parity ^= 1;
+      const int e = balanced_exponent(m);
+      if (threadIdx.x == 0) so.expo[item] = e;
+      const int l = int(col / so.R_f), srow = int(col - (long long)l * so.R_f);
+      __nv_bfloat16* ob = so.out + ((long long)(l * R_N + q) * (n / 64) * so.R_f + srow) * 64;
+      float sc1, sc2;
+      slice_scales(e, sc1, sc2);
+      // this thread's own outputs (no barrier needed for ws)
+      for (int i = 2 * threadIdx.x; i < n; i += 2 * kBandThreads) {
+        const float2 v = *reinterpret_cast<const float2*>(ws + i);
+        slice_pair(v.x, v.y, sc1, sc2, ob + (long long)(i >> 6) * so.R_f * 64 + (i & 63), so.slice_stride);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 template <typename K>
 int configure(K kern, size_t smem) {
   CPC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -444,8 +638,26 @@ int launch_spectra(int mode, const double* src, int ncols, double2* o64, float2*
   return CPC_OK;
 }
 
+// which kernel terms go through the FFT and which through the banded kernel
+struct TermSplit {
+  const int* fft_q;  // NULL: all terms
+  int n_fft;
+  const int* band_q;
+  int n_band;
+  const int* band_h;
+};
+TermSplit term_split(const cpc_kernel* P, int cls, const double* U) {
+  TermSplit ts{nullptr, P->R_N, nullptr, 0, nullptr};
+  if (U && P->d_band && P->n_band[cls] > 0) {
+    const int* b = P->d_band + (size_t)cls * 3 * P->R_N;
+    ts = TermSplit{b + 2 * P->R_N, P->R_N - P->n_band[cls], b + P->R_N, P->n_band[cls], b};
+  }
+  return ts;
+}
+
 template <typename T, int LOGN, bool SLICE, bool XIN>
-int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const SliceOut& so, cudaStream_t s) {
+int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const SliceOut& so, cudaStream_t s,
+                const int* qlist, int n_q) {
   using G = Geometry<LOGN, T>;
   using V = typename cvec<T>::type;
   const size_t smem = sizeof(V) * G::slots * padded_len(1 << LOGN);
@@ -454,8 +666,7 @@ int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const
   if (st) return st;
   int per_sm = 0;
   CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::threads, smem));
-  const long long n_items = (long long)ncols * P->R_N;
-  const long long groups = (n_items + G::slots - 1) / G::slots;
+  const long long groups = (long long)((ncols + G::slots - 1) / G::slots) * n_q;
   const long long grid = std::max(1LL, std::min(groups, (long long)std::max(1, per_sm) * sm_count()));
   const T* phat;
   const V* hw;
@@ -472,9 +683,28 @@ int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const
   }
   const int slot = timing_begin("conv_kernel", s);
   kern<<<int(grid), G::threads, smem, s>>>(static_cast<const V*>(Uhat), phat, hw, tw, hwl, twl,
-                                           static_cast<T*>(W), P->R_N, n_items, so);
+                                           static_cast<T*>(W), P->R_N, ncols, qlist, n_q, so);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("conv_kernel");
+  return CPC_OK;
+}
+
+template <typename T, bool SLICE>
+int launch_band(const cpc_kernel* P, int ncols, const double* U, T* W, const SliceOut& so, const TermSplit& ts,
+                cudaStream_t s) {
+  const size_t smem = sizeof(T) * (size_t(P->n) + 2 * kBandHalo) + (SLICE ? sizeof(float) * size_t(P->n) : 0);
+  auto kern = band_conv_kernel<T, SLICE>;
+  int st = configure(kern, smem);
+  if (st) return st;
+  int per_sm = 0;
+  CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBandThreads, smem));
+  const long long items = (long long)ncols * ts.n_band;
+  const long long grid = std::max(1LL, std::min(items, (long long)std::max(1, per_sm) * sm_count()));
+  const void* taps = sizeof(T) == 4 ? static_cast<const void*>(P->d_taps32) : static_cast<const void*>(P->d_taps64);
+  const int slot = timing_begin("band_conv_kernel", s);
+  kern<<<int(grid), kBandThreads, smem, s>>>(U, P->n, ncols, P->R_N, ts.band_q, ts.n_band, ts.band_h, taps, W, so);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("band_conv_kernel");
   return CPC_OK;
 }
 
@@ -530,17 +760,34 @@ __global__ void kernel_pairs_kernel(const double* __restrict__ phat64, int R_N, 
 
 template <typename T, int LOGN, bool SLICE, bool XIN = false>
 int dispatch_conv(int logn, const cpc_kernel* P, int ncols, const void* Uhat, void* W, const SliceOut& so,
-                  cudaStream_t s) {
+                  cudaStream_t s, const int* qlist, int n_q) {
   if constexpr (LOGN > kMaxLogN) {
     return fail(CPC_ERR_UNSUPPORTED, "conv: n too large");
   } else {
     if constexpr (SLICE && LOGN < 7) {
       if (logn == LOGN) return fail(CPC_ERR_UNSUPPORTED, "sliced conv: n must be at least 128");
     } else {
-      if (logn == LOGN) return launch_conv<T, LOGN, SLICE, XIN>(P, ncols, Uhat, W, so, s);
+      if (logn == LOGN) return launch_conv<T, LOGN, SLICE, XIN>(P, ncols, Uhat, W, so, s, qlist, n_q);
     }
-    return dispatch_conv<T, LOGN + 1, SLICE, XIN>(logn, P, ncols, Uhat, W, so, s);
+    return dispatch_conv<T, LOGN + 1, SLICE, XIN>(logn, P, ncols, Uhat, W, so, s, qlist, n_q);
   }
+}
+
+// all R_N terms of ncols columns: the banded terms from U (when given), the
+// rest by FFT from the spectra or operands Uhat
+template <typename T, bool SLICE, bool XIN>
+int run_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const SliceOut& so, cudaStream_t s,
+             const double* U) {
+  if (ilog2(P->n) > kMaxLogN) return fail(CPC_ERR_UNSUPPORTED, "conv: n too large");
+  if (SLICE && P->n < 128) return fail(CPC_ERR_UNSUPPORTED, "sliced conv: n must be at least 128");
+  const TermSplit ts = term_split(P, sizeof(T) == 4 ? 0 : 1, U);
+  int st = CPC_OK;
+  if (ts.n_band > 0) {
+    st = launch_band<T, SLICE>(P, ncols, U, static_cast<T*>(W), so, ts, s);
+    if (st) return st;
+  }
+  if (ts.n_fft > 0) st = dispatch_conv<T, kMinLogN, SLICE, XIN>(ilog2(P->n), P, ncols, Uhat, W, so, s, ts.fft_q, ts.n_fft);
+  return st;
 }
 
 }  // namespace
@@ -618,23 +865,93 @@ int build_kernel_pairs(cpc_kernel* P, cudaStream_t s) {
   return CPC_OK;
 }
 
-int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W, int precision,
-                          cudaStream_t s) {
-  const SliceOut none{nullptr, 0, nullptr, 0};
-  if (precision == CPC_FP64)
-    return dispatch_conv<double, kMinLogN, false>(ilog2(P->n), P, ncols, Uhat, W, none, s);
-  return dispatch_conv<float, kMinLogN, false>(ilog2(P->n), P, ncols, Uhat, W, none, s);
+// Half-widths of the banded terms from the float64 host tables p_q[m],
+// m = 0..n-1 (the vector is even).  Class 0 (float32 W): the smallest H with
+// the tail 2 sum_{m>H} |p_q[m]| at most 2^-32 of the whole sum
+// |p_q[0]| + 2 sum_{m>0} |p_q[m]|, widened until the taps beyond (H+1)/2
+// hold at most 2^-9 of the sum (their lo parts are dropped); class 1
+// (float64 W): tail at most 2^-60 of the sum.  H is rounded up to an
+// instantiated width; terms wider than the class's maximum (or n - 1) stay
+// with the FFT.
+int build_band_tables(cpc_kernel* P, int max32, int max64, cudaStream_t s) {
+  if (P->kind != CPC_KERNEL_CONV) return CPC_OK;
+  const int R_N = P->R_N, n = P->n;
+  std::vector<int> band(size_t(6) * R_N, 0);
+  std::vector<float2> t32(size_t(R_N) * kBandTaps, make_float2(0.0f, 0.0f));
+  std::vector<double> t64(size_t(R_N) * kBandTaps, 0.0);
+  std::vector<double> tail(n);
+  for (int cls = 0; cls < 2; ++cls) {
+    const double tau = cls == 0 ? std::ldexp(1.0, -32) : std::ldexp(1.0, -60);
+    const int hmax = cls == 0 ? max32 : max64;
+    int* hq = band.data() + size_t(cls) * 3 * R_N;
+    int nb = 0, nf = 0;
+    P->band_h[cls].assign(R_N, -1);
+    for (int q = 0; q < R_N; ++q) {
+      const double* p = P->p.data() + size_t(q) * n;
+      // tail[H] = 2 sum_{m > H} |p[m]|
+      double acc = 0.0;
+      for (int m = n - 1; m >= 0; --m) {
+        tail[m] = acc;
+        acc += (m > 0 ? 2.0 : 1.0) * std::fabs(p[m]);
+      }
+      const double sum = acc;
+      int H = 0;
+      while (H < n - 1 && tail[H] > tau * sum) ++H;
+      int need = H;
+      if (cls == 0) {
+        int L = 0;
+        while (L < n - 1 && tail[L] > std::ldexp(sum, -9)) ++L;
+        need = std::max(H, 2 * L - 1);
+      }
+      int width = -1;
+      for (int k = 0; k < kBandNumWidths; ++k)
+        if (band_width(k) >= need) { width = band_width(k); break; }
+      if (hmax < 0 || width < 0 || width > hmax || width >= n || !(sum > 0.0)) {
+        hq[q] = -1;
+        hq[2 * R_N + nf++] = q;
+        continue;
+      }
+      hq[q] = width;
+      hq[R_N + nb++] = q;
+      P->band_h[cls][q] = width;
+      for (int m = 0; m <= width; ++m) {
+        const float hi = float(p[m]);
+        t32[size_t(q) * kBandTaps + m] = make_float2(hi, float(p[m] - double(hi)));
+        t64[size_t(q) * kBandTaps + m] = p[m];
+      }
+    }
+    P->n_band[cls] = nb;
+  }
+  P->band_max[0] = max32;
+  P->band_max[1] = max64;
+  if (!P->d_band) {
+    CPC_CUDA(cudaMalloc(&P->d_band, sizeof(int) * band.size()));
+    CPC_CUDA(cudaMalloc(&P->d_taps32, sizeof(float2) * t32.size()));
+    CPC_CUDA(cudaMalloc(&P->d_taps64, sizeof(double) * t64.size()));
+  }
+  CPC_CUDA(cudaMemcpyAsync(P->d_band, band.data(), sizeof(int) * band.size(), cudaMemcpyHostToDevice, s));
+  CPC_CUDA(cudaMemcpyAsync(P->d_taps32, t32.data(), sizeof(float2) * t32.size(), cudaMemcpyHostToDevice, s));
+  CPC_CUDA(cudaMemcpyAsync(P->d_taps64, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice, s));
+  CPC_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
+  return CPC_OK;
 }
 
-int convolve_operands32(const cpc_kernel* P, int ncols, const void* X, float* W, cudaStream_t s) {
+int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W, int precision,
+                          cudaStream_t s, const double* U) {
   const SliceOut none{nullptr, 0, nullptr, 0};
-  return dispatch_conv<float, kMinLogN, false, true>(ilog2(P->n), P, ncols, X, W, none, s);
+  if (precision == CPC_FP64) return run_conv<double, false, false>(P, ncols, Uhat, W, none, s, U);
+  return run_conv<float, false, false>(P, ncols, Uhat, W, none, s, U);
+}
+
+int convolve_operands32(const cpc_kernel* P, int ncols, const void* X, float* W, cudaStream_t s, const double* U) {
+  const SliceOut none{nullptr, 0, nullptr, 0};
+  return run_conv<float, false, true>(P, ncols, X, W, none, s, U);
 }
 
 int convolve_operands32_sliced(const cpc_kernel* P, int R_f, const void* X, float* W, __nv_bfloat16* slices,
-                               long long slice_stride, int* expo, cudaStream_t s) {
+                               long long slice_stride, int* expo, cudaStream_t s, const double* U) {
   const SliceOut so{slices, slice_stride, expo, R_f};
-  return dispatch_conv<float, kMinLogN, true, true>(ilog2(P->n), P, 3 * R_f, X, W, so, s);
+  return run_conv<float, true, true>(P, 3 * R_f, X, W, so, s, U);
 }
 
 size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision) {
@@ -691,13 +1008,13 @@ int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int pre
   if (precision == CPC_FP64) {
     st = forward_spectra(P, ncols, U, h64, nullptr, s);
     if (st) return st;
-    return convolve_from_spectra(P, ncols, h64, W, precision, s);
+    return convolve_from_spectra(P, ncols, h64, W, precision, s, U);
   }
   // float32: the convolution operands straight from the float64 transforms
   // (they fit in the float64-spectra part of the workspace)
   st = forward_operands32(P, ncols, U, h64, s);
   if (st) return st;
-  return convolve_operands32(P, ncols, h64, static_cast<float*>(W), s);
+  return convolve_operands32(P, ncols, h64, static_cast<float*>(W), s, U);
 }
 }  // namespace cpc
 

@@ -139,6 +139,69 @@ def test_convolution_and_energy_fp32(cpc, name, spec):
     assert rel(G2.cpu().numpy(), G0) < 2e-6
 
 
+def _tail_fraction(p, H):
+    """2 sum_{m>H} |p[m]| over |p[0]| + 2 sum_{m>0} |p[m]| for an even kernel vector."""
+    a = np.abs(p)
+    return 2.0 * a[H + 1:].sum() / (a[0] + 2.0 * a[1:].sum())
+
+
+@pytest.mark.parametrize("name,spec", [CASES[2], CASES[3]])
+def test_banded_convolution(cpc, name, spec):
+    """Narrow kernel terms convolved as the finite sum over their band (Sec. 2.5,
+    Eq. conv): the chosen half-widths meet the tail bound of their W type, and
+    W agrees with the oracle with the band on (default), at the widest
+    instantiated widths, and off (every term through the FFT)."""
+    n, b, M, g = _case(name, spec)
+    h = 2 * b / n
+    P = cpc.make_newton_kernel(n, b, M)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    U = cpc.cp_sample_gaussians(n, b, dev(g["a"]), dev(g["X"]))
+    U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
+    W0 = ocp.convolve_factors(U0, P0)
+    R_N = P0.shape[0]
+    for prec, tau, hmax in (("fp32", 2.0 ** -32, 20), ("fp64", 2.0 ** -60, 24)):
+        hw = P.banding(prec)
+        assert (hw >= 0).any() and (hw < 0).any(), hw
+        for q in np.nonzero(hw >= 0)[0]:
+            assert hw[q] <= hmax and _tail_fraction(P0[q], hw[q]) <= tau
+        for q in np.nonzero(hw < 0)[0]:  # FFT terms: their band would be wider than hmax
+            too_wide = _tail_fraction(P0[q], hmax) > tau
+            lo_wide = prec == "fp32" and _tail_fraction(P0[q], (hmax + 1) // 2) > 2.0 ** -9
+            assert too_wide or lo_wide
+    banded64 = np.nonzero(P.banding("fp64") >= 0)[0]
+    banded32 = np.nonzero(P.banding("fp32") >= 0)[0]
+    rows = lambda qs: np.concatenate([k * R_N + qs for k in range(U0.shape[1])])
+    results = {}
+    for mode in ("default", "widest", "off"):
+        if mode == "widest":
+            P.set_banding(32, 32)
+        elif mode == "off":
+            P.set_banding(-1, -1)
+            assert (P.banding("fp32") < 0).all() and (P.banding("fp64") < 0).all()
+        W64 = cpc.cp_convolve(P, U, "fp64").cpu().numpy()
+        W32 = cpc.cp_convolve(P, U, "fp32").double().cpu().numpy()
+        assert col_rel_err(W64, W0) < TOL64
+        assert col_rel_err(W32, W0) < 2e-6
+        results[mode] = (W64, W32)
+    # the direct sums are float64-exact and, in float32, no worse than the
+    # rounding of U and of the taps (the transform's error is larger)
+    W64, W32 = results["default"]
+    assert col_rel_err(W64[:, rows(banded64)], W0[:, rows(banded64)]) < 1e-14
+    assert col_rel_err(W32[:, rows(banded32)], W0[:, rows(banded32)]) < 3e-7
+    # banded and FFT-only factors agree to the float32 transform's rounding
+    assert col_rel_err(results["off"][1], W32) < 1e-6
+    # the energy path (W and its tensor-core slices in one pass), band off and on
+    G0 = ocp.conv_matrices(U0, W0, R_N)
+    E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
+    kappa = cancellation(G0, g["c"], h)
+    for mx in (-1, 20):
+        P.set_banding(mx, 24)
+        E, W, G = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp32", want_G=True)
+        assert abs(E.item() / E0 - 1) < EH_TOL * max(kappa, 1.0)
+        assert rel(G.cpu().numpy(), G0) < 2e-6
+        assert torch.equal(W, cpc.cp_convolve(P, U, "fp32"))
+
+
 @pytest.mark.parametrize("name,spec", [CASES[0], CASES[2], CASES[3]])
 def test_convolution_and_energy_fp64tc(cpc, name, spec):
     # float64 convolutions (the same V_H factors as CPC_FP64) and the
