@@ -32,7 +32,8 @@ import workloads  # noqa: E402
 
 WORKLOAD = "density600_n8192"
 # kernels timed by the library's events in the density step
-TIMED = ("spectra_kernel", "conv_kernel", "band_conv_kernel", "slice_rows_kernel", "gemm3_tc_kernel")
+CHEB = ("cheb_moments_kernel", "cheb_coef_kernel", "cheb_eval_kernel")
+TIMED = ("spectra_kernel", "conv_kernel", "band_conv_kernel", *CHEB, "slice_rows_kernel", "gemm3_tc_kernel")
 METRIC = "1D factor convolutions/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # GB300 unit counts for ALU roofs: 152 SMs, 128 FP32 lanes per SM (FMA = 2 flop)
@@ -56,8 +57,9 @@ def parse():
     ap.add_argument("--rf", type=int, default=None,
                     help="override the rank R_f (profiling a smaller case of the same kernels)")
     ap.add_argument("--cpu-sample", type=float, default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--no-band", action="store_true",
-                    help="send every kernel term through the FFT (no banded direct sums), for comparison")
+    ap.add_argument("--conv-paths", default="all", choices=["all", "band", "fft"],
+                    help="convolution paths: all (banded, Chebyshev and FFT terms), band (banded and FFT) "
+                         "or fft (every term through the FFT), for comparison")
     ap.add_argument("--workload", default=WORKLOAD,
                     choices=[WORKLOAD, "basis80_n4096", "density200_n4096", "lattice32_n16384",
                              "lattice_energy256_n16384", "nuclear80_n4096", "tei80_n4096"],
@@ -276,8 +278,8 @@ def run_ours(args, ws, rank, local):
     n, b, M, R_f = cfg["n"], cfg["b"], cfg["M"], cfg["R_f"]
     P = cpc.make_newton_kernel(n, b, M, "conv", device=dev)
     R_N = P.R_N
-    if args.no_band:
-        P.set_banding(-1, -1)
+    if args.conv_paths != "all":
+        P.set_conv_paths(*({"band": (20, 24, -1, -1), "fft": (-1, -1, -1, -1)}[args.conv_paths]))
     g = workloads.mixture_for(WORKLOAD, args.seed + rank)
     if args.rf:
         R_f = args.rf
@@ -337,8 +339,9 @@ def run_ours(args, ws, rank, local):
     E_fast = bufs[2].item()
     energy_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in evs]))  # the cp_hartree_energy call
     spec_ms = kt["spectra_kernel"][0] / max(1, kt["spectra_kernel"][1])
-    # the convolutions: FFT terms (conv_kernel) and banded terms (band_conv_kernel)
-    conv_ms = (kt["conv_kernel"][0] + kt["band_conv_kernel"][0]) / args.steps
+    # the convolutions: FFT terms (conv_kernel), banded terms (band_conv_kernel)
+    # and smooth terms (the three Chebyshev kernels)
+    conv_ms = (kt["conv_kernel"][0] + kt["band_conv_kernel"][0] + sum(kt[k][0] for k in CHEB)) / args.steps
     gram_ms = energy_ms - spec_ms - conv_ms  # slicing of U, contraction, final sum
     ms_step = ms_total / args.steps
     convs_per_step = 3 * R_f * R_N
@@ -384,12 +387,13 @@ def run_ours(args, ws, rank, local):
             mso = so.elapsed_time(to) / args.fp64_steps
             kto = {k: cpc.kernel_timing_read(k) for k in TIMED}
             sp_o = kto["spectra_kernel"][0] / max(1, kto["spectra_kernel"][1])
-            cv_o = (kto["conv_kernel"][0] + kto["band_conv_kernel"][0]) / args.fp64_steps
+            cv_o = (kto["conv_kernel"][0] + kto["band_conv_kernel"][0] + sum(kto[k][0] for k in CHEB)) / args.fp64_steps
             en_o = float(np.mean([e[0].elapsed_time(e[1]) for e in eo]))
             others[form] = {"ms_per_step": mso, "value": convs_per_step / (mso * 1e-3),
                             "spectra_ms": sp_o, "conv_ms": cv_o, "contraction_ms": en_o - sp_o - cv_o,
                             "conv_fft_ms": kto["conv_kernel"][0] / args.fp64_steps,
                             "conv_band_ms": kto["band_conv_kernel"][0] / args.fp64_steps,
+                            "conv_cheb_ms": sum(kto[k][0] for k in CHEB) / args.fp64_steps,
                             "E_H": bf[2].item()}
             if form == "fp64tc" and kto["gemm3_tc_kernel"][1]:
                 # the float64-accurate tensor-core contraction: 15 bf16 slice products
@@ -429,11 +433,13 @@ def run_ours(args, ws, rank, local):
     # convolution, the method's work: per convolution an n-point complex inverse
     # FFT (5 n log2 n flop) and the spectral product (6 n flop); bytes: the V_H
     # factors written once plus the operand spectra and kernel pairs read once.
-    # conv_kernel takes the n_fft wide terms; the banded terms are direct sums
-    # (band_conv_kernel): W written once and each factor column read once.
-    hw = P.banding(prec)
+    # conv_kernel takes the n_fft FFT terms; the banded terms are direct sums
+    # (band_conv_kernel) and the smooth terms Chebyshev sums (cheb_conv_kernels):
+    # for both, W written once and each factor column read once.
+    hw, rk = P.conv_paths(prec)
     n_band = int((hw >= 0).sum())
-    n_fft = R_N - n_band
+    n_smooth = int((rk > 0).sum())
+    n_fft = R_N - n_band - n_smooth
     conv_k_ms, _ = per_launch("conv_kernel", conv_ms)
     conv_flops = 3 * R_f * n_fft * (5 * n * math.log2(n) + 6 * n)
     # (operands: 16 bytes per bin of each factor column, float4 (X1, X2) or double2;
@@ -465,6 +471,17 @@ def run_ours(args, ws, rank, local):
             "taps_multiply_adds": bd_taps,
             "note": "direct sums over the band of the narrow kernel terms; float32 W: the bf16 slices "
                     "(6 B per output) are written too and not counted"}
+    if n_smooth:
+        ch_parts = {k: per_launch(k, 0.0)[0] for k in CHEB}
+        ch_ms = sum(ch_parts.values())
+        # bytes: W of the smooth terms written once, each factor column read once (moments)
+        ch_bytes = 3 * R_f * n_smooth * n * elem + 3 * R_f * n * 8
+        kernels["cheb_conv_kernels"] = {
+            "ms": ch_ms, "bound": "hbm", "achieved": ch_bytes / (ch_ms * 1e-3) / 1e9, "unit": "GB/s",
+            "peak": hbm_peak, "frac": ch_bytes / (ch_ms * 1e-3) / 1e9 / hbm_peak, "algorithmic_bytes": ch_bytes,
+            "terms": n_smooth, "ranks": [int(x) for x in rk[rk > 0]], "parts_ms": ch_parts,
+            "note": "separable Chebyshev form of the smooth kernel terms (moments, coefficients, evaluation); "
+                    "float32 W: the bf16 slices (6 B per output) are written too and not counted"}
     # contraction, the method's work: the unique entries of the symmetric convolution
     # matrices (Sec. 3.2), 3 axes x R_N terms x R_f (R_f + 1) / 2 entries x n cells, 2 flop
     # per multiply-add; the fused product over axes and weighted sum are not counted
@@ -515,7 +532,7 @@ def run_ours(args, ws, rank, local):
         "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if not args.rf else f"{WORKLOAD} (R_f={R_f} profiling case)", "n": n, "box": [-b, b], "R_f": R_f, "R_N": R_N,
                    "convolutions_per_step": convs_per_step, "precision_form": prec,
-                   "terms_fft": n_fft, "terms_banded": n_band,
+                   "terms_fft": n_fft, "terms_banded": n_band, "terms_chebyshev": n_smooth,
                    "l2": "each step writes the V_H factors (%.2f GB), far larger than L2" % (
                        3 * R_f * R_N * n * elem / 1e9)},
         "E_H": E_fast, "E_H_evals_per_s": ws * args.steps / (ms_total * 1e-3),
@@ -527,7 +544,8 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": ws * convs_per_step * e2e_steps / e2e_s, "unit": "convolutions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
         # sample, spectra, conv (+ W slices), [slice U,] contraction, final sum
-        "gpu_launches": ({"fp32": 6, "fp64tc": 8}.get(prec, 5) + (1 if n_band else 0)) * args.steps,
+        "gpu_launches": ({"fp32": 6, "fp64tc": 8}.get(prec, 5) + (1 if n_band else 0) + (3 if n_smooth else 0)
+                         - (0 if n_fft else 1)) * args.steps,
         "clocks": clk,
     }
     if ws == 1 and not args.no_cpu_baseline:

@@ -109,23 +109,40 @@ int cpc_kernel_tables(const cpc_kernel* P, double* t, double* a, double* p);
 /* Releases the kernel's device tables and the handle (NULL is a no-op). */
 int cpc_kernel_free(cpc_kernel* P);
 
-/* Banded direct convolution of the narrow kernel terms (Sec. 2.5, Eq. conv
- * as a finite sum).  A CONV kernel with a large exponent t_q has a Galerkin
- * vector p_q a few cells wide; for such a term cp_convolve (and every call
- * that convolves U) forms W = p_q * U as the sum over |m| <= H_q,
- * H_q the smallest half-width whose tail 2 sum_{m > H_q} |p_q[m]| is at most
- * 2^-32 (float32 W) or 2^-60 (float64 W) of |p_q[0]| + 2 sum_{m>0} |p_q[m]|,
- * rounded up to an instantiated width (0..8, 10..16 step 2, 20..32 step 4).
- * Terms with H_q above the maximum of their W type go through the FFT.
- * make_newton_kernel sets the maxima to 20 (float32 W) and 24 (float64 W).
- * cpc_kernel_set_banding sets them (each in [-1, 32]; -1 sends every term
- * through the FFT), rebuilds the device tables on `stream` and synchronises
- * it; no call that uses P may run meanwhile.  cpc_kernel_banding writes H_q
- * (or -1 for an FFT term) for the W type of `precision` into the host array
- * half_width[R_N].  cp_convolve_from_spectra has no U and always takes the
- * FFT for every term. */
-int cpc_kernel_set_banding(cpc_kernel* P, int max_half_width32, int max_half_width64, void* stream);
-int cpc_kernel_banding(const cpc_kernel* P, int precision, int* half_width);
+/* How each kernel term of a CONV kernel is convolved (Sec. 2.5, Eq. conv)
+ * by cp_convolve and every call that convolves U; all three give W = p_q * U
+ * to within the rounding of the W type:
+ *  - banded: the Galerkin vector of a term with a large exponent t_q is a few
+ *    cells wide; W is the direct sum over |m| <= H_q, H_q the smallest
+ *    half-width whose tail 2 sum_{m > H_q} |p_q[m]| is at most 2^-32 (float32
+ *    W) or 2^-60 (float64 W) of |p_q[0]| + 2 sum_{m>0} |p_q[m]|, rounded up
+ *    to an instantiated width (0..8, 10..16 step 2, 20..32 step 4);
+ *  - smooth: a term with a small exponent is, on [-b, b]^2, the polynomial
+ *    p_q(x - y) ~ sum_{k,l<K} C_kl T_k(x/b) T_l(y/b) (Chebyshev, K in
+ *    {4, 8, 12, 16}, within 2^-34 (float32 W) or 2^-46 (float64 W) of p_q[0]
+ *    on a lattice of grid cells); W = sum_k d_k T_k(x_i/b) with
+ *    d = C (sum_j T_l(x_j/b) U[j]);
+ *  - FFT: every other term (length-2n real transforms).
+ * make_newton_kernel sets the largest half-width to 20 (float32 W) and 24
+ * (float64 W) and the largest rank to 16.  cpc_kernel_set_conv_paths sets
+ * them (half-widths in [-1, 32], ranks in [-1, 16]; -1 disables that path),
+ * rebuilds the device tables on `stream` and synchronises it; no call that
+ * uses P may run meanwhile.  cpc_kernel_conv_paths writes, for the W type of
+ * `precision`, each term's half-width (or -1) into half_width[R_N] and rank
+ * (or -1) into rank[R_N], host arrays, either may be NULL.
+ * cp_convolve_from_spectra has no U and takes the FFT for every term. */
+int cpc_kernel_set_conv_paths(cpc_kernel* P, int max_half_width32, int max_half_width64, int max_rank32,
+                              int max_rank64, void* stream);
+int cpc_kernel_conv_paths(const cpc_kernel* P, int precision, int* half_width, int* rank);
+
+/* The host part of the path choice alone, with no device work (CONV kernel
+ * of make_newton_kernel(n, b, M), limits as cpc_kernel_set_conv_paths):
+ * half_width[2][R_N] and rank[2][R_N] (row 0: float32 W, row 1: float64 W;
+ * -1 where the path is not taken) and the Chebyshev coefficients
+ * cheb[R_N][16][16] (C_q[k][l]; zero for terms never fitted), all HOST
+ * arrays, any may be NULL. */
+int make_newton_kernel_paths(int n, double b, int M, int max_half_width32, int max_half_width64, int max_rank32,
+                             int max_rank64, int* half_width, int* rank, double* cheb);
 
 /* ---- a3: grid sampling of Gaussians (Sec. 3.1, Eq. disc_GTO) --------------
  * U[l][k][i] = exp(-a_k (x_i - X[k][l])^2) for R Gaussians exp(-a_k |x - X_k|^2).
@@ -150,9 +167,9 @@ int cp_hadamard_pairs(int n, int n_in, int n_pairs, const int* pa, const int* pb
  * the factors of V_H = f * P_R.  U: [3][R_f][n] float64.  W: [3][R_f*R_N][n],
  * float64 for CPC_FP64 and CPC_SPLIT, float32 for CPC_FP32.  Implemented as length-2n real
  * FFT convolutions in the chosen precision (the spectra of U are formed in
- * float64), except for the narrow kernel terms, which are summed directly
- * over their band (cpc_kernel_set_banding).  Workspace: cp_convolve_workspace
- * bytes. */
+ * float64), except for the narrow kernel terms, summed directly over their
+ * band, and the smooth ones, evaluated in their separable Chebyshev form
+ * (cpc_kernel_set_conv_paths).  Workspace: cp_convolve_workspace bytes. */
 size_t cp_convolve_workspace(const cpc_kernel* P, int R_f, int precision);
 int cp_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision,
                 void* ws, size_t ws_bytes, void* stream);

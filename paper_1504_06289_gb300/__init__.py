@@ -86,18 +86,23 @@ class NewtonKernel:
               "cpc_kernel_tables")
         return t, a, p
 
-    def set_banding(self, max_half_width32: int, max_half_width64: int, stream=None):
-        """Largest half-width of the kernel terms convolved by the banded direct
-        sum, per W type (-1: every term through the FFT)."""
+    def set_conv_paths(self, max_half_width32: int = 20, max_half_width64: int = 24, max_rank32: int = 16,
+                       max_rank64: int = 16, stream=None):
+        """Largest half-width of the banded terms and largest rank of the smooth
+        (Chebyshev) terms, per W type (-1 disables the path; the FFT takes the rest)."""
         with torch.cuda.device(self.device):
-            check(load().cpc_kernel_set_banding(self._h, int(max_half_width32), int(max_half_width64),
-                                                _stream(stream)), "cpc_kernel_set_banding")
+            check(load().cpc_kernel_set_conv_paths(self._h, int(max_half_width32), int(max_half_width64),
+                                                   int(max_rank32), int(max_rank64), _stream(stream)),
+                  "cpc_kernel_set_conv_paths")
 
-    def banding(self, precision: str = "fp32") -> np.ndarray:
-        """Half-width of each banded term for the W type of `precision` (-1: FFT)."""
+    def conv_paths(self, precision: str = "fp32"):
+        """(half_width, rank) of every kernel term for the W type of `precision`:
+        banded terms have half_width >= 0, smooth terms rank > 0, the rest -1, -1 (FFT)."""
         hw = np.empty(self.R_N, dtype=np.int32)
-        check(load().cpc_kernel_banding(self._h, _prec(precision), hw.ctypes.data), "cpc_kernel_banding")
-        return hw
+        rk = np.empty(self.R_N, dtype=np.int32)
+        check(load().cpc_kernel_conv_paths(self._h, _prec(precision), hw.ctypes.data, rk.ctypes.data),
+              "cpc_kernel_conv_paths")
+        return hw, rk
 
     def close(self):
         if self._h is not None:
@@ -120,6 +125,21 @@ def make_newton_kernel_tables(n: int, b: float, M: int, kind: str = "conv"):
     check(load().make_newton_kernel_tables(int(n), float(b), int(M), KIND[kind], t.ctypes.data, a.ctypes.data,
                                            p.ctypes.data, C.byref(hs), C.byref(u0)), "make_newton_kernel_tables")
     return t, a, p, hs.value, u0.value
+
+
+def make_newton_kernel_paths(n: int, b: float, M: int, max_half_width32: int = 20, max_half_width64: int = 24,
+                             max_rank32: int = 16, max_rank64: int = 16):
+    """Host-only path choice of a CONV kernel's terms, no GPU needed: (half_width,
+    rank, cheb) with half_width and rank of shape (2, R_N) (row 0 float32 W, row 1
+    float64 W; -1 where the path is not taken) and cheb (R_N, 16, 16)."""
+    R_N = 2 * M + 1
+    hw = np.empty((2, R_N), dtype=np.int32)
+    rk = np.empty((2, R_N), dtype=np.int32)
+    cheb = np.empty((R_N, 16, 16))
+    check(load().make_newton_kernel_paths(int(n), float(b), int(M), int(max_half_width32), int(max_half_width64),
+                                          int(max_rank32), int(max_rank64), hw.ctypes.data, rk.ctypes.data,
+                                          cheb.ctypes.data), "make_newton_kernel_paths")
+    return hw, rk, cheb
 
 
 def make_newton_kernel(n: int, b: float, M: int, kind: str = "conv", device="cuda",

@@ -20,8 +20,9 @@ PROTOTYPES = {
     "cpc_kernel_info": (i32, [vp, P_i32, P_f64, P_i32, P_i32, P_i32, P_f64, P_f64]),
     "cpc_kernel_tables": (i32, [vp, vp, vp, vp]),
     "cpc_kernel_free": (i32, [vp]),
-    "cpc_kernel_set_banding": (i32, [vp, i32, i32, vp]),
-    "cpc_kernel_banding": (i32, [vp, i32, vp]),
+    "cpc_kernel_set_conv_paths": (i32, [vp, i32, i32, i32, i32, vp]),
+    "cpc_kernel_conv_paths": (i32, [vp, i32, vp, vp]),
+    "make_newton_kernel_paths": (i32, [i32, f64, i32, i32, i32, i32, i32, vp, vp, vp]),
     "cp_sample_gaussians": (i32, [i32, f64, i32, vp, vp, vp, vp]),
     "cp_hadamard_pairs": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
     "cp_convolve_workspace": (sz, [vp, i32, i32]),

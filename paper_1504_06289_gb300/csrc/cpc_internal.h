@@ -43,19 +43,27 @@ struct cpc_kernel {
   float2* d_hw32 = nullptr;
   // CONV only: Parseval weights d_q[2f+j] = w_f phat_q[f] / (2n), float32, [R_N][2(n+1)]
   float* d_specw32 = nullptr;
-  // CONV only: the banded direct convolution of narrow kernel terms
-  // (spectra.cu).  Per precision class (0: float32 W, 1: float64 W): the
-  // half-width used for each term (-1: the term goes through the FFT), the
-  // list of banded terms and the list of FFT terms.  d_band holds
-  // [class][3][R_N] ints in that order; the taps are p_q[0..kBandHalo]
-  // (float32 class: float2 (hi, lo), float64 class: double), zero beyond the
-  // term's half-width.
+  // CONV only: how each kernel term is convolved (spectra.cu), per precision
+  // class (0: float32 W, 1: float64 W): by the FFT, by the banded direct sum
+  // (narrow terms, half-width H) or by the separable Chebyshev form (smooth
+  // terms, rank K).  d_terms holds [class][5][R_N] ints: H per term (-1: not
+  // banded), K per term (-1: not smooth), then the lists of banded, smooth
+  // and FFT terms.  Banded taps p_q[0..kBandHalo] (float32 class: float2
+  // (hi, lo); float64 class: double), zero beyond H; Chebyshev coefficients
+  // C_q [R_N][16][16] float64 and the Chebyshev table T_k(x_i/b) [16][n]
+  // (float2 (hi, lo) and double).
   int band_max[2] = {-1, -1};  // largest half-width sent to the banded kernel
+  int rank_max[2] = {-1, -1};  // largest rank sent to the Chebyshev kernels
   int n_band[2] = {0, 0};
-  std::vector<int> band_h[2];  // host copy of the half-widths
-  int* d_band = nullptr;
+  int n_smooth[2] = {0, 0};
+  std::vector<int> band_h[2];  // host copies of the half-widths and ranks
+  std::vector<int> rank_k[2];
+  int* d_terms = nullptr;
   float2* d_taps32 = nullptr;
   double* d_taps64 = nullptr;
+  double* d_cheb = nullptr;
+  float2* d_tcheb32 = nullptr;
+  double* d_tcheb64 = nullptr;
   // MASTER kernels: scratch of the tensor-core sub-grid evaluation (the bf16
   // slices of the S3 rows, pre-swizzled per 64-point sub-tile, and their
   // exponents); calls on unordered streams sharing one kernel race on it
@@ -108,29 +116,49 @@ int compute_kernel_spectrum(cpc_kernel* P, cudaStream_t s);
 int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uhat64,
                     float2* Uhat32, cudaStream_t s);
 // batched convolution from spectra.  U: the factor columns themselves
-// (float64 [ncols][n]) or NULL; with U, the kernel terms of the banded set
-// are convolved directly from U (band_conv_kernel) and the FFT takes the rest
+// (float64 [ncols][n]) or NULL; with U, the banded terms are convolved
+// directly from U (band_conv_kernel), the smooth terms by the Chebyshev form
+// (scratch: smooth_scratch_bytes, 256-byte aligned) and the FFT takes the rest
 int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W,
-                          int precision, cudaStream_t s, const double* U = nullptr);
+                          int precision, cudaStream_t s, const double* U = nullptr, void* scratch = nullptr);
 // float32 convolution operands (X1, X2) from float64 transforms of U, and the
 // convolutions from them (also writing the tensor-core contraction's W
 // slices and row exponents, n >= 128, in the _sliced form); U as above
 int forward_operands32(const cpc_kernel* P, int ncols, const double* U, void* X, cudaStream_t s);
 size_t operands32_bytes(const cpc_kernel* P, int ncols);
 int convolve_operands32(const cpc_kernel* P, int ncols, const void* X, float* W, cudaStream_t s,
-                        const double* U = nullptr);
+                        const double* U = nullptr, void* scratch = nullptr);
 int convolve_operands32_sliced(const cpc_kernel* P, int R_f, const void* X, float* W, __nv_bfloat16* slices,
-                               long long slice_stride, int* expo, cudaStream_t s, const double* U = nullptr);
+                               long long slice_stride, int* expo, cudaStream_t s, const double* U = nullptr,
+                               void* scratch = nullptr);
 int build_kernel_pairs(cpc_kernel* P, cudaStream_t s);
-// the banded terms of each precision class from the host tables (at most
-// max32 / max64 cells of half-width; a negative maximum bands nothing)
-int build_band_tables(cpc_kernel* P, int max32, int max64, cudaStream_t s);
+// the convolution path of every kernel term, per precision class, from the
+// host tables: banded if its half-width is at most band32 / band64, else
+// Chebyshev if its rank is at most rank32 / rank64, else FFT (a negative
+// maximum disables that path)
+int build_term_tables(cpc_kernel* P, int band32, int band64, int rank32, int rank64, cudaStream_t s);
+// the host part of build_term_tables (no device work): per class the ints
+// [H per term][K per term][banded list][smooth list][FFT list], the taps, the
+// Chebyshev coefficients [R_N][16][16] and the table T_k(x_i/b) [16][n]
+struct TermPlan {
+  std::vector<int> terms;  // [2][5][R_N]
+  std::vector<float2> taps32;
+  std::vector<double> taps64, cheb, tcheb;
+  int n_band[2] = {0, 0}, n_smooth[2] = {0, 0};
+};
+void plan_term_paths(const cpc_kernel* P, int band32, int band64, int rank32, int rank64, TermPlan& tp);
 // default maxima: where the direct sum still costs less than the transform
 // per output (float32 W: about 1.5 instructions per tap against about 110
 // per output for the 8192-point float32 transform; float64 W: 2H + 1 float64
-// operations against about 60)
+// operations against about 60); the Chebyshev form costs about 2K (float32)
+// or K (float64) multiply-adds per output, below the transform for any K <= 16
 constexpr int kDefaultBand32 = 20;
 constexpr int kDefaultBand64 = 24;
+constexpr int kDefaultRank = 16;
+// scratch of the Chebyshev path (moments and coefficients of ncols columns)
+size_t smooth_scratch_bytes(const cpc_kernel* P, int ncols);
+// the convolution workspace without that scratch (which follows it)
+size_t conv_spectra_bytes(const cpc_kernel* P, int R_f, int precision);
 
 // float32 contractions (gram32.cu)
 size_t eh32_partials(int R_f, int R_N);

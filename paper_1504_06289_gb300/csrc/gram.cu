@@ -555,7 +555,8 @@ int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doub
     long long sl_stride;
     int* ex;
     tc_w_slices(P, R_f, tws, &sl, &sl_stride, &ex);
-    st = convolve_operands32_sliced(P, R_f, X, static_cast<float*>(W), sl, sl_stride, ex, s, U);
+    st = convolve_operands32_sliced(P, R_f, X, static_cast<float*>(W), sl, sl_stride, ex, s, U,
+                                    static_cast<unsigned char*>(ws) + conv_spectra_bytes(P, R_f, precision));
     if (st) return st;
     double* partial = static_cast<double*>(cws);
     st = launch_eh_tc(P, R_f, U, static_cast<const float*>(W), c, G, partial, tws, s, true);

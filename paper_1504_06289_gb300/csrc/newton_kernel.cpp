@@ -241,6 +241,29 @@ int make_newton_kernel_tables(int n, double b, int M, int kind, double* t, doubl
   return CPC_OK;
 }
 
+int make_newton_kernel_paths(int n, double b, int M, int max_half_width32, int max_half_width64, int max_rank32,
+                             int max_rank64, int* half_width, int* rank, double* cheb) {
+  clear_error();
+  int st = validate_kernel_args(n, b, M, CPC_KERNEL_CONV, "make_newton_kernel_paths");
+  if (st) return st;
+  if (max_half_width32 < -1 || max_half_width32 > 32 || max_half_width64 < -1 || max_half_width64 > 32 ||
+      max_rank32 < -1 || max_rank32 > 16 || max_rank64 < -1 || max_rank64 > 16)
+    return fail(CPC_ERR_INVALID, "make_newton_kernel_paths: half-widths in [-1, 32], ranks in [-1, 16]");
+  cpc_kernel K;
+  K.n = n; K.b = b; K.h = 2.0 * b / n; K.M = M; K.R_N = 2 * M + 1; K.kind = CPC_KERNEL_CONV;
+  K.len = n;
+  host_tables(&K);
+  TermPlan tp;
+  plan_term_paths(&K, max_half_width32, max_half_width64, max_rank32, max_rank64, tp);
+  for (int cls = 0; cls < 2; ++cls)
+    for (int q = 0; q < K.R_N; ++q) {
+      if (half_width) half_width[cls * K.R_N + q] = tp.terms[size_t(cls) * 5 * K.R_N + q];
+      if (rank) rank[cls * K.R_N + q] = tp.terms[size_t(cls) * 5 * K.R_N + K.R_N + q];
+    }
+  if (cheb) std::memcpy(cheb, tp.cheb.data(), sizeof(double) * tp.cheb.size());
+  return CPC_OK;
+}
+
 int make_newton_kernel(int n, double b, int M, int kind, void* stream, cpc_kernel** out) {
   clear_error();
   if (!out) return fail(CPC_ERR_INVALID, "make_newton_kernel: out is NULL");
@@ -296,7 +319,7 @@ int make_newton_kernel(int n, double b, int M, int kind, void* stream, cpc_kerne
     if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: spectral weights"); cleanup(); return st; }
     st = build_spectral_weights(P, P->d_specw32, s);
     if (st != CPC_OK) { cleanup(); return st; }
-    st = build_band_tables(P, kDefaultBand32, kDefaultBand64, s);
+    st = build_term_tables(P, kDefaultBand32, kDefaultBand64, kDefaultRank, kDefaultRank, s);
     if (st != CPC_OK) { cleanup(); return st; }
   }
   e = cudaStreamSynchronize(s);
@@ -326,22 +349,29 @@ int cpc_kernel_tables(const cpc_kernel* P, double* t, double* a, double* p) {
   return CPC_OK;
 }
 
-int cpc_kernel_set_banding(cpc_kernel* P, int max_half_width32, int max_half_width64, void* stream) {
+int cpc_kernel_set_conv_paths(cpc_kernel* P, int max_half_width32, int max_half_width64, int max_rank32,
+                              int max_rank64, void* stream) {
   clear_error();
-  if (!P) return fail(CPC_ERR_INVALID, "cpc_kernel_set_banding: NULL kernel");
-  if (P->kind != CPC_KERNEL_CONV) return fail(CPC_ERR_INVALID, "cpc_kernel_set_banding: needs a CONV kernel");
+  if (!P) return fail(CPC_ERR_INVALID, "cpc_kernel_set_conv_paths: NULL kernel");
+  if (P->kind != CPC_KERNEL_CONV) return fail(CPC_ERR_INVALID, "cpc_kernel_set_conv_paths: needs a CONV kernel");
   if (max_half_width32 < -1 || max_half_width32 > 32 || max_half_width64 < -1 || max_half_width64 > 32)
-    return fail(CPC_ERR_INVALID, "cpc_kernel_set_banding: half-widths must lie in [-1, 32]");
-  return build_band_tables(P, max_half_width32, max_half_width64, static_cast<cudaStream_t>(stream));
+    return fail(CPC_ERR_INVALID, "cpc_kernel_set_conv_paths: half-widths must lie in [-1, 32]");
+  if (max_rank32 < -1 || max_rank32 > 16 || max_rank64 < -1 || max_rank64 > 16)
+    return fail(CPC_ERR_INVALID, "cpc_kernel_set_conv_paths: ranks must lie in [-1, 16]");
+  return build_term_tables(P, max_half_width32, max_half_width64, max_rank32, max_rank64,
+                           static_cast<cudaStream_t>(stream));
 }
 
-int cpc_kernel_banding(const cpc_kernel* P, int precision, int* half_width) {
+int cpc_kernel_conv_paths(const cpc_kernel* P, int precision, int* half_width, int* rank) {
   clear_error();
-  if (!P || !half_width) return fail(CPC_ERR_INVALID, "cpc_kernel_banding: NULL argument");
-  if (!known_precision(precision)) return fail(CPC_ERR_UNSUPPORTED, "cpc_kernel_banding: unknown precision form");
+  if (!P) return fail(CPC_ERR_INVALID, "cpc_kernel_conv_paths: NULL kernel");
+  if (!known_precision(precision)) return fail(CPC_ERR_UNSUPPORTED, "cpc_kernel_conv_paths: unknown precision form");
   const int cls = storage_precision(precision) == CPC_FP32 ? 0 : 1;
-  for (int q = 0; q < P->R_N; ++q)
-    half_width[q] = (P->kind == CPC_KERNEL_CONV && !P->band_h[cls].empty()) ? P->band_h[cls][q] : -1;
+  const bool conv = P->kind == CPC_KERNEL_CONV;
+  for (int q = 0; q < P->R_N; ++q) {
+    if (half_width) half_width[q] = (conv && !P->band_h[cls].empty()) ? P->band_h[cls][q] : -1;
+    if (rank) rank[q] = (conv && !P->rank_k[cls].empty()) ? P->rank_k[cls][q] : -1;
+  }
   return CPC_OK;
 }
 
@@ -360,9 +390,12 @@ int cpc_kernel_free(cpc_kernel* P) {
   cudaFree(P->d_hw64);
   cudaFree(P->d_hw32);
   cudaFree(P->d_specw32);
-  cudaFree(P->d_band);
+  cudaFree(P->d_terms);
   cudaFree(P->d_taps32);
   cudaFree(P->d_taps64);
+  cudaFree(P->d_cheb);
+  cudaFree(P->d_tcheb32);
+  cudaFree(P->d_tcheb64);
   cudaFree(P->d_lat);
   delete P;
   return CPC_OK;

@@ -434,7 +434,7 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
 // as the finite sum it is).  The Galerkin vector p_q of a term with a large
 // exponent t_q is a bell a few cells wide: beyond a half-width H_q its
 // entries add up to less than a set fraction of sum_m |p_q[|m|]| (2^-32 for
-// float32 W, 2^-60 for float64 W; build_band_tables picks H_q from the host
+// float32 W, 2^-60 for float64 W; build_term_tables picks H_q from the host
 // float64 tables), and
 //   W[i] = sum_{|m| <= H} p_q[|m|] U[i - m]      (U = 0 outside the grid)
 // costs about 2H + 1 multiply-adds per output instead of a length-2n
@@ -558,9 +558,10 @@ band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const 
   const long long k1 = n_items * (blockIdx.x + 1) / gridDim.x;
   long long staged = -1;
   int parity = 0;
-  for (long long k = k0; k < k1; ++k) {
-    const long long col = k / n_band;
-    const int q = __ldg(qlist + int(k - col * n_band));
+  long long col = k0 / n_band;
+  int jq = int(k0 - col * n_band);
+  for (long long k = k0; k < k1; ++k, (++jq == n_band ? (jq = 0, ++col) : 0)) {
+    const int q = __ldg(qlist + jq);
     if (col != staged) {
       __syncthreads();  // every reader of the previous column is done
       const double2* src = reinterpret_cast<const double2*>(U + (size_t)col * n);
@@ -595,6 +596,254 @@ band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const 
       for (int i = 2 * threadIdx.x; i < n; i += 2 * kBandThreads) {
         const float2 v = *reinterpret_cast<const float2*>(ws + i);
         slice_pair(v.x, v.y, sc1, sc2, ob + (long long)(i >> 6) * so.R_f * 64 + (i & 63), so.slice_stride);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Separable Chebyshev form of the smooth kernel terms (Sec. 2.5, Eq. conv).
+// A term with a small exponent t_q varies slowly across the whole box: on
+// [-b, b]^2 the kernel g_q(x, y) = f_q(x - y) (f_q(m h) = p_q[m], the cell
+// integral of the term's Gaussian) is, to a set fraction of f_q(0) (2^-34 for
+// float32 W, 2^-46 for float64 W, checked on the grid by the host; float64
+// evaluation noise of the check itself is near 2^-50), the polynomial
+// sum_{k,l<K} C_kl T_k(x/b) T_l(y/b).  Then
+//   W[i] = sum_j g_q(x_i, x_j) U[j] = sum_k d_k T_k(x_i/b),
+//   d_k  = sum_l C_kl m_l,  m_l = sum_j T_l(x_j/b) U[j],
+// so each convolution costs K multiply-adds per output once the K moments of
+// its column are known (they are shared by all smooth terms).
+//   cheb_moments_kernel: m_l of every column;
+//   cheb_coef_kernel: d = C_q m per (column, term) in float64, stored in the
+//     W type, with a header per item: term, rank and, for the sliced float32
+//     path, the row exponent from the bound sum_k |d_k| >= max_i |W[i]|
+//     (|T_k| <= 1), so every CTA of a row slices with the same exponent;
+//   cheb_eval_kernel: W[i] = sum_k d_k T_k(x_i/b) with the thread's table
+//     entries in registers, CTAs over 512-cell blocks x item ranges.
+constexpr int kCheb = 16;  // largest rank (ranks are 4, 8, 12 or 16)
+constexpr int kChebThreads = 256;
+
+// Moments as a small GEMM, Mom = T (kCheb x n) U^T (n x ncols): a CTA takes
+// 64 columns and a range of kChebCells cells (blockIdx.y), stages the table
+// rows and the columns (rounded to T) of CH cells at a time in shared memory,
+// and each thread accumulates 4 columns of one k (float32 class: products
+// with the (hi, lo) table summed without loss by TwoSum within a stage and
+// flushed into float64 once per stage: the moments are shared by every smooth
+// term of a column, so their rounding would not average out, and float64
+// arithmetic is scarce on this GPU).  Partial moments of every cell range go
+// to Part[range][col][k] and are summed by cheb_coef_kernel.
+constexpr int kChebCols = 64;
+constexpr int kChebCells = 512;
+__host__ __device__ constexpr int cheb_ranges(int n) { return n > kChebCells ? n / kChebCells : 1; }
+
+template <typename T>
+__global__ void __launch_bounds__(kChebThreads)
+cheb_moments_kernel(const double* __restrict__ U, int n, int ncols, const void* __restrict__ tcheb,
+                    double* __restrict__ Part) {
+  using V = typename cvec<T>::type;
+  constexpr int CH = sizeof(T) == 4 ? 64 : 32;        // cells per stage
+  __shared__ __align__(16) V ts[kCheb][CH];           // float32 class: (hi, lo); float64: (T, unused)
+  __shared__ __align__(16) T us[CH][kChebCols + 4];    // [cell][column], padded
+  const int t = threadIdx.x;
+  const int k = t / 16, c4 = 4 * (t % 16);              // this thread: moment k of columns c4..c4+3
+  const int col0 = blockIdx.x * kChebCols;
+  const int cells = n / cheb_ranges(n);
+  const int j0 = blockIdx.y * cells;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int jb = j0; jb < j0 + cells; jb += CH) {
+    const int w = min(CH, j0 + cells - jb);
+    __syncthreads();  // the previous stage is consumed
+    for (int x = t; x < kCheb * CH; x += kChebThreads) {
+      const int kk = x / CH, jj = x % CH;
+      if (jj < w) {
+        if constexpr (sizeof(T) == 4) ts[kk][jj] = __ldg(static_cast<const float2*>(tcheb) + (size_t)kk * n + jb + jj);
+        else ts[kk][jj] = make_double2(__ldg(static_cast<const double*>(tcheb) + (size_t)kk * n + jb + jj), 0.0);
+      }
+    }
+    for (int x = t; x < kChebCols * CH; x += kChebThreads) {
+      const int cc = x / CH, jj = x % CH;
+      const int c = col0 + cc;
+      us[jj][cc] = (c < ncols && jj < w) ? T(__ldg(U + (size_t)c * n + jb + jj)) : T(0);
+    }
+    __syncthreads();
+    if constexpr (sizeof(T) == 4) {
+      // per column an unevaluated sum s + e of the stage's products
+      // (TwoSum, Knuth), flushed into float64 at the end of the stage
+      float sm[4] = {0.f, 0.f, 0.f, 0.f}, er[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int jj = 0; jj < w; ++jj) {
+        const V tk = ts[k][jj];
+        const float4 v = *reinterpret_cast<const float4*>(&us[jj][c4]);
+        const float u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const float p = fmaf(tk.x, u[m], tk.y * u[m]);
+          const float t2 = sm[m] + p;
+          const float bp = t2 - sm[m];
+          er[m] += (sm[m] - (t2 - bp)) + (p - bp);
+          sm[m] = t2;
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 4; ++m) acc[m] += double(sm[m]) + double(er[m]);
+    } else {
+      for (int jj = 0; jj < w; ++jj) {
+        const V tk = ts[k][jj];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[m] = fma(tk.x, us[jj][c4 + m], acc[m]);
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int c = col0 + c4 + m;
+    if (c < ncols) Part[((size_t)blockIdx.y * ncols + c) * kCheb + k] = acc[m];
+  }
+}
+
+// one CTA per column: the moments summed over the cell ranges once, then one
+// thread per smooth term j: d_k for k < K (zero up to kCheb) into
+// D[col n_smooth + j][kCheb], and the item's header (term q, rank K, row
+// exponent e)
+constexpr int kChebCoefThreads = 64;
+template <typename T, bool SLICE>
+__global__ void __launch_bounds__(kChebCoefThreads)
+cheb_coef_kernel(int n, int ncols, const int* __restrict__ qlist, int n_smooth, const int* __restrict__ kq,
+                 const double* __restrict__ cheb, const double* __restrict__ Part, T* __restrict__ D,
+                 int4* __restrict__ Hdr) {
+  const int col = blockIdx.x;
+  __shared__ double m[kCheb];
+  if (threadIdx.x < kCheb) {
+    double acc = 0.0;
+    for (int r = 0; r < cheb_ranges(n); ++r) acc += Part[((size_t)r * ncols + col) * kCheb + threadIdx.x];
+    m[threadIdx.x] = acc;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n_smooth; j += kChebCoefThreads) {
+    const int q = __ldg(qlist + j);
+    const int K = __ldg(kq + q);
+    const double* C = cheb + (size_t)q * kCheb * kCheb;
+    const long long k = (long long)col * n_smooth + j;
+    double bound = 0.0;
+    for (int r = 0; r < kCheb; ++r) {
+      double d = 0.0;
+      if (r < K)
+        for (int l = 0; l < K; ++l) d = fma(__ldg(C + r * kCheb + l), m[l], d);
+      D[k * kCheb + r] = T(d);
+      bound += fabs(double(T(d)));
+    }
+    int e = 0;
+    if constexpr (SLICE) {
+      // the float32 sum of K products of |T| <= 1 stays below bound (1 + K 2^-23)
+      e = balanced_exponent(__double2float_ru(bound * (1.0 + 0x1p-16)));
+    }
+    Hdr[k] = make_int4(q, K, e, 0);
+  }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void cheb_pair(const typename cvec<T>::type* dk, const float4* t32, const double2* t64,
+                                          T& w0, T& w1) {
+  // dk: the item's coefficients as pairs (d_2r, d_2r+1); smallest terms first
+  if constexpr (sizeof(T) == 4) {
+    float a0 = 0.0f, a1 = 0.0f;
+#pragma unroll
+    for (int r = K / 2 - 1; r >= 0; --r) {
+      const float2 d = dk[r];
+      // (hi, lo) of T_k at cells i (x, y) and i+1 (z, w)
+      a0 = fmaf(t32[2 * r + 1].x, d.y, fmaf(t32[2 * r + 1].y, d.y, a0));
+      a1 = fmaf(t32[2 * r + 1].z, d.y, fmaf(t32[2 * r + 1].w, d.y, a1));
+      a0 = fmaf(t32[2 * r].x, d.x, fmaf(t32[2 * r].y, d.x, a0));
+      a1 = fmaf(t32[2 * r].z, d.x, fmaf(t32[2 * r].w, d.x, a1));
+    }
+    w0 = a0;
+    w1 = a1;
+  } else {
+    double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+    for (int r = K / 2 - 1; r >= 0; --r) {
+      const double2 d = dk[r];
+      a0 = fma(t64[2 * r + 1].x, d.y, a0);
+      a1 = fma(t64[2 * r + 1].y, d.y, a1);
+      a0 = fma(t64[2 * r].x, d.x, a0);
+      a1 = fma(t64[2 * r].y, d.x, a1);
+    }
+    w0 = a0;
+    w1 = a1;
+  }
+}
+
+// grid: x = 512-cell blocks of the rows, y = ranges of items (col, j); the
+// records (d row and header) of kChebBatch items at a time are staged in
+// shared memory with coalesced loads, then every thread evaluates its two
+// cells for each of them
+constexpr int kChebBatch = 32;
+template <typename T, bool SLICE>
+__global__ void __launch_bounds__(kChebThreads, 2)
+cheb_eval_kernel(int n, int ncols, int R_N, int n_smooth, const void* __restrict__ tcheb, const T* __restrict__ D,
+                 const int4* __restrict__ Hdr, T* __restrict__ W, SliceOut so) {
+  using V = typename cvec<T>::type;
+  __shared__ __align__(16) T sd[kChebBatch][kCheb];
+  __shared__ int4 sh[kChebBatch];
+  const int i = blockIdx.x * 2 * kChebThreads + 2 * threadIdx.x;  // cells i, i+1
+  const bool on = i < n;
+  // this thread's table entries: T_k at cells i and i+1
+  float4 t32[sizeof(T) == 4 ? kCheb : 1];
+  double2 t64[sizeof(T) == 8 ? kCheb : 1];
+  if constexpr (sizeof(T) == 4) {
+    const float2* tc = static_cast<const float2*>(tcheb);
+#pragma unroll
+    for (int k = 0; k < kCheb; ++k)
+      t32[k] = on ? __ldg(reinterpret_cast<const float4*>(tc + (size_t)k * n + i)) : make_float4(0.f, 0.f, 0.f, 0.f);
+  } else {
+    const double* tc = static_cast<const double*>(tcheb);
+#pragma unroll
+    for (int k = 0; k < kCheb; ++k)
+      t64[k] = on ? __ldg(reinterpret_cast<const double2*>(tc + (size_t)k * n + i)) : make_double2(0.0, 0.0);
+  }
+  const long long n_items = (long long)ncols * n_smooth;
+  const long long k0 = n_items * blockIdx.y / gridDim.y, k1 = n_items * (blockIdx.y + 1) / gridDim.y;
+  // (col, j) and, sliced, (axis l, row srow) of item k, advanced incrementally
+  int col = int(k0 / n_smooth), j = int(k0 - (long long)col * n_smooth);
+  int l = SLICE ? col / so.R_f : 0, srow = SLICE ? col - l * so.R_f : 0;
+  const int chunk_off = (i >> 6) * so.R_f * 64 + (i & 63);
+  for (long long kb = k0; kb < k1; kb += kChebBatch) {
+    const int nb = int(min((long long)kChebBatch, k1 - kb));
+    __syncthreads();  // the previous batch is consumed
+    {
+      // d rows as 16-byte pieces, then the headers
+      constexpr int PIECES = kCheb * sizeof(T) / 16;
+      const uint4* src = reinterpret_cast<const uint4*>(D + kb * kCheb);
+      uint4* dst = reinterpret_cast<uint4*>(&sd[0][0]);
+      for (int x = threadIdx.x; x < nb * PIECES; x += kChebThreads) dst[x] = __ldg(src + x);
+      if (threadIdx.x < nb) sh[threadIdx.x] = __ldg(Hdr + kb + threadIdx.x);
+    }
+    __syncthreads();
+    for (int b = 0; b < nb; ++b) {
+      const int4 h = sh[b];  // (q, K, e)
+      const V* dk = reinterpret_cast<const V*>(sd[b]);
+      T w0, w1;
+      if (h.y <= 4) cheb_pair<T, 4>(dk, t32, t64, w0, w1);
+      else if (h.y <= 8) cheb_pair<T, 8>(dk, t32, t64, w0, w1);
+      else if (h.y <= 12) cheb_pair<T, 12>(dk, t32, t64, w0, w1);
+      else cheb_pair<T, 16>(dk, t32, t64, w0, w1);
+      if (on) {
+        const long long item = (long long)col * R_N + h.x;
+        __stcs(reinterpret_cast<V*>(W + (size_t)item * n + i), cmk<V>(w0, w1));
+        if constexpr (SLICE) {
+          float sc1, sc2;
+          slice_scales(h.z, sc1, sc2);
+          __nv_bfloat16* ob = so.out + ((long long)(l * R_N + h.x) * (n / 64) * so.R_f + srow) * 64;
+          slice_pair(float(w0), float(w1), sc1, sc2, ob + chunk_off, so.slice_stride);
+          if (threadIdx.x == 0 && blockIdx.x == 0) so.expo[item] = h.z;
+        }
+      }
+      if (++j == n_smooth) {
+        j = 0;
+        ++col;
+        if (SLICE && ++srow == so.R_f) {
+          srow = 0;
+          ++l;
+        }
       }
     }
   }
@@ -638,19 +887,24 @@ int launch_spectra(int mode, const double* src, int ncols, double2* o64, float2*
   return CPC_OK;
 }
 
-// which kernel terms go through the FFT and which through the banded kernel
+// how the kernel terms of one precision class are convolved
 struct TermSplit {
   const int* fft_q;  // NULL: all terms
   int n_fft;
   const int* band_q;
   int n_band;
   const int* band_h;
+  const int* smooth_q;
+  int n_smooth;
+  const int* smooth_k;
 };
 TermSplit term_split(const cpc_kernel* P, int cls, const double* U) {
-  TermSplit ts{nullptr, P->R_N, nullptr, 0, nullptr};
-  if (U && P->d_band && P->n_band[cls] > 0) {
-    const int* b = P->d_band + (size_t)cls * 3 * P->R_N;
-    ts = TermSplit{b + 2 * P->R_N, P->R_N - P->n_band[cls], b + P->R_N, P->n_band[cls], b};
+  TermSplit ts{nullptr, P->R_N, nullptr, 0, nullptr, nullptr, 0, nullptr};
+  if (U && P->d_terms && P->n_band[cls] + P->n_smooth[cls] > 0) {
+    const int R_N = P->R_N;
+    const int* b = P->d_terms + (size_t)cls * 5 * R_N;
+    ts = TermSplit{b + 4 * R_N, R_N - P->n_band[cls] - P->n_smooth[cls], b + 2 * R_N, P->n_band[cls], b,
+                   b + 3 * R_N, P->n_smooth[cls], b + R_N};
   }
   return ts;
 }
@@ -773,17 +1027,57 @@ int dispatch_conv(int logn, const cpc_kernel* P, int ncols, const void* Uhat, vo
   }
 }
 
-// all R_N terms of ncols columns: the banded terms from U (when given), the
-// rest by FFT from the spectra or operands Uhat
+template <typename T, bool SLICE>
+int launch_smooth(const cpc_kernel* P, int ncols, const double* U, T* W, const SliceOut& so, const TermSplit& ts,
+                  void* scratch, cudaStream_t s) {
+  if (!scratch) return fail(CPC_ERR_WORKSPACE, "conv: the Chebyshev path needs its scratch");
+  const int n = P->n;
+  unsigned char* sc = static_cast<unsigned char*>(scratch);
+  double* Part = reinterpret_cast<double*>(sc);
+  sc += align256(sizeof(double) * size_t(cheb_ranges(n)) * ncols * kCheb);
+  int4* Hdr = reinterpret_cast<int4*>(sc);
+  sc += align256(sizeof(int4) * size_t(ncols) * P->R_N);
+  T* D = reinterpret_cast<T*>(sc);
+  const void* tcheb = sizeof(T) == 4 ? static_cast<const void*>(P->d_tcheb32) : static_cast<const void*>(P->d_tcheb64);
+  int slot = timing_begin("cheb_moments_kernel", s);
+  cheb_moments_kernel<T><<<dim3((ncols + kChebCols - 1) / kChebCols, cheb_ranges(n)), kChebThreads, 0, s>>>(
+      U, n, ncols, tcheb, Part);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("cheb_moments_kernel");
+  const long long items = (long long)ncols * ts.n_smooth;
+  slot = timing_begin("cheb_coef_kernel", s);
+  cheb_coef_kernel<T, SLICE><<<ncols, kChebCoefThreads, 0, s>>>(n, ncols, ts.smooth_q, ts.n_smooth, ts.smooth_k,
+                                                                 P->d_cheb, Part, D, Hdr);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("cheb_coef_kernel");
+  slot = timing_begin("cheb_eval_kernel", s);
+  auto kern = cheb_eval_kernel<T, SLICE>;
+  int per_sm = 0;
+  CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kChebThreads, 0));
+  const int bx = std::max(1, n / (2 * kChebThreads));
+  const long long by = std::max(1LL, std::min(items, ((long long)std::max(1, per_sm) * sm_count() + bx - 1) / bx));
+  kern<<<dim3(bx, unsigned(by)), kChebThreads, 0, s>>>(n, ncols, P->R_N, ts.n_smooth, tcheb, D, Hdr, W, so);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("cheb_eval_kernel");
+  return CPC_OK;
+}
+
+// all R_N terms of ncols columns: the banded and smooth terms from U (when
+// given), the rest by FFT from the spectra or operands Uhat
 template <typename T, bool SLICE, bool XIN>
 int run_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const SliceOut& so, cudaStream_t s,
-             const double* U) {
+             const double* U, void* scratch) {
   if (ilog2(P->n) > kMaxLogN) return fail(CPC_ERR_UNSUPPORTED, "conv: n too large");
   if (SLICE && P->n < 128) return fail(CPC_ERR_UNSUPPORTED, "sliced conv: n must be at least 128");
-  const TermSplit ts = term_split(P, sizeof(T) == 4 ? 0 : 1, U);
+  TermSplit ts = term_split(P, sizeof(T) == 4 ? 0 : 1, U);
+  if (ts.n_smooth > 0 && !scratch) ts = term_split(P, sizeof(T) == 4 ? 0 : 1, nullptr);  // all by FFT
   int st = CPC_OK;
   if (ts.n_band > 0) {
     st = launch_band<T, SLICE>(P, ncols, U, static_cast<T*>(W), so, ts, s);
+    if (st) return st;
+  }
+  if (ts.n_smooth > 0) {
+    st = launch_smooth<T, SLICE>(P, ncols, U, static_cast<T*>(W), so, ts, scratch, s);
     if (st) return st;
   }
   if (ts.n_fft > 0) st = dispatch_conv<T, kMinLogN, SLICE, XIN>(ilog2(P->n), P, ncols, Uhat, W, so, s, ts.fft_q, ts.n_fft);
@@ -865,93 +1159,225 @@ int build_kernel_pairs(cpc_kernel* P, cudaStream_t s) {
   return CPC_OK;
 }
 
-// Half-widths of the banded terms from the float64 host tables p_q[m],
-// m = 0..n-1 (the vector is even).  Class 0 (float32 W): the smallest H with
-// the tail 2 sum_{m>H} |p_q[m]| at most 2^-32 of the whole sum
-// |p_q[0]| + 2 sum_{m>0} |p_q[m]|, widened until the taps beyond (H+1)/2
-// hold at most 2^-9 of the sum (their lo parts are dropped); class 1
-// (float64 W): tail at most 2^-60 of the sum.  H is rounded up to an
-// instantiated width; terms wider than the class's maximum (or n - 1) stay
-// with the FFT.
-int build_band_tables(cpc_kernel* P, int max32, int max64, cudaStream_t s) {
-  if (P->kind != CPC_KERNEL_CONV) return CPC_OK;
+// ---- host: the convolution path of every kernel term ----------------------
+// Banded: from the float64 host tables p_q[m], m = 0..n-1 (the vector is
+// even).  Class 0 (float32 W): the smallest H with the tail
+// 2 sum_{m>H} |p_q[m]| at most 2^-32 of the whole sum
+// |p_q[0]| + 2 sum_{m>0} |p_q[m]|, widened until the taps beyond (H+1)/2 hold
+// at most 2^-9 of the sum (their lo parts are dropped); class 1 (float64 W):
+// tail at most 2^-60 of the sum.  H is rounded up to an instantiated width.
+static int band_half_width(const double* p, int n, int cls, std::vector<double>& tail) {
+  const double tau = cls == 0 ? std::ldexp(1.0, -32) : std::ldexp(1.0, -60);
+  double acc = 0.0;
+  for (int m = n - 1; m >= 0; --m) {  // tail[H] = 2 sum_{m > H} |p[m]|
+    tail[m] = acc;
+    acc += (m > 0 ? 2.0 : 1.0) * std::fabs(p[m]);
+  }
+  const double sum = acc;
+  if (!(sum > 0.0)) return -1;
+  int H = 0;
+  while (H < n - 1 && tail[H] > tau * sum) ++H;
+  int need = H;
+  if (cls == 0) {
+    int L = 0;
+    while (L < n - 1 && tail[L] > std::ldexp(sum, -9)) ++L;
+    need = std::max(H, 2 * L - 1);
+  }
+  for (int k = 0; k < kBandNumWidths; ++k)
+    if (band_width(k) >= need) return band_width(k) < n ? band_width(k) : -1;
+  return -1;
+}
+
+// Smooth: the Chebyshev coefficients C[k][l] (k, l < kCheb) of
+// g(x, y) = f_q(x - y) on [-b, b]^2, f_q(s) = a_q^{1/3} int_{s-h/2}^{s+h/2}
+// exp(-t_q^2 x^2) dx (so f_q(m h) = p_q[m]), by interpolation at the
+// kChebFit x kChebFit Chebyshev points of the first kind
+// x_j = b cos(pi (j + 1/2) / kChebFit):
+//   C[k][l] = (2 / N)^2 sum_{j,l'} g(x_j, x_l') T_k(x_j/b) T_l(x_l'/b),
+// halved for k = 0 and for l = 0.
+constexpr int kChebFit = 48;
+static void cheb_fit(const cpc_kernel* P, int q, double* C) {
+  constexpr int N = kChebFit;
+  const double kPi = 3.14159265358979323846;
+  const double b = P->b, h = P->h, t = P->t[q], sc = std::cbrt(P->a[q]);
+  std::vector<double> x(N), A(size_t(kCheb) * N), g(size_t(N) * N), tmp(size_t(kCheb) * N);
+  for (int j = 0; j < N; ++j) {
+    const double th = kPi * (j + 0.5) / N;
+    x[j] = b * std::cos(th);
+    for (int k = 0; k < kCheb; ++k) A[size_t(k) * N + j] = (k == 0 ? 1.0 : 2.0) / N * std::cos(k * th);
+  }
+  for (int j = 0; j < N; ++j)
+    for (int l = 0; l <= j; ++l) {
+      const double d = x[j] - x[l];
+      g[size_t(j) * N + l] = g[size_t(l) * N + j] = sc * gauss_cell_integral(t, d - 0.5 * h, d + 0.5 * h);
+    }
+  for (int k = 0; k < kCheb; ++k)
+    for (int l = 0; l < N; ++l) {
+      double acc = 0.0;
+      for (int j = 0; j < N; ++j) acc += A[size_t(k) * N + j] * g[size_t(j) * N + l];
+      tmp[size_t(k) * N + l] = acc;
+    }
+  for (int k = 0; k < kCheb; ++k)
+    for (int m = 0; m < kCheb; ++m) {
+      double acc = 0.0;
+      for (int l = 0; l < N; ++l) acc += tmp[size_t(k) * N + l] * A[size_t(m) * N + l];
+      C[size_t(k) * kCheb + m] = acc;
+    }
+}
+
+// T_k(x_i / b) at the cell centres, k < kCheb: [kCheb][n]
+static void cheb_table(int n, std::vector<double>& Tt) {
+  Tt.resize(size_t(kCheb) * n);
+  for (int i = 0; i < n; ++i) {
+    const double th = std::acos(-1.0 + (2.0 * i + 1.0) / n);
+    for (int k = 0; k < kCheb; ++k) Tt[size_t(k) * n + i] = std::cos(k * th);
+  }
+}
+
+// The smallest rank K in {4, 8, 12, 16} (at most kmax) whose expansion
+// matches p_q[|i - j|] within eps/4 of p_q[0] at a lattice of grid cells
+// (97 indices per axis from 0 to n-1, all cells when n <= 97); -1 if none.
+static int cheb_rank(const double* C, const double* p, const std::vector<double>& Tt, int n, int kmax, double eps) {
+  std::vector<int> idx;
+  if (n <= 97) {
+    for (int i = 0; i < n; ++i) idx.push_back(i);
+  } else {
+    for (int m = 0; m <= 96; ++m) idx.push_back(int((long long)m * (n - 1) / 96));
+  }
+  const double bound = 0.25 * eps * std::fabs(p[0]);
+  std::vector<double> V(idx.size() * kCheb);
+  for (int K = 4; K <= std::min(kmax, kCheb); K += 4) {
+    for (size_t jj = 0; jj < idx.size(); ++jj)
+      for (int k = 0; k < K; ++k) {
+        double acc = 0.0;
+        for (int l = 0; l < K; ++l) acc += C[size_t(k) * kCheb + l] * Tt[size_t(l) * n + idx[jj]];
+        V[jj * kCheb + k] = acc;
+      }
+    double err = 0.0;
+    for (size_t ii = 0; ii < idx.size() && err <= bound; ++ii)
+      for (size_t jj = 0; jj < idx.size(); ++jj) {
+        double acc = 0.0;
+        for (int k = 0; k < K; ++k) acc += Tt[size_t(k) * n + idx[ii]] * V[jj * kCheb + k];
+        err = std::max(err, std::fabs(acc - p[std::abs(idx[ii] - idx[jj])]));
+      }
+    if (err <= bound) return K;
+  }
+  return -1;
+}
+
+void plan_term_paths(const cpc_kernel* P, int band32, int band64, int rank32, int rank64, TermPlan& tp) {
   const int R_N = P->R_N, n = P->n;
-  std::vector<int> band(size_t(6) * R_N, 0);
-  std::vector<float2> t32(size_t(R_N) * kBandTaps, make_float2(0.0f, 0.0f));
-  std::vector<double> t64(size_t(R_N) * kBandTaps, 0.0);
+  tp.terms.assign(size_t(10) * R_N, 0);
+  tp.taps32.assign(size_t(R_N) * kBandTaps, make_float2(0.0f, 0.0f));
+  tp.taps64.assign(size_t(R_N) * kBandTaps, 0.0);
+  tp.cheb.assign(size_t(R_N) * kCheb * kCheb, 0.0);
   std::vector<double> tail(n);
+  std::vector<char> fitted(R_N, 0);
+  cheb_table(n, tp.tcheb);
   for (int cls = 0; cls < 2; ++cls) {
-    const double tau = cls == 0 ? std::ldexp(1.0, -32) : std::ldexp(1.0, -60);
-    const int hmax = cls == 0 ? max32 : max64;
-    int* hq = band.data() + size_t(cls) * 3 * R_N;
-    int nb = 0, nf = 0;
-    P->band_h[cls].assign(R_N, -1);
+    const int hmax = cls == 0 ? band32 : band64;
+    const int kmax = cls == 0 ? rank32 : rank64;
+    const double eps = cls == 0 ? std::ldexp(1.0, -32) : std::ldexp(1.0, -44);
+    int* hq = tp.terms.data() + size_t(cls) * 5 * R_N;
+    int *kq = hq + R_N, *bl = hq + 2 * R_N, *sl = hq + 3 * R_N, *fl = hq + 4 * R_N;
+    int nb = 0, ns = 0, nf = 0;
     for (int q = 0; q < R_N; ++q) {
       const double* p = P->p.data() + size_t(q) * n;
-      // tail[H] = 2 sum_{m > H} |p[m]|
-      double acc = 0.0;
-      for (int m = n - 1; m >= 0; --m) {
-        tail[m] = acc;
-        acc += (m > 0 ? 2.0 : 1.0) * std::fabs(p[m]);
-      }
-      const double sum = acc;
-      int H = 0;
-      while (H < n - 1 && tail[H] > tau * sum) ++H;
-      int need = H;
-      if (cls == 0) {
-        int L = 0;
-        while (L < n - 1 && tail[L] > std::ldexp(sum, -9)) ++L;
-        need = std::max(H, 2 * L - 1);
-      }
-      int width = -1;
-      for (int k = 0; k < kBandNumWidths; ++k)
-        if (band_width(k) >= need) { width = band_width(k); break; }
-      if (hmax < 0 || width < 0 || width > hmax || width >= n || !(sum > 0.0)) {
-        hq[q] = -1;
-        hq[2 * R_N + nf++] = q;
+      hq[q] = kq[q] = -1;
+      const int H = hmax >= 0 ? band_half_width(p, n, cls, tail) : -1;
+      if (H >= 0 && H <= hmax) {
+        hq[q] = H;
+        bl[nb++] = q;
+        for (int m = 0; m <= H; ++m) {
+          const float hi = float(p[m]);
+          tp.taps32[size_t(q) * kBandTaps + m] = make_float2(hi, float(p[m] - double(hi)));
+          tp.taps64[size_t(q) * kBandTaps + m] = p[m];
+        }
         continue;
       }
-      hq[q] = width;
-      hq[R_N + nb++] = q;
-      P->band_h[cls][q] = width;
-      for (int m = 0; m <= width; ++m) {
-        const float hi = float(p[m]);
-        t32[size_t(q) * kBandTaps + m] = make_float2(hi, float(p[m] - double(hi)));
-        t64[size_t(q) * kBandTaps + m] = p[m];
+      if (kmax >= 4 && p[0] > 0.0) {
+        double* C = tp.cheb.data() + size_t(q) * kCheb * kCheb;
+        if (!fitted[q]) {
+          cheb_fit(P, q, C);
+          fitted[q] = 1;
+        }
+        const int K = cheb_rank(C, p, tp.tcheb, n, kmax, eps);
+        if (K > 0) {
+          kq[q] = K;
+          sl[ns++] = q;
+          continue;
+        }
       }
+      fl[nf++] = q;
     }
-    P->n_band[cls] = nb;
+    tp.n_band[cls] = nb;
+    tp.n_smooth[cls] = ns;
   }
-  P->band_max[0] = max32;
-  P->band_max[1] = max64;
-  if (!P->d_band) {
-    CPC_CUDA(cudaMalloc(&P->d_band, sizeof(int) * band.size()));
-    CPC_CUDA(cudaMalloc(&P->d_taps32, sizeof(float2) * t32.size()));
-    CPC_CUDA(cudaMalloc(&P->d_taps64, sizeof(double) * t64.size()));
+}
+
+int build_term_tables(cpc_kernel* P, int band32, int band64, int rank32, int rank64, cudaStream_t s) {
+  if (P->kind != CPC_KERNEL_CONV) return CPC_OK;
+  const int R_N = P->R_N;
+  TermPlan tp;
+  plan_term_paths(P, band32, band64, rank32, rank64, tp);
+  for (int cls = 0; cls < 2; ++cls) {
+    const int* hq = tp.terms.data() + size_t(cls) * 5 * R_N;
+    P->band_h[cls].assign(hq, hq + R_N);
+    P->rank_k[cls].assign(hq + R_N, hq + 2 * R_N);
+    P->n_band[cls] = tp.n_band[cls];
+    P->n_smooth[cls] = tp.n_smooth[cls];
   }
-  CPC_CUDA(cudaMemcpyAsync(P->d_band, band.data(), sizeof(int) * band.size(), cudaMemcpyHostToDevice, s));
-  CPC_CUDA(cudaMemcpyAsync(P->d_taps32, t32.data(), sizeof(float2) * t32.size(), cudaMemcpyHostToDevice, s));
-  CPC_CUDA(cudaMemcpyAsync(P->d_taps64, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice, s));
+  P->band_max[0] = band32;
+  P->band_max[1] = band64;
+  P->rank_max[0] = rank32;
+  P->rank_max[1] = rank64;
+  std::vector<float2> tc32(tp.tcheb.size());
+  for (size_t k = 0; k < tp.tcheb.size(); ++k) {
+    const float hi = float(tp.tcheb[k]);
+    tc32[k] = make_float2(hi, float(tp.tcheb[k] - double(hi)));
+  }
+  if (!P->d_terms) {
+    CPC_CUDA(cudaMalloc(&P->d_terms, sizeof(int) * tp.terms.size()));
+    CPC_CUDA(cudaMalloc(&P->d_taps32, sizeof(float2) * tp.taps32.size()));
+    CPC_CUDA(cudaMalloc(&P->d_taps64, sizeof(double) * tp.taps64.size()));
+    CPC_CUDA(cudaMalloc(&P->d_cheb, sizeof(double) * tp.cheb.size()));
+    CPC_CUDA(cudaMalloc(&P->d_tcheb32, sizeof(float2) * tc32.size()));
+    CPC_CUDA(cudaMalloc(&P->d_tcheb64, sizeof(double) * tp.tcheb.size()));
+  }
+  CPC_CUDA(cudaMemcpyAsync(P->d_terms, tp.terms.data(), sizeof(int) * tp.terms.size(), cudaMemcpyHostToDevice, s));
+  CPC_CUDA(cudaMemcpyAsync(P->d_taps32, tp.taps32.data(), sizeof(float2) * tp.taps32.size(), cudaMemcpyHostToDevice, s));
+  CPC_CUDA(cudaMemcpyAsync(P->d_taps64, tp.taps64.data(), sizeof(double) * tp.taps64.size(), cudaMemcpyHostToDevice, s));
+  CPC_CUDA(cudaMemcpyAsync(P->d_cheb, tp.cheb.data(), sizeof(double) * tp.cheb.size(), cudaMemcpyHostToDevice, s));
+  CPC_CUDA(cudaMemcpyAsync(P->d_tcheb32, tc32.data(), sizeof(float2) * tc32.size(), cudaMemcpyHostToDevice, s));
+  CPC_CUDA(cudaMemcpyAsync(P->d_tcheb64, tp.tcheb.data(), sizeof(double) * tp.tcheb.size(), cudaMemcpyHostToDevice, s));
   CPC_CUDA(cudaStreamSynchronize(s));  // the host vectors go out of scope
   return CPC_OK;
 }
 
 int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W, int precision,
-                          cudaStream_t s, const double* U) {
+                          cudaStream_t s, const double* U, void* scratch) {
   const SliceOut none{nullptr, 0, nullptr, 0};
-  if (precision == CPC_FP64) return run_conv<double, false, false>(P, ncols, Uhat, W, none, s, U);
-  return run_conv<float, false, false>(P, ncols, Uhat, W, none, s, U);
+  if (precision == CPC_FP64) return run_conv<double, false, false>(P, ncols, Uhat, W, none, s, U, scratch);
+  return run_conv<float, false, false>(P, ncols, Uhat, W, none, s, U, scratch);
 }
 
-int convolve_operands32(const cpc_kernel* P, int ncols, const void* X, float* W, cudaStream_t s, const double* U) {
+int convolve_operands32(const cpc_kernel* P, int ncols, const void* X, float* W, cudaStream_t s, const double* U,
+                        void* scratch) {
   const SliceOut none{nullptr, 0, nullptr, 0};
-  return run_conv<float, false, true>(P, ncols, X, W, none, s, U);
+  return run_conv<float, false, true>(P, ncols, X, W, none, s, U, scratch);
 }
 
 int convolve_operands32_sliced(const cpc_kernel* P, int R_f, const void* X, float* W, __nv_bfloat16* slices,
-                               long long slice_stride, int* expo, cudaStream_t s, const double* U) {
+                               long long slice_stride, int* expo, cudaStream_t s, const double* U, void* scratch) {
   const SliceOut so{slices, slice_stride, expo, R_f};
-  return run_conv<float, true, true>(P, 3 * R_f, X, W, so, s, U);
+  return run_conv<float, true, true>(P, 3 * R_f, X, W, so, s, U, scratch);
+}
+
+size_t smooth_scratch_bytes(const cpc_kernel* P, int ncols) {
+  // partial moments [ranges][ncols][kCheb] float64, item headers [ncols R_N]
+  // int4, coefficients [ncols R_N][kCheb] (float64 at most)
+  return align256(sizeof(double) * size_t(cheb_ranges(P->n)) * ncols * kCheb) +
+         align256(sizeof(int4) * size_t(ncols) * P->R_N) + align256(sizeof(double) * size_t(ncols) * P->R_N * kCheb);
 }
 
 size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision) {
@@ -963,13 +1389,21 @@ size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision) {
 
 using namespace cpc;
 
-extern "C" size_t cp_convolve_workspace(const cpc_kernel* P, int R_f, int precision) {
-  if (!P || R_f <= 0) return 0;
+namespace cpc {
+// the spectra (or float32 operands) part of the convolution workspace; the
+// Chebyshev scratch follows it
+size_t conv_spectra_bytes(const cpc_kernel* P, int R_f, int precision) {
   precision = storage_precision(precision);
   // float32 forms keep a float64 copy of the spectra too (they are formed in float64)
   size_t b = spectra_bytes(P, 3 * R_f, precision);
   if (precision != CPC_FP64) b += spectra_bytes(P, 3 * R_f, CPC_FP64);
   return b;
+}
+}  // namespace cpc
+
+extern "C" size_t cp_convolve_workspace(const cpc_kernel* P, int R_f, int precision) {
+  if (!P || R_f <= 0) return 0;
+  return conv_spectra_bytes(P, R_f, precision) + smooth_scratch_bytes(P, 3 * R_f);
 }
 
 namespace cpc {
@@ -1005,16 +1439,17 @@ int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int pre
   unsigned char* w = static_cast<unsigned char*>(ws);
   double2* h64 = reinterpret_cast<double2*>(w);
   int st;
+  void* scratch = w + conv_spectra_bytes(P, R_f, precision);
   if (precision == CPC_FP64) {
     st = forward_spectra(P, ncols, U, h64, nullptr, s);
     if (st) return st;
-    return convolve_from_spectra(P, ncols, h64, W, precision, s, U);
+    return convolve_from_spectra(P, ncols, h64, W, precision, s, U, scratch);
   }
   // float32: the convolution operands straight from the float64 transforms
   // (they fit in the float64-spectra part of the workspace)
   st = forward_operands32(P, ncols, U, h64, s);
   if (st) return st;
-  return convolve_operands32(P, ncols, h64, static_cast<float*>(W), s, U);
+  return convolve_operands32(P, ncols, h64, static_cast<float*>(W), s, U, scratch);
 }
 }  // namespace cpc
 

@@ -132,7 +132,13 @@ def test_convolution_and_energy_fp32(cpc, name, spec):
     W2 = cpc.cp_convolve_from_spectra(P, spec, "fp32")
     assert col_rel_err(W2.cpu().numpy(), W.double().cpu().numpy()) < 1e-6
     E3, G3 = cpc.cp_hartree_energy_from_factors(P, U, dev(g["c"]), W, "fp32", want_G=True)
-    assert E3.item() == E.item()
+    # from_factors slices W with each row's exact maximum; the energy path
+    # slices the Chebyshev rows with the exponent of the bound sum_k |d_k|
+    # (at most one step larger: a bit less of W's last digit), so the two
+    # agree to float32 slicing, not bits, and both meet the oracle bar
+    assert abs(E3.item() / E0 - 1) < EH_TOL
+    assert abs(E3.item() / E.item() - 1) < 1e-8
+    assert rel(G3.cpu().numpy(), G0) < 2e-6
     # energy from the spectra alone (Parseval), no V_H factors
     E2, G2 = cpc.cp_hartree_energy_from_spectra(P, spec, dev(g["c"]), want_G=True)
     assert abs(E2.item() / E0 - 1) < EH_TOL_SPECTRAL * kappa
@@ -146,11 +152,13 @@ def _tail_fraction(p, H):
 
 
 @pytest.mark.parametrize("name,spec", [CASES[2], CASES[3]])
-def test_banded_convolution(cpc, name, spec):
-    """Narrow kernel terms convolved as the finite sum over their band (Sec. 2.5,
-    Eq. conv): the chosen half-widths meet the tail bound of their W type, and
-    W agrees with the oracle with the band on (default), at the widest
-    instantiated widths, and off (every term through the FFT)."""
+def test_convolution_paths(cpc, name, spec):
+    """The three ways a kernel term is convolved (Sec. 2.5, Eq. conv): banded
+    direct sums for narrow terms (their half-widths meet the tail bound of the
+    W type), the separable Chebyshev form for smooth terms, and the FFT.  W
+    agrees with the oracle with every path on (the default), at the widest
+    limits, with the band alone and with the FFT alone; each path's own rows
+    are held to its bound."""
     n, b, M, g = _case(name, spec)
     h = 2 * b / n
     P = cpc.make_newton_kernel(n, b, M)
@@ -159,47 +167,55 @@ def test_banded_convolution(cpc, name, spec):
     U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
     W0 = ocp.convolve_factors(U0, P0)
     R_N = P0.shape[0]
+    paths = {}
     for prec, tau, hmax in (("fp32", 2.0 ** -32, 20), ("fp64", 2.0 ** -60, 24)):
-        hw = P.banding(prec)
-        assert (hw >= 0).any() and (hw < 0).any(), hw
-        for q in np.nonzero(hw >= 0)[0]:
+        hw, rk = P.conv_paths(prec)
+        band, smooth = hw >= 0, rk > 0
+        assert band.any() and smooth.any() and (~band & ~smooth).any(), (hw, rk)
+        assert not (band & smooth).any()
+        assert set(rk[smooth].tolist()) <= {4, 8, 12, 16}
+        for q in np.nonzero(band)[0]:
             assert hw[q] <= hmax and _tail_fraction(P0[q], hw[q]) <= tau
-        for q in np.nonzero(hw < 0)[0]:  # FFT terms: their band would be wider than hmax
-            too_wide = _tail_fraction(P0[q], hmax) > tau
-            lo_wide = prec == "fp32" and _tail_fraction(P0[q], (hmax + 1) // 2) > 2.0 ** -9
-            assert too_wide or lo_wide
-    banded64 = np.nonzero(P.banding("fp64") >= 0)[0]
-    banded32 = np.nonzero(P.banding("fp32") >= 0)[0]
+        paths[prec] = (np.nonzero(band)[0], np.nonzero(smooth)[0])
     rows = lambda qs: np.concatenate([k * R_N + qs for k in range(U0.shape[1])])
     results = {}
-    for mode in ("default", "widest", "off"):
-        if mode == "widest":
-            P.set_banding(32, 32)
-        elif mode == "off":
-            P.set_banding(-1, -1)
-            assert (P.banding("fp32") < 0).all() and (P.banding("fp64") < 0).all()
+    for mode, limits in (("default", None), ("widest", (32, 32, 16, 16)), ("band", (20, 24, -1, -1)),
+                         ("fft", (-1, -1, -1, -1))):
+        if limits is not None:
+            P.set_conv_paths(*limits)
+        if mode == "fft":
+            for prec in ("fp32", "fp64"):
+                hw, rk = P.conv_paths(prec)
+                assert (hw < 0).all() and (rk < 0).all()
         W64 = cpc.cp_convolve(P, U, "fp64").cpu().numpy()
         W32 = cpc.cp_convolve(P, U, "fp32").double().cpu().numpy()
-        assert col_rel_err(W64, W0) < TOL64
-        assert col_rel_err(W32, W0) < 2e-6
+        assert col_rel_err(W64, W0) < TOL64, mode
+        assert col_rel_err(W32, W0) < 2e-6, mode
         results[mode] = (W64, W32)
-    # the direct sums are float64-exact and, in float32, no worse than the
-    # rounding of U and of the taps (the transform's error is larger)
+    # each path against its own bound: banded float64 sums are exact up to
+    # rounding, Chebyshev float64 within 2^-46 of p_q[0] per column weight;
+    # float32 paths no worse than the rounding of U, the taps and the table
     W64, W32 = results["default"]
-    assert col_rel_err(W64[:, rows(banded64)], W0[:, rows(banded64)]) < 1e-14
-    assert col_rel_err(W32[:, rows(banded32)], W0[:, rows(banded32)]) < 3e-7
-    # banded and FFT-only factors agree to the float32 transform's rounding
-    assert col_rel_err(results["off"][1], W32) < 1e-6
-    # the energy path (W and its tensor-core slices in one pass), band off and on
+    (b64, s64), (b32, s32) = paths["fp64"], paths["fp32"]
+    assert col_rel_err(W64[:, rows(b64)], W0[:, rows(b64)]) < 1e-14
+    assert col_rel_err(W64[:, rows(s64)], W0[:, rows(s64)]) < 1e-12
+    assert col_rel_err(W32[:, rows(b32)], W0[:, rows(b32)]) < 3e-7
+    assert col_rel_err(W32[:, rows(s32)], W0[:, rows(s32)]) < 3e-7
+    # the paths and the FFT alone agree to the float32 transform's rounding
+    assert col_rel_err(results["fft"][1], W32) < 1e-6
+    # the energy path (W and its tensor-core slices in one pass per path)
     G0 = ocp.conv_matrices(U0, W0, R_N)
     E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
     kappa = cancellation(G0, g["c"], h)
-    for mx in (-1, 20):
-        P.set_banding(mx, 24)
+    for limits in ((-1, -1, -1, -1), (20, 24, 16, 16)):
+        P.set_conv_paths(*limits)
         E, W, G = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp32", want_G=True)
         assert abs(E.item() / E0 - 1) < EH_TOL * max(kappa, 1.0)
         assert rel(G.cpu().numpy(), G0) < 2e-6
         assert torch.equal(W, cpc.cp_convolve(P, U, "fp32"))
+        E64, W64e, G64 = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp64", want_G=True)
+        assert abs(E64.item() / E0 - 1) < TOL64
+        assert rel(G64.cpu().numpy(), G0) < TOL64
 
 
 @pytest.mark.parametrize("name,spec", [CASES[0], CASES[2], CASES[3]])
