@@ -69,7 +69,7 @@ static_assert(BM == BN, "the symmetric E_H tiling uses square 128 x 128 blocks")
 static_assert(BN == 128, "TMEM: 4 accumulators or 3 + the product over axes, 128 columns each");
 constexpr int READERS = 16;  // accumulator reader warps: lane quadrant x column quarter
 constexpr int BNW = BN / 4;  // columns read by one reader warp
-constexpr int THREADS = (READERS + 1) * 32;  // + one TMA/MMA warp
+constexpr int THREADS = (READERS + 2) * 32;  // + the MMA warp + the TMA warp
 constexpr uint32_t TMEM_COLS = 512;  // 3 groups x 128 columns, then the product over axes
 constexpr uint32_t PROD_COL = 3 * BN;
 // per-column exponents (3 axes) and coefficients; rows mode: the 4 column quarters of each row
@@ -314,7 +314,10 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, v
 // even CTA's full barrier; one thread of the even CTA issues the pair MMAs
 // (each CTA's TMEM receives its 128 rows x 128 columns).  In each CTA, warps
 // 0-15 read the accumulators (warp w: TMEM lanes 32 (w % 4).., columns
-// 32 (w / 4)..), warp 16 drives the copies.  GROUP consecutive chunks (256
+// 32 (w / 4)..), warp 16 issues the pair's MMAs (even CTA) and warp 17 drives
+// the copies (both CTAs): with copies and MMAs in one thread, the copy issue
+// and the waits for a stage to empty kept the MMA queue from staying full
+// (measured: 42% of that thread's time outside MMA issue).  GROUP consecutive chunks (256
 // or 512 cells) accumulate before each readout (S_0 and S_1 stay exact).
 // Barriers: full[stage] (even CTA: both halves landed), sfree[stage] (both
 // CTAs: the MMAs reading a stage finished), done (both CTAs: a group of
@@ -323,10 +326,10 @@ __device__ __forceinline__ bool wait_or_abort(uint64_t* mbar, uint32_t parity, v
 // GOUT (CPC_FP64_TC): the readers fold in float64 and write G (both
 // triangles); there is no product over axes and no E_H or row sum here.
 // register cap: each of the SM's four sub-partitions holds 16K registers and
-// a block's warps are spread over them, so the 17 warps put 5 on one: at most
-// 16384 / (5 x 32) = 102 registers per thread, 96 in steps of 8 (104 and 120
-// did not launch); with the cap ptxas spills 40-108 bytes instead of the
-// 144-168 bytes it chose under __launch_bounds__(544, 1)
+// a block's warps are spread over them, so the 18 warps put 5 on two of them:
+// at most 16384 / (5 x 32) = 102 registers per thread, 96 in steps of 8 (104
+// and 120 did not launch with 17 warps); with the cap ptxas spills 40-108
+// bytes instead of the 144-168 bytes it chose under __launch_bounds__
 template <class F, bool GOUT>
 __global__ void __cluster_dims__(2, 1, 1) __maxnreg__(96)
 gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, Args g) {
@@ -404,45 +407,39 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const uint32_t freeb_even = umma::mapa(umma::smem_u32(freeb), 0);
   double sum = 0.0;
 
-  if (warp == READERS) {
+  if (warp == READERS + 1) {
     if (lane == 0) {
-      // both CTAs' copies count on the even CTA's full barrier, which expects both halves
-      auto load = [&](int tt) {
+      // copies: chunk tt goes to stage tt % STAGES once the MMAs of chunk
+      // tt - STAGES (the stage's previous contents) finished; both CTAs'
+      // copies count on the even CTA's full barrier, which expects both halves
+      for (int tt = 0; tt < TT; ++tt) {
+        if (tt >= F::STAGES &&
+            !wait_or_abort(&sfree[tt % F::STAGES], ((tt - F::STAGES) / F::STAGES) & 1, abort_flag))
+          break;
         if (rank == 0) mbar_expect_tx(umma::smem_u32(&full[tt % F::STAGES]), 2 * F::STAGE_BYTES);
         issue_stage<F>(&mapA, &mapB, g, sbase, umma::mapa(umma::smem_u32(&full[tt % F::STAGES]), 0), tt, T, q,
                        r0, sb0);
-      };
-      if (rank == 0) {
-        for (int tt = 0; tt < F::STAGES - 1 && tt < TT; ++tt) load(tt);
-        for (int tt = 0; tt < TT; ++tt) {
-          const int t = tt % T, gi = (tt / T) * GA + t / GROUP;  // group of this chunk
-          const bool first = (t % GROUP == 0), last = (t % GROUP == GROUP - 1) || (t == T - 1);
-          if (!wait_or_abort(&full[tt % F::STAGES], (tt / F::STAGES) & 1, abort_flag)) break;
-          if (first && gi >= 1 && !wait_or_abort(freeb, (gi - 1) & 1, abort_flag)) break;
-          umma::fence_after();
-          issue_mmas<F>(sbase + (tt % F::STAGES) * F::STAGE_BYTES, tbase, first ? 0u : 1u);
-          umma::mma_commit_pair(&sfree[tt % F::STAGES]);
-          if (last) umma::mma_commit_pair(done);
-          const int tn = tt + F::STAGES - 1;
-          if (tn < TT) {
-            // stage tn % F::STAGES last held chunk tt - 1: wait until its MMAs finished
-            if (tt >= 1 && !wait_or_abort(&sfree[(tt - 1) % F::STAGES], ((tt - 1) / F::STAGES) & 1, abort_flag)) break;
-            load(tn);
-          }
-        }
-      } else {
-        for (int tt = 0; tt < F::STAGES - 1 && tt < TT; ++tt) load(tt);
-        for (int tt = 0; tt + F::STAGES - 1 < TT; ++tt) {
-          const int tn = tt + F::STAGES - 1;
-          if (tt >= 1 && !wait_or_abort(&sfree[(tt - 1) % F::STAGES], ((tt - 1) / F::STAGES) & 1, abort_flag)) break;
-          load(tn);
-        }
       }
       // drain: every commit of the pair has arrived on this CTA's stage barriers
       // before the CTA can leave
       if (!*abort_flag)
         for (int tt = (TT > F::STAGES ? TT - F::STAGES : 0); tt < TT; ++tt)
           if (!wait_or_abort(&sfree[tt % F::STAGES], (tt / F::STAGES) & 1, abort_flag)) break;
+    }
+  } else if (warp == READERS) {
+    if (lane == 0 && rank == 0) {
+      // the pair's MMAs: wait for a chunk's data (and, at the start of a group,
+      // for the readers to empty the accumulators), issue, commit
+      for (int tt = 0; tt < TT; ++tt) {
+        const int t = tt % T, gi = (tt / T) * GA + t / GROUP;  // group of this chunk
+        const bool first = (t % GROUP == 0), last = (t % GROUP == GROUP - 1) || (t == T - 1);
+        if (!wait_or_abort(&full[tt % F::STAGES], (tt / F::STAGES) & 1, abort_flag)) break;
+        if (first && gi >= 1 && !wait_or_abort(freeb, (gi - 1) & 1, abort_flag)) break;
+        umma::fence_after();
+        issue_mmas<F>(sbase + (tt % F::STAGES) * F::STAGE_BYTES, tbase, first ? 0u : 1u);
+        umma::mma_commit_pair(&sfree[tt % F::STAGES]);
+        if (last) umma::mma_commit_pair(done);
+      }
     }
   } else {
     const int quad = warp & 3, part = warp >> 2;
