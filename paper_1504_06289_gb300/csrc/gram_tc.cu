@@ -495,20 +495,24 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             lo32[cb * 8 + j] += e;
           }
         } else {
+          // two columns at a time in paired float32 instructions (the same
+          // roundings as the scalar fold: y - x is written fma(x, -1, y))
+          const float2 k8 = make_float2(1.0f / 256.0f, 1.0f / 256.0f);
+          const float2 k16 = make_float2(1.0f / 65536.0f, 1.0f / 65536.0f);
+          const float2 m1 = make_float2(-1.0f, -1.0f);
 #pragma unroll
           for (int j = 0; j < 8; j += 2) {
-            float e[2];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const float v = fmaf(v2[j + h], 1.0f / 65536.0f, fmaf(v1[j + h], 1.0f / 256.0f, v0[j + h]));
-              float& t = tot[cb * 8 + j + h];
-              const float sm = t + v, bb = sm - t;
-              e[h] = (t - (sm - bb)) + (v - bb);
-              t = sm;
-            }
+            const float2 v = __ffma2_rn(make_float2(v2[j], v2[j + 1]), k16,
+                                        __ffma2_rn(make_float2(v1[j], v1[j + 1]), k8, make_float2(v0[j], v0[j + 1])));
+            const float2 t = make_float2(tot[cb * 8 + j], tot[cb * 8 + j + 1]);
+            const float2 sm = __fadd2_rn(t, v);
+            const float2 bb = __ffma2_rn(t, m1, sm);                                   // sm - t
+            const float2 e = __fadd2_rn(__ffma2_rn(__ffma2_rn(bb, m1, sm), m1, t),      // t - (sm - bb)
+                                        __ffma2_rn(bb, m1, v));                         // + (v - bb)
+            tot[cb * 8 + j] = sm.x;
+            tot[cb * 8 + j + 1] = sm.y;
             __nv_bfloat162& L = lo[(cb * 8 + j) / 2];
-            const float2 f = __bfloat1622float2(L);
-            L = __floats2bfloat162_rn(f.x + e[0], f.y + e[1]);
+            L = __float22bfloat162_rn(__fadd2_rn(__bfloat1622float2(L), e));
           }
         }
       }
