@@ -30,12 +30,14 @@
  *           bulk convolutions in float32 (V_H factors stored as float) and
  *           the contractions with float32 products, float32 partial sums over
  *           chunks of 256 cells and float64 cross-tile reductions.  CPC_SPLIT
- *           keeps the convolutions in float64 (V_H factors stored as double,
- *           exactly as CPC_FP64) and runs the contractions with float32
+ *           keeps the convolutions at float64 accuracy (V_H factors stored as
+ *           double; the FFT terms in double-float arithmetic, pairs of
+ *           float32 carrying about 48 bits, within about 1e-13 of CPC_FP64's
+ *           float64 transform) and runs the contractions with float32
  *           products as in CPC_FP32, so E_H loses only the float32 rounding
  *           of its operands.  CPC_FP64_TC (cp_hartree_energy and
  *           cp_hartree_energy_from_factors only, n a multiple of 128) keeps
- *           the float64 convolutions of CPC_FP64 and runs the E_H contraction
+ *           the float64-accurate convolutions of CPC_SPLIT and runs the E_H contraction
  *           on the tensor cores: each float64 operand row is split exactly
  *           into five bf16 slices (40 bits of its row maximum), the slice
  *           pairs down to 2^-32 of the row scales are multiplied and summed
@@ -165,7 +167,9 @@ int cp_hadamard_pairs(int n, int n_in, int n_pairs, const int* pa, const int* pb
  * W[l][k*R_N + q][i] = sum_{j=0}^{n-1} U[l][k][j] * p_q[i - j],  i = 0..n-1,
  * for every axis l, rank k < R_f and kernel term q < R_N of a CONV kernel:
  * the factors of V_H = f * P_R.  U: [3][R_f][n] float64.  W: [3][R_f*R_N][n],
- * float64 for CPC_FP64 and CPC_SPLIT, float32 for CPC_FP32.  Implemented as length-2n real
+ * float64 for CPC_FP64, CPC_SPLIT and CPC_FP64_TC, float32 for CPC_FP32
+ * (CPC_SPLIT and CPC_FP64_TC: the FFT terms in double-float arithmetic,
+ * within about 1e-13 of CPC_FP64).  Implemented as length-2n real
  * FFT convolutions in the chosen precision (the spectra of U are formed in
  * float64), except for the narrow kernel terms, summed directly over their
  * band, and the smooth ones, evaluated in their separable Chebyshev form

@@ -58,6 +58,13 @@ struct cpc_kernel {
   int n_smooth[2] = {0, 0};
   std::vector<int> band_h[2];  // host copies of the half-widths and ranks
   std::vector<int> rank_k[2];
+  // double-float copies (hi, lo) of the float64 FFT tables for the float64
+  // forms other than CPC_FP64: pass twiddles [n] and half-angle factors
+  // [n+1] as float4 (re hi, re lo, im hi, im lo), kernel spectra [R_N][n+1]
+  // as float2
+  float4* d_twdf = nullptr;
+  float4* d_hwdf = nullptr;
+  float2* d_phatdf = nullptr;
   int* d_terms = nullptr;
   float2* d_taps32 = nullptr;
   double* d_taps64 = nullptr;
@@ -121,6 +128,12 @@ int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uh
 // (scratch: smooth_scratch_bytes, 256-byte aligned) and the FFT takes the rest
 int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W,
                           int precision, cudaStream_t s, const double* U = nullptr, void* scratch = nullptr);
+// CPC_SPLIT and CPC_FP64_TC: the FFT terms in double-float arithmetic from
+// the float64 spectra (converted in place to double-float pairs: the array
+// is consumed), W in float64; banded and smooth terms as for CPC_FP64
+int convolve_spectra_df(const cpc_kernel* P, int ncols, void* Uhat, double* W, cudaStream_t s, const double* U,
+                        void* scratch);
+int build_df_tables(cpc_kernel* P, cudaStream_t s);
 // float32 convolution operands (X1, X2) from float64 transforms of U, and the
 // convolutions from them (also writing the tensor-core contraction's W
 // slices and row exponents, n >= 128, in the _sliced form); U as above

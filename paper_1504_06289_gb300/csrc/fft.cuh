@@ -12,11 +12,25 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "dfloat.cuh"
+
 namespace cpc {
 
 template <typename T> struct cvec;
 template <> struct cvec<double> { using type = double2; };
 template <> struct cvec<float> { using type = float2; };
+template <> struct cvec<df> { using type = dfc; };
+
+// read-only loads of table entries (double-float entries as one 16-byte load)
+__device__ __forceinline__ float2 ld_tw(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ld_tw(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ dfc ld_tw(const dfc* p) {
+  const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  dfc r;
+  r.x = df(v.x, v.y);
+  r.y = df(v.z, v.w);
+  return r;
+}
 
 template <typename V> __device__ __forceinline__ V cmk(decltype(V::x) x, decltype(V::x) y) { V r; r.x = x; r.y = y; return r; }
 template <typename V> __device__ __forceinline__ V cadd(V a, V b) { return cmk<V>(a.x + b.x, a.y + b.y); }
@@ -151,7 +165,7 @@ struct FftPlan {
 // with a second table of the rounding errors, 2^24 (w^e - fl(w^e)) in fp16.
 template <int SIGN, typename V>
 __device__ __forceinline__ V twiddle(V x, const V* __restrict__ twp, const __half2* __restrict__ twl, int k) {
-  V w = __ldg(twp + k);
+  V w = ld_tw(twp + k);
   if constexpr (sizeof(decltype(V::x)) == 4) {
     const float2 l = __half22float2(__ldg(twl + k));
     const float lx = l.x * (1.0f / 16777216.0f), ly = (SIGN > 0 ? -l.y : l.y) * (1.0f / 16777216.0f);

@@ -321,6 +321,8 @@ int make_newton_kernel(int n, double b, int M, int kind, void* stream, cpc_kerne
     if (st != CPC_OK) { cleanup(); return st; }
     st = build_term_tables(P, kDefaultBand32, kDefaultBand64, kDefaultRank, kDefaultRank, s);
     if (st != CPC_OK) { cleanup(); return st; }
+    st = build_df_tables(P, s);
+    if (st != CPC_OK) { cleanup(); return st; }
   }
   e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: synchronize"); cleanup(); return st; }
@@ -390,6 +392,9 @@ int cpc_kernel_free(cpc_kernel* P) {
   cudaFree(P->d_hw64);
   cudaFree(P->d_hw32);
   cudaFree(P->d_specw32);
+  cudaFree(P->d_twdf);
+  cudaFree(P->d_hwdf);
+  cudaFree(P->d_phatdf);
   cudaFree(P->d_terms);
   cudaFree(P->d_taps32);
   cudaFree(P->d_taps64);

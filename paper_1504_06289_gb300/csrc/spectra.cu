@@ -850,6 +850,101 @@ cheb_eval_kernel(int n, int ncols, int R_N, int n_smooth, const void* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// The FFT terms of CPC_SPLIT and CPC_FP64_TC in double-float arithmetic
+// (dfloat.cuh): the same transform as conv_kernel<double> (float64 plan,
+// per-pass twiddles, half-angle step), with every table and the factor
+// spectra as double-float pairs, so the transform runs on the float32 pipes;
+// W is written in float64.  Error of the transform about 1e-13 relative
+// (13 levels of double-float operations), far below the float64 forms' 1e-10
+// bar; CPC_FP64 keeps the float64 transform.
+template <int LOGN>
+__global__ void __launch_bounds__(Geometry<LOGN, double>::threads, Geometry<LOGN, double>::min_blocks)
+conv_df_kernel(const dfc* __restrict__ Uhat, const df* __restrict__ phat, const dfc* __restrict__ hw,
+               const dfc* __restrict__ tw, double* __restrict__ W, int R_N, int ncols, const int* __restrict__ qlist,
+               int n_q) {
+  using V = dfc;
+  using G = Geometry<LOGN, double>;
+  using PL = typename G::PL;
+  constexpr int NC = PL::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int slot = threadIdx.x / PL::TPF;
+  const int t = threadIdx.x % PL::TPF;
+  V* sbuf = reinterpret_cast<V*>(smem_raw) + slot * padded_len(NC);
+  const df scale(1.0 / double(2 * NC));  // a power of two: exact
+  const long long n_groups = (long long)((ncols + G::slots - 1) / G::slots) * n_q;
+  const long long g_begin = n_groups * blockIdx.x / gridDim.x;
+  const long long g_end = n_groups * (blockIdx.x + 1) / gridDim.x;
+  for (long long g = g_begin; g < g_end; ++g) {
+    const long long cb = g / n_q;
+    const int qi = int(g - cb * n_q);
+    const int q = qlist ? __ldg(qlist + qi) : qi;
+    const long long colr = cb * G::slots + slot;
+    const bool active = colr < ncols;
+    const long long col = active ? colr : ncols - 1;
+    const long long item = col * R_N + q;
+    const V* Uc = Uhat + (size_t)col * (NC + 1);
+    const float2* pq = reinterpret_cast<const float2*>(phat) + (size_t)q * (NC + 1);
+    {
+      // Z'[f] = (A + B) + i e^{+2 pi i f/2n} (A - B), A = Y[f], B = conj Y[n-f], Y = Uhat * phat
+      V v[PL::B1][PL::R1];
+      constexpr int stride = NC / PL::R1, nbf = NC / (PL::R1 * PL::B1);
+#pragma unroll
+      for (int b = 0; b < PL::B1; ++b) {
+        const int j = b * nbf + t;
+#pragma unroll
+        for (int r = 0; r < PL::R1; ++r) {
+          const int f = j + r * stride;
+          const V uf = ld_tw(Uc + f), ur = ld_tw(Uc + (NC - f));
+          const float2 pf2 = __ldg(pq + f), pr2 = __ldg(pq + (NC - f));
+          const df pf(pf2.x, pf2.y), pr(pr2.x, pr2.y);
+          const V A = cmk<V>(uf.x * pf, uf.y * pf);
+          const V B = cmk<V>(ur.x * pr, -(ur.y * pr));
+          const V sm = cadd(A, B), d = csub(A, B);
+          const V wd = twiddle<+1>(d, hw, nullptr, f);  // e^{+i theta} (A - B)
+          v[b][r] = cmk<V>(sm.x - wd.y, sm.y + wd.x);
+        }
+        dft<PL::R1, +1>(v[b]);
+      }
+      pass_store<NC, PL::R1, PL::B1>(sbuf, v, t, 1);
+    }
+    __syncthreads();
+    middle_passes<LOGN, G::LOGP, +1>(sbuf, t, tw, nullptr);
+    {
+      V v[1][PL::P];
+      pass_compute<NC, PL::P, 1, +1>(sbuf, v, t, NC / PL::P, tw + pass_table_offset<LOGN, G::LOGP>(PL::NP - 1),
+                                     nullptr);
+      if (active) {
+        double* out = W + (size_t)item * NC;
+#pragma unroll
+        for (int r = 0; r < PL::P / 2; ++r) {
+          const int o = t + r * (NC / PL::P);  // complex output o -> reals 2o, 2o+1
+          const V w = cmk<V>(v[0][r].x * scale, v[0][r].y * scale);
+          __stcs(reinterpret_cast<double2*>(out + 2 * o), make_double2(w.x.to_double(), w.y.to_double()));
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// in place: double pairs -> (hi, lo) float pairs of the same 16 bytes
+__global__ void to_df_kernel(double2* __restrict__ a, long long count) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+       k += (long long)gridDim.x * blockDim.x) {
+    const double2 v = a[k];
+    const df x(v.x), y(v.y);
+    reinterpret_cast<float4*>(a)[k] = make_float4(x.hi, x.lo, y.hi, y.lo);
+  }
+}
+__global__ void to_df_copy_kernel(const double* __restrict__ src, float2* __restrict__ dst, long long count) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+       k += (long long)gridDim.x * blockDim.x) {
+    const df x(src[k]);
+    dst[k] = make_float2(x.hi, x.lo);
+  }
+}
+
+// ---------------------------------------------------------------------------
 template <typename K>
 int configure(K kern, size_t smem) {
   CPC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -1024,6 +1119,38 @@ int dispatch_conv(int logn, const cpc_kernel* P, int ncols, const void* Uhat, vo
       if (logn == LOGN) return launch_conv<T, LOGN, SLICE, XIN>(P, ncols, Uhat, W, so, s, qlist, n_q);
     }
     return dispatch_conv<T, LOGN + 1, SLICE, XIN>(logn, P, ncols, Uhat, W, so, s, qlist, n_q);
+  }
+}
+
+template <int LOGN>
+int launch_conv_df(const cpc_kernel* P, int ncols, const dfc* Uhat, double* W, cudaStream_t s, const int* qlist,
+                   int n_q) {
+  using G = Geometry<LOGN, double>;
+  const size_t smem = sizeof(dfc) * G::slots * padded_len(1 << LOGN);
+  auto kern = conv_df_kernel<LOGN>;
+  int st = configure(kern, smem);
+  if (st) return st;
+  int per_sm = 0;
+  CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::threads, smem));
+  const long long groups = (long long)((ncols + G::slots - 1) / G::slots) * n_q;
+  const long long grid = std::max(1LL, std::min(groups, (long long)std::max(1, per_sm) * sm_count()));
+  const int slot = timing_begin("conv_kernel", s);
+  kern<<<int(grid), G::threads, smem, s>>>(Uhat, reinterpret_cast<const df*>(P->d_phatdf),
+                                           reinterpret_cast<const dfc*>(P->d_hwdf),
+                                           reinterpret_cast<const dfc*>(P->d_twdf), W, P->R_N, ncols, qlist, n_q);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("conv_df_kernel");
+  return CPC_OK;
+}
+
+template <int LOGN>
+int dispatch_conv_df(int logn, const cpc_kernel* P, int ncols, const dfc* Uhat, double* W, cudaStream_t s,
+                     const int* qlist, int n_q) {
+  if constexpr (LOGN > kMaxLogN) {
+    return fail(CPC_ERR_UNSUPPORTED, "conv: n too large");
+  } else {
+    if (logn == LOGN) return launch_conv_df<LOGN>(P, ncols, Uhat, W, s, qlist, n_q);
+    return dispatch_conv_df<LOGN + 1>(logn, P, ncols, Uhat, W, s, qlist, n_q);
   }
 }
 
@@ -1373,6 +1500,45 @@ int convolve_operands32_sliced(const cpc_kernel* P, int R_f, const void* X, floa
   return run_conv<float, true, true>(P, 3 * R_f, X, W, so, s, U, scratch);
 }
 
+int convolve_spectra_df(const cpc_kernel* P, int ncols, void* Uhat, double* W, cudaStream_t s, const double* U,
+                        void* scratch) {
+  if (ilog2(P->n) > kMaxLogN) return fail(CPC_ERR_UNSUPPORTED, "conv: n too large");
+  if (!P->d_twdf) return fail(CPC_ERR_INVALID, "conv: kernel has no double-float tables");
+  const SliceOut none{nullptr, 0, nullptr, 0};
+  TermSplit ts = term_split(P, 1, U);
+  if (ts.n_smooth > 0 && !scratch) ts = term_split(P, 1, nullptr);
+  int st = CPC_OK;
+  if (ts.n_band > 0) {
+    st = launch_band<double, false>(P, ncols, U, W, none, ts, s);
+    if (st) return st;
+  }
+  if (ts.n_smooth > 0) {
+    st = launch_smooth<double, false>(P, ncols, U, W, none, ts, scratch, s);
+    if (st) return st;
+  }
+  if (ts.n_fft > 0) {
+    const long long bins = (long long)ncols * (P->n + 1);
+    to_df_kernel<<<int(std::min<long long>((bins + 255) / 256, 4096)), 256, 0, s>>>(static_cast<double2*>(Uhat), bins);
+    CPC_LAUNCH_CHECK("to_df_kernel");
+    st = dispatch_conv_df<kMinLogN>(ilog2(P->n), P, ncols, static_cast<const dfc*>(Uhat), W, s, ts.fft_q, ts.n_fft);
+  }
+  return st;
+}
+
+int build_df_tables(cpc_kernel* P, cudaStream_t s) {
+  const int n = P->n;
+  CPC_CUDA(cudaMalloc(&P->d_twdf, sizeof(float4) * size_t(n)));
+  CPC_CUDA(cudaMalloc(&P->d_hwdf, sizeof(float4) * size_t(n + 1)));
+  CPC_CUDA(cudaMalloc(&P->d_phatdf, sizeof(float2) * size_t(P->R_N) * (n + 1)));
+  to_df_copy_kernel<<<64, 256, 0, s>>>(reinterpret_cast<const double*>(P->d_twp64), reinterpret_cast<float2*>(P->d_twdf),
+                                      2LL * n);
+  to_df_copy_kernel<<<64, 256, 0, s>>>(reinterpret_cast<const double*>(P->d_hw64), reinterpret_cast<float2*>(P->d_hwdf),
+                                      2LL * (n + 1));
+  to_df_copy_kernel<<<64, 256, 0, s>>>(P->d_phat64, P->d_phatdf, (long long)P->R_N * (n + 1));
+  CPC_LAUNCH_CHECK("to_df_copy_kernel");
+  return CPC_OK;
+}
+
 size_t smooth_scratch_bytes(const cpc_kernel* P, int ncols) {
   // partial moments [ranges][ncols][kCheb] float64, item headers [ncols R_N]
   // int4, coefficients [ncols R_N][kCheb] (float64 at most)
@@ -1435,6 +1601,8 @@ int check_conv_args(const cpc_kernel* P, int R_f, const void* U, const void* W, 
 int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision, void* ws,
                  cudaStream_t s) {
   const int ncols = 3 * R_f;
+  // CPC_SPLIT and CPC_FP64_TC: FFT terms in double-float arithmetic
+  const bool dfloat = precision == CPC_SPLIT || precision == CPC_FP64_TC;
   precision = storage_precision(precision);
   unsigned char* w = static_cast<unsigned char*>(ws);
   double2* h64 = reinterpret_cast<double2*>(w);
@@ -1443,6 +1611,7 @@ int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int pre
   if (precision == CPC_FP64) {
     st = forward_spectra(P, ncols, U, h64, nullptr, s);
     if (st) return st;
+    if (dfloat) return convolve_spectra_df(P, ncols, h64, static_cast<double*>(W), s, U, scratch);
     return convolve_from_spectra(P, ncols, h64, W, precision, s, U, scratch);
   }
   // float32: the convolution operands straight from the float64 transforms

@@ -231,8 +231,12 @@ def test_convolution_and_energy_fp64tc(cpc, name, spec):
     U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
     E, W, G = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp64tc", want_G=True)
     assert W.dtype == torch.float64
-    assert torch.equal(W, cpc.cp_convolve(P, U, "fp64"))
+    assert torch.equal(W, cpc.cp_convolve(P, U, "fp64tc"))
     W0 = ocp.convolve_factors(U0, P0)
+    # FFT terms in double-float arithmetic: within the float64 bar of the
+    # oracle, and of the float64 transform to about 1e-13
+    assert col_rel_err(W.cpu().numpy(), W0) < TOL64
+    assert col_rel_err(W.cpu().numpy(), cpc.cp_convolve(P, U, "fp64").cpu().numpy()) < 1e-12
     G0 = ocp.conv_matrices(U0, W0, P0.shape[0])
     E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
     assert abs(E.item() / E0 - 1) < TOL64
@@ -314,6 +318,7 @@ def test_convolution_and_energy_split(cpc, name, spec):
     assert W.dtype == torch.float64
     W0 = ocp.convolve_factors(U0, P0)
     assert col_rel_err(W.cpu().numpy(), W0) < TOL64
+    assert torch.equal(W, cpc.cp_convolve(P, U, "split"))
     G0 = ocp.conv_matrices(U0, W0, P0.shape[0])
     E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
     assert abs(E.item() / E0 - 1) < EH_TOL * max(1.0, cancellation(G0, g["c"], h))
