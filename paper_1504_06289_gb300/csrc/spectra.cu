@@ -615,13 +615,23 @@ band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const 
 // its column are known (they are shared by all smooth terms).
 //   cheb_moments_kernel: m_l of every column;
 //   cheb_coef_kernel: d = C_q m per (column, term) in float64, stored in the
-//     W type, with a header per item: term, rank and, for the sliced float32
-//     path, the row exponent from the bound sum_k |d_k| >= max_i |W[i]|
-//     (|T_k| <= 1), so every CTA of a row slices with the same exponent;
+//     W type, with a record per item: its W and slice rows, its rank and,
+//     for the sliced float32 path, the slice scales of the row exponent from
+//     the bound sum_k |d_k| >= max_i |W[i]| (|T_k| <= 1), so every CTA of a
+//     row slices with the same exponent;
 //   cheb_eval_kernel: W[i] = sum_k d_k T_k(x_i/b) with the thread's table
 //     entries in registers, CTAs over 512-cell blocks x item ranges.
 constexpr int kCheb = 16;  // largest rank (ranks are 4, 8, 12 or 16)
 constexpr int kChebThreads = 256;
+// per (column, smooth term): where its W row and (sliced path) its slice row
+// start, its rank and slice scales, computed once by cheb_coef_kernel
+struct __align__(16) ChebItem {
+  long long w_off;  // element offset of the W row
+  long long s_off;  // element offset of the row in slice 0 (chunk 0)
+  int K;
+  float sc1, sc2;   // 2^(8-e) as two factors (slice_scales)
+  int pad;
+};
 
 // Moments as a small GEMM, Mom = T (kCheb x n) U^T (n x ncols): a CTA takes
 // 64 columns and a range of kChebCells cells (blockIdx.y), stages the table
@@ -702,14 +712,14 @@ cheb_moments_kernel(const double* __restrict__ U, int n, int ncols, const void* 
 
 // one CTA per column: the moments summed over the cell ranges once, then one
 // thread per smooth term j: d_k for k < K (zero up to kCheb) into
-// D[col n_smooth + j][kCheb], and the item's header (term q, rank K, row
-// exponent e)
+// D[col n_smooth + j][kCheb], the item's record, and (sliced path) the row
+// exponent of the contraction
 constexpr int kChebCoefThreads = 64;
 template <typename T, bool SLICE>
 __global__ void __launch_bounds__(kChebCoefThreads)
-cheb_coef_kernel(int n, int ncols, const int* __restrict__ qlist, int n_smooth, const int* __restrict__ kq,
+cheb_coef_kernel(int n, int ncols, int R_N, const int* __restrict__ qlist, int n_smooth, const int* __restrict__ kq,
                  const double* __restrict__ cheb, const double* __restrict__ Part, T* __restrict__ D,
-                 int4* __restrict__ Hdr) {
+                 ChebItem* __restrict__ items, SliceOut so) {
   const int col = blockIdx.x;
   __shared__ double m[kCheb];
   if (threadIdx.x < kCheb) {
@@ -731,12 +741,22 @@ cheb_coef_kernel(int n, int ncols, const int* __restrict__ qlist, int n_smooth, 
       D[k * kCheb + r] = T(d);
       bound += fabs(double(T(d)));
     }
-    int e = 0;
+    const long long item = (long long)col * R_N + q;
+    ChebItem it;
+    it.w_off = item * n;
+    it.s_off = 0;
+    it.K = K;
+    it.sc1 = it.sc2 = 1.0f;
+    it.pad = 0;
     if constexpr (SLICE) {
       // the float32 sum of K products of |T| <= 1 stays below bound (1 + K 2^-23)
-      e = balanced_exponent(__double2float_ru(bound * (1.0 + 0x1p-16)));
+      const int e = balanced_exponent(__double2float_ru(bound * (1.0 + 0x1p-16)));
+      so.expo[item] = e;
+      slice_scales(e, it.sc1, it.sc2);
+      const int l = col / so.R_f, srow = col - l * so.R_f;
+      it.s_off = ((long long)(l * R_N + q) * (n / 64) * so.R_f + srow) * 64;
     }
-    Hdr[k] = make_int4(q, K, e, 0);
+    items[k] = it;
   }
 }
 
@@ -779,11 +799,11 @@ __device__ __forceinline__ void cheb_pair(const typename cvec<T>::type* dk, cons
 constexpr int kChebBatch = 32;
 template <typename T, bool SLICE>
 __global__ void __launch_bounds__(kChebThreads, 2)
-cheb_eval_kernel(int n, int ncols, int R_N, int n_smooth, const void* __restrict__ tcheb, const T* __restrict__ D,
-                 const int4* __restrict__ Hdr, T* __restrict__ W, SliceOut so) {
+cheb_eval_kernel(int n, int ncols, int n_smooth, const void* __restrict__ tcheb, const T* __restrict__ D,
+                 const ChebItem* __restrict__ items, T* __restrict__ W, SliceOut so) {
   using V = typename cvec<T>::type;
   __shared__ __align__(16) T sd[kChebBatch][kCheb];
-  __shared__ int4 sh[kChebBatch];
+  __shared__ ChebItem sh[kChebBatch];
   const int i = blockIdx.x * 2 * kChebThreads + 2 * threadIdx.x;  // cells i, i+1
   const bool on = i < n;
   // this thread's table entries: T_k at cells i and i+1
@@ -802,49 +822,33 @@ cheb_eval_kernel(int n, int ncols, int R_N, int n_smooth, const void* __restrict
   }
   const long long n_items = (long long)ncols * n_smooth;
   const long long k0 = n_items * blockIdx.y / gridDim.y, k1 = n_items * (blockIdx.y + 1) / gridDim.y;
-  // (col, j) and, sliced, (axis l, row srow) of item k, advanced incrementally
-  int col = int(k0 / n_smooth), j = int(k0 - (long long)col * n_smooth);
-  int l = SLICE ? col / so.R_f : 0, srow = SLICE ? col - l * so.R_f : 0;
-  const int chunk_off = (i >> 6) * so.R_f * 64 + (i & 63);
+  const int chunk_off = SLICE ? (i >> 6) * so.R_f * 64 + (i & 63) : 0;
   for (long long kb = k0; kb < k1; kb += kChebBatch) {
     const int nb = int(min((long long)kChebBatch, k1 - kb));
     __syncthreads();  // the previous batch is consumed
     {
-      // d rows as 16-byte pieces, then the headers
+      // d rows and records as 16-byte pieces
       constexpr int PIECES = kCheb * sizeof(T) / 16;
+      constexpr int RP = sizeof(ChebItem) / 16;
       const uint4* src = reinterpret_cast<const uint4*>(D + kb * kCheb);
       uint4* dst = reinterpret_cast<uint4*>(&sd[0][0]);
       for (int x = threadIdx.x; x < nb * PIECES; x += kChebThreads) dst[x] = __ldg(src + x);
-      if (threadIdx.x < nb) sh[threadIdx.x] = __ldg(Hdr + kb + threadIdx.x);
+      const uint4* isrc = reinterpret_cast<const uint4*>(items + kb);
+      uint4* idst = reinterpret_cast<uint4*>(sh);
+      for (int x = threadIdx.x; x < nb * RP; x += kChebThreads) idst[x] = __ldg(isrc + x);
     }
     __syncthreads();
+    if (!on) continue;
     for (int b = 0; b < nb; ++b) {
-      const int4 h = sh[b];  // (q, K, e)
+      const ChebItem& h = sh[b];
       const V* dk = reinterpret_cast<const V*>(sd[b]);
       T w0, w1;
-      if (h.y <= 4) cheb_pair<T, 4>(dk, t32, t64, w0, w1);
-      else if (h.y <= 8) cheb_pair<T, 8>(dk, t32, t64, w0, w1);
-      else if (h.y <= 12) cheb_pair<T, 12>(dk, t32, t64, w0, w1);
+      if (h.K <= 4) cheb_pair<T, 4>(dk, t32, t64, w0, w1);
+      else if (h.K <= 8) cheb_pair<T, 8>(dk, t32, t64, w0, w1);
+      else if (h.K <= 12) cheb_pair<T, 12>(dk, t32, t64, w0, w1);
       else cheb_pair<T, 16>(dk, t32, t64, w0, w1);
-      if (on) {
-        const long long item = (long long)col * R_N + h.x;
-        __stcs(reinterpret_cast<V*>(W + (size_t)item * n + i), cmk<V>(w0, w1));
-        if constexpr (SLICE) {
-          float sc1, sc2;
-          slice_scales(h.z, sc1, sc2);
-          __nv_bfloat16* ob = so.out + ((long long)(l * R_N + h.x) * (n / 64) * so.R_f + srow) * 64;
-          slice_pair(float(w0), float(w1), sc1, sc2, ob + chunk_off, so.slice_stride);
-          if (threadIdx.x == 0 && blockIdx.x == 0) so.expo[item] = h.z;
-        }
-      }
-      if (++j == n_smooth) {
-        j = 0;
-        ++col;
-        if (SLICE && ++srow == so.R_f) {
-          srow = 0;
-          ++l;
-        }
-      }
+      __stcs(reinterpret_cast<V*>(W + h.w_off + i), cmk<V>(w0, w1));
+      if constexpr (SLICE) slice_pair(float(w0), float(w1), h.sc1, h.sc2, so.out + h.s_off + chunk_off, so.slice_stride);
     }
   }
 }
@@ -1162,8 +1166,8 @@ int launch_smooth(const cpc_kernel* P, int ncols, const double* U, T* W, const S
   unsigned char* sc = static_cast<unsigned char*>(scratch);
   double* Part = reinterpret_cast<double*>(sc);
   sc += align256(sizeof(double) * size_t(cheb_ranges(n)) * ncols * kCheb);
-  int4* Hdr = reinterpret_cast<int4*>(sc);
-  sc += align256(sizeof(int4) * size_t(ncols) * P->R_N);
+  ChebItem* recs = reinterpret_cast<ChebItem*>(sc);
+  sc += align256(sizeof(ChebItem) * size_t(ncols) * P->R_N);
   T* D = reinterpret_cast<T*>(sc);
   const void* tcheb = sizeof(T) == 4 ? static_cast<const void*>(P->d_tcheb32) : static_cast<const void*>(P->d_tcheb64);
   int slot = timing_begin("cheb_moments_kernel", s);
@@ -1173,8 +1177,8 @@ int launch_smooth(const cpc_kernel* P, int ncols, const double* U, T* W, const S
   CPC_LAUNCH_CHECK("cheb_moments_kernel");
   const long long items = (long long)ncols * ts.n_smooth;
   slot = timing_begin("cheb_coef_kernel", s);
-  cheb_coef_kernel<T, SLICE><<<ncols, kChebCoefThreads, 0, s>>>(n, ncols, ts.smooth_q, ts.n_smooth, ts.smooth_k,
-                                                                 P->d_cheb, Part, D, Hdr);
+  cheb_coef_kernel<T, SLICE><<<ncols, kChebCoefThreads, 0, s>>>(n, ncols, P->R_N, ts.smooth_q, ts.n_smooth,
+                                                                 ts.smooth_k, P->d_cheb, Part, D, recs, so);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("cheb_coef_kernel");
   slot = timing_begin("cheb_eval_kernel", s);
@@ -1183,7 +1187,7 @@ int launch_smooth(const cpc_kernel* P, int ncols, const double* U, T* W, const S
   CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kChebThreads, 0));
   const int bx = std::max(1, n / (2 * kChebThreads));
   const long long by = std::max(1LL, std::min(items, ((long long)std::max(1, per_sm) * sm_count() + bx - 1) / bx));
-  kern<<<dim3(bx, unsigned(by)), kChebThreads, 0, s>>>(n, ncols, P->R_N, ts.n_smooth, tcheb, D, Hdr, W, so);
+  kern<<<dim3(bx, unsigned(by)), kChebThreads, 0, s>>>(n, ncols, ts.n_smooth, tcheb, D, recs, W, so);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("cheb_eval_kernel");
   return CPC_OK;
@@ -1540,10 +1544,10 @@ int build_df_tables(cpc_kernel* P, cudaStream_t s) {
 }
 
 size_t smooth_scratch_bytes(const cpc_kernel* P, int ncols) {
-  // partial moments [ranges][ncols][kCheb] float64, item headers [ncols R_N]
-  // int4, coefficients [ncols R_N][kCheb] (float64 at most)
+  // partial moments [ranges][ncols][kCheb] float64, item records [ncols R_N],
+  // coefficients [ncols R_N][kCheb] (float64 at most)
   return align256(sizeof(double) * size_t(cheb_ranges(P->n)) * ncols * kCheb) +
-         align256(sizeof(int4) * size_t(ncols) * P->R_N) + align256(sizeof(double) * size_t(ncols) * P->R_N * kCheb);
+         align256(sizeof(ChebItem) * size_t(ncols) * P->R_N) + align256(sizeof(double) * size_t(ncols) * P->R_N * kCheb);
 }
 
 size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision) {
