@@ -39,6 +39,7 @@ struct cpc_kernel {
   void* d_twp32_lo = nullptr;  // __half2: 2^24 (exact - float32) of each float32 pass-table entry
   void* d_hw32_lo = nullptr;   // the same for the half-angle table
   void* d_pp32 = nullptr;      // float2 [R_N][n]: kernel-term pairs (p^[f], p^[n-f])
+  float4* d_opf32 = nullptr;   // [n]: float32 operand factors (1 + i e^{i theta_f}, 1 - i e^{i theta_f})
   double2* d_hw64 = nullptr;
   float2* d_hw32 = nullptr;
   // CONV only: Parseval weights d_q[2f+j] = w_f phat_q[f] / (2n), float32, [R_N][2(n+1)]

@@ -308,6 +308,7 @@ int make_newton_kernel(int n, double b, int M, int kind, void* stream, cpc_kerne
     if (e == cudaSuccess) e = cudaMalloc(&P->d_twp32_lo, 4 * size_t(n));
     if (e == cudaSuccess) e = cudaMalloc(&P->d_hw32_lo, 4 * size_t(n + 1));
     if (e == cudaSuccess) e = cudaMalloc(&P->d_pp32, sizeof(float2) * size_t(P->R_N) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&P->d_opf32, sizeof(float4) * size_t(n));
     if (e != cudaSuccess) { st = cuda_fail(e, "make_newton_kernel: FFT tables"); cleanup(); return st; }
     st = build_pass_twiddles(P, s);
     if (st != CPC_OK) { cleanup(); return st; }
@@ -389,6 +390,7 @@ int cpc_kernel_free(cpc_kernel* P) {
   cudaFree(P->d_twp32_lo);
   cudaFree(P->d_hw32_lo);
   cudaFree(P->d_pp32);
+  cudaFree(P->d_opf32);
   cudaFree(P->d_hw64);
   cudaFree(P->d_hw32);
   cudaFree(P->d_specw32);

@@ -155,7 +155,7 @@ spectra_kernel(int mode, const double* __restrict__ src, int ncols, double2* __r
 template <int LOGN>
 __global__ void __launch_bounds__(Geometry<LOGN, float>::threads)
 spectra32_kernel(const double* __restrict__ src, int ncols, const float2* __restrict__ hw,
-                 const __half2* __restrict__ hwl, const double2* __restrict__ hw64, const float2* __restrict__ tw,
+                 const __half2* __restrict__ hwl, const float4* __restrict__ opf, const float2* __restrict__ tw,
                  const __half2* __restrict__ twl, float4* __restrict__ out4) {
   using G = Geometry<LOGN, float>;
   using PL = typename G::PL;
@@ -208,9 +208,10 @@ spectra32_kernel(const double* __restrict__ src, int ncols, const float2* __rest
         return make_float2(0.5f * sm.x + 0.5f * wd.y, 0.5f * sm.y - 0.5f * wd.x);
       };
       auto operands = [&](int f, float2 Uf, float2 Un) {  // Un = U^[n-f]
-        const double2 E = hw64[f];                         // e^{-i theta}; e^{+i theta} = conj
-        const float2 a1 = make_float2(float(1.0 + E.y), float(E.x));   // 1 + i e^{+i theta}
-        const float2 a2 = make_float2(float(1.0 - E.y), float(-E.x));  // 1 - i e^{+i theta}
+        // (1 + i e^{+i theta}, 1 - i e^{+i theta}) formed in float64 and rounded
+        // once, from the table built with the kernel (operand_factor_kernel)
+        const float4 a = __ldg(opf + f);
+        const float2 a1 = make_float2(a.x, a.y), a2 = make_float2(a.z, a.w);
         const float2 X1 = cmul(Uf, a1), X2 = cmul(cconj(Un), a2);
         out4[(size_t)col * NC + f] = make_float4(X1.x, X1.y, X2.x, X2.y);
       };
@@ -1084,7 +1085,7 @@ int launch_spectra32(const double* src, int ncols, float4* o4, const cpc_kernel*
   const int groups = (ncols + G::slots - 1) / G::slots;
   const int grid = std::max(1, std::min(groups, std::max(1, per_sm) * sm_count()));
   const int slot = timing_begin("spectra_kernel", s);
-  kern<<<grid, G::threads, smem, s>>>(src, ncols, P->d_hw32, static_cast<const __half2*>(P->d_hw32_lo), P->d_hw64,
+  kern<<<grid, G::threads, smem, s>>>(src, ncols, P->d_hw32, static_cast<const __half2*>(P->d_hw32_lo), P->d_opf32,
                                       P->d_twp32, static_cast<const __half2*>(P->d_twp32_lo), o4);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("spectra32_kernel");
@@ -1232,6 +1233,16 @@ __global__ void pass_table_kernel(const V* __restrict__ flat, V* __restrict__ ou
   }
 }
 
+// the float32 operand factors of spectra32_kernel, per bin f < n:
+// (1 + i e^{+i theta_f}, 1 - i e^{+i theta_f}), e^{-i theta_f} = hw64[f],
+// formed in float64 and rounded once
+__global__ void operand_factor_kernel(const double2* __restrict__ hw64, int n, float4* __restrict__ opf) {
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n; f += gridDim.x * blockDim.x) {
+    const double2 E = hw64[f];  // e^{-i theta}; e^{+i theta} = conj
+    opf[f] = make_float4(float(1.0 + E.y), float(E.x), float(1.0 - E.y), float(-E.x));
+  }
+}
+
 __global__ void error_table_kernel(const double2* __restrict__ w64, const float2* __restrict__ w32, int count,
                                    __half2* __restrict__ err) {
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x)
@@ -1248,6 +1259,7 @@ int launch_pass_tables(cpc_kernel* P, cudaStream_t s) {
   pass_table_kernel<LOGN, L32><<<8, 256, 0, s>>>(P->d_tw32, P->d_twp32, P->d_tw64,
                                                  static_cast<__half2*>(P->d_twp32_lo));
   error_table_kernel<<<8, 256, 0, s>>>(P->d_hw64, P->d_hw32, P->n + 1, static_cast<__half2*>(P->d_hw32_lo));
+  operand_factor_kernel<<<8, 256, 0, s>>>(P->d_hw64, P->n, P->d_opf32);
   CPC_LAUNCH_CHECK("pass_table_kernel");
   return CPC_OK;
 }
