@@ -130,8 +130,8 @@ int forward_spectra(const cpc_kernel* P, int ncols, const double* U, double2* Uh
 int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void* W,
                           int precision, cudaStream_t s, const double* U = nullptr, void* scratch = nullptr);
 // CPC_SPLIT and CPC_FP64_TC: the FFT terms in double-float arithmetic from
-// the float64 spectra (converted in place to double-float pairs: the array
-// is consumed), W in float64; banded and smooth terms as for CPC_FP64
+// double-float factor spectra (spectra_df_kernel), W in float64; banded and
+// smooth terms as for CPC_FP64
 int convolve_spectra_df(const cpc_kernel* P, int ncols, void* Uhat, double* W, cudaStream_t s, const double* U,
                         void* scratch);
 int build_df_tables(cpc_kernel* P, cudaStream_t s);

@@ -932,15 +932,74 @@ conv_df_kernel(const dfc* __restrict__ Uhat, const df* __restrict__ phat, const 
   }
 }
 
-// in place: double pairs -> (hi, lo) float pairs of the same 16 bytes
-__global__ void to_df_kernel(double2* __restrict__ a, long long count) {
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
-       k += (long long)gridDim.x * blockDim.x) {
-    const double2 v = a[k];
-    const df x(v.x), y(v.y);
-    reinterpret_cast<float4*>(a)[k] = make_float4(x.hi, x.lo, y.hi, y.lo);
+// Forward transforms of the factor columns for the double-float forms: the
+// float64 plan of spectra_kernel (mode 0) in double-float arithmetic, the
+// bins X[f], f = 0..n, written as double-float pairs for conv_df_kernel.
+template <int LOGN>
+__global__ void __launch_bounds__(Geometry<LOGN>::threads)
+spectra_df_kernel(const double* __restrict__ src, int ncols, const dfc* __restrict__ hw, const dfc* __restrict__ tw,
+                  dfc* __restrict__ out) {
+  using V = dfc;
+  using G = Geometry<LOGN>;
+  using PL = typename G::PL;
+  constexpr int NC = PL::NC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V* sbuf = reinterpret_cast<V*>(smem_raw) + (threadIdx.x / PL::TPF) * padded_len(NC);
+  const int slot = threadIdx.x / PL::TPF;
+  const int t = threadIdx.x % PL::TPF;
+  for (int g = blockIdx.x; g * G::slots < ncols; g += gridDim.x) {
+    const int col = g * G::slots + slot;
+    const bool active = col < ncols;
+    const double* x = src + (size_t)(active ? col : ncols - 1) * NC;
+    {
+      V v[PL::B1][PL::R1];
+      constexpr int stride = NC / PL::R1, nbf = NC / (PL::R1 * PL::B1);
+#pragma unroll
+      for (int b = 0; b < PL::B1; ++b) {
+        const int j = b * nbf + t;
+#pragma unroll
+        for (int r = 0; r < PL::R1; ++r) {
+          const int f = j + r * stride;  // packed pair (x[2f], x[2f+1]), zero beyond n
+          V z;
+          if (2 * f < NC) {
+            const double2 a = *reinterpret_cast<const double2*>(x + 2 * f);
+            z.x = df(a.x);
+            z.y = df(a.y);
+          }
+          v[b][r] = z;
+        }
+        dft<PL::R1, -1>(v[b]);
+      }
+      pass_store<NC, PL::R1, PL::B1>(sbuf, v, t, 1);
+    }
+    __syncthreads();
+    middle_passes<LOGN, G::LOGP, -1>(sbuf, t, tw, nullptr);
+    {
+      V v[1][PL::P];
+      pass_compute<NC, PL::P, 1, -1>(sbuf, v, t, NC / PL::P, tw + pass_table_offset<LOGN, G::LOGP>(PL::NP - 1),
+                                     nullptr);
+      __syncthreads();
+      pass_store<NC, PL::P, 1>(sbuf, v, t, NC / PL::P);
+    }
+    __syncthreads();
+    if (active) {
+      // X[f] = (Z[f] + conj Z[n-f])/2 - (i/2) e^{-i theta} (Z[f] - conj Z[n-f]), f = 0..n
+      for (int f = t; f <= NC; f += PL::TPF) {
+        const V Zf = sbuf[pad_index(f & (NC - 1))];
+        const V Zr = cconj(sbuf[pad_index((NC - f) & (NC - 1))]);
+        const V sm = cadd(Zf, Zr), d = csub(Zf, Zr);
+        const V wd = cmul(ld_tw(hw + f), d);
+        const df h(0.5f, 0.0f);
+        V X;
+        X.x = h * (sm.x + wd.y);
+        X.y = h * (sm.y - wd.x);
+        reinterpret_cast<float4*>(out)[(size_t)col * (NC + 1) + f] = make_float4(X.x.hi, X.x.lo, X.y.hi, X.y.lo);
+      }
+    }
+    __syncthreads();
   }
 }
+
 __global__ void to_df_copy_kernel(const double* __restrict__ src, float2* __restrict__ dst, long long count) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
        k += (long long)gridDim.x * blockDim.x) {
@@ -1070,6 +1129,35 @@ int dispatch_spectra(int logn, int mode, const double* src, int ncols, double2* 
   } else {
     if (logn == LOGN) return launch_spectra<LOGN>(mode, src, ncols, o64, o32, r64, r32, P, s, o4);
     return dispatch_spectra<LOGN + 1>(logn, mode, src, ncols, o64, o32, r64, r32, P, s, o4);
+  }
+}
+
+template <int LOGN>
+int launch_spectra_df(const double* src, int ncols, dfc* out, const cpc_kernel* P, cudaStream_t s) {
+  using G = Geometry<LOGN>;
+  const size_t smem = sizeof(dfc) * G::slots * padded_len(1 << LOGN);
+  auto kern = spectra_df_kernel<LOGN>;
+  int st = configure(kern, smem);
+  if (st) return st;
+  int per_sm = 0;
+  CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G::threads, smem));
+  const int groups = (ncols + G::slots - 1) / G::slots;
+  const int grid = std::max(1, std::min(groups, std::max(1, per_sm) * sm_count()));
+  const int slot = timing_begin("spectra_kernel", s);
+  kern<<<grid, G::threads, smem, s>>>(src, ncols, reinterpret_cast<const dfc*>(P->d_hwdf),
+                                      reinterpret_cast<const dfc*>(P->d_twdf), out);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("spectra_df_kernel");
+  return CPC_OK;
+}
+
+template <int LOGN>
+int dispatch_spectra_df(int logn, const double* src, int ncols, dfc* out, const cpc_kernel* P, cudaStream_t s) {
+  if constexpr (LOGN > kMaxLogN) {
+    return fail(CPC_ERR_UNSUPPORTED, "spectra: n too large");
+  } else {
+    if (logn == LOGN) return launch_spectra_df<LOGN>(src, ncols, out, P, s);
+    return dispatch_spectra_df<LOGN + 1>(logn, src, ncols, out, P, s);
   }
 }
 
@@ -1532,12 +1620,8 @@ int convolve_spectra_df(const cpc_kernel* P, int ncols, void* Uhat, double* W, c
     st = launch_smooth<double, false>(P, ncols, U, W, none, ts, scratch, s);
     if (st) return st;
   }
-  if (ts.n_fft > 0) {
-    const long long bins = (long long)ncols * (P->n + 1);
-    to_df_kernel<<<int(std::min<long long>((bins + 255) / 256, 4096)), 256, 0, s>>>(static_cast<double2*>(Uhat), bins);
-    CPC_LAUNCH_CHECK("to_df_kernel");
+  if (ts.n_fft > 0)
     st = dispatch_conv_df<kMinLogN>(ilog2(P->n), P, ncols, static_cast<const dfc*>(Uhat), W, s, ts.fft_q, ts.n_fft);
-  }
   return st;
 }
 
@@ -1624,10 +1708,15 @@ int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int pre
   double2* h64 = reinterpret_cast<double2*>(w);
   int st;
   void* scratch = w + conv_spectra_bytes(P, R_f, precision);
+  if (precision == CPC_FP64 && dfloat) {
+    // factor spectra as double-float pairs in the float64-spectra part of the workspace
+    st = dispatch_spectra_df<kMinLogN>(ilog2(P->n), U, ncols, reinterpret_cast<dfc*>(h64), P, s);
+    if (st) return st;
+    return convolve_spectra_df(P, ncols, h64, static_cast<double*>(W), s, U, scratch);
+  }
   if (precision == CPC_FP64) {
     st = forward_spectra(P, ncols, U, h64, nullptr, s);
     if (st) return st;
-    if (dfloat) return convolve_spectra_df(P, ncols, h64, static_cast<double*>(W), s, U, scratch);
     return convolve_from_spectra(P, ncols, h64, W, precision, s, U, scratch);
   }
   // float32: the convolution operands straight from the float64 transforms
