@@ -80,6 +80,18 @@ struct cpc_kernel {
 
 namespace cpc {
 
+// where a convolution writes the tensor-core contraction's slices of W, in
+// the chunk-blocked layout of its form: float32 W, three bf16 slices in
+// 64-cell chunks [3][3 R_N][n/64][R_f][64]; float64 W (CPC_FP64_TC), five
+// weighted bf16 slices in 32-cell chunks [5][3 R_N][n/32][R_f][32]; and the
+// row exponents [3 R_f R_N] (row = col R_N + q)
+struct SliceRows {
+  __nv_bfloat16* out;
+  long long slice_stride;  // elements between slices
+  int* expo;
+  int R_f;
+};
+
 // error reporting (thread-local message)
 int fail(int status, const std::string& msg);
 
@@ -133,7 +145,12 @@ int convolve_from_spectra(const cpc_kernel* P, int ncols, const void* Uhat, void
 // double-float factor spectra (spectra_df_kernel), W in float64; banded and
 // smooth terms as for CPC_FP64
 int convolve_spectra_df(const cpc_kernel* P, int ncols, void* Uhat, double* W, cudaStream_t s, const double* U,
-                        void* scratch);
+                        void* scratch, const SliceRows* so64 = nullptr);
+bool conv_slices64_supported(const cpc_kernel* P);
+// cp_convolve after argument checks; so64 (CPC_FP64_TC only, n >= 128): also
+// write W's five-digit slices and row exponents for the contraction
+int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision, void* ws, cudaStream_t s,
+                 const SliceRows* so64 = nullptr);
 int build_df_tables(cpc_kernel* P, cudaStream_t s);
 // float32 convolution operands (X1, X2) from float64 transforms of U, and the
 // convolutions from them (also writing the tensor-core contraction's W
@@ -195,8 +212,11 @@ int* tc_status_ptr(const cpc_kernel* P, int R_f, void* ws);
 size_t tc64_partials(int R_f, int R_N);
 size_t tc64_workspace(const cpc_kernel* P, int R_f);
 int* tc64_status_ptr(const cpc_kernel* P, int R_f, void* ws);
+// w_sliced: the convolution already wrote W's slices and row exponents where
+// tc64_w_slices points
 int launch_eh_tc64(const cpc_kernel* P, int R_f, const double* U, const double* W, const double* c, double* G,
-                   double* partial, void* ws, cudaStream_t s);
+                   double* partial, void* ws, cudaStream_t s, bool w_sliced = false);
+SliceRows tc64_w_slices(const cpc_kernel* P, int R_f, void* ws);
 // tensor-core Coulomb-matrix rows (M item factors against Ns rho factors)
 size_t tc_rows_workspace(const cpc_kernel* P, int M, int Ns);
 size_t tc_rows_groups(const cpc_kernel* P, int Ns);

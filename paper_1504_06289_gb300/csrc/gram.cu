@@ -462,8 +462,6 @@ __global__ void adjoint_coef_kernel(int R_f, int R_N, const double* __restrict__
 size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision);
 int check_conv_args(const cpc_kernel* P, int R_f, const void* U, const void* W, int precision,
                     void* ws, size_t ws_bytes, const char* who);
-int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision, void* ws,
-                 cudaStream_t s);
 
 static int tiles(int x) { return (x + TM - 1) / TM; }
 
@@ -563,6 +561,21 @@ int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doub
     if (st) return st;
     finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, (long long)tc_partials(R_f, P->R_N), P->h * P->h * P->h, E_H,
                                            tc_status_ptr(P, R_f, tws));
+    CPC_LAUNCH_CHECK("finalize_sum_kernel");
+    return CPC_OK;
+  }
+  if (precision == CPC_FP64_TC && tc_supported(P) && conv_slices64_supported(P)) {
+    // likewise for the float64 form: the convolution writes W's five-digit
+    // slices and row exponents into the contraction's workspace
+    void* tws = static_cast<unsigned char*>(cws) + align256(sizeof(double) * eh_partials(P, R_f));
+    const SliceRows so = tc64_w_slices(P, R_f, tws);
+    int st = run_convolve(P, R_f, U, W, precision, ws, s, &so);
+    if (st) return st;
+    double* partial = static_cast<double*>(cws);
+    st = launch_eh_tc64(P, R_f, U, static_cast<const double*>(W), c, G, partial, tws, s, true);
+    if (st) return st;
+    finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, (long long)tc64_partials(R_f, P->R_N), P->h * P->h * P->h, E_H,
+                                           tc64_status_ptr(P, R_f, tws));
     CPC_LAUNCH_CHECK("finalize_sum_kernel");
     return CPC_OK;
   }

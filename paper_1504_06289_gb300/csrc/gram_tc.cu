@@ -57,6 +57,7 @@
 #include <type_traits>
 
 #include "cpc_internal.h"
+#include "slice64.cuh"
 #include "umma.cuh"
 
 namespace cpc {
@@ -653,7 +654,7 @@ __global__ void __launch_bounds__(256) row_exponent64_kernel(const double* __res
     if (threadIdx.x == 0) {
       int mm = red[0];
       for (int w = 1; w < 8; ++w) mm = max(mm, red[w]);
-      expo[row] = mm ? mm - 1022 : 0;
+      expo[row] = row_exponent64(mm);
     }
     __syncthreads();
   }
@@ -672,7 +673,7 @@ template <int BKC>
 __global__ void __launch_bounds__(256) slice64_kernel(const double* __restrict__ src, long long rows, int n, int R_f,
                                                       int R_N, __nv_bfloat16* __restrict__ out, long long slice_stride,
                                                       const int* __restrict__ expo) {
-  constexpr int NS = 5;
+  static_assert(BKC == kSlice64Cells, "the slice layout's chunk");
   const int T = n / BKC;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
     // the row's place in the chunk-blocked layout, once per row
@@ -686,29 +687,7 @@ __global__ void __launch_bounds__(256) slice64_kernel(const double* __restrict__
     for (int p = threadIdx.x; p < n / 2; p += 256) {
       const int i = 2 * p;  // even cell: the pair stays in one chunk
       const double2 v = x[p];
-      float t[2][NS];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(h ? v.y : v.x));
-        const int ex = int((bits >> 52) & 0x7FF);
-        const int sh = 1035 + e - ex;
-        long long A = 0;
-        if (ex != 0 && sh < 64) {
-          const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-          A = (long long)((mant + (1ull << (sh - 1))) >> sh);
-        }
-        const float sgn = (bits >> 63) ? -1.0f : 1.0f;
-        const unsigned long long B = (unsigned long long)A + 0x80808080ull;
-        const unsigned lo = (unsigned)B;
-        t[h][0] = sgn * float(int(B >> 32));
-#pragma unroll
-        for (int j = 1; j < NS; ++j)
-          t[h][j] = sgn * float(int((lo >> (8 * (NS - 1 - j))) & 255u) - 128) * __int_as_float((127 - 8 * j) << 23);
-      }
-      __nv_bfloat16* o = ob + (i / BKC) * (long long)R_f * BKC + (i % BKC);
-#pragma unroll
-      for (int j = 0; j < NS; ++j)
-        *reinterpret_cast<__nv_bfloat162*>(o + j * slice_stride) = __floats2bfloat162_rn(t[0][j], t[1][j]);
+      slice64_pair(v.x, v.y, e, ob + (i / BKC) * (long long)R_f * BKC + (i % BKC), slice_stride);
     }
   }
 }
@@ -917,8 +896,15 @@ int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, 
 // CPC_FP64_TC: five weighted slices of the float64 U and W, the convolution
 // matrices in float64 (into G, or the workspace's G when G is NULL), then
 // partial[q R_f + r] = c_r sum_{s >= r} (1 or 2) c_s prod_l G_l[q][r][s]
+SliceRows tc64_w_slices(const cpc_kernel* P, int R_f, void* ws) {
+  const TcLayout L = tc_layout(P, R_f, R_f, tc::Form64::NS, true);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  return SliceRows{reinterpret_cast<__nv_bfloat16*>(w + L.off_b), (long long)(L.b / tc::Form64::NS),
+                   reinterpret_cast<int*>(w + L.off_eb), R_f};
+}
+
 int launch_eh_tc64(const cpc_kernel* P, int R_f, const double* U, const double* W, const double* c, double* G,
-                   double* partial, void* ws, cudaStream_t s) {
+                   double* partial, void* ws, cudaStream_t s, bool w_sliced) {
   const int n = P->n, R_N = P->R_N;
   const TcLayout L = tc_layout(P, R_f, R_f, tc::Form64::NS, true);
   unsigned char* w = static_cast<unsigned char*>(ws);
@@ -926,9 +912,11 @@ int launch_eh_tc64(const cpc_kernel* P, int R_f, const double* U, const double* 
   int st = tc::launch_slice64(U, 3LL * R_f, n, R_f, 1, reinterpret_cast<__nv_bfloat16*>(w),
                               (long long)(L.a / tc::Form64::NS), reinterpret_cast<int*>(w + L.off_ea), s);
   if (st) return st;
-  st = tc::launch_slice64(W, 3LL * R_f * R_N, n, R_f, R_N, reinterpret_cast<__nv_bfloat16*>(w + L.off_b),
-                          (long long)(L.b / tc::Form64::NS), reinterpret_cast<int*>(w + L.off_eb), s);
-  if (st) return st;
+  if (!w_sliced) {  // else the convolution already wrote them
+    st = tc::launch_slice64(W, 3LL * R_f * R_N, n, R_f, R_N, reinterpret_cast<__nv_bfloat16*>(w + L.off_b),
+                            (long long)(L.b / tc::Form64::NS), reinterpret_cast<int*>(w + L.off_eb), s);
+    if (st) return st;
+  }
   double* Gd = G ? G : reinterpret_cast<double*>(w + L.off_g);
   st = launch_tc_kernel<tc::Form64, true>(P, R_f, R_f, L, w, c, c, Gd, partial, s, 0, 1);
   if (st) return st;

@@ -24,6 +24,7 @@
 
 #include "cpc_internal.h"
 #include "fft.cuh"
+#include "slice64.cuh"
 
 namespace cpc {
 
@@ -225,16 +226,13 @@ spectra32_kernel(const double* __restrict__ src, int ncols, const float2* __rest
   }
 }
 
-// Optional second output of the float32 convolution: the exact bf16 slices
-// of each output row (the operand format of the tensor-core contraction,
-// csrc/gram_tc.cu), written in the same chunk-blocked layout and with the
-// same arithmetic as slice_rows_kernel, so the result is bit-identical.
-struct SliceOut {
-  __nv_bfloat16* out;      // [3 slices][3 R_N][n/64][R_f][64]
-  long long slice_stride;  // elements between slices
-  int* expo;               // [3 R_f R_N] row exponents, row = item
-  int R_f;
-};
+// Optional second output of the convolution: the exact bf16 slices of each
+// output row (the operand format of the tensor-core contraction,
+// csrc/gram_tc.cu), written in the chunk-blocked layout (SliceRows) and with
+// the same arithmetic as slice_rows_kernel (float32 W) or slice64_kernel
+// (float64 W), so the result is bit-identical where the row exponent is the
+// same.
+using SliceOut = SliceRows;
 
 // 2^(8-e) as two normal powers of two (here e is in [-147, 129]): two exact
 // multiplies per value instead of ldexpf (a value whose first product would
@@ -317,6 +315,52 @@ __device__ __forceinline__ void slice_epilogue(const float2* v, const SliceOut& 
   for (int r = 0; r < PL::P / 2; ++r) {
     const int i = 2 * (t + r * (NC / PL::P));  // even: the pair (i, i+1) stays in one 64-cell chunk
     slice_pair(v[r].x, v[r].y, sc1, sc2, ob + (long long)(i >> 6) * so.R_f * 64 + (i & 63), so.slice_stride);
+  }
+}
+
+// The float64 counterpart (double-float transforms of CPC_FP64_TC): the row's
+// largest biased exponent field over the TPF threads of one transform (from
+// the values in registers), then the five digits of each of this thread's
+// outputs (reals 2o, 2o+1) in the 32-cell chunks of the float64 form.  The
+// digits are taken in a loop that is not unrolled, from the values staged in
+// the transform's own shared buffer `sb` (free once every thread has passed
+// the barrier at entry): unrolled over the outputs, the digit code overflows
+// the instruction cache of the (fully unrolled) transform.
+template <typename PL>
+__device__ __forceinline__ void slice64_epilogue(const double2* v, double2* sb, const SliceOut& so, long long item,
+                                                 bool active, int slot, int t, int R_N) {
+  constexpr int NC = PL::NC, TPF = PL::TPF, C = kSlice64Cells;
+  __shared__ int red64[32];
+  int m = 0;
+#pragma unroll
+  for (int r = 0; r < PL::P / 2; ++r) m = max(m, max(biased_exponent64(v[r].x), biased_exponent64(v[r].y)));
+  constexpr int LW = TPF < 32 ? TPF : 32;
+#pragma unroll
+  for (int o = LW / 2; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __syncthreads();  // every thread's last reads of the transform buffer are done
+#pragma unroll
+  for (int r = 0; r < PL::P / 2; ++r) sb[t + r * (NC / PL::P)] = v[r];
+  if constexpr (TPF > 32) {
+    constexpr int WPF = TPF / 32;
+    if ((threadIdx.x & 31) == 0) red64[threadIdx.x >> 5] = m;
+    __syncthreads();
+    m = red64[slot * WPF];
+#pragma unroll
+    for (int w = 1; w < WPF; ++w) m = max(m, red64[slot * WPF + w]);
+    __syncthreads();
+  }
+  if (!active) return;
+  const int e = row_exponent64(m);
+  if (t == 0) so.expo[item] = e;
+  const long long col = item / R_N;
+  const int q = int(item - col * R_N);
+  const int l = int(col / so.R_f), srow = int(col - (long long)l * so.R_f);
+  __nv_bfloat16* ob = so.out + ((long long)(l * R_N + q) * (NC / C) * so.R_f + srow) * C;
+#pragma unroll 1
+  for (int r = 0; r < PL::P / 2; ++r) {
+    const int o = t + r * (NC / PL::P), i = 2 * o;
+    const double2 x = sb[o];  // this thread's own entry
+    slice64_pair(x.x, x.y, e, ob + (long long)(i / C) * so.R_f * C + (i % C), so.slice_stride);
   }
 }
 
@@ -447,7 +491,9 @@ conv_kernel(const typename cvec<T>::type* __restrict__ Uhat, const T* __restrict
 // contiguous range of (column, term) items, stages each column once in
 // shared memory (rounded to T, as the FFT path rounds its input, inside a
 // zero border of kBandHalo cells) and writes W, and with SLICE the bf16
-// slices and row exponent with the same arithmetic as the FFT path.
+// slices and row exponent: float32 W with the FFT path's arithmetic (row
+// maximum over the CTA); float64 W with the row exponent bounded from the
+// taps and the column (BandSlice64), so the digits are written as computed.
 constexpr int kBandHalo = 32;          // largest half-width and the zero border
 constexpr int kBandTaps = kBandHalo + 1;
 constexpr int kBandThreads = 256;
@@ -463,11 +509,24 @@ __device__ __forceinline__ decltype(V::x) win_el(const V* win, int d) {
   return (d & 1) ? win[d >> 1].y : win[d >> 1].x;
 }
 
+// Where a banded row's float64 slices go (CPC_FP64_TC): its slice row, and the
+// largest |U| of its column, from which the row exponent is bounded before
+// any output exists: |W[i]| <= sum_m |p_q[|m|]| max|U|, so each output pair is
+// sliced as it is computed (no row reduction, no second pass)
+struct BandSlice64 {
+  __nv_bfloat16* ob;  // the row in slice 0, chunk 0
+  long long stride;   // elements between slices
+  int R_f;
+  int* expo;          // the row's exponent
+  double umax;
+};
+
 // outputs i, i+1 for every even i = 2 threadIdx.x + 2 kBandThreads j < n;
-// returns this thread's largest |W| (SLICE)
+// float32 SLICE: also kept in ws, and this thread's largest |W| returned;
+// float64 SLICE: the digits written as computed
 template <typename T, int H, bool SLICE>
-__device__ __forceinline__ float band_rows(const T* __restrict__ us, int n, const void* __restrict__ taps_q,
-                                           T* __restrict__ w, float* __restrict__ ws) {
+__device__ __forceinline__ T band_rows(const T* __restrict__ us, int n, const void* __restrict__ taps_q,
+                                       T* __restrict__ w, T* __restrict__ ws, const BandSlice64& b64) {
   using V = typename cvec<T>::type;
   constexpr int H2 = (H + 1) & ~1;  // the window starts at an even cell
   constexpr int HL = (H + 1) / 2;   // float32: taps with their lo part
@@ -486,7 +545,17 @@ __device__ __forceinline__ float band_rows(const T* __restrict__ us, int n, cons
 #pragma unroll
     for (int m = 0; m <= H; ++m) ph[m] = __ldg(tp + m);
   }
-  float mx = 0.0f;
+  int e64 = 0;
+  if constexpr (SLICE && sizeof(T) == 8) {
+    // the float64 sum of 2H + 1 products stays below the bound times
+    // (1 + (2H + 2) 2^-53); 2^e above the bound times (1 + 2^-40)
+    double S = fabs(ph[0]);
+#pragma unroll
+    for (int m = 1; m <= H; ++m) S += 2.0 * fabs(ph[m]);
+    e64 = row_exponent64(biased_exponent64(S * b64.umax * (1.0 + 0x1p-40)));
+    if (threadIdx.x == 0) *b64.expo = e64;
+  }
+  T mx = T(0);
   for (int i = 2 * threadIdx.x; i < n; i += 2 * kBandThreads) {
     // cells i - H2 .. i + H2 + 1
     const V* u2 = reinterpret_cast<const V*>(us + kBandHalo + i - H2);
@@ -521,20 +590,26 @@ __device__ __forceinline__ float band_rows(const T* __restrict__ us, int n, cons
     }
     __stcs(reinterpret_cast<V*>(w + i), cmk<V>(a0, a1));
     if constexpr (SLICE) {
-      *reinterpret_cast<float2*>(ws + i) = make_float2(float(a0), float(a1));
-      mx = fmaxf(mx, fmaxf(fabsf(float(a0)), fabsf(float(a1))));
+      if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<V*>(ws + i) = cmk<V>(a0, a1);
+        mx = fmaxf(mx, fmaxf(fabsf(a0), fabsf(a1)));
+      } else {
+        constexpr int C = kSlice64Cells;
+        slice64_pair(a0, a1, e64, b64.ob + (long long)(i / C) * b64.R_f * C + (i % C), b64.stride);
+      }
     }
   }
   return mx;
 }
 
 template <typename T, bool SLICE, int K = 0>
-__device__ __forceinline__ float band_dispatch(int h, const T* us, int n, const void* tq, T* w, float* ws) {
+__device__ __forceinline__ T band_dispatch(int h, const T* us, int n, const void* tq, T* w, T* ws,
+                                           const BandSlice64& b64) {
   if constexpr (K == kBandNumWidths - 1) {
-    return band_rows<T, band_width(K), SLICE>(us, n, tq, w, ws);  // the widest (and any unknown) width
+    return band_rows<T, band_width(K), SLICE>(us, n, tq, w, ws, b64);  // the widest (and any unknown) width
   } else {
-    if (h == band_width(K)) return band_rows<T, band_width(K), SLICE>(us, n, tq, w, ws);
-    return band_dispatch<T, SLICE, K + 1>(h, us, n, tq, w, ws);
+    if (h == band_width(K)) return band_rows<T, band_width(K), SLICE>(us, n, tq, w, ws, b64);
+    return band_dispatch<T, SLICE, K + 1>(h, us, n, tq, w, ws, b64);
   }
 }
 
@@ -548,8 +623,10 @@ band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const 
   using V = typename cvec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* us = reinterpret_cast<T*>(smem_raw);  // [kBandHalo + n + kBandHalo]
-  float* ws = reinterpret_cast<float*>(smem_raw + sizeof(T) * (size_t(n) + 2 * kBandHalo));  // SLICE: [n]
-  __shared__ float red[2][kBandThreads / 32];
+  T* ws = reinterpret_cast<T*>(smem_raw + sizeof(T) * (size_t(n) + 2 * kBandHalo));  // SLICE, float32: [n]
+  __shared__ T red[2][kBandThreads / 32];
+  __shared__ double ured[kBandThreads / 32];
+  double umax = 0.0;  // float64 SLICE: largest |U| of the staged column
   for (int k = threadIdx.x; k < kBandHalo; k += kBandThreads) {
     us[k] = T(0);
     us[kBandHalo + n + k] = T(0);
@@ -566,30 +643,49 @@ band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const 
     if (col != staged) {
       __syncthreads();  // every reader of the previous column is done
       const double2* src = reinterpret_cast<const double2*>(U + (size_t)col * n);
+      double um = 0.0;
       for (int j = threadIdx.x; j < n / 2; j += kBandThreads) {
         const double2 v = src[j];
         *reinterpret_cast<V*>(us + kBandHalo + 2 * j) = cmk<V>(T(v.x), T(v.y));
+        if constexpr (SLICE && sizeof(T) == 8) um = fmax(um, fmax(fabs(v.x), fabs(v.y)));
+      }
+      if constexpr (SLICE && sizeof(T) == 8) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) um = fmax(um, __shfl_xor_sync(0xffffffffu, um, o));
+        if ((threadIdx.x & 31) == 0) ured[threadIdx.x >> 5] = um;
       }
       staged = col;
       __syncthreads();
+      if constexpr (SLICE && sizeof(T) == 8) {
+        umax = ured[0];
+#pragma unroll
+        for (int w = 1; w < kBandThreads / 32; ++w) umax = fmax(umax, ured[w]);
+      }
     }
     const long long item = col * R_N + q;
     const void* tq = (sizeof(T) == 4) ? static_cast<const void*>(static_cast<const float2*>(taps) + (size_t)q * kBandTaps)
                                       : static_cast<const void*>(static_cast<const double*>(taps) + (size_t)q * kBandTaps);
-    float mx = band_dispatch<T, SLICE>(__ldg(hq + q), us, n, tq, W + (size_t)item * n, ws);
-    if constexpr (SLICE) {
+    BandSlice64 b64{nullptr, 0, 0, nullptr, umax};
+    if constexpr (SLICE && sizeof(T) == 8) {
+      constexpr int C = kSlice64Cells;
+      const int l = int(col / so.R_f), srow = int(col - (long long)l * so.R_f);
+      b64 = BandSlice64{so.out + ((long long)(l * R_N + q) * (n / C) * so.R_f + srow) * C, so.slice_stride, so.R_f,
+                        so.expo + item, umax};
+    }
+    T mx = band_dispatch<T, SLICE>(__ldg(hq + q), us, n, tq, W + (size_t)item * n, ws, b64);
+    if constexpr (SLICE && sizeof(T) == 4) {
       // row maximum over the CTA (red is double-buffered: one barrier per item)
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
       if ((threadIdx.x & 31) == 0) red[parity][threadIdx.x >> 5] = mx;
       __syncthreads();
-      float m = red[parity][0];
+      T m = red[parity][0];
 #pragma unroll
-      for (int w = 1; w < kBandThreads / 32; ++w) m = fmaxf(m, red[parity][w]);
+      for (int w = 1; w < kBandThreads / 32; ++w) m = fmax(m, red[parity][w]);
       parity ^= 1;
+      const int l = int(col / so.R_f), srow = int(col - (long long)l * so.R_f);
       const int e = balanced_exponent(m);
       if (threadIdx.x == 0) so.expo[item] = e;
-      const int l = int(col / so.R_f), srow = int(col - (long long)l * so.R_f);
       __nv_bfloat16* ob = so.out + ((long long)(l * R_N + q) * (n / 64) * so.R_f + srow) * 64;
       float sc1, sc2;
       slice_scales(e, sc1, sc2);
@@ -617,7 +713,7 @@ band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const 
 //   cheb_moments_kernel: m_l of every column;
 //   cheb_coef_kernel: d = C_q m per (column, term) in float64, stored in the
 //     W type, with a record per item: its W and slice rows, its rank and,
-//     for the sliced float32 path, the slice scales of the row exponent from
+//     for the sliced paths, the row exponent (float32: as slice scales) from
 //     the bound sum_k |d_k| >= max_i |W[i]| (|T_k| <= 1), so every CTA of a
 //     row slices with the same exponent;
 //   cheb_eval_kernel: W[i] = sum_k d_k T_k(x_i/b) with the thread's table
@@ -630,8 +726,8 @@ struct __align__(16) ChebItem {
   long long w_off;  // element offset of the W row
   long long s_off;  // element offset of the row in slice 0 (chunk 0)
   int K;
-  float sc1, sc2;   // 2^(8-e) as two factors (slice_scales)
-  int pad;
+  float sc1, sc2;   // float32 W: 2^(8-e) as two factors (slice_scales)
+  int e;            // float64 W: the row exponent
 };
 
 // Moments as a small GEMM, Mom = T (kCheb x n) U^T (n x ncols): a CTA takes
@@ -748,14 +844,22 @@ cheb_coef_kernel(int n, int ncols, int R_N, const int* __restrict__ qlist, int n
     it.s_off = 0;
     it.K = K;
     it.sc1 = it.sc2 = 1.0f;
-    it.pad = 0;
+    it.e = 0;
     if constexpr (SLICE) {
-      // the float32 sum of K products of |T| <= 1 stays below bound (1 + K 2^-23)
-      const int e = balanced_exponent(__double2float_ru(bound * (1.0 + 0x1p-16)));
-      so.expo[item] = e;
-      slice_scales(e, it.sc1, it.sc2);
       const int l = col / so.R_f, srow = col - l * so.R_f;
-      it.s_off = ((long long)(l * R_N + q) * (n / 64) * so.R_f + srow) * 64;
+      if constexpr (sizeof(T) == 4) {
+        // the float32 sum of K products of |T| <= 1 stays below bound (1 + K 2^-23)
+        const int e = balanced_exponent(__double2float_ru(bound * (1.0 + 0x1p-16)));
+        so.expo[item] = e;
+        slice_scales(e, it.sc1, it.sc2);
+        it.s_off = ((long long)(l * R_N + q) * (n / 64) * so.R_f + srow) * 64;
+      } else {
+        // float64: the sum stays below bound (1 + K 2^-52); 2^e above that
+        const int e = row_exponent64(biased_exponent64(bound * (1.0 + 0x1p-40)));
+        so.expo[item] = e;
+        it.e = e;
+        it.s_off = ((long long)(l * R_N + q) * (n / kSlice64Cells) * so.R_f + srow) * kSlice64Cells;
+      }
     }
     items[k] = it;
   }
@@ -823,7 +927,8 @@ cheb_eval_kernel(int n, int ncols, int n_smooth, const void* __restrict__ tcheb,
   }
   const long long n_items = (long long)ncols * n_smooth;
   const long long k0 = n_items * blockIdx.y / gridDim.y, k1 = n_items * (blockIdx.y + 1) / gridDim.y;
-  const int chunk_off = SLICE ? (i >> 6) * so.R_f * 64 + (i & 63) : 0;
+  constexpr int C = sizeof(T) == 4 ? 64 : kSlice64Cells;  // cells per chunk of the slice layout
+  const int chunk_off = SLICE ? (i / C) * so.R_f * C + (i % C) : 0;
   for (long long kb = k0; kb < k1; kb += kChebBatch) {
     const int nb = int(min((long long)kChebBatch, k1 - kb));
     __syncthreads();  // the previous batch is consumed
@@ -849,7 +954,10 @@ cheb_eval_kernel(int n, int ncols, int n_smooth, const void* __restrict__ tcheb,
       else if (h.K <= 12) cheb_pair<T, 12>(dk, t32, t64, w0, w1);
       else cheb_pair<T, 16>(dk, t32, t64, w0, w1);
       __stcs(reinterpret_cast<V*>(W + h.w_off + i), cmk<V>(w0, w1));
-      if constexpr (SLICE) slice_pair(float(w0), float(w1), h.sc1, h.sc2, so.out + h.s_off + chunk_off, so.slice_stride);
+      if constexpr (SLICE) {
+        if constexpr (sizeof(T) == 4) slice_pair(w0, w1, h.sc1, h.sc2, so.out + h.s_off + chunk_off, so.slice_stride);
+        else slice64_pair(w0, w1, h.e, so.out + h.s_off + chunk_off, so.slice_stride);
+      }
     }
   }
 }
@@ -862,11 +970,11 @@ cheb_eval_kernel(int n, int ncols, int n_smooth, const void* __restrict__ tcheb,
 // W is written in float64.  Error of the transform about 1e-13 relative
 // (13 levels of double-float operations), far below the float64 forms' 1e-10
 // bar; CPC_FP64 keeps the float64 transform.
-template <int LOGN>
+template <int LOGN, bool SLICE>
 __global__ void __launch_bounds__(Geometry<LOGN, double>::threads, Geometry<LOGN, double>::min_blocks)
 conv_df_kernel(const dfc* __restrict__ Uhat, const df* __restrict__ phat, const dfc* __restrict__ hw,
                const dfc* __restrict__ tw, double* __restrict__ W, int R_N, int ncols, const int* __restrict__ qlist,
-               int n_q) {
+               int n_q, SliceOut so) {
   using V = dfc;
   using G = Geometry<LOGN, double>;
   using PL = typename G::PL;
@@ -918,7 +1026,20 @@ conv_df_kernel(const dfc* __restrict__ Uhat, const df* __restrict__ phat, const 
       V v[1][PL::P];
       pass_compute<NC, PL::P, 1, +1>(sbuf, v, t, NC / PL::P, tw + pass_table_offset<LOGN, G::LOGP>(PL::NP - 1),
                                      nullptr);
-      if (active) {
+      if constexpr (SLICE) {
+        double2 wd[PL::P / 2];
+#pragma unroll
+        for (int r = 0; r < PL::P / 2; ++r) {
+          const V w = cmk<V>(v[0][r].x * scale, v[0][r].y * scale);
+          wd[r] = make_double2(w.x.to_double(), w.y.to_double());
+        }
+        if (active) {
+          double* out = W + (size_t)item * NC;
+#pragma unroll
+          for (int r = 0; r < PL::P / 2; ++r) __stcs(reinterpret_cast<double2*>(out + 2 * (t + r * (NC / PL::P))), wd[r]);
+        }
+        slice64_epilogue<PL>(wd, reinterpret_cast<double2*>(sbuf), so, item, active, slot, t, R_N);
+      } else if (active) {
         double* out = W + (size_t)item * NC;
 #pragma unroll
         for (int r = 0; r < PL::P / 2; ++r) {
@@ -1105,7 +1226,7 @@ int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const
 template <typename T, bool SLICE>
 int launch_band(const cpc_kernel* P, int ncols, const double* U, T* W, const SliceOut& so, const TermSplit& ts,
                 cudaStream_t s) {
-  const size_t smem = sizeof(T) * (size_t(P->n) + 2 * kBandHalo) + (SLICE ? sizeof(float) * size_t(P->n) : 0);
+  const size_t smem = sizeof(T) * (size_t(P->n) + 2 * kBandHalo) + (SLICE && sizeof(T) == 4 ? sizeof(float) * size_t(P->n) : 0);
   auto kern = band_conv_kernel<T, SLICE>;
   int st = configure(kern, smem);
   if (st) return st;
@@ -1215,12 +1336,12 @@ int dispatch_conv(int logn, const cpc_kernel* P, int ncols, const void* Uhat, vo
   }
 }
 
-template <int LOGN>
-int launch_conv_df(const cpc_kernel* P, int ncols, const dfc* Uhat, double* W, cudaStream_t s, const int* qlist,
-                   int n_q) {
+template <int LOGN, bool SLICE>
+int launch_conv_df(const cpc_kernel* P, int ncols, const dfc* Uhat, double* W, const SliceOut& so, cudaStream_t s,
+                   const int* qlist, int n_q) {
   using G = Geometry<LOGN, double>;
   const size_t smem = sizeof(dfc) * G::slots * padded_len(1 << LOGN);
-  auto kern = conv_df_kernel<LOGN>;
+  auto kern = conv_df_kernel<LOGN, SLICE>;
   int st = configure(kern, smem);
   if (st) return st;
   int per_sm = 0;
@@ -1230,20 +1351,25 @@ int launch_conv_df(const cpc_kernel* P, int ncols, const dfc* Uhat, double* W, c
   const int slot = timing_begin("conv_kernel", s);
   kern<<<int(grid), G::threads, smem, s>>>(Uhat, reinterpret_cast<const df*>(P->d_phatdf),
                                            reinterpret_cast<const dfc*>(P->d_hwdf),
-                                           reinterpret_cast<const dfc*>(P->d_twdf), W, P->R_N, ncols, qlist, n_q);
+                                           reinterpret_cast<const dfc*>(P->d_twdf), W, P->R_N, ncols, qlist, n_q,
+                                           so);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("conv_df_kernel");
   return CPC_OK;
 }
 
-template <int LOGN>
-int dispatch_conv_df(int logn, const cpc_kernel* P, int ncols, const dfc* Uhat, double* W, cudaStream_t s,
-                     const int* qlist, int n_q) {
+template <int LOGN, bool SLICE>
+int dispatch_conv_df(int logn, const cpc_kernel* P, int ncols, const dfc* Uhat, double* W, const SliceOut& so,
+                     cudaStream_t s, const int* qlist, int n_q) {
   if constexpr (LOGN > kMaxLogN) {
     return fail(CPC_ERR_UNSUPPORTED, "conv: n too large");
   } else {
-    if (logn == LOGN) return launch_conv_df<LOGN>(P, ncols, Uhat, W, s, qlist, n_q);
-    return dispatch_conv_df<LOGN + 1>(logn, P, ncols, Uhat, W, s, qlist, n_q);
+    if constexpr (SLICE && LOGN < 7) {
+      if (logn == LOGN) return fail(CPC_ERR_UNSUPPORTED, "sliced conv: n must be at least 128");
+    } else {
+      if (logn == LOGN) return launch_conv_df<LOGN, SLICE>(P, ncols, Uhat, W, so, s, qlist, n_q);
+    }
+    return dispatch_conv_df<LOGN + 1, SLICE>(logn, P, ncols, Uhat, W, so, s, qlist, n_q);
   }
 }
 
@@ -1605,25 +1731,33 @@ int convolve_operands32_sliced(const cpc_kernel* P, int R_f, const void* X, floa
 }
 
 int convolve_spectra_df(const cpc_kernel* P, int ncols, void* Uhat, double* W, cudaStream_t s, const double* U,
-                        void* scratch) {
+                        void* scratch, const SliceRows* so64) {
   if (ilog2(P->n) > kMaxLogN) return fail(CPC_ERR_UNSUPPORTED, "conv: n too large");
   if (!P->d_twdf) return fail(CPC_ERR_INVALID, "conv: kernel has no double-float tables");
-  const SliceOut none{nullptr, 0, nullptr, 0};
+  if (so64 && !conv_slices64_supported(P)) return fail(CPC_ERR_UNSUPPORTED, "sliced float64 conv: n out of range");
+  const SliceOut so = so64 ? *so64 : SliceOut{nullptr, 0, nullptr, 0};
   TermSplit ts = term_split(P, 1, U);
   if (ts.n_smooth > 0 && !scratch) ts = term_split(P, 1, nullptr);
   int st = CPC_OK;
   if (ts.n_band > 0) {
-    st = launch_band<double, false>(P, ncols, U, W, none, ts, s);
+    st = so64 ? launch_band<double, true>(P, ncols, U, W, so, ts, s) : launch_band<double, false>(P, ncols, U, W, so, ts, s);
     if (st) return st;
   }
   if (ts.n_smooth > 0) {
-    st = launch_smooth<double, false>(P, ncols, U, W, none, ts, scratch, s);
+    st = so64 ? launch_smooth<double, true>(P, ncols, U, W, so, ts, scratch, s)
+              : launch_smooth<double, false>(P, ncols, U, W, so, ts, scratch, s);
     if (st) return st;
   }
-  if (ts.n_fft > 0)
-    st = dispatch_conv_df<kMinLogN>(ilog2(P->n), P, ncols, static_cast<const dfc*>(Uhat), W, s, ts.fft_q, ts.n_fft);
+  if (ts.n_fft > 0) {
+    const dfc* X = static_cast<const dfc*>(Uhat);
+    st = so64 ? dispatch_conv_df<kMinLogN, true>(ilog2(P->n), P, ncols, X, W, so, s, ts.fft_q, ts.n_fft)
+              : dispatch_conv_df<kMinLogN, false>(ilog2(P->n), P, ncols, X, W, so, s, ts.fft_q, ts.n_fft);
+  }
   return st;
 }
+
+// the float64 sliced convolution needs whole 128-cell tiles
+bool conv_slices64_supported(const cpc_kernel* P) { return P->n >= 128 && P->n % 128 == 0; }
 
 int build_df_tables(cpc_kernel* P, cudaStream_t s) {
   const int n = P->n;
@@ -1698,8 +1832,9 @@ int check_conv_args(const cpc_kernel* P, int R_f, const void* U, const void* W, 
   return CPC_OK;
 }
 
-int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision, void* ws,
-                 cudaStream_t s) {
+int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int precision, void* ws, cudaStream_t s,
+                 const SliceRows* so64) {
+  if (so64 && precision != CPC_FP64_TC) return fail(CPC_ERR_INVALID, "conv: W slices only for CPC_FP64_TC");
   const int ncols = 3 * R_f;
   // CPC_SPLIT and CPC_FP64_TC: FFT terms in double-float arithmetic
   const bool dfloat = precision == CPC_SPLIT || precision == CPC_FP64_TC;
@@ -1712,7 +1847,7 @@ int run_convolve(const cpc_kernel* P, int R_f, const double* U, void* W, int pre
     // factor spectra as double-float pairs in the float64-spectra part of the workspace
     st = dispatch_spectra_df<kMinLogN>(ilog2(P->n), U, ncols, reinterpret_cast<dfc*>(h64), P, s);
     if (st) return st;
-    return convolve_spectra_df(P, ncols, h64, static_cast<double*>(W), s, U, scratch);
+    return convolve_spectra_df(P, ncols, h64, static_cast<double*>(W), s, U, scratch, so64);
   }
   if (precision == CPC_FP64) {
     st = forward_spectra(P, ncols, U, h64, nullptr, s);

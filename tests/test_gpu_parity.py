@@ -250,6 +250,37 @@ def test_convolution_and_energy_fp64tc(cpc, name, spec):
     assert rel(dU.cpu().numpy(), dU0) < TOL64 and rel(dc.cpu().numpy(), dc0) < TOL64
 
 
+@pytest.mark.parametrize("name,spec", [CASES[0], CASES[2], CASES[3]])
+def test_fp64tc_fused_slicing(cpc, name, spec):
+    # cp_hartree_energy's float64 tensor-core form has the convolution kernels
+    # (banded, Chebyshev, double-float FFT) write W's five-digit slices and row
+    # exponents; cp_hartree_energy_from_factors slices the same W in two
+    # streaming passes with each row's largest exponent field.  The FFT rows
+    # take that exponent too; banded and Chebyshev rows take the exponent of a
+    # bound (sum_m |p_q[m]| max|U|, sum_k |d_k|), which may be larger (the
+    # digits then keep a bit or two less of the row's range): G and
+    # E_H agree to 1e-12 of their size on every mix of paths (a misplaced
+    # digit or row exponent would be an O(1) difference)
+    n, b, M, g = _case(name, spec)
+    h = 2 * b / n
+    P = cpc.make_newton_kernel(n, b, M)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    U = cpc.cp_sample_gaussians(n, b, dev(g["a"]), dev(g["X"]))
+    U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
+    W0 = ocp.convolve_factors(U0, P0)
+    G0 = ocp.conv_matrices(U0, W0, P0.shape[0])
+    E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
+    for limits in ((-1, -1, -1, -1), (20, 24, -1, -1), (-1, -1, 16, 16), (20, 24, 16, 16)):
+        P.set_conv_paths(*limits)
+        E, W, G = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp64tc", want_G=True)
+        assert torch.equal(W, cpc.cp_convolve(P, U, "fp64tc"))
+        E2, G2 = cpc.cp_hartree_energy_from_factors(P, U, dev(g["c"]), W, "fp64tc", want_G=True)
+        Gh = G.cpu().numpy()
+        assert rel(Gh, G2.cpu().numpy()) < 1e-12
+        assert abs(E.item() / E2.item() - 1) < 1e-12
+        assert rel(Gh, G0) < TOL64 and abs(E.item() / E0 - 1) < TOL64
+
+
 def test_fp64tc_rejected_where_not_implemented(cpc):
     P = cpc.make_newton_kernel(64, 5.0, 6)  # n not a multiple of 128
     g = workloads.gaussian_mixture(3, 0.5, 5.0, 3, centre_half=1.0)
