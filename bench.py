@@ -33,7 +33,8 @@ import workloads  # noqa: E402
 WORKLOAD = "density600_n8192"
 # kernels timed by the library's events in the density step
 CHEB = ("cheb_moments_kernel", "cheb_coef_kernel", "cheb_eval_kernel")
-TIMED = ("spectra_kernel", "conv_kernel", "band_conv_kernel", *CHEB, "slice_rows_kernel", "gemm3_tc_kernel")
+TIMED = ("spectra_kernel", "conv_kernel", "band_conv_kernel", *CHEB, "slice_rows_kernel", "gemm3_tc_kernel",
+         "cheb_gram_kernel")
 METRIC = "1D factor convolutions/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # GB300 unit counts for ALU roofs: 152 SMs, 128 FP32 lanes per SM (FMA = 2 flop)
@@ -399,7 +400,8 @@ def run_ours(args, ws, rank, local):
                 # the float64-accurate tensor-core contraction: 15 bf16 slice products
                 # per multiply-add of the method's symmetric Gram
                 tc_ms64 = kto["gemm3_tc_kernel"][0] / kto["gemm3_tc_kernel"][1]
-                gf = 3 * R_N * (R_f * (R_f + 1) // 2) * n * 2
+                _, rk64 = P.conv_paths("fp64tc")  # the smooth terms' Gram matrices come from their moments
+                gf = 3 * (R_N - int((rk64 > 0).sum())) * (R_f * (R_f + 1) // 2) * n * 2
                 bf16_peak = float(load_peaks()[0].get("bf16_tflops", 1900.0))
                 others[form]["gemm3_tc_kernel"] = {
                     "ms": tc_ms64, "achieved_TFLOPs": gf / (tc_ms64 * 1e-3) / 1e12,
@@ -469,8 +471,8 @@ def run_ours(args, ws, rank, local):
             "peak": hbm_peak, "frac": bd_bytes / (bd_ms * 1e-3) / 1e9 / hbm_peak, "algorithmic_bytes": bd_bytes,
             "terms": n_band, "half_widths": [int(x) for x in hw[hw >= 0]],
             "taps_multiply_adds": bd_taps,
-            "note": "direct sums over the band of the narrow kernel terms; float32 W: the bf16 slices "
-                    "(6 B per output) are written too and not counted"}
+            "note": "direct sums over the band of the narrow kernel terms; the energy path's bf16 slices "
+                    "(6 B per output for float32 W, 10 B for float64) are written too and not counted"}
     if n_smooth:
         ch_parts = {k: per_launch(k, 0.0)[0] for k in CHEB}
         ch_ms = sum(ch_parts.values())
@@ -480,20 +482,34 @@ def run_ours(args, ws, rank, local):
             "ms": ch_ms, "bound": "hbm", "achieved": ch_bytes / (ch_ms * 1e-3) / 1e9, "unit": "GB/s",
             "peak": hbm_peak, "frac": ch_bytes / (ch_ms * 1e-3) / 1e9 / hbm_peak, "algorithmic_bytes": ch_bytes,
             "terms": n_smooth, "ranks": [int(x) for x in rk[rk > 0]], "parts_ms": ch_parts,
-            "note": "separable Chebyshev form of the smooth kernel terms (moments, coefficients, evaluation); "
-                    "float32 W: the bf16 slices (6 B per output) are written too and not counted"}
+            "note": "separable Chebyshev form of the smooth kernel terms (moments, coefficients, evaluation)"}
     # contraction, the method's work: the unique entries of the symmetric convolution
     # matrices (Sec. 3.2), 3 axes x R_N terms x R_f (R_f + 1) / 2 entries x n cells, 2 flop
-    # per multiply-add; the fused product over axes and weighted sum are not counted
+    # per multiply-add; the fused product over axes and weighted sum are not counted.
+    # The tensor-core forms take the smooth terms' matrices from their Chebyshev moments
+    # (K-term sums, cheb_gram_kernel) and contract only the banded and FFT terms over
+    # the n cells (gemm3_tc_kernel).
     gram_flops = 3 * R_N * (R_f * (R_f + 1) // 2) * n * 2
     if prec in ("fp32", "fp64tc"):
+        n_dense = R_N - n_smooth
+        gram_flops = 3 * n_dense * (R_f * (R_f + 1) // 2) * n * 2
+        if n_smooth:
+            cg_ms, _ = per_launch("cheb_gram_kernel", 0.0)
+            cg_flops = 3 * (R_f * (R_f + 1) // 2) * int(np.sum(rk[rk > 0])) * 2
+            kernels["cheb_gram_kernel"] = {
+                "ms": cg_ms, "bound": "alu", "achieved": cg_flops / (cg_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                "peak": alu32_peak_tf, "frac": cg_flops / (cg_ms * 1e-3) / 1e12 / alu32_peak_tf,
+                "algorithmic_flops": cg_flops, "terms": n_smooth,
+                "note": "convolution matrices of the smooth terms from their Chebyshev moments, "
+                        "G_q = M^T (C_q M), K-term sums in double-float arithmetic (about 16 float32 "
+                        "operations per multiply-add, not counted)"}
         n_slice_products = 6 if prec == "fp32" else 15
         tc_ms, _ = per_launch("gemm3_tc_kernel", gram_ms)
         bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
         tc_tf = gram_flops / (tc_ms * 1e-3) / 1e12
         kernels["gemm3_tc_kernel"] = {
             "ms": tc_ms, "bound": "tensor", "achieved": tc_tf, "peak": bf16_peak, "unit": "TFLOP/s",
-            "frac": tc_tf / bf16_peak, "algorithmic_flops": gram_flops,
+            "frac": tc_tf / bf16_peak, "algorithmic_flops": gram_flops, "terms": n_dense,
             "peak_note": "bf16 dense burst (cuBLAS), " + peak_kind,
             # the implementation's work, kept apart from the method's: every multiply-add
             # is 6 (float32 form) or 15 (float64 form) bf16 slice products (exact slicing)
@@ -504,8 +520,7 @@ def run_ours(args, ws, rank, local):
         # tensor-core form; U only in the float32 form (the convolution slices W)
         sl_tot, sl_cnt = kt.get("slice_rows_kernel", (0.0, 0))
         sl_ms = sl_tot / max(1, sl_cnt)
-        sl_bytes = (3 * R_f * n * (8 + 6) if prec == "fp32"
-                    else 3 * R_f * (R_N + 1) * n * (8 + 10) / 2)  # per launch: two launches (U, W)
+        sl_bytes = 3 * R_f * n * (8 + (6 if prec == "fp32" else 10))  # U only (the convolution slices W)
         kernels["slice_rows_kernel"] = {"ms": sl_ms, "bound": "hbm", "achieved": sl_bytes / (sl_ms * 1e-3) / 1e9,
                                         "peak": hbm_peak, "unit": "GB/s",
                                         "frac": sl_bytes / (sl_ms * 1e-3) / 1e9 / hbm_peak,
@@ -543,8 +558,11 @@ def run_ours(args, ws, rank, local):
         "speedup_vs_fp64_gpu": (fp64["ms_per_step"] / ms_step) if fp64 else None,
         "e2e": {"value": ws * convs_per_step * e2e_steps / e2e_s, "unit": "convolutions/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": 8},
-        # sample, spectra, conv (+ W slices), [slice U,] contraction, final sum
-        "gpu_launches": ({"fp32": 6, "fp64tc": 8}.get(prec, 5) + (1 if n_band else 0) + (3 if n_smooth else 0)
+        # sample, spectra, FFT conv (+ W slices), [slice U (fp64tc: exponents, digits),] contraction,
+        # [fp64tc: E_H from G,] final sum; banded conv; Chebyshev moments, coefficients,
+        # evaluation [and the smooth terms' Gram matrices]
+        "gpu_launches": ({"fp32": 6, "fp64tc": 8}.get(prec, 5) + (1 if n_band else 0)
+                         + ((4 if prec in ("fp32", "fp64tc") else 3) if n_smooth else 0)
                          - (0 if n_fft else 1)) * args.steps,
         "clocks": clk,
     }

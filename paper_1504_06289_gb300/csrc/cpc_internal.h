@@ -47,9 +47,10 @@ struct cpc_kernel {
   // CONV only: how each kernel term is convolved (spectra.cu), per precision
   // class (0: float32 W, 1: float64 W): by the FFT, by the banded direct sum
   // (narrow terms, half-width H) or by the separable Chebyshev form (smooth
-  // terms, rank K).  d_terms holds [class][5][R_N] ints: H per term (-1: not
-  // banded), K per term (-1: not smooth), then the lists of banded, smooth
-  // and FFT terms.  Banded taps p_q[0..kBandHalo] (float32 class: float2
+  // terms, rank K).  d_terms holds [class][kTermRows][R_N] ints: H per term
+  // (-1: not banded), K per term (-1: not smooth), then the lists of banded,
+  // smooth and FFT terms, and of the terms contracted over the cells (banded
+  // then FFT; the smooth terms' Gram matrices come from their moments).  Banded taps p_q[0..kBandHalo] (float32 class: float2
   // (hi, lo); float64 class: double), zero beyond H; Chebyshev coefficients
   // C_q [R_N][16][16] float64 and the Chebyshev table T_k(x_i/b) [16][n]
   // (float2 (hi, lo) and double).
@@ -171,8 +172,9 @@ int build_term_tables(cpc_kernel* P, int band32, int band64, int rank32, int ran
 // the host part of build_term_tables (no device work): per class the ints
 // [H per term][K per term][banded list][smooth list][FFT list], the taps, the
 // Chebyshev coefficients [R_N][16][16] and the table T_k(x_i/b) [16][n]
+constexpr int kTermRows = 6;  // rows of d_terms per precision class
 struct TermPlan {
-  std::vector<int> terms;  // [2][5][R_N]
+  std::vector<int> terms;  // [2][kTermRows][R_N]
   std::vector<float2> taps32;
   std::vector<double> taps64, cheb, tcheb;
   int n_band[2] = {0, 0}, n_smooth[2] = {0, 0};
@@ -188,6 +190,18 @@ constexpr int kDefaultBand64 = 24;
 constexpr int kDefaultRank = 16;
 // scratch of the Chebyshev path (moments and coefficients of ncols columns)
 size_t smooth_scratch_bytes(const cpc_kernel* P, int ncols);
+// Gram matrices of the smooth terms from the moments and float64 coefficients
+// that a convolution of the 3 R_f columns of U left in its scratch (spectra.cu):
+// E_H partials (c given; cheb_gram_partials of them at most) and/or G
+// [3][R_N][R_f][R_f] for those terms.  cheb_gram_active: the W type class has
+// smooth terms (the convolution then takes them through the Chebyshev form
+// whenever it is given U and its scratch); dense_terms: the others, which the
+// cell contraction takes (n_q of them)
+bool cheb_gram_active(const cpc_kernel* P, int cls);
+const int* dense_terms(const cpc_kernel* P, int cls, int* n_q);
+size_t cheb_gram_partials(const cpc_kernel* P, int R_f);
+int launch_cheb_gram(const cpc_kernel* P, int cls, int R_f, const void* scratch, const double* c, double* G,
+                     double* partial, long long* n_partial, cudaStream_t s);
 // the convolution workspace without that scratch (which follows it)
 size_t conv_spectra_bytes(const cpc_kernel* P, int R_f, int precision);
 
@@ -213,9 +227,12 @@ size_t tc64_partials(int R_f, int R_N);
 size_t tc64_workspace(const cpc_kernel* P, int R_f);
 int* tc64_status_ptr(const cpc_kernel* P, int R_f, void* ws);
 // w_sliced: the convolution already wrote W's slices and row exponents where
-// tc64_w_slices points
+// tc64_w_slices points; cheb_scratch: that convolution's scratch, whose
+// moments give the smooth terms' G (the cell contraction then takes only the
+// other terms; NULL: every term by the cell contraction)
 int launch_eh_tc64(const cpc_kernel* P, int R_f, const double* U, const double* W, const double* c, double* G,
-                   double* partial, void* ws, cudaStream_t s, bool w_sliced = false);
+                   double* partial, void* ws, cudaStream_t s, bool w_sliced = false,
+                   const void* cheb_scratch = nullptr);
 SliceRows tc64_w_slices(const cpc_kernel* P, int R_f, void* ws);
 // tensor-core Coulomb-matrix rows (M item factors against Ns rho factors)
 size_t tc_rows_workspace(const cpc_kernel* P, int M, int Ns);
@@ -227,8 +244,11 @@ int launch_rows_tc(const cpc_kernel* P, int M, const double* U_items, int Ns, co
 // where a convolution writes the W slices for launch_eh_tc(..., w_sliced = true)
 void tc_w_slices(const cpc_kernel* P, int R_f, void* ws, __nv_bfloat16** slices, long long* slice_stride,
                  int** expo);
+// qlist: the n_q kernel terms to contract (NULL: all); the partial slots of
+// the others are zeroed
 int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
-                 double* partial, void* ws, cudaStream_t s, bool w_sliced = false);
+                 double* partial, void* ws, cudaStream_t s, bool w_sliced = false, const int* qlist = nullptr,
+                 int n_q = -1);
 // the V_H factors and spectra of CPC_SPLIT and CPC_FP64_TC are float64, like CPC_FP64
 inline int storage_precision(int precision) { return precision == CPC_FP32 ? CPC_FP32 : CPC_FP64; }
 inline bool known_precision(int precision) {

@@ -467,8 +467,9 @@ static int tiles(int x) { return (x + TM - 1) / TM; }
 
 size_t eh_partials(const cpc_kernel* P, int R_f) {
   const int T = tiles(R_f);
+  // (the tensor-core form's partials are followed by the smooth terms' ones)
   return std::max({size_t(T) * (T + 1) / 2 * P->R_N, eh32_partials(R_f, P->R_N), eh32a_partials(R_f, P->R_N),
-                   tc_partials(R_f, P->R_N), tc64_partials(R_f, P->R_N)});
+                   tc_partials(R_f, P->R_N) + cheb_gram_partials(P, R_f), tc64_partials(R_f, P->R_N)});
 }
 
 // contraction workspace: partial sums; float32 form: a float32 copy of U (CUDA-core
@@ -542,9 +543,11 @@ int launch_eh(const cpc_kernel* P, int R_f, const double* U, const double* c, co
 int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const double* c, void* W, double* G,
                        double* E_H, int precision, void* ws, cudaStream_t s) {
   void* cws = static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_f, precision);
+  void* scratch = static_cast<unsigned char*>(ws) + conv_spectra_bytes(P, R_f, precision);
   if (precision == CPC_FP32 && tc_supported(P)) {
     // the convolution writes W and, in the same pass, the W slices of the
-    // tensor-core contraction (no second pass over W)
+    // tensor-core contraction (no second pass over W) for the banded and FFT
+    // terms; the smooth terms' Gram matrices come from their moments
     void* X = ws;  // float32 convolution operands, in the float64-spectra part of the workspace
     int st = forward_operands32(P, 3 * R_f, U, X, s);
     if (st) return st;
@@ -553,13 +556,17 @@ int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doub
     long long sl_stride;
     int* ex;
     tc_w_slices(P, R_f, tws, &sl, &sl_stride, &ex);
-    st = convolve_operands32_sliced(P, R_f, X, static_cast<float*>(W), sl, sl_stride, ex, s, U,
-                                    static_cast<unsigned char*>(ws) + conv_spectra_bytes(P, R_f, precision));
+    st = convolve_operands32_sliced(P, R_f, X, static_cast<float*>(W), sl, sl_stride, ex, s, U, scratch);
     if (st) return st;
     double* partial = static_cast<double*>(cws);
-    st = launch_eh_tc(P, R_f, U, static_cast<const float*>(W), c, G, partial, tws, s, true);
+    int n_q = P->R_N;
+    const int* qlist = dense_terms(P, 0, &n_q);
+    st = launch_eh_tc(P, R_f, U, static_cast<const float*>(W), c, G, partial, tws, s, true, qlist, n_q);
     if (st) return st;
-    finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, (long long)tc_partials(R_f, P->R_N), P->h * P->h * P->h, E_H,
+    long long count = (long long)tc_partials(R_f, P->R_N), n_cheb = 0;
+    st = launch_cheb_gram(P, 0, R_f, scratch, c, G, partial + count, &n_cheb, s);
+    if (st) return st;
+    finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, count + n_cheb, P->h * P->h * P->h, E_H,
                                            tc_status_ptr(P, R_f, tws));
     CPC_LAUNCH_CHECK("finalize_sum_kernel");
     return CPC_OK;
@@ -572,7 +579,8 @@ int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doub
     int st = run_convolve(P, R_f, U, W, precision, ws, s, &so);
     if (st) return st;
     double* partial = static_cast<double*>(cws);
-    st = launch_eh_tc64(P, R_f, U, static_cast<const double*>(W), c, G, partial, tws, s, true);
+    st = launch_eh_tc64(P, R_f, U, static_cast<const double*>(W), c, G, partial, tws, s, true,
+                        cheb_gram_active(P, 1) ? scratch : nullptr);
     if (st) return st;
     finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, (long long)tc64_partials(R_f, P->R_N), P->h * P->h * P->h, E_H,
                                            tc64_status_ptr(P, R_f, tws));

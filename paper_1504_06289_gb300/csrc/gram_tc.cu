@@ -243,6 +243,7 @@ struct Args {
   double* G;               // E_H only (may be NULL)
   int* status;
   int raster;              // rows mode: 256-row blocks whose pairs sweep the column tiles together
+  const int* qlist;        // the kernel terms of blockIdx.y (NULL: term blockIdx.y)
 };
 
 // 5D tiled TMA load into this CTA's shared memory; the innermost coordinate is
@@ -355,7 +356,7 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t rank = umma::cluster_ctarank();
-  const int q = blockIdx.y;
+  const int q = g.qlist ? __ldg(g.qlist + blockIdx.y) : int(blockIdx.y);
   const int n_ct = (g.Ns + BN - 1) / BN;
   const int pair = blockIdx.x >> 1;
   int ct, r0;
@@ -533,7 +534,7 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             tot[j] = 0.0f;
             lo32[j] = 0.0f;
             if (r < g.M && s < g.Ns && (!diag || r <= s)) {
-              double* Gq = g.G + ((size_t)l * gridDim.y + q) * (size_t)g.M * g.M;
+              double* Gq = g.G + ((size_t)l * g.R_N + q) * (size_t)g.M * g.M;
               Gq[(size_t)r * g.M + s] = Gv;
               Gq[(size_t)s * g.M + r] = Gv;
             }
@@ -558,7 +559,7 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
               if (j & 1) lo[j / 2] = __float2bfloat162_rn(0.0f);
               const bool in = r < g.M && s < g.Ns && (!diag || r <= s);
               if (g.G && in) {
-                double* Gq = g.G + ((size_t)l * gridDim.y + q) * (size_t)g.M * g.M;
+                double* Gq = g.G + ((size_t)l * g.R_N + q) * (size_t)g.M * g.M;
                 Gq[(size_t)r * g.M + s] = Gv;
                 Gq[(size_t)s * g.M + r] = Gv;
               }
@@ -804,7 +805,8 @@ namespace {
 // tensor maps of the chunk-blocked slices and the launch
 template <class F, bool GOUT>
 int launch_tc_kernel(const cpc_kernel* P, int M, int Ns, const TcLayout& L, unsigned char* w, const double* c,
-                     const double* c_col, double* G, double* partial, cudaStream_t s, int rows_mode, int raster) {
+                     const double* c_col, double* G, double* partial, cudaStream_t s, int rows_mode, int raster,
+                     const int* qlist = nullptr, int n_q = -1) {
   const int n = P->n, R_N = P->R_N;
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(w);
   __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(w + L.off_b);
@@ -840,9 +842,12 @@ int launch_tc_kernel(const cpc_kernel* P, int M, int Ns, const TcLayout& L, unsi
   }
   const int n_rp = (M + 2 * tc::BM - 1) / (2 * tc::BM), n_ct = (Ns + tc::BN - 1) / tc::BN;
   const long long gx = rows_mode ? 2LL * n_rp * n_ct : 2LL * tc::eh_pair_tiles(n_ct);
-  if (gx > 0x7fffffffLL || R_N > 65535) return fail(CPC_ERR_UNSUPPORTED, "tensor-core contraction: grid too large");
-  dim3 grid((unsigned)gx, R_N);  // clusters of 2 along x
-  tc::Args args{eA, eB, M, Ns, R_N, n, rows_mode, c, c_col, partial, G, status, std::max(1, std::min(raster, n_rp))};
+  if (!qlist) n_q = R_N;
+  if (gx > 0x7fffffffLL || n_q > 65535) return fail(CPC_ERR_UNSUPPORTED, "tensor-core contraction: grid too large");
+  if (n_q <= 0) return CPC_OK;
+  dim3 grid((unsigned)gx, n_q);  // clusters of 2 along x
+  tc::Args args{eA,     eB, M,      Ns, R_N, n, rows_mode, c, c_col, partial, G, status,
+                std::max(1, std::min(raster, n_rp)), qlist};
   auto kern = tc::gemm3_tc_kernel<F, GOUT>;
   CPC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(F::SMEM)));
   {
@@ -865,7 +870,7 @@ int launch_tc_kernel(const cpc_kernel* P, int M, int Ns, const TcLayout& L, unsi
 template <class F>
 int launch_tc_form(const cpc_kernel* P, int M, int Ns, const double* U, const float* W, const double* c,
                    const double* c_col, double* G, double* partial, void* ws, cudaStream_t s, bool w_sliced,
-                   int rows_mode, int raster) {
+                   int rows_mode, int raster, const int* qlist = nullptr, int n_q = -1) {
   const int n = P->n, R_N = P->R_N;
   const TcLayout L = tc_layout(P, M, Ns);
   unsigned char* w = static_cast<unsigned char*>(ws);
@@ -879,18 +884,21 @@ int launch_tc_form(const cpc_kernel* P, int M, int Ns, const double* U, const fl
                                              reinterpret_cast<int*>(w + L.off_eb), s);
     if (st0) return st0;
   }
-  return launch_tc_kernel<F, false>(P, M, Ns, L, w, c, c_col, G, partial, s, rows_mode, raster);
+  return launch_tc_kernel<F, false>(P, M, Ns, L, w, c, c_col, G, partial, s, rows_mode, raster, qlist, n_q);
 }
 int launch_tc(const cpc_kernel* P, int M, int Ns, const double* U, const float* W, const double* c,
               const double* c_col, double* G, double* partial, void* ws, cudaStream_t s, bool w_sliced,
-              int rows_mode, int raster = 1) {
-  return launch_tc_form<tc::Form32>(P, M, Ns, U, W, c, c_col, G, partial, ws, s, w_sliced, rows_mode, raster);
+              int rows_mode, int raster = 1, const int* qlist = nullptr, int n_q = -1) {
+  return launch_tc_form<tc::Form32>(P, M, Ns, U, W, c, c_col, G, partial, ws, s, w_sliced, rows_mode, raster, qlist,
+                                    n_q);
 }
 }  // namespace
 
 int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
-                 double* partial, void* ws, cudaStream_t s, bool w_sliced) {
-  return launch_tc(P, R_f, R_f, U, W, c, c, G, partial, ws, s, w_sliced, 0);
+                 double* partial, void* ws, cudaStream_t s, bool w_sliced, const int* qlist, int n_q) {
+  // with a term list the other terms' partial slots stay zero
+  if (qlist) CPC_CUDA(cudaMemsetAsync(partial, 0, sizeof(double) * tc_partials(R_f, P->R_N), s));
+  return launch_tc(P, R_f, R_f, U, W, c, c, G, partial, ws, s, w_sliced, 0, 1, qlist, n_q);
 }
 
 // CPC_FP64_TC: five weighted slices of the float64 U and W, the convolution
@@ -904,7 +912,7 @@ SliceRows tc64_w_slices(const cpc_kernel* P, int R_f, void* ws) {
 }
 
 int launch_eh_tc64(const cpc_kernel* P, int R_f, const double* U, const double* W, const double* c, double* G,
-                   double* partial, void* ws, cudaStream_t s, bool w_sliced) {
+                   double* partial, void* ws, cudaStream_t s, bool w_sliced, const void* cheb_scratch) {
   const int n = P->n, R_N = P->R_N;
   const TcLayout L = tc_layout(P, R_f, R_f, tc::Form64::NS, true);
   unsigned char* w = static_cast<unsigned char*>(ws);
@@ -918,8 +926,15 @@ int launch_eh_tc64(const cpc_kernel* P, int R_f, const double* U, const double* 
     if (st) return st;
   }
   double* Gd = G ? G : reinterpret_cast<double*>(w + L.off_g);
-  st = launch_tc_kernel<tc::Form64, true>(P, R_f, R_f, L, w, c, c, Gd, partial, s, 0, 1);
+  int n_q = P->R_N;
+  const int* qlist = cheb_scratch ? dense_terms(P, 1, &n_q) : nullptr;
+  st = launch_tc_kernel<tc::Form64, true>(P, R_f, R_f, L, w, c, c, Gd, partial, s, 0, 1, qlist, n_q);
   if (st) return st;
+  if (qlist) {  // the smooth terms' G from their moments
+    long long np = 0;
+    st = launch_cheb_gram(P, 1, R_f, cheb_scratch, nullptr, Gd, nullptr, &np, s);
+    if (st) return st;
+  }
   tc::eh_from_g_kernel<<<dim3(R_f, R_N), 128, 0, s>>>(Gd, c, R_f, R_N, partial);
   CPC_LAUNCH_CHECK("eh_from_g_kernel");
   return CPC_OK;

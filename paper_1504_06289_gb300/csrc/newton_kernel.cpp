@@ -257,8 +257,8 @@ int make_newton_kernel_paths(int n, double b, int M, int max_half_width32, int m
   plan_term_paths(&K, max_half_width32, max_half_width64, max_rank32, max_rank64, tp);
   for (int cls = 0; cls < 2; ++cls)
     for (int q = 0; q < K.R_N; ++q) {
-      if (half_width) half_width[cls * K.R_N + q] = tp.terms[size_t(cls) * 5 * K.R_N + q];
-      if (rank) rank[cls * K.R_N + q] = tp.terms[size_t(cls) * 5 * K.R_N + K.R_N + q];
+      if (half_width) half_width[cls * K.R_N + q] = tp.terms[size_t(cls) * kTermRows * K.R_N + q];
+      if (rank) rank[cls * K.R_N + q] = tp.terms[size_t(cls) * kTermRows * K.R_N + K.R_N + q];
     }
   if (cheb) std::memcpy(cheb, tp.cheb.data(), sizeof(double) * tp.cheb.size());
   return CPC_OK;

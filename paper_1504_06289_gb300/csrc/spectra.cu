@@ -712,22 +712,19 @@ band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const 
 // its column are known (they are shared by all smooth terms).
 //   cheb_moments_kernel: m_l of every column;
 //   cheb_coef_kernel: d = C_q m per (column, term) in float64, stored in the
-//     W type, with a record per item: its W and slice rows, its rank and,
-//     for the sliced paths, the row exponent (float32: as slice scales) from
-//     the bound sum_k |d_k| >= max_i |W[i]| (|T_k| <= 1), so every CTA of a
-//     row slices with the same exponent;
+//     W type (and kept in float64 with the summed moments, for the Gram
+//     matrices of cheb_gram_kernel), with a record per item: its W row and
+//     its rank;
 //   cheb_eval_kernel: W[i] = sum_k d_k T_k(x_i/b) with the thread's table
 //     entries in registers, CTAs over 512-cell blocks x item ranges.
 constexpr int kCheb = 16;  // largest rank (ranks are 4, 8, 12 or 16)
 constexpr int kChebThreads = 256;
-// per (column, smooth term): where its W row and (sliced path) its slice row
-// start, its rank and slice scales, computed once by cheb_coef_kernel
+// per (column, smooth term): where its W row starts and its rank, computed
+// once by cheb_coef_kernel
 struct __align__(16) ChebItem {
   long long w_off;  // element offset of the W row
-  long long s_off;  // element offset of the row in slice 0 (chunk 0)
   int K;
-  float sc1, sc2;   // float32 W: 2^(8-e) as two factors (slice_scales)
-  int e;            // float64 W: the row exponent
+  int pad;
 };
 
 // Moments as a small GEMM, Mom = T (kCheb x n) U^T (n x ncols): a CTA takes
@@ -807,22 +804,23 @@ cheb_moments_kernel(const double* __restrict__ U, int n, int ncols, const void* 
   }
 }
 
-// one CTA per column: the moments summed over the cell ranges once, then one
-// thread per smooth term j: d_k for k < K (zero up to kCheb) into
-// D[col n_smooth + j][kCheb], the item's record, and (sliced path) the row
-// exponent of the contraction
+// one CTA per column: the moments summed over the cell ranges once (kept in
+// Mom[col][kCheb]), then one thread per smooth term j: d_k for k < K (zero up
+// to kCheb) into D[col n_smooth + j][kCheb] (and D64 in float64, when given)
+// and the item's record
 constexpr int kChebCoefThreads = 64;
-template <typename T, bool SLICE>
+template <typename T>
 __global__ void __launch_bounds__(kChebCoefThreads)
 cheb_coef_kernel(int n, int ncols, int R_N, const int* __restrict__ qlist, int n_smooth, const int* __restrict__ kq,
                  const double* __restrict__ cheb, const double* __restrict__ Part, T* __restrict__ D,
-                 ChebItem* __restrict__ items, SliceOut so) {
+                 ChebItem* __restrict__ items, double* __restrict__ Mom, double* __restrict__ D64) {
   const int col = blockIdx.x;
   __shared__ double m[kCheb];
   if (threadIdx.x < kCheb) {
     double acc = 0.0;
     for (int r = 0; r < cheb_ranges(n); ++r) acc += Part[((size_t)r * ncols + col) * kCheb + threadIdx.x];
     m[threadIdx.x] = acc;
+    Mom[(size_t)col * kCheb + threadIdx.x] = acc;  // for the Gram matrices (cheb_gram_kernel)
   }
   __syncthreads();
   for (int j = threadIdx.x; j < n_smooth; j += kChebCoefThreads) {
@@ -830,37 +828,17 @@ cheb_coef_kernel(int n, int ncols, int R_N, const int* __restrict__ qlist, int n
     const int K = __ldg(kq + q);
     const double* C = cheb + (size_t)q * kCheb * kCheb;
     const long long k = (long long)col * n_smooth + j;
-    double bound = 0.0;
     for (int r = 0; r < kCheb; ++r) {
       double d = 0.0;
       if (r < K)
         for (int l = 0; l < K; ++l) d = fma(__ldg(C + r * kCheb + l), m[l], d);
       D[k * kCheb + r] = T(d);
-      bound += fabs(double(T(d)));
+      if (D64) D64[k * kCheb + r] = d;
     }
-    const long long item = (long long)col * R_N + q;
     ChebItem it;
-    it.w_off = item * n;
-    it.s_off = 0;
+    it.w_off = ((long long)col * R_N + q) * n;
     it.K = K;
-    it.sc1 = it.sc2 = 1.0f;
-    it.e = 0;
-    if constexpr (SLICE) {
-      const int l = col / so.R_f, srow = col - l * so.R_f;
-      if constexpr (sizeof(T) == 4) {
-        // the float32 sum of K products of |T| <= 1 stays below bound (1 + K 2^-23)
-        const int e = balanced_exponent(__double2float_ru(bound * (1.0 + 0x1p-16)));
-        so.expo[item] = e;
-        slice_scales(e, it.sc1, it.sc2);
-        it.s_off = ((long long)(l * R_N + q) * (n / 64) * so.R_f + srow) * 64;
-      } else {
-        // float64: the sum stays below bound (1 + K 2^-52); 2^e above that
-        const int e = row_exponent64(biased_exponent64(bound * (1.0 + 0x1p-40)));
-        so.expo[item] = e;
-        it.e = e;
-        it.s_off = ((long long)(l * R_N + q) * (n / kSlice64Cells) * so.R_f + srow) * kSlice64Cells;
-      }
-    }
+    it.pad = 0;
     items[k] = it;
   }
 }
@@ -902,10 +880,10 @@ __device__ __forceinline__ void cheb_pair(const typename cvec<T>::type* dk, cons
 // shared memory with coalesced loads, then every thread evaluates its two
 // cells for each of them
 constexpr int kChebBatch = 32;
-template <typename T, bool SLICE>
+template <typename T>
 __global__ void __launch_bounds__(kChebThreads, 2)
 cheb_eval_kernel(int n, int ncols, int n_smooth, const void* __restrict__ tcheb, const T* __restrict__ D,
-                 const ChebItem* __restrict__ items, T* __restrict__ W, SliceOut so) {
+                 const ChebItem* __restrict__ items, T* __restrict__ W) {
   using V = typename cvec<T>::type;
   __shared__ __align__(16) T sd[kChebBatch][kCheb];
   __shared__ ChebItem sh[kChebBatch];
@@ -927,8 +905,6 @@ cheb_eval_kernel(int n, int ncols, int n_smooth, const void* __restrict__ tcheb,
   }
   const long long n_items = (long long)ncols * n_smooth;
   const long long k0 = n_items * blockIdx.y / gridDim.y, k1 = n_items * (blockIdx.y + 1) / gridDim.y;
-  constexpr int C = sizeof(T) == 4 ? 64 : kSlice64Cells;  // cells per chunk of the slice layout
-  const int chunk_off = SLICE ? (i / C) * so.R_f * C + (i % C) : 0;
   for (long long kb = k0; kb < k1; kb += kChebBatch) {
     const int nb = int(min((long long)kChebBatch, k1 - kb));
     __syncthreads();  // the previous batch is consumed
@@ -954,11 +930,108 @@ cheb_eval_kernel(int n, int ncols, int n_smooth, const void* __restrict__ tcheb,
       else if (h.K <= 12) cheb_pair<T, 12>(dk, t32, t64, w0, w1);
       else cheb_pair<T, 16>(dk, t32, t64, w0, w1);
       __stcs(reinterpret_cast<V*>(W + h.w_off + i), cmk<V>(w0, w1));
-      if constexpr (SLICE) {
-        if constexpr (sizeof(T) == 4) slice_pair(w0, w1, h.sc1, h.sc2, so.out + h.s_off + chunk_off, so.slice_stride);
-        else slice64_pair(w0, w1, h.e, so.out + h.s_off + chunk_off, so.slice_stride);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Gram matrices of the smooth terms (Sec. 3.2, Eq. Factor_Mk_Conv) from their
+// separable form: the Chebyshev path writes W_{l,q}[s][i] = sum_k d_{s,k}
+// T_k(x_i/b) with d_s = C_q m_s, so
+//   G_{l,q}[r][s] = sum_i U_l[r][i] W_{l,q}[s][i] = sum_k m_{r,k} d_{s,k},
+// a K-term sum (K <= 16) per entry in place of the n-term cell sum, with the
+// moments m_r = sum_i T(x_i/b) U_l[r][i] the convolution formed (of the
+// columns as it read them) and the float64 coefficients d.  The sums run in
+// double-float arithmetic (relative error near 2^-44 of sum_k |m_k d_k|,
+// against 2^-24 for the float32 form's cell contraction; each product is
+// taken as hi + lo, the exact error of the leading product by the fused
+// multiply-add plus the cross terms, the running sum as a TwoSum hi part and
+// a float lo part, added once at the end).  A CTA takes one
+// smooth term and one 32 x 32 tile pair (row tile <= column tile) of the
+// symmetric G, four entries per thread; with G it writes both triangles, with
+// c it sums (1 or 2) c_r c_s prod_l G_l[r][s] over r <= s into one partial
+// (the cell contraction's convention).
+constexpr int kGramTile = 32;
+constexpr int kGramThreads = 256;
+__host__ __device__ constexpr int gram_tiles(int R_f) { return (R_f + kGramTile - 1) / kGramTile; }
+
+__global__ void __launch_bounds__(kGramThreads)
+cheb_gram_kernel(int R_f, int R_N, const int* __restrict__ smooth_q, int n_smooth, const int* __restrict__ kq,
+                 const double* __restrict__ Mom, const double* __restrict__ D64, const double* __restrict__ c,
+                 double* __restrict__ G, double* __restrict__ partial) {
+  constexpr int TP = kGramTile + 2;  // padded rows (16-byte aligned for the paired reads)
+  __shared__ __align__(16) float2 mr[3][kCheb][TP];  // double-float (hi, lo)
+  __shared__ __align__(16) float2 ds[3][kCheb][TP];
+  __shared__ double red[kGramThreads / 32];
+  const int j = blockIdx.y;
+  const int q = __ldg(smooth_q + j);
+  const int K = __ldg(kq + q);
+  const int nt = gram_tiles(R_f);
+  int pi = blockIdx.x, rt = 0;
+  while (pi >= nt - rt) {  // pair index -> (row tile, column tile >= row tile)
+    pi -= nt - rt;
+    ++rt;
+  }
+  const int st = rt + pi;
+  const int r0 = rt * kGramTile, s0 = st * kGramTile;
+  // the tile's moments and coefficients, rows of kCheb float64 read whole
+  for (int x = threadIdx.x; x < 3 * kGramTile * kCheb; x += kGramThreads) {
+    const int k = x % kCheb, i = (x / kCheb) % kGramTile, l = x / (kCheb * kGramTile);
+    const int r = r0 + i, sc = s0 + i;
+    const df a = (r < R_f && k < K) ? df(__ldg(Mom + (size_t)(l * R_f + r) * kCheb + k)) : df();
+    const df d = (sc < R_f && k < K) ? df(__ldg(D64 + ((size_t)(l * R_f + sc) * n_smooth + j) * kCheb + k)) : df();
+    mr[l][k][i] = make_float2(a.hi, a.lo);
+    ds[l][k][i] = make_float2(d.hi, d.lo);
+  }
+  __syncthreads();
+  const int tr = threadIdx.x / 8, ts = 4 * (threadIdx.x % 8);
+  const int r = r0 + tr;
+  double Gv[3][4];
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k = 0; k < K; ++k) {
+      const float2 m = mr[l][k][tr];
+      const float4 d01 = *reinterpret_cast<const float4*>(&ds[l][k][ts]);
+      const float4 d23 = *reinterpret_cast<const float4*>(&ds[l][k][ts + 2]);
+      const float dh[4] = {d01.x, d01.z, d23.x, d23.z}, dl[4] = {d01.y, d01.w, d23.y, d23.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float p = m.x * dh[i];
+        const float e = fmaf(m.x, dl[i], fmaf(m.y, dh[i], fmaf(m.x, dh[i], -p)));  // the rest of the product
+        const float sh = hi[i] + p, v = sh - hi[i];
+        lo[i] += ((hi[i] - (sh - v)) + (p - v)) + e;  // TwoSum error of hi + p
+        hi[i] = sh;
       }
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) Gv[l][i] = double(hi[i]) + double(lo[i]);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int sc = s0 + ts + i;
+    if (r >= R_f || sc >= R_f || (rt == st && tr > ts + i)) continue;
+    if (G) {
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        double* Gq = G + ((size_t)l * R_N + q) * R_f * R_f;
+        Gq[(size_t)r * R_f + sc] = Gv[l][i];
+        Gq[(size_t)sc * R_f + r] = Gv[l][i];
+      }
+    }
+    if (c) sum += (r == sc ? 1.0 : 2.0) * __ldg(c + sc) * (Gv[0][i] * Gv[1][i] * Gv[2][i]);
+  }
+  if (!c) return;
+  if (r < R_f) sum *= __ldg(c + r);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kGramThreads / 32; ++w) t += red[w];
+    partial[(size_t)j * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -1182,11 +1255,37 @@ TermSplit term_split(const cpc_kernel* P, int cls, const double* U) {
   TermSplit ts{nullptr, P->R_N, nullptr, 0, nullptr, nullptr, 0, nullptr};
   if (U && P->d_terms && P->n_band[cls] + P->n_smooth[cls] > 0) {
     const int R_N = P->R_N;
-    const int* b = P->d_terms + (size_t)cls * 5 * R_N;
+    const int* b = P->d_terms + (size_t)cls * kTermRows * R_N;
     ts = TermSplit{b + 4 * R_N, R_N - P->n_band[cls] - P->n_smooth[cls], b + 2 * R_N, P->n_band[cls], b,
                    b + 3 * R_N, P->n_smooth[cls], b + R_N};
   }
   return ts;
+}
+
+// the Chebyshev path's scratch: partial moments [ranges][ncols][kCheb], item
+// records [ncols R_N], coefficients in the W type [ncols R_N][kCheb], the
+// summed moments [ncols][kCheb] and the float64 coefficients (float32 W; for
+// float64 W they are D itself)
+struct SmoothScratch {
+  double* Part;
+  ChebItem* recs;
+  void* D;
+  double* Mom;
+  double* D64;
+};
+SmoothScratch smooth_scratch(const cpc_kernel* P, int ncols, const void* scratch, size_t wbytes) {
+  unsigned char* sc = static_cast<unsigned char*>(const_cast<void*>(scratch));
+  SmoothScratch sm;
+  sm.Part = reinterpret_cast<double*>(sc);
+  sc += align256(sizeof(double) * size_t(cheb_ranges(P->n)) * ncols * kCheb);
+  sm.recs = reinterpret_cast<ChebItem*>(sc);
+  sc += align256(sizeof(ChebItem) * size_t(ncols) * P->R_N);
+  sm.D = sc;
+  sc += align256(sizeof(double) * size_t(ncols) * P->R_N * kCheb);
+  sm.Mom = reinterpret_cast<double*>(sc);
+  sc += align256(sizeof(double) * size_t(ncols) * kCheb);
+  sm.D64 = wbytes == sizeof(double) ? static_cast<double*>(sm.D) : reinterpret_cast<double*>(sc);
+  return sm;
 }
 
 template <typename T, int LOGN, bool SLICE, bool XIN>
@@ -1373,17 +1472,15 @@ int dispatch_conv_df(int logn, const cpc_kernel* P, int ncols, const dfc* Uhat, 
   }
 }
 
-template <typename T, bool SLICE>
-int launch_smooth(const cpc_kernel* P, int ncols, const double* U, T* W, const SliceOut& so, const TermSplit& ts,
-                  void* scratch, cudaStream_t s) {
+template <typename T>
+int launch_smooth(const cpc_kernel* P, int ncols, const double* U, T* W, const TermSplit& ts, void* scratch,
+                  cudaStream_t s) {
   if (!scratch) return fail(CPC_ERR_WORKSPACE, "conv: the Chebyshev path needs its scratch");
   const int n = P->n;
-  unsigned char* sc = static_cast<unsigned char*>(scratch);
-  double* Part = reinterpret_cast<double*>(sc);
-  sc += align256(sizeof(double) * size_t(cheb_ranges(n)) * ncols * kCheb);
-  ChebItem* recs = reinterpret_cast<ChebItem*>(sc);
-  sc += align256(sizeof(ChebItem) * size_t(ncols) * P->R_N);
-  T* D = reinterpret_cast<T*>(sc);
+  const SmoothScratch sm = smooth_scratch(P, ncols, scratch, sizeof(T));
+  double* Part = sm.Part;
+  ChebItem* recs = sm.recs;
+  T* D = static_cast<T*>(sm.D);
   const void* tcheb = sizeof(T) == 4 ? static_cast<const void*>(P->d_tcheb32) : static_cast<const void*>(P->d_tcheb64);
   int slot = timing_begin("cheb_moments_kernel", s);
   cheb_moments_kernel<T><<<dim3((ncols + kChebCols - 1) / kChebCols, cheb_ranges(n)), kChebThreads, 0, s>>>(
@@ -1392,17 +1489,18 @@ int launch_smooth(const cpc_kernel* P, int ncols, const double* U, T* W, const S
   CPC_LAUNCH_CHECK("cheb_moments_kernel");
   const long long items = (long long)ncols * ts.n_smooth;
   slot = timing_begin("cheb_coef_kernel", s);
-  cheb_coef_kernel<T, SLICE><<<ncols, kChebCoefThreads, 0, s>>>(n, ncols, P->R_N, ts.smooth_q, ts.n_smooth,
-                                                                 ts.smooth_k, P->d_cheb, Part, D, recs, so);
+  cheb_coef_kernel<T><<<ncols, kChebCoefThreads, 0, s>>>(n, ncols, P->R_N, ts.smooth_q, ts.n_smooth,
+                                                                 ts.smooth_k, P->d_cheb, Part, D, recs, sm.Mom,
+                                                                 sizeof(T) == 4 ? sm.D64 : nullptr);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("cheb_coef_kernel");
   slot = timing_begin("cheb_eval_kernel", s);
-  auto kern = cheb_eval_kernel<T, SLICE>;
+  auto kern = cheb_eval_kernel<T>;
   int per_sm = 0;
   CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kChebThreads, 0));
   const int bx = std::max(1, n / (2 * kChebThreads));
   const long long by = std::max(1LL, std::min(items, ((long long)std::max(1, per_sm) * sm_count() + bx - 1) / bx));
-  kern<<<dim3(bx, unsigned(by)), kChebThreads, 0, s>>>(n, ncols, ts.n_smooth, tcheb, D, recs, W, so);
+  kern<<<dim3(bx, unsigned(by)), kChebThreads, 0, s>>>(n, ncols, ts.n_smooth, tcheb, D, recs, W);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("cheb_eval_kernel");
   return CPC_OK;
@@ -1423,7 +1521,9 @@ int run_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const Sl
     if (st) return st;
   }
   if (ts.n_smooth > 0) {
-    st = launch_smooth<T, SLICE>(P, ncols, U, static_cast<T*>(W), so, ts, scratch, s);
+    // (the sliced form's contraction takes these terms from their moments:
+    // no slices)
+    st = launch_smooth<T>(P, ncols, U, static_cast<T*>(W), ts, scratch, s);
     if (st) return st;
   }
   if (ts.n_fft > 0) st = dispatch_conv<T, kMinLogN, SLICE, XIN>(ilog2(P->n), P, ncols, Uhat, W, so, s, ts.fft_q, ts.n_fft);
@@ -1624,7 +1724,7 @@ static int cheb_rank(const double* C, const double* p, const std::vector<double>
 
 void plan_term_paths(const cpc_kernel* P, int band32, int band64, int rank32, int rank64, TermPlan& tp) {
   const int R_N = P->R_N, n = P->n;
-  tp.terms.assign(size_t(10) * R_N, 0);
+  tp.terms.assign(size_t(2) * kTermRows * R_N, 0);
   tp.taps32.assign(size_t(R_N) * kBandTaps, make_float2(0.0f, 0.0f));
   tp.taps64.assign(size_t(R_N) * kBandTaps, 0.0);
   tp.cheb.assign(size_t(R_N) * kCheb * kCheb, 0.0);
@@ -1635,8 +1735,8 @@ void plan_term_paths(const cpc_kernel* P, int band32, int band64, int rank32, in
     const int hmax = cls == 0 ? band32 : band64;
     const int kmax = cls == 0 ? rank32 : rank64;
     const double eps = cls == 0 ? std::ldexp(1.0, -32) : std::ldexp(1.0, -44);
-    int* hq = tp.terms.data() + size_t(cls) * 5 * R_N;
-    int *kq = hq + R_N, *bl = hq + 2 * R_N, *sl = hq + 3 * R_N, *fl = hq + 4 * R_N;
+    int* hq = tp.terms.data() + size_t(cls) * kTermRows * R_N;
+    int *kq = hq + R_N, *bl = hq + 2 * R_N, *sl = hq + 3 * R_N, *fl = hq + 4 * R_N, *dl = hq + 5 * R_N;
     int nb = 0, ns = 0, nf = 0;
     for (int q = 0; q < R_N; ++q) {
       const double* p = P->p.data() + size_t(q) * n;
@@ -1667,6 +1767,9 @@ void plan_term_paths(const cpc_kernel* P, int band32, int band64, int rank32, in
       }
       fl[nf++] = q;
     }
+    // the terms contracted over the cells: banded, then FFT
+    for (int j = 0; j < nb; ++j) dl[j] = bl[j];
+    for (int j = 0; j < nf; ++j) dl[nb + j] = fl[j];
     tp.n_band[cls] = nb;
     tp.n_smooth[cls] = ns;
   }
@@ -1678,7 +1781,7 @@ int build_term_tables(cpc_kernel* P, int band32, int band64, int rank32, int ran
   TermPlan tp;
   plan_term_paths(P, band32, band64, rank32, rank64, tp);
   for (int cls = 0; cls < 2; ++cls) {
-    const int* hq = tp.terms.data() + size_t(cls) * 5 * R_N;
+    const int* hq = tp.terms.data() + size_t(cls) * kTermRows * R_N;
     P->band_h[cls].assign(hq, hq + R_N);
     P->rank_k[cls].assign(hq + R_N, hq + 2 * R_N);
     P->n_band[cls] = tp.n_band[cls];
@@ -1744,8 +1847,7 @@ int convolve_spectra_df(const cpc_kernel* P, int ncols, void* Uhat, double* W, c
     if (st) return st;
   }
   if (ts.n_smooth > 0) {
-    st = so64 ? launch_smooth<double, true>(P, ncols, U, W, so, ts, scratch, s)
-              : launch_smooth<double, false>(P, ncols, U, W, so, ts, scratch, s);
+    st = launch_smooth<double>(P, ncols, U, W, ts, scratch, s);  // no slices (see run_conv)
     if (st) return st;
   }
   if (ts.n_fft > 0) {
@@ -1758,6 +1860,41 @@ int convolve_spectra_df(const cpc_kernel* P, int ncols, void* Uhat, double* W, c
 
 // the float64 sliced convolution needs whole 128-cell tiles
 bool conv_slices64_supported(const cpc_kernel* P) { return P->n >= 128 && P->n % 128 == 0; }
+
+bool cheb_gram_active(const cpc_kernel* P, int cls) { return P->d_terms && P->n_smooth[cls] > 0; }
+
+const int* dense_terms(const cpc_kernel* P, int cls, int* n_q) {
+  if (!cheb_gram_active(P, cls)) {
+    *n_q = P->R_N;
+    return nullptr;
+  }
+  *n_q = P->R_N - P->n_smooth[cls];
+  return P->d_terms + (size_t)cls * kTermRows * P->R_N + 5 * P->R_N;
+}
+
+size_t cheb_gram_partials(const cpc_kernel* P, int R_f) {
+  const size_t nt = gram_tiles(R_f);
+  return size_t(P->R_N) * nt * (nt + 1) / 2;
+}
+
+int launch_cheb_gram(const cpc_kernel* P, int cls, int R_f, const void* scratch, const double* c, double* G,
+                     double* partial, long long* n_partial, cudaStream_t s) {
+  *n_partial = 0;
+  if (!cheb_gram_active(P, cls)) return CPC_OK;
+  const int ncols = 3 * R_f;
+  const SmoothScratch sm = smooth_scratch(P, ncols, scratch, cls == 0 ? sizeof(float) : sizeof(double));
+  const int R_N = P->R_N, n_smooth = P->n_smooth[cls];
+  const int* rows = P->d_terms + (size_t)cls * kTermRows * R_N;  // K per term, then the smooth list
+  const int nt = gram_tiles(R_f);
+  const dim3 grid(unsigned(nt * (nt + 1) / 2), unsigned(n_smooth));
+  const int slot = timing_begin("cheb_gram_kernel", s);
+  cheb_gram_kernel<<<grid, kGramThreads, 0, s>>>(R_f, R_N, rows + 3 * R_N, n_smooth, rows + R_N, sm.Mom, sm.D64, c, G,
+                                                 partial);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("cheb_gram_kernel");
+  *n_partial = (long long)grid.x * grid.y;
+  return CPC_OK;
+}
 
 int build_df_tables(cpc_kernel* P, cudaStream_t s) {
   const int n = P->n;
@@ -1774,10 +1911,11 @@ int build_df_tables(cpc_kernel* P, cudaStream_t s) {
 }
 
 size_t smooth_scratch_bytes(const cpc_kernel* P, int ncols) {
-  // partial moments [ranges][ncols][kCheb] float64, item records [ncols R_N],
-  // coefficients [ncols R_N][kCheb] (float64 at most)
+  // the layout of smooth_scratch (coefficients sized for float64 twice: the W
+  // type's and the float64 copy)
   return align256(sizeof(double) * size_t(cheb_ranges(P->n)) * ncols * kCheb) +
-         align256(sizeof(ChebItem) * size_t(ncols) * P->R_N) + align256(sizeof(double) * size_t(ncols) * P->R_N * kCheb);
+         align256(sizeof(ChebItem) * size_t(ncols) * P->R_N) +
+         2 * align256(sizeof(double) * size_t(ncols) * P->R_N * kCheb) + align256(sizeof(double) * size_t(ncols) * kCheb);
 }
 
 size_t spectra_bytes(const cpc_kernel* P, int ncols, int precision) {
