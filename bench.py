@@ -693,16 +693,28 @@ def run_coulomb(args, ws, rank, local):
     tc_ms = res[head]["kernel_ms"].get("gemm3_tc_kernel", 0.0)
     if head == "fp32" and tc_ms > 0:
         # the method's work (2 flop per multiply-add of the 3 axes' scalar products
-        # of item factors with the V_H factors of rho) against the bf16 peak; the 6
-        # bf16 slice products per multiply-add are the implementation's, reported apart
+        # of item factors with the V_H factors of rho) against the bf16 peak: the
+        # banded and FFT terms over the n cells, the smooth terms over their K
+        # Chebyshev moments (the second rows contraction, padded to 128 "cells":
+        # the padding and the 6 bf16 slice products per multiply-add are the
+        # implementation's, reported apart)
+        hw, rk = P.conv_paths("fp32")
+        n_band, n_smooth = int((hw >= 0).sum()), int((rk > 0).sum())
+        n_dense = P.R_N - n_smooth
+        flops = 2.0 * 3 * n_factors * R_rho * (n_dense * n + int(np.sum(rk[rk > 0])))
+        impl = 2.0 * 3 * n_factors * R_rho * (n_dense * n + n_smooth * 128) * 6
         achieved = flops / (tc_ms * 1e-3) / 1e12
         peak = float(peaks.get("bf16_tflops", 1900.0))
         roof = {"kernel": "gemm3_tc_kernel", "bound": "tensor", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                "kernel_ms": tc_ms,
-                "slice_products": {"flops": 6 * flops, "TFLOP/s": 6 * achieved, "frac_of_peak": 6 * achieved / peak},
-                "note": "method flops 2*3*factors*R_rho*R_N*n per launch / event time"}
-        launches = 9  # sample, 2 Hadamard, spectra, conv, slice items, slice W, contraction, item sums
+                "kernel_ms": tc_ms, "terms_over_cells": n_dense, "terms_from_moments": n_smooth,
+                "slice_products": {"flops": impl, "TFLOP/s": impl / (tc_ms * 1e-3) / 1e12,
+                                   "frac_of_peak": impl / (tc_ms * 1e-3) / 1e12 / peak},
+                "note": "method flops 2*3*factors*R_rho*(n_dense*n + sum_smooth K_q) over both launches / event time"}
+        # sample, 2 Hadamard; forward transforms, FFT conv, [banded], [Chebyshev x3]; dense columns:
+        # coefficients, slice items, slice W, contraction; [smooth: moments, moment rows, coefficient
+        # rows, coefficients, slice, slice, contraction]; item sums
+        launches = 3 + 2 + (1 if n_band else 0) + (3 if n_smooth else 0) + 4 + (7 if n_smooth else 0) + 1
     else:
         clk = 2070.0
         peak = SMS * FP32_LANES * 2 * clk * 1e6 / 1e12

@@ -202,6 +202,15 @@ const int* dense_terms(const cpc_kernel* P, int cls, int* n_q);
 size_t cheb_gram_partials(const cpc_kernel* P, int R_f);
 int launch_cheb_gram(const cpc_kernel* P, int cls, int R_f, const void* scratch, const double* c, double* G,
                      double* partial, long long* n_partial, cudaStream_t s);
+// rows-mode operands of the smooth terms (float32 W class, CONV kernel):
+// Chebyshev moments of ncols float64 rows U [ncols][n] as float64 rows of
+// `width` (k < 16, zeros beyond; Part: cheb_moment_rows_scratch bytes), and
+// the coefficient rows d of the 3 R_rho columns a convolution left in its
+// scratch, [3 R_rho n_smooth][width] float32 (row (l R_rho + m) n_smooth + j)
+size_t cheb_moment_rows_scratch(const cpc_kernel* P, int ncols);
+int cheb_moment_rows(const cpc_kernel* P, int ncols, const double* U, void* Part, double* out, int width,
+                     cudaStream_t s);
+int cheb_coef_rows(const cpc_kernel* P, int R_rho, const void* scratch, float* out, int width, cudaStream_t s);
 // the convolution workspace without that scratch (which follows it)
 size_t conv_spectra_bytes(const cpc_kernel* P, int R_f, int precision);
 
@@ -238,9 +247,11 @@ SliceRows tc64_w_slices(const cpc_kernel* P, int R_f, void* ws);
 size_t tc_rows_workspace(const cpc_kernel* P, int M, int Ns);
 size_t tc_rows_groups(const cpc_kernel* P, int Ns);
 int* tc_rows_status_ptr(const cpc_kernel* P, int M, int Ns, void* ws);
-// raster: 256-row blocks of item factors whose CTA pairs sweep the column tiles together
+// raster: 256-row blocks of item factors whose CTA pairs sweep the column tiles together;
+// wmap: column s of the Ns is W row (s / n_wmap) R_N_src + wmap[s % n_wmap] (NULL: row s)
 int launch_rows_tc(const cpc_kernel* P, int M, const double* U_items, int Ns, const float* W_rho,
-                   const double* c_rho, double* rowpart, void* ws, cudaStream_t s, int raster);
+                   const double* c_rho, double* rowpart, void* ws, cudaStream_t s, int raster,
+                   const int* wmap = nullptr, int n_wmap = 1, int R_N_src = 1);
 // where a convolution writes the W slices for launch_eh_tc(..., w_sliced = true)
 void tc_w_slices(const cpc_kernel* P, int R_f, void* ws, __nv_bfloat16** slices, long long* slice_stride,
                  int** expo);

@@ -208,7 +208,8 @@ __global__ void finalize_sum_kernel(const double* __restrict__ partial, long lon
 // J[t] = h^3 sum_{r in item t} c[r] sum_g rowpart[g][r]
 __global__ void item_reduce_kernel(int n_items, const int* __restrict__ off, const double* __restrict__ c,
                                    const double* __restrict__ rowpart, int groups, int M, double scale,
-                                   double* __restrict__ J, const int* __restrict__ status = nullptr) {
+                                   double* __restrict__ J, const int* __restrict__ status = nullptr,
+                                   const int* __restrict__ status2 = nullptr) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_items) return;
   double s = 0.0;
@@ -219,7 +220,8 @@ __global__ void item_reduce_kernel(int n_items, const int* __restrict__ off, con
     s += c[r] * rs;
   }
   // a device-side wait of the tensor-core kernel that gave up makes the results NaN
-  J[t] = (status && *status) ? __longlong_as_double(0x7ff8000000000000LL) : scale * s;
+  const bool gave_up = (status && *status) || (status2 && *status2);
+  J[t] = gave_up ? __longlong_as_double(0x7ff8000000000000LL) : scale * s;
 }
 
 // float32 form of the adjoint GEMM.  The K sum runs q-major (kk = (q, k')),
@@ -699,22 +701,50 @@ static cpc_kernel column_view(const cpc_kernel* P) {
   return Q;
 }
 
-// workspace of coulomb_contract (after the convolution's)
+// The tensor-core form takes the smooth kernel terms (CONV kernels with a
+// Chebyshev path) from their moments: G[r][(m, q)] = sum_k m_{r,k} d_{m,q,k}
+// (the identity of cheb_gram_kernel) as a second rows contraction whose
+// "cells" are the kCheb moments and coefficients, zero-padded to a 128-cell
+// tile; the banded and FFT terms are contracted over the n cells (their W
+// rows gathered by the slicing).
+static const int kMomCells = 128;
+static bool coulomb_smooth(const cpc_kernel* P) { return P->kind == CPC_KERNEL_CONV && cheb_gram_active(P, 0); }
+static cpc_kernel moment_view(const cpc_kernel* P) {
+  cpc_kernel Q = column_view(P);
+  Q.n = kMomCells;
+  return Q;
+}
+
+// workspace of coulomb_contract (after the convolution's): column coefficients
+// (dense, smooth), row partials of both contractions (contiguous), their
+// tensor-core scratch, then the smooth terms' operand rows and moment partials
 static size_t contract_bytes(const cpc_kernel* P, int n_factors, int R_rho, int precision) {
   if (precision == CPC_FP32 && tc_supported(P)) {
     const cpc_kernel Q = column_view(P);
     const int Nc = R_rho * P->R_N;
-    return align256(sizeof(double) * Nc) + align256(sizeof(double) * tc_rows_groups(&Q, Nc) * n_factors) +
-           tc_rows_workspace(&Q, n_factors, Nc);
+    size_t b = align256(sizeof(double) * Nc) + align256(sizeof(double) * tc_rows_groups(&Q, Nc) * n_factors) +
+               tc_rows_workspace(&Q, n_factors, Nc);
+    if (coulomb_smooth(P)) {
+      const cpc_kernel Qm = moment_view(P);
+      const int Ns = R_rho * P->n_smooth[0];
+      b += align256(sizeof(double) * Ns) + align256(sizeof(double) * tc_rows_groups(&Qm, Ns) * n_factors) +
+           tc_rows_workspace(&Qm, n_factors, Ns) + align256(sizeof(double) * 3 * size_t(n_factors) * kMomCells) +
+           align256(sizeof(float) * 3 * size_t(Ns) * kMomCells) + cheb_moment_rows_scratch(P, 3 * n_factors);
+    }
+    return b;
   }
   return align256(sizeof(double) * coulomb_groups(R_rho, P->R_N, kTilesMin) * n_factors);
 }
 
 // contraction + segmented item reduction, after W_rho holds the V_H factors
 // J[t] = scale sum_{r in item t} c_items[r] sum_m c_rho[m] sum_q prod_l <u_r^(l), W_rho[l][m R_N + q]>
+// (cheb_scratch: the scratch of the convolution that wrote W_rho, whose
+// Chebyshev coefficients the tensor-core form takes for the smooth terms;
+// NULL: every term over the cells)
 static int coulomb_contract(const cpc_kernel* P, int n_items, const int* off, int n_factors, const double* U_items,
                             const double* c_items, int R_rho, const double* c_rho, const void* W_rho, double* J,
-                            int precision, int tiles_per_cta, double* rowpart, cudaStream_t s, double scale) {
+                            int precision, int tiles_per_cta, double* rowpart, cudaStream_t s, double scale,
+                            const void* cheb_scratch = nullptr) {
   const int n = P->n;
   const int N = R_rho * P->R_N;
   const int groups = coulomb_groups(R_rho, P->R_N, tiles_per_cta);
@@ -731,21 +761,58 @@ static int coulomb_contract(const cpc_kernel* P, int n_items, const int* off, in
     st = launch_rows32(P, n_factors, U_items, N, nullptr, c_rho, rowpart, groups, tiles_per_cta, s,
                        static_cast<const double*>(W_rho));
   } else if (tc_supported(P)) {
-    // tensor cores over the R_rho R_N columns (m, q) as one-term factors:
-    // workspace = column coefficients, one row partial per 128-column tile,
-    // then the tensor-core slices
+    // tensor cores over the R_rho R_N columns (m, q) as one-term factors
+    // (layout in contract_bytes); with smooth terms, the dense columns
+    // (m, dense term j) over the cells and the smooth ones from the moments
     const cpc_kernel Q = column_view(P);
     const int Nc = R_rho * P->R_N;
-    double* cq = rowpart;
-    double* rp = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(rowpart) + align256(sizeof(double) * Nc));
-    expand_coef_kernel<<<(Nc + 255) / 256, 256, 0, s>>>(R_rho, P->R_N, c_rho, cq);
-    CPC_LAUNCH_CHECK("expand_coef_kernel");
-    const int tgroups = (int)tc_rows_groups(&Q, Nc);
-    void* tws = reinterpret_cast<unsigned char*>(rp) + align256(sizeof(double) * (size_t)tgroups * n_factors);
-    st = launch_rows_tc(&Q, n_factors, U_items, Nc, static_cast<const float*>(W_rho), cq, rp, tws, s, tiles_per_cta);
-    if (st) return st;
-    item_reduce_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(n_items, off, c_items, rp, tgroups, n_factors, scale, J,
-                                                           tc_rows_status_ptr(&Q, n_factors, Nc, tws));
+    const bool sm = cheb_scratch && coulomb_smooth(P);
+    int n_dense = P->R_N;
+    const int* dq = sm ? dense_terms(P, 0, &n_dense) : nullptr;
+    const int n_sm = sm ? P->n_smooth[0] : 0;
+    const int Nd = R_rho * n_dense, Ns = R_rho * n_sm;
+    const cpc_kernel Qm = moment_view(P);
+    unsigned char* w = reinterpret_cast<unsigned char*>(rowpart);
+    double* cq = reinterpret_cast<double*>(w);
+    w += align256(sizeof(double) * Nc);
+    double* cqs = reinterpret_cast<double*>(w);
+    if (sm) w += align256(sizeof(double) * Ns);
+    const int tg_d = Nd > 0 ? (int)tc_rows_groups(&Q, Nd) : 0;
+    const int tg_s = Ns > 0 ? (int)tc_rows_groups(&Qm, Ns) : 0;
+    double* rp = reinterpret_cast<double*>(w);  // [tg_d + tg_s][n_factors]
+    w += align256(sizeof(double) * (size_t)tc_rows_groups(&Q, Nc) * n_factors) +
+         (sm ? align256(sizeof(double) * (size_t)tc_rows_groups(&Qm, Ns) * n_factors) : 0);
+    void* tws = w;
+    w += tc_rows_workspace(&Q, n_factors, Nc);
+    const int* status = nullptr;
+    const int* status2 = nullptr;
+    if (Nd > 0) {
+      expand_coef_kernel<<<(Nd + 255) / 256, 256, 0, s>>>(R_rho, n_dense, c_rho, cq);
+      CPC_LAUNCH_CHECK("expand_coef_kernel");
+      st = launch_rows_tc(&Q, n_factors, U_items, Nd, static_cast<const float*>(W_rho), cq, rp, tws, s, tiles_per_cta,
+                          dq, n_dense, P->R_N);
+      if (st) return st;
+      status = tc_rows_status_ptr(&Q, n_factors, Nd, tws);
+    }
+    if (Ns > 0) {
+      void* tws_s = w;
+      w += tc_rows_workspace(&Qm, n_factors, Ns);
+      double* A = reinterpret_cast<double*>(w);
+      w += align256(sizeof(double) * 3 * size_t(n_factors) * kMomCells);
+      float* B = reinterpret_cast<float*>(w);
+      w += align256(sizeof(float) * 3 * size_t(Ns) * kMomCells);
+      st = cheb_moment_rows(P, 3 * n_factors, U_items, w, A, kMomCells, s);
+      if (st) return st;
+      st = cheb_coef_rows(P, R_rho, cheb_scratch, B, kMomCells, s);
+      if (st) return st;
+      expand_coef_kernel<<<(Ns + 255) / 256, 256, 0, s>>>(R_rho, n_sm, c_rho, cqs);
+      CPC_LAUNCH_CHECK("expand_coef_kernel");
+      st = launch_rows_tc(&Qm, n_factors, A, Ns, B, cqs, rp + (size_t)tg_d * n_factors, tws_s, s, tiles_per_cta);
+      if (st) return st;
+      status2 = tc_rows_status_ptr(&Qm, n_factors, Ns, tws_s);
+    }
+    item_reduce_kernel<<<(n_items + 127) / 128, 128, 0, s>>>(n_items, off, c_items, rp, tg_d + tg_s, n_factors, scale,
+                                                           J, status, status2);
     CPC_LAUNCH_CHECK("item_reduce_kernel");
     return CPC_OK;
   } else {
@@ -795,8 +862,9 @@ extern "C" int coulomb_matrix(const cpc_kernel* P, int n_items, const int* off, 
   st = run_convolve(P, R_rho, U_rho, W_rho, precision, ws, s);
   if (st) return st;
   double* rowpart = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_rho, precision));
+  const void* scratch = static_cast<unsigned char*>(ws) + conv_spectra_bytes(P, R_rho, precision);
   return coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision,
-                          tiles_per_cta ? tiles_per_cta : kTilesDefault, rowpart, s, P->h * P->h * P->h);
+                          tiles_per_cta ? tiles_per_cta : kTilesDefault, rowpart, s, P->h * P->h * P->h, scratch);
 }
 
 extern "C" int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* off, int n_factors,
@@ -813,6 +881,7 @@ extern "C" int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* 
   st = run_convolve(P, R_rho, U_rho, W_rho, precision, ws, s);
   if (st) return st;
   double* rowpart = reinterpret_cast<double*>(static_cast<unsigned char*>(ws) + cp_convolve_workspace(P, R_rho, precision));
+  const void* scratch = static_cast<unsigned char*>(ws) + conv_spectra_bytes(P, R_rho, precision);
   // candidates: the tensor-core form (CPC_FP32, n a multiple of 128) rasters
   // its CTA pairs over groups of 1..32 item-row blocks; the CUDA-core forms
   // take 4..128 column tiles per work unit
@@ -834,10 +903,12 @@ extern "C" int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* 
   int best_t = kTilesDefault;
   for (int t = lo; t <= hi; t *= 2) {
     // one untimed launch per candidate, then one timed
-    st = coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, t, rowpart, s, P->h * P->h * P->h);
+    st = coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, t, rowpart, s,
+                          P->h * P->h * P->h, scratch);
     if (st) return st;
     CPC_CUDA(cudaEventRecord(ev.e[0], s));
-    st = coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, t, rowpart, s, P->h * P->h * P->h);
+    st = coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, t, rowpart, s,
+                          P->h * P->h * P->h, scratch);
     if (st) return st;
     CPC_CUDA(cudaEventRecord(ev.e[1], s));
     CPC_CUDA(cudaEventSynchronize(ev.e[1]));
@@ -850,7 +921,7 @@ extern "C" int coulomb_matrix_tune(const cpc_kernel* P, int n_items, const int* 
   if (best_ms) *best_ms = best;
   // leave J computed with the chosen schedule
   return coulomb_contract(P, n_items, off, n_factors, U_items, c_items, R_rho, c_rho, W_rho, J, precision, best_t,
-                          rowpart, s, P->h * P->h * P->h);
+                          rowpart, s, P->h * P->h * P->h, scratch);
 }
 
 // ---- nuclear potential and its Galerkin matrix (Sec. 3.3) ---------------------

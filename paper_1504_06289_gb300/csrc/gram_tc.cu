@@ -130,16 +130,21 @@ __device__ __forceinline__ uint64_t desc_k(uint32_t saddr) {
 // Slices are written chunk-blocked, so that the rows of one operand tile
 // (64 consecutive s, one BKC-cell chunk) are one contiguous block:
 //   out[k][G = l*R_N + q][t][s][i % BKC],  t = i / BKC,  k = slice.
+// With qmap, row number `row` is taken from source row
+// (row / n_qmap) R_N_src + qmap[row % n_qmap]: a subset of the kernel terms
+// of a [..][R_N_src][n] array, compacted.
 template <typename TS, int VPT, class F, int TPB, bool BAL>
 __global__ void __launch_bounds__(TPB) slice_rows_kernel(const TS* __restrict__ src, long long rows, int n, int R_f,
                                                          int R_N, __nv_bfloat16* __restrict__ out,
-                                                         long long slice_stride, int* __restrict__ expo) {
+                                                         long long slice_stride, int* __restrict__ expo,
+                                                         const int* __restrict__ qmap, int n_qmap, int R_N_src) {
   constexpr int NS = F::NS, BKC = F::BKC;
   static_assert(NS == 3, "float32 form: three slices");
   __shared__ float red[TPB / 32];
   const int T = n / BKC;
   for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
-    const TS* x = src + row * n;
+    const long long srow_src = qmap ? (row / n_qmap) * R_N_src + __ldg(qmap + row % n_qmap) : row;
+    const TS* x = src + srow_src * n;
     const long long per_l = (long long)R_f * R_N;
     const int l = (int)(row / per_l);
     const int rem = (int)(row - l * per_l);
@@ -611,11 +616,12 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
 // BAL: balanced digits (the W operand of the float32 form)
 template <typename TS, class F, bool BAL>
 int launch_slice(const TS* src, long long rows, int n, int R_f, int R_N, __nv_bfloat16* out, long long slice_stride,
-                 int* expo, cudaStream_t s) {
+                 int* expo, cudaStream_t s, const int* qmap = nullptr, int n_qmap = 1, int R_N_src = 1) {
   const unsigned grid = (unsigned)std::min<long long>(rows, 1 << 20);
   const int slot = timing_begin("slice_rows_kernel", s);
-#define CPC_SLICE(VPT, TPB) \
-  slice_rows_kernel<TS, VPT, F, TPB, BAL><<<grid, TPB, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo)
+#define CPC_SLICE(VPT, TPB)                                                                                    \
+  slice_rows_kernel<TS, VPT, F, TPB, BAL><<<grid, TPB, 0, s>>>(src, rows, n, R_f, R_N, out, slice_stride, expo, \
+                                                                qmap, n_qmap, R_N_src)
   switch (n) {
     case 128: CPC_SLICE(1, 256); break;
     case 256: CPC_SLICE(1, 256); break;
@@ -870,7 +876,8 @@ int launch_tc_kernel(const cpc_kernel* P, int M, int Ns, const TcLayout& L, unsi
 template <class F>
 int launch_tc_form(const cpc_kernel* P, int M, int Ns, const double* U, const float* W, const double* c,
                    const double* c_col, double* G, double* partial, void* ws, cudaStream_t s, bool w_sliced,
-                   int rows_mode, int raster, const int* qlist = nullptr, int n_q = -1) {
+                   int rows_mode, int raster, const int* qlist = nullptr, int n_q = -1, const int* wmap = nullptr,
+                   int n_wmap = 1, int R_N_src = 1) {
   const int n = P->n, R_N = P->R_N;
   const TcLayout L = tc_layout(P, M, Ns);
   unsigned char* w = static_cast<unsigned char*>(ws);
@@ -881,7 +888,7 @@ int launch_tc_form(const cpc_kernel* P, int M, int Ns, const double* U, const fl
   if (!w_sliced) {  // else the convolution already wrote them (convolve_operands32_sliced)
     st0 = tc::launch_slice<float, F, F::BAL>(W, 3LL * Ns * R_N, n, Ns, R_N,
                                              reinterpret_cast<__nv_bfloat16*>(w + L.off_b), (long long)(L.b / 3),
-                                             reinterpret_cast<int*>(w + L.off_eb), s);
+                                             reinterpret_cast<int*>(w + L.off_eb), s, wmap, n_wmap, R_N_src);
     if (st0) return st0;
   }
   return launch_tc_kernel<F, false>(P, M, Ns, L, w, c, c_col, G, partial, s, rows_mode, raster, qlist, n_q);
@@ -943,8 +950,10 @@ int launch_eh_tc64(const cpc_kernel* P, int R_f, const double* U, const double* 
 // Coulomb-matrix rows: rowpart[(q * n_ct + ct) * M + r] = sum over the 128
 // columns s of tile ct of c_s prod_l G_l[r][s, q] (M item factors, Ns = R_rho)
 int launch_rows_tc(const cpc_kernel* P, int M, const double* U_items, int Ns, const float* W_rho,
-                   const double* c_rho, double* rowpart, void* ws, cudaStream_t s, int raster) {
-  return launch_tc(P, M, Ns, U_items, W_rho, nullptr, c_rho, nullptr, rowpart, ws, s, false, 1, raster);
+                   const double* c_rho, double* rowpart, void* ws, cudaStream_t s, int raster, const int* wmap,
+                   int n_wmap, int R_N_src) {
+  return launch_tc_form<tc::Form32>(P, M, Ns, U_items, W_rho, nullptr, c_rho, nullptr, rowpart, ws, s, false, 1, raster,
+                                    nullptr, -1, wmap, n_wmap, R_N_src);
 }
 
 }  // namespace cpc

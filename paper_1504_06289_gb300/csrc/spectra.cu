@@ -1035,6 +1035,31 @@ cheb_gram_kernel(int R_f, int R_N, const int* __restrict__ smooth_q, int n_smoot
   }
 }
 
+// Rows-mode operands of the smooth terms (the Coulomb matrix): the same
+// identity as cheb_gram_kernel, G[r][(m, q)] = sum_k m_{r,k} d_{m,q,k}, taken
+// by the tensor-core rows contraction with the kCheb moments and coefficients
+// as the "cells" of zero-padded rows.
+//   moment_rows_kernel: out[col][k] = sum over cell ranges of Part (k < kCheb), 0 beyond;
+//   coef_rows_kernel: out[row][k] = D[row][k] (k < kCheb), 0 beyond.
+__global__ void moment_rows_kernel(const double* __restrict__ Part, int ranges, long long ncols, double* __restrict__ out,
+                                   int width) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= ncols * width) return;
+  const long long col = x / width;
+  const int k = int(x - col * width);
+  double acc = 0.0;
+  if (k < kCheb)
+    for (int r = 0; r < ranges; ++r) acc += Part[((size_t)r * ncols + col) * kCheb + k];
+  out[x] = acc;
+}
+__global__ void coef_rows_kernel(const float* __restrict__ D, long long rows, float* __restrict__ out, int width) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= rows * width) return;
+  const long long row = x / width;
+  const int k = int(x - row * width);
+  out[x] = k < kCheb ? D[row * kCheb + k] : 0.0f;
+}
+
 // ---------------------------------------------------------------------------
 // The FFT terms of CPC_SPLIT and CPC_FP64_TC in double-float arithmetic
 // (dfloat.cuh): the same transform as conv_kernel<double> (float64 plan,
@@ -1870,6 +1895,36 @@ const int* dense_terms(const cpc_kernel* P, int cls, int* n_q) {
   }
   *n_q = P->R_N - P->n_smooth[cls];
   return P->d_terms + (size_t)cls * kTermRows * P->R_N + 5 * P->R_N;
+}
+
+size_t cheb_moment_rows_scratch(const cpc_kernel* P, int ncols) {
+  return align256(sizeof(double) * size_t(cheb_ranges(P->n)) * ncols * kCheb);
+}
+
+int cheb_moment_rows(const cpc_kernel* P, int ncols, const double* U, void* Part, double* out, int width,
+                     cudaStream_t s) {
+  if (!P->d_tcheb32 || width < kCheb) return fail(CPC_ERR_INVALID, "cheb_moment_rows: no Chebyshev table");
+  const int n = P->n;
+  double* pt = static_cast<double*>(Part);
+  int slot = timing_begin("cheb_moments_kernel", s);
+  cheb_moments_kernel<float><<<dim3((ncols + kChebCols - 1) / kChebCols, cheb_ranges(n)), kChebThreads, 0, s>>>(
+      U, n, ncols, P->d_tcheb32, pt);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("cheb_moments_kernel");
+  const long long tot = (long long)ncols * width;
+  moment_rows_kernel<<<unsigned((tot + 255) / 256), 256, 0, s>>>(pt, cheb_ranges(n), ncols, out, width);
+  CPC_LAUNCH_CHECK("moment_rows_kernel");
+  return CPC_OK;
+}
+
+int cheb_coef_rows(const cpc_kernel* P, int R_rho, const void* scratch, float* out, int width, cudaStream_t s) {
+  if (!cheb_gram_active(P, 0) || width < kCheb) return fail(CPC_ERR_INVALID, "cheb_coef_rows: no smooth terms");
+  const SmoothScratch sm = smooth_scratch(P, 3 * R_rho, scratch, sizeof(float));
+  const long long rows = 3LL * R_rho * P->n_smooth[0];
+  const long long tot = rows * width;
+  coef_rows_kernel<<<unsigned((tot + 255) / 256), 256, 0, s>>>(static_cast<const float*>(sm.D), rows, out, width);
+  CPC_LAUNCH_CHECK("coef_rows_kernel");
+  return CPC_OK;
 }
 
 size_t cheb_gram_partials(const cpc_kernel* P, int R_f) {

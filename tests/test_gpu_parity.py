@@ -507,6 +507,31 @@ def test_coulomb_matrix_reduced(cpc, precision, tol):
     assert np.max(np.abs(J - J0)) < tol * np.max(np.abs(J0))
 
 
+def test_coulomb_matrix_smooth_terms_from_moments(cpc):
+    # the float32 tensor-core form takes the smooth kernel terms' part of J
+    # from their Chebyshev moments (a second rows contraction whose cells are
+    # the 16 moments of each item factor and the coefficients of each density
+    # column) and the banded and FFT terms over the n cells (their W rows
+    # gathered); with every term sent to the FFT the cell contraction takes
+    # them all: both agree with the oracle and with each other
+    n, b, M = 256, 10.0, 14
+    basis = _basis_case()
+    nb = len(basis["fn_first"]) - 1
+    items = ocoul.item_list(nb)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    J0, _ = ocoul.coulomb_items(n, b, basis, P0, items)
+    P = cpc.make_newton_kernel(n, b, M)
+    _, rk = P.conv_paths("fp32")
+    assert (rk > 0).sum() > 0
+    J = _gpu_coulomb(cpc, P, n, b, basis, items, "fp32")
+    P.set_conv_paths(-1, -1, -1, -1)
+    Jf = _gpu_coulomb(cpc, P, n, b, basis, items, "fp32")
+    scale = np.max(np.abs(J0))
+    assert np.max(np.abs(J - J0)) < 1e-5 * scale
+    assert np.max(np.abs(Jf - J0)) < 1e-5 * scale
+    assert np.max(np.abs(J - Jf)) < 2e-6 * scale
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-7)])
 def test_lattice_sum(cpc, precision, tol):
     n, b, M, L = 1024, 16.0, 20, 8
