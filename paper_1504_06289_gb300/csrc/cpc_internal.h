@@ -217,9 +217,12 @@ size_t conv_spectra_bytes(const cpc_kernel* P, int R_f, int precision);
 // float32 contractions (gram32.cu)
 size_t eh32_partials(int R_f, int R_N);
 int build_spectral_weights(const cpc_kernel* P, float* d, cudaStream_t s);
+// (CPC_SPLIT, W64: qlist, when given, the n_q kernel terms to contract; the
+// other terms' partial slots are zeroed)
 int launch_eh32(const cpc_kernel* P, int R_f, const double* U, const float* W, const float* S32,
                 const float* dtab, const double* c, double* G, double* partial, cudaStream_t s,
-                const double* W64 = nullptr);
+                const double* W64 = nullptr, const int* qlist = nullptr,
+                int n_q = -1);
 int launch_rows32(const cpc_kernel* P, int n_factors, const double* U_items, int N, const float* W,
                   const double* c_rho, double* rowpart, int groups, int tiles_per_cta, cudaStream_t s,
                   const double* W64 = nullptr);

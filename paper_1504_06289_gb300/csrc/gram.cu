@@ -469,9 +469,10 @@ static int tiles(int x) { return (x + TM - 1) / TM; }
 
 size_t eh_partials(const cpc_kernel* P, int R_f) {
   const int T = tiles(R_f);
-  // (the tensor-core form's partials are followed by the smooth terms' ones)
-  return std::max({size_t(T) * (T + 1) / 2 * P->R_N, eh32_partials(R_f, P->R_N), eh32a_partials(R_f, P->R_N),
-                   tc_partials(R_f, P->R_N) + cheb_gram_partials(P, R_f), tc64_partials(R_f, P->R_N)});
+  // (the tensor-core and split forms' partials are followed by the smooth terms' ones)
+  return std::max({size_t(T) * (T + 1) / 2 * P->R_N, eh32_partials(R_f, P->R_N) + cheb_gram_partials(P, R_f),
+                   eh32a_partials(R_f, P->R_N), tc_partials(R_f, P->R_N) + cheb_gram_partials(P, R_f),
+                   tc64_partials(R_f, P->R_N)});
 }
 
 // contraction workspace: partial sums; float32 form: a float32 copy of U (CUDA-core
@@ -586,6 +587,24 @@ int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doub
     if (st) return st;
     finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, (long long)tc64_partials(R_f, P->R_N), P->h * P->h * P->h, E_H,
                                            tc64_status_ptr(P, R_f, tws));
+    CPC_LAUNCH_CHECK("finalize_sum_kernel");
+    return CPC_OK;
+  }
+  if (precision == CPC_SPLIT && cheb_gram_active(P, 1)) {
+    // the split form likewise: the smooth terms' Gram matrices from the
+    // moments, the others by the compensated float32 contraction
+    int st = run_convolve(P, R_f, U, W, precision, ws, s);
+    if (st) return st;
+    double* partial = static_cast<double*>(cws);
+    int n_q = P->R_N;
+    const int* qlist = dense_terms(P, 1, &n_q);
+    st = launch_eh32(P, R_f, U, nullptr, nullptr, nullptr, c, G, partial, s, static_cast<const double*>(W), qlist,
+                     n_q);
+    if (st) return st;
+    long long count = (long long)eh32_partials(R_f, P->R_N), n_cheb = 0;
+    st = launch_cheb_gram(P, 1, R_f, scratch, c, G, partial + count, &n_cheb, s);
+    if (st) return st;
+    finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, count + n_cheb, P->h * P->h * P->h, E_H);
     CPC_LAUNCH_CHECK("finalize_sum_kernel");
     return CPC_OK;
   }

@@ -190,7 +190,8 @@ template <class Op, int MODE, bool COMP = false>
 __global__ void __launch_bounds__(THREADS, 2)
 gemm3_kernel(Op op, int M, int N, const double* __restrict__ wr, const double* __restrict__ wcol, int wcol_div,
              double* __restrict__ partial, double* __restrict__ G, int n_rt, int tiles_per_cta,
-             const float* __restrict__ dtab, long long d_stride) {
+             const float* __restrict__ dtab, long long d_stride, const int* __restrict__ qlist = nullptr,
+             int R_N = 0) {
   extern __shared__ __align__(16) float smem[];
   float* As = smem;
   float* Bs = As + 2 * BK * BM;
@@ -200,8 +201,10 @@ gemm3_kernel(Op op, int M, int N, const double* __restrict__ wr, const double* _
   auto P = [&](int i, int j) -> float& { return prod[(i * TNC + j) * THREADS + tid]; };
   if constexpr (MODE == 0) {
     // blockIdx.x enumerates (row tile, col tile) pairs; tiles entirely below
-    // the diagonal (r > s everywhere) exit.  blockIdx.y is the kernel term q.
-    const int q = blockIdx.y;
+    // the diagonal (r > s everywhere) exit.  blockIdx.y is the kernel term q
+    // (with qlist, the term qlist[blockIdx.y] of R_N).
+    const int q = qlist ? __ldg(qlist + blockIdx.y) : int(blockIdx.y);
+    const int n_terms = qlist ? R_N : int(gridDim.y);
     if constexpr (std::is_same<Op, Spectral>::value) op.d = dtab + (long long)q * d_stride;
     else op.col_off = q;
     const int n_ct = (N + BN - 1) / BN;
@@ -213,7 +216,7 @@ gemm3_kernel(Op op, int M, int N, const double* __restrict__ wr, const double* _
         float tot[TMR][TNC];
         tile_axis<Op, COMP>(op, l, M, N, r0, s0, tot, As, Bs);
         if (G) {
-          double* Gq = G + ((size_t)l * gridDim.y + q) * (size_t)M * M;
+          double* Gq = G + ((size_t)l * n_terms + q) * (size_t)M * M;
 #pragma unroll
           for (int i = 0; i < TMR; ++i)
 #pragma unroll
@@ -322,15 +325,21 @@ int build_spectral_weights(const cpc_kernel* P, float* d, cudaStream_t s) {
 // float32 factors (W) or spatial on float64 factors (W64, CPC_SPLIT).
 int launch_eh32(const cpc_kernel* P, int R_f, const double* U, const float* W, const float* S32,
                 const float* dtab, const double* c, double* G, double* partial, cudaStream_t s,
-                const double* W64) {
+                const double* W64, const int* qlist, int n_q) {
   const int n_rt = (R_f + g32::BM - 1) / g32::BM, n_ct = (R_f + g32::BN - 1) / g32::BN;
   dim3 grid(n_rt * n_ct, P->R_N);
   if (W64) {
+    // (a term list: the partial slots of the other terms are zeroed)
+    if (qlist) {
+      CPC_CUDA(cudaMemsetAsync(partial, 0, sizeof(double) * eh32_partials(R_f, P->R_N), s));
+      if (n_q <= 0) return CPC_OK;
+      grid.y = n_q;
+    }
     g32::SpatialD op{U, W64, (long long)R_f * P->n, (long long)R_f * P->R_N * P->n, P->R_N, 0, P->n};
     CPC_CUDA(cudaFuncSetAttribute(g32::gemm3_kernel<g32::SpatialD, 0, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(g32::kSmemBytes)));
     g32::gemm3_kernel<g32::SpatialD, 0, true><<<grid, g32::THREADS, g32::kSmemBytes, s>>>(
-        op, R_f, R_f, c, c, 1, partial, G, n_rt, 0, nullptr, 0);
+        op, R_f, R_f, c, c, 1, partial, G, n_rt, 0, nullptr, 0, qlist, P->R_N);
   } else if (S32) {
     g32::Spectral op{S32, nullptr, (long long)R_f * 2 * (P->n + 1), 2 * (P->n + 1)};
     CPC_CUDA(cudaFuncSetAttribute(g32::gemm3_kernel<g32::Spectral, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,

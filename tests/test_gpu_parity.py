@@ -354,6 +354,11 @@ def test_convolution_and_energy_split(cpc, name, spec):
     E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
     assert abs(E.item() / E0 - 1) < EH_TOL * max(1.0, cancellation(G0, g["c"], h))
     assert rel(G.cpu().numpy(), G0) < 1e-6
+    # the energy path takes the smooth terms' G from their Chebyshev moments,
+    # the factors path contracts every term of the same W over the cells
+    E2, G2 = cpc.cp_hartree_energy_from_factors(P, U, dev(g["c"]), W, "split", want_G=True)
+    assert rel(G.cpu().numpy(), G2.cpu().numpy()) < 1e-6
+    assert abs(E.item() / E2.item() - 1) < EH_TOL * max(1.0, cancellation(G0, g["c"], h))
     dU, dc = cpc.cp_hartree_energy_adjoint(P, dev(g["c"]), W, G, "split")
     dU0, dc0 = ocp.hartree_energy_adjoint(U0, g["c"], P0, h)
     assert rel(dU.cpu().numpy(), dU0) < 1e-6 and rel(dc.cpu().numpy(), dc0) < 1e-6
