@@ -49,8 +49,12 @@ struct cpc_kernel {
   // (narrow terms, half-width H) or by the separable Chebyshev form (smooth
   // terms, rank K).  d_terms holds [class][kTermRows][R_N] ints: H per term
   // (-1: not banded), K per term (-1: not smooth), then the lists of banded,
-  // smooth and FFT terms, and of the terms contracted over the cells (banded
-  // then FFT; the smooth terms' Gram matrices come from their moments).  Banded taps p_q[0..kBandHalo] (float32 class: float2
+  // smooth and FFT terms, of the terms contracted over the cells (banded then
+  // FFT; the smooth terms' Gram matrices come from their moments), of the
+  // lag-covered banded terms (H < n_lag: their Gram matrices are sums of the
+  // n_lag lag Gram matrices) and the float32 energy path's contraction list
+  // (banded terms with H >= n_lag, FFT terms, then n_lag entries whose W
+  // slice slots, those of the first n_lag covered terms, hold the lag rows).  Banded taps p_q[0..kBandHalo] (float32 class: float2
   // (hi, lo); float64 class: double), zero beyond H; Chebyshev coefficients
   // C_q [R_N][16][16] float64 and the Chebyshev table T_k(x_i/b) [16][n]
   // (float2 (hi, lo) and double).
@@ -58,6 +62,9 @@ struct cpc_kernel {
   int rank_max[2] = {-1, -1};  // largest rank sent to the Chebyshev kernels
   int n_band[2] = {0, 0};
   int n_smooth[2] = {0, 0};
+  int n_lag[2] = {0, 0};   // lag Gram matrices of the energy path (float32 class only)
+  int n_cov[2] = {0, 0};   // banded terms they cover
+  int n_eh[2] = {0, 0};    // entries of the energy path's contraction list
   std::vector<int> band_h[2];  // host copies of the half-widths and ranks
   std::vector<int> rank_k[2];
   // double-float copies (hi, lo) of the float64 FFT tables for the float64
@@ -172,12 +179,13 @@ int build_term_tables(cpc_kernel* P, int band32, int band64, int rank32, int ran
 // the host part of build_term_tables (no device work): per class the ints
 // [H per term][K per term][banded list][smooth list][FFT list], the taps, the
 // Chebyshev coefficients [R_N][16][16] and the table T_k(x_i/b) [16][n]
-constexpr int kTermRows = 6;  // rows of d_terms per precision class
+constexpr int kTermRows = 8;  // rows of d_terms per precision class
+constexpr int kMaxLags = 8;   // largest lag count of the float32 energy path
 struct TermPlan {
   std::vector<int> terms;  // [2][kTermRows][R_N]
   std::vector<float2> taps32;
   std::vector<double> taps64, cheb, tcheb;
-  int n_band[2] = {0, 0}, n_smooth[2] = {0, 0};
+  int n_band[2] = {0, 0}, n_smooth[2] = {0, 0}, n_lag[2] = {0, 0}, n_cov[2] = {0, 0}, n_eh[2] = {0, 0};
 };
 void plan_term_paths(const cpc_kernel* P, int band32, int band64, int rank32, int rank64, TermPlan& tp);
 // default maxima: where the direct sum still costs less than the transform
@@ -199,6 +207,18 @@ size_t smooth_scratch_bytes(const cpc_kernel* P, int ncols);
 // cell contraction takes (n_q of them)
 bool cheb_gram_active(const cpc_kernel* P, int cls);
 const int* dense_terms(const cpc_kernel* P, int cls, int* n_q);
+// the float32 energy path (class 0): its contraction list (n_q entries, the
+// last n_virtual of them lag rows) and the lag-covered banded terms
+const int* eh_terms(const cpc_kernel* P, int* n_q, int* n_virtual);
+// lag rows V_m = U shifted by +m plus U shifted by -m (V_0 = U), m < n_lag, as
+// balanced three-digit slices with their row exponents in the W slice slots
+// of the first n_lag covered terms (SliceRows of the float32 form)
+int lag_slices32(const cpc_kernel* P, int R_f, const double* U, const SliceRows& so, cudaStream_t s);
+// G and E_H partials of the covered terms from the lag Gram matrices S
+// [3][n_lag][R_f][R_f] (float32): G_q = sum_{m <= H_q} p_q[m] S_m
+size_t lag_gram_partials(const cpc_kernel* P, int R_f);
+int launch_lag_gram(const cpc_kernel* P, int R_f, const float* S, const double* c, double* G, double* partial,
+                    long long* n_partial, cudaStream_t s);
 size_t cheb_gram_partials(const cpc_kernel* P, int R_f);
 int launch_cheb_gram(const cpc_kernel* P, int cls, int R_f, const void* scratch, const double* c, double* G,
                      double* partial, long long* n_partial, cudaStream_t s);
@@ -259,10 +279,11 @@ int launch_rows_tc(const cpc_kernel* P, int M, const double* U_items, int Ns, co
 void tc_w_slices(const cpc_kernel* P, int R_f, void* ws, __nv_bfloat16** slices, long long* slice_stride,
                  int** expo);
 // qlist: the n_q kernel terms to contract (NULL: all); the partial slots of
-// the others are zeroed
+// the others are zeroed; the last n_virtual entries are lag rows whose Gram
+// matrices go to Gv [3][n_virtual][R_f][R_f] (float32)
 int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
                  double* partial, void* ws, cudaStream_t s, bool w_sliced = false, const int* qlist = nullptr,
-                 int n_q = -1);
+                 int n_q = -1, float* Gv = nullptr, int n_virtual = 0);
 // the V_H factors and spectra of CPC_SPLIT and CPC_FP64_TC are float64, like CPC_FP64
 inline int storage_precision(int precision) { return precision == CPC_FP32 ? CPC_FP32 : CPC_FP64; }
 inline bool known_precision(int precision) {

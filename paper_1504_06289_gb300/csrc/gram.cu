@@ -471,7 +471,8 @@ size_t eh_partials(const cpc_kernel* P, int R_f) {
   const int T = tiles(R_f);
   // (the tensor-core and split forms' partials are followed by the smooth terms' ones)
   return std::max({size_t(T) * (T + 1) / 2 * P->R_N, eh32_partials(R_f, P->R_N) + cheb_gram_partials(P, R_f),
-                   eh32a_partials(R_f, P->R_N), tc_partials(R_f, P->R_N) + cheb_gram_partials(P, R_f),
+                   eh32a_partials(R_f, P->R_N),
+                   tc_partials(R_f, P->R_N) + cheb_gram_partials(P, R_f) + lag_gram_partials(P, R_f),
                    tc64_partials(R_f, P->R_N)});
 }
 
@@ -480,7 +481,10 @@ size_t eh_partials(const cpc_kernel* P, int R_f) {
 // the tensor-core kernel
 size_t contraction_workspace(const cpc_kernel* P, int R_f, int precision) {
   size_t b = align256(sizeof(double) * eh_partials(P, R_f));
-  if (precision == CPC_FP32) b += tc_supported(P) ? tc_workspace(P, R_f) : eh32a_u32_bytes(P, R_f);
+  // (float32 tensor-core form: then the lag Gram matrices [3][kMaxLags][R_f][R_f])
+  if (precision == CPC_FP32)
+    b += tc_supported(P) ? tc_workspace(P, R_f) + align256(sizeof(double) * 3 * kMaxLags * size_t(R_f) * R_f)
+                         : eh32a_u32_bytes(P, R_f);
   if (precision == CPC_FP64_TC) b += tc64_workspace(P, R_f);
   return b;
 }
@@ -561,16 +565,23 @@ int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doub
     tc_w_slices(P, R_f, tws, &sl, &sl_stride, &ex);
     st = convolve_operands32_sliced(P, R_f, X, static_cast<float*>(W), sl, sl_stride, ex, s, U, scratch);
     if (st) return st;
+    // the lag rows of the narrow terms into the slice slots of covered terms
+    st = lag_slices32(P, R_f, U, SliceRows{sl, sl_stride, ex, R_f}, s);
+    if (st) return st;
     double* partial = static_cast<double*>(cws);
-    int n_q = P->R_N;
-    const int* qlist = dense_terms(P, 0, &n_q);
-    st = launch_eh_tc(P, R_f, U, static_cast<const float*>(W), c, G, partial, tws, s, true, qlist, n_q);
+    float* Sv = reinterpret_cast<float*>(static_cast<unsigned char*>(tws) + tc_workspace(P, R_f));
+    int n_q = P->R_N, n_v = 0;
+    const int* qlist = eh_terms(P, &n_q, &n_v);
+    st = launch_eh_tc(P, R_f, U, static_cast<const float*>(W), c, G, partial, tws, s, true, qlist, n_q, Sv, n_v);
     if (st) return st;
-    long long count = (long long)tc_partials(R_f, P->R_N), n_cheb = 0;
-    st = launch_cheb_gram(P, 0, R_f, scratch, c, G, partial + count, &n_cheb, s);
+    long long count = (long long)tc_partials(R_f, P->R_N), n_more = 0;
+    st = launch_cheb_gram(P, 0, R_f, scratch, c, G, partial + count, &n_more, s);
     if (st) return st;
-    finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, count + n_cheb, P->h * P->h * P->h, E_H,
-                                           tc_status_ptr(P, R_f, tws));
+    count += n_more;
+    st = launch_lag_gram(P, R_f, Sv, c, G, partial + count, &n_more, s);
+    if (st) return st;
+    count += n_more;
+    finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, count, P->h * P->h * P->h, E_H, tc_status_ptr(P, R_f, tws));
     CPC_LAUNCH_CHECK("finalize_sum_kernel");
     return CPC_OK;
   }

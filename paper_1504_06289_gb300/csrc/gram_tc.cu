@@ -249,6 +249,12 @@ struct Args {
   int* status;
   int raster;              // rows mode: 256-row blocks whose pairs sweep the column tiles together
   const int* qlist;        // the kernel terms of blockIdx.y (NULL: term blockIdx.y)
+  // E_H: the last n_virtual rows of the grid are lag rows (their W slice
+  // slots hold lag rows, not the term's W): they write their Gram blocks to
+  // Gv [3][n_virtual][M][M] (float32 form: float, float64 form: double) and
+  // add nothing to E_H
+  void* Gv;
+  int n_virtual;
 };
 
 // 5D tiled TMA load into this CTA's shared memory; the innermost coordinate is
@@ -362,6 +368,8 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t rank = umma::cluster_ctarank();
   const int q = g.qlist ? __ldg(g.qlist + blockIdx.y) : int(blockIdx.y);
+  const int vrow = int(blockIdx.y) - (int(gridDim.y) - g.n_virtual);  // >= 0: a lag row
+  const bool virt = !g.rows_mode && vrow >= 0;
   const int n_ct = (g.Ns + BN - 1) / BN;
   const int pair = blockIdx.x >> 1;
   int ct, r0;
@@ -539,7 +547,8 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
             tot[j] = 0.0f;
             lo32[j] = 0.0f;
             if (r < g.M && s < g.Ns && (!diag || r <= s)) {
-              double* Gq = g.G + ((size_t)l * g.R_N + q) * (size_t)g.M * g.M;
+              double* Gq = virt ? static_cast<double*>(g.Gv) + ((size_t)l * g.n_virtual + vrow) * (size_t)g.M * g.M
+                                : g.G + ((size_t)l * g.R_N + q) * (size_t)g.M * g.M;
               Gq[(size_t)r * g.M + s] = Gv;
               Gq[(size_t)s * g.M + r] = Gv;
             }
@@ -563,7 +572,11 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
               tot[j] = 0.0f;
               if (j & 1) lo[j / 2] = __float2bfloat162_rn(0.0f);
               const bool in = r < g.M && s < g.Ns && (!diag || r <= s);
-              if (g.G && in) {
+              if (in && virt) {
+                float* Gq = static_cast<float*>(g.Gv) + ((size_t)l * g.n_virtual + vrow) * (size_t)g.M * g.M;
+                Gq[(size_t)r * g.M + s] = Gv;
+                Gq[(size_t)s * g.M + r] = Gv;
+              } else if (in && g.G) {
                 double* Gq = g.G + ((size_t)l * g.R_N + q) * (size_t)g.M * g.M;
                 Gq[(size_t)r * g.M + s] = Gv;
                 Gq[(size_t)s * g.M + r] = Gv;
@@ -603,7 +616,7 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
   } else if (tid == 0) {
     double s = 0.0;
     for (int w = 0; w < NT / 32; ++w) s += red[w];
-    g.partial[(size_t)q * gridDim.x + blockIdx.x] = s;
+    if (!virt) g.partial[(size_t)q * gridDim.x + blockIdx.x] = s;
     if (*abort_flag) atomicExch(g.status, 1);
   }
   umma::cluster_sync();  // neither CTA leaves (or frees TMEM) while the pair still works
@@ -812,7 +825,7 @@ namespace {
 template <class F, bool GOUT>
 int launch_tc_kernel(const cpc_kernel* P, int M, int Ns, const TcLayout& L, unsigned char* w, const double* c,
                      const double* c_col, double* G, double* partial, cudaStream_t s, int rows_mode, int raster,
-                     const int* qlist = nullptr, int n_q = -1) {
+                     const int* qlist = nullptr, int n_q = -1, void* Gv = nullptr, int n_virtual = 0) {
   const int n = P->n, R_N = P->R_N;
   __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(w);
   __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(w + L.off_b);
@@ -853,7 +866,7 @@ int launch_tc_kernel(const cpc_kernel* P, int M, int Ns, const TcLayout& L, unsi
   if (n_q <= 0) return CPC_OK;
   dim3 grid((unsigned)gx, n_q);  // clusters of 2 along x
   tc::Args args{eA,     eB, M,      Ns, R_N, n, rows_mode, c, c_col, partial, G, status,
-                std::max(1, std::min(raster, n_rp)), qlist};
+                std::max(1, std::min(raster, n_rp)), qlist, Gv, n_virtual};
   auto kern = tc::gemm3_tc_kernel<F, GOUT>;
   CPC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(F::SMEM)));
   {
@@ -877,7 +890,7 @@ template <class F>
 int launch_tc_form(const cpc_kernel* P, int M, int Ns, const double* U, const float* W, const double* c,
                    const double* c_col, double* G, double* partial, void* ws, cudaStream_t s, bool w_sliced,
                    int rows_mode, int raster, const int* qlist = nullptr, int n_q = -1, const int* wmap = nullptr,
-                   int n_wmap = 1, int R_N_src = 1) {
+                   int n_wmap = 1, int R_N_src = 1, void* Gv = nullptr, int n_virtual = 0) {
   const int n = P->n, R_N = P->R_N;
   const TcLayout L = tc_layout(P, M, Ns);
   unsigned char* w = static_cast<unsigned char*>(ws);
@@ -891,21 +904,24 @@ int launch_tc_form(const cpc_kernel* P, int M, int Ns, const double* U, const fl
                                              reinterpret_cast<int*>(w + L.off_eb), s, wmap, n_wmap, R_N_src);
     if (st0) return st0;
   }
-  return launch_tc_kernel<F, false>(P, M, Ns, L, w, c, c_col, G, partial, s, rows_mode, raster, qlist, n_q);
+  return launch_tc_kernel<F, false>(P, M, Ns, L, w, c, c_col, G, partial, s, rows_mode, raster, qlist, n_q, Gv,
+                                    n_virtual);
 }
 int launch_tc(const cpc_kernel* P, int M, int Ns, const double* U, const float* W, const double* c,
               const double* c_col, double* G, double* partial, void* ws, cudaStream_t s, bool w_sliced,
-              int rows_mode, int raster = 1, const int* qlist = nullptr, int n_q = -1) {
+              int rows_mode, int raster = 1, const int* qlist = nullptr, int n_q = -1, void* Gv = nullptr,
+              int n_virtual = 0) {
   return launch_tc_form<tc::Form32>(P, M, Ns, U, W, c, c_col, G, partial, ws, s, w_sliced, rows_mode, raster, qlist,
-                                    n_q);
+                                    n_q, nullptr, 1, 1, Gv, n_virtual);
 }
 }  // namespace
 
 int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
-                 double* partial, void* ws, cudaStream_t s, bool w_sliced, const int* qlist, int n_q) {
+                 double* partial, void* ws, cudaStream_t s, bool w_sliced, const int* qlist, int n_q, float* Gv,
+                 int n_virtual) {
   // with a term list the other terms' partial slots stay zero
   if (qlist) CPC_CUDA(cudaMemsetAsync(partial, 0, sizeof(double) * tc_partials(R_f, P->R_N), s));
-  return launch_tc(P, R_f, R_f, U, W, c, c, G, partial, ws, s, w_sliced, 0, 1, qlist, n_q);
+  return launch_tc(P, R_f, R_f, U, W, c, c, G, partial, ws, s, w_sliced, 0, 1, qlist, n_q, Gv, n_virtual);
 }
 
 // CPC_FP64_TC: five weighted slices of the float64 U and W, the convolution

@@ -619,7 +619,8 @@ __device__ __forceinline__ T band_dispatch(int h, const T* us, int n, const void
 template <typename T, bool SLICE>
 __global__ void __launch_bounds__(kBandThreads, 2)
 band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const int* __restrict__ qlist, int n_band,
-                 const int* __restrict__ hq, const void* __restrict__ taps, T* __restrict__ W, SliceOut so) {
+                 const int* __restrict__ hq, const void* __restrict__ taps, T* __restrict__ W, SliceOut so,
+                 int slice_min_h) {
   using V = typename cvec<T>::type;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* us = reinterpret_cast<T*>(smem_raw);  // [kBandHalo + n + kBandHalo]
@@ -672,8 +673,11 @@ band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const 
       b64 = BandSlice64{so.out + ((long long)(l * R_N + q) * (n / C) * so.R_f + srow) * C, so.slice_stride, so.R_f,
                         so.expo + item, umax};
     }
-    T mx = band_dispatch<T, SLICE>(__ldg(hq + q), us, n, tq, W + (size_t)item * n, ws, b64);
-    if constexpr (SLICE && sizeof(T) == 4) {
+    const int h = __ldg(hq + q);
+    T mx = band_dispatch<T, SLICE>(h, us, n, tq, W + (size_t)item * n, ws, b64);
+    // float32: the terms with H < slice_min_h get no slices (their Gram
+    // matrices come from the lag Gram matrices); h is the same for the CTA
+    if constexpr (SLICE && sizeof(T) == 4) if (h >= slice_min_h) {
       // row maximum over the CTA (red is double-buffered: one barrier per item)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -1061,6 +1065,139 @@ __global__ void coef_rows_kernel(const float* __restrict__ D, long long rows, fl
 }
 
 // ---------------------------------------------------------------------------
+// Gram matrices of the narrow (banded) terms from lag Gram matrices (Sec. 3.2,
+// Eq. Factor_Mk_Conv with the banded sum of Eq. conv): with
+//   V_m[i] = U[i - m] + U[i + m] (m > 0, zero outside the grid), V_0 = U,
+// a banded term's W is sum_{m <= H} p_q[m] V_m, so
+//   G_q = U^T W_q = sum_{m <= H} p_q[m] S_m,  S_m = U^T V_m,
+// and the L lag Gram matrices S_0..S_{L-1} (contracted over the cells on the
+// tensor cores, as extra rows of the float32 energy path) give every banded
+// term with H < L.  lag_slice32_kernel writes V_m (the column rounded to
+// float32 once, as the banded kernel stages it, then float32 sums: no
+// float64 arithmetic, which runs at 1/64 of the float32 rate here) as the
+// contraction's balanced three-digit slices into the slice slot of the m-th
+// covered term: one CTA per (axis, column) stages the column once in shared
+// memory (zero border of kMaxLags cells), takes the L row maxima in one pass
+// and writes the L rows' digits in a second.
+constexpr int kLagThreads = 256;
+__global__ void __launch_bounds__(kLagThreads)
+lag_slice32_kernel(const double* __restrict__ U, int n, int R_f, int R_N, int L, const int* __restrict__ slots,
+                   SliceOut so) {
+  extern __shared__ __align__(16) float ul[];  // [kMaxLags + n + kMaxLags]
+  __shared__ float red[kMaxLags][kLagThreads / 32];
+  for (int k = threadIdx.x; k < kMaxLags; k += kLagThreads) {
+    ul[k] = 0.0f;
+    ul[kMaxLags + n + k] = 0.0f;
+  }
+  float* u = ul + kMaxLags;
+  for (long long col = blockIdx.x; col < 3LL * R_f; col += gridDim.x) {
+    __syncthreads();  // the previous column is consumed
+    const double2* src = reinterpret_cast<const double2*>(U + col * n);
+    for (int j = threadIdx.x; j < n / 2; j += kLagThreads) {
+      const double2 v = src[j];
+      *reinterpret_cast<float2*>(u + 2 * j) = make_float2(float(v.x), float(v.y));
+    }
+    __syncthreads();
+    float mx[kMaxLags];
+#pragma unroll
+    for (int m = 0; m < kMaxLags; ++m) mx[m] = 0.0f;
+    for (int i = threadIdx.x; i < n; i += kLagThreads) {
+      mx[0] = fmaxf(mx[0], fabsf(u[i]));
+#pragma unroll
+      for (int m = 1; m < kMaxLags; ++m)
+        if (m < L) mx[m] = fmaxf(mx[m], fabsf(u[i - m] + u[i + m]));
+    }
+#pragma unroll
+    for (int m = 0; m < kMaxLags; ++m) {
+      if (m < L) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx[m] = fmaxf(mx[m], __shfl_xor_sync(0xffffffffu, mx[m], o));
+        if ((threadIdx.x & 31) == 0) red[m][threadIdx.x >> 5] = mx[m];
+      }
+    }
+    __syncthreads();
+    const int l = int(col / R_f), srow = int(col - (long long)l * R_f);
+    for (int m = 0; m < L; ++m) {
+      float mm = red[m][0];
+#pragma unroll
+      for (int w = 1; w < kLagThreads / 32; ++w) mm = fmaxf(mm, red[m][w]);
+      const int q = __ldg(slots + m);
+      const int e = balanced_exponent(mm);
+      if (threadIdx.x == 0) so.expo[col * R_N + q] = e;
+      __nv_bfloat16* ob = so.out + ((long long)(l * R_N + q) * (n / 64) * so.R_f + srow) * 64;
+      float sc1, sc2;
+      slice_scales(e, sc1, sc2);
+      for (int i = 2 * threadIdx.x; i < n; i += 2 * kLagThreads) {
+        const float v0 = m ? u[i - m] + u[i + m] : u[i];
+        const float v1 = m ? u[i + 1 - m] + u[i + 1 + m] : u[i + 1];
+        slice_pair(v0, v1, sc1, sc2, ob + (long long)(i >> 6) * so.R_f * 64 + (i & 63), so.slice_stride);
+      }
+    }
+  }
+}
+
+// G_q = sum_{m <= H_q} p_q[m] S_m for the covered terms, in float32 as the
+// cell contraction forms G (S_m are its float32 values, the taps p_q[m] are
+// (hi, lo) pairs as in the banded kernel), the product over axes in float32
+// and the weighted sum in float64, as in the cell contraction: one covered
+// term and one 32 x 32 tile pair (row tile <= column tile) per CTA; E_H
+// partials in the cell contraction's convention (with c) and G (when given)
+__global__ void __launch_bounds__(kGramThreads)
+lag_gram_kernel(int R_f, int R_N, int L, const int* __restrict__ cov, const int* __restrict__ hq,
+                const float2* __restrict__ taps, const float* __restrict__ S, const double* __restrict__ c,
+                double* __restrict__ G, double* __restrict__ partial) {
+  __shared__ double red[kGramThreads / 32];
+  const int j = blockIdx.y;
+  const int q = __ldg(cov + j);
+  const int H = __ldg(hq + q);
+  const int nt = gram_tiles(R_f);
+  int pi = blockIdx.x, rt = 0;
+  while (pi >= nt - rt) {
+    pi -= nt - rt;
+    ++rt;
+  }
+  const int st = rt + pi;
+  float2 p[kMaxLags];
+#pragma unroll
+  for (int m = 0; m < kMaxLags; ++m)
+    p[m] = (m <= H && m < L) ? __ldg(taps + (size_t)q * kBandTaps + m) : make_float2(0.0f, 0.0f);
+  const size_t plane = (size_t)R_f * R_f;
+  double sum = 0.0;
+  for (int x = threadIdx.x; x < kGramTile * kGramTile; x += kGramThreads) {
+    const int r = rt * kGramTile + x / kGramTile, sc = st * kGramTile + x % kGramTile;
+    if (r >= R_f || sc >= R_f || (rt == st && r > sc)) continue;
+    float prod = 1.0f;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      float g = 0.0f;
+#pragma unroll
+      for (int m = 0; m < kMaxLags; ++m)
+        if (m <= H && m < L) {
+          const float sv = S[((size_t)l * L + m) * plane + (size_t)r * R_f + sc];
+          g = fmaf(p[m].x, sv, fmaf(p[m].y, sv, g));
+        }
+      if (G) {
+        double* Gq = G + ((size_t)l * R_N + q) * plane;
+        Gq[(size_t)r * R_f + sc] = g;
+        Gq[(size_t)sc * R_f + r] = g;
+      }
+      prod *= g;
+    }
+    if (c) sum += (r == sc ? 1.0 : 2.0) * __ldg(c + r) * __ldg(c + sc) * double(prod);
+  }
+  if (!c) return;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kGramThreads / 32; ++w) t += red[w];
+    partial[(size_t)j * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // The FFT terms of CPC_SPLIT and CPC_FP64_TC in double-float arithmetic
 // (dfloat.cuh): the same transform as conv_kernel<double> (float64 plan,
 // per-pass twiddles, half-angle step), with every table and the factor
@@ -1349,7 +1486,7 @@ int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const
 
 template <typename T, bool SLICE>
 int launch_band(const cpc_kernel* P, int ncols, const double* U, T* W, const SliceOut& so, const TermSplit& ts,
-                cudaStream_t s) {
+                cudaStream_t s, int slice_min_h = 0) {
   const size_t smem = sizeof(T) * (size_t(P->n) + 2 * kBandHalo) + (SLICE && sizeof(T) == 4 ? sizeof(float) * size_t(P->n) : 0);
   auto kern = band_conv_kernel<T, SLICE>;
   int st = configure(kern, smem);
@@ -1360,7 +1497,8 @@ int launch_band(const cpc_kernel* P, int ncols, const double* U, T* W, const Sli
   const long long grid = std::max(1LL, std::min(items, (long long)std::max(1, per_sm) * sm_count()));
   const void* taps = sizeof(T) == 4 ? static_cast<const void*>(P->d_taps32) : static_cast<const void*>(P->d_taps64);
   const int slot = timing_begin("band_conv_kernel", s);
-  kern<<<int(grid), kBandThreads, smem, s>>>(U, P->n, ncols, P->R_N, ts.band_q, ts.n_band, ts.band_h, taps, W, so);
+  kern<<<int(grid), kBandThreads, smem, s>>>(U, P->n, ncols, P->R_N, ts.band_q, ts.n_band, ts.band_h, taps, W, so,
+                                             slice_min_h);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("band_conv_kernel");
   return CPC_OK;
@@ -1542,7 +1680,10 @@ int run_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const Sl
   if (ts.n_smooth > 0 && !scratch) ts = term_split(P, sizeof(T) == 4 ? 0 : 1, nullptr);  // all by FFT
   int st = CPC_OK;
   if (ts.n_band > 0) {
-    st = launch_band<T, SLICE>(P, ncols, U, static_cast<T*>(W), so, ts, s);
+    // (the sliced float32 form takes its lag-covered terms from the lag Gram
+    // matrices: no slices for them)
+    st = launch_band<T, SLICE>(P, ncols, U, static_cast<T*>(W), so, ts, s,
+                               SLICE && sizeof(T) == 4 ? P->n_lag[0] : 0);
     if (st) return st;
   }
   if (ts.n_smooth > 0) {
@@ -1762,6 +1903,7 @@ void plan_term_paths(const cpc_kernel* P, int band32, int band64, int rank32, in
     const double eps = cls == 0 ? std::ldexp(1.0, -32) : std::ldexp(1.0, -44);
     int* hq = tp.terms.data() + size_t(cls) * kTermRows * R_N;
     int *kq = hq + R_N, *bl = hq + 2 * R_N, *sl = hq + 3 * R_N, *fl = hq + 4 * R_N, *dl = hq + 5 * R_N;
+    int *cl = hq + 6 * R_N, *el = hq + 7 * R_N;
     int nb = 0, ns = 0, nf = 0;
     for (int q = 0; q < R_N; ++q) {
       const double* p = P->p.data() + size_t(q) * n;
@@ -1795,8 +1937,32 @@ void plan_term_paths(const cpc_kernel* P, int band32, int band64, int rank32, in
     // the terms contracted over the cells: banded, then FFT
     for (int j = 0; j < nb; ++j) dl[j] = bl[j];
     for (int j = 0; j < nf; ++j) dl[nb + j] = fl[j];
+    // float32 energy path: the banded terms with H < L take their Gram
+    // matrices from the L lag Gram matrices (L contractions instead of one
+    // per covered term); L minimises L + (banded terms with H >= L), and the
+    // lag rows sit in the slice slots of the first L covered terms
+    int L = 0, cost = nb;
+    if (cls == 0)
+      for (int t = 1; t <= kMaxLags; ++t) {
+        int cov = 0;
+        for (int j = 0; j < nb; ++j) cov += hq[bl[j]] < t;
+        if (cov >= t && t + (nb - cov) < cost) {
+          cost = t + (nb - cov);
+          L = t;
+        }
+      }
+    int nc = 0, ne = 0;
+    for (int j = 0; j < nb; ++j) {
+      if (hq[bl[j]] < L) cl[nc++] = bl[j];
+      else el[ne++] = bl[j];
+    }
+    for (int j = 0; j < nf; ++j) el[ne++] = fl[j];
+    for (int m = 0; m < L; ++m) el[ne++] = cl[m];
     tp.n_band[cls] = nb;
     tp.n_smooth[cls] = ns;
+    tp.n_lag[cls] = L;
+    tp.n_cov[cls] = nc;
+    tp.n_eh[cls] = ne;
   }
 }
 
@@ -1811,6 +1977,9 @@ int build_term_tables(cpc_kernel* P, int band32, int band64, int rank32, int ran
     P->rank_k[cls].assign(hq + R_N, hq + 2 * R_N);
     P->n_band[cls] = tp.n_band[cls];
     P->n_smooth[cls] = tp.n_smooth[cls];
+    P->n_lag[cls] = tp.n_lag[cls];
+    P->n_cov[cls] = tp.n_cov[cls];
+    P->n_eh[cls] = tp.n_eh[cls];
   }
   P->band_max[0] = band32;
   P->band_max[1] = band64;
@@ -1895,6 +2064,54 @@ const int* dense_terms(const cpc_kernel* P, int cls, int* n_q) {
   }
   *n_q = P->R_N - P->n_smooth[cls];
   return P->d_terms + (size_t)cls * kTermRows * P->R_N + 5 * P->R_N;
+}
+
+const int* eh_terms(const cpc_kernel* P, int* n_q, int* n_virtual) {
+  if (!P->d_terms || P->n_eh[0] == 0 || (P->n_smooth[0] == 0 && P->n_lag[0] == 0)) {
+    *n_q = P->R_N;
+    *n_virtual = 0;
+    return nullptr;
+  }
+  *n_q = P->n_eh[0];
+  *n_virtual = P->n_lag[0];
+  return P->d_terms + 7 * P->R_N;
+}
+
+int lag_slices32(const cpc_kernel* P, int R_f, const double* U, const SliceRows& so, cudaStream_t s) {
+  const int L = P->n_lag[0];
+  if (L == 0) return CPC_OK;
+  const size_t smem = sizeof(float) * (size_t(P->n) + 2 * kMaxLags);
+  int st = configure(lag_slice32_kernel, smem);
+  if (st) return st;
+  int per_sm = 0;
+  CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lag_slice32_kernel, kLagThreads, smem));
+  const long long grid = std::max(1LL, std::min(3LL * R_f, (long long)std::max(1, per_sm) * sm_count()));
+  const int slot = timing_begin("lag_slice32_kernel", s);
+  lag_slice32_kernel<<<unsigned(grid), kLagThreads, smem, s>>>(U, P->n, R_f, P->R_N, L, P->d_terms + 6 * P->R_N, so);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("lag_slice32_kernel");
+  return CPC_OK;
+}
+
+size_t lag_gram_partials(const cpc_kernel* P, int R_f) {
+  const size_t nt = gram_tiles(R_f);
+  return size_t(P->R_N) * nt * (nt + 1) / 2;
+}
+
+int launch_lag_gram(const cpc_kernel* P, int R_f, const float* S, const double* c, double* G, double* partial,
+                    long long* n_partial, cudaStream_t s) {
+  *n_partial = 0;
+  const int L = P->n_lag[0];
+  if (L == 0) return CPC_OK;
+  const int nt = gram_tiles(R_f);
+  const dim3 grid(unsigned(nt * (nt + 1) / 2), unsigned(P->n_cov[0]));
+  const int slot = timing_begin("lag_gram_kernel", s);
+  lag_gram_kernel<<<grid, kGramThreads, 0, s>>>(R_f, P->R_N, L, P->d_terms + 6 * P->R_N, P->d_terms, P->d_taps32, S,
+                                                c, G, partial);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("lag_gram_kernel");
+  *n_partial = (long long)grid.x * grid.y;
+  return CPC_OK;
 }
 
 size_t cheb_moment_rows_scratch(const cpc_kernel* P, int ncols) {
