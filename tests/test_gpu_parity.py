@@ -251,6 +251,35 @@ def test_convolution_and_energy_fp64tc(cpc, name, spec):
 
 
 @pytest.mark.parametrize("name,spec", [CASES[0], CASES[2], CASES[3]])
+def test_fp32_energy_path_gram_shortcuts(cpc, name, spec):
+    # the float32 energy path takes the smooth terms' G from their Chebyshev
+    # moments and the narrow banded terms' G as tap-weighted sums of lag Gram
+    # matrices U^T (U shifted by +-m), contracting only the other terms (and
+    # the lag rows) over the cells; the factors path contracts every term of
+    # the same W over the cells: G and E_H agree, and both match the oracle
+    n, b, M, g = _case(name, spec)
+    h = 2 * b / n
+    P = cpc.make_newton_kernel(n, b, M)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    U = cpc.cp_sample_gaussians(n, b, dev(g["a"]), dev(g["X"]))
+    U0 = ocp.sample_gaussians(n, b, g["a"], g["X"])
+    hw, rk = P.conv_paths("fp32")
+    assert (hw >= 0).sum() > 0 and (rk > 0).sum() > 0
+    W0 = ocp.convolve_factors(U0, P0)
+    G0 = ocp.conv_matrices(U0, W0, P0.shape[0])
+    kappa = max(1.0, cancellation(G0, g["c"], h))
+    E, W, G = cpc.cp_hartree_energy(P, U, dev(g["c"]), "fp32", want_G=True)
+    E2, G2 = cpc.cp_hartree_energy_from_factors(P, U, dev(g["c"]), W, "fp32", want_G=True)
+    Gh = G.cpu().numpy()
+    assert rel(Gh, G2.cpu().numpy()) < 2e-6
+    assert rel(Gh, G0) < 2e-6
+    assert np.array_equal(Gh, np.swapaxes(Gh, 2, 3))
+    E0 = ocp.hartree_energy_from_G(G0, g["c"], h)
+    assert abs(E.item() / E0 - 1) < EH_TOL * kappa
+    assert abs(E.item() / E2.item() - 1) < EH_TOL * kappa
+
+
+@pytest.mark.parametrize("name,spec", [CASES[0], CASES[2], CASES[3]])
 def test_fp64tc_fused_slicing(cpc, name, spec):
     # cp_hartree_energy's float64 tensor-core form has the convolution kernels
     # (banded, Chebyshev, double-float FFT) write W's five-digit slices and row
