@@ -215,9 +215,9 @@ const int* eh_terms(const cpc_kernel* P, int* n_q, int* n_virtual);
 // of the first n_lag covered terms (SliceRows of the float32 form)
 int lag_slices32(const cpc_kernel* P, int R_f, const double* U, const SliceRows& so, cudaStream_t s);
 // G and E_H partials of the covered terms from the lag Gram matrices S
-// [3][n_lag][R_f][R_f] (float32): G_q = sum_{m <= H_q} p_q[m] S_m
+// [3][n_lag][R_f][R_f]: G_q = sum_{m <= H_q} p_q[m] S_m
 size_t lag_gram_partials(const cpc_kernel* P, int R_f);
-int launch_lag_gram(const cpc_kernel* P, int R_f, const float* S, const double* c, double* G, double* partial,
+int launch_lag_gram(const cpc_kernel* P, int R_f, const double* S, const double* c, double* G, double* partial,
                     long long* n_partial, cudaStream_t s);
 size_t cheb_gram_partials(const cpc_kernel* P, int R_f);
 int launch_cheb_gram(const cpc_kernel* P, int cls, int R_f, const void* scratch, const double* c, double* G,
@@ -280,10 +280,10 @@ void tc_w_slices(const cpc_kernel* P, int R_f, void* ws, __nv_bfloat16** slices,
                  int** expo);
 // qlist: the n_q kernel terms to contract (NULL: all); the partial slots of
 // the others are zeroed; the last n_virtual entries are lag rows whose Gram
-// matrices go to Gv [3][n_virtual][R_f][R_f] (float32)
+// matrices go to Gv [3][n_virtual][R_f][R_f]
 int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
                  double* partial, void* ws, cudaStream_t s, bool w_sliced = false, const int* qlist = nullptr,
-                 int n_q = -1, float* Gv = nullptr, int n_virtual = 0);
+                 int n_q = -1, double* Gv = nullptr, int n_virtual = 0);
 // the V_H factors and spectra of CPC_SPLIT and CPC_FP64_TC are float64, like CPC_FP64
 inline int storage_precision(int precision) { return precision == CPC_FP32 ? CPC_FP32 : CPC_FP64; }
 inline bool known_precision(int precision) {

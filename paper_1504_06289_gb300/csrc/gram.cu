@@ -569,7 +569,7 @@ int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doub
     st = lag_slices32(P, R_f, U, SliceRows{sl, sl_stride, ex, R_f}, s);
     if (st) return st;
     double* partial = static_cast<double*>(cws);
-    float* Sv = reinterpret_cast<float*>(static_cast<unsigned char*>(tws) + tc_workspace(P, R_f));
+    double* Sv = reinterpret_cast<double*>(static_cast<unsigned char*>(tws) + tc_workspace(P, R_f));
     int n_q = P->R_N, n_v = 0;
     const int* qlist = eh_terms(P, &n_q, &n_v);
     st = launch_eh_tc(P, R_f, U, static_cast<const float*>(W), c, G, partial, tws, s, true, qlist, n_q, Sv, n_v);

@@ -251,8 +251,7 @@ struct Args {
   const int* qlist;        // the kernel terms of blockIdx.y (NULL: term blockIdx.y)
   // E_H: the last n_virtual rows of the grid are lag rows (their W slice
   // slots hold lag rows, not the term's W): they write their Gram blocks to
-  // Gv [3][n_virtual][M][M] (float32 form: float, float64 form: double) and
-  // add nothing to E_H
+  // Gv [3][n_virtual][M][M] (float64) and add nothing to E_H
   void* Gv;
   int n_virtual;
 };
@@ -572,12 +571,9 @@ gemm3_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant_
               tot[j] = 0.0f;
               if (j & 1) lo[j / 2] = __float2bfloat162_rn(0.0f);
               const bool in = r < g.M && s < g.Ns && (!diag || r <= s);
-              if (in && virt) {
-                float* Gq = static_cast<float*>(g.Gv) + ((size_t)l * g.n_virtual + vrow) * (size_t)g.M * g.M;
-                Gq[(size_t)r * g.M + s] = Gv;
-                Gq[(size_t)s * g.M + r] = Gv;
-              } else if (in && g.G) {
-                double* Gq = g.G + ((size_t)l * g.R_N + q) * (size_t)g.M * g.M;
+              if (in && (virt || g.G)) {  // one store path (a second one costs registers)
+                double* Gq = virt ? static_cast<double*>(g.Gv) + ((size_t)l * g.n_virtual + vrow) * (size_t)g.M * g.M
+                                  : g.G + ((size_t)l * g.R_N + q) * (size_t)g.M * g.M;
                 Gq[(size_t)r * g.M + s] = Gv;
                 Gq[(size_t)s * g.M + r] = Gv;
               }
@@ -917,7 +913,7 @@ int launch_tc(const cpc_kernel* P, int M, int Ns, const double* U, const float* 
 }  // namespace
 
 int launch_eh_tc(const cpc_kernel* P, int R_f, const double* U, const float* W, const double* c, double* G,
-                 double* partial, void* ws, cudaStream_t s, bool w_sliced, const int* qlist, int n_q, float* Gv,
+                 double* partial, void* ws, cudaStream_t s, bool w_sliced, const int* qlist, int n_q, double* Gv,
                  int n_virtual) {
   // with a term list the other terms' partial slots stay zero
   if (qlist) CPC_CUDA(cudaMemsetAsync(partial, 0, sizeof(double) * tc_partials(R_f, P->R_N), s));

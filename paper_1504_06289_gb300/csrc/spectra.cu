@@ -809,22 +809,23 @@ cheb_moments_kernel(const double* __restrict__ U, int n, int ncols, const void* 
 }
 
 // one CTA per column: the moments summed over the cell ranges once (kept in
-// Mom[col][kCheb]), then one thread per smooth term j: d_k for k < K (zero up
-// to kCheb) into D[col n_smooth + j][kCheb] (and D64 in float64, when given)
-// and the item's record
+// Mom[col][kCheb] as double-float pairs), then one thread per smooth term j:
+// d_k for k < K (zero up to kCheb) into D[col n_smooth + j][kCheb] (and Ddf as
+// double-float pairs) and the item's record
 constexpr int kChebCoefThreads = 64;
 template <typename T>
 __global__ void __launch_bounds__(kChebCoefThreads)
 cheb_coef_kernel(int n, int ncols, int R_N, const int* __restrict__ qlist, int n_smooth, const int* __restrict__ kq,
                  const double* __restrict__ cheb, const double* __restrict__ Part, T* __restrict__ D,
-                 ChebItem* __restrict__ items, double* __restrict__ Mom, double* __restrict__ D64) {
+                 ChebItem* __restrict__ items, float2* __restrict__ Mom, float2* __restrict__ Ddf) {
   const int col = blockIdx.x;
   __shared__ double m[kCheb];
   if (threadIdx.x < kCheb) {
     double acc = 0.0;
     for (int r = 0; r < cheb_ranges(n); ++r) acc += Part[((size_t)r * ncols + col) * kCheb + threadIdx.x];
     m[threadIdx.x] = acc;
-    Mom[(size_t)col * kCheb + threadIdx.x] = acc;  // for the Gram matrices (cheb_gram_kernel)
+    const df a(acc);  // for the Gram matrices (cheb_gram_kernel), as double-float pairs
+    Mom[(size_t)col * kCheb + threadIdx.x] = make_float2(a.hi, a.lo);
   }
   __syncthreads();
   for (int j = threadIdx.x; j < n_smooth; j += kChebCoefThreads) {
@@ -837,7 +838,8 @@ cheb_coef_kernel(int n, int ncols, int R_N, const int* __restrict__ qlist, int n
       if (r < K)
         for (int l = 0; l < K; ++l) d = fma(__ldg(C + r * kCheb + l), m[l], d);
       D[k * kCheb + r] = T(d);
-      if (D64) D64[k * kCheb + r] = d;
+      const df dd(d);
+      Ddf[k * kCheb + r] = make_float2(dd.hi, dd.lo);
     }
     ChebItem it;
     it.w_off = ((long long)col * R_N + q) * n;
@@ -961,7 +963,7 @@ __host__ __device__ constexpr int gram_tiles(int R_f) { return (R_f + kGramTile 
 
 __global__ void __launch_bounds__(kGramThreads)
 cheb_gram_kernel(int R_f, int R_N, const int* __restrict__ smooth_q, int n_smooth, const int* __restrict__ kq,
-                 const double* __restrict__ Mom, const double* __restrict__ D64, const double* __restrict__ c,
+                 const float2* __restrict__ Mom, const float2* __restrict__ Ddf, const double* __restrict__ c,
                  double* __restrict__ G, double* __restrict__ partial) {
   constexpr int TP = kGramTile + 2;  // padded rows (16-byte aligned for the paired reads)
   __shared__ __align__(16) float2 mr[3][kCheb][TP];  // double-float (hi, lo)
@@ -982,15 +984,14 @@ cheb_gram_kernel(int R_f, int R_N, const int* __restrict__ smooth_q, int n_smoot
   for (int x = threadIdx.x; x < 3 * kGramTile * kCheb; x += kGramThreads) {
     const int k = x % kCheb, i = (x / kCheb) % kGramTile, l = x / (kCheb * kGramTile);
     const int r = r0 + i, sc = s0 + i;
-    const df a = (r < R_f && k < K) ? df(__ldg(Mom + (size_t)(l * R_f + r) * kCheb + k)) : df();
-    const df d = (sc < R_f && k < K) ? df(__ldg(D64 + ((size_t)(l * R_f + sc) * n_smooth + j) * kCheb + k)) : df();
-    mr[l][k][i] = make_float2(a.hi, a.lo);
-    ds[l][k][i] = make_float2(d.hi, d.lo);
+    const float2 z = make_float2(0.0f, 0.0f);
+    mr[l][k][i] = (r < R_f && k < K) ? __ldg(Mom + (size_t)(l * R_f + r) * kCheb + k) : z;
+    ds[l][k][i] = (sc < R_f && k < K) ? __ldg(Ddf + ((size_t)(l * R_f + sc) * n_smooth + j) * kCheb + k) : z;
   }
   __syncthreads();
   const int tr = threadIdx.x / 8, ts = 4 * (threadIdx.x % 8);
   const int r = r0 + tr;
-  double Gv[3][4];
+  float Gh[3][4], Gl[3][4];  // each entry as the unevaluated sum Gh + Gl
 #pragma unroll
   for (int l = 0; l < 3; ++l) {
     float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
@@ -1009,7 +1010,10 @@ cheb_gram_kernel(int R_f, int R_N, const int* __restrict__ smooth_q, int n_smoot
       }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) Gv[l][i] = double(hi[i]) + double(lo[i]);
+    for (int i = 0; i < 4; ++i) {
+      Gh[l][i] = hi[i];
+      Gl[l][i] = lo[i];
+    }
   }
   double sum = 0.0;
 #pragma unroll
@@ -1019,12 +1023,19 @@ cheb_gram_kernel(int R_f, int R_N, const int* __restrict__ smooth_q, int n_smoot
     if (G) {
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
+        const double gv = double(Gh[l][i]) + double(Gl[l][i]);
         double* Gq = G + ((size_t)l * R_N + q) * R_f * R_f;
-        Gq[(size_t)r * R_f + sc] = Gv[l][i];
-        Gq[(size_t)sc * R_f + r] = Gv[l][i];
+        Gq[(size_t)r * R_f + sc] = gv;
+        Gq[(size_t)sc * R_f + r] = gv;
       }
     }
-    if (c) sum += (r == sc ? 1.0 : 2.0) * __ldg(c + sc) * (Gv[0][i] * Gv[1][i] * Gv[2][i]);
+    // E_H: the product over axes in float32, the weighted sum in float64 (as the
+    // cell contraction forms it)
+    if (c) {
+      const float pr = (Gh[0][i] + Gl[0][i]) * (Gh[1][i] + Gl[1][i]) * (Gh[2][i] + Gl[2][i]);
+      const double cs = __ldg(c + sc);
+      sum = fma(r == sc ? cs : 2.0 * cs, double(pr), sum);
+    }
   }
   if (!c) return;
   if (r < R_f) sum *= __ldg(c + r);
@@ -1136,15 +1147,29 @@ lag_slice32_kernel(const double* __restrict__ U, int n, int R_f, int R_N, int L,
   }
 }
 
+// A float64 that holds a float32 value exactly, as float32, by integer work on
+// its IEEE-754 fields (sign, exponent rebiased from 1023 to 127, the top 23
+// mantissa bits): no float64 instruction, whose rate here is 1/64 of
+// float32.  Values below the float32 normal range (2^-126) are taken as zero.
+__device__ __forceinline__ float float_of_exact_double(double d) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(d));
+  const unsigned hi = unsigned(b >> 32);
+  const int e = int((hi >> 20) & 0x7FFu);
+  if (e <= 896) return 0.0f;
+  return __uint_as_float((hi & 0x80000000u) | (unsigned(e - 896) << 23) | ((hi & 0xFFFFFu) << 3) |
+                         unsigned((b & 0xFFFFFFFFull) >> 29));
+}
+
 // G_q = sum_{m <= H_q} p_q[m] S_m for the covered terms, in float32 as the
-// cell contraction forms G (S_m are its float32 values, the taps p_q[m] are
-// (hi, lo) pairs as in the banded kernel), the product over axes in float32
-// and the weighted sum in float64, as in the cell contraction: one covered
+// cell contraction forms G (S_m are its float32 values, stored as float64;
+// the taps p_q[m] are (hi, lo) pairs as in the banded kernel), the product
+// over axes in float32 and the weighted sum in float64, as in the cell
+// contraction: one covered
 // term and one 32 x 32 tile pair (row tile <= column tile) per CTA; E_H
 // partials in the cell contraction's convention (with c) and G (when given)
 __global__ void __launch_bounds__(kGramThreads)
 lag_gram_kernel(int R_f, int R_N, int L, const int* __restrict__ cov, const int* __restrict__ hq,
-                const float2* __restrict__ taps, const float* __restrict__ S, const double* __restrict__ c,
+                const float2* __restrict__ taps, const double* __restrict__ S, const double* __restrict__ c,
                 double* __restrict__ G, double* __restrict__ partial) {
   __shared__ double red[kGramThreads / 32];
   const int j = blockIdx.y;
@@ -1173,7 +1198,7 @@ lag_gram_kernel(int R_f, int R_N, int L, const int* __restrict__ cov, const int*
 #pragma unroll
       for (int m = 0; m < kMaxLags; ++m)
         if (m <= H && m < L) {
-          const float sv = S[((size_t)l * L + m) * plane + (size_t)r * R_f + sc];
+          const float sv = float_of_exact_double(S[((size_t)l * L + m) * plane + (size_t)r * R_f + sc]);
           g = fmaf(p[m].x, sv, fmaf(p[m].y, sv, g));
         }
       if (G) {
@@ -1425,15 +1450,15 @@ TermSplit term_split(const cpc_kernel* P, int cls, const double* U) {
 }
 
 // the Chebyshev path's scratch: partial moments [ranges][ncols][kCheb], item
-// records [ncols R_N], coefficients in the W type [ncols R_N][kCheb], the
-// summed moments [ncols][kCheb] and the float64 coefficients (float32 W; for
-// float64 W they are D itself)
+// records [ncols R_N], coefficients in the W type [ncols R_N][kCheb], then
+// for the Gram matrices the summed moments [ncols][kCheb] and the
+// coefficients [ncols R_N][kCheb] as double-float pairs
 struct SmoothScratch {
   double* Part;
   ChebItem* recs;
   void* D;
-  double* Mom;
-  double* D64;
+  float2* Mom;  // summed moments, double-float pairs
+  float2* Ddf;  // coefficients, double-float pairs
 };
 SmoothScratch smooth_scratch(const cpc_kernel* P, int ncols, const void* scratch, size_t wbytes) {
   unsigned char* sc = static_cast<unsigned char*>(const_cast<void*>(scratch));
@@ -1444,9 +1469,9 @@ SmoothScratch smooth_scratch(const cpc_kernel* P, int ncols, const void* scratch
   sc += align256(sizeof(ChebItem) * size_t(ncols) * P->R_N);
   sm.D = sc;
   sc += align256(sizeof(double) * size_t(ncols) * P->R_N * kCheb);
-  sm.Mom = reinterpret_cast<double*>(sc);
-  sc += align256(sizeof(double) * size_t(ncols) * kCheb);
-  sm.D64 = wbytes == sizeof(double) ? static_cast<double*>(sm.D) : reinterpret_cast<double*>(sc);
+  sm.Mom = reinterpret_cast<float2*>(sc);
+  sc += align256(sizeof(float2) * size_t(ncols) * kCheb);
+  sm.Ddf = reinterpret_cast<float2*>(sc);
   return sm;
 }
 
@@ -1654,7 +1679,7 @@ int launch_smooth(const cpc_kernel* P, int ncols, const double* U, T* W, const T
   slot = timing_begin("cheb_coef_kernel", s);
   cheb_coef_kernel<T><<<ncols, kChebCoefThreads, 0, s>>>(n, ncols, P->R_N, ts.smooth_q, ts.n_smooth,
                                                                  ts.smooth_k, P->d_cheb, Part, D, recs, sm.Mom,
-                                                                 sizeof(T) == 4 ? sm.D64 : nullptr);
+                                                                 sm.Ddf);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("cheb_coef_kernel");
   slot = timing_begin("cheb_eval_kernel", s);
@@ -2098,7 +2123,7 @@ size_t lag_gram_partials(const cpc_kernel* P, int R_f) {
   return size_t(P->R_N) * nt * (nt + 1) / 2;
 }
 
-int launch_lag_gram(const cpc_kernel* P, int R_f, const float* S, const double* c, double* G, double* partial,
+int launch_lag_gram(const cpc_kernel* P, int R_f, const double* S, const double* c, double* G, double* partial,
                     long long* n_partial, cudaStream_t s) {
   *n_partial = 0;
   const int L = P->n_lag[0];
@@ -2160,7 +2185,7 @@ int launch_cheb_gram(const cpc_kernel* P, int cls, int R_f, const void* scratch,
   const int nt = gram_tiles(R_f);
   const dim3 grid(unsigned(nt * (nt + 1) / 2), unsigned(n_smooth));
   const int slot = timing_begin("cheb_gram_kernel", s);
-  cheb_gram_kernel<<<grid, kGramThreads, 0, s>>>(R_f, R_N, rows + 3 * R_N, n_smooth, rows + R_N, sm.Mom, sm.D64, c, G,
+  cheb_gram_kernel<<<grid, kGramThreads, 0, s>>>(R_f, R_N, rows + 3 * R_N, n_smooth, rows + R_N, sm.Mom, sm.Ddf, c, G,
                                                  partial);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("cheb_gram_kernel");
