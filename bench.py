@@ -506,14 +506,15 @@ def run_ours(args, ws, rank, local):
     cg_ms = 0.0
     if prec in ("fp32", "fp64tc", "split"):
         n_dense = R_N - n_smooth
-        if prec == "fp32":
+        if prec in ("fp32", "fp64tc"):
             # lag rows replace the covered banded terms in the cell contraction
             n_lag, n_cov = lag_count(hw)
             n_dense += n_lag - n_cov
             if n_lag:
                 ls_ms, _ = per_launch("lag_slice32_kernel", 0.0)
                 lg_ms, _ = per_launch("lag_gram_kernel", 0.0)
-                lag_bytes = 3 * R_f * n * 8 + 3 * R_f * n_lag * n * 6  # U read, lag-row slices written
+                # U read, lag-row slices written (3 bf16 digits per cell, 5 in the float64 form)
+                lag_bytes = 3 * R_f * n * 8 + 3 * R_f * n_lag * n * (6 if prec == "fp32" else 10)
                 kernels["lag_kernels"] = {
                     "ms": ls_ms + lg_ms, "bound": "hbm", "achieved": lag_bytes / ((ls_ms + lg_ms) * 1e-3) / 1e9,
                     "unit": "GB/s", "peak": hbm_peak,
@@ -596,7 +597,7 @@ def run_ours(args, ws, rank, local):
         # [fp64tc: E_H from G,] final sum; banded conv; Chebyshev moments, coefficients,
         # evaluation [and the smooth terms' Gram matrices]
         "gpu_launches": ({"fp32": 6, "fp64tc": 8}.get(prec, 5) + (1 if n_band else 0)
-                         + (2 if prec == "fp32" and lag_count(hw)[0] else 0)
+                         + (2 if prec in ("fp32", "fp64tc") and lag_count(hw)[0] else 0)
                          + ((4 if prec in ("fp32", "fp64tc", "split") else 3) if n_smooth else 0)
                          - (0 if n_fft else 1)) * args.steps,
         "clocks": clk,

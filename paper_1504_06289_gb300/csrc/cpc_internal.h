@@ -180,7 +180,7 @@ int build_term_tables(cpc_kernel* P, int band32, int band64, int rank32, int ran
 // [H per term][K per term][banded list][smooth list][FFT list], the taps, the
 // Chebyshev coefficients [R_N][16][16] and the table T_k(x_i/b) [16][n]
 constexpr int kTermRows = 8;  // rows of d_terms per precision class
-constexpr int kMaxLags = 8;   // largest lag count of the float32 energy path
+constexpr int kMaxLags = 8;   // largest lag count of the tensor-core energy paths
 struct TermPlan {
   std::vector<int> terms;  // [2][kTermRows][R_N]
   std::vector<float2> taps32;
@@ -207,9 +207,14 @@ size_t smooth_scratch_bytes(const cpc_kernel* P, int ncols);
 // cell contraction takes (n_q of them)
 bool cheb_gram_active(const cpc_kernel* P, int cls);
 const int* dense_terms(const cpc_kernel* P, int cls, int* n_q);
-// the float32 energy path (class 0): its contraction list (n_q entries, the
-// last n_virtual of them lag rows) and the lag-covered banded terms
-const int* eh_terms(const cpc_kernel* P, int* n_q, int* n_virtual);
+// the tensor-core energy path of W type class cls (FP32: 0, FP64_TC: 1): its
+// contraction list (n_q entries, the last n_virtual of them lag rows; NULL:
+// every term)
+const int* eh_terms(const cpc_kernel* P, int cls, int* n_q, int* n_virtual);
+// FP64_TC: the lag rows as five-digit float64 slices (as lag_slices32), and
+// the covered terms' G = sum_m p_q[m] S_m in float64 into G [3][R_N][R_f][R_f]
+int lag_slices64(const cpc_kernel* P, int R_f, const double* U, const SliceRows& so, cudaStream_t s);
+int launch_lag_gram64(const cpc_kernel* P, int R_f, const double* S, double* G, cudaStream_t s);
 // lag rows V_m = U shifted by +m plus U shifted by -m (V_0 = U), m < n_lag, as
 // balanced three-digit slices with their row exponents in the W slice slots
 // of the first n_lag covered terms (SliceRows of the float32 form)
@@ -260,8 +265,9 @@ size_t tc64_workspace(const cpc_kernel* P, int R_f);
 int* tc64_status_ptr(const cpc_kernel* P, int R_f, void* ws);
 // w_sliced: the convolution already wrote W's slices and row exponents where
 // tc64_w_slices points; cheb_scratch: that convolution's scratch, whose
-// moments give the smooth terms' G (the cell contraction then takes only the
-// other terms; NULL: every term by the cell contraction)
+// moments give the smooth terms' G, the lag rows (lag_slices64, already in
+// the W slices) the lag-covered terms' G (the cell contraction then takes
+// only the other terms; NULL: every term by the cell contraction)
 int launch_eh_tc64(const cpc_kernel* P, int R_f, const double* U, const double* W, const double* c, double* G,
                    double* partial, void* ws, cudaStream_t s, bool w_sliced = false,
                    const void* cheb_scratch = nullptr);

@@ -571,7 +571,7 @@ int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doub
     double* partial = static_cast<double*>(cws);
     double* Sv = reinterpret_cast<double*>(static_cast<unsigned char*>(tws) + tc_workspace(P, R_f));
     int n_q = P->R_N, n_v = 0;
-    const int* qlist = eh_terms(P, &n_q, &n_v);
+    const int* qlist = eh_terms(P, 0, &n_q, &n_v);
     st = launch_eh_tc(P, R_f, U, static_cast<const float*>(W), c, G, partial, tws, s, true, qlist, n_q, Sv, n_v);
     if (st) return st;
     long long count = (long long)tc_partials(R_f, P->R_N), n_more = 0;
@@ -592,9 +592,13 @@ int run_hartree_energy(const cpc_kernel* P, int R_f, const double* U, const doub
     const SliceRows so = tc64_w_slices(P, R_f, tws);
     int st = run_convolve(P, R_f, U, W, precision, ws, s, &so);
     if (st) return st;
+    st = lag_slices64(P, R_f, U, so, s);  // the lag rows of the narrow terms
+    if (st) return st;
     double* partial = static_cast<double*>(cws);
+    // (with smooth or lag-covered terms, their G come from the convolution's
+    // scratch and the lag rows; the contraction then takes the rest)
     st = launch_eh_tc64(P, R_f, U, static_cast<const double*>(W), c, G, partial, tws, s, true,
-                        cheb_gram_active(P, 1) ? scratch : nullptr);
+                        cheb_gram_active(P, 1) || P->n_lag[1] > 0 ? scratch : nullptr);
     if (st) return st;
     finalize_sum_kernel<<<1, 1024, 0, s>>>(partial, (long long)tc64_partials(R_f, P->R_N), P->h * P->h * P->h, E_H,
                                            tc64_status_ptr(P, R_f, tws));

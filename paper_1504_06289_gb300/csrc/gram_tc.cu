@@ -755,7 +755,7 @@ namespace {
 // convolution matrices G,) then the W slices (each 256-aligned)
 struct TcLayout {
   size_t a, b;  // slice elements of A and W (all slices, 3 axes)
-  size_t off_ea, off_eb, off_status, off_g, off_b, total;
+  size_t off_ea, off_eb, off_status, off_g, off_b, off_v, total;
 };
 TcLayout tc_layout(const cpc_kernel* P, int M, int Ns, int ns = 3, bool with_g = false) {
   TcLayout L;
@@ -766,7 +766,9 @@ TcLayout tc_layout(const cpc_kernel* P, int M, int Ns, int ns = 3, bool with_g =
   L.off_status = L.off_eb + align256(4 * size_t(3) * Ns * P->R_N);
   L.off_g = L.off_status + 256;
   L.off_b = L.off_g + (with_g ? align256(sizeof(double) * 3 * size_t(P->R_N) * M * M) : 0);
-  L.total = L.off_b + align256(2 * L.b);
+  // (CPC_FP64_TC: then the lag rows' Gram matrices [3][kMaxLags][M][M])
+  L.off_v = L.off_b + align256(2 * L.b);
+  L.total = L.off_v + (with_g ? align256(sizeof(double) * 3 * kMaxLags * size_t(M) * M) : 0);
   return L;
 }
 }  // namespace
@@ -945,13 +947,16 @@ int launch_eh_tc64(const cpc_kernel* P, int R_f, const double* U, const double* 
     if (st) return st;
   }
   double* Gd = G ? G : reinterpret_cast<double*>(w + L.off_g);
-  int n_q = P->R_N;
-  const int* qlist = cheb_scratch ? dense_terms(P, 1, &n_q) : nullptr;
-  st = launch_tc_kernel<tc::Form64, true>(P, R_f, R_f, L, w, c, c, Gd, partial, s, 0, 1, qlist, n_q);
+  int n_q = P->R_N, n_v = 0;
+  const int* qlist = cheb_scratch ? eh_terms(P, 1, &n_q, &n_v) : nullptr;
+  double* Gv = reinterpret_cast<double*>(w + L.off_v);
+  st = launch_tc_kernel<tc::Form64, true>(P, R_f, R_f, L, w, c, c, Gd, partial, s, 0, 1, qlist, n_q, Gv, n_v);
   if (st) return st;
-  if (qlist) {  // the smooth terms' G from their moments
+  if (qlist) {  // the smooth terms' G from their moments, the narrow ones' from the lag Gram matrices
     long long np = 0;
     st = launch_cheb_gram(P, 1, R_f, cheb_scratch, nullptr, Gd, nullptr, &np, s);
+    if (st) return st;
+    st = launch_lag_gram64(P, R_f, Gv, Gd, s);
     if (st) return st;
   }
   tc::eh_from_g_kernel<<<dim3(R_f, R_N), 128, 0, s>>>(Gd, c, R_f, R_N, partial);

@@ -546,7 +546,7 @@ __device__ __forceinline__ T band_rows(const T* __restrict__ us, int n, const vo
     for (int m = 0; m <= H; ++m) ph[m] = __ldg(tp + m);
   }
   int e64 = 0;
-  if constexpr (SLICE && sizeof(T) == 8) {
+  if constexpr (SLICE && sizeof(T) == 8) if (b64.ob) {  // (NULL: a lag-covered term, no slices)
     // the float64 sum of 2H + 1 products stays below the bound times
     // (1 + (2H + 2) 2^-53); 2^e above the bound times (1 + 2^-40)
     double S = fabs(ph[0]);
@@ -593,7 +593,7 @@ __device__ __forceinline__ T band_rows(const T* __restrict__ us, int n, const vo
       if constexpr (sizeof(T) == 4) {
         *reinterpret_cast<V*>(ws + i) = cmk<V>(a0, a1);
         mx = fmaxf(mx, fmaxf(fabsf(a0), fabsf(a1)));
-      } else {
+      } else if (b64.ob) {
         constexpr int C = kSlice64Cells;
         slice64_pair(a0, a1, e64, b64.ob + (long long)(i / C) * b64.R_f * C + (i % C), b64.stride);
       }
@@ -666,14 +666,14 @@ band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const 
     const long long item = col * R_N + q;
     const void* tq = (sizeof(T) == 4) ? static_cast<const void*>(static_cast<const float2*>(taps) + (size_t)q * kBandTaps)
                                       : static_cast<const void*>(static_cast<const double*>(taps) + (size_t)q * kBandTaps);
+    const int h = __ldg(hq + q);
     BandSlice64 b64{nullptr, 0, 0, nullptr, umax};
-    if constexpr (SLICE && sizeof(T) == 8) {
+    if constexpr (SLICE && sizeof(T) == 8) if (h >= slice_min_h) {
       constexpr int C = kSlice64Cells;
       const int l = int(col / so.R_f), srow = int(col - (long long)l * so.R_f);
       b64 = BandSlice64{so.out + ((long long)(l * R_N + q) * (n / C) * so.R_f + srow) * C, so.slice_stride, so.R_f,
                         so.expo + item, umax};
     }
-    const int h = __ldg(hq + q);
     T mx = band_dispatch<T, SLICE>(h, us, n, tq, W + (size_t)item * n, ws, b64);
     // float32: the terms with H < slice_min_h get no slices (their Gram
     // matrices come from the lag Gram matrices); h is the same for the CTA
@@ -1143,6 +1143,96 @@ lag_slice32_kernel(const double* __restrict__ U, int n, int R_f, int R_N, int L,
         const float v1 = m ? u[i + 1 - m] + u[i + 1 + m] : u[i + 1];
         slice_pair(v0, v1, sc1, sc2, ob + (long long)(i >> 6) * so.R_f * 64 + (i & 63), so.slice_stride);
       }
+    }
+  }
+}
+
+// The float64 form's lag rows (FP64_TC): V_m in float64 (one addition per
+// cell), sliced into the five weighted digits of the float64 form with the
+// row's largest exponent field, into the slot of the m-th covered term; a CTA
+// per (axis, column) stages the column in shared memory as lag_slice32_kernel.
+__global__ void __launch_bounds__(kLagThreads)
+lag_slice64_kernel(const double* __restrict__ U, int n, int R_f, int R_N, int L, const int* __restrict__ slots,
+                   SliceOut so) {
+  extern __shared__ __align__(16) double ud[];  // [kMaxLags + n + kMaxLags]
+  __shared__ int red[kMaxLags][kLagThreads / 32];
+  constexpr int C = kSlice64Cells;
+  for (int k = threadIdx.x; k < kMaxLags; k += kLagThreads) {
+    ud[k] = 0.0;
+    ud[kMaxLags + n + k] = 0.0;
+  }
+  double* u = ud + kMaxLags;
+  for (long long col = blockIdx.x; col < 3LL * R_f; col += gridDim.x) {
+    __syncthreads();  // the previous column is consumed
+    const double2* src = reinterpret_cast<const double2*>(U + col * n);
+    for (int j = threadIdx.x; j < n / 2; j += kLagThreads) *reinterpret_cast<double2*>(u + 2 * j) = src[j];
+    __syncthreads();
+    int mb[kMaxLags];
+#pragma unroll
+    for (int m = 0; m < kMaxLags; ++m) mb[m] = 0;
+    for (int i = threadIdx.x; i < n; i += kLagThreads) {
+      mb[0] = max(mb[0], biased_exponent64(u[i]));
+#pragma unroll
+      for (int m = 1; m < kMaxLags; ++m)
+        if (m < L) mb[m] = max(mb[m], biased_exponent64(u[i - m] + u[i + m]));
+    }
+#pragma unroll
+    for (int m = 0; m < kMaxLags; ++m) {
+      if (m < L) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mb[m] = max(mb[m], __shfl_xor_sync(0xffffffffu, mb[m], o));
+        if ((threadIdx.x & 31) == 0) red[m][threadIdx.x >> 5] = mb[m];
+      }
+    }
+    __syncthreads();
+    const int l = int(col / R_f), srow = int(col - (long long)l * R_f);
+    for (int m = 0; m < L; ++m) {
+      int mm = red[m][0];
+#pragma unroll
+      for (int w = 1; w < kLagThreads / 32; ++w) mm = max(mm, red[m][w]);
+      const int q = __ldg(slots + m);
+      const int e = row_exponent64(mm);
+      if (threadIdx.x == 0) so.expo[col * R_N + q] = e;
+      __nv_bfloat16* ob = so.out + ((long long)(l * R_N + q) * (n / C) * so.R_f + srow) * C;
+      for (int i = 2 * threadIdx.x; i < n; i += 2 * kLagThreads) {
+        const double v0 = m ? u[i - m] + u[i + m] : u[i];
+        const double v1 = m ? u[i + 1 - m] + u[i + 1 + m] : u[i + 1];
+        slice64_pair(v0, v1, e, ob + (long long)(i / C) * so.R_f * C + (i % C), so.slice_stride);
+      }
+    }
+  }
+}
+
+// FP64_TC: G_q = sum_{m <= H_q} p_q[m] S_m of the covered terms in float64
+// into G (both triangles), for the E_H sum over G that follows
+__global__ void __launch_bounds__(kGramThreads)
+lag_gram64_kernel(int R_f, int R_N, int L, const int* __restrict__ cov, const int* __restrict__ hq,
+                  const double* __restrict__ taps, const double* __restrict__ S, double* __restrict__ G) {
+  const int q = __ldg(cov + blockIdx.y);
+  const int H = __ldg(hq + q);
+  const int nt = gram_tiles(R_f);
+  int pi = blockIdx.x, rt = 0;
+  while (pi >= nt - rt) {
+    pi -= nt - rt;
+    ++rt;
+  }
+  const int st = rt + pi;
+  double p[kMaxLags];
+#pragma unroll
+  for (int m = 0; m < kMaxLags; ++m) p[m] = (m <= H && m < L) ? __ldg(taps + (size_t)q * kBandTaps + m) : 0.0;
+  const size_t plane = (size_t)R_f * R_f;
+  for (int x = threadIdx.x; x < kGramTile * kGramTile; x += kGramThreads) {
+    const int r = rt * kGramTile + x / kGramTile, sc = st * kGramTile + x % kGramTile;
+    if (r >= R_f || sc >= R_f || (rt == st && r > sc)) continue;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      double g = 0.0;
+#pragma unroll
+      for (int m = 0; m < kMaxLags; ++m)
+        if (m <= H && m < L) g = fma(p[m], S[((size_t)l * L + m) * plane + (size_t)r * R_f + sc], g);
+      double* Gq = G + ((size_t)l * R_N + q) * plane;
+      Gq[(size_t)r * R_f + sc] = g;
+      Gq[(size_t)sc * R_f + r] = g;
     }
   }
 }
@@ -1962,13 +2052,13 @@ void plan_term_paths(const cpc_kernel* P, int band32, int band64, int rank32, in
     // the terms contracted over the cells: banded, then FFT
     for (int j = 0; j < nb; ++j) dl[j] = bl[j];
     for (int j = 0; j < nf; ++j) dl[nb + j] = fl[j];
-    // float32 energy path: the banded terms with H < L take their Gram
-    // matrices from the L lag Gram matrices (L contractions instead of one
-    // per covered term); L minimises L + (banded terms with H >= L), and the
-    // lag rows sit in the slice slots of the first L covered terms
+    // tensor-core energy paths (FP32: class 0, FP64_TC: class 1): the banded
+    // terms with H < L take their Gram matrices from the L lag Gram matrices
+    // (L contractions instead of one per covered term); L minimises
+    // L + (banded terms with H >= L), and the lag rows sit in the slice slots
+    // of the first L covered terms
     int L = 0, cost = nb;
-    if (cls == 0)
-      for (int t = 1; t <= kMaxLags; ++t) {
+    for (int t = 1; t <= kMaxLags; ++t) {
         int cov = 0;
         for (int j = 0; j < nb; ++j) cov += hq[bl[j]] < t;
         if (cov >= t && t + (nb - cov) < cost) {
@@ -2062,7 +2152,9 @@ int convolve_spectra_df(const cpc_kernel* P, int ncols, void* Uhat, double* W, c
   if (ts.n_smooth > 0 && !scratch) ts = term_split(P, 1, nullptr);
   int st = CPC_OK;
   if (ts.n_band > 0) {
-    st = so64 ? launch_band<double, true>(P, ncols, U, W, so, ts, s) : launch_band<double, false>(P, ncols, U, W, so, ts, s);
+    // (FP64_TC: the lag-covered terms get no slices)
+    st = so64 ? launch_band<double, true>(P, ncols, U, W, so, ts, s, P->n_lag[1])
+              : launch_band<double, false>(P, ncols, U, W, so, ts, s);
     if (st) return st;
   }
   if (ts.n_smooth > 0) {
@@ -2091,15 +2183,45 @@ const int* dense_terms(const cpc_kernel* P, int cls, int* n_q) {
   return P->d_terms + (size_t)cls * kTermRows * P->R_N + 5 * P->R_N;
 }
 
-const int* eh_terms(const cpc_kernel* P, int* n_q, int* n_virtual) {
-  if (!P->d_terms || P->n_eh[0] == 0 || (P->n_smooth[0] == 0 && P->n_lag[0] == 0)) {
+const int* eh_terms(const cpc_kernel* P, int cls, int* n_q, int* n_virtual) {
+  if (!P->d_terms || P->n_eh[cls] == 0 || (P->n_smooth[cls] == 0 && P->n_lag[cls] == 0)) {
     *n_q = P->R_N;
     *n_virtual = 0;
     return nullptr;
   }
-  *n_q = P->n_eh[0];
-  *n_virtual = P->n_lag[0];
-  return P->d_terms + 7 * P->R_N;
+  *n_q = P->n_eh[cls];
+  *n_virtual = P->n_lag[cls];
+  return P->d_terms + (size_t)cls * kTermRows * P->R_N + 7 * P->R_N;
+}
+
+int lag_slices64(const cpc_kernel* P, int R_f, const double* U, const SliceRows& so, cudaStream_t s) {
+  const int L = P->n_lag[1];
+  if (L == 0) return CPC_OK;
+  const size_t smem = sizeof(double) * (size_t(P->n) + 2 * kMaxLags);
+  int st = configure(lag_slice64_kernel, smem);
+  if (st) return st;
+  int per_sm = 0;
+  CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lag_slice64_kernel, kLagThreads, smem));
+  const long long grid = std::max(1LL, std::min(3LL * R_f, (long long)std::max(1, per_sm) * sm_count()));
+  const int slot = timing_begin("lag_slice32_kernel", s);
+  lag_slice64_kernel<<<unsigned(grid), kLagThreads, smem, s>>>(U, P->n, R_f, P->R_N, L,
+                                                               P->d_terms + (size_t)kTermRows * P->R_N + 6 * P->R_N, so);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("lag_slice64_kernel");
+  return CPC_OK;
+}
+
+int launch_lag_gram64(const cpc_kernel* P, int R_f, const double* S, double* G, cudaStream_t s) {
+  const int L = P->n_lag[1];
+  if (L == 0) return CPC_OK;
+  const int nt = gram_tiles(R_f);
+  const dim3 grid(unsigned(nt * (nt + 1) / 2), unsigned(P->n_cov[1]));
+  const int* rows = P->d_terms + (size_t)kTermRows * P->R_N;
+  const int slot = timing_begin("lag_gram_kernel", s);
+  lag_gram64_kernel<<<grid, kGramThreads, 0, s>>>(R_f, P->R_N, L, rows + 6 * P->R_N, rows, P->d_taps64, S, G);
+  timing_end(slot, s);
+  CPC_LAUNCH_CHECK("lag_gram64_kernel");
+  return CPC_OK;
 }
 
 int lag_slices32(const cpc_kernel* P, int R_f, const double* U, const SliceRows& so, cudaStream_t s) {
