@@ -534,6 +534,7 @@ def run_ours(args, ws, rank, local):
                 "note": "convolution matrices of the smooth terms from their Chebyshev moments, "
                         "G_q = M^T (C_q M), K-term sums in double-float arithmetic (about 16 float32 "
                         "operations per multiply-add, not counted)"}
+    if prec in ("fp32", "fp64tc"):
         n_slice_products = 6 if prec == "fp32" else 15
         tc_ms, _ = per_launch("gemm3_tc_kernel", gram_ms)
         bf16_peak = float(peaks.get("bf16_tflops", 1900.0))

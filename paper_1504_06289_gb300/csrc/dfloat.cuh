@@ -12,6 +12,20 @@
 
 namespace cpc {
 
+// A float32 as float64, exactly, by integer work on the IEEE-754 fields (the
+// exponent rebiased from 127 to 1023, the mantissa moved to the top of the
+// 52-bit field): no conversion instruction, which like the float64
+// arithmetic runs at a small fraction of the float32 rate on this GPU.
+// Subnormal floats (below 2^-126) are taken as zero.
+__device__ __forceinline__ double double_of_float_exact(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e = (b >> 23) & 0xFFu;
+  if (e == 0) return 0.0;
+  const unsigned long long ed = e == 0xFFu ? 0x7FFull : (unsigned long long)(e + 896u);
+  return __longlong_as_double((long long)(((unsigned long long)(b >> 31) << 63) | (ed << 52) |
+                                          ((unsigned long long)(b & 0x7FFFFFu) << 29)));
+}
+
 struct __align__(8) df {
   float hi, lo;
   __host__ __device__ df() : hi(0.0f), lo(0.0f) {}
@@ -19,6 +33,9 @@ struct __align__(8) df {
   // exact split of a double into its leading float and the rounded rest
   __host__ __device__ explicit df(double d) : hi(float(d)), lo(float(d - double(float(d)))) {}
   __host__ __device__ explicit df(int i) : df(double(i)) {}
+  // hi + lo rounded to float64 (the conversion instructions: in the
+  // double-float FFT, whose float32 pipes are the busy ones, they measured
+  // faster than double_of_float_exact)
   __host__ __device__ double to_double() const { return double(hi) + double(lo); }
 };
 

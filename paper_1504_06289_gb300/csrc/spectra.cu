@@ -613,10 +613,89 @@ __device__ __forceinline__ T band_dispatch(int h, const T* us, int n, const void
   }
 }
 
+// Double-float arithmetic for the float64-accurate forms CPC_SPLIT and
+// CPC_FP64_TC (dfloat.cuh; the float64 pipe of this GPU runs at 1/64 of the
+// float32 rate): a product of a double-float tap or coefficient with a
+// double-float value, taken as hi + lo (the exact error of the leading
+// product by the fused multiply-add plus the cross terms), added to a running
+// sum kept as a TwoSum hi part and a float lo part; the sum is rounded to
+// float64 once at the end.  About 2^-47 of each product; at most 33 products.
+__device__ __forceinline__ void df_acc(float& h, float& l, float2 p, float sh, float sl) {
+  const float pr = p.x * sh;
+  const float e = fmaf(p.x, sl, fmaf(p.y, sh, fmaf(p.x, sh, -pr)));
+  const float t = h + pr, v = t - h;
+  l += ((h - (t - v)) + (pr - v)) + e;
+  h = t;
+}
+// a + b of two double-float values (TwoSum of the hi parts, the lo parts added)
+__device__ __forceinline__ float2 df_add2(float2 a, float2 b) {
+  const float s = a.x + b.x, v = s - a.x;
+  return make_float2(s, ((a.x - (s - v)) + (b.x - v)) + (a.y + b.y));
+}
+
+// The banded sum in double-float: the column staged as (hi, lo) pairs, taps
+// p_q[m] as the float32 class's (hi, lo) pairs, W written in float64 and, for
+// CPC_FP64_TC, sliced as computed (BandSlice64) with the row exponent from the
+// bound sum_m |p_q[m]| max|U|, here summed in float32 with a 2^-16 margin.
+template <int H, bool SLICE>
+__device__ __forceinline__ void band_rows_df(const float2* __restrict__ us, int n, const float2* __restrict__ tp,
+                                             double* __restrict__ w, const BandSlice64& b64) {
+  float2 p[H + 1];
+#pragma unroll
+  for (int m = 0; m <= H; ++m) p[m] = __ldg(tp + m);
+  int e64 = 0;
+  if constexpr (SLICE) if (b64.ob) {
+    float S = fabsf(p[0].x);
+#pragma unroll
+    for (int m = 1; m <= H; ++m) S += 2.0f * fabsf(p[m].x);
+    e64 = row_exponent64(biased_exponent64(double(S) * b64.umax * (1.0 + 0x1p-16)));
+    if (threadIdx.x == 0) *b64.expo = e64;
+  }
+  for (int i = 2 * threadIdx.x; i < n; i += 2 * kBandThreads) {
+    // cells i - H .. i + 1 + H, read from shared memory (a register window of
+    // 2 H + 2 pairs would spill)
+    const float2* u = us + kBandHalo + i;
+    float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+    // smallest taps first
+#pragma unroll
+    for (int m = H; m >= 1; --m) {
+      const float2 s0 = df_add2(u[-m], u[m]);
+      const float2 s1 = df_add2(u[1 - m], u[1 + m]);
+      df_acc(h0, l0, p[m], s0.x, s0.y);
+      df_acc(h1, l1, p[m], s1.x, s1.y);
+    }
+    const float2 c0 = u[0], c1 = u[1];
+    df_acc(h0, l0, p[0], c0.x, c0.y);
+    df_acc(h1, l1, p[0], c1.x, c1.y);
+    const double a0 = double_of_float_exact(h0) + double_of_float_exact(l0);
+    const double a1 = double_of_float_exact(h1) + double_of_float_exact(l1);
+    __stcs(reinterpret_cast<double2*>(w + i), make_double2(a0, a1));
+    if constexpr (SLICE) {
+      if (b64.ob) {
+        constexpr int C = kSlice64Cells;
+        slice64_pair(a0, a1, e64, b64.ob + (long long)(i / C) * b64.R_f * C + (i % C), b64.stride);
+      }
+    }
+  }
+}
+
+template <bool SLICE, int K = 0>
+__device__ __forceinline__ void band_dispatch_df(int h, const float2* us, int n, const float2* tq, double* w,
+                                                 const BandSlice64& b64) {
+  if constexpr (K == kBandNumWidths - 1) {
+    band_rows_df<band_width(K), SLICE>(us, n, tq, w, b64);
+  } else {
+    if (h == band_width(K)) return band_rows_df<band_width(K), SLICE>(us, n, tq, w, b64);
+    band_dispatch_df<SLICE, K + 1>(h, us, n, tq, w, b64);
+  }
+}
+
 // U: [ncols][n] float64 factor columns; items (col, j), j < n_band, term
 // qlist[j] with half-width hq[qlist[j]] (a value of band_width); taps:
-// [R_N][kBandTaps] (float32 W: float2, float64 W: double); W row col R_N + q.
-template <typename T, bool SLICE>
+// [R_N][kBandTaps] (float32 W and DF: float2 (hi, lo), float64 W: double); W
+// row col R_N + q.  DF (float64 W only): double-float arithmetic
+// (band_rows_df), the column staged as (hi, lo) pairs.
+template <typename T, bool SLICE, bool DF = false>
 __global__ void __launch_bounds__(kBandThreads, 2)
 band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const int* __restrict__ qlist, int n_band,
                  const int* __restrict__ hq, const void* __restrict__ taps, T* __restrict__ W, SliceOut so,
@@ -647,7 +726,13 @@ band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const 
       double um = 0.0;
       for (int j = threadIdx.x; j < n / 2; j += kBandThreads) {
         const double2 v = src[j];
-        *reinterpret_cast<V*>(us + kBandHalo + 2 * j) = cmk<V>(T(v.x), T(v.y));
+        if constexpr (DF) {
+          const df d0(v.x), d1(v.y);
+          *reinterpret_cast<float4*>(reinterpret_cast<float2*>(us) + kBandHalo + 2 * j) =
+              make_float4(d0.hi, d0.lo, d1.hi, d1.lo);
+        } else {
+          *reinterpret_cast<V*>(us + kBandHalo + 2 * j) = cmk<V>(T(v.x), T(v.y));
+        }
         if constexpr (SLICE && sizeof(T) == 8) um = fmax(um, fmax(fabs(v.x), fabs(v.y)));
       }
       if constexpr (SLICE && sizeof(T) == 8) {
@@ -674,7 +759,14 @@ band_conv_kernel(const double* __restrict__ U, int n, int ncols, int R_N, const 
       b64 = BandSlice64{so.out + ((long long)(l * R_N + q) * (n / C) * so.R_f + srow) * C, so.slice_stride, so.R_f,
                         so.expo + item, umax};
     }
-    T mx = band_dispatch<T, SLICE>(h, us, n, tq, W + (size_t)item * n, ws, b64);
+    T mx = T(0);
+    if constexpr (DF) {
+      static_assert(sizeof(T) == 8, "double-float banded sums write float64 W");
+      band_dispatch_df<SLICE>(h, reinterpret_cast<const float2*>(us), n,
+                              static_cast<const float2*>(taps) + (size_t)q * kBandTaps, W + (size_t)item * n, b64);
+    } else {
+      mx = band_dispatch<T, SLICE>(h, us, n, tq, W + (size_t)item * n, ws, b64);
+    }
     // float32: the terms with H < slice_min_h get no slices (their Gram
     // matrices come from the lag Gram matrices); h is the same for the CTA
     if constexpr (SLICE && sizeof(T) == 4) if (h >= slice_min_h) {
@@ -881,24 +973,45 @@ __device__ __forceinline__ void cheb_pair(const typename cvec<T>::type* dk, cons
   }
 }
 
+// the double-float evaluation (float64 W of CPC_SPLIT and CPC_FP64_TC): the
+// coefficients as (hi, lo) pairs (dk2[r]: d_2r and d_2r+1), the table as the
+// float32 class's (hi, lo) pairs, sums as df_acc, W rounded to float64 once
+template <int K>
+__device__ __forceinline__ void cheb_pair_df(const float4* dk2, const float4* t32, double& w0, double& w1) {
+  float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
+#pragma unroll
+  for (int r = K / 2 - 1; r >= 0; --r) {
+    const float4 d = dk2[r];
+    const float2 dh = make_float2(d.z, d.w), dl = make_float2(d.x, d.y);
+    df_acc(h0, l0, dh, t32[2 * r + 1].x, t32[2 * r + 1].y);
+    df_acc(h1, l1, dh, t32[2 * r + 1].z, t32[2 * r + 1].w);
+    df_acc(h0, l0, dl, t32[2 * r].x, t32[2 * r].y);
+    df_acc(h1, l1, dl, t32[2 * r].z, t32[2 * r].w);
+  }
+  w0 = double_of_float_exact(h0) + double_of_float_exact(l0);
+  w1 = double_of_float_exact(h1) + double_of_float_exact(l1);
+}
+
 // grid: x = 512-cell blocks of the rows, y = ranges of items (col, j); the
 // records (d row and header) of kChebBatch items at a time are staged in
 // shared memory with coalesced loads, then every thread evaluates its two
-// cells for each of them
+// cells for each of them.  DF (float64 W only): D holds the coefficients as
+// double-float pairs and tcheb the float32 class's (hi, lo) table.
 constexpr int kChebBatch = 32;
-template <typename T>
+template <typename T, bool DF = false>
 __global__ void __launch_bounds__(kChebThreads, 2)
-cheb_eval_kernel(int n, int ncols, int n_smooth, const void* __restrict__ tcheb, const T* __restrict__ D,
+cheb_eval_kernel(int n, int ncols, int n_smooth, const void* __restrict__ tcheb, const void* __restrict__ D,
                  const ChebItem* __restrict__ items, T* __restrict__ W) {
   using V = typename cvec<T>::type;
-  __shared__ __align__(16) T sd[kChebBatch][kCheb];
+  static_assert(!DF || sizeof(T) == 8, "double-float evaluation writes float64 W");
+  __shared__ __align__(16) T sd[kChebBatch][kCheb];  // (DF: kCheb (hi, lo) pairs per row, the same bytes)
   __shared__ ChebItem sh[kChebBatch];
   const int i = blockIdx.x * 2 * kChebThreads + 2 * threadIdx.x;  // cells i, i+1
   const bool on = i < n;
   // this thread's table entries: T_k at cells i and i+1
-  float4 t32[sizeof(T) == 4 ? kCheb : 1];
-  double2 t64[sizeof(T) == 8 ? kCheb : 1];
-  if constexpr (sizeof(T) == 4) {
+  float4 t32[sizeof(T) == 4 || DF ? kCheb : 1];
+  double2 t64[sizeof(T) == 8 && !DF ? kCheb : 1];
+  if constexpr (sizeof(T) == 4 || DF) {
     const float2* tc = static_cast<const float2*>(tcheb);
 #pragma unroll
     for (int k = 0; k < kCheb; ++k)
@@ -918,7 +1031,7 @@ cheb_eval_kernel(int n, int ncols, int n_smooth, const void* __restrict__ tcheb,
       // d rows and records as 16-byte pieces
       constexpr int PIECES = kCheb * sizeof(T) / 16;
       constexpr int RP = sizeof(ChebItem) / 16;
-      const uint4* src = reinterpret_cast<const uint4*>(D + kb * kCheb);
+      const uint4* src = reinterpret_cast<const uint4*>(static_cast<const T*>(D) + kb * kCheb);
       uint4* dst = reinterpret_cast<uint4*>(&sd[0][0]);
       for (int x = threadIdx.x; x < nb * PIECES; x += kChebThreads) dst[x] = __ldg(src + x);
       const uint4* isrc = reinterpret_cast<const uint4*>(items + kb);
@@ -929,12 +1042,20 @@ cheb_eval_kernel(int n, int ncols, int n_smooth, const void* __restrict__ tcheb,
     if (!on) continue;
     for (int b = 0; b < nb; ++b) {
       const ChebItem& h = sh[b];
-      const V* dk = reinterpret_cast<const V*>(sd[b]);
       T w0, w1;
-      if (h.K <= 4) cheb_pair<T, 4>(dk, t32, t64, w0, w1);
-      else if (h.K <= 8) cheb_pair<T, 8>(dk, t32, t64, w0, w1);
-      else if (h.K <= 12) cheb_pair<T, 12>(dk, t32, t64, w0, w1);
-      else cheb_pair<T, 16>(dk, t32, t64, w0, w1);
+      if constexpr (DF) {
+        const float4* dk2 = reinterpret_cast<const float4*>(sd[b]);
+        if (h.K <= 4) cheb_pair_df<4>(dk2, t32, w0, w1);
+        else if (h.K <= 8) cheb_pair_df<8>(dk2, t32, w0, w1);
+        else if (h.K <= 12) cheb_pair_df<12>(dk2, t32, w0, w1);
+        else cheb_pair_df<16>(dk2, t32, w0, w1);
+      } else {
+        const V* dk = reinterpret_cast<const V*>(sd[b]);
+        if (h.K <= 4) cheb_pair<T, 4>(dk, t32, t64, w0, w1);
+        else if (h.K <= 8) cheb_pair<T, 8>(dk, t32, t64, w0, w1);
+        else if (h.K <= 12) cheb_pair<T, 12>(dk, t32, t64, w0, w1);
+        else cheb_pair<T, 16>(dk, t32, t64, w0, w1);
+      }
       __stcs(reinterpret_cast<V*>(W + h.w_off + i), cmk<V>(w0, w1));
     }
   }
@@ -1599,18 +1720,19 @@ int launch_conv(const cpc_kernel* P, int ncols, const void* Uhat, void* W, const
   return CPC_OK;
 }
 
-template <typename T, bool SLICE>
+// DF (float64 W): the banded sums in double-float arithmetic
+template <typename T, bool SLICE, bool DF = false>
 int launch_band(const cpc_kernel* P, int ncols, const double* U, T* W, const SliceOut& so, const TermSplit& ts,
                 cudaStream_t s, int slice_min_h = 0) {
   const size_t smem = sizeof(T) * (size_t(P->n) + 2 * kBandHalo) + (SLICE && sizeof(T) == 4 ? sizeof(float) * size_t(P->n) : 0);
-  auto kern = band_conv_kernel<T, SLICE>;
+  auto kern = band_conv_kernel<T, SLICE, DF>;
   int st = configure(kern, smem);
   if (st) return st;
   int per_sm = 0;
   CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBandThreads, smem));
   const long long items = (long long)ncols * ts.n_band;
   const long long grid = std::max(1LL, std::min(items, (long long)std::max(1, per_sm) * sm_count()));
-  const void* taps = sizeof(T) == 4 ? static_cast<const void*>(P->d_taps32) : static_cast<const void*>(P->d_taps64);
+  const void* taps = sizeof(T) == 4 || DF ? static_cast<const void*>(P->d_taps32) : static_cast<const void*>(P->d_taps64);
   const int slot = timing_begin("band_conv_kernel", s);
   kern<<<int(grid), kBandThreads, smem, s>>>(U, P->n, ncols, P->R_N, ts.band_q, ts.n_band, ts.band_h, taps, W, so,
                                              slice_min_h);
@@ -1750,7 +1872,8 @@ int dispatch_conv_df(int logn, const cpc_kernel* P, int ncols, const dfc* Uhat, 
   }
 }
 
-template <typename T>
+// DF (float64 W): the evaluation in double-float arithmetic
+template <typename T, bool DF = false>
 int launch_smooth(const cpc_kernel* P, int ncols, const double* U, T* W, const TermSplit& ts, void* scratch,
                   cudaStream_t s) {
   if (!scratch) return fail(CPC_ERR_WORKSPACE, "conv: the Chebyshev path needs its scratch");
@@ -1773,12 +1896,14 @@ int launch_smooth(const cpc_kernel* P, int ncols, const double* U, T* W, const T
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("cheb_coef_kernel");
   slot = timing_begin("cheb_eval_kernel", s);
-  auto kern = cheb_eval_kernel<T>;
+  auto kern = cheb_eval_kernel<T, DF>;
   int per_sm = 0;
   CPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kChebThreads, 0));
   const int bx = std::max(1, n / (2 * kChebThreads));
   const long long by = std::max(1LL, std::min(items, ((long long)std::max(1, per_sm) * sm_count() + bx - 1) / bx));
-  kern<<<dim3(bx, unsigned(by)), kChebThreads, 0, s>>>(n, ncols, ts.n_smooth, tcheb, D, recs, W);
+  const void* te = DF ? static_cast<const void*>(P->d_tcheb32) : tcheb;
+  const void* De = DF ? static_cast<const void*>(sm.Ddf) : static_cast<const void*>(D);
+  kern<<<dim3(bx, unsigned(by)), kChebThreads, 0, s>>>(n, ncols, ts.n_smooth, te, De, recs, W);
   timing_end(slot, s);
   CPC_LAUNCH_CHECK("cheb_eval_kernel");
   return CPC_OK;
@@ -2153,12 +2278,12 @@ int convolve_spectra_df(const cpc_kernel* P, int ncols, void* Uhat, double* W, c
   int st = CPC_OK;
   if (ts.n_band > 0) {
     // (FP64_TC: the lag-covered terms get no slices)
-    st = so64 ? launch_band<double, true>(P, ncols, U, W, so, ts, s, P->n_lag[1])
-              : launch_band<double, false>(P, ncols, U, W, so, ts, s);
+    st = so64 ? launch_band<double, true, true>(P, ncols, U, W, so, ts, s, P->n_lag[1])
+              : launch_band<double, false, true>(P, ncols, U, W, so, ts, s);
     if (st) return st;
   }
   if (ts.n_smooth > 0) {
-    st = launch_smooth<double>(P, ncols, U, W, ts, scratch, s);  // no slices (see run_conv)
+    st = launch_smooth<double, true>(P, ncols, U, W, ts, scratch, s);  // no slices (see run_conv)
     if (st) return st;
   }
   if (ts.n_fft > 0) {
