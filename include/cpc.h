@@ -146,6 +146,20 @@ int cpc_kernel_conv_paths(const cpc_kernel* P, int precision, int* half_width, i
 int make_newton_kernel_paths(int n, double b, int M, int max_half_width32, int max_half_width64, int max_rank32,
                              int max_rank64, int* half_width, int* rank, double* cheb);
 
+/* The energy paths' contraction plan of the same kernel, host only:
+ * plan[2][3] (HOST array; row 0: float32 W, row 1: float64 W) = the number
+ * L of lag Gram matrices S_m = U^T (U shifted by +m plus U shifted by -m),
+ * m < L (L minimises L plus the number of banded terms with half-width
+ * >= L, at most 8, with at least L terms below it), the number of banded
+ * terms with half-width < L whose convolution matrices are the sums
+ * sum_{m <= H} p_q[m] S_m (Sec. 3.2 Eq. Factor_Mk_Conv with the banded sum
+ * of Sec. 2.5 Eq. conv), and the number of rows the tensor-core contraction
+ * takes over the cells (banded terms with half-width >= L, FFT terms, L lag
+ * rows; the smooth terms' matrices come from their Chebyshev moments).  The
+ * FP32 and FP64_TC energy paths (cp_hartree_energy) use rows 0 and 1. */
+int make_newton_kernel_eh_plan(int n, double b, int M, int max_half_width32, int max_half_width64, int max_rank32,
+                               int max_rank64, int* plan);
+
 /* ---- a3: grid sampling of Gaussians (Sec. 3.1, Eq. disc_GTO) --------------
  * U[l][k][i] = exp(-a_k (x_i - X[k][l])^2) for R Gaussians exp(-a_k |x - X_k|^2).
  * a: [R], X: [R][3] (row k holds X_k), U: [3][R][n]; all float64 device. */

@@ -26,6 +26,7 @@ __all__ = [
     "cp_factor_spectra", "cp_convolve_from_spectra", "cp_hartree_energy_from_spectra",
     "cp_hartree_energy_noalloc", "cp_hartree_energy_adjoint", "cp_gaussian_param_grad",
     "coulomb_matrix", "nuclear_matrix", "tei_cholesky", "tei_coulomb", "tei_exchange", "lattice_potential_sum", "lattice_interaction_energy", "CPHartreeEnergy", "CpcError",
+    "make_newton_kernel_paths", "make_newton_kernel_eh_plan",
 ]
 
 
@@ -125,6 +126,18 @@ def make_newton_kernel_tables(n: int, b: float, M: int, kind: str = "conv"):
     check(load().make_newton_kernel_tables(int(n), float(b), int(M), KIND[kind], t.ctypes.data, a.ctypes.data,
                                            p.ctypes.data, C.byref(hs), C.byref(u0)), "make_newton_kernel_tables")
     return t, a, p, hs.value, u0.value
+
+
+def make_newton_kernel_eh_plan(n: int, b: float, M: int, max_half_width32: int = 20, max_half_width64: int = 24,
+                               max_rank32: int = 16, max_rank64: int = 16):
+    """Host-only contraction plan of the energy paths: an int array (2, 3), per W type
+    (row 0 float32, row 1 float64) the lag count L, the banded terms it covers and the
+    rows the tensor-core contraction takes over the cells."""
+    plan = np.empty((2, 3), dtype=np.int32)
+    check(load().make_newton_kernel_eh_plan(int(n), float(b), int(M), int(max_half_width32), int(max_half_width64),
+                                            int(max_rank32), int(max_rank64), plan.ctypes.data),
+          "make_newton_kernel_eh_plan")
+    return plan
 
 
 def make_newton_kernel_paths(n: int, b: float, M: int, max_half_width32: int = 20, max_half_width64: int = 24,

@@ -23,6 +23,7 @@ PROTOTYPES = {
     "cpc_kernel_set_conv_paths": (i32, [vp, i32, i32, i32, i32, vp]),
     "cpc_kernel_conv_paths": (i32, [vp, i32, vp, vp]),
     "make_newton_kernel_paths": (i32, [i32, f64, i32, i32, i32, i32, i32, vp, vp, vp]),
+    "make_newton_kernel_eh_plan": (i32, [i32, f64, i32, i32, i32, i32, i32, vp]),
     "cp_sample_gaussians": (i32, [i32, f64, i32, vp, vp, vp, vp]),
     "cp_hadamard_pairs": (i32, [i32, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp]),
     "cp_convolve_workspace": (sz, [vp, i32, i32]),

@@ -241,20 +241,47 @@ int make_newton_kernel_tables(int n, double b, int M, int kind, double* t, doubl
   return CPC_OK;
 }
 
-int make_newton_kernel_paths(int n, double b, int M, int max_half_width32, int max_half_width64, int max_rank32,
-                             int max_rank64, int* half_width, int* rank, double* cheb) {
-  clear_error();
-  int st = validate_kernel_args(n, b, M, CPC_KERNEL_CONV, "make_newton_kernel_paths");
+// the host path plan of a CONV kernel of make_newton_kernel(n, b, M), with no
+// device work (make_newton_kernel_paths, make_newton_kernel_eh_plan)
+static int host_plan(int n, double b, int M, int max_half_width32, int max_half_width64, int max_rank32,
+                     int max_rank64, const char* who, cpc_kernel& K, TermPlan& tp) {
+  int st = validate_kernel_args(n, b, M, CPC_KERNEL_CONV, who);
   if (st) return st;
   if (max_half_width32 < -1 || max_half_width32 > 32 || max_half_width64 < -1 || max_half_width64 > 32 ||
       max_rank32 < -1 || max_rank32 > 16 || max_rank64 < -1 || max_rank64 > 16)
-    return fail(CPC_ERR_INVALID, "make_newton_kernel_paths: half-widths in [-1, 32], ranks in [-1, 16]");
-  cpc_kernel K;
+    return fail(CPC_ERR_INVALID, std::string(who) + ": half-widths in [-1, 32], ranks in [-1, 16]");
   K.n = n; K.b = b; K.h = 2.0 * b / n; K.M = M; K.R_N = 2 * M + 1; K.kind = CPC_KERNEL_CONV;
   K.len = n;
   host_tables(&K);
-  TermPlan tp;
   plan_term_paths(&K, max_half_width32, max_half_width64, max_rank32, max_rank64, tp);
+  return CPC_OK;
+}
+
+int make_newton_kernel_eh_plan(int n, double b, int M, int max_half_width32, int max_half_width64, int max_rank32,
+                               int max_rank64, int* plan) {
+  clear_error();
+  if (!plan) return fail(CPC_ERR_INVALID, "make_newton_kernel_eh_plan: plan is NULL");
+  cpc_kernel K;
+  TermPlan tp;
+  int st = host_plan(n, b, M, max_half_width32, max_half_width64, max_rank32, max_rank64,
+                     "make_newton_kernel_eh_plan", K, tp);
+  if (st) return st;
+  for (int cls = 0; cls < 2; ++cls) {
+    plan[3 * cls] = tp.n_lag[cls];
+    plan[3 * cls + 1] = tp.n_cov[cls];
+    plan[3 * cls + 2] = tp.n_eh[cls];
+  }
+  return CPC_OK;
+}
+
+int make_newton_kernel_paths(int n, double b, int M, int max_half_width32, int max_half_width64, int max_rank32,
+                             int max_rank64, int* half_width, int* rank, double* cheb) {
+  clear_error();
+  cpc_kernel K;
+  TermPlan tp;
+  int st = host_plan(n, b, M, max_half_width32, max_half_width64, max_rank32, max_rank64,
+                     "make_newton_kernel_paths", K, tp);
+  if (st) return st;
   for (int cls = 0; cls < 2; ++cls)
     for (int q = 0; q < K.R_N; ++q) {
       if (half_width) half_width[cls * K.R_N + q] = tp.terms[size_t(cls) * kTermRows * K.R_N + q];

@@ -110,3 +110,33 @@ def test_limits_switch_paths_off(cpc):
     for bad in ((33, 24, 16, 16), (20, -2, 16, 16), (20, 24, 17, 16), (20, 24, 16, -2)):
         with pytest.raises(CpcError):
             cpc.make_newton_kernel_paths(256, 6.0, 12, *bad)
+
+
+@pytest.mark.parametrize("n,b,M", [(8192, 20.0, 30), (4096, 20.0, 25), (256, 6.0, 12), (1024, 8.0, 16)])
+def test_energy_path_lag_plan(cpc, n, b, M):
+    # the energy paths take the banded terms with half-width H < L from L lag
+    # Gram matrices S_m = U^T (U shifted by +-m), m < L (G_q = sum_{m<=H}
+    # p_q[m] S_m, exact algebra of the banded sum): L must minimise the rows
+    # contracted over the cells, L + #(banded terms with H >= L), over
+    # 0 <= L <= 8 with at least L covered terms (their slice slots hold the
+    # lag rows), and the row count must add up with the FFT terms
+    hw, rk, _ = cpc.make_newton_kernel_paths(n, b, M)
+    plan = cpc.make_newton_kernel_eh_plan(n, b, M)
+    R_N = 2 * M + 1
+    for cls in (0, 1):
+        h = [int(x) for x in hw[cls] if x >= 0]
+        n_smooth = int((rk[cls] > 0).sum())
+        n_fft = R_N - len(h) - n_smooth
+        L, n_cov, n_eh = (int(x) for x in plan[cls])
+        feasible = [t for t in range(0, 9) if sum(x < t for x in h) >= t]
+        best = min(t + sum(x >= t for x in h) for t in feasible)
+        assert L in feasible and L + sum(x >= L for x in h) == best
+        # ties go to the smallest L (no lag rows unless they save a row)
+        assert all(t + sum(x >= t for x in h) > best for t in feasible if t < L)
+        assert n_cov == sum(x < L for x in h)
+        assert n_eh == (len(h) - n_cov) + n_fft + L
+    # the float32 class of the headline workload: half-widths 14, 10, 6, 4, 2,
+    # 2, 1, 1 and eight 0: three lags cover twelve terms, 24 rows
+    if (n, b, M) == (8192, 20.0, 30):
+        assert tuple(plan[0]) == (3, 12, 24)
+        assert tuple(plan[1]) == (2, 10, 26)
