@@ -37,26 +37,6 @@ TIMED = ("spectra_kernel", "conv_kernel", "band_conv_kernel", *CHEB, "slice_rows
          "cheb_gram_kernel", "lag_slice32_kernel", "lag_gram_kernel")
 
 
-def lag_count(hw):
-    """The float32 energy path's lag count L (the library's rule): L lag Gram
-    matrices cover the banded terms with half-width H < L; L minimises
-    L + (banded terms with H >= L), at most 8, with at least L covered terms."""
-    h = [int(x) for x in hw if x >= 0]
-    best, cost = 0, len(h)
-    for t in range(1, 9):
-        cov = sum(x < t for x in h)
-        if cov >= t and t + len(h) - cov < cost:
-            best, cost = t, t + len(h) - cov
-    return best, sum(x < best for x in h)
-METRIC = "1D factor convolutions/s"
-PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# GB300 unit counts for ALU roofs: 152 SMs, 128 FP32 lanes per SM (FMA = 2 flop)
-SMS = 152
-FP32_LANES = 128
-# nominal GB300 float64 CUDA-core rate (GFLOP/s): a context figure, not measured here
-FP64_PEAK_GFLOPS = 1250.0
-
-
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,6 +274,9 @@ def run_ours(args, ws, rank, local):
     R_N = P.R_N
     if args.conv_paths != "all":
         P.set_conv_paths(*({"band": (20, 24, -1, -1), "fft": (-1, -1, -1, -1)}[args.conv_paths]))
+    # the energy paths' lag plan (host only): per W type the lag count and the banded terms it covers
+    eh_plan = cpc.make_newton_kernel_eh_plan(
+        n, b, M, *({"all": (20, 24, 16, 16), "band": (20, 24, -1, -1), "fft": (-1, -1, -1, -1)}[args.conv_paths]))
     g = workloads.mixture_for(WORKLOAD, args.seed + rank)
     if args.rf:
         R_f = args.rf
@@ -508,7 +491,7 @@ def run_ours(args, ws, rank, local):
         n_dense = R_N - n_smooth
         if prec in ("fp32", "fp64tc"):
             # lag rows replace the covered banded terms in the cell contraction
-            n_lag, n_cov = lag_count(hw)
+            n_lag, n_cov = (int(x) for x in eh_plan[0 if prec == "fp32" else 1][:2])
             n_dense += n_lag - n_cov
             if n_lag:
                 ls_ms, _ = per_launch("lag_slice32_kernel", 0.0)
@@ -598,7 +581,7 @@ def run_ours(args, ws, rank, local):
         # [fp64tc: E_H from G,] final sum; banded conv; Chebyshev moments, coefficients,
         # evaluation [and the smooth terms' Gram matrices]
         "gpu_launches": ({"fp32": 6, "fp64tc": 8}.get(prec, 5) + (1 if n_band else 0)
-                         + (2 if prec in ("fp32", "fp64tc") and lag_count(hw)[0] else 0)
+                         + (2 if prec in ("fp32", "fp64tc") and eh_plan[0 if prec == "fp32" else 1][0] else 0)
                          + ((4 if prec in ("fp32", "fp64tc", "split") else 3) if n_smooth else 0)
                          - (0 if n_fft else 1)) * args.steps,
         "clocks": clk,
