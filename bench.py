@@ -35,6 +35,13 @@ WORKLOAD = "density600_n8192"
 CHEB = ("cheb_moments_kernel", "cheb_coef_kernel", "cheb_eval_kernel")
 TIMED = ("spectra_kernel", "conv_kernel", "band_conv_kernel", *CHEB, "slice_rows_kernel", "gemm3_tc_kernel",
          "cheb_gram_kernel", "lag_slice32_kernel", "lag_gram_kernel")
+METRIC = "1D factor convolutions/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# GB300 unit counts for ALU roofs: 152 SMs, 128 FP32 lanes per SM (FMA = 2 flop)
+SMS = 152
+FP32_LANES = 128
+# nominal GB300 float64 CUDA-core rate (GFLOP/s): a context figure, not measured here
+FP64_PEAK_GFLOPS = 1250.0
 
 
 def parse():
