@@ -217,6 +217,15 @@ int cp_convolve_from_spectra(const cpc_kernel* P, int R_f, const void* spec, voi
  * as float32 operands with float32 products); other n: float32 products on
  * CUDA cores.  CPC_SPLIT: float32
  * products of U and W (rounded on load), compensated float32 accumulation.
+ * CPC_FP64_TC: five weighted bf16 slices per float64 operand on the tensor
+ * cores, G in float64.  The same G by other orders of the same sums, in the
+ * CPC_FP32, CPC_SPLIT and CPC_FP64_TC forms: a smooth term's (Chebyshev path)
+ * from its moments, G[k'][k] = sum_j m_k'[j] d_k[j] with d_k = C_q m_k
+ * (double-float sums), and in CPC_FP32 and CPC_FP64_TC a narrow term's
+ * (banded path, half-width H below the plan's lag count L) from lag Gram
+ * matrices, G = sum_{m <= H} p_q[m] U^T (U shifted by +m plus U shifted by
+ * -m) (make_newton_kernel_eh_plan); the other terms are contracted over the
+ * cells.  CPC_FP64 contracts every term over the cells.
  * All forms reduce across tiles in float64.  If a device-side wait of the
  * tensor-core kernel gives up, E_H is written as NaN.  c: [R_f] float64.  G: NULL or
  * [3][R_N][R_f][R_f] float64 (needed by the adjoint).  E_H: one float64 on
