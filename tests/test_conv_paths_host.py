@@ -140,3 +140,68 @@ def test_energy_path_lag_plan(cpc, n, b, M):
     if (n, b, M) == (8192, 20.0, 30):
         assert tuple(plan[0]) == (3, 12, 24)
         assert tuple(plan[1]) == (2, 10, 26)
+
+
+def _gaussian_columns(n, b, count, seed):
+    rng = np.random.default_rng(seed)
+    x = -b + (np.arange(n) + 0.5) * (2 * b / n)
+    return np.stack([np.exp(-a * (x - c) ** 2)
+                     for a, c in zip(10 ** rng.uniform(-1, 1.5, count), rng.uniform(-1, 1, count))])
+
+
+@pytest.mark.parametrize("n,b,M", CONFIGS[:2])
+def test_gram_from_moments_matches_oracle(cpc, n, b, M):
+    """The energy paths' Gram matrices of smooth terms: G = m^T d with the K
+    moments m = T u of every column and d = C_q m (Sec. 3.2 Eq.
+    Factor_Mk_Conv on the separable form), against the oracle's U^T (p_q * U):
+    |dG[r][s]| <= eps p_q[0] sum|u_r| sum|u_s| (the fit bound, both sides)."""
+    hw, rk, cheb = cpc.make_newton_kernel_paths(n, b, M)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    T = cheb_table(n)
+    U = _gaussian_columns(n, b, 8, 11)
+    s1 = np.abs(U).sum(axis=1)
+    for cls in (0, 1):
+        for q in np.nonzero(rk[cls] > 0)[0]:
+            K = rk[cls, q]
+            m = T[:K] @ U.T                      # (K, cols)
+            G = m.T @ (cheb[q, :K, :K] @ m)      # (cols, cols)
+            G0 = U @ ocp.conv1d(U.T, P0[q])      # U^T (p_q * U) with cols as rows of U
+            bound = EPS[cls] * abs(P0[q][0]) * np.outer(s1, s1)
+            assert np.all(np.abs(G - G0) <= bound), (cls, q)
+            assert np.allclose(G, G.T, rtol=0, atol=1e-15 * np.abs(G).max())
+
+
+@pytest.mark.parametrize("n,b,M", CONFIGS[:2])
+def test_gram_from_lags_matches_oracle(cpc, n, b, M):
+    """The energy paths' Gram matrices of narrow terms: G_q = sum_{m <= H}
+    p_q[m] S_m with S_0 = U U^T, S_m = U (U shifted by +m plus U shifted by
+    -m)^T (zero outside the grid), for the terms the plan covers (H < L),
+    against the oracle's U^T (p_q * U) with p_q cut at H: the same sums in
+    another order (float64 rounding apart), and within the banded tail bound
+    of the untruncated p_q."""
+    hw, _, _ = cpc.make_newton_kernel_paths(n, b, M)
+    plan = cpc.make_newton_kernel_eh_plan(n, b, M)
+    _, _, P0 = oracle_conv_kernel(n, b, M)
+    U = _gaussian_columns(n, b, 8, 13)
+    for cls in (0, 1):
+        L = int(plan[cls][0])
+        assert L >= 1
+        S = []
+        for m in range(L):
+            V = U.copy() if m == 0 else np.zeros_like(U)
+            if m:
+                V[:, m:] += U[:, :-m]
+                V[:, :-m] += U[:, m:]
+            S.append(U @ V.T)
+        covered = [q for q in range(2 * M + 1) if 0 <= hw[cls, q] < L]
+        assert len(covered) == int(plan[cls][1])
+        for q in covered:
+            H = int(hw[cls, q])
+            G = sum(P0[q][m] * S[m] for m in range(H + 1))
+            p_cut = np.where(np.arange(n) <= H, P0[q], 0.0)
+            Gcut = U @ ocp.conv1d(U.T, p_cut)
+            assert np.max(np.abs(G - Gcut)) <= 1e-13 * np.max(np.abs(Gcut))
+            G0 = U @ ocp.conv1d(U.T, P0[q])
+            tail = TAU[cls] * (abs(P0[q][0]) + 2 * np.abs(P0[q][1:]).sum())
+            assert np.max(np.abs(G - G0)) <= tail * np.abs(U).sum(axis=1).max() * np.abs(U).max() + \
+                1e-13 * np.max(np.abs(G0))
